@@ -1,0 +1,358 @@
+"""Pins for the CPU oracle: each test checks the oracle against something
+other than itself (published test vectors, LAPACK through scipy, brute force,
+closed forms, exactness limits and the paper's theorems)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_1609_08130_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_vectors():
+    for row in _golden("splitmix64.txt"):
+        seed = int(row[0])
+        want = [int(v, 16) for v in row[1:]]
+        got = [int(v) for v in inputs.splitmix64(seed, len(want))]
+        assert got == want
+
+
+def test_normal_moments():
+    z = inputs.normal(7, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+    u = inputs.uniform(3, 100000)
+    assert u.min() >= 0.0 and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.01
+
+
+def test_grid_points_are_cell_centres():
+    p = inputs.grid_points(4, 2)
+    assert p.shape == (16, 2)
+    assert np.allclose(p[:4, 0], [0.125, 0.375, 0.625, 0.875]) and np.allclose(p[:4, 1], 0.125)
+    p3 = inputs.grid_points(4, 3)
+    assert p3.shape == (64, 3) and np.allclose(p3[16], [0.125, 0.125, 0.375])
+
+
+# ---------------------------------------------------------------------------
+# kernel entries
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,kind", [(2, 0), (3, 1)])
+def test_kernel_entries_match_libm(dim, kind):
+    pts = inputs.random_points(11, 40, dim)
+    A = oracle.dense_matrix(pts, kind, diag=1.0, w=0.5)
+    for i, j in [(0, 1), (3, 17), (39, 2), (5, 5)]:
+        if i == j:
+            want = 1.0
+        else:
+            r = math.dist(pts[i], pts[j])
+            want = 0.5 * (-math.log(r) / (2 * math.pi) if kind == 0 else 1.0 / (4 * math.pi * r))
+        assert A[i, j] == pytest.approx(want, rel=1e-15, abs=0)
+
+
+# ---------------------------------------------------------------------------
+# tree: properties that fix the tree and the DOF order uniquely
+# ---------------------------------------------------------------------------
+
+def _check_tree(pts, leaf):
+    tr = oracle.Tree(pts, leaf)
+    perm = tr.perm()
+    n, dim = pts.shape
+    assert sorted(perm.tolist()) == list(range(n))
+    nd = tr.nodes()
+    x = pts[perm]
+    children = {i: [] for i in range(tr.nnode)}
+    for i in range(1, tr.nnode):
+        children[int(nd["parent"][i])].append(i)
+    for i in range(tr.nnode):
+        t = int(nd["depth"][i])
+        s, c = int(nd["start"][i]), int(nd["count"][i])
+        lo = nd["coord"][i, :dim] * 2.0 ** -t
+        hi = lo + 2.0 ** -t
+        seg = x[s:s + c]
+        assert np.all(seg >= lo) and np.all((seg < hi) | (hi >= 1.0))
+        ch = children[i]
+        if c > leaf and t < 20:
+            assert ch, "over-full node must be split"
+            # children partition the range in ascending child index
+            assert int(nd["start"][ch[0]]) == s
+            idx = [sum(((int(nd["coord"][q, d]) & 1) << d) for d in range(dim)) for q in ch]
+            assert idx == sorted(idx)
+            end = s
+            for q in ch:
+                assert int(nd["start"][q]) == end
+                end += int(nd["count"][q])
+            assert end == s + c
+        else:
+            assert not ch
+            # stable: original indices ascending inside a leaf
+            assert np.all(np.diff(perm[s:s + c]) > 0)
+    return tr, nd
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "random2d"])
+def test_tree_structure(case):
+    if case == "grid2d":
+        pts, leaf = inputs.grid_points(32, 2), 64
+    elif case == "grid3d":
+        pts, leaf = inputs.grid_points(16, 3), 64
+    else:
+        pts, leaf = inputs.random_points(5, 3000, 2), 64
+    tr, nd = _check_tree(pts, leaf)
+    if case == "grid2d":
+        assert tr.maxdepth == 2 and (nd["depth"] == 2).sum() == 16
+    if case == "grid3d":
+        assert tr.maxdepth == 2 and (nd["depth"] == 2).sum() == 64
+
+
+def test_box_order_and_lists_brute_force():
+    """Level order is colour-major (3^d colours) with same-colour boxes >= 3
+    apart; near / ring cell lists equal a brute-force pairwise classification
+    (Fig. 2); interior counts equal the closed forms."""
+    golden = {int(r[0]): (int(r[1]), int(r[2])) for r in _golden("neighbor_counts.txt")}
+    for pts, dim in [(inputs.grid_points(64, 2), 2), (inputs.grid_points(16, 3), 3),
+                     (inputs.random_points(9, 5000, 2), 2)]:
+        tr = oracle.Tree(pts, 64)
+        nd = tr.nodes()
+        x = pts[tr.perm()]
+        for t in range(tr.maxdepth, 1, -1):
+            boxes = tr.level_boxes(t)
+            assert sorted(boxes.tolist()) == sorted(np.nonzero(nd["depth"] == t)[0].tolist())
+            cols = [sum((int(nd["coord"][b, d]) % 3) * 3 ** d for d in range(dim)) for b in boxes]
+            assert cols == sorted(cols)
+            cells = np.minimum(np.floor(x * 2 ** t).astype(np.int64), 2 ** t - 1)
+            for q, b in enumerate(boxes):
+                bc = nd["coord"][b, :dim]
+                for q2 in range(q + 1, len(boxes)):
+                    if cols[q2] != cols[q]:
+                        break
+                    assert np.abs(nd["coord"][boxes[q2], :dim] - bc).max() >= 3
+                delta = cells - bc
+                dist = np.abs(delta).max(axis=1)
+                codes = ((delta + 2) * (5 ** np.arange(dim))).sum(axis=1)
+                want_near = sorted(set(codes[dist == 1].tolist()))
+                want_ring = sorted(set(codes[dist == 2].tolist()))
+                near, ring = tr.box_lists(int(b))
+                assert near.tolist() == want_near and ring.tolist() == want_ring
+                if np.all(bc >= 2) and np.all(bc <= 2 ** t - 3) and dim in golden and pts.shape[0] in (4096,):
+                    assert (len(near), len(ring)) == golden[dim]
+
+
+# ---------------------------------------------------------------------------
+# dense building blocks against LAPACK
+# ---------------------------------------------------------------------------
+
+def test_cpqr_matches_lapack_pivots():
+    rng = np.random.default_rng(0)
+    for m, n in [(50, 20), (200, 64), (30, 40)]:
+        M = rng.standard_normal((m, n)) @ np.diag(np.logspace(0, -8, n)) @ rng.standard_normal((n, n))
+        k, perm, T, rd = oracle.cpqr_id(M, 0.0)
+        _, R, P = sla.qr(M, pivoting=True, mode="economic")
+        kk = min(m, n)
+        # greedy pivoting: same first pivots as LAPACK's dgeqp3 on generic data
+        assert perm[:10].tolist() == P[:10].tolist()
+        assert np.allclose(rd[:kk], np.abs(np.diag(R))[:kk], rtol=1e-6, atol=1e-12 * rd[0])
+
+
+def test_cpqr_id_bound_and_rank():
+    rng = np.random.default_rng(1)
+    # exactly rank 5
+    M = rng.standard_normal((80, 5)) @ rng.standard_normal((5, 30))
+    k, perm, T, rd = oracle.cpqr_id(M, 1e-10)
+    assert k == 5
+    assert np.allclose(M[:, perm[k:]], M[:, perm[:k]] @ T, atol=1e-10 * np.abs(M).max())
+    # decaying spectrum: ||M_R - M_S T||_2 <= sqrt(n-k) eps |R_11| (greedy pivoting)
+    U, _ = np.linalg.qr(rng.standard_normal((300, 60)))
+    V, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    M = U @ np.diag(np.logspace(0, -14, 60)) @ V.T
+    for eps in [1e-3, 1e-6, 1e-9]:
+        k, perm, T, rd = oracle.cpqr_id(M, eps)
+        err = np.linalg.norm(M[:, perm[k:]] - M[:, perm[:k]] @ T, 2)
+        assert err <= math.sqrt(60 - k) * eps * rd[0] * 1.0001
+        assert rd[k - 1] > eps * rd[0] and (k == 60 or rd[k] <= eps * rd[0])
+    # zero matrix: rank 0
+    k, perm, T, rd = oracle.cpqr_id(np.zeros((10, 4)), 1e-6)
+    assert k == 0
+
+
+def test_lu_matches_lapack():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((37, 37))
+    LU, piv, info = oracle.lu(A)
+    lu_ref, piv_ref = sla.lu_factor(A)
+    perm_ref = np.arange(37)
+    for i, p in enumerate(piv_ref):
+        perm_ref[[i, p]] = perm_ref[[p, i]]
+    assert info == 0
+    assert piv.tolist() == perm_ref.tolist()
+    assert np.allclose(LU, lu_ref, rtol=1e-12, atol=1e-12)
+    S = np.ones((3, 3))
+    assert oracle.lu(S)[2] != 0
+
+
+def test_dense_solve_backward_error():
+    pts = inputs.grid_points(24, 2)
+    A = oracle.dense_matrix(pts, 0)
+    b = inputs.normal(1, len(pts))
+    x = oracle.dense_solve(A, b)
+    n = len(pts)
+    assert np.linalg.norm(A @ x - b) / (np.linalg.norm(A, 2) * np.linalg.norm(x)) <= 10 * n * 1.1e-16
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-12, atol=1e-12)
+
+
+def test_matvec_matches_dense():
+    pts = inputs.random_points(4, 300, 3)
+    x = inputs.normal(2, 300)
+    A = oracle.dense_matrix(pts, 1)
+    assert np.allclose(oracle.matvec(pts, 1, x), A @ x, rtol=1e-13, atol=1e-13)
+    rows = np.array([5, 0, 299])
+    assert np.allclose(oracle.matvec(pts, 1, x, rows=rows), (A @ x)[rows], rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# RS-S factorization (Algorithm 1)
+# ---------------------------------------------------------------------------
+
+def _problem(case):
+    if case == "grid2d":
+        return inputs.grid_points(64, 2), 0
+    if case == "grid3d":
+        return inputs.grid_points(16, 3), 1
+    if case == "random2d":
+        return inputs.random_points(21, 3000, 2), 0
+    raise KeyError(case)
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "random2d"])
+def test_factor_exact_limit(case):
+    """eps -> 0: every step is exact block elimination (Sec. 2.1), so F = A
+    and F^{-1} b equals the dense solve (Eq. 3.10, 3.11)."""
+    pts, kind = _problem(case)
+    n = len(pts)
+    tr = oracle.Tree(pts, 64)
+    f = oracle.Factor(tr, kind, 1e-14)
+    assert f.info == 0
+    A = oracle.dense_matrix(pts, kind)
+    x = inputs.normal(3, n)
+    assert np.linalg.norm(f.apply(x) - A @ x) / np.linalg.norm(A @ x) < 1e-12
+    b = inputs.normal(4, n)
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(f.solve(b) - xs) / np.linalg.norm(xs) < 1e-11
+    sign, ld = np.linalg.slogdet(A)
+    assert abs(f.logdet() - ld) < 1e-9 * max(1.0, abs(ld))
+
+
+def test_factor_without_compression_is_exact():
+    """eps = 0 keeps every column as skeleton (k = |B|): F = A."""
+    pts, kind = _problem("grid2d")
+    tr = oracle.Tree(pts[::4].copy(), 64)
+    f = oracle.Factor(tr, kind, 0.0)
+    for b in f.boxes():
+        assert b["r"] == 0 or b["k"] == b["b"]
+    p = pts[::4]
+    A = oracle.dense_matrix(p, kind)
+    x = inputs.normal(5, len(p))
+    assert np.allclose(f.apply(x), A @ x, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "random2d"])
+def test_factor_invariants(case):
+    """Theorem 3.1 (B-P interactions untouched), Corollary 3.2 (far field
+    original at each level start) and the final block-diagonal form of D
+    (Sec. 3.3.3), all checked on the whole matrix, bit for bit."""
+    pts, kind = _problem(case)
+    if len(pts) > 2000:
+        pts = pts[: len(pts) // 2] if case != "grid2d" else inputs.grid_points(32, 2)
+    tr = oracle.Tree(pts, 16 if case == "grid2d" else 32)
+    f = oracle.Factor(tr, kind, 1e-6, check=True)
+    assert f.nbox > 0 and f.violations == 0
+
+
+@pytest.mark.parametrize("case,eps", [("grid2d", 1e-6), ("grid2d", 1e-3), ("grid3d", 1e-3),
+                                      ("random2d", 1e-6)])
+def test_factor_accuracy_band(case, eps):
+    """The paper's tables show e_a ~ O(eps) (Tables 2 and 4); with the
+    second-kind scaling here the apply error must stay below eps."""
+    pts, kind = _problem(case)
+    n = len(pts)
+    tr = oracle.Tree(pts, 64)
+    f = oracle.Factor(tr, kind, eps)
+    x = inputs.normal(6, n)
+    Ax = oracle.matvec(pts, kind, x)
+    ea = np.linalg.norm(f.apply(x) - Ax) / np.linalg.norm(Ax)
+    assert ea < eps
+    xs = f.solve(Ax)
+    assert np.linalg.norm(xs - x) / np.linalg.norm(x) < 10 * eps
+    # some compression actually happened
+    assert sum(b["r"] for b in f.boxes()) > n // 4
+
+
+def test_apply_and_solve_are_inverse():
+    """F^{-1} (F x) = x independently of eps (the factors are exact inverses
+    of one another, Eq. 3.10 vs 3.11)."""
+    pts, kind = _problem("random2d")
+    tr = oracle.Tree(pts, 64)
+    f = oracle.Factor(tr, kind, 1e-3)
+    x = inputs.normal(8, len(pts))
+    assert np.linalg.norm(f.solve(f.apply(x)) - x) / np.linalg.norm(x) < 1e-12
+
+
+def test_symmetric_factors():
+    """K symmetric => V_i = W_i^T (Sec. 3.3.3): E = G^T up to rounding."""
+    pts, kind = _problem("grid2d")
+    tr = oracle.Tree(pts, 64)
+    f = oracle.Factor(tr, kind, 1e-6)
+    for i in range(0, f.nbox, 7):
+        d = f.box_data(i)
+        if d["r"]:
+            assert np.allclose(d["E"], d["G"].T, rtol=1e-9, atol=1e-12 * np.abs(d["E"]).max())
+
+
+def test_proxy_surface_is_needed():
+    """Planted mistake in the oracle's inputs: with only 4 proxy points the
+    discretised Green's identity (Eq. 3.5, 3.6) cannot stand in for the far
+    field outside the proxy surface, so the IDs stop compressing the true far
+    field and the apply error must rise well above the one with the paper's
+    64 points (Sec. 4, Example 1)."""
+    pts, kind = _problem("grid2d")
+    tr = oracle.Tree(pts, 64)
+    x = inputs.normal(9, len(pts))
+    Ax = oracle.matvec(pts, kind, x)
+    good = oracle.Factor(tr, kind, 1e-9, nproxy=64)
+    bad = oracle.Factor(tr, kind, 1e-9, nproxy=4)
+    eg = np.linalg.norm(good.apply(x) - Ax) / np.linalg.norm(Ax)
+    eb = np.linalg.norm(bad.apply(x) - Ax) / np.linalg.norm(Ax)
+    assert eb > 10 * eg
+
+
+def test_degenerate_sizes():
+    # fewer points than one leaf: no skeletonization, F = dense LU
+    pts = inputs.random_points(2, 50, 2)
+    tr = oracle.Tree(pts, 64)
+    f = oracle.Factor(tr, 0, 1e-6)
+    assert f.nbox == 0 and f.ntop == 50
+    A = oracle.dense_matrix(pts, 0)
+    b = inputs.normal(1, 50)
+    assert np.allclose(f.solve(b), np.linalg.solve(A, b), rtol=1e-12)
+    # empty problem
+    tr0 = oracle.Tree(np.zeros((0, 2)), 64)
+    f0 = oracle.Factor(tr0, 0, 1e-6, w=1.0)
+    assert f0.ntop == 0
