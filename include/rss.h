@@ -1,0 +1,139 @@
+/*
+ * rss.h -- C ABI of the GB300 implementation of the strong recursive
+ * skeletonization factorization (RS-S) of Minden, Ho, Damle & Ying,
+ * "A recursive skeletonization factorization based on strong admissibility"
+ * (arXiv:1609.08130).
+ *
+ * The matrix factored is the second-kind discretisation
+ *     A = diag * I + w * K,   K_ij = K(x_i - x_j) (i != j),  K_ii = 0,
+ * of the integral equation of Sec. 1 (Eq. 1.1, 1.3), with the 2D Laplace
+ * kernel K(z) = -log|z| / (2 pi) (Sec. 3.2, Example 1) or the 3D Laplace
+ * kernel K(z) = 1 / (4 pi |z|) (Example 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Points are DEVICE memory, FP64, point-major (x0 y0 [z0] x1 y1 ...).
+ *   - Vectors are DEVICE memory, FP64, in the caller's original point order;
+ *     several right-hand sides are column-major (n x nrhs, leading dim n).
+ *   - The caller owns every buffer it passes; the library owns handles until
+ *     rss_free.  No pointer passed in is kept after the call returns, except
+ *     that a factor keeps its own copy of the points.
+ *   - Calls run on the stream given in rss_options (NULL: the legacy default
+ *     stream) and return after their work is complete (they synchronise the
+ *     stream), so outputs may be read on return.
+ *   - Errors are reported by the return code; rss_last_error() gives a
+ *     thread-local message.  No C++ exception crosses the ABI.
+ */
+#ifndef RSS_H
+#define RSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSS_OK = 0,
+  RSS_EINVAL = 1,   /* bad argument (sizes, pointers, kind, eps, leaf) */
+  RSS_ENOMEM = 2,   /* device or host allocation failed */
+  RSS_ECUDA = 3,    /* a CUDA runtime call failed */
+  RSS_ENUMERIC = 4, /* an exactly singular pivot block was met */
+  RSS_ETIMEOUT = 5, /* a bounded device wait gave up (not used by this path) */
+  RSS_ENOTCONV = 6  /* iterative refinement did not reach the tolerance */
+} rss_status;
+
+typedef enum { RSS_LAPLACE2D_LOG = 0, RSS_LAPLACE3D_INV = 1 } rss_kernel_kind;
+
+/* Matrix A = diag * I + weight * K; weight <= 0 selects 1/N. */
+typedef struct {
+  int kind;      /* rss_kernel_kind */
+  double diag;   /* 1.0 for the second-kind problems */
+  double weight; /* quadrature weight w; <= 0 means 1/N */
+} rss_kernel;
+
+typedef enum { RSS_FP64 = 0, RSS_MIXED = 1 } rss_precision;
+
+typedef struct {
+  int prec;            /* rss_precision: FP64 everywhere, or an FP32 factor */
+  int n_proxy;         /* proxy points; 0: 64 (2D) / 512 (3D) (Sec. 4) */
+  double proxy_radius; /* in box sides; 0: 2.5 (Sec. 3.2) */
+  int use_graphs;      /* capture apply/solve sweeps in CUDA graphs */
+  void *stream;        /* cudaStream_t; NULL = legacy default stream */
+} rss_options;
+
+typedef struct rss_tree rss_tree;
+typedef struct rss_factorization rss_factorization;
+
+/* rss_build_tree -- adaptive quadtree (dim 2) / octree (dim 3) on [0,1]^dim,
+ * nodes split while they hold more than leaf_size points (Sec. 3: "each leaf
+ * box contains a bounded number of DOFs"; Sec. 4: refine until n_occ per
+ * leaf), at most depth 20.  Integer cell of coordinate v at depth t is
+ * floor(v 2^t) clamped to [0, 2^t - 1]; child index = sum_d bit_d << d; the
+ * DOF order is the stable pre-order of the tree (children ascending, points
+ * of a leaf in original order).
+ *   pts: device, n*dim doubles.  n >= 0; dim in {2,3}; leaf_size >= 1.
+ *   out: receives a handle owned by the caller (free with rss_free).
+ * Errors: RSS_EINVAL on bad sizes / NULL out; RSS_ECUDA, RSS_ENOMEM. */
+rss_status rss_build_tree(const double *pts, int64_t n, int dim, int leaf_size, rss_tree **out);
+
+/* rss_tree_query -- copy a tree array into a HOST buffer.
+ * what:  0 perm (int64[n], original index of tree-order DOF g)
+ *        1 node depth (int32[nnode])   2 node parent (int32[nnode], -1 root)
+ *        3 node coords (int32[3*nnode]) 4 node start (int64[nnode])
+ *        5 node count (int64[nnode])   6 sizes (int64[4]: nnode, maxdepth, n, dim)
+ *        100+t  boxes of depth t in elimination order (int32[]): colour-major
+ *               with 3^dim colours c = sum_d (coord_d mod 3) 3^d, Morton order
+ *               within a colour (the paper's order is "fixed but arbitrary",
+ *               Sec. 3.3.1; same-colour boxes are >= 3 apart, Sec. 5)
+ *        200+t  per box of depth t (same order): neighbour cells holding
+ *               points at depth t, int32 records {nnear, nring, codes...}
+ *               with codes sum_d (delta_d + 2) 5^d ascending, near first.
+ * buf may be NULL to ask for the size; *nbytes is in/out (capacity/size).
+ * Errors: RSS_EINVAL for an unknown `what` or a too-small buffer (the size
+ * needed is still written to *nbytes). */
+rss_status rss_tree_query(const rss_tree *tree, int what, void *buf, size_t *nbytes);
+
+/* rss_factor -- RS-S factorization F ~ A (Algorithm 1, Eq. 3.10).  Boxes of
+ * depths maxdepth..2 are strongly skeletonized level by level (Sec. 3.3):
+ * an ID of the box's interactions with the ring of boxes inside the proxy
+ * surface and with the proxy points (Eq. 3.7) splits it into skeleton and
+ * redundant DOFs, then the redundant DOFs are eliminated against the
+ * skeleton and near field (Eq. 3.4).  The remaining DOFs form the top block,
+ * factored by LU.
+ *   pts: device, n*dim doubles (a private copy is kept).
+ *   eps: ID tolerance, >= 0 (0 keeps every column: F = A up to rounding).
+ *   leaf_size: as in rss_build_tree.  opts: may be NULL (defaults).
+ * Errors: RSS_EINVAL, RSS_ENOMEM, RSS_ECUDA, RSS_ENUMERIC (zero pivot). */
+rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, double eps,
+                      int leaf_size, const rss_options *opts, rss_factorization **out);
+
+/* rss_apply -- y = F x (Eq. 3.10).  x, y: device, n x nrhs column-major,
+ * original point order; may not alias.  nrhs >= 1. */
+rss_status rss_apply(const rss_factorization *f, const double *x, double *y, int nrhs);
+
+/* rss_solve -- x = F^{-1} b (Eq. 3.11).  b, x: device, n x nrhs column-major;
+ * may not alias.  nrhs >= 1. */
+rss_status rss_solve(const rss_factorization *f, const double *b, double *x, int nrhs);
+
+/* rss_matvec -- y = A x exactly in FP64 by direct summation over all pairs
+ * (the operator being factored; used for residuals).  Device buffers. */
+rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs);
+
+/* rss_stats -- factor statistics into a HOST int64 array:
+ *   [0] number of skeletonized boxes  [1] top-block size  [2] factor bytes
+ *   [3] maxdepth                      [4] n               [5] precision
+ * followed, per box in elimination order, by {depth, b, k, nj}.
+ * *nbytes in/out as in rss_tree_query. */
+rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes);
+
+/* rss_free -- release a tree or factor handle (NULL-safe). */
+void rss_free(void *handle);
+
+/* rss_last_error -- message of the last failing call on this thread. */
+const char *rss_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSS_H */

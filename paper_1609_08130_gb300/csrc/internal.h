@@ -1,0 +1,106 @@
+// internal.h -- structures shared by the host orchestration (api.cu) and the
+// device kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rss {
+
+// One strongly skeletonized box: where its part of the factor lives.
+// Sizes k, r, nj are written by the device kernels; capacities by the host.
+template <typename T> struct FBox {
+  int cell;   // cell id within its level
+  int depth;  // tree depth t of the box
+  int b;      // |B| (active DOFs at the start of the level)
+  int k, r;   // |S|, |R| (device-written)
+  int nj;     // |J| = k + |N| (device-written)
+  int njmax;  // capacity bound on nj
+  int pad;
+  int64_t *ids; // [b] global tree-order ids: S (pivot order) then R
+  int *loc;     // [b] local indices in the cell's level layout, same order
+  int64_t *J;   // [njmax] global ids of J = [S; N]
+  int *Jnb;     // [njmax] 3^d-neighbourhood code of each J entry's cell
+  int *Jloc;    // [njmax] local index of each J entry in its cell
+  T *Tm;        // k x r column-major (ld k): T = R11^{-1} R12
+  T *LU;        // r x r row-major, L\U of P X_RR
+  int *piv;     // [r] row i of P X_RR is row piv[i] of X_RR
+  T *E;         // nj x r column-major (ld nj): E = X_JR X_RR^{-1}
+  T *G;         // r x nj column-major (ld r):  G = X_RR^{-1} X_RJ
+};
+
+// Device view of one level (depth t): the cells holding active DOFs, their
+// neighbour tables and the pool of pair blocks at Chebyshev distance <= 2.
+// Pair block (c, o) holds rows = cell c's level-start DOFs, columns = the
+// level-start DOFs of neighbour nbr[c*NB+o], column-major with ld = b_c.
+template <typename T> struct LevelDev {
+  int t, dim, ncell, NB;
+  const int *cell_b;
+  const int64_t *cell_dof_off;  // [ncell+1]
+  const int64_t *cell_dofs;     // tree-order ids, ascending within a cell
+  const int *cell_coord;        // [3*ncell]
+  const int *cell_nbr;          // [ncell*NB] or -1
+  const int64_t *pair_off;      // [ncell*NB] element offset into pool or -1
+  int *act_cnt;                 // [ncell] active count
+  int *act_idx;                 // [sum b] active local indices, ascending
+  const int *dof_cell;          // [n] cell of each active DOF at this level
+  const int *dof_loc;           // [n] local index of each active DOF
+  T *pool;
+};
+
+// A list of dense blocks to assemble: block q has rows row_ids[row_off[q] ..
+// + nrow[q]) and columns col_ids[col_off[q] .. + ncol[q]), written
+// column-major (ld nrow[q]) at out + out_off[q] (or its transpose).  Entries whose two DOFs sat
+// at Chebyshev distance <= 2 in the previous level are copied from that
+// level's pool (they may carry Schur-complement updates); all others are
+// kernel entries (Corollary 3.2: unmodified far-field interactions).
+struct AssembleList {
+  int nblock;
+  const int64_t *row_off, *col_off, *out_off;
+  const int *nrow, *ncol;
+  const int64_t *row_ids, *col_ids;
+  int transpose;  // 1: entry (i, j) holds A(col j, row i) (row-major A)
+};
+
+struct ProxyParams {
+  int np;
+  double radius;
+};
+
+// Launchers (kernels.cu).  All run on `st`.
+template <typename T>
+void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, const Points &P,
+                     const KernelParams &K, int64_t maxblk, cudaStream_t st);
+template <typename T>
+void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
+               int mmax, const Points &P, const KernelParams &K, const ProxyParams &px, double eps,
+               T *gscratch, int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err);
+template <typename T>
+void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
+                 T *scratch, int64_t scratch_stride, cudaStream_t st, int *err);
+template <typename T>
+void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_list, int nbox,
+                  int njmax, const T *scratch, int64_t scratch_stride, cudaStream_t st);
+template <typename T>
+void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err);
+
+// Sweeps over the factor (kernels.cu).  v: tree-order working vector,
+// layout v[g * nrhs + c].
+template <typename T>
+void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
+                  cudaStream_t st);
+template <typename T>
+void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v,
+                int nrhs, T *work, cudaStream_t st);
+template <typename T> int64_t id_region_bytes(int b, int PR);
+template <typename T>
+void launch_permute(int dir, const int64_t *perm, const double *in, T *out_or_in, double *out,
+                    int64_t n, int nrhs, cudaStream_t st);
+void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const int64_t *perm,
+                   const double *xin, double *yout, int64_t n, int nrhs, cudaStream_t st);
+
+// Sweep modes.
+enum { SWEEP_SOLVE_FWD = 0, SWEEP_SOLVE_BWD = 1, SWEEP_APPLY_FWD = 2, SWEEP_APPLY_BWD = 3 };
+
+}  // namespace rss

@@ -1,0 +1,1148 @@
+// kernels.cu -- CUDA kernels (sm_103a) for the strong recursive
+// skeletonization factorization (RS-S) and its apply / solve sweeps.
+//
+// Per level (tree depth t) and per colour phase, every box of the phase is
+// skeletonized independently (same-colour boxes are >= 3 cells apart, so
+// their 3^d neighbourhoods -- everything a box reads or writes -- are
+// disjoint):
+//   k_id     : ID of the box (Definition 2.1) from the rows of its
+//              interactions with the ring O inside the proxy surface and the
+//              proxy rows (Eq. 3.7), by a shared-memory Householder
+//              reduction of those rows to a b x b triangle followed by
+//              greedy column-pivoted QR of the triangle;
+//   k_elim   : the operators U_T, L_T (Sec. 3.1) and the elimination of the
+//              redundant DOFs: LU of X_RR, E = X_JR X_RR^{-1},
+//              G = X_RR^{-1} X_RJ (Sec. 2.1, Eq. 3.4);
+//   k_schur  : X_JJ -= E G scattered into the pair blocks of the level.
+// k_assemble builds the pair blocks of a level (Corollary 3.2: entries not
+// reached by any Schur update are kernel entries) and the top block.
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include "internal.h"
+
+namespace rss {
+
+constexpr int NT = 256;  // threads per CTA for the per-box kernels
+
+// ---------------------------------------------------------------------------
+// Assembly of pair blocks / top block
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__ out, LevelDev<T> prev,
+                                                 int has_prev, Points P, KernelParams K) {
+  int q = blockIdx.x;
+  int nr = L.nrow[q], nc = L.ncol[q];
+  const int64_t *rid = L.row_ids + L.row_off[q];
+  const int64_t *cid = L.col_ids + L.col_off[q];
+  T *o = out + L.out_off[q];
+  int64_t tot = (int64_t)nr * nc;
+  for (int64_t e = blockIdx.y * (int64_t)NT + threadIdx.x; e < tot; e += (int64_t)NT * gridDim.y) {
+    int i = (int)(e % nr), j = (int)(e / nr);
+    int64_t gi = rid[i], gj = cid[j];
+    if (L.transpose) {
+      int64_t tg = gi;
+      gi = gj;
+      gj = tg;
+    }
+    T v;
+    bool done = false;
+    if (has_prev) {
+      int ci = prev.dof_cell[gi], cj = prev.dof_cell[gj];
+      int dx = prev.cell_coord[3 * cj] - prev.cell_coord[3 * ci];
+      int dy = prev.cell_coord[3 * cj + 1] - prev.cell_coord[3 * ci + 1];
+      int dz = prev.cell_coord[3 * cj + 2] - prev.cell_coord[3 * ci + 2];
+      if (dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2 && dz >= -2 && dz <= 2) {
+        int64_t off = prev.pair_off[(int64_t)ci * prev.NB + code5(dx, dy, dz, prev.dim)];
+        v = prev.pool[off + prev.dof_loc[gi] + (int64_t)prev.dof_loc[gj] * prev.cell_b[ci]];
+        done = true;
+      }
+    }
+    if (!done) v = entry<T>(P, K, gi, gj);
+    o[e] = v;
+  }
+}
+
+template <typename T>
+void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, const Points &P,
+                     const KernelParams &K, int64_t maxblk, cudaStream_t st) {
+  if (L.nblock == 0) return;
+  LevelDev<T> pv{};
+  if (prev) pv = *prev;
+  int gy = (int)((maxblk + NT * 8 - 1) / (NT * 8));
+  if (gy < 1) gy = 1;
+  if (gy > 1024) gy = 1024;
+  dim3 grid(L.nblock, gy);
+  k_assemble<T><<<grid, NT, 0, st>>>(L, out, pv, prev ? 1 : 0, P, K);
+}
+
+// ---------------------------------------------------------------------------
+// ID: Householder reduction of the proxy-compressed far-field rows, then
+// greedy column-pivoted QR of the b x b triangle.
+// ---------------------------------------------------------------------------
+
+template <typename T> struct IdLayout {
+  // offsets in elements of T within the per-box region
+  int ldr, ldp;
+  int64_t oR, oP, oN, oPerm;  // oPerm in elements of T (ints placed after)
+  int64_t bytes;
+  __host__ __device__ IdLayout(int b, int PR) {
+    ldr = b + 1;
+    ldp = PR + 1;
+    oR = 0;
+    oP = oR + (int64_t)ldr * b;
+    oN = oP + (int64_t)ldp * b;
+    oPerm = oN + b;
+    bytes = oPerm * (int64_t)sizeof(T) + (int64_t)b * sizeof(int) + 16;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, Points P,
+                                           KernelParams K, ProxyParams px, double eps, int PR, T *gscr,
+                                           int64_t gstride, int use_smem, int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ocell[125], s_obase[126], s_ono;
+  __shared__ int64_t s_rowsrc[256];
+  __shared__ T s_r11;
+  __shared__ int s_stop, s_piv, s_k;
+
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int c = fb.cell, b = fb.b, dim = lv.dim;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
+  IdLayout<T> lay(b, PR);
+  T *base = use_smem ? reinterpret_cast<T *>(smem_raw) : gscr + (int64_t)blockIdx.x * gstride;
+  T *R = base + lay.oR;
+  T *pan = base + lay.oP;
+  T *nrm = base + lay.oN;
+  int *perm = reinterpret_cast<int *>(base + lay.oPerm);
+  const int ldr = lay.ldr, ldp = lay.ldp;
+
+  for (int e = tid; e < ldr * b; e += NT) R[e] = (T)0;
+  // Ring O: cells at Chebyshev distance exactly 2 with active DOFs.
+  if (tid == 0) {
+    int no = 0, acc = 0;
+    int lim = dim == 3 ? 2 : 0;
+    for (int dz = -lim; dz <= lim; dz++)
+      for (int dy = -2; dy <= 2; dy++)
+        for (int dx = -2; dx <= 2; dx++) {
+          int m = max(abs(dx), max(abs(dy), abs(dz)));
+          if (m != 2) continue;
+          int code = code5(dx, dy, dz, dim);
+          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+          if (nb < 0) continue;
+          int cnt = lv.act_cnt[nb];
+          if (cnt <= 0) continue;
+          s_ocell[no] = code;  // store the code; the cell is looked up again
+          s_obase[no] = acc;
+          acc += cnt;
+          no++;
+        }
+    s_obase[no] = acc;
+    s_ono = no;
+  }
+  __syncthreads();
+  const int no = s_ono;
+  const int nO = s_obase[no];
+  const int m = nO + px.np;
+  const int64_t coff = lv.cell_dof_off[c];
+  const T w = (T)K.w;
+  // proxy circle / sphere about the box centre (Sec. 3.2)
+  const double D = ldexp(1.0, -lv.t);
+  double ctr[3];
+  for (int d = 0; d < 3; d++) ctr[d] = (lv.cell_coord[3 * c + d] + 0.5) * D;
+
+  for (int p0 = 0; p0 < m; p0 += PR) {
+    const int rows = min(PR, m - p0);
+    // row sources of this panel
+    for (int rr = tid; rr < rows; rr += NT) {
+      int row = p0 + rr;
+      int64_t src;
+      if (row < nO) {
+        int q = 0;
+        while (s_obase[q + 1] <= row) q++;
+        int code = s_ocell[q];
+        int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+        int loc = lv.act_idx[lv.cell_dof_off[nb] + (row - s_obase[q])];
+        // column `loc` of pair block (c, nb): rows are the box's DOFs
+        src = lv.pair_off[(int64_t)c * lv.NB + code] + (int64_t)loc * b;
+      } else {
+        src = -1 - (int64_t)(row - nO);
+      }
+      s_rowsrc[rr] = src;
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * b; e += NT) {
+      int rr = e / b, q = e % b;
+      int64_t src = s_rowsrc[rr];
+      T v;
+      if (src >= 0) {
+        v = lv.pool[src + q];
+      } else {
+        int mm = (int)(-1 - src);
+        double y[3];
+        if (dim == 2) {
+          double th = 2.0 * kPi * (double)mm / (double)px.np;
+          y[0] = ctr[0] + px.radius * D * cos(th);
+          y[1] = ctr[1] + px.radius * D * sin(th);
+          y[2] = 0.0;
+        } else {
+          double z = 1.0 - (2.0 * mm + 1.0) / (double)px.np;
+          double rr2 = sqrt(1.0 - z * z);
+          double ph = (double)mm * kPi * (3.0 - sqrt(5.0));
+          y[0] = ctr[0] + px.radius * D * rr2 * cos(ph);
+          y[1] = ctr[1] + px.radius * D * rr2 * sin(ph);
+          y[2] = ctr[2] + px.radius * D * z;
+        }
+        int64_t g = lv.cell_dofs[coff + q];
+        const double *xg = P.x + g * dim;
+        double r2 = 0.0;
+        for (int d = 0; d < dim; d++) {
+          double dd = y[d] - xg[d];
+          r2 += dd * dd;
+        }
+        v = w * kof(K.kind, (T)r2);
+      }
+      pan[rr + (int64_t)q * ldp] = v;
+    }
+    for (int e = tid; e < (PR - rows) * b; e += NT) {
+      int rr = rows + e / b, q = e % b;
+      pan[rr + (int64_t)q * ldp] = (T)0;
+    }
+    __syncthreads();
+    // [R; panel] -> R, one Householder reflector per column
+    for (int j = 0; j < b; j++) {
+      const T *pj = pan + (int64_t)j * ldp;
+      T s = (T)0;
+      for (int i = lane; i < rows; i += 32) s += pj[i] * pj[i];
+      s = warp_sum(s);
+      if (s > (T)0) {
+        T x0 = R[j + (int64_t)j * ldr];
+        T nrm2 = sqrt(x0 * x0 + s);
+        T beta = x0 >= (T)0 ? -nrm2 : nrm2;
+        T tau = (beta - x0) / beta;
+        T scl = (T)1 / (x0 - beta);
+        for (int cc = j + 1 + warp; cc < b; cc += nwarp) {
+          T *pc = pan + (int64_t)cc * ldp;
+          T d = (T)0;
+          for (int i = lane; i < rows; i += 32) d += pj[i] * pc[i];
+          d = warp_sum(d);
+          T wv = R[j + (int64_t)cc * ldr] + scl * d;
+          T f = tau * wv;
+          T fs = f * scl;
+          for (int i = lane; i < rows; i += 32) pc[i] -= fs * pj[i];
+          if (lane == 0) R[j + (int64_t)cc * ldr] -= f;
+        }
+      }
+      __syncthreads();
+      // every warp has read x0 = R_jj; now it may be replaced by beta
+      if (s > (T)0 && tid == 0) {
+        T x0 = R[j + (int64_t)j * ldr];
+        T nrm2 = sqrt(x0 * x0 + s);
+        R[j + (int64_t)j * ldr] = x0 >= (T)0 ? -nrm2 : nrm2;
+      }
+    }
+    __syncthreads();
+  }
+
+  // Greedy column-pivoted QR of the b x b triangle (Definition 2.1 and the
+  // remark after it): pivot = largest trailing column norm (recomputed each
+  // step), ties to the lowest column; stop at |R_jj| <= eps |R_11|.
+  for (int q = tid; q < b; q += NT) perm[q] = q;
+  if (tid == 0) {
+    s_k = b;
+    s_r11 = (T)0;
+  }
+  __syncthreads();
+  for (int j = 0; j < b; j++) {
+    for (int cc = j + warp; cc < b; cc += nwarp) {
+      const T *col = R + (int64_t)cc * ldr;
+      T s = (T)0;
+      for (int i = j + lane; i < b; i += 32) s += col[i] * col[i];
+      s = warp_sum(s);
+      if (lane == 0) nrm[cc] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T best = (T)-1;
+      int bi = b;
+      for (int cc = j + lane; cc < b; cc += 32) {
+        T v = nrm[cc];
+        if (v > best) {
+          best = v;
+          bi = cc;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        T cn = sqrt(best);
+        if (j == 0) s_r11 = cn;
+        // no valid pivot (all norms NaN) also stops the factorization
+        s_stop = (bi >= b || s_r11 == (T)0 || !(cn > (T)eps * s_r11)) ? 1 : 0;
+        s_piv = bi;
+        if (s_stop) s_k = j;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_piv;
+    if (p != j) {
+      for (int i = tid; i < b; i += NT) {
+        T t0 = R[i + (int64_t)j * ldr];
+        R[i + (int64_t)j * ldr] = R[i + (int64_t)p * ldr];
+        R[i + (int64_t)p * ldr] = t0;
+      }
+      if (tid == 0) {
+        int tp = perm[j];
+        perm[j] = perm[p];
+        perm[p] = tp;
+      }
+    }
+    __syncthreads();
+    {
+      const T *cj = R + (int64_t)j * ldr;
+      T s = (T)0;
+      for (int i = j + 1 + lane; i < b; i += 32) s += cj[i] * cj[i];
+      s = warp_sum(s);
+      T x0 = cj[j];
+      if (s > (T)0) {
+        T nrm2 = sqrt(x0 * x0 + s);
+        T beta = x0 >= (T)0 ? -nrm2 : nrm2;
+        T tau = (beta - x0) / beta;
+        T scl = (T)1 / (x0 - beta);
+        for (int cc = j + 1 + warp; cc < b; cc += nwarp) {
+          T *pc = R + (int64_t)cc * ldr;
+          T d = (T)0;
+          for (int i = j + 1 + lane; i < b; i += 32) d += cj[i] * pc[i];
+          d = warp_sum(d);
+          T wv = pc[j] + scl * d;
+          T f = tau * wv;
+          T fs = f * scl;
+          for (int i = j + 1 + lane; i < b; i += 32) pc[i] -= fs * cj[i];
+          __syncwarp();
+          if (lane == 0) pc[j] -= f;
+        }
+      }
+      __syncthreads();
+      if (s > (T)0 && tid == 0) {
+        T nrm2 = sqrt(x0 * x0 + s);
+        R[j + (int64_t)j * ldr] = x0 >= (T)0 ? -nrm2 : nrm2;
+      }
+      __syncthreads();
+    }
+  }
+  const int k = s_k;
+  const int r = b - k;
+  // T = R11^{-1} R12 by back substitution, one thread per column
+  for (int cc = tid; cc < r; cc += NT) {
+    T *tcol = fb.Tm + (int64_t)cc * k;
+    for (int i = k - 1; i >= 0; i--) {
+      T s = R[i + (int64_t)(k + cc) * ldr];
+      for (int l = i + 1; l < k; l++) s -= R[i + (int64_t)l * ldr] * tcol[l];
+      tcol[i] = s / R[i + (int64_t)i * ldr];
+    }
+  }
+  for (int q = tid; q < b; q += NT) {
+    fb.loc[q] = perm[q];
+    fb.ids[q] = lv.cell_dofs[coff + perm[q]];
+  }
+  if (tid == 0) {
+    fb.k = k;
+    fb.r = r;
+  }
+}
+
+template <typename T>
+void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, int mmax,
+               const Points &P, const KernelParams &K, const ProxyParams &px, double eps, T *gscratch,
+               int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err) {
+  (void)mmax;
+  if (nbox == 0) return;
+  int PR = bmax <= 80 ? 128 : 64;
+  IdLayout<T> lay(bmax, PR);
+  size_t smem = use_smem ? (size_t)lay.bytes : 0;
+  if (use_smem)
+    cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_id<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, P, K, px, eps, PR, gscratch, gscratch_stride,
+                                  use_smem ? 1 : 0, err);
+}
+
+template <typename T> int64_t id_region_bytes(int b, int PR) { return IdLayout<T>(b, PR).bytes; }
+template int64_t id_region_bytes<float>(int, int);
+template int64_t id_region_bytes<double>(int, int);
+
+// ---------------------------------------------------------------------------
+// Elimination of the redundant DOFs (Sec. 3.1, Eq. 3.4)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
+                                             int64_t sstride, int rmax, int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nn;
+  __shared__ int64_t s_off_in[27], s_off_out[27];
+  __shared__ int s_ld_in[27];
+  __shared__ int s_pivrow;
+
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
+  const int ncode3 = dim == 3 ? 27 : 9;
+  const int center = code3(0, 0, 0, dim);
+
+  // shared: Ts (k x r, ld k), LU (r x r, ld r+1), loc (b ints), piv (r ints)
+  T *Ts = reinterpret_cast<T *>(smem_raw);
+  const int ldl = r + 1;
+  T *LU = Ts + (int64_t)k * r;
+  int *sloc = reinterpret_cast<int *>(LU + (int64_t)r * ldl);
+  int *spiv = sloc + b;
+
+  if (tid == 0) {
+    int nn = 0, acc = k;
+    for (int code = 0; code < ncode3; code++) {
+      int dx, dy, dz;
+      decode3(code, dim, dx, dy, dz);
+      int nb = lv.cell_nbr[(int64_t)c * lv.NB + code5(dx, dy, dz, dim)];
+      s_ncell[code] = nb;
+      if (nb >= 0) {
+        s_off_in[code] = lv.pair_off[(int64_t)nb * lv.NB + code5(-dx, -dy, -dz, dim)];
+        s_off_out[code] = lv.pair_off[(int64_t)c * lv.NB + code5(dx, dy, dz, dim)];
+        s_ld_in[code] = lv.cell_b[nb];
+      }
+      if (code == center || nb < 0) continue;
+      int cnt = lv.act_cnt[nb];
+      if (cnt <= 0) continue;
+      s_ncode[nn] = code;
+      s_nstart[nn] = acc;
+      acc += cnt;
+      nn++;
+    }
+    s_nstart[nn] = acc;
+    s_nn = nn;
+  }
+  for (int q = tid; q < b; q += NT) sloc[q] = fb.loc[q];
+  for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
+  __syncthreads();
+  const int nn = s_nn;
+  const int nj = s_nstart[nn];
+  if (nj > fb.njmax) {
+    if (tid == 0) set_err(err, DERR_INTERNAL);
+    return;
+  }
+  // J = [S (pivot order); N (near cells in code order, active ascending)]
+  for (int a = tid; a < nj; a += NT) {
+    int code, loc;
+    int64_t g;
+    if (a < k) {
+      code = center;
+      loc = sloc[a];
+      g = fb.ids[a];
+    } else {
+      int q = 0;
+      while (s_nstart[q + 1] <= a) q++;
+      code = s_ncode[q];
+      int nb = s_ncell[code];
+      loc = lv.act_idx[lv.cell_dof_off[nb] + (a - s_nstart[q])];
+      g = lv.cell_dofs[lv.cell_dof_off[nb] + loc];
+    }
+    fb.J[a] = g;
+    fb.Jnb[a] = code;
+    fb.Jloc[a] = loc;
+  }
+  if (tid == 0) fb.nj = nj;
+  __syncthreads();
+
+  T *Ep = scratch + (int64_t)blockIdx.x * sstride;  // X_JR, nj x r col-major (ld nj)
+  T *Gp = Ep + (int64_t)nj * r;                      // X_RJ, r x nj col-major (ld r)
+  const T *pool = lv.pool;
+  const T *Aii = pool + s_off_in[center];            // block (c, c), ld b
+
+  // X_JR = A_JR - A_JS T   (L_T applied from the right)
+  for (int a = tid; a < nj; a += NT) {
+    int code = fb.Jnb[a], la = fb.Jloc[a];
+    const T *Ab = pool + s_off_in[code];
+    int64_t ld = s_ld_in[code];
+    const T *row = Ab + la;
+    for (int r0 = 0; r0 < r; r0 += 8) {
+      T acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) acc[u] = (r0 + u < r) ? row[(int64_t)sloc[k + r0 + u] * ld] : (T)0;
+      for (int s = 0; s < k; s++) {
+        T as = row[(int64_t)sloc[s] * ld];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          if (r0 + u < r) acc[u] -= as * Ts[s + (int64_t)(r0 + u) * k];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++)
+        if (r0 + u < r) Ep[a + (int64_t)(r0 + u) * nj] = acc[u];
+    }
+  }
+  // X_RJ = A_RJ - T^T A_SJ  (U_T applied from the left); one warp per column
+  for (int a = warp; a < nj; a += nwarp) {
+    int code = fb.Jnb[a], la = fb.Jloc[a];
+    const T *col = pool + s_off_out[code] + (int64_t)la * b;  // column la of block (c, nb)
+    for (int ri = lane; ri < r; ri += 32) {
+      T acc = col[sloc[k + ri]];
+      for (int s = 0; s < k; s++) acc -= Ts[s + (int64_t)ri * k] * col[sloc[s]];
+      Gp[ri + (int64_t)a * r] = acc;
+    }
+  }
+  __syncthreads();
+  // X_RR = A_RR - T^T A_SR - X_RS T   (X_RS = first k columns of X_RJ)
+  for (int e = tid; e < r * r; e += NT) {
+    int ri = e / r, rj = e % r;
+    int64_t qc = (int64_t)sloc[k + rj] * b;
+    T acc = Aii[sloc[k + ri] + qc];
+    for (int s = 0; s < k; s++) {
+      acc -= Ts[s + (int64_t)ri * k] * Aii[sloc[s] + qc];
+      acc -= Gp[ri + (int64_t)s * r] * Ts[s + (int64_t)rj * k];
+    }
+    LU[ri * ldl + rj] = acc;
+  }
+  for (int i = tid; i < r; i += NT) spiv[i] = i;
+  __syncthreads();
+  // LU with partial pivoting (largest |entry|, ties to the lowest row)
+  for (int j = 0; j < r; j++) {
+    if (warp == 0) {
+      T best = (T)-1;
+      int bi = r;
+      for (int i = j + lane; i < r; i += 32) {
+        T v = fabs(LU[i * ldl + j]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        if (bi >= r) {  // NaN column: keep the diagonal, report
+          bi = j;
+          set_err(err, DERR_NUMERIC);
+        }
+        s_pivrow = bi;
+        if (best == (T)0) set_err(err, DERR_NUMERIC);
+      }
+    }
+    __syncthreads();
+    const int p = s_pivrow;
+    if (p != j) {
+      for (int cc = tid; cc < r; cc += NT) {
+        T t0 = LU[j * ldl + cc];
+        LU[j * ldl + cc] = LU[p * ldl + cc];
+        LU[p * ldl + cc] = t0;
+      }
+      if (tid == 0) {
+        int tp = spiv[j];
+        spiv[j] = spiv[p];
+        spiv[p] = tp;
+      }
+    }
+    __syncthreads();
+    const T d = LU[j * ldl + j];
+    for (int i = j + 1 + tid; i < r; i += NT) LU[i * ldl + j] /= d;
+    __syncthreads();
+    const int rem = r - j - 1;
+    for (int e = tid; e < rem * rem; e += NT) {
+      int i = j + 1 + e / rem, cc = j + 1 + e % rem;
+      LU[i * ldl + cc] -= LU[i * ldl + j] * LU[j * ldl + cc];
+    }
+    __syncthreads();
+  }
+  // E = X_JR X_RR^{-1}: per row, W U = x, Z L = W, E = Z P
+  for (int a = tid; a < nj; a += NT) {
+    T *row = Ep + a;
+    for (int j = 0; j < r; j++) {
+      T s = row[(int64_t)j * nj];
+      for (int i = 0; i < j; i++) s -= row[(int64_t)i * nj] * LU[i * ldl + j];
+      row[(int64_t)j * nj] = s / LU[j * ldl + j];
+    }
+    for (int j = r - 1; j >= 0; j--) {
+      T s = row[(int64_t)j * nj];
+      for (int i = j + 1; i < r; i++) s -= row[(int64_t)i * nj] * LU[i * ldl + j];
+      row[(int64_t)j * nj] = s;
+    }
+    for (int i = 0; i < r; i++) fb.E[a + (int64_t)spiv[i] * nj] = row[(int64_t)i * nj];
+  }
+  // G = X_RR^{-1} X_RJ: per column, y = P x, forward L, backward U
+  for (int a = tid; a < nj; a += NT) {
+    const T *x = Gp + (int64_t)a * r;
+    T *y = fb.G + (int64_t)a * r;
+    for (int i = 0; i < r; i++) y[i] = x[spiv[i]];
+    for (int i = 0; i < r; i++) {
+      T s = y[i];
+      for (int l = 0; l < i; l++) s -= LU[i * ldl + l] * y[l];
+      y[i] = s;
+    }
+    for (int i = r - 1; i >= 0; i--) {
+      T s = y[i];
+      for (int l = i + 1; l < r; l++) s -= LU[i * ldl + l] * y[l];
+      y[i] = s / LU[i * ldl + i];
+    }
+  }
+  for (int e = tid; e < r * r; e += NT) fb.LU[e] = LU[(e / r) * ldl + (e % r)];
+  for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
+  // the box's active DOFs are now its skeleton, kept in ascending order
+  const int64_t coff = lv.cell_dof_off[c];
+  for (int s = tid; s < k; s += NT) {
+    int v = sloc[s], rank = 0;
+    for (int s2 = 0; s2 < k; s2++) rank += sloc[s2] < v;
+    lv.act_idx[coff + rank] = v;
+  }
+  if (tid == 0) lv.act_cnt[c] = k;
+}
+
+template <typename T> int64_t elim_smem_bytes(int b, int k, int r) {
+  return (int64_t)k * r * sizeof(T) + (int64_t)r * (r + 1) * sizeof(T) + (int64_t)(b + r) * sizeof(int) + 16;
+}
+template int64_t elim_smem_bytes<float>(int, int, int);
+template int64_t elim_smem_bytes<double>(int, int, int);
+
+template <typename T>
+void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
+                 int64_t scratch_stride, cudaStream_t st, int *err) {
+  if (nbox == 0) return;
+  // worst case over k + r = b: k r <= b^2/4, r <= b
+  size_t smem = (size_t)bmax * bmax / 4 * sizeof(T) + (size_t)bmax * (bmax + 1) * sizeof(T) +
+                (size_t)2 * bmax * sizeof(int) + 64;
+  cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_elim<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, scratch, scratch_stride, bmax, err);
+}
+
+// ---------------------------------------------------------------------------
+// Schur complement update X_JJ -= E G, scattered into the pair blocks
+// ---------------------------------------------------------------------------
+
+constexpr int ST = 64;   // output tile
+constexpr int SK = 16;   // inner chunk
+
+// S_JJ = X_JJ - X_JR X_RR^{-1} X_RJ = X_JJ - E X_RJ (Sec. 2.1); X_RJ is still in
+// the elimination scratch of this phase (r x nj column-major after X_JR).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_schur(LevelDev<T> lv, const FBox<T> *boxes, const int *box_list,
+                                              int tiles1, const T *scratch, int64_t sstride) {
+  __shared__ T Es[SK][ST + 1];
+  __shared__ T Gs[SK][ST + 1];
+  __shared__ int s_cell3[27];
+  const int bi = blockIdx.x / (tiles1 * tiles1);
+  const int tt = blockIdx.x % (tiles1 * tiles1);
+  const FBox<T> &fb = boxes[box_list[bi]];
+  const int nj = fb.nj, r = fb.r, dim = lv.dim;
+  const int a0 = (tt / tiles1) * ST, c0 = (tt % tiles1) * ST;
+  if (a0 >= nj || c0 >= nj || r == 0) return;
+  const T *Xrj = scratch + (int64_t)bi * sstride + (int64_t)nj * r;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (tid < (dim == 3 ? 27 : 9)) {
+    int dx, dy, dz;
+    decode3(tid, dim, dx, dy, dz);
+    s_cell3[tid] = lv.cell_nbr[(int64_t)fb.cell * lv.NB + code5(dx, dy, dz, dim)];
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int y = 0; y < 4; y++) acc[x][y] = (T)0;
+  for (int r0 = 0; r0 < r; r0 += SK) {
+    for (int e = tid; e < SK * ST; e += NT) {
+      int u = e / ST, i = e % ST;
+      int ri = r0 + u;
+      Es[u][i] = (ri < r && a0 + i < nj) ? fb.E[(a0 + i) + (int64_t)ri * nj] : (T)0;
+      int u2 = e % SK, i2 = e / SK;
+      int ri2 = r0 + u2;
+      Gs[u2][i2] = (ri2 < r && c0 + i2 < nj) ? Xrj[ri2 + (int64_t)(c0 + i2) * r] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < SK; u++) {
+      T ev[4], gv[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) ev[x] = Es[u][tx + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; y++) gv[y] = Gs[u][ty + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++) acc[x][y] += ev[x] * gv[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < 4; y++) {
+    int cc = c0 + ty + 16 * y;
+    if (cc >= nj) continue;
+    int codec = fb.Jnb[cc], lc = fb.Jloc[cc];
+    int cdx, cdy, cdz;
+    decode3(codec, dim, cdx, cdy, cdz);
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      int a = a0 + tx + 16 * x;
+      if (a >= nj) continue;
+      int codea = fb.Jnb[a], la = fb.Jloc[a];
+      int adx, ady, adz;
+      decode3(codea, dim, adx, ady, adz);
+      int ca = s_cell3[codea];
+      int64_t off = lv.pair_off[(int64_t)ca * lv.NB + code5(cdx - adx, cdy - ady, cdz - adz, dim)];
+      lv.pool[off + la + (int64_t)lc * lv.cell_b[ca]] -= acc[x][y];
+    }
+  }
+}
+
+template <typename T>
+void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_list, int nbox, int njmax,
+                  const T *scratch, int64_t scratch_stride, cudaStream_t st) {
+  if (nbox == 0) return;
+  int tiles1 = (njmax + ST - 1) / ST;
+  int64_t grid = (int64_t)nbox * tiles1 * tiles1;
+  k_schur<T><<<(unsigned)grid, NT, 0, st>>>(lv, boxes, box_list, tiles1, scratch, scratch_stride);
+}
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting (top block), row-major, blocked
+// ---------------------------------------------------------------------------
+
+constexpr int LB = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, int *err) {
+  __shared__ T s_val[32];
+  __shared__ int s_idx[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x / 32;
+  for (int j = kb; j < kb + nb; j++) {
+    T best = (T)-1;
+    int bi = n;
+    for (int i = j + tid; i < n; i += blockDim.x) {
+      T v = fabs(A[(int64_t)i * n + j]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_val[warp] = best;
+      s_idx[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? s_val[lane] : (T)-1;
+      bi = lane < nwarp ? s_idx[lane] : n;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        if (bi >= n) {
+          bi = j;
+          set_err(err, DERR_NUMERIC);
+        }
+        s_idx[0] = bi;
+        if (best == (T)0) set_err(err, DERR_NUMERIC);
+      }
+    }
+    __syncthreads();
+    const int p = s_idx[0];
+    if (p != j) {
+      for (int cc = tid; cc < n; cc += blockDim.x) {
+        T t0 = A[(int64_t)j * n + cc];
+        A[(int64_t)j * n + cc] = A[(int64_t)p * n + cc];
+        A[(int64_t)p * n + cc] = t0;
+      }
+      if (tid == 0) {
+        int tp = piv[j];
+        piv[j] = piv[p];
+        piv[p] = tp;
+      }
+    }
+    __syncthreads();
+    const T d = A[(int64_t)j * n + j];
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      T l = A[(int64_t)i * n + j] / d;
+      A[(int64_t)i * n + j] = l;
+      for (int cc = j + 1; cc < kb + nb; cc++) A[(int64_t)i * n + cc] -= l * A[(int64_t)j * n + cc];
+    }
+    __syncthreads();
+  }
+}
+
+// U12 = L11^{-1} A12 for the columns right of the panel (one thread per column)
+template <typename T> __global__ void k_lu_trsm(T *A, int n, int kb, int nb) {
+  int cc = kb + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc >= n) return;
+  for (int i = kb; i < kb + nb; i++) {
+    T s = A[(int64_t)i * n + cc];
+    for (int l = kb; l < i; l++) s -= A[(int64_t)i * n + l] * A[(int64_t)l * n + cc];
+    A[(int64_t)i * n + cc] = s;
+  }
+}
+
+// A22 -= L21 U12 (64 x 64 tiles, inner dimension nb <= 32)
+template <typename T> __global__ void __launch_bounds__(NT) k_lu_gemm(T *A, int n, int kb, int nb) {
+  __shared__ T Ls[64][LB + 1];
+  __shared__ T Us[LB][64 + 1];
+  const int s0 = kb + nb;
+  const int i0 = s0 + blockIdx.y * 64, c0 = s0 + blockIdx.x * 64;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < 64 * LB; e += NT) {
+    int i = e / LB, l = e % LB;
+    Ls[i][l] = (i0 + i < n && l < nb) ? A[(int64_t)(i0 + i) * n + kb + l] : (T)0;
+    int l2 = e / 64, c2 = e % 64;
+    Us[l2][c2] = (c0 + c2 < n && l2 < nb) ? A[(int64_t)(kb + l2) * n + c0 + c2] : (T)0;
+  }
+  __syncthreads();
+  T acc[4][4] = {};
+  for (int l = 0; l < nb; l++) {
+#pragma unroll
+    for (int x = 0; x < 4; x++)
+#pragma unroll
+      for (int y = 0; y < 4; y++) acc[x][y] += Ls[ty + 16 * x][l] * Us[l][tx + 16 * y];
+  }
+#pragma unroll
+  for (int x = 0; x < 4; x++) {
+    int i = i0 + ty + 16 * x;
+    if (i >= n) continue;
+#pragma unroll
+    for (int y = 0; y < 4; y++) {
+      int cc = c0 + tx + 16 * y;
+      if (cc < n) A[(int64_t)i * n + cc] -= acc[x][y];
+    }
+  }
+}
+
+template <typename T> __global__ void k_iota(int *p, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = i;
+}
+
+template <typename T> void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err) {
+  if (n <= 0) return;
+  k_iota<T><<<(n + 255) / 256, 256, 0, st>>>(piv, n);
+  for (int kb = 0; kb < n; kb += LB) {
+    int nb = min(LB, n - kb);
+    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, err);
+    int rem = n - kb - nb;
+    if (rem > 0) {
+      k_lu_trsm<T><<<(rem + 127) / 128, 128, 0, st>>>(A, n, kb, nb);
+      dim3 g((rem + 63) / 64, (rem + 63) / 64);
+      k_lu_gemm<T><<<g, NT, 0, st>>>(A, n, kb, nb);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sweeps: apply F (Eq. 3.10) or F^{-1} (Eq. 3.11) box by box
+// ---------------------------------------------------------------------------
+
+// In-place LU solve / multiply on a vector in shared memory by one warp.
+template <typename T>
+__device__ void warp_lu_solve(const T *LU, const int *piv, int r, T *x, T *tmp, int lane) {
+  for (int i = lane; i < r; i += 32) tmp[i] = x[piv[i]];
+  __syncwarp();
+  for (int i = 0; i < r; i++) {
+    T yi = tmp[i];
+    for (int l = i + 1 + lane; l < r; l += 32) tmp[l] -= LU[(int64_t)l * r + i] * yi;
+    __syncwarp();
+  }
+  for (int i = r - 1; i >= 0; i--) {
+    T yi = tmp[i] / LU[(int64_t)i * r + i];
+    __syncwarp();
+    if (lane == 0) tmp[i] = yi;
+    for (int l = lane; l < i; l += 32) tmp[l] -= LU[(int64_t)l * r + i] * yi;
+    __syncwarp();
+  }
+  for (int i = lane; i < r; i += 32) x[i] = tmp[i];
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, int first, T *v, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const FBox<T> &fb = boxes[first + blockIdx.x];
+  const int k = fb.k, r = fb.r, nj = fb.nj;
+  if (r == 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
+  T *vS = reinterpret_cast<T *>(smem_raw);   // k x nrhs
+  T *vR = vS + (int64_t)k * nrhs;            // r x nrhs
+  T *tmp = vR + (int64_t)r * nrhs;           // scratch
+  const int64_t *S = fb.ids, *Rr = fb.ids + k;
+  for (int e = tid; e < k * nrhs; e += NT) vS[e] = v[S[e / nrhs] * nrhs + e % nrhs];
+  for (int e = tid; e < r * nrhs; e += NT) vR[e] = v[Rr[e / nrhs] * nrhs + e % nrhs];
+  __syncthreads();
+  if (mode == SWEEP_SOLVE_FWD) {
+    // U_T: v_R -= T^T v_S
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int ri = e / nrhs, c = e % nrhs;
+      T s = (T)0;
+      for (int q = 0; q < k; q++) s += fb.Tm[q + (int64_t)ri * k] * vS[q * nrhs + c];
+      vR[e] -= s;
+    }
+    __syncthreads();
+    // L: v_J -= E v_R
+    for (int e = tid; e < nj * nrhs; e += NT) {
+      int a = e % nj, c = e / nj;
+      T s = (T)0;
+      for (int ri = 0; ri < r; ri++) s += fb.E[a + (int64_t)ri * nj] * vR[ri * nrhs + c];
+      v[fb.J[a] * nrhs + c] -= s;
+    }
+    // D^{-1} on R (v_R is final for this box): one warp per right-hand side
+    for (int c = warp; c < nrhs; c += nwarp) {
+      T *col = tmp + (int64_t)warp * 2 * r;
+      T *wk = col + r;
+      for (int i = lane; i < r; i += 32) col[i] = vR[i * nrhs + c];
+      __syncwarp();
+      warp_lu_solve(fb.LU, fb.piv, r, col, wk, lane);
+      for (int i = lane; i < r; i += 32) v[Rr[i] * nrhs + c] = col[i];
+      __syncwarp();
+    }
+  } else if (mode == SWEEP_SOLVE_BWD) {
+    // U: v_R -= G v_J
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int ri = e % r, c = e / r;
+      T s = (T)0;
+      for (int a = 0; a < nj; a++) s += fb.G[ri + (int64_t)a * r] * v[fb.J[a] * nrhs + c];
+      vR[ri * nrhs + c] -= s;
+    }
+    __syncthreads();
+    // L_T: v_S -= T v_R
+    for (int e = tid; e < k * nrhs; e += NT) {
+      int q = e / nrhs, c = e % nrhs;
+      T s = (T)0;
+      for (int ri = 0; ri < r; ri++) s += fb.Tm[q + (int64_t)ri * k] * vR[ri * nrhs + c];
+      v[S[q] * nrhs + c] = vS[e] - s;
+    }
+    for (int e = tid; e < r * nrhs; e += NT) v[Rr[e / nrhs] * nrhs + e % nrhs] = vR[e];
+  } else if (mode == SWEEP_APPLY_FWD) {
+    // L_T^{-1}: v_S += T v_R
+    for (int e = tid; e < k * nrhs; e += NT) {
+      int q = e / nrhs, c = e % nrhs;
+      T s = (T)0;
+      for (int ri = 0; ri < r; ri++) s += fb.Tm[q + (int64_t)ri * k] * vR[ri * nrhs + c];
+      v[S[q] * nrhs + c] = vS[e] + s;
+    }
+    __syncthreads();
+    // U^{-1}: v_R += G v_J (v_S already updated in v)
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int ri = e % r, c = e / r;
+      T s = (T)0;
+      for (int a = 0; a < nj; a++) s += fb.G[ri + (int64_t)a * r] * v[fb.J[a] * nrhs + c];
+      vR[ri * nrhs + c] += s;
+    }
+    __syncthreads();
+    // D: y_R = P^T L U v_R
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int i = e % r, c = e / r;
+      T s = (T)0;
+      for (int l = i; l < r; l++) s += fb.LU[(int64_t)i * r + l] * vR[l * nrhs + c];
+      tmp[i + (int64_t)c * r] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int i = e % r, c = e / r;
+      T s = tmp[i + (int64_t)c * r];
+      for (int l = 0; l < i; l++) s += fb.LU[(int64_t)i * r + l] * tmp[l + (int64_t)c * r];
+      v[Rr[fb.piv[i]] * nrhs + c] = s;
+    }
+  } else {  // SWEEP_APPLY_BWD
+    // L^{-1}: v_J += E v_R
+    for (int e = tid; e < nj * nrhs; e += NT) {
+      int a = e % nj, c = e / nj;
+      T s = (T)0;
+      for (int ri = 0; ri < r; ri++) s += fb.E[a + (int64_t)ri * nj] * vR[ri * nrhs + c];
+      v[fb.J[a] * nrhs + c] += s;
+    }
+    __syncthreads();
+    // U_T^{-1}: v_R += T^T v_S (v_S updated above, S is part of J)
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int ri = e / nrhs, c = e % nrhs;
+      T s = (T)0;
+      for (int q = 0; q < k; q++) s += fb.Tm[q + (int64_t)ri * k] * v[S[q] * nrhs + c];
+      v[Rr[ri] * nrhs + c] = vR[e] + s;
+    }
+  }
+}
+
+template <typename T>
+void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
+                  cudaStream_t st) {
+  if (count == 0) return;
+  // vS, vR (each <= bmax x nrhs) + per-warp scratch (2 r) or an r x nrhs buffer
+  size_t wk = (size_t)2 * (NT / 32) * bmax;
+  if ((size_t)bmax * nrhs > wk) wk = (size_t)bmax * nrhs;
+  size_t smem = ((size_t)2 * bmax * nrhs + wk) * sizeof(T) + 64;
+  cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs);
+}
+
+// Top block: solve (mode 0) or multiply (mode 1), one CTA per right-hand side.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_top(int mode, const T *LU, const int *piv, const int64_t *top,
+                                              int n, T *v, int nrhs, T *work) {
+  const int c = blockIdx.x;
+  T *y = work + (int64_t)c * 2 * n;
+  T *u = y + n;
+  const int tid = threadIdx.x;
+  if (mode == 0) {
+    for (int i = tid; i < n; i += blockDim.x) y[i] = v[top[piv[i]] * nrhs + c];
+    __syncthreads();
+    for (int i = 0; i < n; i++) {
+      T yi = y[i];
+      for (int l = i + 1 + tid; l < n; l += blockDim.x) y[l] -= LU[(int64_t)l * n + i] * yi;
+      __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      T yi = y[i] / LU[(int64_t)i * n + i];
+      __syncthreads();
+      if (tid == 0) y[i] = yi;
+      for (int l = tid; l < i; l += blockDim.x) y[l] -= LU[(int64_t)l * n + i] * yi;
+      __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) v[top[i] * nrhs + c] = y[i];
+  } else {
+    for (int i = tid; i < n; i += blockDim.x) y[i] = v[top[i] * nrhs + c];
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      T s = (T)0;
+      for (int l = i; l < n; l++) s += LU[(int64_t)i * n + l] * y[l];
+      u[i] = s;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      T s = u[i];
+      for (int l = 0; l < i; l++) s += LU[(int64_t)i * n + l] * u[l];
+      v[top[piv[i]] * nrhs + c] = s;
+    }
+  }
+}
+
+template <typename T>
+void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v, int nrhs,
+                T *work, cudaStream_t st) {
+  if (ntop == 0) return;
+  k_top<T><<<nrhs, 1024, 0, st>>>(mode, LU, piv, top, ntop, v, nrhs, work);
+}
+
+// dir 0: out_t[g*nrhs+c] = in[perm[g] + c*n];  dir 1: out[perm[g] + c*n] = in_t[g*nrhs+c]
+template <typename T>
+__global__ void k_permute(int dir, const int64_t *perm, const double *in, T *tv, double *out, int64_t n,
+                          int nrhs) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * nrhs) return;
+  int64_t g = e / nrhs;
+  int c = (int)(e % nrhs);
+  if (dir == 0)
+    tv[e] = (T)in[perm[g] + (int64_t)c * n];
+  else
+    out[perm[g] + (int64_t)c * n] = (double)tv[e];
+}
+
+template <typename T>
+void launch_permute(int dir, const int64_t *perm, const double *in, T *tv, double *out, int64_t n, int nrhs,
+                    cudaStream_t st) {
+  int64_t tot = n * nrhs;
+  if (tot == 0) return;
+  k_permute<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dir, perm, in, tv, out, n, nrhs);
+}
+
+// Exact FP64 y = A x by direct summation (tree-ordered points, caller order
+// vectors through perm).  One thread per target, sources staged in shared
+// memory.
+__global__ void __launch_bounds__(256) k_matvec(const double *xt, int dim, KernelParams K, const int64_t *perm,
+                                                const double *xin, double *yout, int64_t n, int nrhs) {
+  __shared__ double sp[256 * 3];
+  __shared__ double sx[256 * 4];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int cb = blockIdx.y * 4;
+  const int nc = min(4, nrhs - cb);
+  double xi[3] = {0, 0, 0};
+  if (i < n)
+    for (int d = 0; d < dim; d++) xi[d] = xt[i * dim + d];
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t j0 = 0; j0 < n; j0 += 256) {
+    int64_t j = j0 + threadIdx.x;
+    if (j < n) {
+      for (int d = 0; d < dim; d++) sp[threadIdx.x * 3 + d] = xt[j * dim + d];
+      for (int c = 0; c < nc; c++) sx[threadIdx.x * 4 + c] = xin[perm[j] + (int64_t)(cb + c) * n];
+    }
+    __syncthreads();
+    int lim = (int)min((int64_t)256, n - j0);
+    if (i < n) {
+      for (int q = 0; q < lim; q++) {
+        int64_t jj = j0 + q;
+        double a;
+        if (jj == i) {
+          a = K.diag;
+        } else {
+          double r2 = 0.0;
+          for (int d = 0; d < dim; d++) {
+            double z = xi[d] - sp[q * 3 + d];
+            r2 += z * z;
+          }
+          a = K.w * kof(K.kind, r2);
+        }
+        for (int c = 0; c < nc; c++) acc[c] += a * sx[q * 4 + c];
+      }
+    }
+    __syncthreads();
+  }
+  if (i < n)
+    for (int c = 0; c < nc; c++) yout[perm[i] + (int64_t)(cb + c) * n] = acc[c];
+}
+
+void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const int64_t *perm, const double *xin,
+                   double *yout, int64_t n, int nrhs, cudaStream_t st) {
+  if (n == 0) return;
+  dim3 g((unsigned)((n + 255) / 256), (nrhs + 3) / 4);
+  k_matvec<<<g, 256, 0, st>>>(x_tree, dim, K, perm, xin, yout, n, nrhs);
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define RSS_INST(T)                                                                                          \
+  template void launch_assemble<T>(const AssembleList &, T *, const LevelDev<T> *, const Points &,             \
+                                   const KernelParams &, int64_t, cudaStream_t);                              \
+  template void launch_id<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, int, const Points &,       \
+                             const KernelParams &, const ProxyParams &, double, T *, int64_t, bool, cudaStream_t, \
+                             int *);                                                                          \
+  template void launch_elim<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, T *, int64_t,            \
+                               cudaStream_t, int *);                                                          \
+  template void launch_schur<T>(const LevelDev<T> &, const FBox<T> *, const int *, int, int, const T *, int64_t, \
+                                cudaStream_t);                                                                \
+  template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \
+  template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, cudaStream_t);                 \
+  template void launch_top<T>(int, const T *, const int *, const int64_t *, int, T *, int, T *, cudaStream_t); \
+  template void launch_permute<T>(int, const int64_t *, const double *, T *, double *, int64_t, int,          \
+                                  cudaStream_t);
+RSS_INST(float)
+RSS_INST(double)
+
+}  // namespace rss

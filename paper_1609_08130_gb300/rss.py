@@ -1,0 +1,230 @@
+"""Thin Python binding of the RS-S C ABI (include/rss.h).
+
+Argument marshalling only: every step of the factorization, apply and solve
+runs in the CUDA kernels of ``librss.so``.  Device buffers are torch CUDA
+tensors; the binding passes their data pointers and the current stream.
+There is no fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_INC = os.path.join(os.path.dirname(_HERE), "include")
+LIB_PATH = os.path.join(_HERE, "librss.so")
+SOURCES = ["api.cu", "kernels.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+RSS_OK, RSS_EINVAL, RSS_ENOMEM, RSS_ECUDA, RSS_ENUMERIC, RSS_ETIMEOUT, RSS_ENOTCONV = range(7)
+LAPLACE2D_LOG, LAPLACE3D_INV = 0, 1
+FP64, MIXED = 0, 1
+
+
+def _nvcc():
+    for c in [os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"]:
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False) -> str:
+    """Compile librss.so in-tree for sm_103a (translation units in parallel)."""
+    srcs = [os.path.join(_CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(_CSRC, h) for h in ("common.cuh", "internal.h")] + \
+        [os.path.join(_INC, "rss.h")]
+    if not force and os.path.exists(LIB_PATH) and \
+            os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
+        return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *NVCC_FLAGS, "--threads", "2", "-o", tmp, *srcs]
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class RSSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rss status {status}: {msg}")
+        self.status = status
+
+
+class _Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("diag", C.c_double), ("weight", C.c_double)]
+
+
+class _Options(C.Structure):
+    _fields_ = [("prec", C.c_int), ("n_proxy", C.c_int), ("proxy_radius", C.c_double),
+                ("use_graphs", C.c_int), ("stream", C.c_void_p)]
+
+
+_lib = None
+
+# Every entry point declared in include/rss.h, with its ctypes signature.
+_SIGS = {
+    "rss_build_tree": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "rss_tree_query": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rss_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, _Kernel, C.c_double, C.c_int,
+                             C.POINTER(_Options), C.POINTER(C.c_void_p)]),
+    "rss_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rss_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rss_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rss_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rss_free": (None, [C.c_void_p]),
+    "rss_last_error": (C.c_char_p, []),
+}
+
+
+def lib(load_only: bool = False):
+    """Load librss.so (building it first if needed)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH) and not load_only:
+            build()
+        if not os.path.exists(LIB_PATH):
+            raise RSSError(RSS_ECUDA, f"CUDA library not built: {LIB_PATH}")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != RSS_OK:
+        raise RSSError(st, lib().rss_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RSSError(RSS_ECUDA, "no CUDA device")
+    return torch
+
+
+def _dev_f64(t, shape_hint=None):
+    torch = _torch()
+    t = torch.as_tensor(t)
+    if t.device.type != "cuda":
+        t = t.to("cuda")
+    return t.to(torch.float64).contiguous()
+
+
+class Tree:
+    """rss_build_tree: adaptive 2^d-tree; arrays copied out with rss_tree_query."""
+
+    def __init__(self, pts, leaf: int = 64):
+        pts = _dev_f64(pts)
+        n, dim = pts.shape
+        h = C.c_void_p()
+        _check(lib().rss_build_tree(C.c_void_p(pts.data_ptr()), n, dim, leaf, C.byref(h)))
+        self.h = h
+        self.n, self.dim, self.leaf = n, dim, leaf
+        s = self.query(6, "int64")
+        self.nnode, self.maxdepth = int(s[0]), int(s[1])
+
+    def query(self, what: int, dtype: str):
+        import numpy as np
+        nb = C.c_size_t(0)
+        _check(lib().rss_tree_query(self.h, what, None, C.byref(nb)))
+        buf = np.empty(max(nb.value // np.dtype(dtype).itemsize, 1), dtype=dtype)
+        _check(lib().rss_tree_query(self.h, what, C.c_void_p(buf.ctypes.data), C.byref(nb)))
+        return buf[: nb.value // np.dtype(dtype).itemsize]
+
+    def perm(self):
+        return self.query(0, "int64")
+
+    def nodes(self):
+        return dict(depth=self.query(1, "int32"), parent=self.query(2, "int32"),
+                    coord=self.query(3, "int32").reshape(-1, 3), start=self.query(4, "int64"),
+                    count=self.query(5, "int64"))
+
+    def level_boxes(self, t: int):
+        return self.query(100 + t, "int32")
+
+    def box_lists(self, t: int):
+        """Per box of depth t (elimination order): (near codes, ring codes)."""
+        rec = self.query(200 + t, "int32")
+        out, i = [], 0
+        while i < len(rec):
+            nn, nr = int(rec[i]), int(rec[i + 1])
+            out.append((rec[i + 2:i + 2 + nn].copy(), rec[i + 2 + nn:i + 2 + nn + nr].copy()))
+            i += 2 + nn + nr
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.rss_free(self.h)
+            self.h = None
+
+
+class Factorization:
+    """rss_factor: RS-S factorization of A = diag*I + w*K on the given points.
+
+    pts: (n, dim) float64 (moved to the GPU).  kind: 0 2D log kernel, 1 3D
+    1/r kernel.  prec: FP64 or MIXED (FP32 factor).
+    """
+
+    def __init__(self, pts, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
+                 weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None):
+        torch = _torch()
+        pts = _dev_f64(pts)
+        self.n, self.dim = pts.shape
+        self.prec = prec
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream))
+        h = C.c_void_p()
+        _check(lib().rss_factor(C.c_void_p(pts.data_ptr()), self.n, self.dim, _Kernel(kind, diag, weight),
+                                eps, leaf, C.byref(opts), C.byref(h)))
+        self.h = h
+
+    def _vec(self, x):
+        torch = _torch()
+        x = _dev_f64(x)
+        one = x.dim() == 1
+        if one:
+            x = x.reshape(1, -1)
+        if x.shape[1] != self.n:
+            raise RSSError(RSS_EINVAL, "vector length does not match the factor")
+        return x, one, torch.empty_like(x)
+
+    def _call(self, fn, x):
+        x, one, y = self._vec(x)
+        _check(fn(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0]))
+        return y[0] if one else y
+
+    def apply(self, x):
+        """y = F x; x of shape (n,) or (nrhs, n)."""
+        return self._call(lib().rss_apply, x)
+
+    def solve(self, b):
+        """x = F^{-1} b; b of shape (n,) or (nrhs, n)."""
+        return self._call(lib().rss_solve, b)
+
+    def matvec(self, x):
+        """Exact FP64 A x by direct summation."""
+        return self._call(lib().rss_matvec, x)
+
+    def stats(self) -> dict:
+        import numpy as np
+        nb = C.c_size_t(0)
+        _check(lib().rss_stats(self.h, None, C.byref(nb)))
+        buf = np.empty(nb.value // 8, dtype=np.int64)
+        _check(lib().rss_stats(self.h, C.c_void_p(buf.ctypes.data), C.byref(nb)))
+        nbox = int(buf[0])
+        boxes = buf[6:6 + 4 * nbox].reshape(nbox, 4)
+        return dict(nbox=nbox, ntop=int(buf[1]), factor_bytes=int(buf[2]), maxdepth=int(buf[3]),
+                    n=int(buf[4]), prec=int(buf[5]), depth=boxes[:, 0].copy(), b=boxes[:, 1].copy(),
+                    k=boxes[:, 2].copy(), nj=boxes[:, 3].copy())
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.rss_free(self.h)
+            self.h = None

@@ -1,0 +1,157 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars: bit-exact for the tree and index lists; for the factor, the apply and
+solve results must agree with the FP64 oracle's within 10*eps (relative),
+and the GPU's own apply error ||Ax - Fx|| / ||Ax|| must stay within 10*eps of
+the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_08130_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1609_08130_gb300 as p
+    p.build()
+    return p
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+TREE_CASES = {
+    "grid2d": lambda: inputs.grid_points(64, 2),
+    "grid3d": lambda: inputs.grid_points(16, 3),
+    "random2d": lambda: inputs.random_points(5, 5000, 2),
+    "random3d": lambda: inputs.random_points(6, 3000, 3),
+}
+
+
+@pytest.mark.parametrize("case", list(TREE_CASES))
+def test_tree_and_lists_bit_exact(pkg, case):
+    pts = TREE_CASES[case]()
+    leaf = 64 if case != "random3d" else 32
+    gt = pkg.Tree(_cuda(pts), leaf)
+    ot = oracle.Tree(pts, leaf)
+    assert np.array_equal(gt.perm(), ot.perm())
+    gn, on = gt.nodes(), ot.nodes()
+    for key in ["depth", "parent", "coord", "start", "count"]:
+        assert np.array_equal(gn[key], on[key]), key
+    assert gt.maxdepth == ot.maxdepth
+    for t in range(ot.maxdepth, 1, -1):
+        ob = ot.level_boxes(t)
+        assert np.array_equal(gt.level_boxes(t), ob)
+        lists = gt.box_lists(t)
+        for q, node in enumerate(ob):
+            near, ring = ot.box_lists(int(node))
+            assert np.array_equal(lists[q][0], near) and np.array_equal(lists[q][1], ring)
+
+
+FACTOR_CASES = {
+    # name: (points, kind, eps, leaf)
+    "grid2d_4096": (lambda: inputs.grid_points(64, 2), 0, 1e-6, 64),
+    "grid2d_1e9": (lambda: inputs.grid_points(64, 2), 0, 1e-9, 64),
+    "random2d": (lambda: inputs.random_points(21, 3000, 2), 0, 1e-6, 64),
+    "grid3d": (lambda: inputs.grid_points(16, 3), 1, 1e-3, 64),
+    "grid2d_ragged": (lambda: inputs.grid_points(48, 2), 0, 1e-6, 40),
+}
+
+
+def _oracle_factor(pts, kind, eps, leaf):
+    return oracle.Factor(oracle.Tree(pts, leaf), kind, eps)
+
+
+@pytest.mark.parametrize("case", list(FACTOR_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_factor_matches_oracle(pkg, case, prec):
+    mk, kind, eps, leaf = FACTOR_CASES[case]
+    if prec == "mixed" and eps < 1e-7:
+        pytest.skip("an FP32 factor cannot resolve eps below FP32 precision")
+    pts = mk()
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), kind, eps, leaf=leaf, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+    of = _oracle_factor(pts, kind, eps, leaf)
+    st = f.stats()
+    ob = of.boxes()
+    # same boxes in the same elimination order
+    assert st["nbox"] == len(ob)
+    assert [b["depth"] for b in ob] == st["depth"].tolist()
+    assert [b["b"] for b in ob if b["depth"] == st["maxdepth"]] == \
+        st["b"][st["depth"] == st["maxdepth"]].tolist()
+    same_k = np.mean(np.array([b["k"] for b in ob]) == st["k"])
+    if prec == "fp64":
+        assert same_k > 0.9, same_k
+    x = inputs.rhs(11, n, 3)
+    Ax = oracle.matvec(pts, kind, x)
+    Fo = of.apply(x)
+    Fg = f.apply(_cuda(x)).cpu().numpy()
+    rel = np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo)
+    assert rel <= 10 * eps, rel
+    ea_g = np.linalg.norm(Ax - Fg) / np.linalg.norm(Ax)
+    ea_o = np.linalg.norm(Ax - Fo) / np.linalg.norm(Ax)
+    assert ea_g <= ea_o + 10 * eps
+    So = of.solve(Ax)
+    Sg = f.solve(_cuda(Ax)).cpu().numpy()
+    rel_s = np.linalg.norm(Sg - So) / np.linalg.norm(So)
+    assert rel_s <= 10 * eps, rel_s
+    es_g = np.linalg.norm(Sg - x) / np.linalg.norm(x)
+    es_o = np.linalg.norm(So - x) / np.linalg.norm(x)
+    assert es_g <= es_o + 10 * eps
+    # one right-hand side at a time gives the same columns
+    one = f.apply(_cuda(x[1])).cpu().numpy()
+    assert np.allclose(one, Fg[1], rtol=1e-12 if prec == "fp64" else 1e-5, atol=0)
+
+
+def test_exact_limit(pkg):
+    """eps -> 0: the GPU factor reproduces A (exact block elimination)."""
+    pts = inputs.grid_points(32, 2)
+    f = pkg.Factorization(_cuda(pts), 0, 1e-14, leaf=16)
+    x = inputs.normal(3, len(pts))
+    A = oracle.dense_matrix(pts, 0)
+    y = f.apply(_cuda(x)).cpu().numpy()
+    assert np.linalg.norm(y - A @ x) / np.linalg.norm(A @ x) < 1e-12
+    b = inputs.normal(4, len(pts))
+    xs = f.solve(_cuda(b)).cpu().numpy()
+    ref = np.linalg.solve(A, b)
+    assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) < 1e-11
+
+
+def test_matvec_matches_oracle(pkg):
+    pts = inputs.random_points(8, 2000, 3)
+    f = pkg.Factorization(_cuda(pts), 1, 1e-3, leaf=64)
+    x = inputs.rhs(5, 2000, 2)
+    y = f.matvec(_cuda(x)).cpu().numpy()
+    assert np.allclose(y, oracle.matvec(pts, 1, x), rtol=1e-12, atol=1e-14)
+
+
+def test_degenerate_sizes(pkg):
+    # below one leaf: no skeletonization, F is the dense LU
+    pts = inputs.random_points(2, 50, 2)
+    f = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64)
+    assert f.stats()["nbox"] == 0 and f.stats()["ntop"] == 50
+    A = oracle.dense_matrix(pts, 0)
+    b = inputs.normal(1, 50)
+    assert np.allclose(f.solve(_cuda(b)).cpu().numpy(), np.linalg.solve(A, b), rtol=1e-12)
+    # one point
+    f1 = pkg.Factorization(_cuda(pts[:1]), 0, 1e-6, leaf=64)
+    assert np.allclose(f1.solve(_cuda(np.array([2.0]))).cpu().numpy(), [2.0])
+    # empty problem
+    f0 = pkg.Factorization(torch.zeros((0, 2), dtype=torch.float64, device="cuda"), 0, 1e-6, leaf=64)
+    assert f0.stats()["ntop"] == 0
+
+
+def test_bad_arguments_raise(pkg):
+    pts = _cuda(inputs.grid_points(8, 2))
+    with pytest.raises(pkg.RSSError):
+        pkg.Factorization(pts, 5, 1e-6)
+    with pytest.raises(pkg.RSSError):
+        pkg.Factorization(pts, 0, -1.0)
