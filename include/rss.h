@@ -58,8 +58,10 @@ typedef struct {
   int prec;            /* rss_precision: FP64 everywhere, or an FP32 factor */
   int n_proxy;         /* proxy points; 0: 64 (2D) / 512 (3D) (Sec. 4) */
   double proxy_radius; /* in box sides; 0: 2.5 (Sec. 3.2) */
-  int use_graphs;      /* capture apply/solve sweeps in CUDA graphs */
+  int use_graphs;      /* reserved, must be 0 */
   void *stream;        /* cudaStream_t; NULL = legacy default stream */
+  int profile;         /* 1: time every kernel launch with CUDA events on the
+                          stream (see rss_profile) */
 } rss_options;
 
 typedef struct rss_tree rss_tree;
@@ -116,8 +118,26 @@ rss_status rss_apply(const rss_factorization *f, const double *x, double *y, int
  * may not alias.  nrhs >= 1. */
 rss_status rss_solve(const rss_factorization *f, const double *b, double *x, int nrhs);
 
-/* rss_matvec -- y = A x exactly in FP64 by direct summation over all pairs
- * (the operator being factored; used for residuals).  Device buffers. */
+/* rss_solve_refined -- solve A x = b to a relative residual
+ * max_c ||b_c - A x_c|| / ||b_c|| <= tol by GMRES-based iterative refinement
+ * (Carson & Higham): x0 = F^{-1} b, then FP64 residuals with the exact
+ * operator (rss_matvec) and corrections from restarted FGMRES(10) in FP64,
+ * right-preconditioned by the factor's solve (which runs in FP32 for a
+ * RSS_MIXED factor).  The paper uses F as a CG preconditioner instead
+ * (Sec. 4); GMRES is used here because a FP32 factor is not symmetric to
+ * FP64 accuracy.
+ *   b, x: device, n x nrhs column-major, may not alias.  maxit: outer
+ *   refinement steps (>= 0).  iters (may be NULL): total inner iterations;
+ *   relres (may be NULL): final relative residual (max over columns).
+ * Errors: RSS_EINVAL; RSS_ENOTCONV when tol is not met within maxit
+ * (x then holds the last iterate). */
+rss_status rss_solve_refined(const rss_factorization *f, const double *b, double *x, int nrhs, double tol,
+                             int maxit, int *iters, double *relres);
+
+/* rss_matvec -- y = A x in FP64 with the exact operator being factored:
+ * an FFT convolution when the points are the cell centres of an s^dim grid
+ * (s a power of two; exact up to FP64 rounding), direct summation over all
+ * pairs otherwise.  Device buffers, n x nrhs column-major. */
 rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs);
 
 /* rss_stats -- factor statistics into a HOST int64 array:
@@ -127,8 +147,23 @@ rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, in
  * *nbytes in/out as in rss_tree_query. */
 rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes);
 
+/* rss_profile -- per-kernel-class totals of a factor created with
+ * options.profile = 1, accumulated over rss_factor and every later
+ * rss_apply / rss_solve on it, into a HOST double array of 4 * 8 entries:
+ * for class c in {0 assemble, 1 id, 2 elim, 3 schur, 4 top LU, 5 sweep,
+ * 6 top solve/multiply, 7 permute}: {launches, milliseconds (CUDA events on
+ * the launching stream), algorithmic bytes, algorithmic flops}.  The
+ * algorithmic counts are the data the method must move or compute (stated
+ * per class in the implementation), not hardware counters.
+ * reset != 0 clears the totals after copying.  *nbytes in/out. */
+rss_status rss_profile(const rss_factorization *f, int reset, double *buf, size_t *nbytes);
+
 /* rss_free -- release a tree or factor handle (NULL-safe). */
 void rss_free(void *handle);
+
+/* rss_kernel_launches -- number of CUDA kernel launches this library has
+ * made in this process (all devices, all handles). */
+int64_t rss_kernel_launches(void);
 
 /* rss_last_error -- message of the last failing call on this thread. */
 const char *rss_last_error(void);

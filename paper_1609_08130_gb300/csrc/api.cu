@@ -333,9 +333,58 @@ struct Phase {
   int first, count, bmax;
 };
 
+// Per-kernel-class timing with CUDA events on the launching stream, plus the
+// algorithmic bytes and flops of each launch (filled in once the ranks of the
+// boxes it handled are known).
+enum KClass { KC_ASSEMBLE, KC_ID, KC_ELIM, KC_SCHUR, KC_TOPLU, KC_SWEEP, KC_TOP, KC_PERMUTE, KC_N };
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  int first, count, nrhs;
+  double bytes, flops;
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> spare;
+  double ms[KC_N] = {}, bytes[KC_N] = {}, flops[KC_N] = {};
+  int64_t launches[KC_N] = {};
+  cudaEvent_t ev() {
+    if (!spare.empty()) {
+      cudaEvent_t e = spare.back();
+      spare.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  int begin(int cls, cudaStream_t st, int first = 0, int count = 0, int nrhs = 0, double bytes_ = 0,
+            double flops_ = 0) {
+    if (!on) return -1;
+    ProfRec r{cls, ev(), ev(), first, count, nrhs, bytes_, flops_};
+    CK(cudaEventRecord(r.a, st));
+    pending.push_back(r);
+    return (int)pending.size() - 1;
+  }
+  void end(int idx, cudaStream_t st) {
+    if (idx >= 0) CK(cudaEventRecord(pending[idx].b, st));
+  }
+  void reset() {
+    for (int c = 0; c < KC_N; c++) ms[c] = bytes[c] = flops[c] = 0, launches[c] = 0;
+  }
+  ~Prof() {
+    for (auto &r : pending) cudaEventDestroy(r.a), cudaEventDestroy(r.b);
+    for (auto e : spare) cudaEventDestroy(e);
+  }
+};
+
 struct FactorBase {
   uint32_t magic = MAGIC_FACTOR;
   int prec = 0;
+  mutable Prof prof;
   virtual ~FactorBase() {}
 };
 
@@ -358,6 +407,13 @@ template <typename T> struct Factor : FactorBase {
   DBuf d_top, d_topLU, d_toppiv;
   mutable DBuf d_work, d_topwork;
   mutable int work_nrhs = 0;
+  // FP64 residual operator: FFT convolution when the points are the cell
+  // centres of a regular grid, direct summation otherwise
+  int grid_side = 0;
+  std::vector<int64_t> grid_index;  // caller order
+  mutable GridOp G;
+  mutable DBuf g_gidx, g_C, g_X, g_tw;
+  mutable bool grid_ready = false;
 
   void *alloc_store(size_t bytes) {
     store.emplace_back(new DBuf());
@@ -374,11 +430,88 @@ template <typename T> static void ensure_work(const Factor<T> &F, int nrhs) {
   F.work_nrhs = nrhs;
 }
 
+// Algorithmic work of one launch over boxes [first, first+count):
+//   ID     : Householder reduction of the m x b ID matrix (m = |O| + n_p):
+//            2 m b^2 flops; bytes = the |O| x b rows read + T written.
+//   ELIM   : X_JR, X_RJ (2 * 2 nj k r), X_RR (4 r^2 k), LU (2/3 r^3), E and G
+//            solves (2 * 2 nj r^2) flops; bytes = A_BB + near rows/columns
+//            read, E, G, LU written.
+//   SCHUR  : 2 nj^2 r flops; bytes = nj^2 read + written, E and X_RJ read.
+//   SWEEP  : 2 nrhs (k r + 2 nj r + r^2) flops; bytes = the factor's
+//            T, E, G, LU read once + the vector entries touched.
+template <typename T> static void prof_collect(const Factor<T> &F) {
+  Prof &P = F.prof;
+  if (P.pending.empty()) return;
+  const double sz = sizeof(T);
+  for (auto &r : P.pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    double bytes = r.bytes, flops = r.flops;
+    for (int q = r.first; q < r.first + r.count && r.cls != KC_ASSEMBLE && r.cls != KC_TOPLU && r.cls != KC_TOP &&
+                          r.cls != KC_PERMUTE;
+         q++) {
+      const FBox<T> &b = F.h_boxes[q];
+      double B = b.b, k = b.k, rr = b.r, nj = b.nj, no = b.no, m = b.no + F.px.np;
+      if (r.cls == KC_ID) {
+        flops += 2.0 * m * B * B;
+        bytes += (no * B + k * rr) * sz + B * 8.0;
+      } else if (r.cls == KC_ELIM) {
+        flops += 4.0 * nj * k * rr + 4.0 * rr * rr * k + 2.0 / 3.0 * rr * rr * rr + 4.0 * nj * rr * rr;
+        bytes += (B * B + 2.0 * (nj - k) * B + 2.0 * nj * rr + rr * rr) * sz;
+      } else if (r.cls == KC_SCHUR) {
+        flops += 2.0 * nj * nj * rr;
+        bytes += (2.0 * nj * nj + 2.0 * nj * rr) * sz;
+      } else if (r.cls == KC_SWEEP) {
+        flops += 2.0 * r.nrhs * (k * rr + 2.0 * nj * rr + rr * rr);
+        bytes += (k * rr + 2.0 * nj * rr + rr * rr) * sz + 2.0 * (nj + rr) * r.nrhs * sz;
+      }
+    }
+    P.ms[r.cls] += ms;
+    P.bytes[r.cls] += bytes;
+    P.flops[r.cls] += flops;
+    P.launches[r.cls] += 1;
+    P.spare.push_back(r.a);
+    P.spare.push_back(r.b);
+  }
+  P.pending.clear();
+}
+
 static int check_err(DBuf &d_err, cudaStream_t st) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return h;
+}
+
+// Points exactly at the cell centres ((i + 1/2) / s) of an s^dim grid, s a
+// power of two, each cell used once: record every point's grid index.
+template <typename T> static void detect_grid(Factor<T> &F) {
+  const HTree &T_ = F.tree;
+  const int dim = T_.dim;
+  const int64_t n = T_.n;
+  F.grid_side = 0;
+  if (n < 8) return;
+  int64_t s = (int64_t)llround(pow((double)n, 1.0 / dim));
+  int64_t tot = 1;
+  for (int d = 0; d < dim; d++) tot *= s;
+  if (tot != n || (s & (s - 1)) != 0 || 2 * s > 2048) return;
+  std::vector<int64_t> gi(n);
+  std::vector<char> seen(n, 0);
+  for (int64_t g = 0; g < n; g++) {
+    int64_t lin = 0, mul = 1;
+    for (int d = 0; d < dim; d++) {
+      double v = T_.x[g * dim + d] * (double)s - 0.5;
+      double iv = nearbyint(v);
+      if (v != iv || iv < 0 || iv >= (double)s) return;
+      lin += (int64_t)iv * mul;
+      mul *= s;
+    }
+    if (seen[lin]) return;
+    seen[lin] = 1;
+    gi[T_.perm[g]] = lin;
+  }
+  F.grid_side = (int)s;
+  F.grid_index.swap(gi);
 }
 
 template <typename T> static void run_factor(Factor<T> &F) {
@@ -410,6 +543,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
   }
   F.d_err.alloc(sizeof(int), st);
   CK(cudaMemsetAsync(F.d_err.p, 0, sizeof(int), st));
+  detect_grid(F);
 
   int nbox_total = 0;
   for (int t = 2; t <= T_.maxdepth; t++) nbox_total += (int)T_.level[t].size();
@@ -448,7 +582,9 @@ template <typename T> static void run_factor(Factor<T> &F) {
     upload(e2, ncol, st);
     AssembleList L{(int)row_off.size(), ptr<int64_t>(a), ptr<int64_t>(b2), ptr<int64_t>(c2),
                    ptr<int>(d2), ptr<int>(e2), ptr<int64_t>(D.cell_dofs), ptr<int64_t>(D.cell_dofs), 0};
+    int pi = F.prof.begin(KC_ASSEMBLE, st, 0, 0, 0, 2.0 * (double)H.pool_elems * sizeof(T), 0.0);
     launch_assemble<T>(L, ptr<T>(D.pool), prev, F.P, F.K, maxblk, st);
+    F.prof.end(pi, st);
     check_launch("assemble");
   };
 
@@ -573,14 +709,20 @@ template <typename T> static void run_factor(Factor<T> &F) {
     gel.alloc((size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st);
     for (auto &p : ph) {
       const int *bl = ptr<int>(d_list) + p.first;
+      int pi = F.prof.begin(KC_ID, st, base + p.first, p.second);
       launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, H.bmax, 0, F.P, F.K, F.px, F.eps,
                    ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
       check_launch("id");
+      F.prof.end(pi, st);
+      pi = F.prof.begin(KC_ELIM, st, base + p.first, p.second);
       launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, H.bmax, ptr<T>(gel), el_stride, st,
                      ptr<int>(F.d_err));
       check_launch("elim");
+      F.prof.end(pi, st);
+      pi = F.prof.begin(KC_SCHUR, st, base + p.first, p.second);
       launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
       check_launch("schur");
+      F.prof.end(pi, st);
       F.phases.push_back({base + p.first, p.second, H.bmax});
     }
     // ranks of this level -> active DOFs of the next
@@ -591,6 +733,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     if (!ai.empty())
       CK(cudaMemcpyAsync(ai.data(), D->act_idx.p, sizeof(int) * ai.size(), cudaMemcpyDeviceToHost, st));
     int e = check_err(F.d_err, st);
+    prof_collect(F);
     if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the LU of a redundant block"};
     if (e) throw Fail{RSS_ECUDA, "device-side consistency check failed"};
     active.clear();
@@ -629,11 +772,15 @@ template <typename T> static void run_factor(Factor<T> &F) {
       launch_assemble<T>(L, ptr<T>(F.d_topLU), nullptr, F.P, F.K, (int64_t)F.ntop * F.ntop, st);
     }
     check_launch("assemble top");
+    double nt = F.ntop;
+    int pi = F.prof.begin(KC_TOPLU, st, 0, 0, 0, 2.0 * nt * nt * sizeof(T), 2.0 / 3.0 * nt * nt * nt);
     launch_dense_lu<T>(ptr<T>(F.d_topLU), F.ntop, ptr<int>(F.d_toppiv), st, ptr<int>(F.d_err));
     check_launch("top lu");
+    F.prof.end(pi, st);
   }
   prevD.reset();
   int e = check_err(F.d_err, st);
+  prof_collect(F);
   if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the top block"};
   if (e) throw Fail{RSS_ECUDA, "device-side consistency check failed"};
 }
@@ -675,24 +822,197 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   cudaStream_t st = F.st;
   ensure_work(F, nrhs);
   T *v = ptr<T>(F.d_work);
+  Prof &P = F.prof;
+  const double sz = sizeof(T);
+  int pi = P.begin(KC_PERMUTE, st, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
   launch_permute<T>(0, ptr<int64_t>(F.d_perm), in, v, nullptr, F.n, nrhs, st);
+  P.end(pi, st);
   const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
-  if (solve) {
-    for (const Phase &p : F.phases) launch_sweep<T>(SWEEP_SOLVE_FWD, bx, p.first, p.count, v, nrhs, p.bmax, st);
-    launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top), F.ntop, v, nrhs,
-                  ptr<T>(F.d_topwork), st);
-    for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
-      launch_sweep<T>(SWEEP_SOLVE_BWD, bx, it->first, it->count, v, nrhs, it->bmax, st);
-  } else {
-    for (const Phase &p : F.phases) launch_sweep<T>(SWEEP_APPLY_FWD, bx, p.first, p.count, v, nrhs, p.bmax, st);
-    launch_top<T>(1, ptr<T>(F.d_topLU), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top), F.ntop, v, nrhs,
-                  ptr<T>(F.d_topwork), st);
-    for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
-      launch_sweep<T>(SWEEP_APPLY_BWD, bx, it->first, it->count, v, nrhs, it->bmax, st);
+  const int fwd = solve ? SWEEP_SOLVE_FWD : SWEEP_APPLY_FWD, bwd = solve ? SWEEP_SOLVE_BWD : SWEEP_APPLY_BWD;
+  for (const Phase &p : F.phases) {
+    pi = P.begin(KC_SWEEP, st, p.first, p.count, nrhs);
+    launch_sweep<T>(fwd, bx, p.first, p.count, v, nrhs, p.bmax, st);
+    P.end(pi, st);
   }
+  double nt = F.ntop;
+  pi = P.begin(KC_TOP, st, 0, 0, 0, nt * nt * sz + 2.0 * nt * nrhs * sz, 2.0 * nt * nt * nrhs);
+  launch_top<T>(solve ? 0 : 1, ptr<T>(F.d_topLU), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top), F.ntop, v, nrhs,
+                ptr<T>(F.d_topwork), st);
+  P.end(pi, st);
+  for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
+    pi = P.begin(KC_SWEEP, st, it->first, it->count, nrhs);
+    launch_sweep<T>(bwd, bx, it->first, it->count, v, nrhs, it->bmax, st);
+    P.end(pi, st);
+  }
+  pi = P.begin(KC_PERMUTE, st, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
   launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, out, F.n, nrhs, st);
+  P.end(pi, st);
   check_launch("sweeps");
   CK(cudaStreamSynchronize(st));
+  prof_collect(F);
+}
+
+template <typename T> static void apply_A(const Factor<T> &F, const double *x, double *y, int nrhs) {
+  if (F.grid_side > 0) {
+    if (!F.grid_ready) {
+      GridOp &G = F.G;
+      G.dim = F.dim;
+      G.s = F.grid_side;
+      G.L = 2 * F.grid_side;
+      G.logL = 0;
+      while ((1 << G.logL) < G.L) G.logL++;
+      G.n = F.n;
+      G.h = 1.0 / F.grid_side;
+      G.kind = F.K.kind;
+      G.w = F.K.w;
+      G.diag = F.K.diag;
+      int64_t tot = 1;
+      for (int d = 0; d < G.dim; d++) tot *= G.L;
+      upload(F.g_gidx, F.grid_index, F.st);
+      F.g_C.alloc(sizeof(double2) * tot, F.st);
+      F.g_X.alloc(sizeof(double2) * tot, F.st);
+      F.g_tw.alloc(sizeof(double2) * (G.L / 2 + 1), F.st);
+      G.gidx = ptr<int64_t>(F.g_gidx);
+      G.C = ptr<double2>(F.g_C);
+      G.X = ptr<double2>(F.g_X);
+      G.tw = ptr<double2>(F.g_tw);
+      grid_op_setup(G, F.st);
+      check_launch("grid operator setup");
+      F.grid_ready = true;
+    }
+    grid_op_apply(F.G, x, y, nrhs, F.st);
+  } else {
+    launch_matvec(ptr<double>(F.d_x), F.dim, F.K, ptr<int64_t>(F.d_perm), x, y, F.n, nrhs, F.st);
+  }
+  check_launch("residual operator");
+}
+
+// GMRES-based iterative refinement (Carson & Higham): FP64 residuals with
+// the exact operator, each correction from restarted, right-preconditioned
+// FGMRES in FP64 whose preconditioner is the factor's solve (FP32 for the
+// mixed factor).  All right-hand sides advance in lock step.
+template <typename T>
+static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
+                   double *relres) {
+  cudaStream_t st = F.st;
+  const int64_t n = F.n, nn = n * nrhs;
+  const int m = 10;
+  DBuf r, w, V, Z, part, dres;
+  r.alloc(sizeof(double) * nn, st);
+  w.alloc(sizeof(double) * nn, st);
+  V.alloc(sizeof(double) * nn * (m + 1), st);
+  Z.alloc(sizeof(double) * nn * m, st);
+  part.alloc(sizeof(double) * (m + 1) * nrhs * 240, st);
+  dres.alloc(sizeof(double) * (m + 1) * nrhs * 2, st);
+  double *pr = ptr<double>(r), *pw = ptr<double>(w), *pV = ptr<double>(V), *pZ = ptr<double>(Z);
+  double *dd = ptr<double>(dres), *dc = dd + (m + 1) * nrhs;
+  std::vector<double> h((m + 1) * nrhs), h2((m + 1) * nrhs);
+  auto dots = [&](const double *Vb, int nv, const double *vec, std::vector<double> &out) {
+    multidot(Vb, nn, nv, vec, n, nrhs, ptr<double>(part), dd, st);
+    check_launch("multidot");
+    out.resize((size_t)nv * nrhs);
+    CK(cudaMemcpyAsync(out.data(), dd, sizeof(double) * nv * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  };
+  auto comb = [&](double *y, double alpha, const double *Vb, int nv, const std::vector<double> &coef) {
+    CK(cudaMemcpyAsync(dc, coef.data(), sizeof(double) * nv * nrhs, cudaMemcpyHostToDevice, st));
+    combine(y, alpha, Vb, nn, nv, dc, n, nrhs, st);
+    check_launch("combine");
+  };
+  // x0 = F^{-1} b
+  do_sweeps(F, b, x, nrhs, true);
+  std::vector<double> bn;
+  dots(b, 1, b, bn);
+  for (auto &v : bn) v = v > 0 ? sqrt(v) : 1.0;
+  int inner = 0;
+  double rel = 0;
+  bool ok = false;
+  for (int outer = 0; outer <= maxit; outer++) {
+    apply_A(F, x, pw, nrhs);
+    CK(cudaMemcpyAsync(pr, b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+    comb(pr, 1.0, pw, 1, std::vector<double>(nrhs, -1.0));
+    std::vector<double> rn;
+    dots(pr, 1, pr, rn);
+    rel = 0;
+    for (int c = 0; c < nrhs; c++) {
+      rn[c] = sqrt(std::max(rn[c], 0.0));
+      rel = std::max(rel, rn[c] / bn[c]);
+    }
+    if (rel <= tol) {
+      ok = true;
+      break;
+    }
+    if (outer == maxit) break;
+    // FGMRES(m) for A d = r, right-preconditioned by F^{-1}
+    std::vector<double> inv(nrhs);
+    for (int c = 0; c < nrhs; c++) inv[c] = rn[c] > 0 ? 1.0 / rn[c] : 0.0;
+    CK(cudaMemsetAsync(pV, 0, sizeof(double) * nn, st));
+    comb(pV, 0.0, pr, 1, inv);
+    std::vector<double> H((size_t)nrhs * (m + 1) * m, 0.0), g((size_t)nrhs * (m + 1), 0.0), cs(nrhs * m),
+        sn(nrhs * m);
+    for (int c = 0; c < nrhs; c++) g[c * (m + 1)] = rn[c];
+    int jdone = 0;
+    for (int j = 0; j < m; j++) {
+      do_sweeps(F, pV + j * nn, pZ + j * nn, nrhs, true);
+      apply_A(F, pZ + j * nn, pw, nrhs);
+      std::vector<double> hh, hh2, hn;
+      dots(pV, j + 1, pw, hh);  // hh[c * (j+1) + i]
+      std::vector<double> neg(hh.size());
+      for (size_t q = 0; q < hh.size(); q++) neg[q] = -hh[q];
+      comb(pw, 1.0, pV, j + 1, neg);
+      dots(pV, j + 1, pw, hh2);
+      for (size_t q = 0; q < hh2.size(); q++) neg[q] = -hh2[q], hh[q] += hh2[q];
+      comb(pw, 1.0, pV, j + 1, neg);
+      dots(pw, 1, pw, hn);
+      std::vector<double> invn(nrhs);
+      double worst = 0;
+      for (int c = 0; c < nrhs; c++) {
+        double hnc = sqrt(std::max(hn[c], 0.0));
+        invn[c] = hnc > 0 ? 1.0 / hnc : 0.0;
+        double *Hc = &H[(size_t)c * (m + 1) * m];
+        for (int i = 0; i <= j; i++) Hc[i * m + j] = hh[c * (j + 1) + i];
+        Hc[(j + 1) * m + j] = hnc;
+        // previous rotations, then a new one zeroing H[j+1][j]
+        for (int i = 0; i < j; i++) {
+          double a0 = Hc[i * m + j], a1 = Hc[(i + 1) * m + j];
+          Hc[i * m + j] = cs[c * m + i] * a0 + sn[c * m + i] * a1;
+          Hc[(i + 1) * m + j] = -sn[c * m + i] * a0 + cs[c * m + i] * a1;
+        }
+        double a0 = Hc[j * m + j], a1 = Hc[(j + 1) * m + j];
+        double rr = hypot(a0, a1);
+        double cc = rr > 0 ? a0 / rr : 1.0, ss = rr > 0 ? a1 / rr : 0.0;
+        cs[c * m + j] = cc;
+        sn[c * m + j] = ss;
+        Hc[j * m + j] = rr;
+        Hc[(j + 1) * m + j] = 0.0;
+        double *gc = &g[(size_t)c * (m + 1)];
+        gc[j + 1] = -ss * gc[j];
+        gc[j] = cc * gc[j];
+        worst = std::max(worst, fabs(gc[j + 1]) / bn[c]);
+      }
+      CK(cudaMemsetAsync(pV + (j + 1) * nn, 0, sizeof(double) * nn, st));
+      comb(pV + (j + 1) * nn, 0.0, pw, 1, invn);
+      inner++;
+      jdone = j + 1;
+      if (worst <= 0.5 * tol) break;
+    }
+    // y = H^{-1} g (upper triangular), x += Z y
+    std::vector<double> y((size_t)nrhs * jdone);
+    for (int c = 0; c < nrhs; c++) {
+      const double *Hc = &H[(size_t)c * (m + 1) * m];
+      const double *gc = &g[(size_t)c * (m + 1)];
+      for (int i = jdone - 1; i >= 0; i--) {
+        double sacc = gc[i];
+        for (int l = i + 1; l < jdone; l++) sacc -= Hc[i * m + l] * y[c * jdone + l];
+        y[c * jdone + i] = Hc[i * m + i] != 0 ? sacc / Hc[i * m + i] : 0.0;
+      }
+    }
+    comb(x, 1.0, pZ, jdone, y);
+  }
+  if (iters) *iters = inner;
+  if (relres) *relres = rel;
+  CK(cudaStreamSynchronize(st));
+  return ok;
 }
 
 static rss_status sweep_entry(const rss_factorization *f, const double *in, double *out, int nrhs, bool solve) {
@@ -713,6 +1033,8 @@ static rss_status sweep_entry(const rss_factorization *f, const double *in, doub
 extern "C" {
 
 const char *rss_last_error(void) { return g_last_error.c_str(); }
+
+int64_t rss_kernel_launches(void) { return (int64_t)launches_total(); }
 
 rss_status rss_build_tree(const double *pts, int64_t n, int dim, int leaf_size, rss_tree **out) {
   return guard([&] {
@@ -810,6 +1132,7 @@ rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, 
       throw Fail{RSS_EINVAL, "rss_factor: bad arguments"};
     rss_options o{};
     if (opts) o = *opts;
+    const bool prof_on = o.profile != 0;
     if (o.prec != RSS_FP64 && o.prec != RSS_MIXED) throw Fail{RSS_EINVAL, "rss_factor: bad precision"};
     cudaStream_t st = (cudaStream_t)o.stream;
     std::vector<double> h;
@@ -835,15 +1158,39 @@ rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, 
       auto *F = new Factor<double>();
       res->impl.reset(F);
       F->prec = RSS_FP64;
+      F->prof.on = prof_on;
       setup(F);
     } else {
       auto *F = new Factor<float>();
       res->impl.reset(F);
       F->prec = RSS_MIXED;
+      F->prof.on = prof_on;
       setup(F);
     }
     *out = res.release();
   });
+}
+
+rss_status rss_solve_refined(const rss_factorization *f, const double *b, double *x, int nrhs, double tol,
+                             int maxit, int *iters, double *relres) {
+  bool ok = false;
+  rss_status stt = guard([&] {
+    if (!f || !f->impl || nrhs < 1 || !(tol > 0) || maxit < 0) throw Fail{RSS_EINVAL, "rss_solve_refined: bad arguments"};
+    if (f->impl->prec == RSS_FP64) {
+      auto &F = static_cast<const Factor<double> &>(*f->impl);
+      if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
+      ok = F.n == 0 || refine(F, b, x, nrhs, tol, maxit, iters, relres);
+    } else {
+      auto &F = static_cast<const Factor<float> &>(*f->impl);
+      if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
+      ok = F.n == 0 || refine(F, b, x, nrhs, tol, maxit, iters, relres);
+    }
+  });
+  if (stt == RSS_OK && !ok) {
+    g_last_error = "rss_solve_refined: tolerance not reached";
+    return RSS_ENOTCONV;
+  }
+  return stt;
 }
 
 rss_status rss_apply(const rss_factorization *f, const double *x, double *y, int nrhs) {
@@ -859,9 +1206,7 @@ rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, in
     if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "rss_matvec: bad arguments"};
     auto run = [&](const auto &F) {
       if (F.n > 0 && (!x || !y)) throw Fail{RSS_EINVAL, "NULL vector"};
-      launch_matvec(ptr<double>(F.d_x), F.dim, F.K, ptr<int64_t>(F.d_perm), x, y, F.n, nrhs,
-                    F.st);
-      check_launch("matvec");
+      if (F.n > 0) apply_A(F, x, y, nrhs);
       CK(cudaStreamSynchronize(F.st));
     };
     if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
@@ -890,6 +1235,26 @@ rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes) {
       if (cap < need) throw Fail{RSS_EINVAL, "rss_stats: buffer too small"};
       memcpy(buf, s.data(), need);
     }
+  });
+}
+
+rss_status rss_profile(const rss_factorization *f, int reset, double *buf, size_t *nbytes) {
+  return guard([&] {
+    if (!f || !f->impl || !nbytes) throw Fail{RSS_EINVAL, "rss_profile: bad arguments"};
+    Prof &P = f->impl->prof;
+    const size_t need = sizeof(double) * 4 * KC_N;
+    size_t cap = *nbytes;
+    *nbytes = need;
+    if (buf) {
+      if (cap < need) throw Fail{RSS_EINVAL, "rss_profile: buffer too small"};
+      for (int c = 0; c < KC_N; c++) {
+        buf[4 * c] = (double)P.launches[c];
+        buf[4 * c + 1] = P.ms[c];
+        buf[4 * c + 2] = P.bytes[c];
+        buf[4 * c + 3] = P.flops[c];
+      }
+    }
+    if (reset) P.reset();
   });
 }
 

@@ -17,7 +17,7 @@ template <typename T> struct FBox {
   int k, r;   // |S|, |R| (device-written)
   int nj;     // |J| = k + |N| (device-written)
   int njmax;  // capacity bound on nj
-  int pad;
+  int no;     // |O| active DOFs in the ring inside the proxy surface (device-written)
   int64_t *ids; // [b] global tree-order ids: S (pivot order) then R
   int *loc;     // [b] local indices in the cell's level layout, same order
   int64_t *J;   // [njmax] global ids of J = [S; N]
@@ -99,6 +99,29 @@ void launch_permute(int dir, const int64_t *perm, const double *in, T *out_or_in
                     int64_t n, int nrhs, cudaStream_t st);
 void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const int64_t *perm,
                    const double *xin, double *yout, int64_t n, int nrhs, cudaStream_t st);
+
+// FP64 operator x -> A x for points on an s^d grid of cell centres, by FFT
+// convolution on the circulant of side L = 2s (refine.cu).
+struct GridOp {
+  int dim = 0, s = 0, L = 0, logL = 0;
+  int64_t n = 0;
+  double h = 0, w = 0, diag = 1;
+  int kind = 0;
+  const int64_t *gidx = nullptr;  // grid linear index of each point (caller order)
+  double2 *C = nullptr;           // spectrum of the embedded kernel
+  double2 *X = nullptr;           // work
+  double2 *tw = nullptr;          // twiddles
+};
+void grid_op_setup(GridOp &G, cudaStream_t st);
+void grid_op_apply(const GridOp &G, const double *x, double *y, int nrhs, cudaStream_t st);
+void multidot(const double *V, int64_t vstride, int nv, const double *w, int64_t n, int nrhs, double *part,
+              double *out, cudaStream_t st);
+void combine(double *y, double alpha, const double *V, int64_t vstride, int nv, const double *coef, int64_t n,
+             int nrhs, cudaStream_t st);
+
+// Process-wide count of kernel launches made by this library.
+void count_launch(int n = 1);
+long long launches_total();
 
 // Sweep modes.
 enum { SWEEP_SOLVE_FWD = 0, SWEEP_SOLVE_BWD = 1, SWEEP_APPLY_FWD = 2, SWEEP_APPLY_BWD = 3 };

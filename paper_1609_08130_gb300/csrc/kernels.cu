@@ -19,9 +19,15 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "internal.h"
 
 namespace rss {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 constexpr int NT = 256;  // threads per CTA for the per-box kernels
 
@@ -74,7 +80,7 @@ void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, con
   if (gy < 1) gy = 1;
   if (gy > 1024) gy = 1024;
   dim3 grid(L.nblock, gy);
-  k_assemble<T><<<grid, NT, 0, st>>>(L, out, pv, prev ? 1 : 0, P, K);
+  k_assemble<T><<<grid, NT, 0, st>>>(L, out, pv, prev ? 1 : 0, P, K); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -358,6 +364,7 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   if (tid == 0) {
     fb.k = k;
     fb.r = r;
+    fb.no = nO;
   }
 }
 
@@ -373,7 +380,7 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   if (use_smem)
     cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_id<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, P, K, px, eps, PR, gscratch, gscratch_stride,
-                                  use_smem ? 1 : 0, err);
+                                  use_smem ? 1 : 0, err); count_launch();
 }
 
 template <typename T> int64_t id_region_bytes(int b, int PR) { return IdLayout<T>(b, PR).bytes; }
@@ -623,7 +630,7 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   size_t smem = (size_t)bmax * bmax / 4 * sizeof(T) + (size_t)bmax * (bmax + 1) * sizeof(T) +
                 (size_t)2 * bmax * sizeof(int) + 64;
   cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_elim<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, scratch, scratch_stride, bmax, err);
+  k_elim<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, scratch, scratch_stride, bmax, err); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -710,7 +717,7 @@ void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_li
   if (nbox == 0) return;
   int tiles1 = (njmax + ST - 1) / ST;
   int64_t grid = (int64_t)nbox * tiles1 * tiles1;
-  k_schur<T><<<(unsigned)grid, NT, 0, st>>>(lv, boxes, box_list, tiles1, scratch, scratch_stride);
+  k_schur<T><<<(unsigned)grid, NT, 0, st>>>(lv, boxes, box_list, tiles1, scratch, scratch_stride); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -845,15 +852,15 @@ template <typename T> __global__ void k_iota(int *p, int n) {
 
 template <typename T> void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err) {
   if (n <= 0) return;
-  k_iota<T><<<(n + 255) / 256, 256, 0, st>>>(piv, n);
+  k_iota<T><<<(n + 255) / 256, 256, 0, st>>>(piv, n); count_launch();
   for (int kb = 0; kb < n; kb += LB) {
     int nb = min(LB, n - kb);
-    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, err);
+    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, err); count_launch();
     int rem = n - kb - nb;
     if (rem > 0) {
-      k_lu_trsm<T><<<(rem + 127) / 128, 128, 0, st>>>(A, n, kb, nb);
+      k_lu_trsm<T><<<(rem + 127) / 128, 128, 0, st>>>(A, n, kb, nb); count_launch();
       dim3 g((rem + 63) / 64, (rem + 63) / 64);
-      k_lu_gemm<T><<<g, NT, 0, st>>>(A, n, kb, nb);
+      k_lu_gemm<T><<<g, NT, 0, st>>>(A, n, kb, nb); count_launch();
     }
   }
 }
@@ -999,7 +1006,7 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
   if ((size_t)bmax * nrhs > wk) wk = (size_t)bmax * nrhs;
   size_t smem = ((size_t)2 * bmax * nrhs + wk) * sizeof(T) + 64;
   cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs);
+  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs); count_launch();
 }
 
 // Top block: solve (mode 0) or multiply (mode 1), one CTA per right-hand side.
@@ -1047,7 +1054,7 @@ template <typename T>
 void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v, int nrhs,
                 T *work, cudaStream_t st) {
   if (ntop == 0) return;
-  k_top<T><<<nrhs, 1024, 0, st>>>(mode, LU, piv, top, ntop, v, nrhs, work);
+  k_top<T><<<nrhs, 1024, 0, st>>>(mode, LU, piv, top, ntop, v, nrhs, work); count_launch();
 }
 
 // dir 0: out_t[g*nrhs+c] = in[perm[g] + c*n];  dir 1: out[perm[g] + c*n] = in_t[g*nrhs+c]
@@ -1069,7 +1076,7 @@ void launch_permute(int dir, const int64_t *perm, const double *in, T *tv, doubl
                     cudaStream_t st) {
   int64_t tot = n * nrhs;
   if (tot == 0) return;
-  k_permute<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dir, perm, in, tv, out, n, nrhs);
+  k_permute<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dir, perm, in, tv, out, n, nrhs); count_launch();
 }
 
 // Exact FP64 y = A x by direct summation (tree-ordered points, caller order
@@ -1121,7 +1128,7 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const i
                    double *yout, int64_t n, int nrhs, cudaStream_t st) {
   if (n == 0) return;
   dim3 g((unsigned)((n + 255) / 256), (nrhs + 3) / 4);
-  k_matvec<<<g, 256, 0, st>>>(x_tree, dim, K, perm, xin, yout, n, nrhs);
+  k_matvec<<<g, 256, 0, st>>>(x_tree, dim, K, perm, xin, yout, n, nrhs); count_launch();
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,229 @@
+// refine.cu -- FP64 residual operator and vector kernels of the iterative
+// refinement (GMRES-IR) around the factorization.
+//
+// When the points are the cell centres of an s^d grid, K_ij = kappa(I_i - I_j)
+// depends only on the integer offset of the two cells, so K x is a discrete
+// convolution.  It is applied exactly (to FP64 rounding) by embedding the
+// kernel in a circulant of side L = 2s and using a radix-2 Stockham FFT
+// written here (one CTA per line, the line held in shared memory).  Two real
+// right-hand sides share one complex transform (x1 + i x2): the embedded
+// kernel is real and even, so its spectrum is real and the real and
+// imaginary parts of the product transform back to K x1 and K x2.
+//
+// This operator is the FP64 residual r = b - A x of the iterative
+// refinement; it is not part of the factorization itself.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rss {
+
+// One radix-2 Stockham FFT of length L (power of two, L <= 2048) per CTA
+// over lines of a complex array: line q starts at base(q) and has stride
+// `stride`; lines are enumerated as q = q0 + blockIdx.x.  sign = -1 forward,
+// +1 inverse (unscaled).
+__global__ void __launch_bounds__(256) k_fft_lines(double2 *data, int L, int logL, int64_t stride,
+                                                   int64_t line_mul, int64_t line_div, int64_t line_mul2,
+                                                   const double2 *tw, int sign) {
+  extern __shared__ double2 sh[];
+  double2 *a = sh, *b = sh + L;
+  // line index -> base offset: q = hi * line_div + lo  ->  base = hi*line_mul2 + lo*line_mul
+  const int64_t q = blockIdx.x;
+  const int64_t base = (q / line_div) * line_mul2 + (q % line_div) * line_mul;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) a[i] = data[base + (int64_t)i * stride];
+  __syncthreads();
+  // Stockham autosort: pass p combines sub-transforms of length m = 2^p
+  int m = 1;
+  for (int p = 0; p < logL; p++) {
+    const int half = L >> 1;
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {
+      int j = t % m;           // position inside the sub-transform
+      int k = t / m;           // which sub-transform pair
+      double2 u = a[k * m + j];
+      double2 v = a[k * m + j + half];
+      // twiddle exp(sign * 2 pi i j / (2m)) = tw[j * (L / (2m))]^(sign)
+      double2 w = tw[j * (L / (2 * m))];
+      if (sign > 0) w.y = -w.y;
+      double2 vw = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+      b[2 * k * m + j] = make_double2(u.x + vw.x, u.y + vw.y);
+      b[2 * k * m + j + m] = make_double2(u.x - vw.x, u.y - vw.y);
+    }
+    __syncthreads();
+    double2 *t0 = a;
+    a = b;
+    b = t0;
+    m <<= 1;
+  }
+  for (int i = threadIdx.x; i < L; i += blockDim.x) data[base + (int64_t)i * stride] = a[i];
+}
+
+// tw[k] = exp(-2 pi i k / L), k < L/2
+__global__ void k_twiddle(double2 *tw, int L) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L / 2) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)L, &s, &c);
+  tw[k] = make_double2(c, s);
+}
+
+// Embedded kernel c[delta] on the L^d circulant: offsets e in (-s, s) per
+// axis, 0 at e = 0 and at the unused index s.
+__global__ void k_embed_kernel(double2 *C, int dim, int s, int L, double h, int kind, double w) {
+  int64_t tot = 1;
+  for (int d = 0; d < dim; d++) tot *= L;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  int64_t rem = e;
+  double r2 = 0.0;
+  bool zero = false;
+  for (int d = 0; d < dim; d++) {
+    int i = (int)(rem % L);
+    rem /= L;
+    if (i == s) zero = true;
+    int off = i < s ? i : i - L;
+    r2 += (double)off * off;
+  }
+  double v = 0.0;
+  if (!zero && r2 > 0.0) v = w * kof(kind, r2 * h * h);
+  C[e] = make_double2(v, 0.0);
+}
+
+// X[grid(i)] = x1[i] + i x2[i] (zero elsewhere); grid(i): linear index of
+// point i (caller order) in the s^d grid, embedded in L^d.
+__global__ void k_pack(double2 *X, const int64_t *gidx, const double *x, int64_t n, int nrhs, int c0,
+                       int dim, int s, int L) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t g = gidx[i], pos = 0, mul = 1;
+  for (int d = 0; d < dim; d++) {
+    pos += (g % s) * mul;
+    g /= s;
+    mul *= L;
+  }
+  double re = x[i + (int64_t)c0 * n];
+  double im = (c0 + 1 < nrhs) ? x[i + (int64_t)(c0 + 1) * n] : 0.0;
+  X[pos] = make_double2(re, im);
+}
+
+__global__ void k_mul_real(double2 *X, const double2 *C, int64_t tot, double scale) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  double c = C[e].x * scale;
+  X[e] = make_double2(X[e].x * c, X[e].y * c);
+}
+
+// y = diag * x + (K x)  for the two packed columns
+__global__ void k_unpack(const double2 *X, const int64_t *gidx, const double *x, double *y, int64_t n,
+                         int nrhs, int c0, int dim, int s, int L, double diag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t g = gidx[i], pos = 0, mul = 1;
+  for (int d = 0; d < dim; d++) {
+    pos += (g % s) * mul;
+    g /= s;
+    mul *= L;
+  }
+  double2 v = X[pos];
+  y[i + (int64_t)c0 * n] = diag * x[i + (int64_t)c0 * n] + v.x;
+  if (c0 + 1 < nrhs) y[i + (int64_t)(c0 + 1) * n] = diag * x[i + (int64_t)(c0 + 1) * n] + v.y;
+}
+
+static void fft_nd(double2 *X, int dim, int L, int logL, const double2 *tw, int sign, cudaStream_t st) {
+  size_t smem = (size_t)2 * L * sizeof(double2);
+  int64_t tot = 1;
+  for (int d = 0; d < dim; d++) tot *= L;
+  int64_t lines = tot / L;
+  for (int ax = 0; ax < dim; ax++) {
+    int64_t stride = 1;
+    for (int d = 0; d < ax; d++) stride *= L;
+    // lines along axis ax: q = hi * stride + lo, lo < stride; base = hi * stride * L + lo
+    k_fft_lines<<<(unsigned)lines, 256, smem, st>>>(X, L, logL, stride, 1, stride, stride * L, tw, sign); count_launch();
+  }
+}
+
+void grid_op_setup(GridOp &G, cudaStream_t st) {
+  int64_t tot = 1;
+  for (int d = 0; d < G.dim; d++) tot *= G.L;
+  cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * G.L * (int)sizeof(double2));
+  k_twiddle<<<(G.L / 2 + 255) / 256, 256, 0, st>>>(G.tw, G.L); count_launch();
+  k_embed_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G.C, G.dim, G.s, G.L, G.h, G.kind, G.w); count_launch();
+  fft_nd(G.C, G.dim, G.L, G.logL, G.tw, -1, st);
+}
+
+void grid_op_apply(const GridOp &G, const double *x, double *y, int nrhs, cudaStream_t st) {
+  int64_t tot = 1;
+  for (int d = 0; d < G.dim; d++) tot *= G.L;
+  for (int c0 = 0; c0 < nrhs; c0 += 2) {
+    cudaMemsetAsync(G.X, 0, sizeof(double2) * tot, st);
+    k_pack<<<(unsigned)((G.n + 255) / 256), 256, 0, st>>>(G.X, G.gidx, x, G.n, nrhs, c0, G.dim, G.s, G.L); count_launch();
+    fft_nd(G.X, G.dim, G.L, G.logL, G.tw, -1, st);
+    k_mul_real<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G.X, G.C, tot, 1.0 / (double)tot); count_launch();
+    fft_nd(G.X, G.dim, G.L, G.logL, G.tw, +1, st);
+    k_unpack<<<(unsigned)((G.n + 255) / 256), 256, 0, st>>>(G.X, G.gidx, x, y, G.n, nrhs, c0, G.dim, G.s, G.L,
+                                                             G.diag); count_launch();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector kernels for the Krylov loop (column-major n x nrhs blocks).
+// Reductions are two-pass and deterministic.
+// ---------------------------------------------------------------------------
+
+constexpr int RB = 256;      // threads per reduction block
+constexpr int RBLK = 240;    // blocks per column in the first pass
+
+// part[(c * nv + i) * RBLK + blk] = partial sum of V_i[:,c] . w[:,c]
+__global__ void __launch_bounds__(RB) k_multidot_part(const double *V, int64_t vstride, int nv, const double *w,
+                                                      int64_t n, int nrhs, double *part) {
+  __shared__ double red[RB / 32];
+  const int c = blockIdx.y, i = blockIdx.z, blk = blockIdx.x;
+  const double *vi = V + (int64_t)i * vstride + (int64_t)c * n;
+  const double *wc = w + (int64_t)c * n;
+  double s = 0.0;
+  for (int64_t e = blk * (int64_t)RB + threadIdx.x; e < n; e += (int64_t)RB * RBLK) s += vi[e] * wc[e];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < RB / 32 ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) part[((int64_t)c * nv + i) * RBLK + blk] = s;
+  }
+}
+
+__global__ void k_multidot_final(const double *part, int cnt, double *out) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  double s = 0.0;
+  for (int b = 0; b < RBLK; b++) s += part[(int64_t)q * RBLK + b];
+  out[q] = s;
+}
+
+// out[c * nv + i] = V_i[:,c] . w[:,c]
+void multidot(const double *V, int64_t vstride, int nv, const double *w, int64_t n, int nrhs, double *part,
+              double *out, cudaStream_t st) {
+  dim3 g(RBLK, nrhs, nv);
+  k_multidot_part<<<g, RB, 0, st>>>(V, vstride, nv, w, n, nrhs, part); count_launch();
+  int cnt = nrhs * nv;
+  k_multidot_final<<<(cnt + 127) / 128, 128, 0, st>>>(part, cnt, out); count_launch();
+}
+
+// y[:,c] = alpha * y[:,c] + sum_i coef[c * nv + i] * V_i[:,c]
+__global__ void k_combine(double *y, double alpha, const double *V, int64_t vstride, int nv, const double *coef,
+                          int64_t n, int nrhs) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * nrhs) return;
+  int c = (int)(e / n);
+  double s = alpha * y[e];
+  for (int i = 0; i < nv; i++) s += coef[c * nv + i] * V[(int64_t)i * vstride + e];
+  y[e] = s;
+}
+
+void combine(double *y, double alpha, const double *V, int64_t vstride, int nv, const double *coef, int64_t n,
+             int nrhs, cudaStream_t st) {
+  int64_t tot = n * nrhs;
+  if (tot == 0) return;
+  k_combine<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(y, alpha, V, vstride, nv, coef, n, nrhs); count_launch();
+}
+
+}  // namespace rss

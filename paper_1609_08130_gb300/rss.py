@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "librss.so")
-SOURCES = ["api.cu", "kernels.cu"]
+SOURCES = ["api.cu", "kernels.cu", "refine.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
             os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), *NVCC_FLAGS, "--threads", "2", "-o", tmp, *srcs]
+    cmd = [_nvcc(), *NVCC_FLAGS, "--threads", "3", "-o", tmp, *srcs]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -59,7 +59,7 @@ class _Kernel(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("n_proxy", C.c_int), ("proxy_radius", C.c_double),
-                ("use_graphs", C.c_int), ("stream", C.c_void_p)]
+                ("use_graphs", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
 
 
 _lib = None
@@ -73,9 +73,13 @@ _SIGS = {
     "rss_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rss_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rss_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rss_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_free": (None, [C.c_void_p]),
     "rss_last_error": (C.c_char_p, []),
+    "rss_kernel_launches": (C.c_int64, []),
 }
 
 
@@ -94,6 +98,11 @@ def lib(load_only: bool = False):
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernel launches made by librss.so in this process so far."""
+    return int(lib().rss_kernel_launches())
 
 
 def _check(st: int):
@@ -172,14 +181,15 @@ class Factorization:
     """
 
     def __init__(self, pts, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
-                 weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None):
+                 weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
+                 profile: bool = False):
         torch = _torch()
         pts = _dev_f64(pts)
         self.n, self.dim = pts.shape
         self.prec = prec
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
-        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream))
+        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile))
         h = C.c_void_p()
         _check(lib().rss_factor(C.c_void_p(pts.data_ptr()), self.n, self.dim, _Kernel(kind, diag, weight),
                                 eps, leaf, C.byref(opts), C.byref(h)))
@@ -208,6 +218,18 @@ class Factorization:
         """x = F^{-1} b; b of shape (n,) or (nrhs, n)."""
         return self._call(lib().rss_solve, b)
 
+    def solve_refined(self, b, tol: float = 1e-10, maxit: int = 10, check: bool = True):
+        """GMRES-IR solve of A x = b to relative residual tol.  Returns
+        (x, inner iterations, final relative residual)."""
+        b, one, x = self._vec(b)
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        st = lib().rss_solve_refined(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), b.shape[0],
+                                     tol, maxit, C.byref(it), C.byref(rr))
+        if check or st != RSS_ENOTCONV:
+            _check(st)
+        return (x[0] if one else x), it.value, rr.value
+
     def matvec(self, x):
         """Exact FP64 A x by direct summation."""
         return self._call(lib().rss_matvec, x)
@@ -223,6 +245,19 @@ class Factorization:
         return dict(nbox=nbox, ntop=int(buf[1]), factor_bytes=int(buf[2]), maxdepth=int(buf[3]),
                     n=int(buf[4]), prec=int(buf[5]), depth=boxes[:, 0].copy(), b=boxes[:, 1].copy(),
                     k=boxes[:, 2].copy(), nj=boxes[:, 3].copy())
+
+    PROFILE_CLASSES = ["assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve", "permute"]
+
+    def profile(self, reset: bool = False) -> dict:
+        """Per-kernel-class {launches, ms, bytes, flops} (needs profile=True)."""
+        import numpy as np
+        nb = C.c_size_t(0)
+        _check(lib().rss_profile(self.h, 0, None, C.byref(nb)))
+        buf = np.empty(nb.value // 8)
+        _check(lib().rss_profile(self.h, int(reset), C.c_void_p(buf.ctypes.data), C.byref(nb)))
+        buf = buf.reshape(-1, 4)
+        return {name: dict(launches=int(buf[i, 0]), ms=float(buf[i, 1]), bytes=float(buf[i, 2]),
+                           flops=float(buf[i, 3])) for i, name in enumerate(self.PROFILE_CLASSES)}
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -155,3 +155,41 @@ def test_bad_arguments_raise(pkg):
         pkg.Factorization(pts, 5, 1e-6)
     with pytest.raises(pkg.RSSError):
         pkg.Factorization(pts, 0, -1.0)
+
+
+@pytest.mark.parametrize("n_side,dim,kind", [(64, 2, 0), (16, 3, 1), (128, 2, 0)])
+def test_grid_matvec_matches_direct_sum(pkg, n_side, dim, kind):
+    """The FFT residual operator on grid points equals the oracle's direct
+    FP64 sum (all rows for small grids, sampled rows otherwise)."""
+    pts = inputs.grid_points(n_side, dim)
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), kind, 1e-3, leaf=64, prec=pkg.MIXED)
+    x = inputs.rhs(9, n, 3)
+    y = f.matvec(_cuda(x)).cpu().numpy()
+    rows = None if n <= 4096 else inputs.splitmix64(5, 64) % np.uint64(n)
+    rows = None if rows is None else rows.astype(np.int64)
+    ref = oracle.matvec(pts, kind, x, rows=rows)
+    got = y if rows is None else y[:, rows]
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", ["grid2d", "random2d", "grid3d"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_refined_solve_reaches_tolerance(pkg, case, prec):
+    """GMRES-IR reaches a 1e-10 relative residual, checked with the oracle's
+    exact FP64 matvec (not with the library's own residual)."""
+    if case == "grid2d":
+        pts, kind, eps = inputs.grid_points(64, 2), 0, 1e-6
+    elif case == "random2d":
+        pts, kind, eps = inputs.random_points(13, 3000, 2), 0, 1e-6
+    else:
+        pts, kind, eps = inputs.grid_points(16, 3), 1, 1e-3
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), kind, eps, leaf=64, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+    b = inputs.rhs(1, n, 4)
+    x, iters, rel = f.solve_refined(_cuda(b), tol=1e-10, maxit=10)
+    x = x.cpu().numpy()
+    r = b - oracle.matvec(pts, kind, x)
+    true_rel = max(np.linalg.norm(r[c]) / np.linalg.norm(b[c]) for c in range(4))
+    assert rel <= 1e-10 and true_rel <= 2e-10, (rel, true_rel, iters)
+    assert iters <= 10
