@@ -7,6 +7,7 @@
 // tables and pair-block offsets) once the ranks of the previous level are
 // known, and launches one ID / elimination / Schur launch per colour phase.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -110,6 +111,50 @@ static inline uint64_t morton_key(const int64_t *c, int dim, int bits) {
   return k;
 }
 
+// Bit spreading by shift-and-mask (same interleaving as morton_key, x in
+// the lowest bit of each group), for up to 21 bits per coordinate.
+static inline uint64_t spread2(uint64_t x) {
+  x &= 0x1fffffULL;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffULL;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffULL;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+  x = (x | (x << 2)) & 0x3333333333333333ULL;
+  x = (x | (x << 1)) & 0x5555555555555555ULL;
+  return x;
+}
+static inline uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffULL;
+  x = (x | (x << 32)) & 0x001f00000000ffffULL;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffULL;
+  x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+  x = (x | (x << 2)) & 0x1249249249249249ULL;
+  return x;
+}
+static inline uint64_t morton_fast(const int64_t *c, int dim) {
+  return dim == 2 ? (spread2(c[0]) | (spread2(c[1]) << 1))
+                  : (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
+}
+
+// Stable LSD radix sort of idx by key (8-bit digits over the used bits).
+static void radix_sort_by_key(std::vector<uint64_t> &key, std::vector<int64_t> &idx, int key_bits) {
+  const size_t n = key.size();
+  std::vector<uint64_t> k2(n);
+  std::vector<int64_t> i2(n);
+  for (int sh = 0; sh < key_bits; sh += 8) {
+    size_t cnt[257] = {0};
+    for (size_t q = 0; q < n; q++) cnt[((key[q] >> sh) & 255) + 1]++;
+    for (int d = 0; d < 256; d++) cnt[d + 1] += cnt[d];
+    for (size_t q = 0; q < n; q++) {
+      size_t pos = cnt[(key[q] >> sh) & 255]++;
+      k2[pos] = key[q];
+      i2[pos] = idx[q];
+    }
+    key.swap(k2);
+    idx.swap(i2);
+  }
+}
+
 struct HTree {
   uint32_t magic = MAGIC_TREE;
   int dim = 2, leaf = 64, maxdepth = 0;
@@ -137,17 +182,15 @@ static void build_tree(HTree &T, const double *pts_host) {
   const int dim = T.dim;
   const int64_t n = T.n;
   const int MAXD = 20;
-  std::vector<uint64_t> key(n);
+  std::vector<uint64_t> ks(n);
   for (int64_t i = 0; i < n; i++) {
     int64_t c[3] = {0, 0, 0};
     for (int d = 0; d < dim; d++) c[d] = cell_at(pts_host[i * dim + d], MAXD);
-    key[i] = morton_key(c, dim, MAXD);
+    ks[i] = morton_fast(c, dim);
   }
   T.perm.resize(n);
   for (int64_t i = 0; i < n; i++) T.perm[i] = i;
-  std::stable_sort(T.perm.begin(), T.perm.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
-  std::vector<uint64_t> ks(n);
-  for (int64_t g = 0; g < n; g++) ks[g] = key[T.perm[g]];
+  radix_sort_by_key(ks, T.perm, dim * MAXD);  // stable: equal keys keep index order
   T.maxdepth = 0;
   struct Frame {
     int64_t lo, hi;
@@ -261,39 +304,67 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   const int dim = T.dim;
   L.NB = dim == 2 ? 25 : 125;
   const int bits = std::max(t, 1);
-  std::vector<uint64_t> dk(active.size());
-  for (size_t q = 0; q < active.size(); q++) {
+  const size_t na = active.size();
+  std::vector<uint64_t> dk(na);
+  bool sorted = true;
+  for (size_t q = 0; q < na; q++) {
     int64_t c[3] = {0, 0, 0};
     for (int d = 0; d < dim; d++) c[d] = cell_at(T.x[active[q] * dim + d], t);
-    dk[q] = morton_key(c, dim, bits);
+    dk[q] = morton_fast(c, dim);
+    if (q && dk[q] < dk[q - 1]) sorted = false;
   }
-  L.key = dk;
-  std::sort(L.key.begin(), L.key.end());
-  L.key.erase(std::unique(L.key.begin(), L.key.end()), L.key.end());
+  std::vector<int> cid(na);
+  if (sorted) {
+    // cells are runs of the (tree-ordered) active list: no sort needed
+    for (size_t q = 0; q < na; q++) {
+      if (q == 0 || dk[q] != dk[q - 1]) L.key.push_back(dk[q]);
+      cid[q] = (int)L.key.size() - 1;
+    }
+  } else {
+    L.key = dk;
+    std::sort(L.key.begin(), L.key.end());
+    L.key.erase(std::unique(L.key.begin(), L.key.end()), L.key.end());
+    for (size_t q = 0; q < na; q++) cid[q] = find_key(L.key, dk[q]);
+  }
   L.ncell = (int)L.key.size();
   L.cell_b.assign(L.ncell, 0);
-  std::vector<int> cid(active.size());
-  for (size_t q = 0; q < active.size(); q++) {
-    cid[q] = find_key(L.key, dk[q]);
-    L.cell_b[cid[q]]++;
-  }
+  for (size_t q = 0; q < na; q++) L.cell_b[cid[q]]++;
   L.cell_dof_off.assign(L.ncell + 1, 0);
   for (int c = 0; c < L.ncell; c++) L.cell_dof_off[c + 1] = L.cell_dof_off[c] + L.cell_b[c];
-  L.cell_dofs.resize(active.size());
-  std::vector<int64_t> fill(L.cell_dof_off.begin(), L.cell_dof_off.end() - 1);
-  for (size_t q = 0; q < active.size(); q++) L.cell_dofs[fill[cid[q]]++] = active[q];
+  L.cell_dofs.resize(na);
   L.cell_coord.assign(3 * L.ncell, 0);
-  for (int c = 0; c < L.ncell; c++) {
-    uint64_t k = L.key[c];
-    for (int d = 0; d < dim; d++) {
-      int v = 0;
-      for (int b = 0; b < bits; b++) v |= (int)((k >> (dim * b + d)) & 1) << b;
-      L.cell_coord[3 * c + d] = v;
+  {
+    std::vector<int64_t> fill(L.cell_dof_off.begin(), L.cell_dof_off.end() - 1);
+    for (size_t q = 0; q < na; q++) {
+      int c = cid[q];
+      if (fill[c] == L.cell_dof_off[c])
+        for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = (int)cell_at(T.x[active[q] * dim + d], t);
+      L.cell_dofs[fill[c]++] = active[q];
     }
   }
   L.cell_nbr.assign((size_t)L.ncell * L.NB, -1);
   L.pair_off.assign((size_t)L.ncell * L.NB, -1);
   const int64_t side = (int64_t)1 << t;
+  // dense cell lookup when the level grid is small enough, else binary search
+  int64_t grid_cells = 1;
+  for (int d = 0; d < dim; d++) grid_cells *= side;
+  std::vector<int> dense;
+  if (grid_cells <= ((int64_t)1 << 24)) {
+    dense.assign(grid_cells, -1);
+    for (int c = 0; c < L.ncell; c++) {
+      int64_t lin = 0, mul = 1;
+      for (int d = 0; d < dim; d++) lin += (int64_t)L.cell_coord[3 * c + d] * mul, mul *= side;
+      dense[lin] = c;
+    }
+  }
+  auto lookup = [&](const int64_t *p) -> int {
+    if (!dense.empty()) {
+      int64_t lin = 0, mul = 1;
+      for (int d = 0; d < dim; d++) lin += p[d] * mul, mul *= side;
+      return dense[lin];
+    }
+    return find_key(L.key, morton_fast(p, dim));
+  };
   int64_t off = 0;
   for (int c = 0; c < L.ncell; c++) {
     L.bmax = std::max(L.bmax, L.cell_b[c]);
@@ -305,7 +376,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
           bool ok = true;
           for (int d = 0; d < dim; d++) ok = ok && p[d] >= 0 && p[d] < side;
           if (!ok) continue;
-          int nb = find_key(L.key, morton_key(p, dim, bits));
+          int nb = lookup(p);
           if (nb < 0) continue;
           int code = code5(dx, dy, dz, dim);
           L.cell_nbr[(size_t)c * L.NB + code] = nb;
@@ -316,7 +387,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   L.pool_elems = off;
   for (int node : T.level[t]) {
     int64_t p[3] = {T.coord[3 * node], T.coord[3 * node + 1], T.coord[3 * node + 2]};
-    int c = find_key(L.key, morton_key(p, dim, bits));
+    int c = find_key(L.key, morton_fast(p, dim));
     if (c < 0) continue;  // every DOF of the box has become inactive
     L.box_cell.push_back(c);
     L.box_node.push_back(node);
@@ -330,13 +401,16 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
 // ---------------------------------------------------------------------------
 
 struct Phase {
-  int first, count, bmax;
+  int first, count, bmax, njmax;
 };
 
 // Per-kernel-class timing with CUDA events on the launching stream, plus the
 // algorithmic bytes and flops of each launch (filled in once the ranks of the
 // boxes it handled are known).
-enum KClass { KC_ASSEMBLE, KC_ID, KC_ELIM, KC_SCHUR, KC_TOPLU, KC_SWEEP, KC_TOP, KC_PERMUTE, KC_N };
+enum KClass {
+  KC_ASSEMBLE, KC_ID, KC_ELIM, KC_SCHUR, KC_TOPLU, KC_SWEEP, KC_TOP, KC_PERMUTE,
+  KC_HOST_TREE, KC_HOST_LEVEL, KC_HOST_WAIT, KC_REFINE_OP, KC_N
+};
 
 struct ProfRec {
   int cls;
@@ -375,6 +449,12 @@ struct Prof {
   void reset() {
     for (int c = 0; c < KC_N; c++) ms[c] = bytes[c] = flops[c] = 0, launches[c] = 0;
   }
+  // host wall-clock intervals (tree build, level preparation, waits)
+  void host(int cls, double msv) {
+    if (!on) return;
+    ms[cls] += msv;
+    launches[cls] += 1;
+  }
   ~Prof() {
     for (auto &r : pending) cudaEventDestroy(r.a), cudaEventDestroy(r.b);
     for (auto e : spare) cudaEventDestroy(e);
@@ -396,7 +476,7 @@ template <typename T> struct Factor : FactorBase {
   cudaStream_t st = nullptr;
   int64_t n = 0;
   int dim = 2;
-  DBuf d_x, d_perm, d_cell, d_off, d_err;
+  DBuf d_x, d_perm, d_cell, d_off, d_err, d_proxy;
   Points P{};
   std::vector<std::unique_ptr<DBuf>> store;  // factor storage chunks
   int64_t factor_bytes = 0;
@@ -447,9 +527,8 @@ template <typename T> static void prof_collect(const Factor<T> &F) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
     double bytes = r.bytes, flops = r.flops;
-    for (int q = r.first; q < r.first + r.count && r.cls != KC_ASSEMBLE && r.cls != KC_TOPLU && r.cls != KC_TOP &&
-                          r.cls != KC_PERMUTE;
-         q++) {
+    const bool per_box = r.cls == KC_ID || r.cls == KC_ELIM || r.cls == KC_SCHUR || r.cls == KC_SWEEP;
+    for (int q = r.first; per_box && q < r.first + r.count; q++) {
       const FBox<T> &b = F.h_boxes[q];
       double B = b.b, k = b.k, rr = b.r, nj = b.nj, no = b.no, m = b.no + F.px.np;
       if (r.cls == KC_ID) {
@@ -474,6 +553,10 @@ template <typename T> static void prof_collect(const Factor<T> &F) {
     P.spare.push_back(r.b);
   }
   P.pending.clear();
+}
+
+static inline double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 static int check_err(DBuf &d_err, cudaStream_t st) {
@@ -544,6 +627,26 @@ template <typename T> static void run_factor(Factor<T> &F) {
   F.d_err.alloc(sizeof(int), st);
   CK(cudaMemsetAsync(F.d_err.p, 0, sizeof(int), st));
   detect_grid(F);
+  {
+    // proxy surface template (Sec. 3.2): unit circle with n_p equispaced
+    // angles in 2D, Fibonacci sphere with n_p points in 3D
+    std::vector<double> u((size_t)3 * F.px.np, 0.0);
+    for (int m = 0; m < F.px.np; m++) {
+      if (dim == 2) {
+        double th = 2.0 * kPi * (double)m / (double)F.px.np;
+        u[3 * m] = cos(th);
+        u[3 * m + 1] = sin(th);
+      } else {
+        double z = 1.0 - (2.0 * m + 1.0) / (double)F.px.np;
+        double rr = sqrt(1.0 - z * z);
+        double ph = (double)m * kPi * (3.0 - sqrt(5.0));
+        u[3 * m] = rr * cos(ph);
+        u[3 * m + 1] = rr * sin(ph);
+        u[3 * m + 2] = z;
+      }
+    }
+    upload(F.d_proxy, u, st);
+  }
 
   int nbox_total = 0;
   for (int t = 2; t <= T_.maxdepth; t++) nbox_total += (int)T_.level[t].size();
@@ -589,6 +692,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
   };
 
   for (int t = T_.maxdepth; t >= 2; t--) {
+    double th0 = now_ms();
     HLevel H = build_level(T_, t, active);
     std::unique_ptr<DLevel<T>> D(new DLevel<T>());
     upload(D->cell_b, H.cell_b, st);
@@ -630,7 +734,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     // factor records of this level's boxes
     const int base = (int)F.h_boxes.size();
     const int nb = (int)H.box_cell.size();
-    int njmax_lvl = 0;
+    int njmax_lvl = 0, ring_max = 0;
     std::vector<int> njmaxv(nb);
     size_t sz_i64 = 0, sz_i32 = 0, sz_T = 0;
     for (int q = 0; q < nb; q++) {
@@ -646,9 +750,21 @@ template <typename T> static void run_factor(Factor<T> &F) {
           }
       njmaxv[q] = nj;
       njmax_lvl = std::max(njmax_lvl, nj);
+      {
+        // DOFs of the ring inside the proxy surface, bounded by level-start counts
+        int ring = 0, lim2 = dim == 3 ? 2 : 0;
+        for (int dz = -lim2; dz <= lim2; dz++)
+          for (int dy = -2; dy <= 2; dy++)
+            for (int dx = -2; dx <= 2; dx++) {
+              if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) != 2) continue;
+              int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
+              if (nbc >= 0) ring += H.cell_b[nbc];
+            }
+        ring_max = std::max(ring_max, ring);
+      }
       sz_i64 += (size_t)b + nj;
       sz_i32 += (size_t)b + 2 * (size_t)nj + b;
-      sz_T += (size_t)b * b / 4 + 1 + (size_t)b * b + 2 * (size_t)nj * b;
+      sz_T += (size_t)b * b / 4 + 1 + (size_t)2 * b * b + 2 * (size_t)nj * b;
     }
     int64_t *p64 = (int64_t *)F.alloc_store(sz_i64 * sizeof(int64_t));
     int *p32 = (int *)F.alloc_store(sz_i32 * sizeof(int));
@@ -675,6 +791,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
       fb.Tm = pT;
       pT += (size_t)b * b / 4 + 1;
       fb.LU = pT;
+      pT += (size_t)b * b;
+      fb.Xi = pT;
       pT += (size_t)b * b;
       fb.E = pT;
       pT += (size_t)nj * b;
@@ -707,10 +825,11 @@ template <typename T> static void run_factor(Factor<T> &F) {
     if (!id_smem) gid.alloc((size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st);
     int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32;
     gel.alloc((size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st);
+    F.prof.host(KC_HOST_LEVEL, now_ms() - th0);
     for (auto &p : ph) {
       const int *bl = ptr<int>(d_list) + p.first;
       int pi = F.prof.begin(KC_ID, st, base + p.first, p.second);
-      launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, H.bmax, 0, F.P, F.K, F.px, F.eps,
+      launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, H.bmax, ring_max, F.P, F.K, F.px, ptr<double>(F.d_proxy), F.eps,
                    ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
       check_launch("id");
       F.prof.end(pi, st);
@@ -723,7 +842,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
       check_launch("schur");
       F.prof.end(pi, st);
-      F.phases.push_back({base + p.first, p.second, H.bmax});
+      F.phases.push_back({base + p.first, p.second, H.bmax, njmax_lvl});
     }
     // ranks of this level -> active DOFs of the next
     CK(cudaMemcpyAsync(F.h_boxes.data() + base, ptr<FBox<T>>(F.d_boxes) + base, sizeof(FBox<T>) * nb,
@@ -732,14 +851,18 @@ template <typename T> static void run_factor(Factor<T> &F) {
     CK(cudaMemcpyAsync(ac.data(), D->act_cnt.p, sizeof(int) * H.ncell, cudaMemcpyDeviceToHost, st));
     if (!ai.empty())
       CK(cudaMemcpyAsync(ai.data(), D->act_idx.p, sizeof(int) * ai.size(), cudaMemcpyDeviceToHost, st));
+    double tw0 = now_ms();
     int e = check_err(F.d_err, st);
+    F.prof.host(KC_HOST_WAIT, now_ms() - tw0);
     prof_collect(F);
     if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the LU of a redundant block"};
     if (e) throw Fail{RSS_ECUDA, "device-side consistency check failed"};
+    double ta0 = now_ms();
     active.clear();
     for (int c = 0; c < H.ncell; c++)
       for (int q = 0; q < ac[c]; q++) active.push_back(H.cell_dofs[H.cell_dof_off[c] + ai[H.cell_dof_off[c] + q]]);
-    std::sort(active.begin(), active.end());
+    if (!std::is_sorted(active.begin(), active.end())) std::sort(active.begin(), active.end());
+    F.prof.host(KC_HOST_LEVEL, now_ms() - ta0);
     prevD = std::move(D);
     prevH = std::move(H);
     prev_slot = slot;
@@ -831,7 +954,7 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   const int fwd = solve ? SWEEP_SOLVE_FWD : SWEEP_APPLY_FWD, bwd = solve ? SWEEP_SOLVE_BWD : SWEEP_APPLY_BWD;
   for (const Phase &p : F.phases) {
     pi = P.begin(KC_SWEEP, st, p.first, p.count, nrhs);
-    launch_sweep<T>(fwd, bx, p.first, p.count, v, nrhs, p.bmax, st);
+    launch_sweep<T>(fwd, bx, p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
     P.end(pi, st);
   }
   double nt = F.ntop;
@@ -841,7 +964,7 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   P.end(pi, st);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
     pi = P.begin(KC_SWEEP, st, it->first, it->count, nrhs);
-    launch_sweep<T>(bwd, bx, it->first, it->count, v, nrhs, it->bmax, st);
+    launch_sweep<T>(bwd, bx, it->first, it->count, v, nrhs, it->bmax, it->njmax, st);
     P.end(pi, st);
   }
   pi = P.begin(KC_PERMUTE, st, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
@@ -852,7 +975,15 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   prof_collect(F);
 }
 
+template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs);
+
 template <typename T> static void apply_A(const Factor<T> &F, const double *x, double *y, int nrhs) {
+  int pi = F.prof.begin(KC_REFINE_OP, F.st);
+  apply_A_impl(F, x, y, nrhs);
+  F.prof.end(pi, F.st);
+}
+
+template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs) {
   if (F.grid_side > 0) {
     if (!F.grid_ready) {
       GridOp &G = F.G;
@@ -1012,6 +1143,7 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
   if (iters) *iters = inner;
   if (relres) *relres = rel;
   CK(cudaStreamSynchronize(st));
+  prof_collect(F);
   return ok;
 }
 
@@ -1145,7 +1277,9 @@ rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, 
       F->tree.dim = dim;
       F->tree.leaf = leaf_size;
       F->tree.n = n;
+      double tt0 = now_ms();
       build_tree(F->tree, h.data());
+      F->prof.host(KC_HOST_TREE, now_ms() - tt0);
       F->K.kind = kernel.kind;
       F->K.diag = kernel.diag;
       F->K.w = kernel.weight > 0 ? kernel.weight : (n > 0 ? 1.0 / (double)n : 1.0);

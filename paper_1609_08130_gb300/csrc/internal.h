@@ -26,6 +26,7 @@ template <typename T> struct FBox {
   T *Tm;        // k x r column-major (ld k): T = R11^{-1} R12
   T *LU;        // r x r row-major, L\U of P X_RR
   int *piv;     // [r] row i of P X_RR is row piv[i] of X_RR
+  T *Xi;        // r x r column-major: X_RR^{-1} = U^{-1} L^{-1} P formed from the LU
   T *E;         // nj x r column-major (ld nj): E = X_JR X_RR^{-1}
   T *G;         // r x nj column-major (ld r):  G = X_RR^{-1} X_RJ
 };
@@ -74,8 +75,9 @@ void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, con
                      const KernelParams &K, int64_t maxblk, cudaStream_t st);
 template <typename T>
 void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
-               int mmax, const Points &P, const KernelParams &K, const ProxyParams &px, double eps,
-               T *gscratch, int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err);
+               int mmax, const Points &P, const KernelParams &K, const ProxyParams &px,
+               const double *proxy_unit, double eps, T *gscratch, int64_t gscratch_stride, bool use_smem,
+               cudaStream_t st, int *err);
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
                  T *scratch, int64_t scratch_stride, cudaStream_t st, int *err);
@@ -89,7 +91,7 @@ void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err);
 // layout v[g * nrhs + c].
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
-                  cudaStream_t st);
+                  int njmax, cudaStream_t st);
 template <typename T>
 void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v,
                 int nrhs, T *work, cudaStream_t st);

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "internal.h"
@@ -368,12 +369,363 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-level ID for boxes with b <= 32*CPL.  W warps share one box: each
+// folds a disjoint set of 'PR'-row panels of the ID matrix into its own b x b
+// triangle (lane l owns columns l, l+32, ...; the panel sits in registers and
+// the Householder vector is broadcast by shuffles, so no block barrier is
+// needed), the W triangles are folded into the first one, and that warp runs
+// the greedy column-pivoted QR on it.
+// ---------------------------------------------------------------------------
+
+template <typename T> struct IdwRows;
+template <> struct IdwRows<float> { static constexpr int PR = 32; };
+template <> struct IdwRows<double> { static constexpr int PR = 16; };
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Fold the PR rows held in `pan` into the triangle R (row-major, ld ldr).
+template <typename T, int CPL, int PR>
+__device__ __forceinline__ void fold_rows(T (&pan)[PR][CPL], T *R, int ldr, int b, int lane) {
+  for (int j = 0; j < b; j++) {
+    const int slot = j >> 5, owner = j & 31;
+    T v[PR];
+    T s0 = (T)0, s1 = (T)0;
+#pragma unroll
+    for (int i = 0; i < PR; i++) {
+      T src = pan[i][0];
+#pragma unroll
+      for (int q = 1; q < CPL; q++)
+        if (slot == q) src = pan[i][q];
+      v[i] = __shfl_sync(FULL, src, owner);
+      if (i & 1) s1 += v[i] * v[i];
+      else s0 += v[i] * v[i];
+    }
+    const T s = s0 + s1;
+    if (s > (T)0) {
+      const T x0 = R[j * ldr + j];
+      const T nrm = sqrt(x0 * x0 + s);
+      const T beta = x0 >= (T)0 ? -nrm : nrm;
+      const T tau = (beta - x0) / beta;
+      const T scl = (T)1 / (x0 - beta);
+#pragma unroll
+      for (int q = 0; q < CPL; q++) {
+        const int col = lane + 32 * q;
+        if (col > j && col < b) {
+          T d0 = (T)0, d1 = (T)0, d2 = (T)0, d3 = (T)0;
+#pragma unroll
+          for (int i = 0; i < PR; i += 4) {
+            d0 += v[i] * pan[i][q];
+            d1 += v[i + 1] * pan[i + 1][q];
+            d2 += v[i + 2] * pan[i + 2][q];
+            d3 += v[i + 3] * pan[i + 3][q];
+          }
+          const T wv = R[j * ldr + col] + scl * ((d0 + d1) + (d2 + d3));
+          const T f = tau * wv;
+          const T fs = f * scl;
+          R[j * ldr + col] -= f;
+#pragma unroll
+          for (int i = 0; i < PR; i++) pan[i][q] -= fs * v[i];
+        }
+      }
+      __syncwarp();
+      if (lane == owner) R[j * ldr + j] = beta;
+      __syncwarp();
+    }
+  }
+}
+
+template <typename T, int CPL>
+__global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int W,
+                                             Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
+                                             double eps, int ring_max, int *err) {
+  constexpr int PR = IdwRows<T>::PR;
+  constexpr int BM = 32 * CPL;        // max b
+  constexpr int LDR = BM + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpc = blockDim.x >> 5;
+  const int bpc = wpc / W;                      // boxes per CTA
+  const int lb = warp / W, sw = warp % W;       // local box, sub-warp
+  const int qbox = blockIdx.x * bpc + lb;
+  T *Rw = reinterpret_cast<T *>(smem_raw) + (size_t)warp * BM * LDR;
+  int *ibase = reinterpret_cast<int *>(smem_raw + (((size_t)wpc * BM * LDR * sizeof(T) + 15) & ~(size_t)15));
+  int *s_ocode = ibase + lb * (125 + 126 + BM + 4);
+  int *s_obase = s_ocode + 125;
+  int *perm = s_obase + 126;
+  int *s_misc = perm + BM;                      // [0] ring count, [1] k
+  // element offset in the pool of the column holding each ring row
+  int64_t *s_rowsrc = reinterpret_cast<int64_t *>(ibase + ((125 + 126 + BM + 4 + 1) & ~1));
+  const bool active = qbox < nbox;
+  FBox<T> *fbp = active ? &boxes[box_list[qbox]] : nullptr;
+  const int c = active ? fbp->cell : 0;
+  const int b = active ? fbp->b : 0;
+  const int dim = lv.dim;
+
+  for (int e = lane; e < BM * LDR; e += 32) Rw[e] = (T)0;
+  // ring O (Chebyshev distance 2) cells with active DOFs, by sub-warp 0
+  if (active && sw == 0) {
+    const int lim = dim == 3 ? 2 : 0;
+    int cnt_here = 0;
+    int no = 0, acc = 0;
+    const int ncode = dim == 3 ? 125 : 25;
+    for (int base = 0; base < ncode; base += 32) {
+      int code = base + lane;
+      int cnt = 0;
+      if (code < ncode) {
+        int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+        int mm = max(abs(dx), max(abs(dy), abs(dz)));
+        (void)lim;
+        if (mm == 2) {
+          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+          if (nb >= 0) cnt = lv.act_cnt[nb];
+        }
+      }
+      unsigned mask = __ballot_sync(FULL, cnt > 0);
+      // exclusive prefix of counts among flagged lanes
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int pos = __popc(mask & ((1u << lane) - 1));
+      if (cnt > 0) {
+        s_ocode[no + pos] = code;
+        s_obase[no + pos] = acc + incl - cnt;
+      }
+      no += __popc(mask);
+      acc += __shfl_sync(FULL, incl, 31);
+      cnt_here += cnt;
+    }
+    if (lane == 0) {
+      s_obase[no] = acc;
+      s_misc[0] = no;
+    }
+    (void)cnt_here;
+  }
+  __syncthreads();
+  if (active) {
+    // ring rows -> pool offsets, all warps of the box in parallel
+    const int no = s_misc[0];
+    const int nO = s_obase[no];
+    if (nO > ring_max) {
+      if (threadIdx.x == 0) set_err(err, DERR_INTERNAL);
+    } else {
+      for (int q = 0; q < no; q++) {
+        const int code = s_ocode[q];
+        const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+        const int64_t abase = lv.cell_dof_off[nb];
+        const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
+        for (int t = threadIdx.x; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
+          s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+      }
+    }
+  }
+  __syncthreads();
+  if (active && s_obase[s_misc[0]] <= ring_max) {
+    const int no = s_misc[0];
+    const int nO = s_obase[no];
+    const int m = nO + px.np;
+    const int64_t coff = lv.cell_dof_off[c];
+    const double D = ldexp(1.0, -lv.t);
+    double ctr[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) ctr[d] = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
+    const double rad = px.radius * D;
+    // own columns: positions relative to the box centre (for the proxy rows)
+    double xq[CPL][3];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+      int col = lane + 32 * q;
+      int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
+#pragma unroll
+      for (int d = 0; d < 3; d++) xq[q][d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr[d] : 0.0;
+    }
+    const T w = (T)K.w;
+    const int npan = (m + PR - 1) / PR;
+    for (int pnl = sw; pnl < npan; pnl += W) {
+      T pan[PR][CPL];
+#pragma unroll
+      for (int i = 0; i < PR; i++) {
+        const int row = pnl * PR + i;
+        int64_t src = -1;
+        int pm = -1;
+        if (row < nO) src = s_rowsrc[row];
+        else if (row < m) pm = row - nO;
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+          const int col = lane + 32 * q;
+          T v = (T)0;
+          if (col < b) {
+            if (src >= 0) {
+              v = lv.pool[src + col];
+            } else if (pm >= 0) {
+              double r2 = 0.0;
+#pragma unroll
+              for (int d = 0; d < 3; d++) {
+                double dd = rad * proxy_unit[3 * pm + d] - xq[q][d];
+                r2 += dd * dd;
+              }
+              v = w * kof(K.kind, (T)r2);
+            }
+          }
+          pan[i][q] = v;
+        }
+      }
+      fold_rows<T, CPL, PR>(pan, Rw, LDR, b, lane);
+    }
+  }
+  __syncthreads();
+  if (!active || sw != 0 || s_obase[s_misc[0]] > ring_max) return;
+  // fold the other sub-warps' triangles into this one
+  T *R = Rw;
+  for (int o = 1; o < W; o++) {
+    const T *Ro = Rw + (size_t)o * BM * LDR;
+    for (int p0 = 0; p0 < b; p0 += PR) {
+      T pan[PR][CPL];
+#pragma unroll
+      for (int i = 0; i < PR; i++)
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+          int col = lane + 32 * q, row = p0 + i;
+          pan[i][q] = (row < b && col < b) ? Ro[row * LDR + col] : (T)0;
+        }
+      fold_rows<T, CPL, PR>(pan, R, LDR, b, lane);
+    }
+  }
+  // greedy column-pivoted QR of the triangle
+  for (int q = lane; q < b; q += 32) perm[q] = q;
+  __syncwarp();
+  T r11 = (T)0;
+  int k = b;
+  for (int j = 0; j < b; j++) {
+    T best = (T)-1;
+    int bi = b;
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+      int col = lane + 32 * q;
+      if (col >= j && col < b) {
+        T sacc = (T)0;
+        for (int i = j; i < b; i++) sacc += R[i * LDR + col] * R[i * LDR + col];
+        if (sacc > best) {
+          best = sacc;
+          bi = col;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(FULL, best, o);
+      int oi = __shfl_xor_sync(FULL, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    const T cn = sqrt(best);
+    if (j == 0) r11 = cn;
+    // no valid pivot (all norms NaN) also stops
+    if (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) {
+      k = j;
+      break;
+    }
+    const int p = bi;
+    if (p != j) {
+      for (int i = lane; i < b; i += 32) {
+        T t0 = R[i * LDR + j];
+        R[i * LDR + j] = R[i * LDR + p];
+        R[i * LDR + p] = t0;
+      }
+      if (lane == 0) {
+        int tp = perm[j];
+        perm[j] = perm[p];
+        perm[p] = tp;
+      }
+    }
+    __syncwarp();
+    T sacc = (T)0;
+    for (int i = j + 1; i < b; i++) sacc += R[i * LDR + j] * R[i * LDR + j];
+    if (sacc > (T)0) {
+      const T x0 = R[j * LDR + j];
+      const T nrm = sqrt(x0 * x0 + sacc);
+      const T beta = x0 >= (T)0 ? -nrm : nrm;
+      const T tau = (beta - x0) / beta;
+      const T scl = (T)1 / (x0 - beta);
+#pragma unroll
+      for (int q = 0; q < CPL; q++) {
+        const int col = lane + 32 * q;
+        if (col > j && col < b) {
+          T d = (T)0;
+          for (int i = j + 1; i < b; i++) d += R[i * LDR + j] * R[i * LDR + col];
+          const T f = tau * (R[j * LDR + col] + scl * d);
+          const T fs = f * scl;
+          R[j * LDR + col] -= f;
+          for (int i = j + 1; i < b; i++) R[i * LDR + col] -= fs * R[i * LDR + j];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) R[j * LDR + j] = beta;
+      __syncwarp();
+    }
+  }
+  FBox<T> &fb = *fbp;
+  const int r = b - k;
+  // T = R11^{-1} R12, one lane per column
+  for (int cc = lane; cc < r; cc += 32) {
+    T *tcol = fb.Tm + (int64_t)cc * k;
+    for (int i = k - 1; i >= 0; i--) {
+      T sacc = R[i * LDR + k + cc];
+      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
+      tcol[i] = sacc / R[i * LDR + i];
+    }
+  }
+  const int64_t coff = lv.cell_dof_off[c];
+  for (int q = lane; q < b; q += 32) {
+    fb.loc[q] = perm[q];
+    fb.ids[q] = lv.cell_dofs[coff + perm[q]];
+  }
+  if (lane == 0) {
+    fb.k = k;
+    fb.r = r;
+    fb.no = s_obase[s_misc[0]];
+  }
+}
+
+template <typename T, int CPL>
+static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int W,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       double eps, int ring_max, cudaStream_t st, int *err) {
+  constexpr int BM = 32 * CPL;
+  // one box per CTA of W warps, each warp with its own b x b triangle
+  const size_t tri = (size_t)BM * (BM + 1) * sizeof(T);
+  int wmax = (int)((200u << 10) / tri);
+  if (wmax < 1) wmax = 1;
+  if (W > wmax) W = wmax;
+  const int wpc = W;
+  size_t smem = (((size_t)wpc * tri + 15) & ~(size_t)15) + (size_t)((125 + 126 + BM + 4 + 1) & ~1) * sizeof(int) +
+                (size_t)ring_max * sizeof(int64_t) + 16;
+  cudaFuncSetAttribute(k_idw<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idw<T, CPL><<<nbox, wpc * 32, smem, st>>>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max,
+                                              err);
+  count_launch();
+}
+
 template <typename T>
 void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, int mmax,
-               const Points &P, const KernelParams &K, const ProxyParams &px, double eps, T *gscratch,
-               int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err) {
+               const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit, double eps,
+               T *gscratch, int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err) {
   (void)mmax;
   if (nbox == 0) return;
+  if (bmax <= 128) {
+    // warps per box: enough warps in flight to cover the SMs
+    int W = nbox >= 600 ? 1 : (nbox >= 300 ? 2 : 4);
+    const int ring_max = mmax;
+    if (bmax <= 64) launch_idw<T, 2>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max, st, err);
+    else if (bmax <= 96) launch_idw<T, 3>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max, st, err);
+    else launch_idw<T, 4>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max, st, err);
+    return;
+  }
   int PR = bmax <= 80 ? 128 : 64;
   IdLayout<T> lay(bmax, PR);
   size_t smem = use_smem ? (size_t)lay.bytes : 0;
@@ -606,10 +958,302 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
   }
   for (int e = tid; e < r * r; e += NT) fb.LU[e] = LU[(e / r) * ldl + (e % r)];
   for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
+  // X_RR^{-1} = U^{-1} L^{-1} P, one column per thread (column piv[i] is
+  // U^{-1} L^{-1} e_i), kept for the solve sweeps
+  for (int i0 = tid; i0 < r; i0 += NT) {
+    T *x = fb.Xi + (int64_t)spiv[i0] * r;
+    for (int i = 0; i < r; i++) {
+      T sacc = i == i0 ? (T)1 : (T)0;
+      for (int l = 0; l < i; l++) sacc -= LU[i * ldl + l] * x[l];
+      x[i] = sacc;
+    }
+    for (int i = r - 1; i >= 0; i--) {
+      T sacc = x[i];
+      for (int l = i + 1; l < r; l++) sacc -= LU[i * ldl + l] * x[l];
+      x[i] = sacc / LU[i * ldl + i];
+    }
+  }
   // the box's active DOFs are now its skeleton, kept in ascending order
   const int64_t coff = lv.cell_dof_off[c];
   for (int s = tid; s < k; s += NT) {
     int v = sloc[s], rank = 0;
+    for (int s2 = 0; s2 < k; s2++) rank += sloc[s2] < v;
+    lv.act_idx[coff + rank] = v;
+  }
+  if (tid == 0) lv.act_cnt[c] = k;
+}
+
+// ---------------------------------------------------------------------------
+// Elimination, shared-memory form for b small enough: the LU of X_RR is
+// computed by one warp (no block barriers), X_RR^{-1} = U^{-1} L^{-1} P is
+// formed column by column from the LU factors, and E = X_JR X_RR^{-1},
+// G = X_RR^{-1} X_RJ are produced in chunks of CH rows / columns of J as
+// shared-memory products, written coalesced.  X_RJ is kept in the scratch
+// for the Schur update.
+// ---------------------------------------------------------------------------
+
+template <typename T> struct ElimChunk;
+template <> struct ElimChunk<float> { static constexpr int CH = 64; };
+template <> struct ElimChunk<double> { static constexpr int CH = 32; };
+
+template <typename T>
+__host__ __device__ inline size_t elim2_smem(int b, int k, int r) {
+  constexpr int CH = ElimChunk<T>::CH;
+  const int ldx = r | 1;
+  size_t pers = (size_t)k * r * 3 + (size_t)r * (r + 1);
+  size_t u1 = (size_t)b * (b + 1);
+  size_t u2 = (size_t)ldx * r + (size_t)(CH + 1) * b + (size_t)(b + 1) * CH;
+  size_t nT = pers + (u1 > u2 ? u1 : u2);
+  return nT * sizeof(T) + (size_t)(b + 2 * r + 8) * sizeof(int) + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
+                                              int64_t sstride, int *err) {
+  constexpr int CH = ElimChunk<T>::CH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nact[27], s_nn;
+  __shared__ int64_t s_off_in[27], s_off_out[27];
+  __shared__ int s_ld_in[27];
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ncode3 = dim == 3 ? 27 : 9;
+  const int center = code3(0, 0, 0, dim);
+  const int ldx = r | 1, ldl = r + 1, ldb = b + 1;
+  T *Ts = reinterpret_cast<T *>(smem_raw);          // k x r  (s + ri*k)
+  T *XRS = Ts + (size_t)k * r;                      // r x k  (ri + s*r)
+  T *XSR = XRS + (size_t)k * r;                     // k x r  (s + ri*k)
+  T *LU = XSR + (size_t)k * r;                      // r x r row-major, ld r+1
+  T *U0 = LU + (size_t)r * ldl;                     // union region
+  T *Ab = U0;                                       // A_BB in (S|R) order, column-major, ld b+1
+  T *Xi = U0;                                       // X_RR^{-1}, column-major, ld ldx (after the LU)
+  T *rawJ = Xi + (size_t)ldx * r;                   // CH rows of J x b  (al + p*(CH+1)) -> X_JR in place
+  T *rawC = rawJ + (size_t)(CH + 1) * b;            // b x CH columns of J (p + al*(b+1)) -> X_RJ in place
+  const size_t u1 = (size_t)b * ldb, u2 = (size_t)ldx * r + (size_t)(CH + 1) * b + (size_t)ldb * CH;
+  int *sloc = reinterpret_cast<int *>(U0 + (u1 > u2 ? u1 : u2));
+  int *spiv = sloc + b;
+  int *spinv = spiv + r;
+
+  if (tid == 0) {
+    int nn = 0, acc = k;
+    for (int code = 0; code < ncode3; code++) {
+      int dx, dy, dz;
+      decode3(code, dim, dx, dy, dz);
+      int nb = lv.cell_nbr[(int64_t)c * lv.NB + code5(dx, dy, dz, dim)];
+      s_ncell[code] = nb;
+      if (nb >= 0) {
+        s_off_in[code] = lv.pair_off[(int64_t)nb * lv.NB + code5(-dx, -dy, -dz, dim)];
+        s_off_out[code] = lv.pair_off[(int64_t)c * lv.NB + code5(dx, dy, dz, dim)];
+        s_ld_in[code] = lv.cell_b[nb];
+      }
+      if (code == center || nb < 0) continue;
+      int cnt = lv.act_cnt[nb];
+      if (cnt <= 0) continue;
+      s_ncode[nn] = code;
+      s_nstart[nn] = acc;
+      s_nact[nn] = (int)lv.cell_dof_off[nb];
+      acc += cnt;
+      nn++;
+    }
+    s_nstart[nn] = acc;
+    s_nn = nn;
+  }
+  for (int q = tid; q < b; q += NT) sloc[q] = fb.loc[q];
+  for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
+  __syncthreads();
+  const int nn = s_nn;
+  const int nj = s_nstart[nn];
+  if (nj > fb.njmax) {
+    if (tid == 0) set_err(err, DERR_INTERNAL);
+    return;
+  }
+  // J = [S (pivot order); N (near cells in code order, active ascending)]
+  for (int a = tid; a < nj; a += NT) {
+    int code, loc;
+    int64_t g;
+    if (a < k) {
+      code = center;
+      loc = sloc[a];
+      g = fb.ids[a];
+    } else {
+      int q = 0;
+      while (s_nstart[q + 1] <= a) q++;
+      code = s_ncode[q];
+      loc = lv.act_idx[s_nact[q] + (a - s_nstart[q])];
+      g = lv.cell_dofs[s_nact[q] + loc];
+    }
+    fb.J[a] = g;
+    fb.Jnb[a] = code;
+    fb.Jloc[a] = loc;
+  }
+  if (tid == 0) fb.nj = nj;
+  // stage A_BB in (S|R) order
+  const T *Aii = lv.pool + s_off_in[center];
+  for (int e = tid; e < b * b; e += NT) {
+    int pp = e % b, qq = e / b;
+    Ab[pp + qq * ldb] = Aii[sloc[pp] + (int64_t)sloc[qq] * b];
+  }
+  __syncthreads();
+  // X_RS = A_RS - T^T A_SS,  X_SR = A_SR - A_SS T
+  for (int e = tid; e < r * k; e += NT) {
+    int ri = e % r, s2 = e / r;
+    T acc = Ab[(k + ri) + s2 * ldb];
+    for (int s1 = 0; s1 < k; s1++) acc -= Ts[s1 + ri * k] * Ab[s1 + s2 * ldb];
+    XRS[ri + s2 * r] = acc;
+  }
+  for (int e = tid; e < r * k; e += NT) {
+    int s2 = e % k, ri = e / k;
+    T acc = Ab[s2 + (k + ri) * ldb];
+    for (int s1 = 0; s1 < k; s1++) acc -= Ab[s2 + s1 * ldb] * Ts[s1 + ri * k];
+    XSR[s2 + ri * k] = acc;
+  }
+  __syncthreads();
+  // X_RR = A_RR - T^T A_SR - X_RS T
+  for (int e = tid; e < r * r; e += NT) {
+    int ri = e % r, rj = e / r;
+    T acc = Ab[(k + ri) + (k + rj) * ldb];
+    for (int s1 = 0; s1 < k; s1++) {
+      acc -= Ts[s1 + ri * k] * Ab[s1 + (k + rj) * ldb];
+      acc -= XRS[ri + s1 * r] * Ts[s1 + rj * k];
+    }
+    LU[ri * ldl + rj] = acc;
+  }
+  __syncthreads();
+  // LU with partial pivoting by warp 0 (largest |entry|, ties to the lowest row)
+  if (warp == 0) {
+    for (int i = lane; i < r; i += 32) spiv[i] = i;
+    __syncwarp();
+    for (int j = 0; j < r; j++) {
+      T best = (T)-1;
+      int bi = r;
+      for (int i = j + lane; i < r; i += 32) {
+        T v = fabs(LU[i * ldl + j]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(FULL, best, o);
+        int oi = __shfl_xor_sync(FULL, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (bi >= r) {  // NaN column: keep the diagonal, report
+        bi = j;
+        if (lane == 0) set_err(err, DERR_NUMERIC);
+      }
+      if (best == (T)0 && lane == 0) set_err(err, DERR_NUMERIC);
+      if (bi != j) {
+        for (int cc = lane; cc < r; cc += 32) {
+          T t0 = LU[j * ldl + cc];
+          LU[j * ldl + cc] = LU[bi * ldl + cc];
+          LU[bi * ldl + cc] = t0;
+        }
+        if (lane == 0) {
+          int tp = spiv[j];
+          spiv[j] = spiv[bi];
+          spiv[bi] = tp;
+        }
+      }
+      __syncwarp();
+      const T d = LU[j * ldl + j];
+      for (int i = j + 1 + lane; i < r; i += 32) LU[i * ldl + j] /= d;
+      __syncwarp();
+      for (int i = j + 1; i < r; i++) {
+        const T l = LU[i * ldl + j];
+        for (int cc = j + 1 + lane; cc < r; cc += 32) LU[i * ldl + cc] -= l * LU[j * ldl + cc];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += NT) spinv[spiv[i]] = i;
+  for (int e = tid; e < r * r; e += NT) fb.LU[e] = LU[(e / r) * ldl + (e % r)];
+  for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
+  __syncthreads();
+  // X_RR^{-1} = U^{-1} L^{-1} P: column cc is U^{-1} L^{-1} e_{pinv[cc]}
+  for (int cc = tid; cc < r; cc += NT) {
+    T *x = Xi + (size_t)cc * ldx;
+    const int i0 = spinv[cc];
+    for (int i = 0; i < r; i++) {
+      T sacc = i == i0 ? (T)1 : (T)0;
+      for (int l = 0; l < i; l++) sacc -= LU[i * ldl + l] * x[l];
+      x[i] = sacc;
+    }
+    for (int i = r - 1; i >= 0; i--) {
+      T sacc = x[i];
+      for (int l = i + 1; l < r; l++) sacc -= LU[i * ldl + l] * x[l];
+      x[i] = sacc / LU[i * ldl + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += NT) fb.Xi[e] = Xi[(e % r) + (size_t)(e / r) * ldx];
+  T *Xrj_out = scratch + (int64_t)blockIdx.x * sstride + (int64_t)nj * r;  // r x nj, for the Schur update
+  for (int a0 = 0; a0 < nj; a0 += CH) {
+    const int na = min(CH, nj - a0);
+    // raw rows A(J_a, B) and columns A(B, J_a) of the chunk (S rows come from X_SR / X_RS)
+    for (int e = tid; e < na * b; e += NT) {
+      int al = e % na, pp = e / na, a = a0 + al;
+      if (a < k) {
+        if (pp >= k) rawJ[al + pp * (CH + 1)] = XSR[a + (pp - k) * k];
+      } else {
+        int code = fb.Jnb[a], la = fb.Jloc[a];
+        rawJ[al + pp * (CH + 1)] = lv.pool[s_off_in[code] + la + (int64_t)sloc[pp] * s_ld_in[code]];
+      }
+    }
+    for (int e = tid; e < na * b; e += NT) {
+      int pp = e % b, al = e / b, a = a0 + al;
+      if (a < k) {
+        if (pp >= k) rawC[pp + al * ldb] = XRS[(pp - k) + a * r];
+      } else {
+        int code = fb.Jnb[a], la = fb.Jloc[a];
+        rawC[pp + al * ldb] = lv.pool[s_off_out[code] + (int64_t)la * b + sloc[pp]];
+      }
+    }
+    __syncthreads();
+    // in place: X_JR = A_JR - A_JS T (rows a >= k);  X_RJ = A_RJ - T^T A_SJ
+    for (int e = tid; e < na * r; e += NT) {
+      int al = e % na, ri = e / na;
+      if (a0 + al >= k) {
+        T acc = rawJ[al + (k + ri) * (CH + 1)];
+        for (int s1 = 0; s1 < k; s1++) acc -= rawJ[al + s1 * (CH + 1)] * Ts[s1 + ri * k];
+        rawJ[al + (k + ri) * (CH + 1)] = acc;
+      }
+    }
+    for (int e = tid; e < na * r; e += NT) {
+      int ri = e % r, al = e / r;
+      T acc = rawC[(k + ri) + al * ldb];
+      if (a0 + al >= k) {
+        for (int s1 = 0; s1 < k; s1++) acc -= Ts[s1 + ri * k] * rawC[s1 + al * ldb];
+        rawC[(k + ri) + al * ldb] = acc;
+      }
+      Xrj_out[ri + (int64_t)(a0 + al) * r] = acc;
+    }
+    __syncthreads();
+    // E chunk = X_JR chunk * X_RR^{-1};  G chunk = X_RR^{-1} * X_RJ chunk
+    for (int e = tid; e < na * r; e += NT) {
+      int al = e % na, ri = e / na;
+      T acc = (T)0;
+      for (int l = 0; l < r; l++) acc += rawJ[al + (k + l) * (CH + 1)] * Xi[l + (size_t)ri * ldx];
+      fb.E[(a0 + al) + (int64_t)ri * nj] = acc;
+    }
+    for (int e = tid; e < na * r; e += NT) {
+      int ri = e % r, al = e / r;
+      T acc = (T)0;
+      for (int l = 0; l < r; l++) acc += Xi[ri + (size_t)l * ldx] * rawC[(k + l) + al * ldb];
+      fb.G[ri + (int64_t)(a0 + al) * r] = acc;
+    }
+    __syncthreads();
+  }
+  // the box's active DOFs are now its skeleton, kept in ascending order
+  const int64_t coff = lv.cell_dof_off[c];
+  for (int s1 = tid; s1 < k; s1 += NT) {
+    int v = sloc[s1], rank = 0;
     for (int s2 = 0; s2 < k; s2++) rank += sloc[s2] < v;
     lv.act_idx[coff + rank] = v;
   }
@@ -626,6 +1270,17 @@ template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
                  int64_t scratch_stride, cudaStream_t st, int *err) {
   if (nbox == 0) return;
+  {
+    // worst case over k + r = b of the shared-memory form
+    size_t worst = 0;
+    for (int r = 0; r <= bmax; r++) worst = std::max(worst, elim2_smem<T>(bmax, bmax - r, r));
+    if (worst <= (size_t)(220 << 10)) {
+      cudaFuncSetAttribute(k_elim2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)worst);
+      k_elim2<T><<<nbox, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, err);
+      count_launch();
+      return;
+    }
+  }
   // worst case over k + r = b: k r <= b^2/4, r <= b
   size_t smem = (size_t)bmax * bmax / 4 * sizeof(T) + (size_t)bmax * (bmax + 1) * sizeof(T) +
                 (size_t)2 * bmax * sizeof(int) + 64;
@@ -896,115 +1551,122 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
   const FBox<T> &fb = boxes[first + blockIdx.x];
   const int k = fb.k, r = fb.r, nj = fb.nj;
   if (r == 0) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
-  T *vS = reinterpret_cast<T *>(smem_raw);   // k x nrhs
-  T *vR = vS + (int64_t)k * nrhs;            // r x nrhs
-  T *tmp = vR + (int64_t)r * nrhs;           // scratch
+  const int tid = threadIdx.x;
+  // vectors in shared memory, layout [i * nrhs + c]
+  T *vS = reinterpret_cast<T *>(smem_raw);   // k
+  T *vR = vS + (size_t)k * nrhs;              // r
+  T *vJ = vR + (size_t)r * nrhs;              // nj
+  T *tmp = vJ + (size_t)nj * nrhs;            // r
   const int64_t *S = fb.ids, *Rr = fb.ids + k;
   for (int e = tid; e < k * nrhs; e += NT) vS[e] = v[S[e / nrhs] * nrhs + e % nrhs];
   for (int e = tid; e < r * nrhs; e += NT) vR[e] = v[Rr[e / nrhs] * nrhs + e % nrhs];
+  if (mode == SWEEP_SOLVE_BWD)
+    for (int e = tid; e < nj * nrhs; e += NT) vJ[e] = v[fb.J[e / nrhs] * nrhs + e % nrhs];
   __syncthreads();
   if (mode == SWEEP_SOLVE_FWD) {
     // U_T: v_R -= T^T v_S
     for (int e = tid; e < r * nrhs; e += NT) {
-      int ri = e / nrhs, c = e % nrhs;
-      T s = (T)0;
-      for (int q = 0; q < k; q++) s += fb.Tm[q + (int64_t)ri * k] * vS[q * nrhs + c];
-      vR[e] -= s;
+      int ri = e % r, c = e / r;
+      T acc = (T)0;
+      for (int q = 0; q < k; q++) acc += fb.Tm[q + (int64_t)ri * k] * vS[q * nrhs + c];
+      tmp[ri * nrhs + c] = vR[ri * nrhs + c] - acc;
     }
     __syncthreads();
     // L: v_J -= E v_R
     for (int e = tid; e < nj * nrhs; e += NT) {
       int a = e % nj, c = e / nj;
-      T s = (T)0;
-      for (int ri = 0; ri < r; ri++) s += fb.E[a + (int64_t)ri * nj] * vR[ri * nrhs + c];
-      v[fb.J[a] * nrhs + c] -= s;
+      T acc = (T)0;
+      for (int ri = 0; ri < r; ri++) acc += fb.E[a + (int64_t)ri * nj] * tmp[ri * nrhs + c];
+      v[fb.J[a] * nrhs + c] -= acc;
     }
-    // D^{-1} on R (v_R is final for this box): one warp per right-hand side
-    for (int c = warp; c < nrhs; c += nwarp) {
-      T *col = tmp + (int64_t)warp * 2 * r;
-      T *wk = col + r;
-      for (int i = lane; i < r; i += 32) col[i] = vR[i * nrhs + c];
-      __syncwarp();
-      warp_lu_solve(fb.LU, fb.piv, r, col, wk, lane);
-      for (int i = lane; i < r; i += 32) v[Rr[i] * nrhs + c] = col[i];
-      __syncwarp();
+    // D^{-1} on R (v_R is final for this box): x_R = X_RR^{-1} v_R
+    for (int e = tid; e < r * nrhs; e += NT) {
+      int i = e % r, c = e / r;
+      T acc = (T)0;
+      for (int l = 0; l < r; l++) acc += fb.Xi[i + (int64_t)l * r] * tmp[l * nrhs + c];
+      v[Rr[i] * nrhs + c] = acc;
     }
   } else if (mode == SWEEP_SOLVE_BWD) {
     // U: v_R -= G v_J
     for (int e = tid; e < r * nrhs; e += NT) {
       int ri = e % r, c = e / r;
-      T s = (T)0;
-      for (int a = 0; a < nj; a++) s += fb.G[ri + (int64_t)a * r] * v[fb.J[a] * nrhs + c];
-      vR[ri * nrhs + c] -= s;
+      T acc = (T)0;
+      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * vJ[a * nrhs + c];
+      vR[ri * nrhs + c] -= acc;
     }
     __syncthreads();
     // L_T: v_S -= T v_R
     for (int e = tid; e < k * nrhs; e += NT) {
-      int q = e / nrhs, c = e % nrhs;
-      T s = (T)0;
-      for (int ri = 0; ri < r; ri++) s += fb.Tm[q + (int64_t)ri * k] * vR[ri * nrhs + c];
-      v[S[q] * nrhs + c] = vS[e] - s;
+      int q = e % k, c = e / k;
+      T acc = (T)0;
+      for (int ri = 0; ri < r; ri++) acc += fb.Tm[q + (int64_t)ri * k] * vR[ri * nrhs + c];
+      v[S[q] * nrhs + c] = vS[q * nrhs + c] - acc;
     }
     for (int e = tid; e < r * nrhs; e += NT) v[Rr[e / nrhs] * nrhs + e % nrhs] = vR[e];
   } else if (mode == SWEEP_APPLY_FWD) {
     // L_T^{-1}: v_S += T v_R
     for (int e = tid; e < k * nrhs; e += NT) {
-      int q = e / nrhs, c = e % nrhs;
-      T s = (T)0;
-      for (int ri = 0; ri < r; ri++) s += fb.Tm[q + (int64_t)ri * k] * vR[ri * nrhs + c];
-      v[S[q] * nrhs + c] = vS[e] + s;
+      int q = e % k, c = e / k;
+      T acc = (T)0;
+      for (int ri = 0; ri < r; ri++) acc += fb.Tm[q + (int64_t)ri * k] * vR[ri * nrhs + c];
+      vS[q * nrhs + c] += acc;
+      v[S[q] * nrhs + c] = vS[q * nrhs + c];
     }
     __syncthreads();
-    // U^{-1}: v_R += G v_J (v_S already updated in v)
+    // gather v_J (its S part was just updated)
+    for (int e = tid; e < nj * nrhs; e += NT) {
+      int a = e / nrhs, c = e % nrhs;
+      vJ[e] = a < k ? vS[a * nrhs + c] : v[fb.J[a] * nrhs + c];
+    }
+    __syncthreads();
+    // U^{-1}: v_R += G v_J
     for (int e = tid; e < r * nrhs; e += NT) {
       int ri = e % r, c = e / r;
-      T s = (T)0;
-      for (int a = 0; a < nj; a++) s += fb.G[ri + (int64_t)a * r] * v[fb.J[a] * nrhs + c];
-      vR[ri * nrhs + c] += s;
+      T acc = (T)0;
+      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * vJ[a * nrhs + c];
+      vR[ri * nrhs + c] += acc;
     }
     __syncthreads();
     // D: y_R = P^T L U v_R
     for (int e = tid; e < r * nrhs; e += NT) {
       int i = e % r, c = e / r;
-      T s = (T)0;
-      for (int l = i; l < r; l++) s += fb.LU[(int64_t)i * r + l] * vR[l * nrhs + c];
-      tmp[i + (int64_t)c * r] = s;
+      T acc = (T)0;
+      for (int l = i; l < r; l++) acc += fb.LU[(int64_t)i * r + l] * vR[l * nrhs + c];
+      tmp[i * nrhs + c] = acc;
     }
     __syncthreads();
     for (int e = tid; e < r * nrhs; e += NT) {
       int i = e % r, c = e / r;
-      T s = tmp[i + (int64_t)c * r];
-      for (int l = 0; l < i; l++) s += fb.LU[(int64_t)i * r + l] * tmp[l + (int64_t)c * r];
-      v[Rr[fb.piv[i]] * nrhs + c] = s;
+      T acc = tmp[i * nrhs + c];
+      for (int l = 0; l < i; l++) acc += fb.LU[(int64_t)i * r + l] * tmp[l * nrhs + c];
+      v[Rr[fb.piv[i]] * nrhs + c] = acc;
     }
   } else {  // SWEEP_APPLY_BWD
     // L^{-1}: v_J += E v_R
     for (int e = tid; e < nj * nrhs; e += NT) {
       int a = e % nj, c = e / nj;
-      T s = (T)0;
-      for (int ri = 0; ri < r; ri++) s += fb.E[a + (int64_t)ri * nj] * vR[ri * nrhs + c];
-      v[fb.J[a] * nrhs + c] += s;
+      T acc = (T)0;
+      for (int ri = 0; ri < r; ri++) acc += fb.E[a + (int64_t)ri * nj] * vR[ri * nrhs + c];
+      T nv = v[fb.J[a] * nrhs + c] + acc;
+      v[fb.J[a] * nrhs + c] = nv;
+      if (a < k) vS[a * nrhs + c] = nv;  // S is the head of J
     }
     __syncthreads();
-    // U_T^{-1}: v_R += T^T v_S (v_S updated above, S is part of J)
+    // U_T^{-1}: v_R += T^T v_S
     for (int e = tid; e < r * nrhs; e += NT) {
-      int ri = e / nrhs, c = e % nrhs;
-      T s = (T)0;
-      for (int q = 0; q < k; q++) s += fb.Tm[q + (int64_t)ri * k] * v[S[q] * nrhs + c];
-      v[Rr[ri] * nrhs + c] = vR[e] + s;
+      int ri = e % r, c = e / r;
+      T acc = (T)0;
+      for (int q = 0; q < k; q++) acc += fb.Tm[q + (int64_t)ri * k] * vS[q * nrhs + c];
+      v[Rr[ri] * nrhs + c] = vR[ri * nrhs + c] + acc;
     }
   }
 }
 
 template <typename T>
-void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
+void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax, int njmax,
                   cudaStream_t st) {
   if (count == 0) return;
-  // vS, vR (each <= bmax x nrhs) + per-warp scratch (2 r) or an r x nrhs buffer
-  size_t wk = (size_t)2 * (NT / 32) * bmax;
-  if ((size_t)bmax * nrhs > wk) wk = (size_t)bmax * nrhs;
-  size_t smem = ((size_t)2 * bmax * nrhs + wk) * sizeof(T) + 64;
+  size_t smem = ((size_t)3 * bmax + (size_t)njmax) * nrhs * sizeof(T) + 64;
   cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs); count_launch();
 }
@@ -1138,14 +1800,15 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const i
   template void launch_assemble<T>(const AssembleList &, T *, const LevelDev<T> *, const Points &,             \
                                    const KernelParams &, int64_t, cudaStream_t);                              \
   template void launch_id<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, int, const Points &,       \
-                             const KernelParams &, const ProxyParams &, double, T *, int64_t, bool, cudaStream_t, \
+                             const KernelParams &, const ProxyParams &, const double *, double, T *, int64_t, bool,  \
+                             cudaStream_t,                                                                   \
                              int *);                                                                          \
   template void launch_elim<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, T *, int64_t,            \
                                cudaStream_t, int *);                                                          \
   template void launch_schur<T>(const LevelDev<T> &, const FBox<T> *, const int *, int, int, const T *, int64_t, \
                                 cudaStream_t);                                                                \
   template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \
-  template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, cudaStream_t);                 \
+  template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t);            \
   template void launch_top<T>(int, const T *, const int *, const int64_t *, int, T *, int, T *, cudaStream_t); \
   template void launch_permute<T>(int, const int64_t *, const double *, T *, double *, int64_t, int,          \
                                   cudaStream_t);

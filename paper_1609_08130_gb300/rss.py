@@ -246,7 +246,8 @@ class Factorization:
                     n=int(buf[4]), prec=int(buf[5]), depth=boxes[:, 0].copy(), b=boxes[:, 1].copy(),
                     k=boxes[:, 2].copy(), nj=boxes[:, 3].copy())
 
-    PROFILE_CLASSES = ["assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve", "permute"]
+    PROFILE_CLASSES = ["assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve", "permute",
+                       "host_tree", "host_level", "host_wait", "refine_op"]
 
     def profile(self, reset: bool = False) -> dict:
         """Per-kernel-class {launches, ms, bytes, flops} (needs profile=True)."""
