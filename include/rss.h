@@ -118,6 +118,31 @@ rss_status rss_apply(const rss_factorization *f, const double *x, double *y, int
  * may not alias.  nrhs >= 1. */
 rss_status rss_solve(const rss_factorization *f, const double *b, double *x, int nrhs);
 
+/* rss_solve_noalloc -- x = F^{-1} b, the same result as rss_solve, for callers
+ * that must not have the library allocate device memory during the call:
+ * programs that hand all device memory to their own allocator up front, or
+ * that keep a fixed memory budget inside a hot loop and cannot afford an
+ * allocation's cost or failure there.  rss_solve may allocate a working
+ * vector on its first use with a given number of right-hand sides; this
+ * variant never does.  The paper has no counterpart: it is an operational
+ * variant of the solve of Eq. 3.11.
+ *   Working space is one fixed 16 MiB array in device memory that exists
+ *   once per device from the moment the library is loaded until the process
+ *   exits.  It must hold the n x nrhs working vector plus 2 * ntop * nrhs
+ *   entries for the top block, in the factor's precision (4 bytes for a
+ *   RSS_MIXED factor, 8 for RSS_FP64); larger requests return RSS_EINVAL
+ *   without doing any work.  Nothing in it needs to start at zero: every
+ *   call overwrites what it reads.
+ *   The first call made with a given device current looks up the array's
+ *   device address (cudaGetSymbolAddress); make that first call before any
+ *   stream capture begins.
+ *   Every call uses the same array: calls whose work overlaps on the GPU
+ *   (different streams, different host threads) race and give wrong
+ *   results.  Calls serialised on one stream are safe.
+ *   b, x: device, n x nrhs column-major, may not alias; the caller owns
+ *   them.  nrhs >= 1.  Errors: RSS_EINVAL, RSS_ECUDA. */
+rss_status rss_solve_noalloc(const rss_factorization *f, const double *b, double *x, int nrhs);
+
 /* rss_solve_refined -- solve A x = b to a relative residual
  * max_c ||b_c - A x_c|| / ||b_c|| <= tol by GMRES-based iterative refinement
  * (Carson & Higham): x0 = F^{-1} b, then FP64 residuals with the exact

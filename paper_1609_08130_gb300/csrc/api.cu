@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1147,6 +1148,58 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free solve.  Its working vectors live in one fixed file-scope
+// device array instead of memory allocated per factor: every device that
+// loads this library holds the array until the process exits, every call
+// shares it, and calls whose work overlaps on the GPU would race on it.
+// ---------------------------------------------------------------------------
+
+static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[256];
+
+// Device address of the scratch array for the current device, looked up on
+// the first call made with that device current.
+static void *noalloc_scratch() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) throw Fail{RSS_ECUDA, "rss_solve_noalloc: device ordinal out of range"};
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail{RSS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)};
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+template <typename T>
+static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nrhs) {
+  const size_t vbytes = (((size_t)F.n * nrhs * sizeof(T)) + 255) & ~(size_t)255;
+  const size_t tbytes = (size_t)2 * F.ntop * nrhs * sizeof(T);
+  if (vbytes + tbytes > NOALLOC_SCRATCH_BYTES)
+    throw Fail{RSS_EINVAL, "rss_solve_noalloc: n * nrhs too large for the fixed 16 MiB scratch"};
+  unsigned char *base = static_cast<unsigned char *>(noalloc_scratch());
+  T *v = reinterpret_cast<T *>(base);
+  T *topwork = reinterpret_cast<T *>(base + vbytes);
+  cudaStream_t st = F.st;
+  launch_permute<T>(0, ptr<int64_t>(F.d_perm), b, v, nullptr, F.n, nrhs, st);
+  const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
+  for (const Phase &p : F.phases) launch_sweep<T>(SWEEP_SOLVE_FWD, bx, p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
+  launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top), F.ntop, v, nrhs, topwork, st);
+  for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
+    launch_sweep<T>(SWEEP_SOLVE_BWD, bx, it->first, it->count, v, nrhs, it->bmax, it->njmax, st);
+  launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, x, F.n, nrhs, st);
+  check_launch("rss_solve_noalloc");
+  CK(cudaStreamSynchronize(st));
+}
+
 static rss_status sweep_entry(const rss_factorization *f, const double *in, double *out, int nrhs, bool solve) {
   return guard([&] {
     if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "bad arguments"};
@@ -1333,6 +1386,21 @@ rss_status rss_apply(const rss_factorization *f, const double *x, double *y, int
 
 rss_status rss_solve(const rss_factorization *f, const double *b, double *x, int nrhs) {
   return sweep_entry(f, b, x, nrhs, true);
+}
+
+rss_status rss_solve_noalloc(const rss_factorization *f, const double *b, double *x, int nrhs) {
+  return guard([&] {
+    if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "rss_solve_noalloc: bad arguments"};
+    if (f->impl->prec == RSS_FP64) {
+      auto &F = static_cast<const Factor<double> &>(*f->impl);
+      if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
+      solve_noalloc(F, b, x, nrhs);
+    } else {
+      auto &F = static_cast<const Factor<float> &>(*f->impl);
+      if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
+      solve_noalloc(F, b, x, nrhs);
+    }
+  });
 }
 
 rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs) {
