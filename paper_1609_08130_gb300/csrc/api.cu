@@ -13,6 +13,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/rss.h"
@@ -137,20 +138,65 @@ static inline uint64_t morton_fast(const int64_t *c, int dim) {
                   : (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
 }
 
-// Stable LSD radix sort of idx by key (8-bit digits over the used bits).
+// Stable LSD radix sort of idx by key: 11-bit digits over the used bits,
+// host threads over contiguous chunks (per-thread digit histograms give
+// every thread its own stable output positions), and digit passes in which
+// every key has the same digit are skipped.
 static void radix_sort_by_key(std::vector<uint64_t> &key, std::vector<int64_t> &idx, int key_bits) {
   const size_t n = key.size();
+  const int RB = 11, NBK = 1 << RB;
+  unsigned hw = std::thread::hardware_concurrency();
+  int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
+  if (n < ((size_t)1 << 15)) nt = 1;
   std::vector<uint64_t> k2(n);
   std::vector<int64_t> i2(n);
-  for (int sh = 0; sh < key_bits; sh += 8) {
-    size_t cnt[257] = {0};
-    for (size_t q = 0; q < n; q++) cnt[((key[q] >> sh) & 255) + 1]++;
-    for (int d = 0; d < 256; d++) cnt[d + 1] += cnt[d];
-    for (size_t q = 0; q < n; q++) {
-      size_t pos = cnt[(key[q] >> sh) & 255]++;
-      k2[pos] = key[q];
-      i2[pos] = idx[q];
+  std::vector<size_t> cnt((size_t)nt * NBK);
+  auto range = [&](int t, size_t &lo, size_t &hi) {
+    lo = n * t / nt;
+    hi = n * (t + 1) / nt;
+  };
+  for (int sh = 0; sh < key_bits; sh += RB) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    auto hist = [&](int t) {
+      size_t lo, hi;
+      range(t, lo, hi);
+      size_t *c = &cnt[(size_t)t * NBK];
+      for (size_t q = lo; q < hi; q++) c[(key[q] >> sh) & (NBK - 1)]++;
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(hist, t);
+    hist(0);
+    for (auto &x : th) x.join();
+    th.clear();
+    // skip a digit on which all keys agree
+    int used = 0;
+    for (int d = 0; d < NBK && used < 2; d++) {
+      size_t tot = 0;
+      for (int t = 0; t < nt; t++) tot += cnt[(size_t)t * NBK + d];
+      if (tot) used++;
     }
+    if (used < 2) continue;
+    // exclusive offsets in (digit, thread) order
+    size_t acc = 0;
+    for (int d = 0; d < NBK; d++)
+      for (int t = 0; t < nt; t++) {
+        size_t c = cnt[(size_t)t * NBK + d];
+        cnt[(size_t)t * NBK + d] = acc;
+        acc += c;
+      }
+    auto scatter = [&](int t) {
+      size_t lo, hi;
+      range(t, lo, hi);
+      size_t *c = &cnt[(size_t)t * NBK];
+      for (size_t q = lo; q < hi; q++) {
+        size_t pos = c[(key[q] >> sh) & (NBK - 1)]++;
+        k2[pos] = key[q];
+        i2[pos] = idx[q];
+      }
+    };
+    for (int t = 1; t < nt; t++) th.emplace_back(scatter, t);
+    scatter(0);
+    for (auto &x : th) x.join();
     key.swap(k2);
     idx.swap(i2);
   }
@@ -235,14 +281,14 @@ static void build_tree(HTree &T, const double *pts_host) {
     for (int d = 0; d < dim; d++) T.x[g * dim + d] = pts_host[T.perm[g] * dim + d];
   T.level.assign(T.maxdepth + 1, {});
   for (int i = 0; i < (int)T.depth.size(); i++) T.level[T.depth[i]].push_back(i);
-  for (auto &lv : T.level) {
-    std::sort(lv.begin(), lv.end(), [&](int a, int b) {
-      int ca = colour_of(&T.coord[3 * a], dim), cb = colour_of(&T.coord[3 * b], dim);
-      if (ca != cb) return ca < cb;
-      int64_t pa[3] = {T.coord[3 * a], T.coord[3 * a + 1], T.coord[3 * a + 2]};
-      int64_t pb[3] = {T.coord[3 * b], T.coord[3 * b + 1], T.coord[3 * b + 2]};
-      return morton_key(pa, dim, 21) < morton_key(pb, dim, 21);
-    });
+  {
+    // elimination order within a depth: colour-major, Morton within a colour
+    std::vector<std::pair<int, uint64_t>> ord(T.depth.size());
+    for (size_t i = 0; i < T.depth.size(); i++) {
+      int64_t pc[3] = {T.coord[3 * i], T.coord[3 * i + 1], T.coord[3 * i + 2]};
+      ord[i] = {colour_of(&T.coord[3 * i], dim), morton_fast(pc, dim)};
+    }
+    for (auto &lv : T.level) std::sort(lv.begin(), lv.end(), [&](int a, int b) { return ord[a] < ord[b]; });
   }
 }
 

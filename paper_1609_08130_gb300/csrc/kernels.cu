@@ -385,54 +385,106 @@ template <> struct IdwRows<double> { static constexpr int PR = 16; };
 constexpr unsigned FULL = 0xffffffffu;
 
 // Fold the PR rows held in `pan` into the triangle R (row-major, ld ldr).
+// The owner lane of column j publishes the column and its squared norm
+// through the warp's shared buffer `vbuf` (PR + 4 entries, 16-byte aligned);
+// the owner of column j+1 publishes it into the other half of the double
+// buffer as soon as its own update for step j is done, so the next step
+// starts from data already in shared memory.  The slot loop is unrolled so
+// that lanes whose columns lie left of j drop out at compile time.
+template <typename T, int PR>
+__device__ __forceinline__ void publish_col(T *dst, const T (&col)[PR]) {
+  T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+#pragma unroll
+  for (int i = 0; i < PR; i += 4) {
+    s0 += col[i] * col[i];
+    s1 += col[i + 1] * col[i + 1];
+    s2 += col[i + 2] * col[i + 2];
+    s3 += col[i + 3] * col[i + 3];
+  }
+#pragma unroll
+  for (int i = 0; i < PR; i++) dst[i] = col[i];
+  dst[PR] = (s0 + s1) + (s2 + s3);
+}
+
 template <typename T, int CPL, int PR>
-__device__ __forceinline__ void fold_rows(T (&pan)[PR][CPL], T *R, int ldr, int b, int lane) {
-  for (int j = 0; j < b; j++) {
-    const int slot = j >> 5, owner = j & 31;
-    T v[PR];
-    T s0 = (T)0, s1 = (T)0;
+__device__ __forceinline__ void fold_rows(T (&pan)[PR][CPL], T *R, int ldr, int b, int lane, T *vbuf) {
+  constexpr int VS = PR + 4;  // one half of the double buffer
+  if (b <= 0) return;
+  // column 0 is owned by lane 0, slot 0
+  if (lane == 0) {
+    T col[PR];
 #pragma unroll
-    for (int i = 0; i < PR; i++) {
-      T src = pan[i][0];
+    for (int i = 0; i < PR; i++) col[i] = pan[i][0];
+    publish_col<T, PR>(vbuf, col);
+  }
+  __syncwarp();
 #pragma unroll
-      for (int q = 1; q < CPL; q++)
-        if (slot == q) src = pan[i][q];
-      v[i] = __shfl_sync(FULL, src, owner);
-      if (i & 1) s1 += v[i] * v[i];
-      else s0 += v[i] * v[i];
-    }
-    const T s = s0 + s1;
-    if (s > (T)0) {
-      const T x0 = R[j * ldr + j];
-      const T nrm = sqrt(x0 * x0 + s);
-      const T beta = x0 >= (T)0 ? -nrm : nrm;
-      const T tau = (beta - x0) / beta;
-      const T scl = (T)1 / (x0 - beta);
+  for (int q = 0; q < CPL; q++) {
+    for (int jj = 0; jj < 32; jj++) {
+      const int j = q * 32 + jj;
+      if (j >= b) break;
+      const T *vb = vbuf + (j & 1) * VS;
+      T *vn = vbuf + ((j + 1) & 1) * VS;
+      T v[PR];
 #pragma unroll
-      for (int q = 0; q < CPL; q++) {
-        const int col = lane + 32 * q;
-        if (col > j && col < b) {
-          T d0 = (T)0, d1 = (T)0, d2 = (T)0, d3 = (T)0;
+      for (int i = 0; i < PR; i++) v[i] = vb[i];
+      const T s = vb[PR];
+      // owner of the next column (same slot unless jj == 31)
+      const int jn = j + 1;
+      const int on = jn & 31, qn = jn >> 5;
+      if (s > (T)0) {
+        const T x0 = R[j * ldr + j];
+        const T nrm = sqrt(x0 * x0 + s);
+        const T beta = x0 >= (T)0 ? -nrm : nrm;
+        const T tau = (beta - x0) / beta;
+        const T scl = (T)1 / (x0 - beta);
 #pragma unroll
-          for (int i = 0; i < PR; i += 4) {
-            d0 += v[i] * pan[i][q];
-            d1 += v[i + 1] * pan[i + 1][q];
-            d2 += v[i + 2] * pan[i + 2][q];
-            d3 += v[i + 3] * pan[i + 3][q];
+        for (int qq = q; qq < CPL; qq++) {
+          const int col = lane + 32 * qq;
+          const bool act = (qq > q ? true : lane > jj) && col < b;
+          if (act) {
+            T d[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) d[u] = (T)0;
+#pragma unroll
+            for (int i = 0; i < PR; i += 8)
+#pragma unroll
+              for (int u = 0; u < 8 && i + u < PR; u++) d[u] += v[i + u] * pan[i + u][qq];
+            const T dd = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
+            const T wv = R[j * ldr + col] + scl * dd;
+            const T f = tau * wv;
+            const T fs = f * scl;
+            R[j * ldr + col] -= f;
+#pragma unroll
+            for (int i = 0; i < PR; i++) pan[i][qq] -= fs * v[i];
+            // publish the next pivot column as soon as it is updated
+            if (jn < b && col == jn) {
+              T cn[PR];
+#pragma unroll
+              for (int i = 0; i < PR; i++) cn[i] = pan[i][qq];
+              publish_col<T, PR>(vn, cn);
+            }
           }
-          const T wv = R[j * ldr + col] + scl * ((d0 + d1) + (d2 + d3));
-          const T f = tau * wv;
-          const T fs = f * scl;
-          R[j * ldr + col] -= f;
-#pragma unroll
-          for (int i = 0; i < PR; i++) pan[i][q] -= fs * v[i];
         }
+        __syncwarp();
+        if (lane == jj) R[j * ldr + j] = beta;
+      } else if (jn < b && lane == on) {
+        // nothing to annihilate: column jn is unchanged, publish it as is
+        T cn[PR];
+#pragma unroll
+        for (int i = 0; i < PR; i++) {
+          T x = pan[i][0];
+#pragma unroll
+          for (int u = 1; u < CPL; u++)
+            if (qn == u) x = pan[i][u];
+          cn[i] = x;
+        }
+        publish_col<T, PR>(vn, cn);
       }
-      __syncwarp();
-      if (lane == owner) R[j * ldr + j] = beta;
       __syncwarp();
     }
   }
+  __syncwarp();
 }
 
 template <typename T, int CPL>
@@ -449,7 +501,9 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
   const int lb = warp / W, sw = warp % W;       // local box, sub-warp
   const int qbox = blockIdx.x * bpc + lb;
   T *Rw = reinterpret_cast<T *>(smem_raw) + (size_t)warp * BM * LDR;
-  int *ibase = reinterpret_cast<int *>(smem_raw + (((size_t)wpc * BM * LDR * sizeof(T) + 15) & ~(size_t)15));
+  const size_t tri_bytes = (((size_t)wpc * BM * LDR * sizeof(T) + 15) & ~(size_t)15);
+  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)warp * 2 * (PR + 4);  // column broadcast
+  int *ibase = reinterpret_cast<int *>(smem_raw + tri_bytes + (size_t)wpc * 2 * (PR + 4) * sizeof(T));
   int *s_ocode = ibase + lb * (125 + 126 + BM + 4);
   int *s_obase = s_ocode + 125;
   int *perm = s_obase + 126;
@@ -573,27 +627,32 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
           pan[i][q] = v;
         }
       }
-      fold_rows<T, CPL, PR>(pan, Rw, LDR, b, lane);
+      fold_rows<T, CPL, PR>(pan, Rw, LDR, b, lane, vbuf);
+    }
+  }
+  // tree merge of the sub-warps' triangles: in round `step`, sub-warp sw
+  // (a multiple of 2*step) absorbs sub-warp sw + step
+  const bool ok_ring = active && s_obase[s_misc[0]] <= ring_max;
+  for (int step = 1; step < W; step <<= 1) {
+    __syncthreads();
+    if (ok_ring && sw % (2 * step) == 0 && sw + step < W) {
+      const T *Ro = Rw + (size_t)step * BM * LDR;
+      for (int p0 = 0; p0 < b; p0 += PR) {
+        T pan[PR][CPL];
+#pragma unroll
+        for (int i = 0; i < PR; i++)
+#pragma unroll
+          for (int q = 0; q < CPL; q++) {
+            int col = lane + 32 * q, row = p0 + i;
+            pan[i][q] = (row < b && col < b) ? Ro[row * LDR + col] : (T)0;
+          }
+        fold_rows<T, CPL, PR>(pan, Rw, LDR, b, lane, vbuf);
+      }
     }
   }
   __syncthreads();
-  if (!active || sw != 0 || s_obase[s_misc[0]] > ring_max) return;
-  // fold the other sub-warps' triangles into this one
+  if (!ok_ring || sw != 0) return;
   T *R = Rw;
-  for (int o = 1; o < W; o++) {
-    const T *Ro = Rw + (size_t)o * BM * LDR;
-    for (int p0 = 0; p0 < b; p0 += PR) {
-      T pan[PR][CPL];
-#pragma unroll
-      for (int i = 0; i < PR; i++)
-#pragma unroll
-        for (int q = 0; q < CPL; q++) {
-          int col = lane + 32 * q, row = p0 + i;
-          pan[i][q] = (row < b && col < b) ? Ro[row * LDR + col] : (T)0;
-        }
-      fold_rows<T, CPL, PR>(pan, R, LDR, b, lane);
-    }
-  }
   // greedy column-pivoted QR of the triangle
   for (int q = lane; q < b; q += 32) perm[q] = q;
   __syncwarp();
@@ -606,8 +665,18 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
     for (int q = 0; q < CPL; q++) {
       int col = lane + 32 * q;
       if (col >= j && col < b) {
-        T sacc = (T)0;
-        for (int i = j; i < b; i++) sacc += R[i * LDR + col] * R[i * LDR + col];
+        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+        int i = j;
+        for (; i + 3 < b; i += 4) {
+          const T x0 = R[i * LDR + col], x1 = R[(i + 1) * LDR + col];
+          const T x2 = R[(i + 2) * LDR + col], x3 = R[(i + 3) * LDR + col];
+          a0 += x0 * x0;
+          a1 += x1 * x1;
+          a2 += x2 * x2;
+          a3 += x3 * x3;
+        }
+        for (; i < b; i++) a0 += R[i * LDR + col] * R[i * LDR + col];
+        const T sacc = (a0 + a1) + (a2 + a3);
         if (sacc > best) {
           best = sacc;
           bi = col;
@@ -644,8 +713,20 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
       }
     }
     __syncwarp();
-    T sacc = (T)0;
-    for (int i = j + 1; i < b; i++) sacc += R[i * LDR + j] * R[i * LDR + j];
+    T sacc;
+    {
+      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+      int i = j + 1;
+      for (; i + 3 < b; i += 4) {
+        const T x0 = R[i * LDR + j], x1 = R[(i + 1) * LDR + j], x2 = R[(i + 2) * LDR + j], x3 = R[(i + 3) * LDR + j];
+        a0 += x0 * x0;
+        a1 += x1 * x1;
+        a2 += x2 * x2;
+        a3 += x3 * x3;
+      }
+      for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + j];
+      sacc = (a0 + a1) + (a2 + a3);
+    }
     if (sacc > (T)0) {
       const T x0 = R[j * LDR + j];
       const T nrm = sqrt(x0 * x0 + sacc);
@@ -656,8 +737,16 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
       for (int q = 0; q < CPL; q++) {
         const int col = lane + 32 * q;
         if (col > j && col < b) {
-          T d = (T)0;
-          for (int i = j + 1; i < b; i++) d += R[i * LDR + j] * R[i * LDR + col];
+          T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+          int i = j + 1;
+          for (; i + 3 < b; i += 4) {
+            a0 += R[i * LDR + j] * R[i * LDR + col];
+            a1 += R[(i + 1) * LDR + j] * R[(i + 1) * LDR + col];
+            a2 += R[(i + 2) * LDR + j] * R[(i + 2) * LDR + col];
+            a3 += R[(i + 3) * LDR + j] * R[(i + 3) * LDR + col];
+          }
+          for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + col];
+          const T d = (a0 + a1) + (a2 + a3);
           const T f = tau * (R[j * LDR + col] + scl * d);
           const T fs = f * scl;
           R[j * LDR + col] -= f;
@@ -692,6 +781,411 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column-per-thread ID for boxes with b <= NC (64 or 128).  A "fold group" is
+// NC threads; thread c owns column c of the group's b x b triangle R (shared
+// memory, row-major) and holds column c of a PR-row panel of the ID matrix in
+// registers.  One Householder reflector per column step: the owner of column
+// j publishes it (and its squared norm) through a double buffer as soon as
+// its update of step j-1 is done, the group synchronises on a named barrier,
+// and every thread updates its own column.  G groups per box split the rows
+// and their triangles are merged by a tree; group 0 then runs the greedy
+// column-pivoted QR of the triangle, again one column per thread.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The owner of column j publishes [v (PR entries) | tau | scl | beta | flag]
+// for the reflector of step j, computed from its column, its squared norm
+// and the current diagonal R[j][j]; flag = 0 means there is nothing to
+// annihilate.  Entries are padded to a multiple of four for vector loads.
+template <typename T, int PR>
+__device__ __forceinline__ void publish_reflector(T *dst, const T (&pan)[PR], T x0) {
+  T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+#pragma unroll
+  for (int i = 0; i < PR; i += 4) {
+    s0 += pan[i] * pan[i];
+    s1 += pan[i + 1] * pan[i + 1];
+    s2 += pan[i + 2] * pan[i + 2];
+    s3 += pan[i + 3] * pan[i + 3];
+  }
+  const T s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+  for (int i = 0; i < PR; i++) dst[i] = pan[i];
+  if (s > (T)0) {
+    const T nrm = sqrt(x0 * x0 + s);
+    const T beta = x0 >= (T)0 ? -nrm : nrm;
+    dst[PR] = (beta - x0) / beta;
+    dst[PR + 1] = (T)1 / (x0 - beta);
+    dst[PR + 2] = beta;
+    dst[PR + 3] = (T)1;
+  } else {
+    dst[PR + 3] = (T)0;
+  }
+}
+
+template <typename T, int PR> __device__ __forceinline__ void load_vec(T (&v)[PR], const T *src);
+template <> __device__ __forceinline__ void load_vec<float, 32>(float (&v)[32], const float *src) {
+  const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    float4 t = s4[i];
+    v[4 * i] = t.x;
+    v[4 * i + 1] = t.y;
+    v[4 * i + 2] = t.z;
+    v[4 * i + 3] = t.w;
+  }
+}
+template <> __device__ __forceinline__ void load_vec<double, 16>(double (&v)[16], const double *src) {
+  const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    double2 t = s2[i];
+    v[2 * i] = t.x;
+    v[2 * i + 1] = t.y;
+  }
+}
+
+// Fold the PR rows in `pan` (this thread's column `col`) into R.  The
+// reflector of step j is published by the owner of column j at the end of
+// step j-1 (double buffer), so each step costs one barrier and, per thread,
+// one vector load, a dot product and an update of its own column.
+template <typename T, int PR>
+__device__ __forceinline__ void fold_group(T (&pan)[PR], T *R, int ldr, int b, int col, T *vbuf, int bar_id,
+                                           int nthr) {
+  constexpr int VS = PR + 4;
+  if (col == 0 && b > 0) publish_reflector<T, PR>(vbuf, pan, R[0]);
+  for (int j = 0; j < b; j++) {
+    group_bar(bar_id, nthr);
+    const T *vb = vbuf + (j & 1) * VS;
+    T *vn = vbuf + ((j + 1) & 1) * VS;
+    const T flag = vb[PR + 3];
+    if (flag != (T)0) {
+      if (col > j && col < b) {
+        T v[PR];
+        load_vec<T, PR>(v, vb);
+        const T tau = vb[PR], scl = vb[PR + 1];
+        T d[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) d[u] = (T)0;
+#pragma unroll
+        for (int i = 0; i < PR; i += 8)
+#pragma unroll
+          for (int u = 0; u < 8 && i + u < PR; u++) d[u] += v[i + u] * pan[i + u];
+        const T dd = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
+        const T rj = R[j * ldr + col];
+        const T f = tau * (rj + scl * dd);
+        const T fs = f * scl;
+#pragma unroll
+        for (int i = 0; i < PR; i++) pan[i] -= fs * v[i];
+        R[j * ldr + col] = rj - f;
+        if (col == j + 1) publish_reflector<T, PR>(vn, pan, R[col * ldr + col]);
+      } else if (col == j) {
+        R[j * ldr + j] = vb[PR + 2];  // nobody reads R[j][j] again in this fold
+      }
+    } else if (col == j + 1 && col < b) {
+      publish_reflector<T, PR>(vn, pan, R[col * ldr + col]);
+    }
+  }
+  group_bar(bar_id, nthr);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
+                                             Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
+                                             double eps, int ring_max, int *err) {
+  constexpr int PR = IdwRows<T>::PR;
+  constexpr int LDR = NC + 1;
+  constexpr int VS = PR + 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ocode[125], s_obase[126], s_no;
+  __shared__ T s_red_v[8];
+  __shared__ int s_red_i[8];
+  __shared__ T s_hh[4];  // x0, beta, tau, scl of the current CPQR step
+  __shared__ int s_stop, s_piv, s_k;
+  const int tid = threadIdx.x;
+  const int grp = tid / NC, col = tid % NC;
+  const int bar_id = 1 + grp;
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int c = fb.cell, b = fb.b, dim = lv.dim;
+  T *Rg = reinterpret_cast<T *>(smem_raw) + (size_t)grp * NC * LDR;
+  const size_t tri_bytes = (((size_t)G * NC * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)grp * 2 * VS;
+  int64_t *s_rowsrc = reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)G * 2 * VS * sizeof(T) + 15) & ~(size_t)15));
+  int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
+
+  for (int e = col; e < NC * LDR; e += NC) Rg[e] = (T)0;
+  if (tid < 32) {
+    const int ncode = dim == 3 ? 125 : 25;
+    int no = 0, acc = 0;
+    for (int base = 0; base < ncode; base += 32) {
+      int code = base + tid, cnt = 0;
+      if (code < ncode) {
+        int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+        if (max(abs(dx), max(abs(dy), abs(dz))) == 2) {
+          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+          if (nb >= 0) cnt = lv.act_cnt[nb];
+        }
+      }
+      unsigned mask = __ballot_sync(FULL, cnt > 0);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, o);
+        if (tid >= o) incl += t;
+      }
+      int pos = __popc(mask & ((1u << tid) - 1));
+      if (cnt > 0) {
+        s_ocode[no + pos] = code;
+        s_obase[no + pos] = acc + incl - cnt;
+      }
+      no += __popc(mask);
+      acc += __shfl_sync(FULL, incl, 31);
+    }
+    if (tid == 0) {
+      s_obase[no] = acc;
+      s_no = no;
+    }
+  }
+  __syncthreads();
+  const int no = s_no;
+  const int nO = s_obase[no];
+  if (nO > ring_max) {
+    if (tid == 0) set_err(err, DERR_INTERNAL);
+    return;  // uniform: every thread sees the same nO
+  }
+  for (int q = 0; q < no; q++) {
+    const int code = s_ocode[q];
+    const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+    const int64_t abase = lv.cell_dof_off[nb];
+    const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
+    for (int t = tid; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
+      s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+  }
+  __syncthreads();
+  const int m = nO + px.np;
+  const int64_t coff = lv.cell_dof_off[c];
+  const double D = ldexp(1.0, -lv.t);
+  const double rad = px.radius * D;
+  double xq[3];
+  {
+    const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
+      xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+    }
+  }
+  const T w = (T)K.w;
+  const int npan = (m + PR - 1) / PR;
+  for (int pnl = grp; pnl < npan; pnl += G) {
+    T pan[PR];
+#pragma unroll
+    for (int i = 0; i < PR; i++) {
+      const int row = pnl * PR + i;
+      T v = (T)0;
+      if (col < b) {
+        if (row < nO) {
+          v = lv.pool[s_rowsrc[row] + col];
+        } else if (row < m) {
+          const int pm = row - nO;
+          double r2 = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; d++) {
+            const double dd = rad * proxy_unit[3 * pm + d] - xq[d];
+            r2 += dd * dd;
+          }
+          v = w * kof(K.kind, (T)r2);
+        }
+      }
+      pan[i] = v;
+    }
+    fold_group<T, PR>(pan, Rg, LDR, b, col, vbuf, bar_id, NC);
+  }
+  // tree merge: in round `step`, group g (a multiple of 2*step) absorbs g + step
+  for (int step = 1; step < G; step <<= 1) {
+    __syncthreads();
+    if (grp % (2 * step) == 0 && grp + step < G) {
+      const T *Ro = Rg + (size_t)step * NC * LDR;
+      for (int p0 = 0; p0 < b; p0 += PR) {
+        T pan[PR];
+#pragma unroll
+        for (int i = 0; i < PR; i++) pan[i] = (p0 + i < b && col < b) ? Ro[(p0 + i) * LDR + col] : (T)0;
+        fold_group<T, PR>(pan, Rg, LDR, b, col, vbuf, bar_id, NC);
+      }
+    }
+  }
+  __syncthreads();
+  if (grp != 0) return;
+  // greedy column-pivoted QR of the triangle, one column per thread
+  T *R = Rg;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = NC / 32;
+  if (col < b) perm[col] = col;
+  if (tid == 0) s_k = b;
+  T r11 = (T)0;
+  for (int j = 0; j < b; j++) {
+    T best = (T)-1;
+    int bi = b;
+    if (col >= j && col < b) {
+      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+      int i = j;
+      for (; i + 3 < b; i += 4) {
+        const T x0 = R[i * LDR + col], x1 = R[(i + 1) * LDR + col];
+        const T x2 = R[(i + 2) * LDR + col], x3 = R[(i + 3) * LDR + col];
+        a0 += x0 * x0;
+        a1 += x1 * x1;
+        a2 += x2 * x2;
+        a3 += x3 * x3;
+      }
+      for (; i < b; i++) a0 += R[i * LDR + col] * R[i * LDR + col];
+      best = (a0 + a1) + (a2 + a3);
+      bi = col;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(FULL, best, o);
+      int oi = __shfl_xor_sync(FULL, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_red_v[wid] = best;
+      s_red_i[wid] = bi;
+    }
+    group_bar(1, NC);
+    if (tid == 0) {
+      for (int u = 1; u < NW; u++)
+        if (s_red_v[u] > best || (s_red_v[u] == best && s_red_i[u] < bi)) {
+          best = s_red_v[u];
+          bi = s_red_i[u];
+        }
+      const T cn = sqrt(best);
+      if (j == 0) r11 = cn;
+      // no valid pivot (all norms NaN) also stops
+      const int stop = (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
+      s_stop = stop;
+      s_piv = bi;
+      if (stop) s_k = j;
+    }
+    group_bar(1, NC);
+    if (s_stop) break;
+    const int p = s_piv;
+    if (p != j) {
+      for (int i = col; i < b; i += NC) {
+        T t0 = R[i * LDR + j];
+        R[i * LDR + j] = R[i * LDR + p];
+        R[i * LDR + p] = t0;
+      }
+      if (tid == 0) {
+        int tp = perm[j];
+        perm[j] = perm[p];
+        perm[p] = tp;
+      }
+    }
+    group_bar(1, NC);
+    if (col == j) {
+      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+      int i = j + 1;
+      for (; i + 3 < b; i += 4) {
+        const T x0 = R[i * LDR + j], x1 = R[(i + 1) * LDR + j], x2 = R[(i + 2) * LDR + j], x3 = R[(i + 3) * LDR + j];
+        a0 += x0 * x0;
+        a1 += x1 * x1;
+        a2 += x2 * x2;
+        a3 += x3 * x3;
+      }
+      for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + j];
+      const T sacc = (a0 + a1) + (a2 + a3);
+      const T x0 = R[j * LDR + j];
+      if (sacc > (T)0) {
+        const T nrm = sqrt(x0 * x0 + sacc);
+        const T beta = x0 >= (T)0 ? -nrm : nrm;
+        s_hh[0] = x0;
+        s_hh[1] = beta;
+        s_hh[2] = (beta - x0) / beta;
+        s_hh[3] = (T)1 / (x0 - beta);
+      } else {
+        s_hh[2] = (T)0;  // tau = 0: no reflection
+      }
+    }
+    group_bar(1, NC);
+    const T tau = s_hh[2];
+    if (tau != (T)0 && col > j && col < b) {
+      const T scl = s_hh[3];
+      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+      int i = j + 1;
+      for (; i + 3 < b; i += 4) {
+        a0 += R[i * LDR + j] * R[i * LDR + col];
+        a1 += R[(i + 1) * LDR + j] * R[(i + 1) * LDR + col];
+        a2 += R[(i + 2) * LDR + j] * R[(i + 2) * LDR + col];
+        a3 += R[(i + 3) * LDR + j] * R[(i + 3) * LDR + col];
+      }
+      for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + col];
+      const T d = (a0 + a1) + (a2 + a3);
+      const T f = tau * (R[j * LDR + col] + scl * d);
+      const T fs = f * scl;
+      R[j * LDR + col] -= f;
+      int i2 = j + 1;
+      for (; i2 + 3 < b; i2 += 4) {
+        const T y0 = R[i2 * LDR + col], y1 = R[(i2 + 1) * LDR + col];
+        const T y2 = R[(i2 + 2) * LDR + col], y3 = R[(i2 + 3) * LDR + col];
+        const T z0 = R[i2 * LDR + j], z1 = R[(i2 + 1) * LDR + j];
+        const T z2 = R[(i2 + 2) * LDR + j], z3 = R[(i2 + 3) * LDR + j];
+        R[i2 * LDR + col] = y0 - fs * z0;
+        R[(i2 + 1) * LDR + col] = y1 - fs * z1;
+        R[(i2 + 2) * LDR + col] = y2 - fs * z2;
+        R[(i2 + 3) * LDR + col] = y3 - fs * z3;
+      }
+      for (; i2 < b; i2++) R[i2 * LDR + col] -= fs * R[i2 * LDR + j];
+    }
+    group_bar(1, NC);
+    if (tau != (T)0 && col == j) R[j * LDR + j] = s_hh[1];
+    group_bar(1, NC);
+  }
+  group_bar(1, NC);
+  const int k = s_k;
+  const int r = b - k;
+  // T = R11^{-1} R12, one thread per column
+  for (int cc = col; cc < r; cc += NC) {
+    T *tcol = fb.Tm + (int64_t)cc * k;
+    for (int i = k - 1; i >= 0; i--) {
+      T sacc = R[i * LDR + k + cc];
+      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
+      tcol[i] = sacc / R[i * LDR + i];
+    }
+  }
+  if (col < b) {
+    fb.loc[col] = perm[col];
+    fb.ids[col] = lv.cell_dofs[coff + perm[col]];
+  }
+  if (tid == 0) {
+    fb.k = k;
+    fb.r = r;
+    fb.no = nO;
+  }
+}
+
+template <typename T, int NC>
+static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       double eps, int ring_max, cudaStream_t st, int *err) {
+  constexpr int PR = IdwRows<T>::PR;
+  const size_t tri = (size_t)NC * (NC + 1) * sizeof(T);
+  int gmax = (int)((190u << 10) / tri);
+  if (gmax < 1) gmax = 1;
+  if (G > gmax) G = gmax;
+  if (G * NC > 256) G = 256 / NC;
+  size_t smem = (((size_t)G * tri + 15) & ~(size_t)15) + (((size_t)G * 2 * (PR + 4) * sizeof(T) + 15) & ~(size_t)15) +
+                (size_t)ring_max * sizeof(int64_t) + (size_t)NC * sizeof(int) + 16;
+  cudaFuncSetAttribute(k_idc<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idc<T, NC><<<nbox, G * NC, smem, st>>>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, err);
+  count_launch();
+}
+
 template <typename T, int CPL>
 static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int W,
                        const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
@@ -703,8 +1197,8 @@ static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
   if (wmax < 1) wmax = 1;
   if (W > wmax) W = wmax;
   const int wpc = W;
-  size_t smem = (((size_t)wpc * tri + 15) & ~(size_t)15) + (size_t)((125 + 126 + BM + 4 + 1) & ~1) * sizeof(int) +
-                (size_t)ring_max * sizeof(int64_t) + 16;
+  size_t smem = (((size_t)wpc * tri + 15) & ~(size_t)15) + (size_t)wpc * 2 * (IdwRows<T>::PR + 4) * sizeof(T) +
+                (size_t)((125 + 126 + BM + 4 + 1) & ~1) * sizeof(int) + (size_t)ring_max * sizeof(int64_t) + 16;
   cudaFuncSetAttribute(k_idw<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_idw<T, CPL><<<nbox, wpc * 32, smem, st>>>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max,
                                               err);
@@ -719,11 +1213,12 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   if (nbox == 0) return;
   if (bmax <= 128) {
     // warps per box: enough warps in flight to cover the SMs
-    int W = nbox >= 600 ? 1 : (nbox >= 300 ? 2 : 4);
     const int ring_max = mmax;
-    if (bmax <= 64) launch_idw<T, 2>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max, st, err);
-    else if (bmax <= 96) launch_idw<T, 3>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max, st, err);
-    else launch_idw<T, 4>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max, st, err);
+    // fold groups per box: enough boxes resident at once to finish a phase
+    // in one wave when the phase is large, more groups per box when small
+    const int G = nbox >= 300 ? 2 : 4;
+    if (bmax <= 64) launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+    else launch_idc<T, 128>(lv, boxes, box_list, nbox, G >= 4 ? 2 : 1, P, K, px, proxy_unit, eps, ring_max, st, err);
     return;
   }
   int PR = bmax <= 80 ? 128 : 64;
@@ -992,8 +1487,46 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
 // for the Schur update.
 // ---------------------------------------------------------------------------
 
+// C (m x n) = A (m x K) B (K x n) from shared memory with a 2 x 4 register
+// tile per thread (256 threads as 16 x 16, a 32 x 64 block per pass);
+// A(i,l) = A[i*sai + l*sal], B(l,j) = B[l*sbl + j*sbj]; each result goes
+// to out(i, j, value).
+template <typename T, typename Out>
+__device__ __forceinline__ void smem_gemm(int m, int n, int K, const T *A, int sai, int sal, const T *B, int sbl,
+                                          int sbj, Out out) {
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  for (int i0 = 0; i0 < m; i0 += 32)
+    for (int j0 = 0; j0 < n; j0 += 64) {
+      T acc[2][4];
+#pragma unroll
+      for (int x = 0; x < 2; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++) acc[x][y] = (T)0;
+      const bool rv[2] = {i0 + ti < m, i0 + ti + 16 < m};
+      bool cv[4];
+#pragma unroll
+      for (int y = 0; y < 4; y++) cv[y] = j0 + tj + 16 * y < n;
+      for (int l = 0; l < K; l++) {
+        T a[2], bb[4];
+#pragma unroll
+        for (int x = 0; x < 2; x++) a[x] = rv[x] ? A[(i0 + ti + 16 * x) * sai + l * sal] : (T)0;
+#pragma unroll
+        for (int y = 0; y < 4; y++) bb[y] = cv[y] ? B[l * sbl + (j0 + tj + 16 * y) * sbj] : (T)0;
+#pragma unroll
+        for (int x = 0; x < 2; x++)
+#pragma unroll
+          for (int y = 0; y < 4; y++) acc[x][y] += a[x] * bb[y];
+      }
+#pragma unroll
+      for (int x = 0; x < 2; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++)
+          if (rv[x] && cv[y]) out(i0 + ti + 16 * x, j0 + tj + 16 * y, acc[x][y]);
+    }
+}
+
 template <typename T> struct ElimChunk;
-template <> struct ElimChunk<float> { static constexpr int CH = 64; };
+template <> struct ElimChunk<float> { static constexpr int CH = 32; };
 template <> struct ElimChunk<double> { static constexpr int CH = 32; };
 
 template <typename T>
@@ -1015,6 +1548,8 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nact[27], s_nn;
   __shared__ int64_t s_off_in[27], s_off_out[27];
   __shared__ int s_ld_in[27];
+  __shared__ int64_t s_rb[ElimChunk<T>::CH], s_cb[ElimChunk<T>::CH];
+  __shared__ int s_rl[ElimChunk<T>::CH];
   FBox<T> &fb = boxes[box_list[blockIdx.x]];
   const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1095,29 +1630,33 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     Ab[pp + qq * ldb] = Aii[sloc[pp] + (int64_t)sloc[qq] * b];
   }
   __syncthreads();
-  // X_RS = A_RS - T^T A_SS,  X_SR = A_SR - A_SS T
+  // X_RS = A_RS - T^T A_SS,  X_SR = A_SR - A_SS T,  then
+  // X_RR = A_RR - T^T A_SR - X_RS T (all as tiled shared-memory products)
   for (int e = tid; e < r * k; e += NT) {
     int ri = e % r, s2 = e / r;
-    T acc = Ab[(k + ri) + s2 * ldb];
-    for (int s1 = 0; s1 < k; s1++) acc -= Ts[s1 + ri * k] * Ab[s1 + s2 * ldb];
-    XRS[ri + s2 * r] = acc;
+    XRS[ri + s2 * r] = Ab[(k + ri) + s2 * ldb];
   }
   for (int e = tid; e < r * k; e += NT) {
     int s2 = e % k, ri = e / k;
-    T acc = Ab[s2 + (k + ri) * ldb];
-    for (int s1 = 0; s1 < k; s1++) acc -= Ab[s2 + s1 * ldb] * Ts[s1 + ri * k];
-    XSR[s2 + ri * k] = acc;
+    XSR[s2 + ri * k] = Ab[s2 + (k + ri) * ldb];
   }
-  __syncthreads();
-  // X_RR = A_RR - T^T A_SR - X_RS T
   for (int e = tid; e < r * r; e += NT) {
     int ri = e % r, rj = e / r;
-    T acc = Ab[(k + ri) + (k + rj) * ldb];
-    for (int s1 = 0; s1 < k; s1++) {
-      acc -= Ts[s1 + ri * k] * Ab[s1 + (k + rj) * ldb];
-      acc -= XRS[ri + s1 * r] * Ts[s1 + rj * k];
-    }
-    LU[ri * ldl + rj] = acc;
+    LU[ri * ldl + rj] = Ab[(k + ri) + (k + rj) * ldb];
+  }
+  __syncthreads();
+  {
+    T *xrs = XRS, *xsr = XSR, *lu = LU;
+    const int rr = r, kk = k, ll = ldl;
+    smem_gemm<T>(r, k, k, Ts, k, 1, Ab, 1, ldb, [&](int ri, int s2, T v) { xrs[ri + s2 * rr] -= v; });
+    smem_gemm<T>(k, r, k, Ab, 1, ldb, Ts, 1, k, [&](int s2, int ri, T v) { xsr[s2 + ri * kk] -= v; });
+    smem_gemm<T>(r, r, k, Ts, k, 1, Ab + (size_t)k * ldb, 1, ldb, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
+  }
+  __syncthreads();
+  {
+    T *lu = LU;
+    const int ll = ldl;
+    smem_gemm<T>(r, r, k, XRS, 1, r, Ts, 1, k, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
   }
   __syncthreads();
   // LU with partial pivoting by warp 0 (largest |entry|, ties to the lowest row)
@@ -1164,9 +1703,31 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       const T d = LU[j * ldl + j];
       for (int i = j + 1 + lane; i < r; i += 32) LU[i * ldl + j] /= d;
       __syncwarp();
-      for (int i = j + 1; i < r; i++) {
-        const T l = LU[i * ldl + j];
-        for (int cc = j + 1 + lane; cc < r; cc += 32) LU[i * ldl + cc] -= l * LU[j * ldl + cc];
+      // rank-1 update: this lane's columns of the pivot row stay in registers,
+      // rows are taken four at a time (loads before stores)
+      const int c0 = j + 1 + lane, c1 = c0 + 32, c2 = c0 + 64, c3 = c0 + 96;
+      const T p0 = c0 < r ? LU[j * ldl + c0] : (T)0, p1 = c1 < r ? LU[j * ldl + c1] : (T)0;
+      const T p2 = c2 < r ? LU[j * ldl + c2] : (T)0, p3 = c3 < r ? LU[j * ldl + c3] : (T)0;
+      for (int i = j + 1; i < r; i += 4) {
+        T l[4], x[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int ii = i + u < r ? i + u : j;  // j: harmless dummy row (never stored)
+          l[u] = LU[ii * ldl + j];
+          x[u][0] = c0 < r ? LU[ii * ldl + c0] : (T)0;
+          x[u][1] = c1 < r ? LU[ii * ldl + c1] : (T)0;
+          x[u][2] = c2 < r ? LU[ii * ldl + c2] : (T)0;
+          x[u][3] = c3 < r ? LU[ii * ldl + c3] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (i + u >= r) break;
+          const int ii = i + u;
+          if (c0 < r) LU[ii * ldl + c0] = x[u][0] - l[u] * p0;
+          if (c1 < r) LU[ii * ldl + c1] = x[u][1] - l[u] * p1;
+          if (c2 < r) LU[ii * ldl + c2] = x[u][2] - l[u] * p2;
+          if (c3 < r) LU[ii * ldl + c3] = x[u][3] - l[u] * p3;
+        }
       }
       __syncwarp();
     }
@@ -1177,18 +1738,35 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
   __syncthreads();
   // X_RR^{-1} = U^{-1} L^{-1} P: column cc is U^{-1} L^{-1} e_{pinv[cc]}
+  // (four partial sums per dot product to shorten the dependence chains)
   for (int cc = tid; cc < r; cc += NT) {
     T *x = Xi + (size_t)cc * ldx;
     const int i0 = spinv[cc];
     for (int i = 0; i < r; i++) {
-      T sacc = i == i0 ? (T)1 : (T)0;
-      for (int l = 0; l < i; l++) sacc -= LU[i * ldl + l] * x[l];
-      x[i] = sacc;
+      const T *Li = LU + i * ldl;
+      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+      int l = i0;  // x[l] = 0 for l < i0
+      for (; l + 3 < i; l += 4) {
+        s0 += Li[l] * x[l];
+        s1 += Li[l + 1] * x[l + 1];
+        s2 += Li[l + 2] * x[l + 2];
+        s3 += Li[l + 3] * x[l + 3];
+      }
+      for (; l < i; l++) s0 += Li[l] * x[l];
+      x[i] = (i == i0 ? (T)1 : (T)0) - ((s0 + s1) + (s2 + s3));
     }
     for (int i = r - 1; i >= 0; i--) {
-      T sacc = x[i];
-      for (int l = i + 1; l < r; l++) sacc -= LU[i * ldl + l] * x[l];
-      x[i] = sacc / LU[i * ldl + i];
+      const T *Ui = LU + i * ldl;
+      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+      int l = i + 1;
+      for (; l + 3 < r; l += 4) {
+        s0 += Ui[l] * x[l];
+        s1 += Ui[l + 1] * x[l + 1];
+        s2 += Ui[l + 2] * x[l + 2];
+        s3 += Ui[l + 3] * x[l + 3];
+      }
+      for (; l < r; l++) s0 += Ui[l] * x[l];
+      x[i] = (x[i] - ((s0 + s1) + (s2 + s3))) / Ui[i];
     }
   }
   __syncthreads();
@@ -1196,57 +1774,82 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   T *Xrj_out = scratch + (int64_t)blockIdx.x * sstride + (int64_t)nj * r;  // r x nj, for the Schur update
   for (int a0 = 0; a0 < nj; a0 += CH) {
     const int na = min(CH, nj - a0);
-    // raw rows A(J_a, B) and columns A(B, J_a) of the chunk (S rows come from X_SR / X_RS)
-    for (int e = tid; e < na * b; e += NT) {
-      int al = e % na, pp = e / na, a = a0 + al;
-      if (a < k) {
-        if (pp >= k) rawJ[al + pp * (CH + 1)] = XSR[a + (pp - k) * k];
-      } else {
-        int code = fb.Jnb[a], la = fb.Jloc[a];
-        rawJ[al + pp * (CH + 1)] = lv.pool[s_off_in[code] + la + (int64_t)sloc[pp] * s_ld_in[code]];
+    // raw rows A(J_a, B) and columns A(B, J_a) of the chunk (S rows come from
+    // X_SR / X_RS); the row / column bases of the chunk are resolved first so
+    // the element loads below are independent of one another
+    if (tid < na) {
+      const int a = a0 + tid;
+      const int code = fb.Jnb[a], la = fb.Jloc[a];
+      s_rb[tid] = s_off_in[code] + la;
+      s_rl[tid] = s_ld_in[code];
+      s_cb[tid] = s_off_out[code] + (int64_t)la * b;
+    }
+    __syncthreads();
+    for (int e0 = tid; e0 < na * b; e0 += 4 * NT) {
+      T val[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * NT;
+        val[u] = (T)0;
+        if (e < na * b) {
+          const int al = e % na, pp = e / na, a = a0 + al;
+          if (a < k) val[u] = pp >= k ? XSR[a + (pp - k) * k] : (T)0;
+          else val[u] = lv.pool[s_rb[al] + (int64_t)sloc[pp] * s_rl[al]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * NT;
+        if (e < na * b) rawJ[(e % na) + (e / na) * (CH + 1)] = val[u];
       }
     }
-    for (int e = tid; e < na * b; e += NT) {
-      int pp = e % b, al = e / b, a = a0 + al;
-      if (a < k) {
-        if (pp >= k) rawC[pp + al * ldb] = XRS[(pp - k) + a * r];
-      } else {
-        int code = fb.Jnb[a], la = fb.Jloc[a];
-        rawC[pp + al * ldb] = lv.pool[s_off_out[code] + (int64_t)la * b + sloc[pp]];
+    for (int e0 = tid; e0 < na * b; e0 += 4 * NT) {
+      T val[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * NT;
+        val[u] = (T)0;
+        if (e < na * b) {
+          const int pp = e % b, al = e / b, a = a0 + al;
+          if (a < k) val[u] = pp >= k ? XRS[(pp - k) + a * r] : (T)0;
+          else val[u] = lv.pool[s_cb[al] + sloc[pp]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * NT;
+        if (e < na * b) rawC[(e % b) + (e / b) * ldb] = val[u];
       }
     }
     __syncthreads();
     // in place: X_JR = A_JR - A_JS T (rows a >= k);  X_RJ = A_RJ - T^T A_SJ
-    for (int e = tid; e < na * r; e += NT) {
-      int al = e % na, ri = e / na;
-      if (a0 + al >= k) {
-        T acc = rawJ[al + (k + ri) * (CH + 1)];
-        for (int s1 = 0; s1 < k; s1++) acc -= rawJ[al + s1 * (CH + 1)] * Ts[s1 + ri * k];
-        rawJ[al + (k + ri) * (CH + 1)] = acc;
-      }
-    }
-    for (int e = tid; e < na * r; e += NT) {
-      int ri = e % r, al = e / r;
-      T acc = rawC[(k + ri) + al * ldb];
-      if (a0 + al >= k) {
-        for (int s1 = 0; s1 < k; s1++) acc -= Ts[s1 + ri * k] * rawC[s1 + al * ldb];
-        rawC[(k + ri) + al * ldb] = acc;
-      }
-      Xrj_out[ri + (int64_t)(a0 + al) * r] = acc;
+    {
+      const int ldj = CH + 1;
+      T *rJ = rawJ;
+      T *rC = rawC;
+      const int kk = k, aa0 = a0;
+      smem_gemm<T>(na, r, k, rawJ, 1, ldj, Ts, 1, k, [&](int al, int ri, T v) {
+        if (aa0 + al >= kk) rJ[al + (kk + ri) * ldj] -= v;
+      });
+      smem_gemm<T>(r, na, k, Ts, k, 1, rawC, 1, ldb, [&](int ri, int al, T v) {
+        if (aa0 + al >= kk) rC[(kk + ri) + al * ldb] -= v;
+      });
     }
     __syncthreads();
-    // E chunk = X_JR chunk * X_RR^{-1};  G chunk = X_RR^{-1} * X_RJ chunk
-    for (int e = tid; e < na * r; e += NT) {
-      int al = e % na, ri = e / na;
-      T acc = (T)0;
-      for (int l = 0; l < r; l++) acc += rawJ[al + (k + l) * (CH + 1)] * Xi[l + (size_t)ri * ldx];
-      fb.E[(a0 + al) + (int64_t)ri * nj] = acc;
-    }
     for (int e = tid; e < na * r; e += NT) {
       int ri = e % r, al = e / r;
-      T acc = (T)0;
-      for (int l = 0; l < r; l++) acc += Xi[ri + (size_t)l * ldx] * rawC[(k + l) + al * ldb];
-      fb.G[ri + (int64_t)(a0 + al) * r] = acc;
+      Xrj_out[ri + (int64_t)(a0 + al) * r] = rawC[(k + ri) + al * ldb];
+    }
+    // E chunk = X_JR chunk * X_RR^{-1};  G chunk = X_RR^{-1} * X_RJ chunk
+    {
+      T *Eo = fb.E, *Go = fb.G;
+      const int njj = nj, rr = r, aa0 = a0;
+      smem_gemm<T>(na, r, r, rawJ + (size_t)k * (CH + 1), 1, CH + 1, Xi, 1, ldx, [&](int al, int ri, T v) {
+        Eo[(aa0 + al) + (int64_t)ri * njj] = v;
+      });
+      smem_gemm<T>(r, na, r, Xi, 1, ldx, rawC + k, 1, ldb, [&](int ri, int al, T v) {
+        Go[ri + (int64_t)(aa0 + al) * rr] = v;
+      });
     }
     __syncthreads();
   }
@@ -1274,7 +1877,8 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
     // worst case over k + r = b of the shared-memory form
     size_t worst = 0;
     for (int r = 0; r <= bmax; r++) worst = std::max(worst, elim2_smem<T>(bmax, bmax - r, r));
-    if (worst <= (size_t)(220 << 10)) {
+    // the warp LU keeps at most four pivot-row entries per lane: r <= 128
+    if (worst <= (size_t)(220 << 10) && bmax <= 128) {
       cudaFuncSetAttribute(k_elim2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)worst);
       k_elim2<T><<<nbox, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, err);
       count_launch();
