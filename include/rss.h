@@ -62,7 +62,13 @@ typedef struct {
   void *stream;        /* cudaStream_t; NULL = legacy default stream */
   int profile;         /* 1: time every kernel launch with CUDA events on the
                           stream (see rss_profile) */
+  int flags;           /* RSS_FLAG_* bits; 0 for the defaults */
 } rss_options;
+
+/* Route every box through the large-box kernels (global-memory workspaces),
+ * which otherwise run only when a box is too large for shared memory.  The
+ * result is the same factorization; used to test that path on small cases. */
+#define RSS_FLAG_LARGE_BOX_PATH 1
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;

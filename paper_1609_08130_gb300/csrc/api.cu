@@ -520,6 +520,7 @@ template <typename T> struct Factor : FactorBase {
   KernelParams K{};
   ProxyParams px{};
   double eps = 0;
+  int flags = 0;
   cudaStream_t st = nullptr;
   int64_t n = 0;
   int dim = 2;
@@ -864,24 +865,25 @@ template <typename T> static void run_factor(Factor<T> &F) {
       q = q2;
     }
     // scratch
+    const bool large = (F.flags & RSS_FLAG_LARGE_BOX_PATH) != 0;
     int PR = H.bmax <= 80 ? 128 : 64;
     int64_t idb = id_region_bytes<T>(H.bmax, PR);
-    bool id_smem = idb <= 200 * 1024;
+    bool id_smem = idb <= 200 * 1024 && !large;
     DBuf gid, gel;
     int64_t id_stride = (idb + sizeof(T) - 1) / sizeof(T) + 32;
     if (!id_smem) gid.alloc((size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st);
-    int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32;
+    int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32 + elim_ws_elems<T>(H.bmax);
     gel.alloc((size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st);
     F.prof.host(KC_HOST_LEVEL, now_ms() - th0);
     for (auto &p : ph) {
       const int *bl = ptr<int>(d_list) + p.first;
       int pi = F.prof.begin(KC_ID, st, base + p.first, p.second);
-      launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, H.bmax, ring_max, F.P, F.K, F.px, ptr<double>(F.d_proxy), F.eps,
-                   ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
+      launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ring_max, F.P, F.K, F.px,
+                   ptr<double>(F.d_proxy), F.eps, ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
       check_launch("id");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_ELIM, st, base + p.first, p.second);
-      launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, H.bmax, ptr<T>(gel), el_stride, st,
+      launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ptr<T>(gel), el_stride, st,
                      ptr<int>(F.d_err));
       check_launch("elim");
       F.prof.end(pi, st);
@@ -889,7 +891,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
       check_launch("schur");
       F.prof.end(pi, st);
-      F.phases.push_back({base + p.first, p.second, H.bmax, njmax_lvl});
+      F.phases.push_back({base + p.first, p.second, H.bmax, large ? -njmax_lvl : njmax_lvl});
     }
     // ranks of this level -> active DOFs of the next
     CK(cudaMemcpyAsync(F.h_boxes.data() + base, ptr<FBox<T>>(F.d_boxes) + base, sizeof(FBox<T>) * nb,
@@ -1385,6 +1387,7 @@ rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, 
       F->px.np = o.n_proxy > 0 ? o.n_proxy : (dim == 2 ? 64 : 512);
       F->px.radius = o.proxy_radius > 0 ? o.proxy_radius : 2.5;
       F->eps = eps;
+      F->flags = o.flags;
       run_factor(*F);
     };
     if (o.prec == RSS_FP64) {

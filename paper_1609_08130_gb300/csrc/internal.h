@@ -96,6 +96,7 @@ template <typename T>
 void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v,
                 int nrhs, T *work, cudaStream_t st);
 template <typename T> int64_t id_region_bytes(int b, int PR);
+template <typename T> int64_t elim_ws_elems(int bmax);
 template <typename T>
 void launch_permute(int dir, const int64_t *perm, const double *in, T *out_or_in, double *out,
                     int64_t n, int nrhs, cudaStream_t st);

@@ -1211,7 +1211,9 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
                T *gscratch, int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err) {
   (void)mmax;
   if (nbox == 0) return;
-  if (bmax <= 128) {
+  const bool force_general = bmax < 0;  // large-box path requested
+  if (force_general) bmax = -bmax;
+  if (bmax <= 128 && !force_general) {
     // warps per box: enough warps in flight to cover the SMs
     const int ring_max = mmax;
     // fold groups per box: enough boxes resident at once to finish a phase
@@ -1240,7 +1242,7 @@ template int64_t id_region_bytes<double>(int, int);
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
-                                             int64_t sstride, int rmax, int *err) {
+                                             int64_t sstride, int64_t ws_off, int use_smem, int *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nn;
   __shared__ int64_t s_off_in[27], s_off_out[27];
@@ -1253,8 +1255,9 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
   const int ncode3 = dim == 3 ? 27 : 9;
   const int center = code3(0, 0, 0, dim);
 
-  // shared: Ts (k x r, ld k), LU (r x r, ld r+1), loc (b ints), piv (r ints)
-  T *Ts = reinterpret_cast<T *>(smem_raw);
+  // Ts (k x r, ld k), LU (r x r, ld r+1), loc (b ints), piv (r ints): in
+  // shared memory, or for large boxes in this box's global workspace
+  T *Ts = use_smem ? reinterpret_cast<T *>(smem_raw) : scratch + (int64_t)blockIdx.x * sstride + ws_off;
   const int ldl = r + 1;
   T *LU = Ts + (int64_t)k * r;
   int *sloc = reinterpret_cast<int *>(LU + (int64_t)r * ldl);
@@ -1869,11 +1872,20 @@ template <typename T> int64_t elim_smem_bytes(int b, int k, int r) {
 template int64_t elim_smem_bytes<float>(int, int, int);
 template int64_t elim_smem_bytes<double>(int, int, int);
 
+// Elements of T the large-box elimination needs per box beyond X_JR / X_RJ.
+template <typename T> int64_t elim_ws_elems(int bmax) {
+  return (int64_t)bmax * bmax / 4 + (int64_t)bmax * (bmax + 1) + 2 * (int64_t)bmax + 64;
+}
+template int64_t elim_ws_elems<float>(int);
+template int64_t elim_ws_elems<double>(int);
+
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
                  int64_t scratch_stride, cudaStream_t st, int *err) {
   if (nbox == 0) return;
-  {
+  const bool force_general = bmax < 0;  // large-box path requested
+  if (force_general) bmax = -bmax;
+  if (!force_general) {
     // worst case over k + r = b of the shared-memory form
     size_t worst = 0;
     for (int r = 0; r <= bmax; r++) worst = std::max(worst, elim2_smem<T>(bmax, bmax - r, r));
@@ -1888,8 +1900,13 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   // worst case over k + r = b: k r <= b^2/4, r <= b
   size_t smem = (size_t)bmax * bmax / 4 * sizeof(T) + (size_t)bmax * (bmax + 1) * sizeof(T) +
                 (size_t)2 * bmax * sizeof(int) + 64;
-  cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_elim<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, scratch, scratch_stride, bmax, err); count_launch();
+  const bool use_smem = smem <= (size_t)(220 << 10) && !force_general;
+  // the global workspace sits after the X_JR / X_RJ scratch of the box
+  const int64_t ws_off = scratch_stride - elim_ws_elems<T>(bmax);
+  if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_elim<T><<<nbox, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
+                                                    use_smem ? 1 : 0, err);
+  count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -2149,8 +2166,12 @@ __device__ void warp_lu_solve(const T *LU, const int *piv, int r, T *x, T *tmp, 
   __syncwarp();
 }
 
+// vJ(a, c): the J entries, from the shared copy or, for boxes whose J does
+// not fit in shared memory, straight from the vector
+#define VJ(a, c) (jsh ? vJ[(a) * nrhs + (c)] : v[fb.J[a] * nrhs + (c)])
+
 template <typename T>
-__global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, int first, T *v, int nrhs) {
+__global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, int first, T *v, int nrhs, int jsh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FBox<T> &fb = boxes[first + blockIdx.x];
   const int k = fb.k, r = fb.r, nj = fb.nj;
@@ -2159,12 +2180,12 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
   // vectors in shared memory, layout [i * nrhs + c]
   T *vS = reinterpret_cast<T *>(smem_raw);   // k
   T *vR = vS + (size_t)k * nrhs;              // r
-  T *vJ = vR + (size_t)r * nrhs;              // nj
-  T *tmp = vJ + (size_t)nj * nrhs;            // r
+  T *tmp = vR + (size_t)r * nrhs;             // r
+  T *vJ = tmp + (size_t)r * nrhs;             // nj (when jsh)
   const int64_t *S = fb.ids, *Rr = fb.ids + k;
   for (int e = tid; e < k * nrhs; e += NT) vS[e] = v[S[e / nrhs] * nrhs + e % nrhs];
   for (int e = tid; e < r * nrhs; e += NT) vR[e] = v[Rr[e / nrhs] * nrhs + e % nrhs];
-  if (mode == SWEEP_SOLVE_BWD)
+  if (mode == SWEEP_SOLVE_BWD && jsh)
     for (int e = tid; e < nj * nrhs; e += NT) vJ[e] = v[fb.J[e / nrhs] * nrhs + e % nrhs];
   __syncthreads();
   if (mode == SWEEP_SOLVE_FWD) {
@@ -2195,7 +2216,7 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
     for (int e = tid; e < r * nrhs; e += NT) {
       int ri = e % r, c = e / r;
       T acc = (T)0;
-      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * vJ[a * nrhs + c];
+      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * VJ(a, c);
       vR[ri * nrhs + c] -= acc;
     }
     __syncthreads();
@@ -2217,17 +2238,18 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
       v[S[q] * nrhs + c] = vS[q * nrhs + c];
     }
     __syncthreads();
-    // gather v_J (its S part was just updated)
-    for (int e = tid; e < nj * nrhs; e += NT) {
-      int a = e / nrhs, c = e % nrhs;
-      vJ[e] = a < k ? vS[a * nrhs + c] : v[fb.J[a] * nrhs + c];
-    }
+    // gather v_J (its S part was just updated, also in v)
+    if (jsh)
+      for (int e = tid; e < nj * nrhs; e += NT) {
+        int a = e / nrhs, c = e % nrhs;
+        vJ[e] = a < k ? vS[a * nrhs + c] : v[fb.J[a] * nrhs + c];
+      }
     __syncthreads();
     // U^{-1}: v_R += G v_J
     for (int e = tid; e < r * nrhs; e += NT) {
       int ri = e % r, c = e / r;
       T acc = (T)0;
-      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * vJ[a * nrhs + c];
+      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * VJ(a, c);
       vR[ri * nrhs + c] += acc;
     }
     __syncthreads();
@@ -2270,9 +2292,16 @@ template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax, int njmax,
                   cudaStream_t st) {
   if (count == 0) return;
+  const bool force_general = njmax < 0;  // large-box path requested
+  if (force_general) njmax = -njmax;
   size_t smem = ((size_t)3 * bmax + (size_t)njmax) * nrhs * sizeof(T) + 64;
+  int jsh = 1;
+  if (smem > (size_t)(200 << 10) || force_general) {
+    jsh = 0;
+    smem = (size_t)3 * bmax * nrhs * sizeof(T) + 64;
+  }
   cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs); count_launch();
+  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs, jsh); count_launch();
 }
 
 // Top block: solve (mode 0) or multiply (mode 1), one CTA per right-hand side.

@@ -23,6 +23,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", 
 RSS_OK, RSS_EINVAL, RSS_ENOMEM, RSS_ECUDA, RSS_ENUMERIC, RSS_ETIMEOUT, RSS_ENOTCONV = range(7)
 LAPLACE2D_LOG, LAPLACE3D_INV = 0, 1
 FP64, MIXED = 0, 1
+FLAG_LARGE_BOX_PATH = 1
 
 
 def _nvcc():
@@ -59,7 +60,7 @@ class _Kernel(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("n_proxy", C.c_int), ("proxy_radius", C.c_double),
-                ("use_graphs", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
+                ("use_graphs", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int), ("flags", C.c_int)]
 
 
 _lib = None
@@ -183,14 +184,14 @@ class Factorization:
 
     def __init__(self, pts, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
                  weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
-                 profile: bool = False):
+                 profile: bool = False, flags: int = 0):
         torch = _torch()
         pts = _dev_f64(pts)
         self.n, self.dim = pts.shape
         self.prec = prec
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
-        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile))
+        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags))
         h = C.c_void_p()
         _check(lib().rss_factor(C.c_void_p(pts.data_ptr()), self.n, self.dim, _Kernel(kind, diag, weight),
                                 eps, leaf, C.byref(opts), C.byref(h)))

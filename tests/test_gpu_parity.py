@@ -193,3 +193,40 @@ def test_refined_solve_reaches_tolerance(pkg, case, prec):
     true_rel = max(np.linalg.norm(r[c]) / np.linalg.norm(b[c]) for c in range(4))
     assert rel <= 1e-10 and true_rel <= 2e-10, (rel, true_rel, iters)
     assert iters <= 10
+
+
+@pytest.mark.parametrize("case", ["grid2d_4096", "grid3d"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_large_box_path_matches_oracle(pkg, case, prec):
+    """The kernels used for boxes too large for shared memory (3D upper
+    levels), forced on every box of small problems, against the oracle."""
+    mk, kind, eps, leaf = FACTOR_CASES[case]
+    pts = mk()
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), kind, eps, leaf=leaf, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED,
+                          flags=pkg.rss.FLAG_LARGE_BOX_PATH)
+    of = _oracle_factor(pts, kind, eps, leaf)
+    x = inputs.rhs(12, n, 2)
+    Fo = of.apply(x)
+    Fg = f.apply(_cuda(x)).cpu().numpy()
+    assert np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo) <= 10 * eps
+    So = of.solve(x)
+    Sg = f.solve(_cuda(x)).cpu().numpy()
+    assert np.linalg.norm(Sg - So) / np.linalg.norm(So) <= 10 * eps
+
+
+def test_3d_grid32_refined_full_size(pkg):
+    """3D Laplace on the 32^3 grid (N = 32768), eps = 1e-3 FP32 factor as the
+    preconditioner of the FP64 refinement: the residual of the refined
+    solution, evaluated by the oracle's direct sum on 64 sampled rows, is at
+    the 1e-10 level."""
+    pts = inputs.grid_points(32, 3)
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), 1, 1e-3, leaf=64, prec=pkg.MIXED)
+    b = inputs.rhs(1, n, 2)
+    x, iters, rel = f.solve_refined(_cuda(b), tol=1e-10, maxit=20)
+    x = x.cpu().numpy()
+    rows = (inputs.splitmix64(17, 64) % np.uint64(n)).astype(np.int64)
+    r = b[:, rows] - oracle.matvec(pts, 1, x, rows=rows)
+    assert rel <= 1e-10
+    assert np.abs(r).max() <= 1e-9 * np.abs(b).max()
