@@ -116,6 +116,18 @@ rss_status rss_tree_query(const rss_tree *tree, int what, void *buf, size_t *nby
 rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, double eps,
                       int leaf_size, const rss_options *opts, rss_factorization **out);
 
+/* rss_factor_batched -- factor nprob independent problems into one handle
+ * (the matrix is block diagonal, one block per problem; problem p's weight is
+ * kernel.weight or 1/n[p]).  Every (tree depth, colour) phase is one launch
+ * over the boxes of all problems (the boxes of one colour are independent
+ * within a problem and across problems).
+ *   pts: HOST array of nprob DEVICE pointers (n[p]*dim doubles each);
+ *   n: HOST array of nprob sizes.  Vectors passed to rss_apply / rss_solve /
+ *   rss_solve_refined on the handle are the problems' vectors concatenated in
+ *   problem order (sum n[p] rows).  Errors as rss_factor. */
+rss_status rss_factor_batched(int nprob, const double *const *pts, const int64_t *n, int dim, rss_kernel kernel,
+                              double eps, int leaf_size, const rss_options *opts, rss_factorization **out);
+
 /* rss_apply -- y = F x (Eq. 3.10).  x, y: device, n x nrhs column-major,
  * original point order; may not alias.  nrhs >= 1. */
 rss_status rss_apply(const rss_factorization *f, const double *x, double *y, int nrhs);

@@ -516,7 +516,11 @@ struct FactorBase {
 };
 
 template <typename T> struct Factor : FactorBase {
-  HTree tree;
+  // one or more independent problems, DOFs concatenated in problem order
+  std::vector<HTree> trees;
+  std::vector<int64_t> pdof;  // DOF offset of each problem (nprob + 1)
+  std::vector<double> pw;     // weight w of each problem
+  int nprob = 1, maxdepth = 0;
   KernelParams K{};
   ProxyParams px{};
   double eps = 0;
@@ -524,24 +528,29 @@ template <typename T> struct Factor : FactorBase {
   cudaStream_t st = nullptr;
   int64_t n = 0;
   int dim = 2;
-  DBuf d_x, d_perm, d_cell, d_off, d_err, d_proxy;
+  DBuf d_x, d_perm, d_cell, d_off, d_err, d_proxy, d_wdof;
   Points P{};
   std::vector<std::unique_ptr<DBuf>> store;  // factor storage chunks
   int64_t factor_bytes = 0;
   DBuf d_boxes;
   std::vector<FBox<T>> h_boxes;
   std::vector<Phase> phases;
-  int ntop = 0;
-  DBuf d_top, d_topLU, d_toppiv;
+  // top blocks, one per problem
+  int ntop = 0;  // total over problems
+  std::vector<int> h_tn;
+  std::vector<int64_t> h_toff, h_loff;
+  DBuf d_top, d_topLU, d_toppiv, d_tn, d_toff, d_loff;
   mutable DBuf d_work, d_topwork;
   mutable int work_nrhs = 0;
-  // FP64 residual operator: FFT convolution when the points are the cell
-  // centres of a regular grid, direct summation otherwise
+  // FP64 residual operator: FFT convolution when a single problem's points
+  // are the cell centres of a regular grid, direct summation otherwise
   int grid_side = 0;
   std::vector<int64_t> grid_index;  // caller order
   mutable GridOp G;
   mutable DBuf g_gidx, g_C, g_X, g_tw;
   mutable bool grid_ready = false;
+  int mv_ntile = 0;
+  DBuf d_mv_ts, d_mv_te, d_mv_sb, d_mv_se;
 
   void *alloc_store(size_t bytes) {
     store.emplace_back(new DBuf());
@@ -617,7 +626,9 @@ static int check_err(DBuf &d_err, cudaStream_t st) {
 // Points exactly at the cell centres ((i + 1/2) / s) of an s^dim grid, s a
 // power of two, each cell used once: record every point's grid index.
 template <typename T> static void detect_grid(Factor<T> &F) {
-  const HTree &T_ = F.tree;
+  F.grid_side = 0;
+  if (F.nprob != 1) return;
+  const HTree &T_ = F.trees[0];
   const int dim = T_.dim;
   const int64_t n = T_.n;
   F.grid_side = 0;
@@ -645,32 +656,92 @@ template <typename T> static void detect_grid(Factor<T> &F) {
   F.grid_index.swap(gi);
 }
 
+// Merge the depth-t cells of several problems into one level: cell ids,
+// DOF ids (problem offset), neighbour tables, pair-block offsets and boxes
+// are shifted; cells of different problems are never neighbours.  Boxes are
+// ordered colour-major over all problems (each problem keeps its own order
+// within a colour).
+static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vector<int> &box_prob, int prob) {
+  const int cbase = H.ncell;
+  const int64_t dbase = H.cell_dofs.size(), pbase = H.pool_elems;
+  if (H.cell_dof_off.empty()) H.cell_dof_off.push_back(0);
+  for (int c = 0; c < Hp.ncell; c++) {
+    H.cell_b.push_back(Hp.cell_b[c]);
+    H.cell_dof_off.push_back(dbase + Hp.cell_dof_off[c + 1]);
+    for (int d = 0; d < 3; d++) H.cell_coord.push_back(Hp.cell_coord[3 * c + d]);
+    for (int o = 0; o < Hp.NB; o++) {
+      int nb = Hp.cell_nbr[(size_t)c * Hp.NB + o];
+      H.cell_nbr.push_back(nb >= 0 ? nb + cbase : -1);
+      int64_t po = Hp.pair_off[(size_t)c * Hp.NB + o];
+      H.pair_off.push_back(po >= 0 ? po + pbase : -1);
+    }
+  }
+  for (int64_t g : Hp.cell_dofs) H.cell_dofs.push_back(g + dof_off);
+  for (size_t q = 0; q < Hp.box_cell.size(); q++) {
+    H.box_cell.push_back(Hp.box_cell[q] + cbase);
+    H.box_node.push_back(Hp.box_node[q]);
+    H.box_colour.push_back(Hp.box_colour[q]);
+    box_prob.push_back(prob);
+  }
+  H.ncell += Hp.ncell;
+  H.pool_elems += Hp.pool_elems;
+  H.bmax = std::max(H.bmax, Hp.bmax);
+}
+
 template <typename T> static void run_factor(Factor<T> &F) {
-  HTree &T_ = F.tree;
-  const int dim = T_.dim;
-  const int64_t n = T_.n;
+  const int dim = F.dim;
+  const int64_t n = F.n;
+  const int np = F.nprob;
   cudaStream_t st = F.st;
-  // points
-  upload(F.d_x, T_.x, st);
-  upload(F.d_perm, T_.perm, st);
+  // points: tree order of every problem, concatenated
   {
-    int fine = T_.maxdepth;
-    double D = ldexp(1.0, -fine);
+    std::vector<double> x((size_t)std::max<int64_t>(n, 1) * dim);
+    std::vector<int64_t> perm(std::max<int64_t>(n, 1));
+    std::vector<double> wd;
     std::vector<int> cell((size_t)3 * std::max<int64_t>(n, 1), 0);
     std::vector<float> off((size_t)3 * std::max<int64_t>(n, 1), 0.f);
-    for (int64_t g = 0; g < n; g++)
-      for (int d = 0; d < dim; d++) {
-        int64_t c = cell_at(T_.x[g * dim + d], fine);
-        cell[3 * g + d] = (int)c;
-        off[3 * g + d] = (float)(T_.x[g * dim + d] - (double)c * D);
+    const double D = ldexp(1.0, -20);
+    if (np > 1) wd.resize(std::max<int64_t>(n, 1));
+    for (int p = 0; p < np; p++) {
+      const HTree &Tp = F.trees[p];
+      const int64_t o = F.pdof[p];
+      for (int64_t g = 0; g < Tp.n; g++) {
+        perm[o + g] = o + Tp.perm[g];
+        for (int d = 0; d < dim; d++) {
+          double v = Tp.x[g * dim + d];
+          x[(o + g) * dim + d] = v;
+          int64_t c = cell_at(v, 20);
+          cell[3 * (o + g) + d] = (int)c;
+          off[3 * (o + g) + d] = (float)(v - (double)c * D);
+        }
+        if (np > 1) wd[o + g] = F.pw[p];
       }
+    }
+    upload(F.d_x, x, st);
+    upload(F.d_perm, perm, st);
     upload(F.d_cell, cell, st);
     upload(F.d_off, off, st);
+    if (np > 1) upload(F.d_wdof, wd, st);
     F.P.x = ptr<double>(F.d_x);
     F.P.cell = ptr<int>(F.d_cell);
     F.P.off = ptr<float>(F.d_off);
     F.P.D = (float)D;
     F.P.dim = dim;
+    F.P.wdof = np > 1 ? ptr<double>(F.d_wdof) : nullptr;
+    // direct-sum residual tiles: 256 targets of one problem against its sources
+    std::vector<int64_t> ts, te, sb, se;
+    for (int p = 0; p < np; p++)
+      for (int64_t t0 = F.pdof[p]; t0 < F.pdof[p + 1]; t0 += 256) {
+        ts.push_back(t0);
+        te.push_back(std::min(t0 + 256, F.pdof[p + 1]));
+        sb.push_back(F.pdof[p]);
+        se.push_back(F.pdof[p + 1]);
+      }
+    F.mv_ntile = (int)ts.size();
+    upload(F.d_mv_ts, ts, st);
+    upload(F.d_mv_te, te, st);
+    upload(F.d_mv_sb, sb, st);
+    upload(F.d_mv_se, se, st);
   }
   F.d_err.alloc(sizeof(int), st);
   CK(cudaMemsetAsync(F.d_err.p, 0, sizeof(int), st));
@@ -696,14 +767,22 @@ template <typename T> static void run_factor(Factor<T> &F) {
     upload(F.d_proxy, u, st);
   }
 
+  F.maxdepth = 0;
   int nbox_total = 0;
-  for (int t = 2; t <= T_.maxdepth; t++) nbox_total += (int)T_.level[t].size();
+  for (const HTree &Tp : F.trees) {
+    F.maxdepth = std::max(F.maxdepth, Tp.maxdepth);
+    for (int t = 2; t <= Tp.maxdepth; t++) nbox_total += (int)Tp.level[t].size();
+  }
   F.d_boxes.alloc(sizeof(FBox<T>) * std::max(nbox_total, 1), st);
   F.h_boxes.clear();
   F.phases.clear();
 
-  std::vector<int64_t> active(n);
-  for (int64_t g = 0; g < n; g++) active[g] = g;
+  // active DOFs of every problem (local tree-order ids, ascending)
+  std::vector<std::vector<int64_t>> active(np);
+  for (int p = 0; p < np; p++) {
+    active[p].resize(F.trees[p].n);
+    for (int64_t g = 0; g < F.trees[p].n; g++) active[p][g] = g;
+  }
   DBuf d_dof_cell[2], d_dof_loc[2];
   std::unique_ptr<DLevel<T>> prevD;
   HLevel prevH;
@@ -739,9 +818,42 @@ template <typename T> static void run_factor(Factor<T> &F) {
     check_launch("assemble");
   };
 
-  for (int t = T_.maxdepth; t >= 2; t--) {
+  for (int t = F.maxdepth; t >= 2; t--) {
     double th0 = now_ms();
-    HLevel H = build_level(T_, t, active);
+    // this depth's cells of every problem deep enough, merged
+    HLevel H;
+    H.t = t;
+    H.dim = dim;
+    H.NB = dim == 2 ? 25 : 125;
+    std::vector<int> box_prob;
+    std::vector<int> cell_base(np + 1, 0);
+    for (int p = 0; p < np; p++) {
+      cell_base[p] = H.ncell;
+      if (F.trees[p].maxdepth < t || active[p].empty()) continue;
+      HLevel Hp = build_level(F.trees[p], t, active[p]);
+      append_level(H, Hp, F.pdof[p], box_prob, p);
+    }
+    cell_base[np] = H.ncell;
+    if (H.cell_dof_off.empty()) H.cell_dof_off.push_back(0);
+    if (H.box_cell.empty()) continue;  // no problem has boxes at this depth
+    // colour-major order over all problems (stable: problem order within a colour)
+    {
+      const int nb0 = (int)H.box_cell.size();
+      std::vector<int> ordr(nb0);
+      for (int q = 0; q < nb0; q++) ordr[q] = q;
+      std::stable_sort(ordr.begin(), ordr.end(), [&](int a, int b) { return H.box_colour[a] < H.box_colour[b]; });
+      std::vector<int> bc(nb0), bn(nb0), bcol(nb0), bp(nb0);
+      for (int q = 0; q < nb0; q++) {
+        bc[q] = H.box_cell[ordr[q]];
+        bn[q] = H.box_node[ordr[q]];
+        bcol[q] = H.box_colour[ordr[q]];
+        bp[q] = box_prob[ordr[q]];
+      }
+      H.box_cell.swap(bc);
+      H.box_node.swap(bn);
+      H.box_colour.swap(bcol);
+      box_prob.swap(bp);
+    }
     std::unique_ptr<DLevel<T>> D(new DLevel<T>());
     upload(D->cell_b, H.cell_b, st);
     upload(D->cell_dof_off, H.cell_dof_off, st);
@@ -907,10 +1019,15 @@ template <typename T> static void run_factor(Factor<T> &F) {
     if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the LU of a redundant block"};
     if (e) throw Fail{RSS_ECUDA, "device-side consistency check failed"};
     double ta0 = now_ms();
-    active.clear();
-    for (int c = 0; c < H.ncell; c++)
-      for (int q = 0; q < ac[c]; q++) active.push_back(H.cell_dofs[H.cell_dof_off[c] + ai[H.cell_dof_off[c] + q]]);
-    if (!std::is_sorted(active.begin(), active.end())) std::sort(active.begin(), active.end());
+    for (int p = 0; p < np; p++) {
+      if (cell_base[p + 1] == cell_base[p]) continue;
+      std::vector<int64_t> &act = active[p];
+      act.clear();
+      for (int c = cell_base[p]; c < cell_base[p + 1]; c++)
+        for (int q = 0; q < ac[c]; q++)
+          act.push_back(H.cell_dofs[H.cell_dof_off[c] + ai[H.cell_dof_off[c] + q]] - F.pdof[p]);
+      if (!std::is_sorted(act.begin(), act.end())) std::sort(act.begin(), act.end());
+    }
     F.prof.host(KC_HOST_LEVEL, now_ms() - ta0);
     prevD = std::move(D);
     prevH = std::move(H);
@@ -918,35 +1035,48 @@ template <typename T> static void run_factor(Factor<T> &F) {
     have_prev = true;
   }
 
-  // top block: all DOFs still active (Sec. 3.3.3), dense LU
-  F.ntop = (int)active.size();
-  upload(F.d_top, active, st);
-  F.d_topLU.alloc((size_t)F.ntop * F.ntop * sizeof(T) + 16, st);
+  // top blocks: every problem's DOFs still active (Sec. 3.3.3), dense LU
+  std::vector<int64_t> top;
+  F.h_tn.assign(np, 0);
+  F.h_toff.assign(np + 1, 0);
+  F.h_loff.assign(np + 1, 0);
+  for (int p = 0; p < np; p++) {
+    F.h_tn[p] = (int)active[p].size();
+    F.h_toff[p + 1] = F.h_toff[p] + F.h_tn[p];
+    F.h_loff[p + 1] = F.h_loff[p] + (int64_t)F.h_tn[p] * F.h_tn[p];
+    for (int64_t g : active[p]) top.push_back(g + F.pdof[p]);
+  }
+  F.ntop = (int)top.size();
+  upload(F.d_top, top, st);
+  upload(F.d_tn, F.h_tn, st);
+  upload(F.d_toff, F.h_toff, st);
+  upload(F.d_loff, F.h_loff, st);
+  F.d_topLU.alloc((size_t)F.h_loff[np] * sizeof(T) + 16, st);
   F.d_toppiv.alloc((size_t)F.ntop * sizeof(int) + 16, st);
-  F.factor_bytes += (int64_t)F.ntop * F.ntop * sizeof(T) + (int64_t)F.ntop * (sizeof(int) + 8);
+  F.factor_bytes += (int64_t)F.h_loff[np] * sizeof(T) + (int64_t)F.ntop * (sizeof(int) + 8);
   if (F.ntop > 0) {
-    std::vector<int64_t> z1{0}, z2{0}, z3{0};
-    std::vector<int> nr{F.ntop}, nc{F.ntop};
-    DBuf a, b2, c2, d2, e2;
-    upload(a, z1, st);
-    upload(b2, z2, st);
-    upload(c2, z3, st);
-    upload(d2, nr, st);
-    upload(e2, nc, st);
-    AssembleList L{1, ptr<int64_t>(a), ptr<int64_t>(b2), ptr<int64_t>(c2), ptr<int>(d2), ptr<int>(e2),
-                   ptr<int64_t>(F.d_top), ptr<int64_t>(F.d_top), 0};
-    // the dense LU works on a row-major matrix: assemble the transpose layout
-    L.transpose = 1;
+    std::vector<int> nr(F.h_tn.begin(), F.h_tn.end());
+    DBuf d_nr;
+    upload(d_nr, nr, st);
+    // the dense LU works on row-major matrices: assemble the transpose layout
+    AssembleList L{np, ptr<int64_t>(F.d_toff), ptr<int64_t>(F.d_toff), ptr<int64_t>(F.d_loff), ptr<int>(d_nr),
+                   ptr<int>(d_nr), ptr<int64_t>(F.d_top), ptr<int64_t>(F.d_top), 1};
+    int maxt = *std::max_element(F.h_tn.begin(), F.h_tn.end());
     if (have_prev) {
       LevelDev<T> pv = prevD->view(prevH, ptr<int>(d_dof_cell[prev_slot]), ptr<int>(d_dof_loc[prev_slot]));
-      launch_assemble<T>(L, ptr<T>(F.d_topLU), &pv, F.P, F.K, (int64_t)F.ntop * F.ntop, st);
+      launch_assemble<T>(L, ptr<T>(F.d_topLU), &pv, F.P, F.K, (int64_t)maxt * maxt, st);
     } else {
-      launch_assemble<T>(L, ptr<T>(F.d_topLU), nullptr, F.P, F.K, (int64_t)F.ntop * F.ntop, st);
+      launch_assemble<T>(L, ptr<T>(F.d_topLU), nullptr, F.P, F.K, (int64_t)maxt * maxt, st);
     }
     check_launch("assemble top");
-    double nt = F.ntop;
-    int pi = F.prof.begin(KC_TOPLU, st, 0, 0, 0, 2.0 * nt * nt * sizeof(T), 2.0 / 3.0 * nt * nt * nt);
-    launch_dense_lu<T>(ptr<T>(F.d_topLU), F.ntop, ptr<int>(F.d_toppiv), st, ptr<int>(F.d_err));
+    double fl = 0;
+    for (int tn : F.h_tn) fl += 2.0 / 3.0 * (double)tn * tn * tn;
+    int pi = F.prof.begin(KC_TOPLU, st, 0, 0, 0, 2.0 * (double)F.h_loff[np] * sizeof(T), fl);
+    if (np == 1)
+      launch_dense_lu<T>(ptr<T>(F.d_topLU), F.ntop, ptr<int>(F.d_toppiv), st, ptr<int>(F.d_err));
+    else
+      launch_lu_batched<T>(ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_toff),
+                           ptr<int>(F.d_tn), np, st, ptr<int>(F.d_err));
     check_launch("top lu");
     F.prof.end(pi, st);
   }
@@ -1008,8 +1138,8 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   }
   double nt = F.ntop;
   pi = P.begin(KC_TOP, st, 0, 0, 0, nt * nt * sz + 2.0 * nt * nrhs * sz, 2.0 * nt * nt * nrhs);
-  launch_top<T>(solve ? 0 : 1, ptr<T>(F.d_topLU), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top), F.ntop, v, nrhs,
-                ptr<T>(F.d_topwork), st);
+  launch_top<T>(solve ? 0 : 1, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
+                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, ptr<T>(F.d_topwork), st);
   P.end(pi, st);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
     pi = P.begin(KC_SWEEP, st, it->first, it->count, nrhs);
@@ -1062,7 +1192,9 @@ template <typename T> static void apply_A_impl(const Factor<T> &F, const double 
     }
     grid_op_apply(F.G, x, y, nrhs, F.st);
   } else {
-    launch_matvec(ptr<double>(F.d_x), F.dim, F.K, ptr<int64_t>(F.d_perm), x, y, F.n, nrhs, F.st);
+    launch_matvec(ptr<double>(F.d_x), F.dim, F.K, F.P.wdof, ptr<int64_t>(F.d_perm), x, y, F.n, nrhs, F.mv_ntile,
+                  ptr<int64_t>(F.d_mv_ts), ptr<int64_t>(F.d_mv_te), ptr<int64_t>(F.d_mv_sb), ptr<int64_t>(F.d_mv_se),
+                  F.st);
   }
   check_launch("residual operator");
 }
@@ -1240,7 +1372,8 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
   launch_permute<T>(0, ptr<int64_t>(F.d_perm), b, v, nullptr, F.n, nrhs, st);
   const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
   for (const Phase &p : F.phases) launch_sweep<T>(SWEEP_SOLVE_FWD, bx, p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
-  launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top), F.ntop, v, nrhs, topwork, st);
+  launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
+                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, topwork, st);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
     launch_sweep<T>(SWEEP_SOLVE_BWD, bx, it->first, it->count, v, nrhs, it->bmax, it->njmax, st);
   launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, x, F.n, nrhs, st);
@@ -1357,33 +1490,56 @@ rss_status rss_tree_query(const rss_tree *tree, int what, void *buf, size_t *nby
   });
 }
 
-rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, double eps, int leaf_size,
-                      const rss_options *opts, rss_factorization **out) {
+// Factor one or several independent problems into one handle.
+static rss_status factor_impl(int nprob, const double *const *pts, const int64_t *n, int dim, rss_kernel kernel,
+                              double eps, int leaf_size, const rss_options *opts, rss_factorization **out) {
   return guard([&] {
-    if (!out || n < 0 || (dim != 2 && dim != 3) || leaf_size < 1 || (n > 0 && !pts) || !(eps >= 0.0) ||
+    if (!out || nprob < 1 || !pts || !n || (dim != 2 && dim != 3) || leaf_size < 1 || !(eps >= 0.0) ||
         (kernel.kind != RSS_LAPLACE2D_LOG && kernel.kind != RSS_LAPLACE3D_INV))
       throw Fail{RSS_EINVAL, "rss_factor: bad arguments"};
+    for (int p = 0; p < nprob; p++)
+      if (n[p] < 0 || (n[p] > 0 && !pts[p])) throw Fail{RSS_EINVAL, "rss_factor: bad arguments"};
     rss_options o{};
     if (opts) o = *opts;
     const bool prof_on = o.profile != 0;
     if (o.prec != RSS_FP64 && o.prec != RSS_MIXED) throw Fail{RSS_EINVAL, "rss_factor: bad precision"};
     cudaStream_t st = (cudaStream_t)o.stream;
-    std::vector<double> h;
-    fetch_points(pts, n, dim, h, st);
+    std::vector<std::vector<double>> h(nprob);
+    for (int p = 0; p < nprob; p++) fetch_points(pts[p], n[p], dim, h[p], st);
     std::unique_ptr<rss_factorization> res(new rss_factorization());
     auto setup = [&](auto *F) {
       F->st = st;
-      F->n = n;
       F->dim = dim;
-      F->tree.dim = dim;
-      F->tree.leaf = leaf_size;
-      F->tree.n = n;
+      F->nprob = nprob;
+      F->trees.resize(nprob);
+      F->pdof.assign(nprob + 1, 0);
+      F->pw.assign(nprob, 1.0);
+      for (int p = 0; p < nprob; p++) {
+        F->pdof[p + 1] = F->pdof[p] + n[p];
+        F->pw[p] = kernel.weight > 0 ? kernel.weight : (n[p] > 0 ? 1.0 / (double)n[p] : 1.0);
+        F->trees[p].dim = dim;
+        F->trees[p].leaf = leaf_size;
+        F->trees[p].n = n[p];
+      }
+      F->n = F->pdof[nprob];
       double tt0 = now_ms();
-      build_tree(F->tree, h.data());
+      if (nprob == 1) {
+        build_tree(F->trees[0], h[0].data());
+      } else {
+        // independent trees on host threads
+        unsigned hw = std::thread::hardware_concurrency();
+        int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; t++)
+          th.emplace_back([&, t] {
+            for (int p = t; p < nprob; p += nt) build_tree(F->trees[p], h[p].data());
+          });
+        for (auto &x : th) x.join();
+      }
       F->prof.host(KC_HOST_TREE, now_ms() - tt0);
       F->K.kind = kernel.kind;
       F->K.diag = kernel.diag;
-      F->K.w = kernel.weight > 0 ? kernel.weight : (n > 0 ? 1.0 / (double)n : 1.0);
+      F->K.w = F->pw[0];
       F->px.np = o.n_proxy > 0 ? o.n_proxy : (dim == 2 ? 64 : 512);
       F->px.radius = o.proxy_radius > 0 ? o.proxy_radius : 2.5;
       F->eps = eps;
@@ -1405,6 +1561,18 @@ rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, 
     }
     *out = res.release();
   });
+}
+
+rss_status rss_factor(const double *pts, int64_t n, int dim, rss_kernel kernel, double eps, int leaf_size,
+                      const rss_options *opts, rss_factorization **out) {
+  const double *p[1] = {pts};
+  int64_t nn[1] = {n};
+  return factor_impl(1, p, nn, dim, kernel, eps, leaf_size, opts, out);
+}
+
+rss_status rss_factor_batched(int nprob, const double *const *pts, const int64_t *n, int dim, rss_kernel kernel,
+                              double eps, int leaf_size, const rss_options *opts, rss_factorization **out) {
+  return factor_impl(nprob, pts, n, dim, kernel, eps, leaf_size, opts, out);
 }
 
 rss_status rss_solve_refined(const rss_factorization *f, const double *b, double *x, int nrhs, double tol,
@@ -1470,7 +1638,7 @@ rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes) {
     if (!f || !f->impl || !nbytes) throw Fail{RSS_EINVAL, "rss_stats: bad arguments"};
     std::vector<int64_t> s;
     auto fill = [&](const auto &F) {
-      s = {(int64_t)F.h_boxes.size(), F.ntop, F.factor_bytes, F.tree.maxdepth, F.n, F.prec};
+      s = {(int64_t)F.h_boxes.size(), F.ntop, F.factor_bytes, F.maxdepth, F.n, F.prec};
       for (const auto &b : F.h_boxes) {
         s.push_back(b.depth);
         s.push_back(b.b);

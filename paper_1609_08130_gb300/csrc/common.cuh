@@ -36,11 +36,12 @@ __host__ __device__ __forceinline__ void decode3(int c, int dim, int &dx, int &d
 // that cell, so differences of nearby points keep full FP32 relative
 // accuracy without FP64 arithmetic: x_i - x_j = (c_i - c_j) D + (d_i - d_j).
 struct Points {
-  const double *x;  // n*dim, tree order
-  const int *cell;  // n*3 integer cells at depth `fine`
-  const float *off; // n*3 offsets in the cell
-  float D;          // side of a finest cell
+  const double *x;     // n*dim, tree order
+  const int *cell;     // n*3 integer cells at depth 20
+  const float *off;    // n*3 offsets in the cell
+  float D;             // side of a depth-20 cell
   int dim;
+  const double *wdof;  // per-DOF weight w (several problems), or NULL: KernelParams::w
 };
 
 template <typename T> struct Dist2;
@@ -89,7 +90,13 @@ struct KernelParams {
 template <typename T>
 __device__ __forceinline__ T entry(const Points &P, const KernelParams &K, int64_t i, int64_t j) {
   if (i == j) return (T)K.diag;
-  return (T)K.w * kof(K.kind, Dist2<T>::eval(P, i, j));
+  const double w = P.wdof ? P.wdof[i] : K.w;
+  return (T)w * kof(K.kind, Dist2<T>::eval(P, i, j));
+}
+
+// Weight of the problem a DOF belongs to.
+__device__ __forceinline__ double weight_of(const Points &P, const KernelParams &K, int64_t i) {
+  return P.wdof ? P.wdof[i] : K.w;
 }
 
 // Warp reductions.

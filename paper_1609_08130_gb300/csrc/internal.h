@@ -93,15 +93,19 @@ template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
                   int njmax, cudaStream_t st);
 template <typename T>
-void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v,
-                int nrhs, T *work, cudaStream_t st);
+void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, const int64_t *top, const int64_t *toff,
+                const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st);
+template <typename T>
+void launch_lu_batched(T *LU, const int64_t *loff, int *piv, const int64_t *toff, const int *tn, int nprob,
+                       cudaStream_t st, int *err);
 template <typename T> int64_t id_region_bytes(int b, int PR);
 template <typename T> int64_t elim_ws_elems(int bmax);
 template <typename T>
 void launch_permute(int dir, const int64_t *perm, const double *in, T *out_or_in, double *out,
                     int64_t n, int nrhs, cudaStream_t st);
-void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const int64_t *perm,
-                   const double *xin, double *yout, int64_t n, int nrhs, cudaStream_t st);
+void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const double *wdof, const int64_t *perm,
+                   const double *xin, double *yout, int64_t n, int nrhs, int ntile, const int64_t *tstart,
+                   const int64_t *tend, const int64_t *sbeg, const int64_t *send, cudaStream_t st);
 
 // FP64 operator x -> A x for points on an s^d grid of cell centres, by FFT
 // convolution on the circulant of side L = 2s (refine.cu).

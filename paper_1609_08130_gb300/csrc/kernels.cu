@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   const int nO = s_obase[no];
   const int m = nO + px.np;
   const int64_t coff = lv.cell_dof_off[c];
-  const T w = (T)K.w;
+  const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
   // proxy circle / sphere about the box centre (Sec. 3.2)
   const double D = ldexp(1.0, -lv.t);
   double ctr[3];
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, con
 #pragma unroll
       for (int d = 0; d < 3; d++) xq[q][d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr[d] : 0.0;
     }
-    const T w = (T)K.w;
+    const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
     const int npan = (m + PR - 1) / PR;
     for (int pnl = sw; pnl < npan; pnl += W) {
       T pan[PR][CPL];
@@ -978,7 +978,7 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
       xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
     }
   }
-  const T w = (T)K.w;
+  const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
   const int npan = (m + PR - 1) / PR;
   for (int pnl = grp; pnl < npan; pnl += G) {
     T pan[PR];
@@ -2304,12 +2304,21 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
   k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs, jsh); count_launch();
 }
 
-// Top block: solve (mode 0) or multiply (mode 1), one CTA per right-hand side.
+// Top blocks of one or more problems (Sec. 3.3.3): problem p has tn[p] DOFs
+// with global ids top[toff[p] ...], its LU (row-major, P A = L U) at
+// LU + loff[p] and pivots at piv + toff[p].  Solve (mode 0) or multiply
+// (mode 1); one CTA per (problem, right-hand side).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_top(int mode, const T *LU, const int *piv, const int64_t *top,
-                                              int n, T *v, int nrhs, T *work) {
-  const int c = blockIdx.x;
-  T *y = work + (int64_t)c * 2 * n;
+__global__ void __launch_bounds__(1024) k_top(int mode, const T *LUall, const int64_t *loff, const int *pivall,
+                                              const int64_t *topall, const int64_t *toff, const int *tn, T *v,
+                                              int nrhs, T *work) {
+  const int p = blockIdx.x / nrhs, c = blockIdx.x % nrhs;
+  const int n = tn[p];
+  if (n == 0) return;
+  const T *LU = LUall + loff[p];
+  const int *piv = pivall + toff[p];
+  const int64_t *top = topall + toff[p];
+  T *y = work + 2 * (toff[p] * nrhs + (int64_t)c * n);
   T *u = y + n;
   const int tid = threadIdx.x;
   if (mode == 0) {
@@ -2346,10 +2355,96 @@ __global__ void __launch_bounds__(1024) k_top(int mode, const T *LU, const int *
 }
 
 template <typename T>
-void launch_top(int mode, const T *LU, const int *piv, const int64_t *top, int ntop, T *v, int nrhs,
-                T *work, cudaStream_t st) {
-  if (ntop == 0) return;
-  k_top<T><<<nrhs, 1024, 0, st>>>(mode, LU, piv, top, ntop, v, nrhs, work); count_launch();
+void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, const int64_t *top, const int64_t *toff,
+                const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st) {
+  if (ntop_total == 0 || nprob == 0) return;
+  k_top<T><<<nprob * nrhs, 1024, 0, st>>>(mode, LU, loff, piv, top, toff, tn, v, nrhs, work);
+  count_launch();
+}
+
+// LU with partial pivoting of many small dense blocks, one CTA per block
+// (row-major, in place; pivot = largest |entry|, ties to the lowest row).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_batched(T *LUall, const int64_t *loff, int *pivall, const int64_t *toff,
+                                                    const int *tn, int *err) {
+  __shared__ T s_val[8];
+  __shared__ int s_idx[8];
+  const int p = blockIdx.x, n = tn[p];
+  T *A = LUall + loff[p];
+  int *piv = pivall + toff[p];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += blockDim.x) piv[i] = i;
+  __syncthreads();
+  for (int j = 0; j < n; j++) {
+    T best = (T)-1;
+    int bi = n;
+    for (int i = j + tid; i < n; i += blockDim.x) {
+      T v = fabs(A[(int64_t)i * n + j]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_val[warp] = best;
+      s_idx[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int u = 1; u < (int)(blockDim.x >> 5); u++)
+        if (s_val[u] > best || (s_val[u] == best && s_idx[u] < bi)) {
+          best = s_val[u];
+          bi = s_idx[u];
+        }
+      if (bi >= n) {
+        bi = j;
+        set_err(err, DERR_NUMERIC);
+      }
+      if (best == (T)0) set_err(err, DERR_NUMERIC);
+      s_idx[0] = bi;
+    }
+    __syncthreads();
+    const int pr = s_idx[0];
+    if (pr != j) {
+      for (int cc = tid; cc < n; cc += blockDim.x) {
+        T t0 = A[(int64_t)j * n + cc];
+        A[(int64_t)j * n + cc] = A[(int64_t)pr * n + cc];
+        A[(int64_t)pr * n + cc] = t0;
+      }
+      if (tid == 0) {
+        int tp = piv[j];
+        piv[j] = piv[pr];
+        piv[pr] = tp;
+      }
+    }
+    __syncthreads();
+    const T d = A[(int64_t)j * n + j];
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) A[(int64_t)i * n + j] /= d;
+    __syncthreads();
+    const int rem = n - j - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      int i = j + 1 + e / rem, cc = j + 1 + e % rem;
+      A[(int64_t)i * n + cc] -= A[(int64_t)i * n + j] * A[(int64_t)j * n + cc];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_lu_batched(T *LU, const int64_t *loff, int *piv, const int64_t *toff, const int *tn, int nprob,
+                       cudaStream_t st, int *err) {
+  if (nprob == 0) return;
+  k_lu_batched<T><<<nprob, 256, 0, st>>>(LU, loff, piv, toff, tn, err);
+  count_launch();
 }
 
 // dir 0: out_t[g*nrhs+c] = in[perm[g] + c*n];  dir 1: out[perm[g] + c*n] = in_t[g*nrhs+c]
@@ -2374,56 +2469,68 @@ void launch_permute(int dir, const int64_t *perm, const double *in, T *tv, doubl
   k_permute<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dir, perm, in, tv, out, n, nrhs); count_launch();
 }
 
-// Exact FP64 y = A x by direct summation (tree-ordered points, caller order
-// vectors through perm).  One thread per target, sources staged in shared
-// memory.
-__global__ void __launch_bounds__(256) k_matvec(const double *xt, int dim, KernelParams K, const int64_t *perm,
-                                                const double *xin, double *yout, int64_t n, int nrhs) {
+// Exact FP64 y = A x by direct summation (tree-ordered points, caller-order
+// vectors through perm), for one or several independent problems: tile q
+// covers targets [tstart[q], tend[q]) of a problem whose DOFs are
+// [sbeg[q], send[q]); sources are staged in shared memory.  Each point's
+// weight comes from wdof (or K.w).
+__global__ void __launch_bounds__(256) k_matvec(const double *xt, int dim, KernelParams K, const double *wdof,
+                                                const int64_t *perm, const double *xin, double *yout, int64_t n,
+                                                int nrhs, const int64_t *tstart, const int64_t *tend,
+                                                const int64_t *sbeg, const int64_t *send) {
   __shared__ double sp[256 * 3];
   __shared__ double sx[256 * 4];
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int q = blockIdx.x;
+  const int64_t i = tstart[q] + threadIdx.x;
+  const bool live = i < tend[q];
+  const int64_t j0b = sbeg[q], j1b = send[q];
   const int cb = blockIdx.y * 4;
   const int nc = min(4, nrhs - cb);
   double xi[3] = {0, 0, 0};
-  if (i < n)
+  double w = K.w;
+  if (live) {
     for (int d = 0; d < dim; d++) xi[d] = xt[i * dim + d];
+    if (wdof) w = wdof[i];
+  }
   double acc[4] = {0, 0, 0, 0};
-  for (int64_t j0 = 0; j0 < n; j0 += 256) {
+  for (int64_t j0 = j0b; j0 < j1b; j0 += 256) {
     int64_t j = j0 + threadIdx.x;
-    if (j < n) {
+    if (j < j1b) {
       for (int d = 0; d < dim; d++) sp[threadIdx.x * 3 + d] = xt[j * dim + d];
       for (int c = 0; c < nc; c++) sx[threadIdx.x * 4 + c] = xin[perm[j] + (int64_t)(cb + c) * n];
     }
     __syncthreads();
-    int lim = (int)min((int64_t)256, n - j0);
-    if (i < n) {
-      for (int q = 0; q < lim; q++) {
-        int64_t jj = j0 + q;
+    int lim = (int)min((int64_t)256, j1b - j0);
+    if (live) {
+      for (int qq = 0; qq < lim; qq++) {
+        int64_t jj = j0 + qq;
         double a;
         if (jj == i) {
           a = K.diag;
         } else {
           double r2 = 0.0;
           for (int d = 0; d < dim; d++) {
-            double z = xi[d] - sp[q * 3 + d];
+            double z = xi[d] - sp[qq * 3 + d];
             r2 += z * z;
           }
-          a = K.w * kof(K.kind, r2);
+          a = w * kof(K.kind, r2);
         }
-        for (int c = 0; c < nc; c++) acc[c] += a * sx[q * 4 + c];
+        for (int c = 0; c < nc; c++) acc[c] += a * sx[qq * 4 + c];
       }
     }
     __syncthreads();
   }
-  if (i < n)
+  if (live)
     for (int c = 0; c < nc; c++) yout[perm[i] + (int64_t)(cb + c) * n] = acc[c];
 }
 
-void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const int64_t *perm, const double *xin,
-                   double *yout, int64_t n, int nrhs, cudaStream_t st) {
-  if (n == 0) return;
-  dim3 g((unsigned)((n + 255) / 256), (nrhs + 3) / 4);
-  k_matvec<<<g, 256, 0, st>>>(x_tree, dim, K, perm, xin, yout, n, nrhs); count_launch();
+void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const double *wdof, const int64_t *perm,
+                   const double *xin, double *yout, int64_t n, int nrhs, int ntile, const int64_t *tstart,
+                   const int64_t *tend, const int64_t *sbeg, const int64_t *send, cudaStream_t st) {
+  if (n == 0 || ntile == 0) return;
+  dim3 g((unsigned)ntile, (nrhs + 3) / 4);
+  k_matvec<<<g, 256, 0, st>>>(x_tree, dim, K, wdof, perm, xin, yout, n, nrhs, tstart, tend, sbeg, send);
+  count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -2442,7 +2549,10 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const i
                                 cudaStream_t);                                                                \
   template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \
   template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t);            \
-  template void launch_top<T>(int, const T *, const int *, const int64_t *, int, T *, int, T *, cudaStream_t); \
+  template void launch_top<T>(int, const T *, const int64_t *, const int *, const int64_t *, const int64_t *,     \
+                             const int *, int, int, T *, int, T *, cudaStream_t);                            \
+  template void launch_lu_batched<T>(T *, const int64_t *, int *, const int64_t *, const int *, int, cudaStream_t, \
+                                     int *);                                                                  \
   template void launch_permute<T>(int, const int64_t *, const double *, T *, double *, int64_t, int,          \
                                   cudaStream_t);
 RSS_INST(float)

@@ -71,6 +71,8 @@ _SIGS = {
     "rss_tree_query": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, _Kernel, C.c_double, C.c_int,
                              C.POINTER(_Options), C.POINTER(C.c_void_p)]),
+    "rss_factor_batched": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_int, _Kernel,
+                                     C.c_double, C.c_int, C.POINTER(_Options), C.POINTER(C.c_void_p)]),
     "rss_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -196,6 +198,32 @@ class Factorization:
         _check(lib().rss_factor(C.c_void_p(pts.data_ptr()), self.n, self.dim, _Kernel(kind, diag, weight),
                                 eps, leaf, C.byref(opts), C.byref(h)))
         self.h = h
+
+    @classmethod
+    def batched(cls, pts_list, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
+                weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
+                profile: bool = False, flags: int = 0):
+        """rss_factor_batched: one handle for several independent problems;
+        vectors are the problems' vectors concatenated in order."""
+        torch = _torch()
+        pts = [_dev_f64(p) for p in pts_list]
+        dim = pts[0].shape[1]
+        self = cls.__new__(cls)
+        self.n = int(sum(p.shape[0] for p in pts))
+        self.dim = dim
+        self.prec = prec
+        self.sizes = [int(p.shape[0]) for p in pts]
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        self._keep = pts
+        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags))
+        arr = (C.c_void_p * len(pts))(*[p.data_ptr() for p in pts])
+        ns = (C.c_int64 * len(pts))(*self.sizes)
+        h = C.c_void_p()
+        _check(lib().rss_factor_batched(len(pts), arr, ns, dim, _Kernel(kind, diag, weight), eps, leaf,
+                                        C.byref(opts), C.byref(h)))
+        self.h = h
+        return self
 
     def _vec(self, x):
         torch = _torch()

@@ -230,3 +230,55 @@ def test_3d_grid32_refined_full_size(pkg):
     r = b[:, rows] - oracle.matvec(pts, 1, x, rows=rows)
     assert rel <= 1e-10
     assert np.abs(r).max() <= 1e-9 * np.abs(b).max()
+
+
+def _batched_case(count=6, cap=3000):
+    """The first problems of the batched 2D workload (iid uniform points,
+    sizes from the workload's size stream), keeping those of at most `cap`
+    points so the oracle stays quick."""
+    sizes = inputs.batched_sizes(64)
+    out = []
+    for p, n in enumerate(sizes):
+        if n <= cap:
+            out.append(inputs.batched_problem(p, int(n)))
+        if len(out) == count:
+            break
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_matches_oracle(pkg, prec):
+    """Several independent problems factored in one handle (one launch per
+    level and colour over all of them) against the oracle, problem by
+    problem; w = 1/N_p per problem."""
+    probs = _batched_case()
+    eps = 1e-6
+    f = pkg.Factorization.batched([_cuda(p) for p in probs], 0, eps, leaf=64,
+                                  prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+    sizes = [len(p) for p in probs]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    x = np.concatenate([inputs.normal(40 + i, n) for i, n in enumerate(sizes)])
+    y = f.apply(_cuda(x)).cpu().numpy()
+    z = f.solve(_cuda(x)).cpu().numpy()
+    for i, pts in enumerate(probs):
+        of = oracle.Factor(oracle.Tree(pts, 64), 0, eps)
+        seg = slice(off[i], off[i + 1])
+        yo = of.apply(x[seg])
+        zo = of.solve(x[seg])
+        assert np.linalg.norm(y[seg] - yo) / np.linalg.norm(yo) <= 10 * eps
+        assert np.linalg.norm(z[seg] - zo) / np.linalg.norm(zo) <= 10 * eps
+
+
+def test_batched_refined_solve(pkg):
+    probs = _batched_case(count=5)
+    f = pkg.Factorization.batched([_cuda(p) for p in probs], 0, 1e-6, leaf=64, prec=pkg.MIXED)
+    sizes = [len(p) for p in probs]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    b = np.concatenate([inputs.normal(2000 + i, n) for i, n in enumerate(sizes)])
+    x, iters, rel = f.solve_refined(_cuda(b), tol=1e-10, maxit=10)
+    x = x.cpu().numpy()
+    assert rel <= 1e-10
+    for i, pts in enumerate(probs):
+        seg = slice(off[i], off[i + 1])
+        r = b[seg] - oracle.matvec(pts, 0, x[seg])
+        assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(b)
