@@ -55,8 +55,11 @@ __global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__
     }
     T v;
     bool done = false;
-    if (has_prev) {
-      int ci = prev.dof_cell[gi], cj = prev.dof_cell[gj];
+    // A DOF without a cell at the previous level belongs to a problem whose
+    // tree is shallower than the merged previous level: none of its entries
+    // has been updated yet, so the kernel entry is the value.
+    int ci = has_prev ? prev.dof_cell[gi] : -1, cj = has_prev ? prev.dof_cell[gj] : -1;
+    if (ci >= 0 && cj >= 0) {
       int dx = prev.cell_coord[3 * cj] - prev.cell_coord[3 * ci];
       int dy = prev.cell_coord[3 * cj + 1] - prev.cell_coord[3 * ci + 1];
       int dz = prev.cell_coord[3 * cj + 2] - prev.cell_coord[3 * ci + 2];

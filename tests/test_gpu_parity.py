@@ -282,3 +282,29 @@ def test_batched_refined_solve(pkg):
         seg = slice(off[i], off[i + 1])
         r = b[seg] - oracle.matvec(pts, 0, x[seg])
         assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_mixed_depths(pkg, prec):
+    """Problems whose trees end at different depths share a handle: at the
+    deeper levels only some problems have cells, and the shallower problems'
+    blocks are first assembled at their own deepest level (kernel entries,
+    no Schur update yet).  Each problem is compared with the oracle."""
+    probs = [inputs.batched_problem(0, 100), inputs.batched_problem(1, 1200), inputs.batched_problem(2, 6000)]
+    depths = [pkg.Tree(_cuda(p), 64).maxdepth for p in probs]
+    assert len(set(depths)) == 3, depths
+    eps = 1e-6
+    f = pkg.Factorization.batched([_cuda(p) for p in probs], 0, eps, leaf=64,
+                                  prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+    sizes = [len(p) for p in probs]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    x = np.concatenate([inputs.normal(70 + i, n) for i, n in enumerate(sizes)])
+    y = f.apply(_cuda(x)).cpu().numpy()
+    z = f.solve(_cuda(x)).cpu().numpy()
+    for i, pts in enumerate(probs):
+        of = oracle.Factor(oracle.Tree(pts, 64), 0, eps)
+        seg = slice(off[i], off[i + 1])
+        yo = of.apply(x[seg])
+        zo = of.solve(x[seg])
+        assert np.linalg.norm(y[seg] - yo) / np.linalg.norm(yo) <= 10 * eps
+        assert np.linalg.norm(z[seg] - zo) / np.linalg.norm(zo) <= 10 * eps
