@@ -54,6 +54,8 @@ typedef struct {
 
 typedef enum { RSS_FP64 = 0, RSS_MIXED = 1 } rss_precision;
 
+typedef struct rss_mlp rss_mlp; /* rank-proposal network (rss_mlp_create) */
+
 typedef struct {
   int prec;            /* rss_precision: FP64 everywhere, or an FP32 factor */
   int n_proxy;         /* proxy points; 0: 64 (2D) / 512 (3D) (Sec. 4) */
@@ -63,6 +65,8 @@ typedef struct {
   int profile;         /* 1: time every kernel launch with CUDA events on the
                           stream (see rss_profile) */
   int flags;           /* RSS_FLAG_* bits; 0 for the defaults */
+  const rss_mlp *mlp;  /* rank proposal presizing the factor storage, or NULL
+                          (see rss_mlp_create); borrowed for the call only */
 } rss_options;
 
 /* Route every box through the large-box kernels (global-memory workspaces),
@@ -186,22 +190,88 @@ rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, in
 /* rss_stats -- factor statistics into a HOST int64 array:
  *   [0] number of skeletonized boxes  [1] top-block size  [2] factor bytes
  *   [3] maxdepth                      [4] n               [5] precision
- * followed, per box in elimination order, by {depth, b, k, nj}.
- * *nbytes in/out as in rss_tree_query. */
+ *   [6] bytes reserved for the boxes' T, LU, X_RR^{-1}, E and G (with the
+ *       overflow space when a rank proposal was used)
+ *   [7] bytes those arrays need at the ranks found: sum of k r + 2 r^2 + 2 nj r
+ *   [8] overflow bytes taken by boxes whose r exceeded their reservation
+ *   [9] 1 when a proposal left a level short and the factorization was redone
+ *       with full-size reservations, else 0
+ *  [10] 1 when the reservations came from a rank proposal (options.mlp)
+ * followed, per box in elimination order, by {depth, b, k, nj, rres, njres}
+ * (rres, njres: the r and |J| its storage was reserved for).  *nbytes in/out
+ * as in rss_tree_query. */
 rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes);
 
 /* rss_profile -- per-kernel-class totals of a factor created with
  * options.profile = 1, accumulated over rss_factor and every later
- * rss_apply / rss_solve on it, into a HOST double array of 4 * 8 entries:
+ * rss_apply / rss_solve on it, into a HOST double array of 4 * 12 entries:
  * for class c in {0 assemble, 1 id, 2 elim, 3 schur, 4 top LU, 5 sweep,
- * 6 top solve/multiply, 7 permute}: {launches, milliseconds (CUDA events on
- * the launching stream), algorithmic bytes, algorithmic flops}.  The
- * algorithmic counts are the data the method must move or compute (stated
- * per class in the implementation), not hardware counters.
+ * 6 top solve/multiply, 7 permute, 8 host tree build, 9 host level build,
+ * 10 host wait at level end, 11 FP64 residual operator}: {launches or calls,
+ * milliseconds (CUDA events on the launching stream; host wall time for the
+ * host classes), algorithmic bytes, algorithmic flops}.  The algorithmic
+ * counts are the data the method must move or compute (stated per class in
+ * the implementation), not hardware counters.
  * reset != 0 clears the totals after copying.  *nbytes in/out. */
 rss_status rss_profile(const rss_factorization *f, int reset, double *buf, size_t *nbytes);
 
-/* rss_free -- release a tree or factor handle (NULL-safe). */
+/* Rank proposal (not in the paper).  A small network predicts each box's
+ * skeleton fraction k/b from features known before its ID; rss_factor with
+ * options.mlp reserves each box's LU, X_RR^{-1}, E and G for the predicted
+ * r = b - k and |J| = k + (near DOFs still active at the box's turn: the
+ * predicted skeletons of neighbours eliminated in an earlier colour phase,
+ * all DOFs of the others), each plus a margin, instead of for r = b and the
+ * level-start |J|.  The column-pivoted QR still
+ * decides every rank (Sec. 2.2, Definition 2.1): a box that does not fit its
+ * reservation takes the level's overflow space, and if that runs out the
+ * factorization is redone with full-size reservations (rss_stats [9]).  The
+ * factor is the same either way.
+ *
+ * Network: 16 features -> 64 -> 64 -> 64 (tanh) -> 1, parameters one FP32
+ * vector of RSS_MLP_NPARAM values in the order W1 (64 x 16 row-major, row =
+ * output unit), b1, W2 (64 x 64), b2, W3 (64 x 64), b3, w4 (64), b4.  The
+ * forward and backward passes read the parameters rounded to bfloat16 and
+ * compute in FP32; Adam keeps the FP32 master copy.  Features per box (FP32):
+ *   0 dim == 3    1 kernel kind    2 -log10(eps)/10    3 log2(1+b)/10
+ *   4 log2(1+|N|)/10 (near DOFs)   5 log2(1+|O|)/10 (ring DOFs, Sec. 3.2)
+ *   6 near cells present/(3^d-1)   7 ring cells present/(5^d-3^d)
+ *   8 leaf box    9 b / (sum of the children's b), 1 for a leaf
+ *  10 depth/10   11 log2(1+n_p)/10  12 proxy radius/5   13..15 zero. */
+#define RSS_MLP_NFEAT 16
+#define RSS_MLP_NPARAM 9473
+
+/* rss_mlp_create -- a network on `stream` (cudaStream_t, NULL = legacy
+ * default).  params: HOST array of RSS_MLP_NPARAM FP32 values, or NULL for
+ * Glorot-uniform weights from SplitMix64(seed) (uniform = top 53 bits of
+ * output i times 2^-53 for flat parameter i) and zero biases.  Free with
+ * rss_free.  Errors: RSS_EINVAL, RSS_ENOMEM, RSS_ECUDA. */
+rss_status rss_mlp_create(const float *params, uint64_t seed, void *stream, rss_mlp **out);
+
+/* rss_mlp_params -- copy the FP32 master parameters to a HOST array of
+ * RSS_MLP_NPARAM values. */
+rss_status rss_mlp_params(const rss_mlp *m, float *params);
+
+/* rss_mlp_predict -- y[i] = network(X[i]) for n samples.  X: DEVICE, n x 16
+ * FP32 row-major; y: DEVICE, n FP32. */
+rss_status rss_mlp_predict(const rss_mlp *m, const float *X, int64_t n, float *y);
+
+/* rss_mlp_grad -- gradient of the loss mean_i (network(X[i]) - y[i])^2 with
+ * respect to the parameters (DEVICE, RSS_MLP_NPARAM FP32, same order), and the
+ * loss (HOST double, may be NULL).  X, y: DEVICE, n >= 1 samples. */
+rss_status rss_mlp_grad(const rss_mlp *m, const float *X, const float *y, int64_t n, float *grad, double *loss);
+
+/* rss_mlp_train -- `iters` full-batch Adam steps (beta1 0.9, beta2 0.999,
+ * eps 1e-8, learning rate lr) on the loss above; the step counter persists
+ * across calls.  *loss (HOST, may be NULL): the loss before the last step. */
+rss_status rss_mlp_train(rss_mlp *m, const float *X, const float *y, int64_t n, int iters, float lr,
+                         double *loss);
+
+/* rss_box_features -- every skeletonized box's features (HOST, nbox x 16
+ * FP32, elimination order as in rss_stats) and the rank k its ID found (HOST,
+ * nbox int32): training data for the network.  nbox must equal rss_stats [0]. */
+rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *rank, int64_t nbox);
+
+/* rss_free -- release a tree, factor or network handle (NULL-safe). */
 void rss_free(void *handle);
 
 /* rss_kernel_launches -- number of CUDA kernel launches this library has

@@ -6,5 +6,5 @@ The compute path is the CUDA library ``librss.so`` (C ABI in
 :mod:`.inputs` makes seeded synthetic workloads.
 """
 from . import inputs  # noqa: F401
-from .rss import (FP64, MIXED, LAPLACE2D_LOG, LAPLACE3D_INV, Factorization, RSSError, Tree,  # noqa: F401
+from .rss import (FP64, MIXED, LAPLACE2D_LOG, LAPLACE3D_INV, Factorization, Mlp, RSSError, Tree,  # noqa: F401
                   build, kernel_launches, lib)

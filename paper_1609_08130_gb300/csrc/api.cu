@@ -14,6 +14,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/rss.h"
@@ -98,7 +99,14 @@ template <typename U> static void upload(DBuf &d, const std::vector<U> &h, cudaS
 // Tree
 // ---------------------------------------------------------------------------
 
-static const uint32_t MAGIC_TREE = 0x52535354u, MAGIC_FACTOR = 0x52535346u;
+static const uint32_t MAGIC_TREE = 0x52535354u, MAGIC_FACTOR = 0x52535346u, MAGIC_MLP = 0x5253534Du;
+
+// Device state of the rank-proposal network: FP32 master parameters, their
+// bfloat16 copy, Adam moments and step, gradient and loss.
+struct MlpModel {
+  cudaStream_t st = nullptr;
+  DBuf theta, wbf, m, v, grad, step, loss;
+};
 
 static inline int64_t cell_at(double v, int t) {
   int64_t m = (int64_t)1 << t;
@@ -551,6 +559,13 @@ template <typename T> struct Factor : FactorBase {
   mutable bool grid_ready = false;
   int mv_ntile = 0;
   DBuf d_mv_ts, d_mv_te, d_mv_sb, d_mv_se;
+  // rank proposal: the network (borrowed during rss_factor only), the
+  // features of every box (MLP_NFEAT each, box order) and storage accounting
+  const struct MlpModel *mlp = nullptr;
+  std::vector<float> feats;
+  int64_t reserved_T = 0, used_T = 0, ovf_used = 0;  // elements of T
+  int retries = 0;
+  DBuf d_ovf_used;
 
   void *alloc_store(size_t bytes) {
     store.emplace_back(new DBuf());
@@ -688,6 +703,53 @@ static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vect
   H.bmax = std::max(H.bmax, Hp.bmax);
 }
 
+// A level ran out of overflow space for boxes whose rank exceeded the
+// proposed reservation: the factorization is redone with full reservations.
+struct Retry {};
+
+// Features of a box for the rank proposal, all known before its ID runs:
+//   0 dim == 3            1 kernel kind          2 -log10(eps) / 10
+//   3 log2(1 + b) / 10    4 log2(1 + |N|) / 10   5 log2(1 + |O|) / 10
+//   6 near cells present / (3^d - 1)             7 ring cells present / (5^d - 3^d)
+//   8 leaf box (its DOFs are points)             9 b / (sum of its children's b), 1 for a leaf
+//  10 depth / 10          11 log2(1 + n_p) / 10  12 proxy radius / 5
+//  13..15 zero
+// |N| counts the level-start DOFs of the 3^d - 1 neighbour cells, |O| those of
+// the ring at distance 2 (Sec. 3.2).
+static void box_features(float *f, int dim, int kind, double eps, const ProxyParams &px, int depth, int b,
+                         int nnear, int nring, int nnear_cells, int nring_cells, bool leaf, int child_sum) {
+  const double n3 = dim == 3 ? 26.0 : 8.0, n5 = dim == 3 ? 98.0 : 16.0;
+  f[0] = dim == 3 ? 1.f : 0.f;
+  f[1] = (float)kind;
+  f[2] = (float)(eps > 0 ? -log10(eps) / 10.0 : 1.6);
+  f[3] = (float)(log2(1.0 + b) / 10.0);
+  f[4] = (float)(log2(1.0 + nnear) / 10.0);
+  f[5] = (float)(log2(1.0 + nring) / 10.0);
+  f[6] = (float)(nnear_cells / n3);
+  f[7] = (float)(nring_cells / n5);
+  f[8] = leaf ? 1.f : 0.f;
+  f[9] = leaf || child_sum <= 0 ? 1.f : (float)((double)b / child_sum);
+  f[10] = (float)(depth / 10.0);
+  f[11] = (float)(log2(1.0 + px.np) / 10.0);
+  f[12] = (float)(px.radius / 5.0);
+  for (int i = 13; i < MLP_NFEAT; i++) f[i] = 0.f;
+}
+
+// Proposed skeleton size from the predicted fraction k/b (NaN: k = b).
+static int propose_k(int b, float frac) {
+  if (!(frac == frac)) return b;
+  const double f = std::min(1.0, std::max(0.0, (double)frac));
+  return std::min(b, std::max(0, (int)std::lround(f * b)));
+}
+
+// Redundant DOFs to reserve storage for: the proposal's r plus a margin of
+// max(4, b/8), at most b (NaN: no proposal, r = b).
+static int reserve_rank(int b, float frac) {
+  if (!(frac == frac)) return b;
+  const int r = b - propose_k(b, frac) + std::max(4, (b + 7) / 8);
+  return std::min(b, std::max(0, r));
+}
+
 template <typename T> static void run_factor(Factor<T> &F) {
   const int dim = F.dim;
   const int64_t n = F.n;
@@ -818,6 +880,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
     check_launch("assemble");
   };
 
+  std::unordered_map<int64_t, int> child_b;  // (problem, node) -> sum of its children's b
+  if (F.mlp) F.d_ovf_used.alloc(sizeof(unsigned long long), st);
   for (int t = F.maxdepth; t >= 2; t--) {
     double th0 = now_ms();
     // this depth's cells of every problem deep enough, merged
@@ -891,51 +955,108 @@ template <typename T> static void run_factor(Factor<T> &F) {
     }
     prevD.reset();  // stream-ordered free of the previous level
 
-    // factor records of this level's boxes
+    // factor records of this level's boxes, and each box's features for the
+    // rank proposal (sizes and geometry known before its ID)
     const int base = (int)F.h_boxes.size();
     const int nb = (int)H.box_cell.size();
     int njmax_lvl = 0, ring_max = 0;
     std::vector<int> njmaxv(nb);
-    size_t sz_i64 = 0, sz_i32 = 0, sz_T = 0;
+    std::vector<float> fx((size_t)nb * MLP_NFEAT, 0.f);
     for (int q = 0; q < nb; q++) {
       int c = H.box_cell[q], b = H.cell_b[c];
-      int nj = b;
+      int nj = b, nnear_cells = 0;
       int lim = dim == 3 ? 1 : 0;
       for (int dz = -lim; dz <= lim; dz++)
         for (int dy = -1; dy <= 1; dy++)
           for (int dx = -1; dx <= 1; dx++) {
             if (!dx && !dy && !dz) continue;
             int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
-            if (nbc >= 0) nj += H.cell_b[nbc];
+            if (nbc >= 0) nj += H.cell_b[nbc], nnear_cells++;
           }
       njmaxv[q] = nj;
       njmax_lvl = std::max(njmax_lvl, nj);
-      {
-        // DOFs of the ring inside the proxy surface, bounded by level-start counts
-        int ring = 0, lim2 = dim == 3 ? 2 : 0;
-        for (int dz = -lim2; dz <= lim2; dz++)
-          for (int dy = -2; dy <= 2; dy++)
-            for (int dx = -2; dx <= 2; dx++) {
-              if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) != 2) continue;
-              int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
-              if (nbc >= 0) ring += H.cell_b[nbc];
-            }
-        ring_max = std::max(ring_max, ring);
+      // DOFs of the ring inside the proxy surface, bounded by level-start counts
+      int ring = 0, nring_cells = 0, lim2 = dim == 3 ? 2 : 0;
+      for (int dz = -lim2; dz <= lim2; dz++)
+        for (int dy = -2; dy <= 2; dy++)
+          for (int dx = -2; dx <= 2; dx++) {
+            if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) != 2) continue;
+            int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
+            if (nbc >= 0) ring += H.cell_b[nbc], nring_cells++;
+          }
+      ring_max = std::max(ring_max, ring);
+      const HTree &Tp = F.trees[box_prob[q]];
+      const int node = H.box_node[q];
+      const bool leaf = !(Tp.count[node] > Tp.leaf && Tp.depth[node] < 20);
+      int csum = 0;
+      if (!leaf) {
+        auto it = child_b.find(((int64_t)box_prob[q] << 32) | (uint32_t)node);
+        csum = it == child_b.end() ? 0 : it->second;
       }
-      sz_i64 += (size_t)b + nj;
-      sz_i32 += (size_t)b + 2 * (size_t)nj + b;
-      sz_T += (size_t)b * b / 4 + 1 + (size_t)2 * b * b + 2 * (size_t)nj * b;
+      box_features(&fx[(size_t)q * MLP_NFEAT], dim, F.K.kind, F.eps, F.px, t, b, nj - b, ring, nnear_cells,
+                   nring_cells, leaf, csum);
+    }
+    // reservations: full size (r = b, |J| = level-start count), or from the
+    // proposed ranks plus margins
+    std::vector<int> rres(nb), njres(njmaxv);
+    for (int q = 0; q < nb; q++) rres[q] = H.cell_b[H.box_cell[q]];
+    if (F.mlp) {
+      double tp0 = now_ms();
+      DBuf d_fx, d_pr;
+      upload(d_fx, fx, st);
+      d_pr.alloc(sizeof(float) * std::max(nb, 1), st);
+      mlp_forward(ptr<void>(F.mlp->wbf), ptr<float>(d_fx), nb, ptr<float>(d_pr), st);
+      check_launch("mlp_forward");
+      std::vector<float> pr(nb);
+      CK(cudaMemcpyAsync(pr.data(), d_pr.p, sizeof(float) * nb, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      // proposed k per box; |J| at the box's turn counts the proposed
+      // skeletons of neighbours eliminated in an earlier colour phase and all
+      // level-start DOFs of the others
+      std::vector<int> khat(nb), cell_box(H.ncell, -1);
+      for (int q = 0; q < nb; q++) {
+        const int b = H.cell_b[H.box_cell[q]];
+        rres[q] = reserve_rank(b, pr[q]);
+        khat[q] = propose_k(b, pr[q]);
+        cell_box[H.box_cell[q]] = q;
+      }
+      for (int q = 0; q < nb; q++) {
+        const int c = H.box_cell[q];
+        int64_t nj = khat[q];
+        const int lim = dim == 3 ? 1 : 0;
+        for (int dz = -lim; dz <= lim; dz++)
+          for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+              if (!dx && !dy && !dz) continue;
+              const int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
+              if (nbc < 0) continue;
+              const int qn = cell_box[nbc];
+              nj += (qn >= 0 && H.box_colour[qn] < H.box_colour[q]) ? khat[qn] : H.cell_b[nbc];
+            }
+        njres[q] = (int)std::min<int64_t>(njmaxv[q], nj + std::max<int64_t>(8, nj / 8));
+      }
+      F.prof.host(KC_HOST_LEVEL, now_ms() - tp0);
+    }
+    size_t sz_i64 = 0, sz_i32 = 0, sz_T = 0;
+    for (int q = 0; q < nb; q++) {
+      const size_t b = H.cell_b[H.box_cell[q]], nj = njmaxv[q], rr = rres[q], njr = njres[q];
+      sz_i64 += b + nj;
+      sz_i32 += b + 2 * nj + b;
+      sz_T += b * b / 4 + 1 + 2 * rr * rr + 2 * njr * rr;
     }
     int64_t *p64 = (int64_t *)F.alloc_store(sz_i64 * sizeof(int64_t));
     int *p32 = (int *)F.alloc_store(sz_i32 * sizeof(int));
     T *pT = (T *)F.alloc_store(sz_T * sizeof(T));
+    F.reserved_T += (int64_t)sz_T;
     for (int q = 0; q < nb; q++) {
-      int c = H.box_cell[q], b = H.cell_b[c], nj = njmaxv[q];
+      int c = H.box_cell[q], b = H.cell_b[c], nj = njmaxv[q], rr = rres[q], njr = njres[q];
       FBox<T> fb{};
       fb.cell = c;
       fb.depth = t;
       fb.b = b;
       fb.njmax = nj;
+      fb.rres = rr;
+      fb.njres = njr;
       fb.ids = p64;
       p64 += b;
       fb.J = p64;
@@ -951,14 +1072,25 @@ template <typename T> static void run_factor(Factor<T> &F) {
       fb.Tm = pT;
       pT += (size_t)b * b / 4 + 1;
       fb.LU = pT;
-      pT += (size_t)b * b;
+      pT += (size_t)rr * rr;
       fb.Xi = pT;
-      pT += (size_t)b * b;
+      pT += (size_t)rr * rr;
       fb.E = pT;
-      pT += (size_t)nj * b;
+      pT += (size_t)njr * rr;
       fb.G = pT;
-      pT += (size_t)nj * b;
+      pT += (size_t)njr * rr;
       F.h_boxes.push_back(fb);
+    }
+    F.feats.insert(F.feats.end(), fx.begin(), fx.end());
+    // overflow space for boxes whose rank leaves more than the reservation
+    Overflow<T> ovf{nullptr, nullptr, 0};
+    if (F.mlp) {
+      int64_t cap = (int64_t)(sz_T / 16) + 2 * (2 * (int64_t)H.bmax * H.bmax + 2 * (int64_t)njmax_lvl * H.bmax) + 64;
+      ovf.base = (T *)F.alloc_store((size_t)cap * sizeof(T));
+      ovf.cap = cap;
+      ovf.used = ptr<unsigned long long>(F.d_ovf_used);
+      F.reserved_T += cap;
+      CK(cudaMemsetAsync(F.d_ovf_used.p, 0, sizeof(unsigned long long), st));
     }
     CK(cudaMemcpyAsync(ptr<FBox<T>>(F.d_boxes) + base, F.h_boxes.data() + base, sizeof(FBox<T>) * nb,
                        cudaMemcpyHostToDevice, st));
@@ -995,7 +1127,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       check_launch("id");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_ELIM, st, base + p.first, p.second);
-      launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ptr<T>(gel), el_stride, st,
+      launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ptr<T>(gel), el_stride, ovf, st,
                      ptr<int>(F.d_err));
       check_launch("elim");
       F.prof.end(pi, st);
@@ -1012,12 +1144,25 @@ template <typename T> static void run_factor(Factor<T> &F) {
     CK(cudaMemcpyAsync(ac.data(), D->act_cnt.p, sizeof(int) * H.ncell, cudaMemcpyDeviceToHost, st));
     if (!ai.empty())
       CK(cudaMemcpyAsync(ai.data(), D->act_idx.p, sizeof(int) * ai.size(), cudaMemcpyDeviceToHost, st));
+    unsigned long long ovf_used = 0;
+    if (F.mlp) CK(cudaMemcpyAsync(&ovf_used, F.d_ovf_used.p, sizeof(ovf_used), cudaMemcpyDeviceToHost, st));
     double tw0 = now_ms();
     int e = check_err(F.d_err, st);
     F.prof.host(KC_HOST_WAIT, now_ms() - tw0);
     prof_collect(F);
     if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the LU of a redundant block"};
+    if (e == DERR_CAPACITY) throw Retry{};
     if (e) throw Fail{RSS_ECUDA, "device-side consistency check failed"};
+    F.ovf_used += (int64_t)ovf_used;
+    // ranks of this level: storage they need, and child sizes for the next level's features
+    child_b.clear();
+    for (int q = 0; q < nb; q++) {
+      const FBox<T> &fb = F.h_boxes[base + q];
+      F.used_T += (int64_t)fb.k * fb.r + 2 * (int64_t)fb.r * fb.r + 2 * (int64_t)fb.nj * fb.r;
+      const HTree &Tp = F.trees[box_prob[q]];
+      const int par = Tp.parent[H.box_node[q]];
+      if (par >= 0) child_b[((int64_t)box_prob[q] << 32) | (uint32_t)par] += fb.b;
+    }
     double ta0 = now_ms();
     for (int p = 0; p < np; p++) {
       if (cell_base[p + 1] == cell_base[p]) continue;
@@ -1092,6 +1237,11 @@ template <typename T> static void run_factor(Factor<T> &F) {
 struct rss_factorization {
   uint32_t magic = rss::MAGIC_FACTOR;
   std::unique_ptr<rss::FactorBase> impl;
+};
+
+struct rss_mlp {
+  uint32_t magic = rss::MAGIC_MLP;
+  std::unique_ptr<rss::MlpModel> impl;
 };
 
 using namespace rss;
@@ -1506,6 +1656,11 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
     cudaStream_t st = (cudaStream_t)o.stream;
     std::vector<std::vector<double>> h(nprob);
     for (int p = 0; p < nprob; p++) fetch_points(pts[p], n[p], dim, h[p], st);
+    const MlpModel *mlp = nullptr;
+    if (o.mlp) {
+      if (o.mlp->magic != MAGIC_MLP || !o.mlp->impl) throw Fail{RSS_EINVAL, "rss_factor: bad rank-proposal handle"};
+      mlp = o.mlp->impl.get();
+    }
     std::unique_ptr<rss_factorization> res(new rss_factorization());
     auto setup = [&](auto *F) {
       F->st = st;
@@ -1546,18 +1701,32 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
       F->flags = o.flags;
       run_factor(*F);
     };
-    if (o.prec == RSS_FP64) {
-      auto *F = new Factor<double>();
-      res->impl.reset(F);
-      F->prec = RSS_FP64;
-      F->prof.on = prof_on;
-      setup(F);
-    } else {
-      auto *F = new Factor<float>();
-      res->impl.reset(F);
-      F->prec = RSS_MIXED;
-      F->prof.on = prof_on;
-      setup(F);
+    // A proposal that leaves a level short of storage costs one more run with
+    // full-size reservations; the ranks (and so the factor) are the same.
+    for (int attempt = 0;; attempt++) {
+      try {
+        if (o.prec == RSS_FP64) {
+          auto *F = new Factor<double>();
+          res->impl.reset(F);
+          F->prec = RSS_FP64;
+          F->prof.on = prof_on;
+          F->mlp = attempt == 0 ? mlp : nullptr;
+          F->retries = attempt;
+          setup(F);
+        } else {
+          auto *F = new Factor<float>();
+          res->impl.reset(F);
+          F->prec = RSS_MIXED;
+          F->prof.on = prof_on;
+          F->mlp = attempt == 0 ? mlp : nullptr;
+          F->retries = attempt;
+          setup(F);
+        }
+        break;
+      } catch (const Retry &) {
+        if (attempt > 0) throw Fail{RSS_ECUDA, "storage check failed with full-size reservations"};
+        CK(cudaStreamSynchronize(st));
+      }
     }
     *out = res.release();
   });
@@ -1638,12 +1807,16 @@ rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes) {
     if (!f || !f->impl || !nbytes) throw Fail{RSS_EINVAL, "rss_stats: bad arguments"};
     std::vector<int64_t> s;
     auto fill = [&](const auto &F) {
-      s = {(int64_t)F.h_boxes.size(), F.ntop, F.factor_bytes, F.maxdepth, F.n, F.prec};
+      const int64_t sz = F.prec == RSS_FP64 ? 8 : 4;
+      s = {(int64_t)F.h_boxes.size(), F.ntop, F.factor_bytes, F.maxdepth, F.n, F.prec, F.reserved_T * sz,
+           F.used_T * sz, F.ovf_used * sz, F.retries, F.mlp ? 1 : 0};
       for (const auto &b : F.h_boxes) {
         s.push_back(b.depth);
         s.push_back(b.b);
         s.push_back(b.k);
         s.push_back(b.nj);
+        s.push_back(b.rres);
+        s.push_back(b.njres);
       }
     };
     if (f->impl->prec == RSS_FP64) fill(static_cast<const Factor<double> &>(*f->impl));
@@ -1677,12 +1850,174 @@ rss_status rss_profile(const rss_factorization *f, int reset, double *buf, size_
   });
 }
 
+rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *rank, int64_t nbox) {
+  return guard([&] {
+    if (!f || !f->impl) throw Fail{RSS_EINVAL, "rss_box_features: bad arguments"};
+    auto fill = [&](const auto &F) {
+      if (nbox != (int64_t)F.h_boxes.size()) throw Fail{RSS_EINVAL, "rss_box_features: nbox does not match"};
+      if (nbox > 0 && (!feat || !rank)) throw Fail{RSS_EINVAL, "rss_box_features: bad arguments"};
+      if (nbox > 0) memcpy(feat, F.feats.data(), sizeof(float) * MLP_NFEAT * (size_t)nbox);
+      for (int64_t q = 0; q < nbox; q++) rank[q] = F.h_boxes[q].k;
+    };
+    if (f->impl->prec == RSS_FP64) fill(static_cast<const Factor<double> &>(*f->impl));
+    else fill(static_cast<const Factor<float> &>(*f->impl));
+  });
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): output i of the stream seeded s is
+// the finaliser applied to s + (i + 1) * 0x9E3779B97F4A7C15.
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+rss_status rss_mlp_create(const float *params, uint64_t seed, void *stream, rss_mlp **out) {
+  return guard([&] {
+    if (!out) throw Fail{RSS_EINVAL, "rss_mlp_create: bad arguments"};
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> th(MLP_NPARAM, 0.f);
+    if (params) {
+      memcpy(th.data(), params, sizeof(float) * MLP_NPARAM);
+    } else {
+      // Glorot-uniform weights U(-s, s), s = sqrt(6 / (fan_in + fan_out)); zero biases
+      const int H = MLP_HIDDEN, NF = MLP_NFEAT;
+      struct Blk { int off, n, fin, fout; } blks[] = {
+          {0, H * NF, NF, H}, {H * NF + H, H * H, H, H}, {H * NF + 2 * H + H * H, H * H, H, H},
+          {H * NF + 3 * H + 2 * H * H, H, H, 1}};
+      for (const Blk &b : blks) {
+        const double sc = sqrt(6.0 / (b.fin + b.fout));
+        for (int i = 0; i < b.n; i++) {
+          const double u = (double)(splitmix64_at(seed, (uint64_t)(b.off + i)) >> 11) * 0x1.0p-53;
+          th[b.off + i] = (float)((2.0 * u - 1.0) * sc);
+        }
+      }
+    }
+    std::unique_ptr<rss_mlp> h(new rss_mlp());
+    h->impl.reset(new MlpModel());
+    MlpModel &M = *h->impl;
+    M.st = st;
+    upload(M.theta, th, st);
+    M.wbf.alloc(sizeof(uint16_t) * MLP_NPARAM, st);
+    M.m.alloc(sizeof(float) * MLP_NPARAM, st);
+    M.v.alloc(sizeof(float) * MLP_NPARAM, st);
+    M.grad.alloc(sizeof(float) * MLP_NPARAM, st);
+    M.step.alloc(sizeof(int), st);
+    M.loss.alloc(sizeof(double), st);
+    CK(cudaMemsetAsync(M.m.p, 0, sizeof(float) * MLP_NPARAM, st));
+    CK(cudaMemsetAsync(M.v.p, 0, sizeof(float) * MLP_NPARAM, st));
+    CK(cudaMemsetAsync(M.step.p, 0, sizeof(int), st));
+    mlp_round(ptr<float>(M.theta), M.wbf.p, st);
+    check_launch("mlp_round");
+    CK(cudaStreamSynchronize(st));
+    *out = h.release();
+  });
+}
+
+static const MlpModel &mlp_of(const rss_mlp *m) {
+  if (!m || m->magic != MAGIC_MLP || !m->impl) throw Fail{RSS_EINVAL, "bad rank-proposal handle"};
+  return *m->impl;
+}
+
+rss_status rss_mlp_params(const rss_mlp *m, float *params) {
+  return guard([&] {
+    const MlpModel &M = mlp_of(m);
+    if (!params) throw Fail{RSS_EINVAL, "rss_mlp_params: bad arguments"};
+    CK(cudaMemcpyAsync(params, M.theta.p, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, M.st));
+    CK(cudaStreamSynchronize(M.st));
+  });
+}
+
+rss_status rss_mlp_predict(const rss_mlp *m, const float *X, int64_t n, float *y) {
+  return guard([&] {
+    const MlpModel &M = mlp_of(m);
+    if (n < 0 || (n > 0 && (!X || !y))) throw Fail{RSS_EINVAL, "rss_mlp_predict: bad arguments"};
+    mlp_forward(M.wbf.p, X, n, y, M.st);
+    check_launch("mlp_forward");
+    CK(cudaStreamSynchronize(M.st));
+  });
+}
+
+rss_status rss_mlp_grad(const rss_mlp *m, const float *X, const float *y, int64_t n, float *grad, double *loss) {
+  return guard([&] {
+    const MlpModel &M = mlp_of(m);
+    if (n < 1 || !X || !y || !grad) throw Fail{RSS_EINVAL, "rss_mlp_grad: bad arguments"};
+    const int nblk = mlp_grad_blocks(n);
+    DBuf part, lpart;
+    part.alloc(sizeof(float) * (size_t)nblk * MLP_NPARAM, M.st);
+    lpart.alloc(sizeof(double) * nblk, M.st);
+    mlp_gradient(M.wbf.p, X, y, n, ptr<float>(part), ptr<double>(lpart), grad, ptr<double>(M.loss), M.st);
+    check_launch("mlp_gradient");
+    double l = 0;
+    CK(cudaMemcpyAsync(&l, M.loss.p, sizeof(double), cudaMemcpyDeviceToHost, M.st));
+    CK(cudaStreamSynchronize(M.st));
+    if (loss) *loss = l;
+  });
+}
+
+rss_status rss_mlp_train(rss_mlp *m, const float *X, const float *y, int64_t n, int iters, float lr, double *loss) {
+  return guard([&] {
+    MlpModel &M = const_cast<MlpModel &>(mlp_of(m));
+    if (n < 1 || !X || !y || iters < 0 || !(lr > 0.f)) throw Fail{RSS_EINVAL, "rss_mlp_train: bad arguments"};
+    const int nblk = mlp_grad_blocks(n);
+    DBuf part, lpart;
+    part.alloc(sizeof(float) * (size_t)nblk * MLP_NPARAM, M.st);
+    lpart.alloc(sizeof(double) * nblk, M.st);
+    if (iters > 0) {
+      // one iteration (gradient, reduction, Adam) captured once, replayed
+      cudaStream_t cs = nullptr;
+      cudaEvent_t ev = nullptr;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      auto cleanup = [&] {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (ev) cudaEventDestroy(ev);
+        if (cs) cudaStreamDestroy(cs);
+      };
+      try {
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, M.st));
+        CK(cudaStreamWaitEvent(cs, ev, 0));
+        // kernel attributes are set by an uncaptured gradient call first
+        mlp_gradient(M.wbf.p, X, y, n, ptr<float>(part), ptr<double>(lpart), ptr<float>(M.grad),
+                     ptr<double>(M.loss), cs);
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        mlp_gradient(M.wbf.p, X, y, n, ptr<float>(part), ptr<double>(lpart), ptr<float>(M.grad),
+                     ptr<double>(M.loss), cs);
+        mlp_adam(ptr<float>(M.theta), ptr<float>(M.m), ptr<float>(M.v), ptr<float>(M.grad), M.wbf.p,
+                 ptr<int>(M.step), lr, cs);
+        CK(cudaStreamEndCapture(cs, &g));
+        count_launch(-3);  // the capture launched nothing
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        for (int it = 0; it < iters; it++) CK(cudaGraphLaunch(ge, cs));
+        count_launch(3 * iters);
+        CK(cudaEventRecord(ev, cs));
+        CK(cudaStreamWaitEvent(M.st, ev, 0));
+      } catch (...) {
+        if (cs) cudaStreamSynchronize(cs);
+        cleanup();
+        throw;
+      }
+      CK(cudaStreamSynchronize(M.st));
+      cleanup();
+    }
+    double l = 0;
+    CK(cudaMemcpyAsync(&l, M.loss.p, sizeof(double), cudaMemcpyDeviceToHost, M.st));
+    CK(cudaStreamSynchronize(M.st));
+    if (loss) *loss = l;
+  });
+}
+
 void rss_free(void *handle) {
   if (!handle) return;
-  // both handle types start with a distinct 32-bit tag
+  // every handle type starts with a distinct 32-bit tag
   uint32_t magic = *static_cast<const uint32_t *>(handle);
   if (magic == MAGIC_TREE) delete static_cast<rss_tree *>(handle);
   else if (magic == MAGIC_FACTOR) delete static_cast<rss_factorization *>(handle);
+  else if (magic == MAGIC_MLP) delete static_cast<rss_mlp *>(handle);
 }
 
 }  // extern "C"

@@ -13,7 +13,7 @@ namespace rss {
 constexpr double kPi = 3.14159265358979323846;
 
 // Device error word: the first failing kernel records its code here.
-enum DevErr { DERR_NONE = 0, DERR_NUMERIC = 4, DERR_INTERNAL = 7 };
+enum DevErr { DERR_NONE = 0, DERR_NUMERIC = 4, DERR_INTERNAL = 7, DERR_CAPACITY = 8 };
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 

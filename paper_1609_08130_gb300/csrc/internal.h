@@ -18,6 +18,8 @@ template <typename T> struct FBox {
   int nj;     // |J| = k + |N| (device-written)
   int njmax;  // capacity bound on nj
   int no;     // |O| active DOFs in the ring inside the proxy surface (device-written)
+  int rres;   // |R| and |J| the storage below was reserved for (LU, Xi: rres^2;
+  int njres;  // E, G: njres * rres each); a box that does not fit takes overflow space
   int64_t *ids; // [b] global tree-order ids: S (pivot order) then R
   int *loc;     // [b] local indices in the cell's level layout, same order
   int64_t *J;   // [njmax] global ids of J = [S; N]
@@ -29,6 +31,16 @@ template <typename T> struct FBox {
   T *Xi;        // r x r column-major: X_RR^{-1} = U^{-1} L^{-1} P formed from the LU
   T *E;         // nj x r column-major (ld nj): E = X_JR X_RR^{-1}
   T *G;         // r x nj column-major (ld r):  G = X_RR^{-1} X_RJ
+};
+
+// Overflow space of one level: a box whose rank left r > rres takes
+// 2 r^2 + 2 njmax r elements here (bump allocation); when it is exhausted the
+// box records DERR_CAPACITY and the factorization is redone with full-size
+// reservations.
+template <typename T> struct Overflow {
+  T *base;
+  unsigned long long *used;  // elements taken so far
+  int64_t cap;               // elements available (0: none)
 };
 
 // Device view of one level (depth t): the cells holding active DOFs, their
@@ -80,7 +92,7 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
                cudaStream_t st, int *err);
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
-                 T *scratch, int64_t scratch_stride, cudaStream_t st, int *err);
+                 T *scratch, int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err);
 template <typename T>
 void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_list, int nbox,
                   int njmax, const T *scratch, int64_t scratch_stride, cudaStream_t st);
@@ -125,6 +137,19 @@ void multidot(const double *V, int64_t vstride, int nv, const double *w, int64_t
               double *out, cudaStream_t st);
 void combine(double *y, double alpha, const double *V, int64_t vstride, int nv, const double *coef, int64_t n,
              int nrhs, cudaStream_t st);
+
+// Rank-proposal network (mlp.cu).  Features per box: MLP_NFEAT FP32 values;
+// parameters: MLP_NPARAM (layout in mlp.cu); wbf: their bfloat16 copy.
+constexpr int MLP_NFEAT = 16, MLP_HIDDEN = 64;
+constexpr int MLP_NPARAM = MLP_HIDDEN * MLP_NFEAT + MLP_HIDDEN + 2 * (MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN) +
+                           MLP_HIDDEN + 1;
+void mlp_round(const float *theta, void *wbf, cudaStream_t st);
+void mlp_forward(const void *wbf, const float *X, int64_t n, float *out, cudaStream_t st);
+int mlp_grad_blocks(int64_t n);
+void mlp_gradient(const void *wbf, const float *X, const float *y, int64_t n, float *part, double *lpart, float *grad,
+                  double *loss, cudaStream_t st);
+void mlp_adam(float *theta, float *m, float *v, const float *grad, void *wbf, int *step, float lr,
+              cudaStream_t st);
 
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n = 1);

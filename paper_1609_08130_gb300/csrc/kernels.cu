@@ -1243,14 +1243,46 @@ template int64_t id_region_bytes<double>(int, int);
 // Elimination of the redundant DOFs (Sec. 3.1, Eq. 3.4)
 // ---------------------------------------------------------------------------
 
+// Storage for the box's LU, X_RR^{-1} (r x r each), E and G (nj x r each)
+// (run by one thread, before any of them is written): the host's reservation
+// when the rank the ID found and the box's |J| fit it, else a slice of the
+// level's overflow space.  When neither has room the box records
+// DERR_CAPACITY, eliminates nothing (r = 0, so the Schur launch skips it) and
+// the host redoes the factorization with full-size reservations.
+template <typename T>
+__device__ bool claim_storage(FBox<T> &fb, int nj, const Overflow<T> &ov, int *err) {
+  const int r = fb.r;
+  if (r <= fb.rres && (int64_t)nj * r <= (int64_t)fb.njres * fb.rres) return true;
+  const int64_t need = (2 * (int64_t)r * r + 2 * (int64_t)nj * r + 3) & ~int64_t(3);
+  if (ov.cap > 0) {
+    const unsigned long long o = atomicAdd(ov.used, (unsigned long long)need);
+    if ((int64_t)o + need <= ov.cap) {
+      T *p = ov.base + o;
+      fb.LU = p;
+      p += (int64_t)r * r;
+      fb.Xi = p;
+      p += (int64_t)r * r;
+      fb.E = p;
+      p += (int64_t)nj * r;
+      fb.G = p;
+      return true;
+    }
+  }
+  set_err(err, DERR_CAPACITY);
+  fb.k = fb.b;
+  fb.r = 0;
+  return false;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
-                                             int64_t sstride, int64_t ws_off, int use_smem, int *err) {
+                                             int64_t sstride, int64_t ws_off, int use_smem, Overflow<T> ovf,
+                                             int *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nn;
   __shared__ int64_t s_off_in[27], s_off_out[27];
   __shared__ int s_ld_in[27];
-  __shared__ int s_pivrow;
+  __shared__ int s_pivrow, s_ok;
 
   FBox<T> &fb = boxes[box_list[blockIdx.x]];
   const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
@@ -1288,10 +1320,12 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
     }
     s_nstart[nn] = acc;
     s_nn = nn;
+    s_ok = acc <= fb.njmax ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
   }
   for (int q = tid; q < b; q += NT) sloc[q] = fb.loc[q];
   for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
   __syncthreads();
+  if (!s_ok) return;
   const int nn = s_nn;
   const int nj = s_nstart[nn];
   if (nj > fb.njmax) {
@@ -1548,10 +1582,10 @@ __host__ __device__ inline size_t elim2_smem(int b, int k, int r) {
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
-                                              int64_t sstride, int *err) {
+                                              int64_t sstride, Overflow<T> ovf, int *err) {
   constexpr int CH = ElimChunk<T>::CH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nact[27], s_nn;
+  __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nact[27], s_nn, s_ok;
   __shared__ int64_t s_off_in[27], s_off_out[27];
   __shared__ int s_ld_in[27];
   __shared__ int64_t s_rb[ElimChunk<T>::CH], s_cb[ElimChunk<T>::CH];
@@ -1599,10 +1633,12 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     }
     s_nstart[nn] = acc;
     s_nn = nn;
+    s_ok = acc <= fb.njmax ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
   }
   for (int q = tid; q < b; q += NT) sloc[q] = fb.loc[q];
   for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
   __syncthreads();
+  if (!s_ok) return;
   const int nn = s_nn;
   const int nj = s_nstart[nn];
   if (nj > fb.njmax) {
@@ -1884,7 +1920,7 @@ template int64_t elim_ws_elems<double>(int);
 
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
-                 int64_t scratch_stride, cudaStream_t st, int *err) {
+                 int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err) {
   if (nbox == 0) return;
   const bool force_general = bmax < 0;  // large-box path requested
   if (force_general) bmax = -bmax;
@@ -1895,7 +1931,7 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
     // the warp LU keeps at most four pivot-row entries per lane: r <= 128
     if (worst <= (size_t)(220 << 10) && bmax <= 128) {
       cudaFuncSetAttribute(k_elim2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)worst);
-      k_elim2<T><<<nbox, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, err);
+      k_elim2<T><<<nbox, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, ovf, err);
       count_launch();
       return;
     }
@@ -1908,7 +1944,7 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   const int64_t ws_off = scratch_stride - elim_ws_elems<T>(bmax);
   if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_elim<T><<<nbox, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
-                                                    use_smem ? 1 : 0, err);
+                                                    use_smem ? 1 : 0, ovf, err);
   count_launch();
 }
 
@@ -2547,7 +2583,7 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
                              cudaStream_t,                                                                   \
                              int *);                                                                          \
   template void launch_elim<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, T *, int64_t,            \
-                               cudaStream_t, int *);                                                          \
+                               const Overflow<T> &, cudaStream_t, int *);                                     \
   template void launch_schur<T>(const LevelDev<T> &, const FBox<T> *, const int *, int, int, const T *, int64_t, \
                                 cudaStream_t);                                                                \
   template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "librss.so")
-SOURCES = ["api.cu", "kernels.cu", "refine.cu"]
+SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
             os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), *NVCC_FLAGS, "--threads", "3", "-o", tmp, *srcs]
+    cmd = [_nvcc(), *NVCC_FLAGS, "--threads", "4", "-o", tmp, *srcs]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -60,7 +60,12 @@ class _Kernel(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("n_proxy", C.c_int), ("proxy_radius", C.c_double),
-                ("use_graphs", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int), ("flags", C.c_int)]
+                ("use_graphs", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int), ("flags", C.c_int),
+                ("mlp", C.c_void_p)]
+
+
+MLP_NFEAT = 16
+MLP_NPARAM = 9473
 
 
 _lib = None
@@ -81,6 +86,14 @@ _SIGS = {
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rss_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rss_mlp_create": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "rss_mlp_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rss_mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "rss_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                               C.POINTER(C.c_double)]),
+    "rss_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_float,
+                                C.POINTER(C.c_double)]),
+    "rss_box_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "rss_free": (None, [C.c_void_p]),
     "rss_last_error": (C.c_char_p, []),
     "rss_kernel_launches": (C.c_int64, []),
@@ -186,14 +199,15 @@ class Factorization:
 
     def __init__(self, pts, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
                  weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
-                 profile: bool = False, flags: int = 0):
+                 profile: bool = False, flags: int = 0, mlp=None):
         torch = _torch()
         pts = _dev_f64(pts)
         self.n, self.dim = pts.shape
         self.prec = prec
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
-        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags))
+        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags),
+                        mlp.h if mlp is not None else None)
         h = C.c_void_p()
         _check(lib().rss_factor(C.c_void_p(pts.data_ptr()), self.n, self.dim, _Kernel(kind, diag, weight),
                                 eps, leaf, C.byref(opts), C.byref(h)))
@@ -202,7 +216,7 @@ class Factorization:
     @classmethod
     def batched(cls, pts_list, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
                 weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
-                profile: bool = False, flags: int = 0):
+                profile: bool = False, flags: int = 0, mlp=None):
         """rss_factor_batched: one handle for several independent problems;
         vectors are the problems' vectors concatenated in order."""
         torch = _torch()
@@ -216,7 +230,8 @@ class Factorization:
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
         self._keep = pts
-        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags))
+        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags),
+                        mlp.h if mlp is not None else None)
         arr = (C.c_void_p * len(pts))(*[p.data_ptr() for p in pts])
         ns = (C.c_int64 * len(pts))(*self.sizes)
         h = C.c_void_p()
@@ -271,10 +286,21 @@ class Factorization:
         buf = np.empty(nb.value // 8, dtype=np.int64)
         _check(lib().rss_stats(self.h, C.c_void_p(buf.ctypes.data), C.byref(nb)))
         nbox = int(buf[0])
-        boxes = buf[6:6 + 4 * nbox].reshape(nbox, 4)
+        boxes = buf[11:11 + 6 * nbox].reshape(nbox, 6)
         return dict(nbox=nbox, ntop=int(buf[1]), factor_bytes=int(buf[2]), maxdepth=int(buf[3]),
-                    n=int(buf[4]), prec=int(buf[5]), depth=boxes[:, 0].copy(), b=boxes[:, 1].copy(),
-                    k=boxes[:, 2].copy(), nj=boxes[:, 3].copy())
+                    n=int(buf[4]), prec=int(buf[5]), reserved_bytes=int(buf[6]), used_bytes=int(buf[7]),
+                    overflow_bytes=int(buf[8]), retried=int(buf[9]), proposal=int(buf[10]),
+                    depth=boxes[:, 0].copy(), b=boxes[:, 1].copy(), k=boxes[:, 2].copy(),
+                    nj=boxes[:, 3].copy(), rres=boxes[:, 4].copy(), njres=boxes[:, 5].copy())
+
+    def box_features(self):
+        """rss_box_features: (features (nbox, 16) float32, ranks (nbox,) int32)."""
+        import numpy as np
+        nbox = self.stats()["nbox"]
+        feat = np.zeros((nbox, MLP_NFEAT), dtype=np.float32)
+        rank = np.zeros(nbox, dtype=np.int32)
+        _check(lib().rss_box_features(self.h, C.c_void_p(feat.ctypes.data), C.c_void_p(rank.ctypes.data), nbox))
+        return feat, rank
 
     PROFILE_CLASSES = ["assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve", "permute",
                        "host_tree", "host_level", "host_wait", "refine_op"]
@@ -294,3 +320,67 @@ class Factorization:
         if getattr(self, "h", None) and _lib is not None:
             _lib.rss_free(self.h)
             self.h = None
+
+
+class Mlp:
+    """rss_mlp_*: the rank-proposal network (16 -> 64 -> 64 -> 64 -> 1, tanh),
+    evaluated and trained by the library's CUDA kernels.  params: FP32 host
+    array of MLP_NPARAM values, or None for a seeded Glorot initialisation."""
+
+    def __init__(self, params=None, seed: int = 0, stream=None):
+        import numpy as np
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        h = C.c_void_p()
+        if params is not None:
+            self._init = np.ascontiguousarray(params, dtype=np.float32)
+            if self._init.size != MLP_NPARAM:
+                raise RSSError(RSS_EINVAL, "wrong number of parameters")
+            pp = C.c_void_p(self._init.ctypes.data)
+        else:
+            pp = None
+        _check(lib().rss_mlp_create(pp, C.c_uint64(seed), C.c_void_p(st.cuda_stream), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.rss_free(self.h)
+            self.h = None
+
+    def params(self):
+        import numpy as np
+        out = np.empty(MLP_NPARAM, dtype=np.float32)
+        _check(lib().rss_mlp_params(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    @staticmethod
+    def _f32(t):
+        torch = _torch()
+        t = torch.as_tensor(t)
+        if t.device.type != "cuda":
+            t = t.to("cuda")
+        return t.to(torch.float32).contiguous()
+
+    def predict(self, X):
+        torch = _torch()
+        X = self._f32(X)
+        y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        _check(lib().rss_mlp_predict(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(y.data_ptr())))
+        return y
+
+    def grad(self, X, y):
+        torch = _torch()
+        X, y = self._f32(X), self._f32(y)
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        loss = C.c_double()
+        _check(lib().rss_mlp_grad(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), X.shape[0],
+                                  C.c_void_p(g.data_ptr()), C.byref(loss)))
+        return g, loss.value
+
+    def train(self, X, y, iters: int, lr: float = 1e-3) -> float:
+        X, y = self._f32(X), self._f32(y)
+        loss = C.c_double()
+        _check(lib().rss_mlp_train(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), X.shape[0],
+                                   int(iters), C.c_float(lr), C.byref(loss)))
+        return loss.value
