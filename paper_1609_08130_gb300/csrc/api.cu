@@ -7,7 +7,10 @@
 // tables and pair-block offsets) once the ranks of the previous level are
 // known, and launches one ID / elimination / Schur launch per colour phase.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -96,6 +99,101 @@ template <typename U> static void upload(DBuf &d, const std::vector<U> &h, cudaS
 }
 
 // ---------------------------------------------------------------------------
+// Host worker pool: parallel_for(n, f) runs f(0..n-1) on up to 16 threads
+// created once per process (the calling thread works too).  Calls from
+// several host threads are serialised; an exception in f is rethrown in the
+// caller.
+// ---------------------------------------------------------------------------
+
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool *p = new HostPool();  // never destroyed: workers end with the process
+    return *p;
+  }
+  int size() const { return (int)th_.size() + 1; }
+  void parallel_for(int64_t n, const std::function<void(int64_t)> &f) {
+    if (n <= 0) return;
+    if (n == 1 || th_.empty()) {
+      for (int64_t i = 0; i < n; i++) f(i);
+      return;
+    }
+    std::lock_guard<std::mutex> call(call_m_);
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      job_ = &f;
+      njob_ = n;
+      next_.store(0);
+      err_ = nullptr;
+      active_ = (int)th_.size();
+      gen_++;
+    }
+    cv_.notify_all();
+    run();
+    std::unique_lock<std::mutex> lk(m_);
+    done_cv_.wait(lk, [&] { return active_ == 0; });
+    job_ = nullptr;
+    if (err_) std::rethrow_exception(err_);
+  }
+
+ private:
+  HostPool() {
+    unsigned hw = std::thread::hardware_concurrency();
+    int nt = (int)std::min<unsigned>(hw ? hw : 1, 16) - 1;
+    for (int i = 0; i < nt; i++) {
+      th_.emplace_back([this] { worker(); });
+      th_.back().detach();
+    }
+  }
+  void run() {
+    for (;;) {
+      const int64_t i = next_.fetch_add(1);
+      if (i >= njob_) break;
+      try {
+        (*job_)(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(m_);
+        if (!err_) err_ = std::current_exception();
+      }
+    }
+  }
+  void worker() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+      }
+      run();
+      std::lock_guard<std::mutex> lk(m_);
+      if (--active_ == 0) done_cv_.notify_all();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex m_, call_m_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int64_t)> *job_ = nullptr;
+  int64_t njob_ = 0;
+  std::atomic<int64_t> next_{0};
+  int active_ = 0;
+  uint64_t gen_ = 0;
+  std::exception_ptr err_;
+};
+
+// parallel_for over [0, n) in chunks of at least `grain` indices
+template <typename F> static void parallel_range(int64_t n, int64_t grain, F &&f) {
+  HostPool &P = HostPool::get();
+  const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>((n + grain - 1) / std::max<int64_t>(grain, 1),
+                                                                4 * (int64_t)P.size()));
+  if (nchunk <= 1) {
+    f(0, n);
+    return;
+  }
+  P.parallel_for(nchunk, [&](int64_t c) { f(n * c / nchunk, n * (c + 1) / nchunk); });
+}
+
+// ---------------------------------------------------------------------------
 // Tree
 // ---------------------------------------------------------------------------
 
@@ -146,16 +244,13 @@ static inline uint64_t morton_fast(const int64_t *c, int dim) {
                   : (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
 }
 
-// Stable LSD radix sort of idx by key: 11-bit digits over the used bits,
-// host threads over contiguous chunks (per-thread digit histograms give
-// every thread its own stable output positions), and digit passes in which
-// every key has the same digit are skipped.
+// Stable LSD radix sort of idx by key (11-bit digits over the low key_bits
+// bits; a digit on which all keys agree is skipped).  Large inputs split
+// the histogram and scatter passes over the host pool.
 static void radix_sort_by_key(std::vector<uint64_t> &key, std::vector<int64_t> &idx, int key_bits) {
   const size_t n = key.size();
   const int RB = 11, NBK = 1 << RB;
-  unsigned hw = std::thread::hardware_concurrency();
-  int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
-  if (n < ((size_t)1 << 15)) nt = 1;
+  const int nt = n < ((size_t)1 << 18) ? 1 : std::min(16, HostPool::get().size());
   std::vector<uint64_t> k2(n);
   std::vector<int64_t> i2(n);
   std::vector<size_t> cnt((size_t)nt * NBK);
@@ -165,18 +260,12 @@ static void radix_sort_by_key(std::vector<uint64_t> &key, std::vector<int64_t> &
   };
   for (int sh = 0; sh < key_bits; sh += RB) {
     std::fill(cnt.begin(), cnt.end(), 0);
-    auto hist = [&](int t) {
+    HostPool::get().parallel_for(nt, [&](int64_t t) {
       size_t lo, hi;
-      range(t, lo, hi);
+      range((int)t, lo, hi);
       size_t *c = &cnt[(size_t)t * NBK];
       for (size_t q = lo; q < hi; q++) c[(key[q] >> sh) & (NBK - 1)]++;
-    };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nt; t++) th.emplace_back(hist, t);
-    hist(0);
-    for (auto &x : th) x.join();
-    th.clear();
-    // skip a digit on which all keys agree
+    });
     int used = 0;
     for (int d = 0; d < NBK && used < 2; d++) {
       size_t tot = 0;
@@ -192,19 +281,16 @@ static void radix_sort_by_key(std::vector<uint64_t> &key, std::vector<int64_t> &
         cnt[(size_t)t * NBK + d] = acc;
         acc += c;
       }
-    auto scatter = [&](int t) {
+    HostPool::get().parallel_for(nt, [&](int64_t t) {
       size_t lo, hi;
-      range(t, lo, hi);
+      range((int)t, lo, hi);
       size_t *c = &cnt[(size_t)t * NBK];
       for (size_t q = lo; q < hi; q++) {
         size_t pos = c[(key[q] >> sh) & (NBK - 1)]++;
         k2[pos] = key[q];
         i2[pos] = idx[q];
       }
-    };
-    for (int t = 1; t < nt; t++) th.emplace_back(scatter, t);
-    scatter(0);
-    for (auto &x : th) x.join();
+    });
     key.swap(k2);
     idx.swap(i2);
   }
@@ -215,7 +301,9 @@ struct HTree {
   int dim = 2, leaf = 64, maxdepth = 0;
   int64_t n = 0;
   std::vector<int64_t> perm;
-  std::vector<double> x;  // tree order
+  std::vector<double> x;    // tree order
+  std::vector<uint64_t> key;  // depth-20 Morton key of each DOF, tree order
+  std::vector<int> c20;       // depth-20 integer cell of each DOF (dim per DOF), tree order
   std::vector<int> depth, parent, coord;
   std::vector<int64_t> start, count;
   std::vector<std::vector<int>> level;  // boxes per depth, elimination order
@@ -232,27 +320,45 @@ static int colour_of(const int *c, int dim) {
 
 // Build by sorting on the depth-20 Morton key: a node of depth t is the run
 // of points sharing the key's top dim*t bits; children come out in child
-// index order because x is the lowest bit of each group.
+// index order because x is the lowest bit of each group.  The radix sort
+// uses only the key's top D0 levels (a few below the depth a uniform
+// distribution needs); a node that still has to split at depth D0 re-sorts
+// its range on the full key.  Points of a leaf are finally put back in
+// original order, so the result is that of a full-key sort.
 static void build_tree(HTree &T, const double *pts_host) {
   const int dim = T.dim;
   const int64_t n = T.n;
   const int MAXD = 20;
+  std::vector<uint64_t> kf(n);
+  std::vector<int> cc((size_t)n * dim);
+  parallel_range(n, (int64_t)1 << 16, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; i++) {
+      int64_t c[3] = {0, 0, 0};
+      for (int d = 0; d < dim; d++) {
+        c[d] = cell_at(pts_host[i * dim + d], MAXD);
+        cc[(size_t)i * dim + d] = (int)c[d];
+      }
+      kf[i] = morton_fast(c, dim);
+    }
+  });
+  int D0 = 0;
+  while (D0 < MAXD && ((int64_t)T.leaf << (dim * D0)) < n) D0++;
+  D0 = std::min(MAXD, D0 + 3);
+  const int shift0 = dim * (MAXD - D0);
   std::vector<uint64_t> ks(n);
-  for (int64_t i = 0; i < n; i++) {
-    int64_t c[3] = {0, 0, 0};
-    for (int d = 0; d < dim; d++) c[d] = cell_at(pts_host[i * dim + d], MAXD);
-    ks[i] = morton_fast(c, dim);
-  }
+  for (int64_t i = 0; i < n; i++) ks[i] = kf[i] >> shift0;
   T.perm.resize(n);
   for (int64_t i = 0; i < n; i++) T.perm[i] = i;
-  radix_sort_by_key(ks, T.perm, dim * MAXD);  // stable: equal keys keep index order
+  radix_sort_by_key(ks, T.perm, dim * D0);  // stable: equal keys keep index order
+  for (int64_t p = 0; p < n; p++) ks[p] = kf[T.perm[p]];
   T.maxdepth = 0;
   struct Frame {
     int64_t lo, hi;
     int depth, parent;
     int c[3];
   };
-  std::vector<Frame> stack;
+  std::vector<Frame> stack, ch;
+  std::vector<std::pair<uint64_t, int64_t>> tmp;
   stack.push_back({0, n, 0, -1, {0, 0, 0}});
   while (!stack.empty()) {
     Frame f = stack.back();
@@ -265,9 +371,16 @@ static void build_tree(HTree &T, const double *pts_host) {
     T.count.push_back(f.hi - f.lo);
     T.maxdepth = std::max(T.maxdepth, f.depth);
     if (f.hi - f.lo > T.leaf && f.depth < MAXD) {
+      if (f.depth == D0) {
+        // order below D0 on the full key (ties by original index)
+        tmp.resize(f.hi - f.lo);
+        for (int64_t p = f.lo; p < f.hi; p++) tmp[p - f.lo] = {ks[p], T.perm[p]};
+        std::sort(tmp.begin(), tmp.end());
+        for (int64_t p = f.lo; p < f.hi; p++) ks[p] = tmp[p - f.lo].first, T.perm[p] = tmp[p - f.lo].second;
+      }
       // children: split [lo,hi) by the dim bits of depth f.depth+1
       int shift = dim * (MAXD - f.depth - 1);
-      std::vector<Frame> ch;
+      ch.clear();
       int64_t p = f.lo;
       while (p < f.hi) {
         uint64_t grp = (ks[p] >> shift) & ((1u << dim) - 1);
@@ -285,8 +398,18 @@ static void build_tree(HTree &T, const double *pts_host) {
     }
   }
   T.x.resize((size_t)n * dim);
-  for (int64_t g = 0; g < n; g++)
-    for (int d = 0; d < dim; d++) T.x[g * dim + d] = pts_host[T.perm[g] * dim + d];
+  T.key.resize(n);
+  T.c20.resize((size_t)n * dim);
+  parallel_range(n, (int64_t)1 << 16, [&](int64_t lo, int64_t hi) {
+    for (int64_t g = lo; g < hi; g++) {
+      const int64_t i = T.perm[g];
+      T.key[g] = kf[i];
+      for (int d = 0; d < dim; d++) {
+        T.x[g * dim + d] = pts_host[i * dim + d];
+        T.c20[g * dim + d] = cc[(size_t)i * dim + d];
+      }
+    }
+  });
   T.level.assign(T.maxdepth + 1, {});
   for (int i = 0; i < (int)T.depth.size(); i++) T.level[T.depth[i]].push_back(i);
   {
@@ -358,14 +481,14 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   L.dim = T.dim;
   const int dim = T.dim;
   L.NB = dim == 2 ? 25 : 125;
-  const int bits = std::max(t, 1);
   const size_t na = active.size();
+  // depth-t cell and key of a DOF from its depth-20 ones: floor(v 2^20) >> (20 - t)
+  // = floor(v 2^t) (clamping included), and the Morton key drops dim bits per level
+  const int ksh = dim * (20 - t), csh = 20 - t;
   std::vector<uint64_t> dk(na);
   bool sorted = true;
   for (size_t q = 0; q < na; q++) {
-    int64_t c[3] = {0, 0, 0};
-    for (int d = 0; d < dim; d++) c[d] = cell_at(T.x[active[q] * dim + d], t);
-    dk[q] = morton_fast(c, dim);
+    dk[q] = T.key[active[q]] >> ksh;
     if (q && dk[q] < dk[q - 1]) sorted = false;
   }
   std::vector<int> cid(na);
@@ -393,7 +516,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
     for (size_t q = 0; q < na; q++) {
       int c = cid[q];
       if (fill[c] == L.cell_dof_off[c])
-        for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = (int)cell_at(T.x[active[q] * dim + d], t);
+        for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = T.c20[active[q] * dim + d] >> csh;
       L.cell_dofs[fill[c]++] = active[q];
     }
   }
@@ -764,21 +887,26 @@ template <typename T> static void run_factor(Factor<T> &F) {
     std::vector<float> off((size_t)3 * std::max<int64_t>(n, 1), 0.f);
     const double D = ldexp(1.0, -20);
     if (np > 1) wd.resize(std::max<int64_t>(n, 1));
-    for (int p = 0; p < np; p++) {
+    // split by problem and, within large problems, by DOF ranges
+    std::vector<std::pair<int, int64_t>> chunks;
+    for (int p = 0; p < np; p++)
+      for (int64_t g0 = 0; g0 < F.trees[p].n; g0 += (int64_t)1 << 16) chunks.push_back({p, g0});
+    HostPool::get().parallel_for((int64_t)chunks.size(), [&](int64_t ci) {
+      const int p = chunks[ci].first;
       const HTree &Tp = F.trees[p];
-      const int64_t o = F.pdof[p];
-      for (int64_t g = 0; g < Tp.n; g++) {
+      const int64_t o = F.pdof[p], g1 = std::min<int64_t>(Tp.n, chunks[ci].second + ((int64_t)1 << 16));
+      for (int64_t g = chunks[ci].second; g < g1; g++) {
         perm[o + g] = o + Tp.perm[g];
         for (int d = 0; d < dim; d++) {
-          double v = Tp.x[g * dim + d];
+          const double v = Tp.x[g * dim + d];
+          const int c = Tp.c20[g * dim + d];
           x[(o + g) * dim + d] = v;
-          int64_t c = cell_at(v, 20);
-          cell[3 * (o + g) + d] = (int)c;
+          cell[3 * (o + g) + d] = c;
           off[3 * (o + g) + d] = (float)(v - (double)c * D);
         }
         if (np > 1) wd[o + g] = F.pw[p];
       }
-    }
+    });
     upload(F.d_x, x, st);
     upload(F.d_perm, perm, st);
     upload(F.d_cell, cell, st);
@@ -852,20 +980,36 @@ template <typename T> static void run_factor(Factor<T> &F) {
   bool have_prev = false;
 
   auto assemble_pairs = [&](const HLevel &H, DLevel<T> &D, const LevelDev<T> *prev) {
-    std::vector<int64_t> row_off, col_off, out_off;
-    std::vector<int> nrow, ncol;
+    // one entry per (cell, neighbour at distance <= 2), in cell order
+    std::vector<int64_t> first(H.ncell + 1, 0);
     int64_t maxblk = 0;
-    for (int c = 0; c < H.ncell; c++)
+    for (int c = 0; c < H.ncell; c++) {
+      int cnt = 0;
       for (int o = 0; o < H.NB; o++) {
-        int nb = H.cell_nbr[(size_t)c * H.NB + o];
+        const int nb = H.cell_nbr[(size_t)c * H.NB + o];
         if (nb < 0) continue;
-        row_off.push_back(H.cell_dof_off[c]);
-        col_off.push_back(H.cell_dof_off[nb]);
-        out_off.push_back(H.pair_off[(size_t)c * H.NB + o]);
-        nrow.push_back(H.cell_b[c]);
-        ncol.push_back(H.cell_b[nb]);
+        cnt++;
         maxblk = std::max(maxblk, (int64_t)H.cell_b[c] * H.cell_b[nb]);
       }
+      first[c + 1] = first[c] + cnt;
+    }
+    const int64_t npair = first[H.ncell];
+    std::vector<int64_t> row_off(npair), col_off(npair), out_off(npair);
+    std::vector<int> nrow(npair), ncol(npair);
+    parallel_range(H.ncell, 2048, [&](int64_t c0, int64_t c1) {
+      int64_t e = first[c0];
+      for (int64_t c = c0; c < c1; c++)
+        for (int o = 0; o < H.NB; o++) {
+          const int nb = H.cell_nbr[(size_t)c * H.NB + o];
+          if (nb < 0) continue;
+          row_off[e] = H.cell_dof_off[c];
+          col_off[e] = H.cell_dof_off[nb];
+          out_off[e] = H.pair_off[(size_t)c * H.NB + o];
+          nrow[e] = H.cell_b[c];
+          ncol[e] = H.cell_b[nb];
+          e++;
+        }
+    });
     DBuf a, b2, c2, d2, e2;
     upload(a, row_off, st);
     upload(b2, col_off, st);
@@ -891,12 +1035,35 @@ template <typename T> static void run_factor(Factor<T> &F) {
     H.NB = dim == 2 ? 25 : 125;
     std::vector<int> box_prob;
     std::vector<int> cell_base(np + 1, 0);
-    for (int p = 0; p < np; p++) {
-      cell_base[p] = H.ncell;
-      if (F.trees[p].maxdepth < t || active[p].empty()) continue;
-      HLevel Hp = build_level(F.trees[p], t, active[p]);
-      append_level(H, Hp, F.pdof[p], box_prob, p);
+    if (np == 1) {
+      if (F.trees[0].maxdepth >= t && !active[0].empty()) {
+        H = build_level(F.trees[0], t, active[0]);
+        box_prob.assign(H.box_cell.size(), 0);
+      }
+    } else {
+      std::vector<HLevel> Hs(np);
+      HostPool::get().parallel_for(np, [&](int64_t p) {
+        if (F.trees[p].maxdepth >= t && !active[p].empty()) Hs[p] = build_level(F.trees[p], t, active[p]);
+      });
+      size_t nc = 0, nd = 0, nbx = 0;
+      for (int p = 0; p < np; p++) nc += Hs[p].ncell, nd += Hs[p].cell_dofs.size(), nbx += Hs[p].box_cell.size();
+      H.cell_b.reserve(nc);
+      H.cell_dof_off.reserve(nc + 1);
+      H.cell_coord.reserve(3 * nc);
+      H.cell_nbr.reserve(nc * H.NB);
+      H.pair_off.reserve(nc * H.NB);
+      H.cell_dofs.reserve(nd);
+      H.box_cell.reserve(nbx);
+      H.box_node.reserve(nbx);
+      H.box_colour.reserve(nbx);
+      box_prob.reserve(nbx);
+      for (int p = 0; p < np; p++) {
+        cell_base[p] = H.ncell;
+        if (Hs[p].ncell == 0) continue;
+        append_level(H, Hs[p], F.pdof[p], box_prob, p);
+      }
     }
+    if (np == 1) cell_base[0] = 0;
     cell_base[np] = H.ncell;
     if (H.cell_dof_off.empty()) H.cell_dof_off.push_back(0);
     if (H.box_cell.empty()) continue;  // no problem has boxes at this depth
@@ -925,26 +1092,25 @@ template <typename T> static void run_factor(Factor<T> &F) {
     upload(D->cell_coord, H.cell_coord, st);
     upload(D->cell_nbr, H.cell_nbr, st);
     upload(D->pair_off, H.pair_off, st);
-    {
-      std::vector<int> ac(H.cell_b), ai(H.cell_dofs.size());
-      for (int c = 0; c < H.ncell; c++)
-        for (int q = 0; q < H.cell_b[c]; q++) ai[H.cell_dof_off[c] + q] = q;
-      upload(D->act_cnt, ac, st);
-      upload(D->act_idx, ai, st);
-    }
     D->pool.alloc((size_t)H.pool_elems * sizeof(T), st);
-    // per-DOF maps of this level
+    // active lists (every level-start DOF active, local order) and the
+    // per-DOF maps of this level (-1 for DOFs in no cell), built on the device
     int slot = have_prev ? 1 - prev_slot : 0;
     {
-      std::vector<int> dc(std::max<int64_t>(n, 1), -1), dl(std::max<int64_t>(n, 1), -1);
-      for (int c = 0; c < H.ncell; c++)
-        for (int q = 0; q < H.cell_b[c]; q++) {
-          int64_t g = H.cell_dofs[H.cell_dof_off[c] + q];
-          dc[g] = c;
-          dl[g] = q;
-        }
-      upload(d_dof_cell[slot], dc, st);
-      upload(d_dof_loc[slot], dl, st);
+      const size_t nd = std::max<size_t>(H.cell_dofs.size(), 1), nn = (size_t)std::max<int64_t>(n, 1);
+      D->act_cnt.alloc(sizeof(int) * std::max(H.ncell, 1), st);
+      D->act_idx.alloc(sizeof(int) * nd, st);
+      if (H.ncell > 0)
+        CK(cudaMemcpyAsync(D->act_cnt.p, D->cell_b.p, sizeof(int) * H.ncell, cudaMemcpyDeviceToDevice, st));
+      if (d_dof_cell[slot].bytes < sizeof(int) * nn) {
+        d_dof_cell[slot].alloc(sizeof(int) * nn, st);
+        d_dof_loc[slot].alloc(sizeof(int) * nn, st);
+      }
+      CK(cudaMemsetAsync(d_dof_cell[slot].p, 0xFF, sizeof(int) * nn, st));
+      CK(cudaMemsetAsync(d_dof_loc[slot].p, 0xFF, sizeof(int) * nn, st));
+      launch_level_maps(H.ncell, ptr<int64_t>(D->cell_dof_off), ptr<int64_t>(D->cell_dofs), ptr<int>(D->act_idx),
+                        ptr<int>(d_dof_cell[slot]), ptr<int>(d_dof_loc[slot]), st);
+      check_launch("level_maps");
     }
     LevelDev<T> view = D->view(H, ptr<int>(d_dof_cell[slot]), ptr<int>(d_dof_loc[slot]));
     if (have_prev) {
@@ -960,9 +1126,10 @@ template <typename T> static void run_factor(Factor<T> &F) {
     const int base = (int)F.h_boxes.size();
     const int nb = (int)H.box_cell.size();
     int njmax_lvl = 0, ring_max = 0;
-    std::vector<int> njmaxv(nb);
+    std::vector<int> njmaxv(nb), ringv(nb);
     std::vector<float> fx((size_t)nb * MLP_NFEAT, 0.f);
-    for (int q = 0; q < nb; q++) {
+    parallel_range(nb, 1024, [&](int64_t q0, int64_t q1) {
+    for (int64_t q = q0; q < q1; q++) {
       int c = H.box_cell[q], b = H.cell_b[c];
       int nj = b, nnear_cells = 0;
       int lim = dim == 3 ? 1 : 0;
@@ -974,7 +1141,6 @@ template <typename T> static void run_factor(Factor<T> &F) {
             if (nbc >= 0) nj += H.cell_b[nbc], nnear_cells++;
           }
       njmaxv[q] = nj;
-      njmax_lvl = std::max(njmax_lvl, nj);
       // DOFs of the ring inside the proxy surface, bounded by level-start counts
       int ring = 0, nring_cells = 0, lim2 = dim == 3 ? 2 : 0;
       for (int dz = -lim2; dz <= lim2; dz++)
@@ -984,7 +1150,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
             int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
             if (nbc >= 0) ring += H.cell_b[nbc], nring_cells++;
           }
-      ring_max = std::max(ring_max, ring);
+      ringv[q] = ring;
       const HTree &Tp = F.trees[box_prob[q]];
       const int node = H.box_node[q];
       const bool leaf = !(Tp.count[node] > Tp.leaf && Tp.depth[node] < 20);
@@ -996,6 +1162,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
       box_features(&fx[(size_t)q * MLP_NFEAT], dim, F.K.kind, F.eps, F.px, t, b, nj - b, ring, nnear_cells,
                    nring_cells, leaf, csum);
     }
+    });
+    for (int q = 0; q < nb; q++) njmax_lvl = std::max(njmax_lvl, njmaxv[q]), ring_max = std::max(ring_max, ringv[q]);
     // reservations: full size (r = b, |J| = level-start count), or from the
     // proposed ranks plus margins
     std::vector<int> rres(nb), njres(njmaxv);
@@ -1164,15 +1332,15 @@ template <typename T> static void run_factor(Factor<T> &F) {
       if (par >= 0) child_b[((int64_t)box_prob[q] << 32) | (uint32_t)par] += fb.b;
     }
     double ta0 = now_ms();
-    for (int p = 0; p < np; p++) {
-      if (cell_base[p + 1] == cell_base[p]) continue;
+    HostPool::get().parallel_for(np, [&](int64_t p) {
+      if (cell_base[p + 1] == cell_base[p]) return;
       std::vector<int64_t> &act = active[p];
       act.clear();
       for (int c = cell_base[p]; c < cell_base[p + 1]; c++)
         for (int q = 0; q < ac[c]; q++)
           act.push_back(H.cell_dofs[H.cell_dof_off[c] + ai[H.cell_dof_off[c] + q]] - F.pdof[p]);
       if (!std::is_sorted(act.begin(), act.end())) std::sort(act.begin(), act.end());
-    }
+    });
     F.prof.host(KC_HOST_LEVEL, now_ms() - ta0);
     prevD = std::move(D);
     prevH = std::move(H);

@@ -110,6 +110,10 @@ void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, cons
 template <typename T>
 void launch_lu_batched(T *LU, const int64_t *loff, int *piv, const int64_t *toff, const int *tn, int nprob,
                        cudaStream_t st, int *err);
+// Per level: act_idx[j] = local index of level DOF j in its cell; for each
+// level DOF g: dof_cell[g] = its cell, dof_loc[g] = its local index.
+void launch_level_maps(int ncell, const int64_t *cell_dof_off, const int64_t *cell_dofs, int *act_idx, int *dof_cell,
+                       int *dof_loc, cudaStream_t st);
 template <typename T> int64_t id_region_bytes(int b, int PR);
 template <typename T> int64_t elim_ws_elems(int bmax);
 template <typename T>

@@ -87,6 +87,30 @@ void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, con
   k_assemble<T><<<grid, NT, 0, st>>>(L, out, pv, prev ? 1 : 0, P, K); count_launch();
 }
 
+// One warp per cell: local indices of its level DOFs and the per-DOF maps.
+__global__ void k_level_maps(int ncell, const int64_t *__restrict__ off, const int64_t *__restrict__ dofs,
+                             int *act_idx, int *dof_cell, int *dof_loc) {
+  const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const int64_t o = off[c], e = off[c + 1];
+  for (int64_t j = o + lane; j < e; j += 32) {
+    const int q = (int)(j - o);
+    const int64_t g = dofs[j];
+    act_idx[j] = q;
+    dof_cell[g] = c;
+    dof_loc[g] = q;
+  }
+}
+
+void launch_level_maps(int ncell, const int64_t *cell_dof_off, const int64_t *cell_dofs, int *act_idx, int *dof_cell,
+                       int *dof_loc, cudaStream_t st) {
+  if (ncell <= 0) return;
+  const int64_t threads = (int64_t)ncell * 32;
+  k_level_maps<<<(unsigned)((threads + NT - 1) / NT), NT, 0, st>>>(ncell, cell_dof_off, cell_dofs, act_idx, dof_cell,
+                                                                 dof_loc);
+  count_launch();
+}
+
 // ---------------------------------------------------------------------------
 // ID: Householder reduction of the proxy-compressed far-field rows, then
 // greedy column-pivoted QR of the b x b triangle.
