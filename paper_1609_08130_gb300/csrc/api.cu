@@ -51,12 +51,20 @@ static void check_launch(const char *what) {
 // Device memory: one library-private stream-ordered pool.
 // ---------------------------------------------------------------------------
 
-static cudaMemPool_t lib_pool() {
-  static cudaMemPool_t pool = nullptr;
-  static int dev_of_pool = -1;
+// Library-private stream-ordered memory pools, per device and kind: kind 0
+// for long-lived data, kind 1 for the large per-level transients (pair-block
+// pools, phase scratch) so that their blocks are reused whole from one
+// factorization to the next instead of being split by small allocations.
+// Freed memory stays in the pool (release threshold: never).
+static cudaMemPool_t lib_pool(int kind = 0) {
+  static std::mutex m;
+  static cudaMemPool_t pools[64][2] = {};
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  if (!pool || dev_of_pool != dev) {
+  if (dev < 0 || dev >= 64) throw Fail{RSS_ECUDA, "device index out of range"};
+  std::lock_guard<std::mutex> lk(m);
+  cudaMemPool_t &pool = pools[dev][kind];
+  if (!pool) {
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -64,7 +72,6 @@ static cudaMemPool_t lib_pool() {
     CK(cudaMemPoolCreate(&pool, &props));
     uint64_t thr = UINT64_MAX;
     CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-    dev_of_pool = dev;
   }
   return pool;
 }
@@ -77,12 +84,12 @@ struct DBuf {
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
   ~DBuf() { release(); }
-  void alloc(size_t nb, cudaStream_t s) {
+  void alloc(size_t nb, cudaStream_t s, int kind = 0) {
     release();
     st = s;
     bytes = nb;
     if (nb == 0) nb = 16;
-    CK(cudaMallocFromPoolAsync(&p, nb, lib_pool(), s));
+    CK(cudaMallocFromPoolAsync(&p, nb, lib_pool(kind), s));
   }
   void release() {
     if (p) cudaFreeAsync(p, st);
@@ -93,9 +100,60 @@ struct DBuf {
 
 template <typename U> static inline U *ptr(const DBuf &b) { return static_cast<U *>(b.p); }
 
+// Make d hold at least `bytes` (contents are not kept).
+static void grow(DBuf &d, size_t bytes, cudaStream_t st, int kind = 0) {
+  if (!d.p || d.bytes < bytes) d.alloc(bytes, st, kind);
+}
+
+// Host-to-device copies go through a per-thread pinned staging ring, so they
+// are asynchronous DMA copies instead of pageable ones.  A region is reused
+// only after the copies that read it have completed (an event per copy).
+struct Staging {
+  char *buf = nullptr;
+  size_t cap = 0, off = 0;
+  std::vector<cudaEvent_t> inflight, spare;
+  void wait_all() {
+    for (cudaEvent_t e : inflight) {
+      cudaEventSynchronize(e);
+      spare.push_back(e);
+    }
+    inflight.clear();
+    off = 0;
+  }
+};
+static thread_local Staging g_stage;
+
+static void staged_h2d(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  Staging &S = g_stage;
+  const size_t need = (bytes + 255) & ~size_t(255);
+  if (need > S.cap) {
+    S.wait_all();
+    if (S.buf) cudaFreeHost(S.buf);
+    S.buf = nullptr;
+    S.cap = 0;
+    size_t cap = std::max<size_t>((size_t)16 << 20, 2 * need);
+    CK(cudaHostAlloc((void **)&S.buf, cap, cudaHostAllocDefault));
+    S.cap = cap;
+  }
+  if (S.off + need > S.cap) S.wait_all();
+  memcpy(S.buf + S.off, src, bytes);
+  CK(cudaMemcpyAsync(dst, S.buf + S.off, bytes, cudaMemcpyHostToDevice, st));
+  cudaEvent_t e;
+  if (S.spare.empty()) {
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  } else {
+    e = S.spare.back();
+    S.spare.pop_back();
+  }
+  CK(cudaEventRecord(e, st));
+  S.inflight.push_back(e);
+  S.off += need;
+}
+
 template <typename U> static void upload(DBuf &d, const std::vector<U> &h, cudaStream_t st) {
   d.alloc(h.size() * sizeof(U), st);
-  if (!h.empty()) CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice, st));
+  if (!h.empty()) staged_h2d(d.p, h.data(), h.size() * sizeof(U), st);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,14 +436,17 @@ static void build_tree(HTree &T, const double *pts_host) {
         std::sort(tmp.begin(), tmp.end());
         for (int64_t p = f.lo; p < f.hi; p++) ks[p] = tmp[p - f.lo].first, T.perm[p] = tmp[p - f.lo].second;
       }
-      // children: split [lo,hi) by the dim bits of depth f.depth+1
-      int shift = dim * (MAXD - f.depth - 1);
+      // children: split [lo,hi) by the dim bits of depth f.depth+1 (the keys
+      // of the range are sorted on those bits: binary search each boundary)
+      const int shift = dim * (MAXD - f.depth - 1);
+      const uint64_t mask = (1u << dim) - 1;
       ch.clear();
       int64_t p = f.lo;
       while (p < f.hi) {
-        uint64_t grp = (ks[p] >> shift) & ((1u << dim) - 1);
-        int64_t q = p;
-        while (q < f.hi && ((ks[q] >> shift) & ((1u << dim) - 1)) == grp) q++;
+        const uint64_t grp = (ks[p] >> shift) & mask;
+        const int64_t q = std::upper_bound(ks.begin() + p, ks.begin() + f.hi, grp,
+                                           [&](uint64_t g, uint64_t k) { return g < ((k >> shift) & mask); }) -
+                          ks.begin();
         Frame cf{p, q, f.depth + 1, id, {0, 0, 0}};
         for (int d = 0; d < dim; d++) cf.c[d] = 2 * f.c[d] + (int)((grp >> d) & 1);
         ch.push_back(cf);
@@ -1025,6 +1086,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
   };
 
   std::unordered_map<int64_t, int> child_b;  // (problem, node) -> sum of its children's b
+  DBuf gid, gel;                             // per-phase ID and elimination scratch, grown as needed
   if (F.mlp) F.d_ovf_used.alloc(sizeof(unsigned long long), st);
   for (int t = F.maxdepth; t >= 2; t--) {
     double th0 = now_ms();
@@ -1092,7 +1154,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     upload(D->cell_coord, H.cell_coord, st);
     upload(D->cell_nbr, H.cell_nbr, st);
     upload(D->pair_off, H.pair_off, st);
-    D->pool.alloc((size_t)H.pool_elems * sizeof(T), st);
+    D->pool.alloc((size_t)H.pool_elems * sizeof(T), st, 1);
     // active lists (every level-start DOF active, local order) and the
     // per-DOF maps of this level (-1 for DOFs in no cell), built on the device
     int slot = have_prev ? 1 - prev_slot : 0;
@@ -1260,8 +1322,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       F.reserved_T += cap;
       CK(cudaMemsetAsync(F.d_ovf_used.p, 0, sizeof(unsigned long long), st));
     }
-    CK(cudaMemcpyAsync(ptr<FBox<T>>(F.d_boxes) + base, F.h_boxes.data() + base, sizeof(FBox<T>) * nb,
-                       cudaMemcpyHostToDevice, st));
+    staged_h2d(ptr<FBox<T>>(F.d_boxes) + base, F.h_boxes.data() + base, sizeof(FBox<T>) * nb, st);
     // colour phases
     std::vector<int> list(nb);
     for (int q = 0; q < nb; q++) list[q] = base + q;
@@ -1281,11 +1342,10 @@ template <typename T> static void run_factor(Factor<T> &F) {
     int PR = H.bmax <= 80 ? 128 : 64;
     int64_t idb = id_region_bytes<T>(H.bmax, PR);
     bool id_smem = idb <= 200 * 1024 && !large;
-    DBuf gid, gel;
     int64_t id_stride = (idb + sizeof(T) - 1) / sizeof(T) + 32;
-    if (!id_smem) gid.alloc((size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st);
+    if (!id_smem) grow(gid, (size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
     int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32 + elim_ws_elems<T>(H.bmax);
-    gel.alloc((size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st);
+    grow(gel, (size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
     F.prof.host(KC_HOST_LEVEL, now_ms() - th0);
     for (auto &p : ph) {
       const int *bl = ptr<int>(d_list) + p.first;
@@ -1545,7 +1605,7 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
     CK(cudaStreamSynchronize(st));
   };
   auto comb = [&](double *y, double alpha, const double *Vb, int nv, const std::vector<double> &coef) {
-    CK(cudaMemcpyAsync(dc, coef.data(), sizeof(double) * nv * nrhs, cudaMemcpyHostToDevice, st));
+    staged_h2d(dc, coef.data(), sizeof(double) * nv * nrhs, st);
     combine(y, alpha, Vb, nn, nv, dc, n, nrhs, st);
     check_launch("combine");
   };

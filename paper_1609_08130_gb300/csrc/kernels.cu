@@ -2351,12 +2351,186 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
   }
 }
 
+// Solve sweeps (Eq. 3.11) for nrhs = NR <= 4 right-hand sides held in
+// registers; one CTA per box.  The large per-box matrices (E: nj x r,
+// G: r x nj, X_RR^{-1}: r x r) are read once, coalesced, with eight
+// independent loads in flight per thread; T (k x r) by one warp per output.
+template <typename T, int NR>
+__global__ void __launch_bounds__(NT) k_sweep_solve(int mode, const FBox<T> *boxes, int first, T *v) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const FBox<T> &fb = boxes[first + blockIdx.x];
+  const int k = fb.k, r = fb.r, nj = fb.nj;
+  if (r == 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nch = r >= NT ? 1 : NT / r;  // groups splitting the inner index of the r-row products
+  T *vS = reinterpret_cast<T *>(smem_raw);  // k x NR
+  T *vR = vS + (size_t)k * NR;               // r x NR
+  T *tmp = vR + (size_t)r * NR;              // r x NR
+  T *part = tmp + (size_t)r * NR;            // nch x r x NR partial sums
+  const int64_t *S = fb.ids, *Rr = fb.ids + k;
+  for (int e = tid; e < k * NR; e += NT) vS[e] = v[S[e / NR] * NR + e % NR];
+  for (int e = tid; e < r * NR; e += NT) vR[e] = v[Rr[e / NR] * NR + e % NR];
+  __syncthreads();
+  if (mode == SWEEP_SOLVE_FWD) {
+    // U_T: tmp = v_R - T^T v_S (one warp per output, lanes over S)
+    for (int ri = warp; ri < r; ri += NT / 32) {
+      const T *tc = fb.Tm + (int64_t)ri * k;
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] = (T)0;
+      for (int q = lane; q < k; q += 32) {
+        const T tq = tc[q];
+#pragma unroll
+        for (int c = 0; c < NR; c++) acc[c] += tq * vS[q * NR + c];
+      }
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] = warp_sum(acc[c]);
+      if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NR; c++) tmp[ri * NR + c] = vR[ri * NR + c] - acc[c];
+    }
+    __syncthreads();
+    // L: v_J -= E tmp (one thread per row of E)
+    for (int a = tid; a < nj; a += NT) {
+      const T *ea = fb.E + a;
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] = (T)0;
+      int ri = 0;
+      for (; ri + 8 <= r; ri += 8) {
+        T ev[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) ev[u] = __ldg(ea + (int64_t)(ri + u) * nj);
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+#pragma unroll
+          for (int c = 0; c < NR; c++) acc[c] += ev[u] * tmp[(ri + u) * NR + c];
+      }
+      for (; ri < r; ri++) {
+        const T ev = __ldg(ea + (int64_t)ri * nj);
+#pragma unroll
+        for (int c = 0; c < NR; c++) acc[c] += ev * tmp[ri * NR + c];
+      }
+      T *vg = v + fb.J[a] * NR;
+#pragma unroll
+      for (int c = 0; c < NR; c++) vg[c] -= acc[c];
+    }
+    // D^{-1} on R: x_R = X_RR^{-1} tmp (rows split over nch groups of columns)
+    if (tid < nch * r) {
+      const int i = tid % r, g = tid / r;
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] = (T)0;
+      int l = g;
+      for (; l + 3 * nch < r; l += 4 * nch) {
+        T xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) xv[u] = __ldg(fb.Xi + i + (int64_t)(l + u * nch) * r);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int c = 0; c < NR; c++) acc[c] += xv[u] * tmp[(l + u * nch) * NR + c];
+      }
+      for (; l < r; l += nch) {
+        const T xv = __ldg(fb.Xi + i + (int64_t)l * r);
+#pragma unroll
+        for (int c = 0; c < NR; c++) acc[c] += xv * tmp[l * NR + c];
+      }
+#pragma unroll
+      for (int c = 0; c < NR; c++) part[((size_t)g * r + i) * NR + c] = acc[c];
+    }
+    __syncthreads();
+    for (int i = tid; i < r; i += NT) {
+      T *vg = v + Rr[i] * NR;
+#pragma unroll
+      for (int c = 0; c < NR; c++) {
+        T s = (T)0;
+        for (int g = 0; g < nch; g++) s += part[((size_t)g * r + i) * NR + c];
+        vg[c] = s;
+      }
+    }
+  } else {
+    // U: v_R -= G v_J (rows of G split over nch groups of J)
+    if (tid < nch * r) {
+      const int ri = tid % r, g = tid / r;
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] = (T)0;
+      int a = g;
+      for (; a + 3 * nch < nj; a += 4 * nch) {
+        T gv[4];
+        int64_t ja[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          gv[u] = __ldg(fb.G + ri + (int64_t)(a + u * nch) * r);
+          ja[u] = fb.J[a + u * nch];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int c = 0; c < NR; c++) acc[c] += gv[u] * v[ja[u] * NR + c];
+      }
+      for (; a < nj; a += nch) {
+        const T gv = __ldg(fb.G + ri + (int64_t)a * r);
+        const int64_t ja = fb.J[a];
+#pragma unroll
+        for (int c = 0; c < NR; c++) acc[c] += gv * v[ja * NR + c];
+      }
+#pragma unroll
+      for (int c = 0; c < NR; c++) part[((size_t)g * r + ri) * NR + c] = acc[c];
+    }
+    __syncthreads();
+    for (int i = tid; i < r; i += NT)
+#pragma unroll
+      for (int c = 0; c < NR; c++) {
+        T s = (T)0;
+        for (int g = 0; g < nch; g++) s += part[((size_t)g * r + i) * NR + c];
+        vR[i * NR + c] -= s;
+      }
+    __syncthreads();
+    // L_T: v_S -= T v_R (one thread per skeleton DOF); v_R written back
+    for (int q = tid; q < k; q += NT) {
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] = (T)0;
+      for (int ri = 0; ri < r; ri++) {
+        const T tv = __ldg(fb.Tm + q + (int64_t)ri * k);
+#pragma unroll
+        for (int c = 0; c < NR; c++) acc[c] += tv * vR[ri * NR + c];
+      }
+      T *vg = v + S[q] * NR;
+#pragma unroll
+      for (int c = 0; c < NR; c++) vg[c] = vS[q * NR + c] - acc[c];
+    }
+    for (int e = tid; e < r * NR; e += NT) v[Rr[e / NR] * NR + e % NR] = vR[e];
+  }
+}
+
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax, int njmax,
                   cudaStream_t st) {
   if (count == 0) return;
   const bool force_general = njmax < 0;  // large-box path requested
   if (force_general) njmax = -njmax;
+  if ((mode == SWEEP_SOLVE_FWD || mode == SWEEP_SOLVE_BWD) && nrhs <= 4 && !force_general) {
+    const size_t smem = ((size_t)4 * bmax + NT) * nrhs * sizeof(T) + 64;
+    if (smem <= (size_t)(200 << 10)) {
+#define RSS_SWEEP_NR(NRV)                                                                          \
+  case NRV:                                                                                       \
+    cudaFuncSetAttribute(k_sweep_solve<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_sweep_solve<T, NRV><<<count, NT, smem, st>>>(mode, boxes, first, v);                         \
+    break;
+      switch (nrhs) {
+        RSS_SWEEP_NR(1)
+        RSS_SWEEP_NR(2)
+        RSS_SWEEP_NR(3)
+        RSS_SWEEP_NR(4)
+      }
+#undef RSS_SWEEP_NR
+      count_launch();
+      return;
+    }
+  }
   size_t smem = ((size_t)3 * bmax + (size_t)njmax) * nrhs * sizeof(T) + 64;
   int jsh = 1;
   if (smem > (size_t)(200 << 10) || force_general) {

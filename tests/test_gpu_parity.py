@@ -308,3 +308,20 @@ def test_batched_mixed_depths(pkg, prec):
         zo = of.solve(x[seg])
         assert np.linalg.norm(y[seg] - yo) / np.linalg.norm(yo) <= 10 * eps
         assert np.linalg.norm(z[seg] - zo) / np.linalg.norm(zo) <= 10 * eps
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_many_rhs_columns_agree(pkg, prec):
+    """The solve of an n x m block equals m single-vector solves, for every
+    block width the sweep kernels specialise (1..4) and a wider one."""
+    pts = inputs.random_points(91, 5000, 2)
+    f = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+    B = inputs.rhs(23, len(pts), 6)
+    single = np.stack([f.solve(_cuda(B[c])).cpu().numpy() for c in range(6)])
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for m in (2, 3, 4, 6):
+        X = f.solve(_cuda(B[:m])).cpu().numpy()
+        np.testing.assert_allclose(X, single[:m], rtol=0, atol=tol * np.abs(single).max())
+        Y = f.apply(_cuda(B[:m])).cpu().numpy()
+        Y1 = np.stack([f.apply(_cuda(B[c])).cpu().numpy() for c in range(m)])
+        np.testing.assert_allclose(Y, Y1, rtol=0, atol=tol * np.abs(Y1).max())
