@@ -641,6 +641,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
 
 struct Phase {
   int first, count, bmax, njmax;
+  int wfirst = 0, wcount = 0;  // solve-sweep work items (box, chunk of J)
 };
 
 // Per-kernel-class timing with CUDA events on the launching stream, plus the
@@ -745,6 +746,9 @@ template <typename T> struct Factor : FactorBase {
   DBuf d_mv_ts, d_mv_te, d_mv_sb, d_mv_se;
   // rank proposal: the network (borrowed during rss_factor only), the
   // features of every box (MLP_NFEAT each, box order) and storage accounting
+  // solve sweeps: work items (box, chunk) of every phase, per-box counters,
+  // partial sums of the backward sweep
+  DBuf d_wbox, d_wchunk, d_wcnt, d_pbuf, d_poff;
   const struct MlpModel *mlp = nullptr;
   std::vector<float> feats;
   int64_t reserved_T = 0, used_T = 0, ovf_used = 0;  // elements of T
@@ -1363,7 +1367,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
       check_launch("schur");
       F.prof.end(pi, st);
-      F.phases.push_back({base + p.first, p.second, H.bmax, large ? -njmax_lvl : njmax_lvl});
+      F.phases.push_back({base + p.first, p.second, H.bmax, large ? -njmax_lvl : njmax_lvl, 0, 0});
     }
     // ranks of this level -> active DOFs of the next
     CK(cudaMemcpyAsync(F.h_boxes.data() + base, ptr<FBox<T>>(F.d_boxes) + base, sizeof(FBox<T>) * nb,
@@ -1406,6 +1410,33 @@ template <typename T> static void run_factor(Factor<T> &F) {
     prevH = std::move(H);
     prev_slot = slot;
     have_prev = true;
+  }
+
+  // solve-sweep work items: every box with r > 0 in chunks of SWEEP_CHUNK rows of J
+  {
+    std::vector<int> wb, wc;
+    std::vector<int64_t> poff(F.h_boxes.size() + 1, 0);
+    for (size_t q = 0; q < F.h_boxes.size(); q++) {
+      const FBox<T> &b = F.h_boxes[q];
+      const int nch = std::max(1, (b.nj + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+      poff[q + 1] = poff[q] + (b.r > 0 ? (int64_t)nch * b.r * 4 : 0);
+    }
+    for (Phase &p : F.phases) {
+      p.wfirst = (int)wb.size();
+      for (int q = p.first; q < p.first + p.count; q++) {
+        const FBox<T> &b = F.h_boxes[q];
+        if (b.r == 0) continue;
+        const int nch = std::max(1, (b.nj + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+        for (int c = 0; c < nch; c++) wb.push_back(q), wc.push_back(c);
+      }
+      p.wcount = (int)wb.size() - p.wfirst;
+    }
+    upload(F.d_wbox, wb, st);
+    upload(F.d_wchunk, wc, st);
+    upload(F.d_poff, poff, st);
+    F.d_wcnt.alloc(sizeof(int) * std::max<size_t>(F.h_boxes.size(), 1), st);
+    CK(cudaMemsetAsync(F.d_wcnt.p, 0, sizeof(int) * std::max<size_t>(F.h_boxes.size(), 1), st));
+    F.d_pbuf.alloc(sizeof(T) * std::max<int64_t>(poff.back(), 1), st);
   }
 
   // top blocks: every problem's DOFs still active (Sec. 3.3.3), dense LU
@@ -1498,6 +1529,20 @@ static void fetch_points(const double *pts, int64_t n, int dim, std::vector<doub
   }
 }
 
+// One phase of a sweep: the chunked solve kernels when they apply, else the
+// one-CTA-per-box kernel (apply sweeps, more than four right-hand sides, the
+// forced large-box path).
+template <typename T> static void sweep_phase(const Factor<T> &F, int mode, const Phase &p, T *v, int nrhs) {
+  const bool solve = mode == SWEEP_SOLVE_FWD || mode == SWEEP_SOLVE_BWD;
+  if (solve && nrhs <= 4 && p.njmax >= 0 && sweep_chunk_smem(p.bmax, nrhs, sizeof(T)) <= (size_t)(200 << 10)) {
+    launch_sweep_chunks<T>(mode, ptr<FBox<T>>(F.d_boxes), ptr<int>(F.d_wbox) + p.wfirst, ptr<int>(F.d_wchunk) + p.wfirst,
+                           p.wcount, v, nrhs, p.bmax, ptr<int>(F.d_wcnt), ptr<T>(F.d_pbuf), ptr<int64_t>(F.d_poff),
+                           F.st);
+    return;
+  }
+  launch_sweep<T>(mode, ptr<FBox<T>>(F.d_boxes), p.first, p.count, v, nrhs, p.bmax, p.njmax, F.st);
+}
+
 template <typename T> static void do_sweeps(const Factor<T> &F, const double *in, double *out, int nrhs, bool solve) {
   cudaStream_t st = F.st;
   ensure_work(F, nrhs);
@@ -1511,7 +1556,7 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   const int fwd = solve ? SWEEP_SOLVE_FWD : SWEEP_APPLY_FWD, bwd = solve ? SWEEP_SOLVE_BWD : SWEEP_APPLY_BWD;
   for (const Phase &p : F.phases) {
     pi = P.begin(KC_SWEEP, st, p.first, p.count, nrhs);
-    launch_sweep<T>(fwd, bx, p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
+    sweep_phase<T>(F, fwd, p, v, nrhs);
     P.end(pi, st);
   }
   double nt = F.ntop;
@@ -1521,7 +1566,7 @@ template <typename T> static void do_sweeps(const Factor<T> &F, const double *in
   P.end(pi, st);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
     pi = P.begin(KC_SWEEP, st, it->first, it->count, nrhs);
-    launch_sweep<T>(bwd, bx, it->first, it->count, v, nrhs, it->bmax, it->njmax, st);
+    sweep_phase<T>(F, bwd, *it, v, nrhs);
     P.end(pi, st);
   }
   pi = P.begin(KC_PERMUTE, st, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
@@ -1749,11 +1794,11 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
   cudaStream_t st = F.st;
   launch_permute<T>(0, ptr<int64_t>(F.d_perm), b, v, nullptr, F.n, nrhs, st);
   const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
-  for (const Phase &p : F.phases) launch_sweep<T>(SWEEP_SOLVE_FWD, bx, p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
+  for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_SOLVE_FWD, p, v, nrhs);
   launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
                 ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, topwork, st);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
-    launch_sweep<T>(SWEEP_SOLVE_BWD, bx, it->first, it->count, v, nrhs, it->bmax, it->njmax, st);
+    sweep_phase<T>(F, SWEEP_SOLVE_BWD, *it, v, nrhs);
   launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, x, F.n, nrhs, st);
   check_launch("rss_solve_noalloc");
   CK(cudaStreamSynchronize(st));

@@ -104,6 +104,15 @@ void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err);
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
                   int njmax, cudaStream_t st);
+// Solve sweeps over work items (box, chunk of SWEEP_CHUNK rows of J) for
+// nrhs <= 4; cnt: per-box counters (zero between launches); pbuf/poff: the
+// backward sweep's per-box partial sums (ceil(nj / SWEEP_CHUNK) x r x 4
+// elements per box).  Shared memory as sweep_chunk_smem.
+constexpr int SWEEP_CHUNK = 128;
+template <typename T>
+void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const int *wchunk, int nwork, T *v,
+                         int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st);
+size_t sweep_chunk_smem(int bmax, int nrhs, int elem);
 template <typename T>
 void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, const int64_t *top, const int64_t *toff,
                 const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st);

@@ -2352,86 +2352,118 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
 }
 
 // Solve sweeps (Eq. 3.11) for nrhs = NR <= 4 right-hand sides held in
-// registers; one CTA per box.  The large per-box matrices (E: nj x r,
-// G: r x nj, X_RR^{-1}: r x r) are read once, coalesced, with eight
-// independent loads in flight per thread; T (k x r) by one warp per output.
+// registers, with every box's rows split into chunks of SWEEP_CHUNK so that
+// large boxes are spread over several CTAs.  The CTAs of one box meet at a
+// per-box counter: the last to finish (no waiting) writes the box's own S
+// and R entries, which every CTA of the box reads first, so the result does
+// not depend on which CTA is last.
 template <typename T, int NR>
-__global__ void __launch_bounds__(NT) k_sweep_solve(int mode, const FBox<T> *boxes, int first, T *v) {
+__device__ __forceinline__ void sweep_gather(const FBox<T> &fb, const T *v, T *vS, T *vR) {
+  const int k = fb.k, r = fb.r;
+  for (int e = threadIdx.x; e < k * NR; e += NT) vS[e] = v[fb.ids[e / NR] * NR + e % NR];
+  for (int e = threadIdx.x; e < r * NR; e += NT) vR[e] = v[fb.ids[k + e / NR] * NR + e % NR];
+}
+
+// Forward sweep (solve): tmp = v_R - T^T v_S; v_N -= E_N tmp over this CTA's
+// chunk of J; the last CTA of the box: v_S -= E_S tmp, v_R = X_RR^{-1} tmp.
+template <typename T, int NR>
+__global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const int *wbox, const int *wchunk, T *v,
+                                                  int *cnt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const FBox<T> &fb = boxes[first + blockIdx.x];
+  __shared__ int s_last;
+  const int bi = wbox[blockIdx.x], ch = wchunk[blockIdx.x];
+  const FBox<T> &fb = boxes[bi];
   const int k = fb.k, r = fb.r, nj = fb.nj;
-  if (r == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nch = r >= NT ? 1 : NT / r;  // groups splitting the inner index of the r-row products
   T *vS = reinterpret_cast<T *>(smem_raw);  // k x NR
   T *vR = vS + (size_t)k * NR;               // r x NR
   T *tmp = vR + (size_t)r * NR;              // r x NR
-  T *part = tmp + (size_t)r * NR;            // nch x r x NR partial sums
-  const int64_t *S = fb.ids, *Rr = fb.ids + k;
-  for (int e = tid; e < k * NR; e += NT) vS[e] = v[S[e / NR] * NR + e % NR];
-  for (int e = tid; e < r * NR; e += NT) vR[e] = v[Rr[e / NR] * NR + e % NR];
+  T *part = tmp + (size_t)r * NR;            // partial sums of X_RR^{-1} tmp
+  sweep_gather<T, NR>(fb, v, vS, vR);
   __syncthreads();
-  if (mode == SWEEP_SOLVE_FWD) {
-    // U_T: tmp = v_R - T^T v_S (one warp per output, lanes over S)
-    for (int ri = warp; ri < r; ri += NT / 32) {
-      const T *tc = fb.Tm + (int64_t)ri * k;
-      T acc[NR];
+  for (int ri = warp; ri < r; ri += NT / 32) {
+    const T *tc = fb.Tm + (int64_t)ri * k;
+    T acc[NR];
 #pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      for (int q = lane; q < k; q += 32) {
-        const T tq = tc[q];
+    for (int c = 0; c < NR; c++) acc[c] = (T)0;
+    for (int q = lane; q < k; q += 32) {
+      const T tq = tc[q];
 #pragma unroll
-        for (int c = 0; c < NR; c++) acc[c] += tq * vS[q * NR + c];
-      }
-#pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] = warp_sum(acc[c]);
-      if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < NR; c++) tmp[ri * NR + c] = vR[ri * NR + c] - acc[c];
+      for (int c = 0; c < NR; c++) acc[c] += tq * vS[q * NR + c];
     }
-    __syncthreads();
-    // L: v_J -= E tmp (one thread per row of E)
-    for (int a = tid; a < nj; a += NT) {
-      const T *ea = fb.E + a;
-      T acc[NR];
 #pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      int ri = 0;
-      for (; ri + 8 <= r; ri += 8) {
-        T ev[8];
+    for (int c = 0; c < NR; c++) acc[c] = warp_sum(acc[c]);
+    if (lane == 0)
 #pragma unroll
-        for (int u = 0; u < 8; u++) ev[u] = __ldg(ea + (int64_t)(ri + u) * nj);
+      for (int c = 0; c < NR; c++) tmp[ri * NR + c] = vR[ri * NR + c] - acc[c];
+  }
+  __syncthreads();
+  // rows of E: two threads per row, each over alternate columns; every lane
+  // of the warp calls this (valid or not) for the final shuffle
+  auto erow = [&](int a, bool valid, T *acc) {
+    const T *ea = fb.E + a;
+    const int h = tid & 1;
+    int ri = valid ? h : r;
+    for (; ri + 14 < r; ri += 16) {
+      T ev[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++)
+      for (int u = 0; u < 8; u++) ev[u] = __ldg(ea + (int64_t)(ri + 2 * u) * nj);
 #pragma unroll
-          for (int c = 0; c < NR; c++) acc[c] += ev[u] * tmp[(ri + u) * NR + c];
-      }
-      for (; ri < r; ri++) {
-        const T ev = __ldg(ea + (int64_t)ri * nj);
+      for (int u = 0; u < 8; u++)
 #pragma unroll
-        for (int c = 0; c < NR; c++) acc[c] += ev * tmp[ri * NR + c];
-      }
+        for (int c = 0; c < NR; c++) acc[c] += ev[u] * tmp[(ri + 2 * u) * NR + c];
+    }
+    for (; ri < r; ri += 2) {
+      const T ev = __ldg(ea + (int64_t)ri * nj);
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] += ev * tmp[ri * NR + c];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+  };
+  {
+    const int a = ch * SWEEP_CHUNK + (tid >> 1);
+    T acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc[c] = (T)0;
+    const bool mine = a < nj && a >= k;
+    erow(a, a < nj, acc);
+    if (mine && (tid & 1) == 0) {
       T *vg = v + fb.J[a] * NR;
 #pragma unroll
       for (int c = 0; c < NR; c++) vg[c] -= acc[c];
     }
-    // D^{-1} on R: x_R = X_RR^{-1} tmp (rows split over nch groups of columns)
-    if (tid < nch * r) {
-      const int i = tid % r, g = tid / r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int nchunk = max(1, (nj + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+    s_last = atomicAdd(cnt + bi, 1) == nchunk - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid == 0) cnt[bi] = 0;
+  // S rows of E (the head of J)
+  for (int a0 = 0; a0 < k; a0 += NT / 2) {
+    const int a = a0 + (tid >> 1);
+    T acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc[c] = (T)0;
+    erow(a, a < k, acc);
+    if (a < k && (tid & 1) == 0) {
+      T *vg = v + fb.ids[a] * NR;
+#pragma unroll
+      for (int c = 0; c < NR; c++) vg[c] = vS[a * NR + c] - acc[c];
+    }
+  }
+  // D^{-1} on R: x_R = X_RR^{-1} tmp (rows split over nch groups of columns)
+  const int nch = r >= NT ? 1 : NT / r;
+  for (int i0 = 0; i0 < r; i0 += NT) {
+    const int i = i0 + tid % (r >= NT ? NT : r), g = r >= NT ? 0 : tid / r;
+    if (i < r && g < nch && tid < (r >= NT ? NT : nch * r)) {
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      int l = g;
-      for (; l + 3 * nch < r; l += 4 * nch) {
-        T xv[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) xv[u] = __ldg(fb.Xi + i + (int64_t)(l + u * nch) * r);
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-#pragma unroll
-          for (int c = 0; c < NR; c++) acc[c] += xv[u] * tmp[(l + u * nch) * NR + c];
-      }
-      for (; l < r; l += nch) {
+      for (int l = g; l < r; l += nch) {
         const T xv = __ldg(fb.Xi + i + (int64_t)l * r);
 #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] += xv * tmp[l * NR + c];
@@ -2439,30 +2471,49 @@ __global__ void __launch_bounds__(NT) k_sweep_solve(int mode, const FBox<T> *box
 #pragma unroll
       for (int c = 0; c < NR; c++) part[((size_t)g * r + i) * NR + c] = acc[c];
     }
-    __syncthreads();
-    for (int i = tid; i < r; i += NT) {
-      T *vg = v + Rr[i] * NR;
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += NT) {
+    T *vg = v + fb.ids[k + i] * NR;
 #pragma unroll
-      for (int c = 0; c < NR; c++) {
-        T s = (T)0;
-        for (int g = 0; g < nch; g++) s += part[((size_t)g * r + i) * NR + c];
-        vg[c] = s;
-      }
+    for (int c = 0; c < NR; c++) {
+      T sum = (T)0;
+      for (int g = 0; g < nch; g++) sum += part[((size_t)g * r + i) * NR + c];
+      vg[c] = sum;
     }
-  } else {
-    // U: v_R -= G v_J (rows of G split over nch groups of J)
-    if (tid < nch * r) {
-      const int ri = tid % r, g = tid / r;
+  }
+}
+
+// Backward sweep (solve): partial sums of G v_J over this CTA's chunk of J
+// into pbuf; the last CTA of the box adds them in chunk order,
+// v_R -= G v_J, v_S -= T v_R, and writes v_R and v_S.
+template <typename T, int NR>
+__global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const int *wbox, const int *wchunk, T *v,
+                                                  int *cnt, T *pbuf, const int64_t *poff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
+  const int bi = wbox[blockIdx.x], ch = wchunk[blockIdx.x];
+  const FBox<T> &fb = boxes[bi];
+  const int k = fb.k, r = fb.r, nj = fb.nj;
+  const int tid = threadIdx.x;
+  T *part = reinterpret_cast<T *>(smem_raw);  // nch x r x NR, then vS, vR for the last CTA
+  const int a0 = ch * SWEEP_CHUNK, a1 = min(nj, a0 + SWEEP_CHUNK);
+  const int nch = r >= NT ? 1 : NT / r;
+  T *pb = pbuf + poff[bi] + (int64_t)ch * r * NR;
+  for (int i0 = 0; i0 < r; i0 += NT) {
+    const int rr = r >= NT ? NT : r;
+    const int i = i0 + tid % rr, g = tid / rr;
+    if (i < r && g < nch) {
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      int a = g;
-      for (; a + 3 * nch < nj; a += 4 * nch) {
+      int a = a0 + g;
+      for (; a + 3 * nch < a1; a += 4 * nch) {
         T gv[4];
         int64_t ja[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          gv[u] = __ldg(fb.G + ri + (int64_t)(a + u * nch) * r);
+          gv[u] = __ldg(fb.G + i + (int64_t)(a + u * nch) * r);
           ja[u] = fb.J[a + u * nch];
         }
 #pragma unroll
@@ -2470,41 +2521,86 @@ __global__ void __launch_bounds__(NT) k_sweep_solve(int mode, const FBox<T> *box
 #pragma unroll
           for (int c = 0; c < NR; c++) acc[c] += gv[u] * v[ja[u] * NR + c];
       }
-      for (; a < nj; a += nch) {
-        const T gv = __ldg(fb.G + ri + (int64_t)a * r);
+      for (; a < a1; a += nch) {
+        const T gv = __ldg(fb.G + i + (int64_t)a * r);
         const int64_t ja = fb.J[a];
 #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] += gv * v[ja * NR + c];
       }
 #pragma unroll
-      for (int c = 0; c < NR; c++) part[((size_t)g * r + ri) * NR + c] = acc[c];
+      for (int c = 0; c < NR; c++) part[((size_t)g * rr + (i - i0)) * NR + c] = acc[c];
     }
     __syncthreads();
-    for (int i = tid; i < r; i += NT)
-#pragma unroll
-      for (int c = 0; c < NR; c++) {
-        T s = (T)0;
-        for (int g = 0; g < nch; g++) s += part[((size_t)g * r + i) * NR + c];
-        vR[i * NR + c] -= s;
-      }
-    __syncthreads();
-    // L_T: v_S -= T v_R (one thread per skeleton DOF); v_R written back
-    for (int q = tid; q < k; q += NT) {
-      T acc[NR];
-#pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      for (int ri = 0; ri < r; ri++) {
-        const T tv = __ldg(fb.Tm + q + (int64_t)ri * k);
-#pragma unroll
-        for (int c = 0; c < NR; c++) acc[c] += tv * vR[ri * NR + c];
-      }
-      T *vg = v + S[q] * NR;
-#pragma unroll
-      for (int c = 0; c < NR; c++) vg[c] = vS[q * NR + c] - acc[c];
+    for (int e = tid; e < (r - i0 < rr ? r - i0 : rr) * NR; e += NT) {
+      const int il = e / NR, c = e % NR;
+      T sum = (T)0;
+      for (int g2 = 0; g2 < nch; g2++) sum += part[((size_t)g2 * rr + il) * NR + c];
+      pb[(int64_t)(i0 + il) * NR + c] = sum;
     }
-    for (int e = tid; e < r * NR; e += NT) v[Rr[e / NR] * NR + e % NR] = vR[e];
+    __syncthreads();
   }
+  __threadfence();
+  if (tid == 0) {
+    const int nchunk = max(1, (nj + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+    s_last = atomicAdd(cnt + bi, 1) == nchunk - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid == 0) cnt[bi] = 0;
+  const int nchunk = max(1, (nj + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+  T *vS = part, *vR = part + (size_t)k * NR;
+  sweep_gather<T, NR>(fb, v, vS, vR);
+  __syncthreads();
+  const T *p0 = pbuf + poff[bi];
+  for (int e = tid; e < r * NR; e += NT) {
+    T sum = (T)0;
+    for (int c2 = 0; c2 < nchunk; c2++) sum += __ldcg(p0 + (int64_t)c2 * r * NR + e);
+    vR[e] -= sum;
+  }
+  __syncthreads();
+  for (int q = tid; q < k; q += NT) {
+    T acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc[c] = (T)0;
+    for (int ri = 0; ri < r; ri++) {
+      const T tv = __ldg(fb.Tm + q + (int64_t)ri * k);
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[c] += tv * vR[ri * NR + c];
+    }
+    T *vg = v + fb.ids[q] * NR;
+#pragma unroll
+    for (int c = 0; c < NR; c++) vg[c] = vS[q * NR + c] - acc[c];
+  }
+  for (int e = tid; e < r * NR; e += NT) v[fb.ids[k + e / NR] * NR + e % NR] = vR[e];
 }
+
+template <typename T>
+void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const int *wchunk, int nwork, T *v,
+                         int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st) {
+  if (nwork == 0) return;
+  const size_t smem = ((size_t)4 * bmax + NT) * nrhs * sizeof(T) + 64;
+#define RSS_SWEEP_NR(NRV)                                                                                   \
+  case NRV:                                                                                                \
+    if (mode == SWEEP_SOLVE_FWD) {                                                                         \
+      cudaFuncSetAttribute(k_sweep_fwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+      k_sweep_fwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt);                           \
+    } else {                                                                                               \
+      cudaFuncSetAttribute(k_sweep_bwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+      k_sweep_bwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt, pbuf, poff);               \
+    }                                                                                                      \
+    break;
+  switch (nrhs) {
+    RSS_SWEEP_NR(1)
+    RSS_SWEEP_NR(2)
+    RSS_SWEEP_NR(3)
+    RSS_SWEEP_NR(4)
+  }
+#undef RSS_SWEEP_NR
+  count_launch();
+}
+
+size_t sweep_chunk_smem(int bmax, int nrhs, int elem) { return ((size_t)4 * bmax + NT) * nrhs * elem + 64; }
 
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax, int njmax,
@@ -2512,25 +2608,6 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
   if (count == 0) return;
   const bool force_general = njmax < 0;  // large-box path requested
   if (force_general) njmax = -njmax;
-  if ((mode == SWEEP_SOLVE_FWD || mode == SWEEP_SOLVE_BWD) && nrhs <= 4 && !force_general) {
-    const size_t smem = ((size_t)4 * bmax + NT) * nrhs * sizeof(T) + 64;
-    if (smem <= (size_t)(200 << 10)) {
-#define RSS_SWEEP_NR(NRV)                                                                          \
-  case NRV:                                                                                       \
-    cudaFuncSetAttribute(k_sweep_solve<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_sweep_solve<T, NRV><<<count, NT, smem, st>>>(mode, boxes, first, v);                         \
-    break;
-      switch (nrhs) {
-        RSS_SWEEP_NR(1)
-        RSS_SWEEP_NR(2)
-        RSS_SWEEP_NR(3)
-        RSS_SWEEP_NR(4)
-      }
-#undef RSS_SWEEP_NR
-      count_launch();
-      return;
-    }
-  }
   size_t smem = ((size_t)3 * bmax + (size_t)njmax) * nrhs * sizeof(T) + 64;
   int jsh = 1;
   if (smem > (size_t)(200 << 10) || force_general) {
@@ -2786,6 +2863,8 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
                                 cudaStream_t);                                                                \
   template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \
   template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t);            \
+  template void launch_sweep_chunks<T>(int, const FBox<T> *, const int *, const int *, int, T *, int, int, int *, \
+                                       T *, const int64_t *, cudaStream_t);                                  \
   template void launch_top<T>(int, const T *, const int64_t *, const int *, const int64_t *, const int64_t *,     \
                              const int *, int, int, T *, int, T *, cudaStream_t);                            \
   template void launch_lu_batched<T>(T *, const int64_t *, int *, const int64_t *, const int *, int, cudaStream_t, \
