@@ -73,6 +73,9 @@ typedef struct {
  * which otherwise run only when a box is too large for shared memory.  The
  * result is the same factorization; used to test that path on small cases. */
 #define RSS_FLAG_LARGE_BOX_PATH 1
+/* Use the built-in launch shapes instead of the autotuner's choices (see
+ * rss_autotune_table). */
+#define RSS_FLAG_NO_AUTOTUNE 2
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;
@@ -270,6 +273,20 @@ rss_status rss_mlp_train(rss_mlp *m, const float *X, const float *y, int64_t n, 
  * FP32, elimination order as in rss_stats) and the rank k its ID found (HOST,
  * nbox int32): training data for the network.  nbox must equal rss_stats [0]. */
 rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *rank, int64_t nbox);
+
+/* rss_autotune_table -- the autotuner's choices so far in this process, as
+ * HOST int32 records of 7: {element bytes (4 FP32 factor, 8 FP64), box-width
+ * class (64 or 128), phase-size class (floor(log2(boxes in the phase))),
+ * chosen fold groups per box of the ID kernel, then the measured time in
+ * microseconds of 1, 2 and 4 groups (0: not a candidate)}.  The ID kernel
+ * splits a box's rows over fold groups whose triangles are merged (Sec. 2.2
+ * ID, computed by Householder QR); more groups shorten each box, fewer fit
+ * more boxes per SM.  The first colour phase that meets a key times every
+ * candidate on its own boxes (the ID launch is idempotent), keeps the fastest
+ * for the rest of the process and re-runs it, so factorizations with the
+ * same key compute the same result.  Disabled per factorization by
+ * RSS_FLAG_NO_AUTOTUNE.  *nbytes in/out as in rss_tree_query. */
+rss_status rss_autotune_table(int32_t *buf, size_t *nbytes);
 
 /* rss_free -- release a tree, factor or network handle (NULL-safe). */
 void rss_free(void *handle);

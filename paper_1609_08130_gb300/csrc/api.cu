@@ -11,6 +11,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <functional>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -891,6 +892,76 @@ static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vect
   H.bmax = std::max(H.bmax, Hp.bmax);
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: the ID kernel's fold groups per box (how many thread groups
+// split a box's rows) trade latency per box against boxes resident per SM;
+// the best value depends on the box width and the number of boxes in a
+// colour phase.  The first phase that meets a (precision, width class,
+// phase-size class) key times every candidate on that phase (the ID launch
+// is idempotent: it only writes the boxes' ID results), keeps the fastest
+// for the rest of the process and re-runs it, so every factorization with
+// that key computes exactly the same thing.
+// ---------------------------------------------------------------------------
+
+struct TuneEntry {
+  int groups;
+  float us[3];  // time of each candidate (1, 2, 4 groups), microseconds; 0 if not tried
+};
+static std::mutex g_tune_m;
+static std::map<std::tuple<int, int, int>, TuneEntry> g_tune;
+
+template <typename T, typename Launch>
+static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
+  const bool tunable = bmax > 0 && bmax <= 128 && !(F.flags & RSS_FLAG_NO_AUTOTUNE);
+  if (!tunable) {
+    set_id_groups(0);
+    launch();
+    return;
+  }
+  int bucket = 0;
+  while ((2 << bucket) <= nbox) bucket++;
+  const auto key = std::make_tuple((int)sizeof(T), bmax <= 64 ? 64 : 128, bucket);
+  int G = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_m);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) G = it->second.groups;
+  }
+  if (G == 0) {
+    const int cands[3] = {1, 2, 4};
+    const int ncand = bmax <= 64 ? 3 : 2;
+    TuneEntry te{0, {0.f, 0.f, 0.f}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    for (int ci = 0; ci < ncand; ci++) {
+      set_id_groups(cands[ci]);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; rep++) {  // the second launch is timed
+        CK(cudaEventRecord(e0, F.st));
+        launch();
+        CK(cudaEventRecord(e1, F.st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      te.us[ci] = 1e3f * ms;
+      if (te.groups == 0 || ms < best) {
+        best = ms;
+        te.groups = cands[ci];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_m);
+    auto ins = g_tune.insert({key, te});
+    G = ins.first->second.groups;  // another thread may have tuned the key first
+  }
+  set_id_groups(G);
+  launch();
+  set_id_groups(0);
+}
+
 // A level ran out of overflow space for boxes whose rank exceeded the
 // proposed reservation: the factorization is redone with full reservations.
 struct Retry {};
@@ -1353,9 +1424,12 @@ template <typename T> static void run_factor(Factor<T> &F) {
     F.prof.host(KC_HOST_LEVEL, now_ms() - th0);
     for (auto &p : ph) {
       const int *bl = ptr<int>(d_list) + p.first;
+      auto id_launch = [&] {
+        launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ring_max, F.P, F.K, F.px,
+                     ptr<double>(F.d_proxy), F.eps, ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
+      };
       int pi = F.prof.begin(KC_ID, st, base + p.first, p.second);
-      launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ring_max, F.P, F.K, F.px,
-                   ptr<double>(F.d_proxy), F.eps, ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
+      tuned_id_launch(F, large ? -H.bmax : H.bmax, p.second, id_launch);
       check_launch("id");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_ELIM, st, base + p.first, p.second);
@@ -2281,6 +2355,29 @@ rss_status rss_mlp_train(rss_mlp *m, const float *X, const float *y, int64_t n, 
     CK(cudaMemcpyAsync(&l, M.loss.p, sizeof(double), cudaMemcpyDeviceToHost, M.st));
     CK(cudaStreamSynchronize(M.st));
     if (loss) *loss = l;
+  });
+}
+
+rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
+  return guard([&] {
+    if (!nbytes) throw Fail{RSS_EINVAL, "rss_autotune_table: bad arguments"};
+    std::vector<int32_t> v;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_m);
+      for (const auto &kv : g_tune) {
+        v.push_back(std::get<0>(kv.first));
+        v.push_back(std::get<1>(kv.first));
+        v.push_back(std::get<2>(kv.first));
+        v.push_back(kv.second.groups);
+        for (int c = 0; c < 3; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
+      }
+    }
+    const size_t need = v.size() * sizeof(int32_t), cap = *nbytes;
+    *nbytes = need;
+    if (buf) {
+      if (cap < need) throw Fail{RSS_EINVAL, "rss_autotune_table: buffer too small"};
+      if (need) memcpy(buf, v.data(), need);
+    }
   });
 }
 

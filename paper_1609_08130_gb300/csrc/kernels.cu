@@ -1232,6 +1232,11 @@ static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
   count_launch();
 }
 
+// Fold groups per box for the next k_idc launch (0: default).  Set by the
+// host's autotuner around a launch_id call on the same thread.
+static thread_local int id_groups_hint = 0;
+void set_id_groups(int G) { id_groups_hint = G; }
+
 template <typename T>
 void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, int mmax,
                const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit, double eps,
@@ -1241,13 +1246,15 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   const bool force_general = bmax < 0;  // large-box path requested
   if (force_general) bmax = -bmax;
   if (bmax <= 128 && !force_general) {
-    // warps per box: enough warps in flight to cover the SMs
     const int ring_max = mmax;
-    // fold groups per box: enough boxes resident at once to finish a phase
-    // in one wave when the phase is large, more groups per box when small
-    const int G = nbox >= 300 ? 2 : 4;
-    if (bmax <= 64) launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
-    else launch_idc<T, 128>(lv, boxes, box_list, nbox, G >= 4 ? 2 : 1, P, K, px, proxy_unit, eps, ring_max, st, err);
+    // fold groups per box: the autotuner's choice for this (precision, box
+    // width, phase size), else the default (enough boxes resident at once to
+    // finish a large phase in one wave, more groups per box when small)
+    const int NCw = bmax <= 64 ? 64 : 128;
+    int G = id_groups_hint;
+    if (G <= 0) G = NCw == 64 ? (nbox >= 300 ? 2 : 4) : (nbox >= 300 ? 1 : 2);
+    if (NCw == 64) launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+    else launch_idc<T, 128>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
     return;
   }
   int PR = bmax <= 80 ? 128 : 64;

@@ -24,6 +24,7 @@ RSS_OK, RSS_EINVAL, RSS_ENOMEM, RSS_ECUDA, RSS_ENUMERIC, RSS_ETIMEOUT, RSS_ENOTC
 LAPLACE2D_LOG, LAPLACE3D_INV = 0, 1
 FP64, MIXED = 0, 1
 FLAG_LARGE_BOX_PATH = 1
+FLAG_NO_AUTOTUNE = 2
 
 
 def _nvcc():
@@ -94,6 +95,7 @@ _SIGS = {
     "rss_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_float,
                                 C.POINTER(C.c_double)]),
     "rss_box_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "rss_autotune_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_free": (None, [C.c_void_p]),
     "rss_last_error": (C.c_char_p, []),
     "rss_kernel_launches": (C.c_int64, []),
@@ -120,6 +122,18 @@ def lib(load_only: bool = False):
 def kernel_launches() -> int:
     """Kernel launches made by librss.so in this process so far."""
     return int(lib().rss_kernel_launches())
+
+
+def autotune_table() -> list:
+    """rss_autotune_table: [{elem_bytes, width, phase_class, groups, us: [t1, t2, t4]}]."""
+    import numpy as np
+    nb = C.c_size_t(0)
+    _check(lib().rss_autotune_table(None, C.byref(nb)))
+    buf = np.zeros(max(nb.value // 4, 1), dtype=np.int32)
+    _check(lib().rss_autotune_table(C.c_void_p(buf.ctypes.data), C.byref(nb)))
+    recs = buf[:nb.value // 4].reshape(-1, 7)
+    return [dict(elem_bytes=int(r[0]), width=int(r[1]), phase_class=int(r[2]), groups=int(r[3]),
+                 us=[int(x) for x in r[4:7]]) for r in recs]
 
 
 def _check(st: int):

@@ -325,3 +325,25 @@ def test_solve_many_rhs_columns_agree(pkg, prec):
         Y = f.apply(_cuda(B[:m])).cpu().numpy()
         Y1 = np.stack([f.apply(_cuda(B[c])).cpu().numpy() for c in range(m)])
         np.testing.assert_allclose(Y, Y1, rtol=0, atol=tol * np.abs(Y1).max())
+
+
+def test_autotuner_choices_are_reproducible(pkg):
+    """The autotuner records a choice per (precision, width, phase size) and
+    factorizations after it compute bit-identical results; switching it off
+    gives a factor of the same accuracy."""
+    pts = inputs.grid_points(128, 2)
+    n = len(pts)
+    f1 = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=pkg.MIXED)
+    tab = pkg.autotune_table()
+    assert tab, "no autotuner entries after a factorization"
+    for e in tab:
+        assert e["groups"] in (1, 2, 4) and e["width"] in (64, 128) and e["elem_bytes"] in (4, 8)
+        assert e["us"][(1, 2, 4).index(e["groups"])] > 0
+    f2 = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=pkg.MIXED)
+    x = _cuda(inputs.rhs(31, n, 2))
+    assert torch.equal(f1.solve(x), f2.solve(x))
+    f3 = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=pkg.MIXED, flags=pkg.rss.FLAG_NO_AUTOTUNE)
+    ax = f1.matvec(x)  # exact FP64 A x
+    for f in (f1, f3):
+        err = torch.linalg.norm(f.apply(x) - ax) / torch.linalg.norm(ax)
+        assert float(err) <= 10 * 1e-6
