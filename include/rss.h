@@ -60,7 +60,8 @@ typedef struct {
   int prec;            /* rss_precision: FP64 everywhere, or an FP32 factor */
   int n_proxy;         /* proxy points; 0: 64 (2D) / 512 (3D) (Sec. 4) */
   double proxy_radius; /* in box sides; 0: 2.5 (Sec. 3.2) */
-  int use_graphs;      /* reserved, must be 0 */
+  int use_graphs;      /* 1: each solve with nrhs <= 4 replays a CUDA graph
+                          of its launch sequence, captured on first use */
   void *stream;        /* cudaStream_t; NULL = legacy default stream */
   int profile;         /* 1: time every kernel launch with CUDA events on the
                           stream (see rss_profile) */

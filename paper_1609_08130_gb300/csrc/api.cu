@@ -735,7 +735,20 @@ template <typename T> struct Factor : FactorBase {
   std::vector<int64_t> h_toff, h_loff;
   DBuf d_top, d_topLU, d_toppiv, d_tn, d_toff, d_loff;
   mutable DBuf d_work, d_topwork;
-  mutable int work_nrhs = 0;
+  mutable int work_nrhs = 0, work_gen = 0;
+  // solve sweeps captured in a CUDA graph, one per nrhs <= 4, replayed with
+  // fixed input/output buffers (options.use_graphs)
+  bool use_graphs = false;
+  struct SweepGraph {
+    int gen = -1, kernels = 0;
+    cudaGraphExec_t exec = nullptr;
+  };
+  mutable SweepGraph sgraph[5];
+  mutable DBuf g_in, g_out;
+  ~Factor() {
+    for (auto &g : sgraph)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+  }
   // FP64 residual operator: FFT convolution when a single problem's points
   // are the cell centres of a regular grid, direct summation otherwise
   int grid_side = 0;
@@ -769,6 +782,7 @@ template <typename T> static void ensure_work(const Factor<T> &F, int nrhs) {
   F.d_work.alloc((size_t)std::max<int64_t>(F.n, 1) * nrhs * sizeof(T), F.st);
   F.d_topwork.alloc((size_t)std::max(F.ntop, 1) * 2 * nrhs * sizeof(T), F.st);
   F.work_nrhs = nrhs;
+  F.work_gen++;  // captured sweeps hold the old buffers
 }
 
 // Algorithmic work of one launch over boxes [first, first+count):
@@ -1606,49 +1620,118 @@ static void fetch_points(const double *pts, int64_t n, int dim, std::vector<doub
 // One phase of a sweep: the chunked solve kernels when they apply, else the
 // one-CTA-per-box kernel (apply sweeps, more than four right-hand sides, the
 // forced large-box path).
-template <typename T> static void sweep_phase(const Factor<T> &F, int mode, const Phase &p, T *v, int nrhs) {
+template <typename T>
+static void sweep_phase(const Factor<T> &F, int mode, const Phase &p, T *v, int nrhs, cudaStream_t st) {
   const bool solve = mode == SWEEP_SOLVE_FWD || mode == SWEEP_SOLVE_BWD;
   if (solve && nrhs <= 4 && p.njmax >= 0 && sweep_chunk_smem(p.bmax, nrhs, sizeof(T)) <= (size_t)(200 << 10)) {
     launch_sweep_chunks<T>(mode, ptr<FBox<T>>(F.d_boxes), ptr<int>(F.d_wbox) + p.wfirst, ptr<int>(F.d_wchunk) + p.wfirst,
-                           p.wcount, v, nrhs, p.bmax, ptr<int>(F.d_wcnt), ptr<T>(F.d_pbuf), ptr<int64_t>(F.d_poff),
-                           F.st);
+                           p.wcount, v, nrhs, p.bmax, ptr<int>(F.d_wcnt), ptr<T>(F.d_pbuf), ptr<int64_t>(F.d_poff), st);
     return;
   }
-  launch_sweep<T>(mode, ptr<FBox<T>>(F.d_boxes), p.first, p.count, v, nrhs, p.bmax, p.njmax, F.st);
+  launch_sweep<T>(mode, ptr<FBox<T>>(F.d_boxes), p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
 }
 
-template <typename T> static void do_sweeps(const Factor<T> &F, const double *in, double *out, int nrhs, bool solve) {
+// Every launch of one application of F (Eq. 3.10) or F^{-1} (Eq. 3.11) on
+// `st`: permute into tree order, forward sweeps over the phases, the top
+// blocks, backward sweeps, permute back.  Per-launch profiling when `prof`.
+template <typename T>
+static void enqueue_sweeps(const Factor<T> &F, const double *in, double *out, T *v, int nrhs, bool solve,
+                           cudaStream_t st, bool prof) {
+  Prof &P = F.prof;
+  auto begin = [&](int cls, int first, int count, int nr, double bytes = 0.0, double flops = 0.0) {
+    return prof ? P.begin(cls, st, first, count, nr, bytes, flops) : -1;
+  };
+  auto end = [&](int pi) {
+    if (prof) P.end(pi, st);
+  };
+  const double sz = sizeof(T);
+  int pi = begin(KC_PERMUTE, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
+  launch_permute<T>(0, ptr<int64_t>(F.d_perm), in, v, nullptr, F.n, nrhs, st);
+  end(pi);
+  const int fwd = solve ? SWEEP_SOLVE_FWD : SWEEP_APPLY_FWD, bwd = solve ? SWEEP_SOLVE_BWD : SWEEP_APPLY_BWD;
+  for (const Phase &p : F.phases) {
+    pi = begin(KC_SWEEP, p.first, p.count, nrhs);
+    sweep_phase<T>(F, fwd, p, v, nrhs, st);
+    end(pi);
+  }
+  double nt = F.ntop;
+  pi = begin(KC_TOP, 0, 0, 0, nt * nt * sz + 2.0 * nt * nrhs * sz, 2.0 * nt * nt * nrhs);
+  launch_top<T>(solve ? 0 : 1, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
+                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, ptr<T>(F.d_topwork), st);
+  end(pi);
+  for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
+    pi = begin(KC_SWEEP, it->first, it->count, nrhs);
+    sweep_phase<T>(F, bwd, *it, v, nrhs, st);
+    end(pi);
+  }
+  pi = begin(KC_PERMUTE, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
+  launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, out, F.n, nrhs, st);
+  end(pi);
+}
+
+// The solve's launch sequence for nrhs <= 4 as a CUDA graph (reading g_in,
+// writing g_out), captured on a private stream and replayed on the factor's
+// stream.  It is captured right after the first (uncaptured) solve with this
+// nrhs, which has set the kernel attributes and loaded the kernels; the GPU
+// is still running that solve while the host captures.  Rebuilt when the
+// working vectors are reallocated.
+template <typename T> static void capture_solve_graph(const Factor<T> &F, int nrhs) {
+  auto &g = F.sgraph[nrhs];
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  const size_t nb = sizeof(double) * (size_t)std::max<int64_t>(F.n, 1) * 4;
+  grow(F.g_in, nb, F.st);
+  grow(F.g_out, nb, F.st);
+  T *v = ptr<T>(F.d_work);
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const long long l0 = launches_total();
+    enqueue_sweeps(F, ptr<double>(F.g_in), ptr<double>(F.g_out), v, nrhs, true, cs, false);
+    g.kernels = (int)(launches_total() - l0);
+    count_launch(-g.kernels);  // captured, not launched
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g.exec = nullptr;
+    throw Fail{RSS_ECUDA, std::string("capturing the solve sweeps: ") + cudaGetErrorString(e)};
+  }
+  g.gen = F.work_gen;
+}
+
+template <typename T>
+static void do_sweeps(const Factor<T> &F, const double *in, double *out, int nrhs, bool solve, bool sync = true) {
   cudaStream_t st = F.st;
   ensure_work(F, nrhs);
   T *v = ptr<T>(F.d_work);
-  Prof &P = F.prof;
-  const double sz = sizeof(T);
-  int pi = P.begin(KC_PERMUTE, st, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
-  launch_permute<T>(0, ptr<int64_t>(F.d_perm), in, v, nullptr, F.n, nrhs, st);
-  P.end(pi, st);
-  const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
-  const int fwd = solve ? SWEEP_SOLVE_FWD : SWEEP_APPLY_FWD, bwd = solve ? SWEEP_SOLVE_BWD : SWEEP_APPLY_BWD;
-  for (const Phase &p : F.phases) {
-    pi = P.begin(KC_SWEEP, st, p.first, p.count, nrhs);
-    sweep_phase<T>(F, fwd, p, v, nrhs);
-    P.end(pi, st);
+  const bool graphed = solve && F.use_graphs && nrhs <= 4 && F.n > 0;
+  if (graphed && !(F.sgraph[nrhs].exec && F.sgraph[nrhs].gen == F.work_gen)) {
+    enqueue_sweeps(F, in, out, v, nrhs, solve, st, F.prof.on);
+    check_launch("sweeps");
+    capture_solve_graph(F, nrhs);
+  } else if (graphed) {
+    cudaGraphExec_t ge = F.sgraph[nrhs].exec;
+    const size_t nb = sizeof(double) * (size_t)F.n * nrhs;
+    int pi = F.prof.begin(KC_SWEEP, st, 0, (int)F.h_boxes.size(), nrhs);
+    CK(cudaMemcpyAsync(F.g_in.p, in, nb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaGraphLaunch(ge, st));
+    CK(cudaMemcpyAsync(out, F.g_out.p, nb, cudaMemcpyDeviceToDevice, st));
+    F.prof.end(pi, st);
+    count_launch(F.sgraph[nrhs].kernels);
+  } else {
+    enqueue_sweeps(F, in, out, v, nrhs, solve, st, F.prof.on);
+    check_launch("sweeps");
   }
-  double nt = F.ntop;
-  pi = P.begin(KC_TOP, st, 0, 0, 0, nt * nt * sz + 2.0 * nt * nrhs * sz, 2.0 * nt * nt * nrhs);
-  launch_top<T>(solve ? 0 : 1, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
-                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, ptr<T>(F.d_topwork), st);
-  P.end(pi, st);
-  for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
-    pi = P.begin(KC_SWEEP, st, it->first, it->count, nrhs);
-    sweep_phase<T>(F, bwd, *it, v, nrhs);
-    P.end(pi, st);
+  if (sync) {
+    CK(cudaStreamSynchronize(st));
+    prof_collect(F);
   }
-  pi = P.begin(KC_PERMUTE, st, 0, 0, 0, (double)F.n * nrhs * (8.0 + sz + 8.0));
-  launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, out, F.n, nrhs, st);
-  P.end(pi, st);
-  check_launch("sweeps");
-  CK(cudaStreamSynchronize(st));
-  prof_collect(F);
 }
 
 template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs);
@@ -1729,7 +1812,7 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
     check_launch("combine");
   };
   // x0 = F^{-1} b
-  do_sweeps(F, b, x, nrhs, true);
+  do_sweeps(F, b, x, nrhs, true, false);
   std::vector<double> bn;
   dots(b, 1, b, bn);
   for (auto &v : bn) v = v > 0 ? sqrt(v) : 1.0;
@@ -1762,7 +1845,7 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
     for (int c = 0; c < nrhs; c++) g[c * (m + 1)] = rn[c];
     int jdone = 0;
     for (int j = 0; j < m; j++) {
-      do_sweeps(F, pV + j * nn, pZ + j * nn, nrhs, true);
+      do_sweeps(F, pV + j * nn, pZ + j * nn, nrhs, true, false);
       apply_A(F, pZ + j * nn, pw, nrhs);
       std::vector<double> hh, hh2, hn;
       dots(pV, j + 1, pw, hh);  // hh[c * (j+1) + i]
@@ -1868,11 +1951,11 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
   cudaStream_t st = F.st;
   launch_permute<T>(0, ptr<int64_t>(F.d_perm), b, v, nullptr, F.n, nrhs, st);
   const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
-  for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_SOLVE_FWD, p, v, nrhs);
+  for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_SOLVE_FWD, p, v, nrhs, st);
   launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
                 ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, topwork, st);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
-    sweep_phase<T>(F, SWEEP_SOLVE_BWD, *it, v, nrhs);
+    sweep_phase<T>(F, SWEEP_SOLVE_BWD, *it, v, nrhs, st);
   launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, x, F.n, nrhs, st);
   check_launch("rss_solve_noalloc");
   CK(cudaStreamSynchronize(st));
@@ -2046,6 +2129,7 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
       F->px.radius = o.proxy_radius > 0 ? o.proxy_radius : 2.5;
       F->eps = eps;
       F->flags = o.flags;
+      F->use_graphs = o.use_graphs != 0;
       run_factor(*F);
     };
     // A proposal that leaves a level short of storage costs one more run with

@@ -32,6 +32,13 @@ long long launches_total() { return g_launches.load(std::memory_order_relaxed); 
 
 constexpr int NT = 256;  // threads per CTA for the per-box kernels
 
+// Kernel attributes are set outside stream capture only (a captured launch
+// reuses the attribute set by an earlier uncaptured one).
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 // ---------------------------------------------------------------------------
 // Assembly of pair blocks / top block
 // ---------------------------------------------------------------------------
@@ -2587,13 +2594,14 @@ void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const 
                          int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st) {
   if (nwork == 0) return;
   const size_t smem = ((size_t)4 * bmax + NT) * nrhs * sizeof(T) + 64;
+  constexpr int SMAX = (200 << 10) + 64;  // callers keep smem within this
 #define RSS_SWEEP_NR(NRV)                                                                                   \
   case NRV:                                                                                                \
     if (mode == SWEEP_SOLVE_FWD) {                                                                         \
-      cudaFuncSetAttribute(k_sweep_fwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+      if (!capturing(st)) cudaFuncSetAttribute(k_sweep_fwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX); \
       k_sweep_fwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt);                           \
     } else {                                                                                               \
-      cudaFuncSetAttribute(k_sweep_bwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+      if (!capturing(st)) cudaFuncSetAttribute(k_sweep_bwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX); \
       k_sweep_bwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt, pbuf, poff);               \
     }                                                                                                      \
     break;
@@ -2621,7 +2629,7 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
     jsh = 0;
     smem = (size_t)3 * bmax * nrhs * sizeof(T) + 64;
   }
-  cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!capturing(st)) cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (200 << 10) + 64);
   k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs, jsh); count_launch();
 }
 

@@ -213,14 +213,14 @@ class Factorization:
 
     def __init__(self, pts, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
                  weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
-                 profile: bool = False, flags: int = 0, mlp=None):
+                 profile: bool = False, flags: int = 0, mlp=None, use_graphs: bool = True):
         torch = _torch()
         pts = _dev_f64(pts)
         self.n, self.dim = pts.shape
         self.prec = prec
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
-        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags),
+        opts = _Options(prec, n_proxy, proxy_radius, int(use_graphs), C.c_void_p(st.cuda_stream), int(profile), int(flags),
                         mlp.h if mlp is not None else None)
         h = C.c_void_p()
         _check(lib().rss_factor(C.c_void_p(pts.data_ptr()), self.n, self.dim, _Kernel(kind, diag, weight),
@@ -230,7 +230,7 @@ class Factorization:
     @classmethod
     def batched(cls, pts_list, kind: int, eps: float, leaf: int = 64, prec: int = FP64, diag: float = 1.0,
                 weight: float = 0.0, n_proxy: int = 0, proxy_radius: float = 0.0, stream=None,
-                profile: bool = False, flags: int = 0, mlp=None):
+                profile: bool = False, flags: int = 0, mlp=None, use_graphs: bool = True):
         """rss_factor_batched: one handle for several independent problems;
         vectors are the problems' vectors concatenated in order."""
         torch = _torch()
@@ -244,7 +244,7 @@ class Factorization:
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
         self._keep = pts
-        opts = _Options(prec, n_proxy, proxy_radius, 0, C.c_void_p(st.cuda_stream), int(profile), int(flags),
+        opts = _Options(prec, n_proxy, proxy_radius, int(use_graphs), C.c_void_p(st.cuda_stream), int(profile), int(flags),
                         mlp.h if mlp is not None else None)
         arr = (C.c_void_p * len(pts))(*[p.data_ptr() for p in pts])
         ns = (C.c_int64 * len(pts))(*self.sizes)

@@ -347,3 +347,21 @@ def test_autotuner_choices_are_reproducible(pkg):
     for f in (f1, f3):
         err = torch.linalg.norm(f.apply(x) - ax) / torch.linalg.norm(ax)
         assert float(err) <= 10 * 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_solve_matches_stream_solve(pkg, prec):
+    """A solve replayed from its captured CUDA graph equals the same solve
+    launched kernel by kernel, bit for bit, for every specialised width and
+    on repeated replays with new data; so does the refined solve."""
+    pts = inputs.random_points(92, 6000, 2)
+    kw = dict(leaf=64, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+    fg = pkg.Factorization(_cuda(pts), 0, 1e-6, use_graphs=True, **kw)
+    fs = pkg.Factorization(_cuda(pts), 0, 1e-6, use_graphs=False, **kw)
+    for seed, m in [(41, 1), (42, 2), (43, 4), (44, 4), (45, 1)]:
+        B = _cuda(inputs.rhs(seed, len(pts), m))
+        assert torch.equal(fg.solve(B), fs.solve(B))
+    B = _cuda(inputs.rhs(46, len(pts), 4))
+    xg, ig, rg = fg.solve_refined(B, tol=1e-10, maxit=10)
+    xs, is_, rs = fs.solve_refined(B, tol=1e-10, maxit=10)
+    assert ig == is_ and rg == rs and torch.equal(xg, xs)
