@@ -907,19 +907,23 @@ static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vect
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: the ID kernel's fold groups per box (how many thread groups
-// split a box's rows) trade latency per box against boxes resident per SM;
-// the best value depends on the box width and the number of boxes in a
-// colour phase.  The first phase that meets a (precision, width class,
+// Autotuner: the ID kernel's launch shape -- threads per column (each
+// thread keeps 32 rows (FP32) of every panel, so more threads per column
+// mean taller panels and fewer sequential reflector steps) and fold groups
+// per box (how many thread groups split a box's rows) -- trades latency per
+// box against boxes resident per SM; the best shape depends on the box width
+// and the number of boxes in a colour phase.  The first phase that meets a (precision, width class,
 // phase-size class) key times every candidate on that phase (the ID launch
 // is idempotent: it only writes the boxes' ID results), keeps the fastest
 // for the rest of the process and re-runs it, so every factorization with
 // that key computes exactly the same thing.
 // ---------------------------------------------------------------------------
 
+// Candidate launch shapes (threads per column, fold groups per box).
+static const int kTuneShapes[8][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}};
 struct TuneEntry {
-  int groups;
-  float us[3];  // time of each candidate (1, 2, 4 groups), microseconds; 0 if not tried
+  int shape;    // index into kTuneShapes
+  float us[8];  // time of each candidate, microseconds; 0 if not a candidate
 };
 static std::mutex g_tune_m;
 static std::map<std::tuple<int, int, int>, TuneEntry> g_tune;
@@ -935,22 +939,23 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
   int bucket = 0;
   while ((2 << bucket) <= nbox) bucket++;
   const auto key = std::make_tuple((int)sizeof(T), bmax <= 64 ? 64 : 128, bucket);
-  int G = 0;
+  const int width = bmax <= 64 ? 64 : 128;
+  int shape = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_m);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) G = it->second.groups;
+    if (it != g_tune.end()) shape = it->second.shape;
   }
-  if (G == 0) {
-    const int cands[3] = {1, 2, 4};
-    const int ncand = bmax <= 64 ? 3 : 2;
-    TuneEntry te{0, {0.f, 0.f, 0.f}};
+  if (shape < 0) {
+    TuneEntry te{-1, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.f;
-    for (int ci = 0; ci < ncand; ci++) {
-      set_id_groups(cands[ci]);
+    for (int ci = 0; ci < 8; ci++) {
+      const int tpc = kTuneShapes[ci][0], g = kTuneShapes[ci][1];
+      if (width * tpc * g > (tpc == 1 ? 256 : 512)) continue;  // the kernels' thread limits
+      set_id_groups(tpc * 16 + g);
       float ms = 0.f;
       for (int rep = 0; rep < 2; rep++) {  // the second launch is timed
         CK(cudaEventRecord(e0, F.st));
@@ -959,19 +964,19 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
       }
-      te.us[ci] = 1e3f * ms;
-      if (te.groups == 0 || ms < best) {
+      te.us[ci] = std::max(1e3f * ms, 1e-3f);
+      if (te.shape < 0 || ms < best) {
         best = ms;
-        te.groups = cands[ci];
+        te.shape = ci;
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lk(g_tune_m);
     auto ins = g_tune.insert({key, te});
-    G = ins.first->second.groups;  // another thread may have tuned the key first
+    shape = ins.first->second.shape;  // another thread may have tuned the key first
   }
-  set_id_groups(G);
+  set_id_groups(kTuneShapes[shape][0] * 16 + kTuneShapes[shape][1]);
   launch();
   set_id_groups(0);
 }
@@ -2452,8 +2457,9 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
         v.push_back(std::get<0>(kv.first));
         v.push_back(std::get<1>(kv.first));
         v.push_back(std::get<2>(kv.first));
-        v.push_back(kv.second.groups);
-        for (int c = 0; c < 3; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
+        v.push_back(kTuneShapes[kv.second.shape][0]);
+        v.push_back(kTuneShapes[kv.second.shape][1]);
+        for (int c = 0; c < 8; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
       }
     }
     const size_t need = v.size() * sizeof(int32_t), cap = *nbytes;
@@ -2463,6 +2469,25 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
       if (need) memcpy(buf, v.data(), need);
     }
   });
+}
+
+rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups) {
+  return guard([&] {
+    int shape = -1;
+    for (int c = 0; c < 8; c++)
+      if (kTuneShapes[c][0] == tpc && kTuneShapes[c][1] == groups) shape = c;
+    if (shape < 0 || (elem_bytes != 4 && elem_bytes != 8) || (width != 64 && width != 128) || phase_class < 0 ||
+        phase_class > 40 || width * tpc * groups > (tpc == 1 ? 256 : 512))
+      throw Fail{RSS_EINVAL, "rss_autotune_set: bad arguments"};
+    std::lock_guard<std::mutex> lk(g_tune_m);
+    TuneEntry te{shape, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+    g_tune[std::make_tuple(elem_bytes, width, phase_class)] = te;
+  });
+}
+
+void rss_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_m);
+  g_tune.clear();
 }
 
 void rss_free(void *handle) {

@@ -90,7 +90,8 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
                int mmax, const Points &P, const KernelParams &K, const ProxyParams &px,
                const double *proxy_unit, double eps, T *gscratch, int64_t gscratch_stride, bool use_smem,
                cudaStream_t st, int *err);
-// Fold groups per box of the next k_idc launch on this thread (0: default).
+// Launch shape of the next ID launch on this thread: threads per column x 16
+// + fold groups per box (0: default).
 void set_id_groups(int G);
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,

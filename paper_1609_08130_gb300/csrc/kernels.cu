@@ -1203,6 +1203,367 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same column-per-thread ID with TPC threads per column and panels of
+// PR = TPC x RPT rows: thread `part` of column c holds rows part*RPT .. +RPT
+// of each panel, with the partial sums of a column combined by shuffles
+// among its TPC lanes.  Each thread does the work per reflector step of
+// k_idc, but a panel holds TPC times as many rows, so a box takes TPC times
+// fewer sequential steps.  The reflectors, the triangle and the greedy
+// pivoting are those of k_idc; only the order of partial sums differs.
+// ---------------------------------------------------------------------------
+
+template <int TPC> __device__ __forceinline__ unsigned col_mask() {
+  return TPC == 1 ? 0xffffffffu : (((1u << TPC) - 1u) << ((threadIdx.x & 31) & ~(TPC - 1)));
+}
+template <typename T, int TPC> __device__ __forceinline__ T col_sum(T v) {
+  const unsigned m = col_mask<TPC>();
+#pragma unroll
+  for (int o = 1; o < TPC; o <<= 1) v += __shfl_xor_sync(m, v, o);
+  return v;
+}
+
+// The TPC threads of the owner column publish [v (PR entries) | tau | scl |
+// beta | flag] for the next reflector; see publish_reflector.
+template <typename T, int PR, int TPC>
+__device__ __forceinline__ void publish_part(T *dst, const T (&pan)[PR / TPC], T x0, int part) {
+  constexpr int RPT = PR / TPC;
+  T s0 = (T)0, s1 = (T)0;
+#pragma unroll
+  for (int i = 0; i < RPT; i += 2) {
+    s0 += pan[i] * pan[i];
+    s1 += pan[i + 1] * pan[i + 1];
+  }
+  const T s = col_sum<T, TPC>(s0 + s1);
+#pragma unroll
+  for (int i = 0; i < RPT; i++) dst[part * RPT + i] = pan[i];
+  if (part == 0) {
+    if (s > (T)0) {
+      const T nrm = sqrt(x0 * x0 + s);
+      const T beta = x0 >= (T)0 ? -nrm : nrm;
+      dst[PR] = (beta - x0) / beta;
+      dst[PR + 1] = (T)1 / (x0 - beta);
+      dst[PR + 2] = beta;
+      dst[PR + 3] = (T)1;
+    } else {
+      dst[PR + 3] = (T)0;
+    }
+  }
+}
+
+template <typename T, int PR, int TPC>
+__device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, int b, int col, int part, T *vbuf,
+                                             int bar_id, int nthr) {
+  constexpr int VS = PR + 4, RPT = PR / TPC;
+  if (col == 0 && b > 0) publish_part<T, PR, TPC>(vbuf, pan, R[0], part);
+  for (int j = 0; j < b; j++) {
+    group_bar(bar_id, nthr);
+    const T *vb = vbuf + (j & 1) * VS;
+    T *vn = vbuf + ((j + 1) & 1) * VS;
+    const T flag = vb[PR + 3];
+    if (flag != (T)0) {
+      if (col > j && col < b) {
+        T v[RPT];
+#pragma unroll
+        for (int i = 0; i < RPT; i++) v[i] = vb[part * RPT + i];
+        const T tau = vb[PR], scl = vb[PR + 1];
+        T d0 = (T)0, d1 = (T)0;
+#pragma unroll
+        for (int i = 0; i < RPT; i += 2) {
+          d0 += v[i] * pan[i];
+          d1 += v[i + 1] * pan[i + 1];
+        }
+        const T rj = R[j * ldr + col];
+        const T dd = col_sum<T, TPC>(d0 + d1);  // also orders the read of rj before the write below
+        const T f = tau * (rj + scl * dd);
+        const T fs = f * scl;
+#pragma unroll
+        for (int i = 0; i < RPT; i++) pan[i] -= fs * v[i];
+        if (part == 0) R[j * ldr + col] = rj - f;
+        if (col == j + 1) publish_part<T, PR, TPC>(vn, pan, R[col * ldr + col], part);
+      } else if (col == j && part == 0) {
+        R[j * ldr + j] = vb[PR + 2];
+      }
+    } else if (col == j + 1 && col < b) {
+      publish_part<T, PR, TPC>(vn, pan, R[col * ldr + col], part);
+    }
+  }
+  group_bar(bar_id, nthr);
+}
+
+template <typename T, int NC, int TPC>
+__global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
+                                             Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
+                                             double eps, int ring_max, int *err) {
+  constexpr int RPT = IdwRows<T>::PR;
+  constexpr int PR = RPT * TPC;
+  constexpr int LDR = NC + 1;
+  constexpr int VS = PR + 4;
+  constexpr int GT = NC * TPC;  // threads per fold group
+  static_assert(RPT % 2 == 0, "rows per thread");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ocode[125], s_obase[126], s_no;
+  __shared__ T s_red_v[16];
+  __shared__ int s_red_i[16];
+  __shared__ T s_hh[4];
+  __shared__ int s_stop, s_piv, s_k;
+  const int tid = threadIdx.x;
+  const int grp = tid / GT, lt = tid % GT;
+  const int col = lt / TPC, part = lt % TPC;
+  const int bar_id = 1 + grp;
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int c = fb.cell, b = fb.b, dim = lv.dim;
+  T *Rg = reinterpret_cast<T *>(smem_raw) + (size_t)grp * NC * LDR;
+  const size_t tri_bytes = (((size_t)G * NC * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)grp * 2 * VS;
+  int64_t *s_rowsrc =
+      reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)G * 2 * VS * sizeof(T) + 15) & ~(size_t)15));
+  int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
+
+  for (int e = lt; e < NC * LDR; e += GT) Rg[e] = (T)0;
+  if (tid < 32) {
+    const int ncode = dim == 3 ? 125 : 25;
+    int no = 0, acc = 0;
+    for (int base = 0; base < ncode; base += 32) {
+      int code = base + tid, cnt = 0;
+      if (code < ncode) {
+        int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+        if (max(abs(dx), max(abs(dy), abs(dz))) == 2) {
+          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+          if (nb >= 0) cnt = lv.act_cnt[nb];
+        }
+      }
+      unsigned mask = __ballot_sync(FULL, cnt > 0);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, o);
+        if (tid >= o) incl += t;
+      }
+      int pos = __popc(mask & ((1u << tid) - 1));
+      if (cnt > 0) {
+        s_ocode[no + pos] = code;
+        s_obase[no + pos] = acc + incl - cnt;
+      }
+      no += __popc(mask);
+      acc += __shfl_sync(FULL, incl, 31);
+    }
+    if (tid == 0) {
+      s_obase[no] = acc;
+      s_no = no;
+    }
+  }
+  __syncthreads();
+  const int no = s_no;
+  const int nO = s_obase[no];
+  if (nO > ring_max) {
+    if (tid == 0) set_err(err, DERR_INTERNAL);
+    return;
+  }
+  for (int q = 0; q < no; q++) {
+    const int code = s_ocode[q];
+    const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+    const int64_t abase = lv.cell_dof_off[nb];
+    const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
+    for (int t = tid; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
+      s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+  }
+  __syncthreads();
+  const int m = nO + px.np;
+  const int64_t coff = lv.cell_dof_off[c];
+  const double D = ldexp(1.0, -lv.t);
+  const double rad = px.radius * D;
+  double xq[3];
+  {
+    const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
+      xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+    }
+  }
+  const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
+  const int npan = (m + PR - 1) / PR;
+  for (int pnl = grp; pnl < npan; pnl += G) {
+    T pan[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+      const int row = pnl * PR + part * RPT + i;
+      T v = (T)0;
+      if (col < b) {
+        if (row < nO) {
+          v = lv.pool[s_rowsrc[row] + col];
+        } else if (row < m) {
+          const int pm = row - nO;
+          double r2 = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; d++) {
+            const double dd = rad * proxy_unit[3 * pm + d] - xq[d];
+            r2 += dd * dd;
+          }
+          v = w * kof(K.kind, (T)r2);
+        }
+      }
+      pan[i] = v;
+    }
+    fold_group_q<T, PR, TPC>(pan, Rg, LDR, b, col, part, vbuf, bar_id, GT);
+  }
+  for (int step = 1; step < G; step <<= 1) {
+    __syncthreads();
+    if (grp % (2 * step) == 0 && grp + step < G) {
+      const T *Ro = Rg + (size_t)step * NC * LDR;
+      for (int p0 = 0; p0 < b; p0 += PR) {
+        T pan[RPT];
+#pragma unroll
+        for (int i = 0; i < RPT; i++) {
+          const int row = p0 + part * RPT + i;
+          pan[i] = (row < b && col < b) ? Ro[row * LDR + col] : (T)0;
+        }
+        fold_group_q<T, PR, TPC>(pan, Rg, LDR, b, col, part, vbuf, bar_id, GT);
+      }
+    }
+  }
+  __syncthreads();
+  if (grp != 0) return;
+  // greedy column-pivoted QR of the triangle; column `col`, rows split over its TPC threads
+  T *R = Rg;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = GT / 32;
+  if (lt < b) perm[lt] = lt;
+  if (tid == 0) s_k = b;
+  T r11 = (T)0;
+  for (int j = 0; j < b; j++) {
+    T best = (T)-1;
+    int bi = b;
+    {
+      T a0 = (T)0;
+      if (col >= j && col < b)
+        for (int i = j + part; i < b; i += TPC) a0 += R[i * LDR + col] * R[i * LDR + col];
+      a0 = col_sum<T, TPC>(a0);
+      if (col >= j && col < b && part == 0) {
+        best = a0;
+        bi = col;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(FULL, best, o);
+      int oi = __shfl_xor_sync(FULL, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_red_v[wid] = best;
+      s_red_i[wid] = bi;
+    }
+    group_bar(1, GT);
+    if (tid == 0) {
+      for (int u = 1; u < NW; u++)
+        if (s_red_v[u] > best || (s_red_v[u] == best && s_red_i[u] < bi)) {
+          best = s_red_v[u];
+          bi = s_red_i[u];
+        }
+      const T cn = sqrt(best);
+      if (j == 0) r11 = cn;
+      const int stop = (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
+      s_stop = stop;
+      s_piv = bi;
+      if (stop) s_k = j;
+    }
+    group_bar(1, GT);
+    if (s_stop) break;
+    const int p = s_piv;
+    if (p != j) {
+      for (int i = lt; i < b; i += GT) {
+        T t0 = R[i * LDR + j];
+        R[i * LDR + j] = R[i * LDR + p];
+        R[i * LDR + p] = t0;
+      }
+      if (tid == 0) {
+        int tp = perm[j];
+        perm[j] = perm[p];
+        perm[p] = tp;
+      }
+    }
+    group_bar(1, GT);
+    if (col == j) {
+      T a0 = (T)0;
+      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + j];
+      const T sacc = col_sum<T, TPC>(a0);
+      if (part == 0) {
+        const T x0 = R[j * LDR + j];
+        if (sacc > (T)0) {
+          const T nrm = sqrt(x0 * x0 + sacc);
+          const T beta = x0 >= (T)0 ? -nrm : nrm;
+          s_hh[0] = x0;
+          s_hh[1] = beta;
+          s_hh[2] = (beta - x0) / beta;
+          s_hh[3] = (T)1 / (x0 - beta);
+        } else {
+          s_hh[2] = (T)0;
+        }
+      }
+    }
+    group_bar(1, GT);
+    const T tau = s_hh[2];
+    if (tau != (T)0 && col > j && col < b) {
+      const T scl = s_hh[3];
+      T a0 = (T)0;
+      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + col];
+      const T rjc = R[j * LDR + col];
+      const T d = col_sum<T, TPC>(a0);
+      const T f = tau * (rjc + scl * d);
+      const T fs = f * scl;
+      if (part == 0) R[j * LDR + col] = rjc - f;
+      for (int i = j + 1 + part; i < b; i += TPC) R[i * LDR + col] -= fs * R[i * LDR + j];
+    }
+    group_bar(1, GT);
+    if (tau != (T)0 && col == j && part == 0) R[j * LDR + j] = s_hh[1];
+    group_bar(1, GT);
+  }
+  group_bar(1, GT);
+  const int k = s_k;
+  const int r = b - k;
+  for (int cc = lt; cc < r; cc += GT) {
+    T *tcol = fb.Tm + (int64_t)cc * k;
+    for (int i = k - 1; i >= 0; i--) {
+      T sacc = R[i * LDR + k + cc];
+      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
+      tcol[i] = sacc / R[i * LDR + i];
+    }
+  }
+  if (lt < b) {
+    fb.loc[lt] = perm[lt];
+    fb.ids[lt] = lv.cell_dofs[coff + perm[lt]];
+  }
+  if (tid == 0) {
+    fb.k = k;
+    fb.r = r;
+    fb.no = nO;
+  }
+}
+
+template <typename T, int NC, int TPC>
+static void launch_idq(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       double eps, int ring_max, cudaStream_t st, int *err) {
+  constexpr int PR = IdwRows<T>::PR * TPC;
+  const size_t tri = (size_t)NC * (NC + 1) * sizeof(T);
+  int gmax = (int)((190u << 10) / tri);
+  if (gmax < 1) gmax = 1;
+  if (G > gmax) G = gmax;
+  if (G * NC * TPC > 512) G = 512 / (NC * TPC);
+  if (G < 1) G = 1;
+  size_t smem = (((size_t)G * tri + 15) & ~(size_t)15) + (((size_t)G * 2 * (PR + 4) * sizeof(T) + 15) & ~(size_t)15) +
+                (size_t)ring_max * sizeof(int64_t) + (size_t)NC * sizeof(int) + 16;
+  cudaFuncSetAttribute(k_idq<T, NC, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idq<T, NC, TPC><<<nbox, G * NC * TPC, smem, st>>>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps,
+                                                      ring_max, err);
+  count_launch();
+}
+
 template <typename T, int NC>
 static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
                        const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
@@ -1239,8 +1600,9 @@ static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
   count_launch();
 }
 
-// Fold groups per box for the next k_idc launch (0: default).  Set by the
-// host's autotuner around a launch_id call on the same thread.
+// Launch shape of the next ID launch on this thread: fold groups per box
+// (hint % 16) and threads per column (hint / 16; 0 or 1: k_idc); 0: default.
+// Set by the host's autotuner around a launch_id call.
 static thread_local int id_groups_hint = 0;
 void set_id_groups(int G) { id_groups_hint = G; }
 
@@ -1258,10 +1620,18 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     // width, phase size), else the default (enough boxes resident at once to
     // finish a large phase in one wave, more groups per box when small)
     const int NCw = bmax <= 64 ? 64 : 128;
-    int G = id_groups_hint;
+    int G = id_groups_hint % 16, TPC = id_groups_hint / 16;
     if (G <= 0) G = NCw == 64 ? (nbox >= 300 ? 2 : 4) : (nbox >= 300 ? 1 : 2);
-    if (NCw == 64) launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
-    else launch_idc<T, 128>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+    if (TPC <= 0) TPC = 1;
+    if (NCw == 64) {
+      if (TPC == 4) launch_idq<T, 64, 4>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (TPC == 2) launch_idq<T, 64, 2>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+    } else {
+      if (TPC == 4) launch_idq<T, 128, 4>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (TPC == 2) launch_idq<T, 128, 2>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else launch_idc<T, 128>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+    }
     return;
   }
   int PR = bmax <= 80 ? 128 : 64;

@@ -337,8 +337,11 @@ def test_autotuner_choices_are_reproducible(pkg):
     tab = pkg.autotune_table()
     assert tab, "no autotuner entries after a factorization"
     for e in tab:
-        assert e["groups"] in (1, 2, 4) and e["width"] in (64, 128) and e["elem_bytes"] in (4, 8)
-        assert e["us"][(1, 2, 4).index(e["groups"])] > 0
+        assert (e["tpc"], e["groups"]) in pkg.rss.AUTOTUNE_SHAPES
+        assert e["width"] in (64, 128) and e["elem_bytes"] in (4, 8)
+        chosen = pkg.rss.AUTOTUNE_SHAPES.index((e["tpc"], e["groups"]))
+        tried = [u for u in e["us"] if u > 0]
+        assert e["us"][chosen] > 0 and e["us"][chosen] == min(tried)
     f2 = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=pkg.MIXED)
     x = _cuda(inputs.rhs(31, n, 2))
     assert torch.equal(f1.solve(x), f2.solve(x))
@@ -365,3 +368,34 @@ def test_graph_solve_matches_stream_solve(pkg, prec):
     xg, ig, rg = fg.solve_refined(B, tol=1e-10, maxit=10)
     xs, is_, rs = fs.solve_refined(B, tol=1e-10, maxit=10)
     assert ig == is_ and rg == rs and torch.equal(xg, xs)
+
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_id_launch_shape_matches_oracle(pkg, prec):
+    """Each launch shape the autotuner may pick (threads per column, fold
+    groups per box), pinned for every key, gives a factor within 10 eps of
+    the oracle's."""
+    lib = pkg.lib()
+    pts = inputs.random_points(93, 3000, 2)  # boxes of width class 64 and 128
+    eps = 1e-6
+    of = oracle.Factor(oracle.Tree(pts, 64), 0, eps)
+    x = inputs.normal(94, len(pts))
+    yo, zo = of.apply(x), of.solve(x)
+    elem = 8 if prec == "fp64" else 4
+    try:
+        for tpc, g in pkg.rss.AUTOTUNE_SHAPES:
+            lib.rss_autotune_clear()
+            for width in (64, 128):
+                if width * tpc * g > (256 if tpc == 1 else 512):
+                    continue
+                for cls in range(0, 20):
+                    assert lib.rss_autotune_set(elem, width, cls, tpc, g) == 0
+            f = pkg.Factorization(_cuda(pts), 0, eps, leaf=64, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
+            y = f.apply(_cuda(x)).cpu().numpy()
+            z = f.solve(_cuda(x)).cpu().numpy()
+            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, (tpc, g)
+            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, g)
+    finally:
+        lib.rss_autotune_clear()
+    assert lib.rss_autotune_set(4, 64, 3, 4, 4) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
