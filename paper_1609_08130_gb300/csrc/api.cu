@@ -930,7 +930,7 @@ static std::map<std::tuple<int, int, int>, TuneEntry> g_tune;
 
 template <typename T, typename Launch>
 static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
-  const bool tunable = bmax > 0 && bmax <= 128 && !(F.flags & RSS_FLAG_NO_AUTOTUNE);
+  const bool tunable = bmax > 0 && bmax <= 256 && !(F.flags & RSS_FLAG_NO_AUTOTUNE);
   if (!tunable) {
     set_id_groups(0);
     launch();
@@ -938,8 +938,8 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
   }
   int bucket = 0;
   while ((2 << bucket) <= nbox) bucket++;
-  const auto key = std::make_tuple((int)sizeof(T), bmax <= 64 ? 64 : 128, bucket);
-  const int width = bmax <= 64 ? 64 : 128;
+  const int width = bmax <= 64 ? 64 : (bmax <= 128 ? 128 : 256);
+  const auto key = std::make_tuple((int)sizeof(T), width, bucket);
   int shape = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_m);
@@ -2476,7 +2476,8 @@ rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc,
     int shape = -1;
     for (int c = 0; c < 8; c++)
       if (kTuneShapes[c][0] == tpc && kTuneShapes[c][1] == groups) shape = c;
-    if (shape < 0 || (elem_bytes != 4 && elem_bytes != 8) || (width != 64 && width != 128) || phase_class < 0 ||
+    if (shape < 0 || (elem_bytes != 4 && elem_bytes != 8) || (width != 64 && width != 128 && width != 256) ||
+        phase_class < 0 ||
         phase_class > 40 || width * tpc * groups > (tpc == 1 ? 256 : 512))
       throw Fail{RSS_EINVAL, "rss_autotune_set: bad arguments"};
     std::lock_guard<std::mutex> lk(g_tune_m);

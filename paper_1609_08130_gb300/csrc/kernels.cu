@@ -861,6 +861,17 @@ __device__ __forceinline__ void publish_reflector(T *dst, const T (&pan)[PR], T 
 }
 
 template <typename T, int PR> __device__ __forceinline__ void load_vec(T (&v)[PR], const T *src);
+template <typename T, int PR> __device__ __forceinline__ void store_vec(T *dst, const T (&v)[PR]);
+template <> __device__ __forceinline__ void store_vec<float, 32>(float *dst, const float (&v)[32]) {
+  float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; i++) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+template <> __device__ __forceinline__ void store_vec<double, 16>(double *dst, const double (&v)[16]) {
+  double2 *d2 = reinterpret_cast<double2 *>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; i++) d2[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
 template <> __device__ __forceinline__ void load_vec<float, 32>(float (&v)[32], const float *src) {
   const float4 *s4 = reinterpret_cast<const float4 *>(src);
 #pragma unroll
@@ -1235,8 +1246,7 @@ __device__ __forceinline__ void publish_part(T *dst, const T (&pan)[PR / TPC], T
     s1 += pan[i + 1] * pan[i + 1];
   }
   const T s = col_sum<T, TPC>(s0 + s1);
-#pragma unroll
-  for (int i = 0; i < RPT; i++) dst[part * RPT + i] = pan[i];
+  store_vec<T, RPT>(dst + part * RPT, pan);
   if (part == 0) {
     if (s > (T)0) {
       const T nrm = sqrt(x0 * x0 + s);
@@ -1264,8 +1274,7 @@ __device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, 
     if (flag != (T)0) {
       if (col > j && col < b) {
         T v[RPT];
-#pragma unroll
-        for (int i = 0; i < RPT; i++) v[i] = vb[part * RPT + i];
+        load_vec<T, RPT>(v, vb + part * RPT);  // 16-byte aligned: VS and RPT are multiples of 4 (FP32) / 2 (FP64)
         const T tau = vb[PR], scl = vb[PR + 1];
         T d0 = (T)0, d1 = (T)0;
 #pragma unroll
@@ -1297,7 +1306,6 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
                                              double eps, int ring_max, int *err) {
   constexpr int RPT = IdwRows<T>::PR;
   constexpr int PR = RPT * TPC;
-  constexpr int LDR = NC + 1;
   constexpr int VS = PR + 4;
   constexpr int GT = NC * TPC;  // threads per fold group
   static_assert(RPT % 2 == 0, "rows per thread");
@@ -1313,14 +1321,17 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
   const int bar_id = 1 + grp;
   FBox<T> &fb = boxes[box_list[blockIdx.x]];
   const int c = fb.cell, b = fb.b, dim = lv.dim;
-  T *Rg = reinterpret_cast<T *>(smem_raw) + (size_t)grp * NC * LDR;
-  const size_t tri_bytes = (((size_t)G * NC * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  // triangle rows x leading dimension: NC x (NC+1), or for the widest class
+  // b x (b+1) (one group; shared memory sized by the level's widest box)
+  const int TR = NC > 128 ? b : NC, LDR = TR + 1;
+  T *Rg = reinterpret_cast<T *>(smem_raw) + (size_t)grp * TR * LDR;
+  const size_t tri_bytes = (((size_t)G * TR * LDR * sizeof(T)) + 15) & ~(size_t)15;
   T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)grp * 2 * VS;
   int64_t *s_rowsrc =
       reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)G * 2 * VS * sizeof(T) + 15) & ~(size_t)15));
   int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
 
-  for (int e = lt; e < NC * LDR; e += GT) Rg[e] = (T)0;
+  for (int e = lt; e < TR * LDR; e += GT) Rg[e] = (T)0;
   if (tid < 32) {
     const int ncode = dim == 3 ? 125 : 25;
     int no = 0, acc = 0;
@@ -1411,7 +1422,7 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
   for (int step = 1; step < G; step <<= 1) {
     __syncthreads();
     if (grp % (2 * step) == 0 && grp + step < G) {
-      const T *Ro = Rg + (size_t)step * NC * LDR;
+      const T *Ro = Rg + (size_t)step * TR * LDR;
       for (int p0 = 0; p0 < b; p0 += PR) {
         T pan[RPT];
 #pragma unroll
@@ -1545,19 +1556,29 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
   }
 }
 
+// Shared memory of a k_idq launch (see the kernel's layout).
+template <typename T, int NC, int TPC> static size_t idq_smem(int bmax, int G, int ring_max) {
+  constexpr int PR = IdwRows<T>::PR * TPC;
+  const int TR = NC > 128 ? bmax : NC;
+  const size_t tri = (size_t)TR * (TR + 1) * sizeof(T);
+  return (((size_t)G * tri + 15) & ~(size_t)15) + (((size_t)G * 2 * (PR + 4) * sizeof(T) + 15) & ~(size_t)15) +
+         (size_t)ring_max * sizeof(int64_t) + (size_t)NC * sizeof(int) + 16;
+}
+
 template <typename T, int NC, int TPC>
-static void launch_idq(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
+static void launch_idq(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G, int bmax,
                        const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
                        double eps, int ring_max, cudaStream_t st, int *err) {
   constexpr int PR = IdwRows<T>::PR * TPC;
-  const size_t tri = (size_t)NC * (NC + 1) * sizeof(T);
+  const int TR = NC > 128 ? bmax : NC;
+  const size_t tri = (size_t)TR * (TR + 1) * sizeof(T);
   int gmax = (int)((190u << 10) / tri);
   if (gmax < 1) gmax = 1;
   if (G > gmax) G = gmax;
   if (G * NC * TPC > 512) G = 512 / (NC * TPC);
   if (G < 1) G = 1;
-  size_t smem = (((size_t)G * tri + 15) & ~(size_t)15) + (((size_t)G * 2 * (PR + 4) * sizeof(T) + 15) & ~(size_t)15) +
-                (size_t)ring_max * sizeof(int64_t) + (size_t)NC * sizeof(int) + 16;
+  (void)PR;
+  const size_t smem = idq_smem<T, NC, TPC>(bmax, G, ring_max);
   cudaFuncSetAttribute(k_idq<T, NC, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_idq<T, NC, TPC><<<nbox, G * NC * TPC, smem, st>>>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps,
                                                       ring_max, err);
@@ -1624,15 +1645,25 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     if (G <= 0) G = NCw == 64 ? (nbox >= 300 ? 2 : 4) : (nbox >= 300 ? 1 : 2);
     if (TPC <= 0) TPC = 1;
     if (NCw == 64) {
-      if (TPC == 4) launch_idq<T, 64, 4>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
-      else if (TPC == 2) launch_idq<T, 64, 2>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+      if (TPC == 4) launch_idq<T, 64, 4>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (TPC == 2) launch_idq<T, 64, 2>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
       else launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
     } else {
-      if (TPC == 4) launch_idq<T, 128, 4>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
-      else if (TPC == 2) launch_idq<T, 128, 2>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
+      if (TPC == 4) launch_idq<T, 128, 4>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (TPC == 2) launch_idq<T, 128, 2>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
       else launch_idc<T, 128>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
     }
     return;
+  }
+  if (bmax <= 256 && !force_general) {
+    // one group per box, the triangle sized by the level's widest box
+    const int TPC = id_groups_hint / 16 == 1 ? 1 : 2;
+    const size_t sm = TPC == 1 ? idq_smem<T, 256, 1>(bmax, 1, mmax) : idq_smem<T, 256, 2>(bmax, 1, mmax);
+    if (sm <= (size_t)(220 << 10)) {
+      if (TPC == 1) launch_idq<T, 256, 1>(lv, boxes, box_list, nbox, 1, bmax, P, K, px, proxy_unit, eps, mmax, st, err);
+      else launch_idq<T, 256, 2>(lv, boxes, box_list, nbox, 1, bmax, P, K, px, proxy_unit, eps, mmax, st, err);
+      return;
+    }
   }
   int PR = bmax <= 80 ? 128 : 64;
   IdLayout<T> lay(bmax, PR);

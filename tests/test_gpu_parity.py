@@ -338,7 +338,7 @@ def test_autotuner_choices_are_reproducible(pkg):
     assert tab, "no autotuner entries after a factorization"
     for e in tab:
         assert (e["tpc"], e["groups"]) in pkg.rss.AUTOTUNE_SHAPES
-        assert e["width"] in (64, 128) and e["elem_bytes"] in (4, 8)
+        assert e["width"] in (64, 128, 256) and e["elem_bytes"] in (4, 8)
         chosen = pkg.rss.AUTOTUNE_SHAPES.index((e["tpc"], e["groups"]))
         tried = [u for u in e["us"] if u > 0]
         assert e["us"][chosen] > 0 and e["us"][chosen] == min(tried)
@@ -399,3 +399,29 @@ def test_every_id_launch_shape_matches_oracle(pkg, prec):
     finally:
         lib.rss_autotune_clear()
     assert lib.rss_autotune_set(4, 64, 3, 4, 4) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
+
+
+def test_wide_box_id_matches_oracle(pkg):
+    """Boxes wider than 128 (an octree's upper level at eps 1e-3) take the ID
+    kernel whose triangle is sized by the box; the factor matches the oracle
+    within 10 eps (mixed precision, both launch shapes)."""
+    lib = pkg.lib()
+    pts = inputs.random_points(5, 10000, 3)  # 16 boxes of 129..140 DOFs at depth 2
+    eps = 1e-3
+    of = oracle.Factor(oracle.Tree(pts, 64), 1, eps)
+    x = inputs.normal(95, len(pts))
+    yo, zo = of.apply(x), of.solve(x)
+    try:
+        for tpc in (1, 2):
+            lib.rss_autotune_clear()
+            for cls in range(0, 20):
+                assert lib.rss_autotune_set(4, 256, cls, tpc, 1) == 0
+            f = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.MIXED)
+            st = f.stats()
+            assert st["b"].max() > 128, st["b"].max()
+            y = f.apply(_cuda(x)).cpu().numpy()
+            z = f.solve(_cuda(x)).cpu().numpy()
+            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, tpc
+            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, tpc
+    finally:
+        lib.rss_autotune_clear()
