@@ -1453,7 +1453,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_ELIM, st, base + p.first, p.second);
       launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ptr<T>(gel), el_stride, ovf, st,
-                     ptr<int>(F.d_err));
+                     ptr<int>(F.d_err), njmax_lvl);
       check_launch("elim");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_SCHUR, st, base + p.first, p.second);

@@ -95,7 +95,7 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
 void set_id_groups(int G);
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
-                 T *scratch, int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err);
+                 T *scratch, int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err, int njmax);
 template <typename T>
 void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_list, int nbox,
                   int njmax, const T *scratch, int64_t scratch_stride, cudaStream_t st);

@@ -1899,37 +1899,8 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
     }
     __syncthreads();
   }
-  // E = X_JR X_RR^{-1}: per row, W U = x, Z L = W, E = Z P
-  for (int a = tid; a < nj; a += NT) {
-    T *row = Ep + a;
-    for (int j = 0; j < r; j++) {
-      T s = row[(int64_t)j * nj];
-      for (int i = 0; i < j; i++) s -= row[(int64_t)i * nj] * LU[i * ldl + j];
-      row[(int64_t)j * nj] = s / LU[j * ldl + j];
-    }
-    for (int j = r - 1; j >= 0; j--) {
-      T s = row[(int64_t)j * nj];
-      for (int i = j + 1; i < r; i++) s -= row[(int64_t)i * nj] * LU[i * ldl + j];
-      row[(int64_t)j * nj] = s;
-    }
-    for (int i = 0; i < r; i++) fb.E[a + (int64_t)spiv[i] * nj] = row[(int64_t)i * nj];
-  }
-  // G = X_RR^{-1} X_RJ: per column, y = P x, forward L, backward U
-  for (int a = tid; a < nj; a += NT) {
-    const T *x = Gp + (int64_t)a * r;
-    T *y = fb.G + (int64_t)a * r;
-    for (int i = 0; i < r; i++) y[i] = x[spiv[i]];
-    for (int i = 0; i < r; i++) {
-      T s = y[i];
-      for (int l = 0; l < i; l++) s -= LU[i * ldl + l] * y[l];
-      y[i] = s;
-    }
-    for (int i = r - 1; i >= 0; i--) {
-      T s = y[i];
-      for (int l = i + 1; l < r; l++) s -= LU[i * ldl + l] * y[l];
-      y[i] = s / LU[i * ldl + i];
-    }
-  }
+  // E = X_JR X_RR^{-1} and G = X_RR^{-1} X_RJ follow in k_elim_gemm, over
+  // every box of the phase at once, from X_JR, X_RJ (scratch) and X_RR^{-1}
   for (int e = tid; e < r * r; e += NT) fb.LU[e] = LU[(e / r) * ldl + (e % r)];
   for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
   // X_RR^{-1} = U^{-1} L^{-1} P, one column per thread (column piv[i] is
@@ -2357,9 +2328,80 @@ template <typename T> int64_t elim_ws_elems(int bmax) {
 template int64_t elim_ws_elems<float>(int);
 template int64_t elim_ws_elems<double>(int);
 
+// E = X_JR X_RR^{-1} (nj x r) and G = X_RR^{-1} X_RJ (r x nj) for the boxes
+// of a phase eliminated by k_elim: blockIdx.x = box of the phase,
+// blockIdx.y = a 64 x 64 output tile of E (the first tiles_e) or of G.
+// X_JR (ld nj) and X_RJ (ld r) are in the box's scratch, X_RR^{-1} in the
+// factor (r x r, column-major).  Shared-memory tiles of 16 along the inner
+// dimension; each thread accumulates a 4 x 4 block.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_elim_gemm(const FBox<T> *boxes, const int *box_list, const T *scratch,
+                                                  int64_t sstride, int tiles_e, int tcols_e, int tcols_g) {
+  __shared__ T As[16][64 + 1];
+  __shared__ T Bs[16][64 + 1];
+  const FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int r = fb.r, nj = fb.nj;
+  if (r == 0) return;
+  const T *Xjr = scratch + (int64_t)blockIdx.x * sstride;
+  const T *Xrj = Xjr + (int64_t)nj * r;
+  const T *Xi = fb.Xi;
+  // C(i, j) = sum_l A(i, l) B(l, j); all operands column-major
+  int m, n, t = blockIdx.y, tcols = tcols_e;
+  const T *A, *B;
+  int64_t lda, ldb, ldc;
+  T *Cp;
+  if (t < tiles_e) {  // E = X_JR Xi: m = nj, n = r
+    m = nj, n = r, A = Xjr, lda = nj, B = Xi, ldb = r, Cp = fb.E, ldc = nj;
+  } else {            // G = Xi X_RJ: m = r, n = nj
+    t -= tiles_e;
+    tcols = tcols_g;
+    m = r, n = nj, A = Xi, lda = r, B = Xrj, ldb = r, Cp = fb.G, ldc = r;
+  }
+  const int i0 = (t / tcols) * 64, j0 = (t % tcols) * 64;
+  if (i0 >= m || j0 >= n) return;
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int y = 0; y < 4; y++) acc[x][y] = (T)0;
+  for (int l0 = 0; l0 < r; l0 += 16) {
+    for (int e = tid; e < 16 * 64; e += NT) {
+      const int ii = e % 64, ll = e / 64;  // A: consecutive rows
+      As[ll][ii] = (i0 + ii < m && l0 + ll < r) ? A[(i0 + ii) + (int64_t)(l0 + ll) * lda] : (T)0;
+      const int l2 = e % 16, jj = e / 16;  // B: consecutive inner index
+      Bs[l2][jj] = (l0 + l2 < r && j0 + jj < n) ? B[(l0 + l2) + (int64_t)(j0 + jj) * ldb] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) av[x] = As[u][ti + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; y++) bv[y] = Bs[u][tj + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++) acc[x][y] += av[x] * bv[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < 4; y++) {
+    const int j = j0 + tj + 16 * y;
+    if (j >= n) continue;
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      const int i = i0 + ti + 16 * x;
+      if (i < m) Cp[i + (int64_t)j * ldc] = acc[x][y];
+    }
+  }
+}
+
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
-                 int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err) {
+                 int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err, int njmax) {
   if (nbox == 0) return;
   const bool force_general = bmax < 0;  // large-box path requested
   if (force_general) bmax = -bmax;
@@ -2384,7 +2426,13 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_elim<T><<<nbox, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
                                                     use_smem ? 1 : 0, ovf, err);
-  count_launch();
+  // E and G: tiles of 64 x 64 over nj x r (E) and r x nj (G), nj <= njmax, r <= bmax
+  const int tr = (bmax + 63) / 64, tn = (std::max(njmax, 1) + 63) / 64;
+  const int tiles_e = tn * tr;  // E: nj x r
+  const int tiles_g = tr * tn;  // G: r x nj
+  k_elim_gemm<T><<<dim3(nbox, tiles_e + tiles_g), NT, 0, st>>>(boxes, box_list, scratch, scratch_stride, tiles_e,
+                                                              tr, tn);
+  count_launch(2);
 }
 
 // ---------------------------------------------------------------------------
@@ -3274,7 +3322,7 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
                              cudaStream_t,                                                                   \
                              int *);                                                                          \
   template void launch_elim<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, T *, int64_t,            \
-                               const Overflow<T> &, cudaStream_t, int *);                                     \
+                               const Overflow<T> &, cudaStream_t, int *, int);                                \
   template void launch_schur<T>(const LevelDev<T> &, const FBox<T> *, const int *, int, int, const T *, int64_t, \
                                 cudaStream_t);                                                                \
   template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \
