@@ -178,6 +178,27 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per launch of a kernel class, from one ncu
+# capture of the full-size default workload (profiles/id_dram_laplace2d_grid512.md),
+# valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {
+    "id": {"bytes_per_launch": 21.28e6,
+           "kernels_sha256": "334c36865b70af698abb1b5e3418905ed44c31b3f3bdd84d708427e18e106af9"},
+}
+
+
+def ncu_traffic(cls):
+    import hashlib
+    t = NCU_TRAFFIC.get(cls)
+    if t is None:
+        return None
+    src = os.path.join(ROOT, "paper_1609_08130_gb300", "csrc", "kernels.cu")
+    with open(src, "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != t["kernels_sha256"]:
+            return None
+    return t["bytes_per_launch"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +322,7 @@ def main():
                 "iters": it64}
 
     peaks = load_peaks()
+    tuned = [[e["width"], e["phase_class"], e["tpc"], e["groups"]] for e in pkg.autotune_table()]
     # dominant kernel class by time inside the timed region
     gpu_classes = {k: v for k, v in prof_tot.items() if not k.startswith("host_")}
     dom = max(gpu_classes.items(), key=lambda kv: kv[1]["ms"])
@@ -316,6 +338,7 @@ def main():
         pk = alu_peak_tflops(args.prec, peaks["sm_mhz"])
         roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                 "traffic": None}
+    roof["traffic"] = ncu_traffic(cls)
     roof["kernel"] = cls
     roof["peak_source"] = ("of measured (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" and peaks["src"] == "measured"
                            else "derived from unit counts and max SM clock" if roof["bound"] == "alu"
@@ -346,6 +369,8 @@ def main():
             "fp64_gpu": fp64,
             "clocks": clk,
             "gpu_launches": int(launches),
+            "autotune": {"id_shapes": tuned, "fields": ["box width class", "phase-size class",
+                                                        "threads per column", "fold groups"]},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
