@@ -322,7 +322,7 @@ def main():
                 "iters": it64}
 
     peaks = load_peaks()
-    tuned = [[e["width"], e["phase_class"], e["tpc"], e["groups"]] for e in pkg.autotune_table()]
+    tuned = [[e["elem_bytes"], e["width"], e["phase_class"], e["tpc"], e["groups"]] for e in pkg.autotune_table()]
     # dominant kernel class by time inside the timed region
     gpu_classes = {k: v for k, v in prof_tot.items() if not k.startswith("host_")}
     dom = max(gpu_classes.items(), key=lambda kv: kv[1]["ms"])
@@ -369,7 +369,7 @@ def main():
             "fp64_gpu": fp64,
             "clocks": clk,
             "gpu_launches": int(launches),
-            "autotune": {"id_shapes": tuned, "fields": ["box width class", "phase-size class",
+            "autotune": {"id_shapes": tuned, "fields": ["element bytes", "box width class", "phase-size class",
                                                         "threads per column", "fold groups"]},
         }
         print(json.dumps(line), flush=True)
