@@ -322,7 +322,8 @@ def main():
                 "iters": it64}
 
     peaks = load_peaks()
-    tuned = [[e["elem_bytes"], e["width"], e["phase_class"], e["tpc"], e["groups"]] for e in pkg.autotune_table()]
+    tuned = [[e["elem_bytes"], e["width"], e["phase_class"], e["tpc"], e["groups"], e["ctas"]]
+             for e in pkg.autotune_table()]
     # dominant kernel class by time inside the timed region
     gpu_classes = {k: v for k, v in prof_tot.items() if not k.startswith("host_")}
     dom = max(gpu_classes.items(), key=lambda kv: kv[1]["ms"])
@@ -370,7 +371,7 @@ def main():
             "clocks": clk,
             "gpu_launches": int(launches),
             "autotune": {"id_shapes": tuned, "fields": ["element bytes", "box width class", "phase-size class",
-                                                        "threads per column", "fold groups"]},
+                                                        "threads per column", "fold groups", "CTAs per box"]},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

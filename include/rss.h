@@ -276,28 +276,31 @@ rss_status rss_mlp_train(rss_mlp *m, const float *X, const float *y, int64_t n, 
 rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *rank, int64_t nbox);
 
 /* rss_autotune_table -- the autotuner's choices so far in this process, as
- * HOST int32 records of 13: {element bytes (4 FP32 factor, 8 FP64), box-width
- * class (64 or 128), phase-size class (floor(log2(boxes in the phase))),
- * chosen threads per column, chosen fold groups per box, then the measured
- * time in microseconds of the 8 candidate shapes (threads per column, groups)
- * = (1,1) (1,2) (1,4) (2,1) (2,2) (2,4) (4,1) (4,2) (0: not a candidate)}.
+ * HOST int32 records of 18: {element bytes (4 FP32 factor, 8 FP64), box-width
+ * class (64, 128 or 256), phase-size class (floor(log2(boxes in the phase))),
+ * chosen threads per column, fold groups per box and CTAs per box, then the
+ * measured time in microseconds of the 12 candidate shapes (threads per
+ * column, groups, CTAs) = (1,1,1) (1,2,1) (1,4,1) (2,1,1) (2,2,1) (2,4,1)
+ * (4,1,1) (4,2,1) (2,1,4) (2,1,8) (4,1,4) (4,1,8) (0: not a candidate)}.
  * The ID kernel (Sec. 2.2: Householder reduction of the ID matrix to a
- * triangle, then greedy column pivoting) splits a box's rows over fold groups
- * whose triangles are merged, and each column over threads that each keep
- * 32 (FP32) or 16 (FP64) rows of every panel; more threads per box mean
- * fewer sequential steps per box, fewer threads fit more boxes per SM.
- * The first colour phase that meets a key times every candidate on its own
- * boxes (the ID launch is idempotent), keeps the fastest for the rest of the
- * process and re-runs it, so factorizations with the same key compute the
- * same result.  Disabled per factorization by RSS_FLAG_NO_AUTOTUNE.
- * *nbytes in/out as in rss_tree_query. */
+ * triangle, then greedy column pivoting) splits each column over threads
+ * that keep 32 (FP32) or 16 (FP64) rows of every panel, a box's rows over
+ * fold groups of one CTA or over several CTAs, whose triangles are merged by
+ * a tree; more threads per box mean fewer sequential steps per box, fewer
+ * fit more boxes per SM.  Several CTAs per box are tried for phases of at
+ * most 256 boxes.  The first colour phase that meets a key times every
+ * candidate on its own boxes (the ID launch is idempotent), keeps the
+ * fastest for the rest of the process and re-runs it, so factorizations with
+ * the same key compute the same result.  Disabled per factorization by
+ * RSS_FLAG_NO_AUTOTUNE.  *nbytes in/out as in rss_tree_query. */
 rss_status rss_autotune_table(int32_t *buf, size_t *nbytes);
 
 /* rss_autotune_set -- fix the shape used for one key (e.g. a table saved
  * from another run), without timing.  Errors: RSS_EINVAL for a shape that is
  * not a candidate or exceeds the kernel's thread limit (256 threads for one
- * thread per column, 512 otherwise). */
-rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups);
+ * thread per column, 512 otherwise; the 256 width class takes several CTAs
+ * per box only with two threads per column). */
+rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas);
 
 /* rss_autotune_clear -- forget every choice; the next factorizations tune
  * again. */

@@ -919,11 +919,15 @@ static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vect
 // that key computes exactly the same thing.
 // ---------------------------------------------------------------------------
 
-// Candidate launch shapes (threads per column, fold groups per box).
-static const int kTuneShapes[8][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}};
+// Candidate launch shapes (threads per column, fold groups per box, CTAs per box).
+constexpr int kNShapes = 12;
+static const int kTuneShapes[kNShapes][3] = {{1, 1, 1}, {1, 2, 1}, {1, 4, 1}, {2, 1, 1}, {2, 2, 1}, {2, 4, 1},
+                                             {4, 1, 1}, {4, 2, 1}, {2, 1, 4}, {2, 1, 8}, {4, 1, 4}, {4, 1, 8}};
+static bool shape_fits(int width, int tpc, int g) { return width * tpc * g <= (tpc == 1 ? 256 : 512); }
+static int shape_hint(int c) { return (kTuneShapes[c][2] << 8) | (kTuneShapes[c][0] << 4) | kTuneShapes[c][1]; }
 struct TuneEntry {
-  int shape;    // index into kTuneShapes
-  float us[8];  // time of each candidate, microseconds; 0 if not a candidate
+  int shape;            // index into kTuneShapes
+  float us[kNShapes];   // time of each candidate, microseconds; 0 if not a candidate
 };
 static std::mutex g_tune_m;
 static std::map<std::tuple<int, int, int>, TuneEntry> g_tune;
@@ -947,15 +951,16 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
     if (it != g_tune.end()) shape = it->second.shape;
   }
   if (shape < 0) {
-    TuneEntry te{-1, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+    TuneEntry te{-1, {}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.f;
-    for (int ci = 0; ci < 8; ci++) {
-      const int tpc = kTuneShapes[ci][0], g = kTuneShapes[ci][1];
-      if (width * tpc * g > (tpc == 1 ? 256 : 512)) continue;  // the kernels' thread limits
-      set_id_groups(tpc * 16 + g);
+    for (int ci = 0; ci < kNShapes; ci++) {
+      const int tpc = kTuneShapes[ci][0], g = kTuneShapes[ci][1], ctas = kTuneShapes[ci][2];
+      if (!shape_fits(width, tpc, g)) continue;  // the kernels' thread limits
+      if (ctas > 1 && (nbox > 256 || (width == 256 && tpc != 2))) continue;  // several CTAs per box: small phases
+      set_id_groups(shape_hint(ci));
       float ms = 0.f;
       for (int rep = 0; rep < 2; rep++) {  // the second launch is timed
         CK(cudaEventRecord(e0, F.st));
@@ -976,7 +981,7 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
     auto ins = g_tune.insert({key, te});
     shape = ins.first->second.shape;  // another thread may have tuned the key first
   }
-  set_id_groups(kTuneShapes[shape][0] * 16 + kTuneShapes[shape][1]);
+  set_id_groups(shape_hint(shape));
   launch();
   set_id_groups(0);
 }
@@ -1180,7 +1185,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
   };
 
   std::unordered_map<int64_t, int> child_b;  // (problem, node) -> sum of its children's b
-  DBuf gid, gel;                             // per-phase ID and elimination scratch, grown as needed
+  DBuf gid, gel, gtri, gcnt;                 // per-phase ID and elimination scratch, grown as needed
   if (F.mlp) F.d_ovf_used.alloc(sizeof(unsigned long long), st);
   for (int t = F.maxdepth; t >= 2; t--) {
     double th0 = now_ms();
@@ -1440,6 +1445,18 @@ template <typename T> static void run_factor(Factor<T> &F) {
     if (!id_smem) grow(gid, (size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
     int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32 + elim_ws_elems<T>(H.bmax);
     grow(gel, (size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
+    // the multi-CTA ID's triangle slots (8 CTAs per box of a phase of up to
+    // 256 boxes) and tree-node counters
+    IdMultiScratch ims{};
+    if (H.bmax <= 256 && !large) {
+      const int64_t se = H.bmax <= 64 ? 64 * 65 : H.bmax <= 128 ? 128 * 129 : (int64_t)H.bmax * (H.bmax + 1);
+      const int64_t slots = 8 * (int64_t)std::min(std::max(maxphase, 1), 256);
+      grow(gtri, (size_t)(slots * se) * sizeof(T), st, 1);
+      grow(gcnt, sizeof(int) * (size_t)slots * 8, st, 1);
+      CK(cudaMemsetAsync(gcnt.p, 0, sizeof(int) * (size_t)slots * 8, st));
+      ims = IdMultiScratch{gtri.p, se, slots, ptr<int>(gcnt)};
+    }
+    set_id_multi(ims);
     F.prof.host(KC_HOST_LEVEL, now_ms() - th0);
     for (auto &p : ph) {
       const int *bl = ptr<int>(d_list) + p.first;
@@ -1462,6 +1479,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       F.prof.end(pi, st);
       F.phases.push_back({base + p.first, p.second, H.bmax, large ? -njmax_lvl : njmax_lvl, 0, 0});
     }
+    set_id_multi(IdMultiScratch{});
     // ranks of this level -> active DOFs of the next
     CK(cudaMemcpyAsync(F.h_boxes.data() + base, ptr<FBox<T>>(F.d_boxes) + base, sizeof(FBox<T>) * nb,
                        cudaMemcpyDeviceToHost, st));
@@ -2457,9 +2475,8 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
         v.push_back(std::get<0>(kv.first));
         v.push_back(std::get<1>(kv.first));
         v.push_back(std::get<2>(kv.first));
-        v.push_back(kTuneShapes[kv.second.shape][0]);
-        v.push_back(kTuneShapes[kv.second.shape][1]);
-        for (int c = 0; c < 8; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
+        for (int f = 0; f < 3; f++) v.push_back(kTuneShapes[kv.second.shape][f]);
+        for (int c = 0; c < kNShapes; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
       }
     }
     const size_t need = v.size() * sizeof(int32_t), cap = *nbytes;
@@ -2471,17 +2488,17 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
   });
 }
 
-rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups) {
+rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas) {
   return guard([&] {
     int shape = -1;
-    for (int c = 0; c < 8; c++)
-      if (kTuneShapes[c][0] == tpc && kTuneShapes[c][1] == groups) shape = c;
+    for (int c = 0; c < kNShapes; c++)
+      if (kTuneShapes[c][0] == tpc && kTuneShapes[c][1] == groups && kTuneShapes[c][2] == ctas) shape = c;
     if (shape < 0 || (elem_bytes != 4 && elem_bytes != 8) || (width != 64 && width != 128 && width != 256) ||
-        phase_class < 0 ||
-        phase_class > 40 || width * tpc * groups > (tpc == 1 ? 256 : 512))
+        phase_class < 0 || phase_class > 40 || !shape_fits(width, tpc, groups) ||
+        (width == 256 && ctas > 1 && tpc != 2))
       throw Fail{RSS_EINVAL, "rss_autotune_set: bad arguments"};
     std::lock_guard<std::mutex> lk(g_tune_m);
-    TuneEntry te{shape, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+    TuneEntry te{shape, {}};
     g_tune[std::make_tuple(elem_bytes, width, phase_class)] = te;
   });
 }

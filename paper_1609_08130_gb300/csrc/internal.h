@@ -90,9 +90,18 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
                int mmax, const Points &P, const KernelParams &K, const ProxyParams &px,
                const double *proxy_unit, double eps, T *gscratch, int64_t gscratch_stride, bool use_smem,
                cudaStream_t st, int *err);
-// Launch shape of the next ID launch on this thread: threads per column x 16
-// + fold groups per box (0: default).
+// Launch shape of the next ID launch on this thread: CTAs per box << 8 |
+// threads per column << 4 | fold groups per box (0: default).
 void set_id_groups(int G);
+// Scratch of the multi-CTA ID: triangle slots (slot_elems elements each,
+// max_slots of them) and tree-node counters (8 x slots ints, zero between
+// launches).
+struct IdMultiScratch {
+  void *tri = nullptr;
+  int64_t slot_elems = 0, max_slots = 0;
+  int *cnt = nullptr;
+};
+void set_id_multi(const IdMultiScratch &m);
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
                  T *scratch, int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err, int njmax);

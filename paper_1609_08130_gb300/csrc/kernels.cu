@@ -1300,6 +1300,143 @@ __device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, 
   group_bar(bar_id, nthr);
 }
 
+// Greedy column-pivoted QR of the box's triangle R (rows x ld LDR, GT = NC x
+// TPC threads of the calling group, column `col` split over its TPC
+// threads), T = R11^{-1} R12 and the box's ID outputs (Definition 2.1).
+template <typename T, int NC, int TPC> struct IdqShared {
+  T red_v[16];
+  int red_i[16];
+  T hh[4];
+  int stop, piv, k;
+};
+
+template <typename T, int NC, int TPC>
+__device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShared<T, NC, TPC> &sh, FBox<T> &fb,
+                           const LevelDev<T> &lv, int64_t coff, int nO) {
+  constexpr int GT = NC * TPC;
+  const int tid = threadIdx.x, lt = tid % GT, col = lt / TPC, part = lt % TPC;
+  T *s_red_v = sh.red_v;
+  int *s_red_i = sh.red_i;
+  T *s_hh = sh.hh;
+  int &s_stop = sh.stop, &s_piv = sh.piv, &s_k = sh.k;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = GT / 32;
+  if (lt < b) perm[lt] = lt;
+  if (tid == 0) s_k = b;
+  T r11 = (T)0;
+  for (int j = 0; j < b; j++) {
+    T best = (T)-1;
+    int bi = b;
+    {
+      T a0 = (T)0;
+      if (col >= j && col < b)
+        for (int i = j + part; i < b; i += TPC) a0 += R[i * LDR + col] * R[i * LDR + col];
+      a0 = col_sum<T, TPC>(a0);
+      if (col >= j && col < b && part == 0) {
+        best = a0;
+        bi = col;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(FULL, best, o);
+      int oi = __shfl_xor_sync(FULL, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_red_v[wid] = best;
+      s_red_i[wid] = bi;
+    }
+    group_bar(1, GT);
+    if (tid == 0) {
+      for (int u = 1; u < NW; u++)
+        if (s_red_v[u] > best || (s_red_v[u] == best && s_red_i[u] < bi)) {
+          best = s_red_v[u];
+          bi = s_red_i[u];
+        }
+      const T cn = sqrt(best);
+      if (j == 0) r11 = cn;
+      const int stop = (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
+      s_stop = stop;
+      s_piv = bi;
+      if (stop) s_k = j;
+    }
+    group_bar(1, GT);
+    if (s_stop) break;
+    const int p = s_piv;
+    if (p != j) {
+      for (int i = lt; i < b; i += GT) {
+        T t0 = R[i * LDR + j];
+        R[i * LDR + j] = R[i * LDR + p];
+        R[i * LDR + p] = t0;
+      }
+      if (tid == 0) {
+        int tp = perm[j];
+        perm[j] = perm[p];
+        perm[p] = tp;
+      }
+    }
+    group_bar(1, GT);
+    if (col == j) {
+      T a0 = (T)0;
+      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + j];
+      const T sacc = col_sum<T, TPC>(a0);
+      if (part == 0) {
+        const T x0 = R[j * LDR + j];
+        if (sacc > (T)0) {
+          const T nrm = sqrt(x0 * x0 + sacc);
+          const T beta = x0 >= (T)0 ? -nrm : nrm;
+          s_hh[0] = x0;
+          s_hh[1] = beta;
+          s_hh[2] = (beta - x0) / beta;
+          s_hh[3] = (T)1 / (x0 - beta);
+        } else {
+          s_hh[2] = (T)0;
+        }
+      }
+    }
+    group_bar(1, GT);
+    const T tau = s_hh[2];
+    if (tau != (T)0 && col > j && col < b) {
+      const T scl = s_hh[3];
+      T a0 = (T)0;
+      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + col];
+      const T rjc = R[j * LDR + col];
+      const T d = col_sum<T, TPC>(a0);
+      const T f = tau * (rjc + scl * d);
+      const T fs = f * scl;
+      if (part == 0) R[j * LDR + col] = rjc - f;
+      for (int i = j + 1 + part; i < b; i += TPC) R[i * LDR + col] -= fs * R[i * LDR + j];
+    }
+    group_bar(1, GT);
+    if (tau != (T)0 && col == j && part == 0) R[j * LDR + j] = s_hh[1];
+    group_bar(1, GT);
+  }
+  group_bar(1, GT);
+  const int k = s_k;
+  const int r = b - k;
+  for (int cc = lt; cc < r; cc += GT) {
+    T *tcol = fb.Tm + (int64_t)cc * k;
+    for (int i = k - 1; i >= 0; i--) {
+      T sacc = R[i * LDR + k + cc];
+      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
+      tcol[i] = sacc / R[i * LDR + i];
+    }
+  }
+  if (lt < b) {
+    fb.loc[lt] = perm[lt];
+    fb.ids[lt] = lv.cell_dofs[coff + perm[lt]];
+  }
+  if (tid == 0) {
+    fb.k = k;
+    fb.r = r;
+    fb.no = nO;
+  }
+}
+
 template <typename T, int NC, int TPC>
 __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
                                              Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
@@ -1311,10 +1448,7 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
   static_assert(RPT % 2 == 0, "rows per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ocode[125], s_obase[126], s_no;
-  __shared__ T s_red_v[16];
-  __shared__ int s_red_i[16];
-  __shared__ T s_hh[4];
-  __shared__ int s_stop, s_piv, s_k;
+  __shared__ IdqShared<T, NC, TPC> s_sh;
   const int tid = threadIdx.x;
   const int grp = tid / GT, lt = tid % GT;
   const int col = lt / TPC, part = lt % TPC;
@@ -1436,124 +1570,184 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
   }
   __syncthreads();
   if (grp != 0) return;
-  // greedy column-pivoted QR of the triangle; column `col`, rows split over its TPC threads
-  T *R = Rg;
-  const int lane = tid & 31, wid = tid >> 5;
-  constexpr int NW = GT / 32;
-  if (lt < b) perm[lt] = lt;
-  if (tid == 0) s_k = b;
-  T r11 = (T)0;
-  for (int j = 0; j < b; j++) {
-    T best = (T)-1;
-    int bi = b;
-    {
-      T a0 = (T)0;
-      if (col >= j && col < b)
-        for (int i = j + part; i < b; i += TPC) a0 += R[i * LDR + col] * R[i * LDR + col];
-      a0 = col_sum<T, TPC>(a0);
-      if (col >= j && col < b && part == 0) {
-        best = a0;
-        bi = col;
+  idq_finish<T, NC, TPC>(Rg, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
+}
+
+// ---------------------------------------------------------------------------
+// One box's ID over C CTAs (for colour phases with few boxes): CTA `chunk`
+// folds panels chunk, chunk + C, ... of the box's ID matrix into its own
+// triangle (as k_idq with one group), writes it to its slot of `tri`, and
+// the slots are merged pairwise up a binary tree.  At each tree node a
+// counter tells the second CTA of the pair to arrive that it merges: it
+// holds (or loads) the left triangle and folds the right one's rows into it,
+// so the result does not depend on arrival order; the first to arrive exits.
+// The CTA that completes the root runs the pivoted QR and writes the ID.
+// No CTA waits for another.
+// ---------------------------------------------------------------------------
+template <typename T, int NC, int TPC>
+__global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int C, Points P,
+                                             KernelParams K, ProxyParams px, const double *proxy_unit, double eps,
+                                             int ring_max, T *tri, int64_t tstride, int *cnt, int *err) {
+  constexpr int RPT = IdwRows<T>::PR;
+  constexpr int PR = RPT * TPC;
+  constexpr int VS = PR + 4;
+  constexpr int GT = NC * TPC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ocode[125], s_obase[126], s_no, s_second;
+  __shared__ IdqShared<T, NC, TPC> s_sh;
+  const int tid = threadIdx.x, lt = tid;
+  const int col = lt / TPC, part = lt % TPC;
+  const int bq = blockIdx.x / C, chunk = blockIdx.x % C;
+  FBox<T> &fb = boxes[box_list[bq]];
+  const int c = fb.cell, b = fb.b, dim = lv.dim;
+  const int TR = NC > 128 ? b : NC, LDR = TR + 1;
+  T *R = reinterpret_cast<T *>(smem_raw);
+  const size_t tri_bytes = (((size_t)TR * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes);
+  int64_t *s_rowsrc = reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)2 * VS * sizeof(T) + 15) & ~(size_t)15));
+  int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
+
+  for (int e = lt; e < TR * LDR; e += GT) R[e] = (T)0;
+  if (tid < 32) {
+    const int ncode = dim == 3 ? 125 : 25;
+    int no = 0, acc = 0;
+    for (int base = 0; base < ncode; base += 32) {
+      int code = base + tid, cnt_ = 0;
+      if (code < ncode) {
+        int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+        if (max(abs(dx), max(abs(dy), abs(dz))) == 2) {
+          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+          if (nb >= 0) cnt_ = lv.act_cnt[nb];
+        }
       }
-    }
+      unsigned mask = __ballot_sync(FULL, cnt_ > 0);
+      int incl = cnt_;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T ov = __shfl_xor_sync(FULL, best, o);
-      int oi = __shfl_xor_sync(FULL, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, o);
+        if (tid >= o) incl += t;
       }
+      int pos = __popc(mask & ((1u << tid) - 1));
+      if (cnt_ > 0) {
+        s_ocode[no + pos] = code;
+        s_obase[no + pos] = acc + incl - cnt_;
+      }
+      no += __popc(mask);
+      acc += __shfl_sync(FULL, incl, 31);
     }
-    if (lane == 0) {
-      s_red_v[wid] = best;
-      s_red_i[wid] = bi;
-    }
-    group_bar(1, GT);
     if (tid == 0) {
-      for (int u = 1; u < NW; u++)
-        if (s_red_v[u] > best || (s_red_v[u] == best && s_red_i[u] < bi)) {
-          best = s_red_v[u];
-          bi = s_red_i[u];
+      s_obase[no] = acc;
+      s_no = no;
+    }
+  }
+  __syncthreads();
+  const int no = s_no;
+  const int nO = s_obase[no];
+  if (nO > ring_max) {
+    if (tid == 0) set_err(err, DERR_INTERNAL);
+    return;  // every CTA of the box sees the same nO: the box's tree is abandoned whole
+  }
+  for (int q = 0; q < no; q++) {
+    const int code = s_ocode[q];
+    const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+    const int64_t abase = lv.cell_dof_off[nb];
+    const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
+    for (int t = tid; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
+      s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+  }
+  __syncthreads();
+  const int m = nO + px.np;
+  const int64_t coff = lv.cell_dof_off[c];
+  const double D = ldexp(1.0, -lv.t);
+  const double rad = px.radius * D;
+  double xq[3];
+  {
+    const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
+      xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+    }
+  }
+  const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
+  const int npan = (m + PR - 1) / PR;
+  for (int pnl = chunk; pnl < npan; pnl += C) {
+    T pan[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+      const int row = pnl * PR + part * RPT + i;
+      T v = (T)0;
+      if (col < b) {
+        if (row < nO) {
+          v = lv.pool[s_rowsrc[row] + col];
+        } else if (row < m) {
+          const int pm = row - nO;
+          double r2 = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; d++) {
+            const double dd = rad * proxy_unit[3 * pm + d] - xq[d];
+            r2 += dd * dd;
+          }
+          v = w * kof(K.kind, (T)r2);
         }
-      const T cn = sqrt(best);
-      if (j == 0) r11 = cn;
-      const int stop = (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
-      s_stop = stop;
-      s_piv = bi;
-      if (stop) s_k = j;
-    }
-    group_bar(1, GT);
-    if (s_stop) break;
-    const int p = s_piv;
-    if (p != j) {
-      for (int i = lt; i < b; i += GT) {
-        T t0 = R[i * LDR + j];
-        R[i * LDR + j] = R[i * LDR + p];
-        R[i * LDR + p] = t0;
       }
-      if (tid == 0) {
-        int tp = perm[j];
-        perm[j] = perm[p];
-        perm[p] = tp;
+      pan[i] = v;
+    }
+    fold_group_q<T, PR, TPC>(pan, R, LDR, b, col, part, vbuf, 1, GT);
+  }
+  T *slots = tri + (int64_t)bq * C * tstride;
+  int cur = chunk;  // first slot of the subtree this CTA carries
+  for (int L = 1; L < C; L <<= 1) {
+    const int ls = cur & ~(2 * L - 1), rs = ls + L;
+    if (rs >= C) continue;  // no right partner at this level: carry the subtree up
+    // publish this subtree's triangle, then count arrivals at the node
+    T *mine = slots + (int64_t)cur * tstride;
+    for (int e = lt; e < TR * LDR; e += GT) mine[e] = R[e];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      int *node = cnt + ((int64_t)bq * 8 + (31 - __clz(L))) * C + ls;
+      const int seen = atomicAdd(node, 1);
+      s_second = seen == 1;
+      if (seen == 1) *node = 0;  // reset for the next launch
+    }
+    __syncthreads();
+    if (!s_second) return;
+    __threadfence();
+    if (cur != ls) {  // came from the right: the left triangle into shared memory
+      const T *left = slots + (int64_t)ls * tstride;
+      for (int e = lt; e < TR * LDR; e += GT) R[e] = __ldcg(left + e);
+      __syncthreads();
+    }
+    const T *right = slots + (int64_t)rs * tstride;
+    for (int p0 = 0; p0 < b; p0 += PR) {
+      T pan[RPT];
+#pragma unroll
+      for (int i = 0; i < RPT; i++) {
+        const int row = p0 + part * RPT + i;
+        pan[i] = (row < b && col < b) ? __ldcg(right + row * LDR + col) : (T)0;
       }
+      fold_group_q<T, PR, TPC>(pan, R, LDR, b, col, part, vbuf, 1, GT);
     }
-    group_bar(1, GT);
-    if (col == j) {
-      T a0 = (T)0;
-      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + j];
-      const T sacc = col_sum<T, TPC>(a0);
-      if (part == 0) {
-        const T x0 = R[j * LDR + j];
-        if (sacc > (T)0) {
-          const T nrm = sqrt(x0 * x0 + sacc);
-          const T beta = x0 >= (T)0 ? -nrm : nrm;
-          s_hh[0] = x0;
-          s_hh[1] = beta;
-          s_hh[2] = (beta - x0) / beta;
-          s_hh[3] = (T)1 / (x0 - beta);
-        } else {
-          s_hh[2] = (T)0;
-        }
-      }
-    }
-    group_bar(1, GT);
-    const T tau = s_hh[2];
-    if (tau != (T)0 && col > j && col < b) {
-      const T scl = s_hh[3];
-      T a0 = (T)0;
-      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + col];
-      const T rjc = R[j * LDR + col];
-      const T d = col_sum<T, TPC>(a0);
-      const T f = tau * (rjc + scl * d);
-      const T fs = f * scl;
-      if (part == 0) R[j * LDR + col] = rjc - f;
-      for (int i = j + 1 + part; i < b; i += TPC) R[i * LDR + col] -= fs * R[i * LDR + j];
-    }
-    group_bar(1, GT);
-    if (tau != (T)0 && col == j && part == 0) R[j * LDR + j] = s_hh[1];
-    group_bar(1, GT);
+    cur = ls;
   }
-  group_bar(1, GT);
-  const int k = s_k;
-  const int r = b - k;
-  for (int cc = lt; cc < r; cc += GT) {
-    T *tcol = fb.Tm + (int64_t)cc * k;
-    for (int i = k - 1; i >= 0; i--) {
-      T sacc = R[i * LDR + k + cc];
-      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
-      tcol[i] = sacc / R[i * LDR + i];
-    }
-  }
-  if (lt < b) {
-    fb.loc[lt] = perm[lt];
-    fb.ids[lt] = lv.cell_dofs[coff + perm[lt]];
-  }
-  if (tid == 0) {
-    fb.k = k;
-    fb.r = r;
-    fb.no = nO;
-  }
+  __syncthreads();
+  idq_finish<T, NC, TPC>(R, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
+}
+
+template <typename T, int NC, int TPC>
+static void launch_idm(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int C, int bmax,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       double eps, int ring_max, T *tri, int64_t tstride, int *cnt, cudaStream_t st, int *err) {
+  constexpr int PR = IdwRows<T>::PR * TPC;
+  const int TR = NC > 128 ? bmax : NC;
+  const size_t smem = ((((size_t)TR * (TR + 1) * sizeof(T)) + 15) & ~(size_t)15) +
+                      ((((size_t)2 * (PR + 4) * sizeof(T)) + 15) & ~(size_t)15) + (size_t)ring_max * sizeof(int64_t) +
+                      (size_t)NC * sizeof(int) + 16;
+  cudaFuncSetAttribute(k_idm<T, NC, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idm<T, NC, TPC><<<nbox * C, NC * TPC, smem, st>>>(lv, boxes, box_list, C, P, K, px, proxy_unit, eps, ring_max,
+                                                      tri, tstride, cnt, err);
+  count_launch();
 }
 
 // Shared memory of a k_idq launch (see the kernel's layout).
@@ -1622,10 +1816,13 @@ static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
 }
 
 // Launch shape of the next ID launch on this thread: fold groups per box
-// (hint % 16) and threads per column (hint / 16; 0 or 1: k_idc); 0: default.
-// Set by the host's autotuner around a launch_id call.
+// (hint & 15), threads per column ((hint >> 4) & 15; 0 or 1: k_idc) and CTAs
+// per box (hint >> 8; more than 1: k_idm); 0: default.  Set by the host's
+// autotuner around a launch_id call, with the multi-CTA scratch.
 static thread_local int id_groups_hint = 0;
+static thread_local IdMultiScratch id_multi{};
 void set_id_groups(int G) { id_groups_hint = G; }
+void set_id_multi(const IdMultiScratch &m) { id_multi = m; }
 
 template <typename T>
 void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, int mmax,
@@ -1641,7 +1838,19 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     // width, phase size), else the default (enough boxes resident at once to
     // finish a large phase in one wave, more groups per box when small)
     const int NCw = bmax <= 64 ? 64 : 128;
-    int G = id_groups_hint % 16, TPC = id_groups_hint / 16;
+    int G = id_groups_hint & 15, TPC = (id_groups_hint >> 4) & 15, C = id_groups_hint >> 8;
+    const int64_t ts = (int64_t)NCw * (NCw + 1);
+    if (C > 1 && TPC >= 2 && id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots && ts <= id_multi.slot_elems &&
+        NCw * TPC <= 512) {
+      if (NCw == 64) {
+        if (TPC == 4) launch_idm<T, 64, 4>(lv, boxes, box_list, nbox, C, bmax, P, K, px, proxy_unit, eps, ring_max, (T *)id_multi.tri, ts, id_multi.cnt, st, err);
+        else launch_idm<T, 64, 2>(lv, boxes, box_list, nbox, C, bmax, P, K, px, proxy_unit, eps, ring_max, (T *)id_multi.tri, ts, id_multi.cnt, st, err);
+      } else {
+        if (TPC == 4) launch_idm<T, 128, 4>(lv, boxes, box_list, nbox, C, bmax, P, K, px, proxy_unit, eps, ring_max, (T *)id_multi.tri, ts, id_multi.cnt, st, err);
+        else launch_idm<T, 128, 2>(lv, boxes, box_list, nbox, C, bmax, P, K, px, proxy_unit, eps, ring_max, (T *)id_multi.tri, ts, id_multi.cnt, st, err);
+      }
+      return;
+    }
     if (G <= 0) G = NCw == 64 ? (nbox >= 300 ? 2 : 4) : (nbox >= 300 ? 1 : 2);
     if (TPC <= 0) TPC = 1;
     if (NCw == 64) {
@@ -1657,7 +1866,17 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   }
   if (bmax <= 256 && !force_general) {
     // one group per box, the triangle sized by the level's widest box
-    const int TPC = id_groups_hint / 16 == 1 ? 1 : 2;
+    const int TPC = ((id_groups_hint >> 4) & 15) == 1 ? 1 : 2, C = id_groups_hint >> 8;
+    if (C > 1 && TPC == 2 && id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots &&
+        (int64_t)bmax * (bmax + 1) <= id_multi.slot_elems) {
+      const size_t smw = (((size_t)bmax * (bmax + 1) * sizeof(T) + 15) & ~(size_t)15) + 2 * (64 + 4) * sizeof(T) + 16 +
+                         (size_t)mmax * sizeof(int64_t) + 256 * sizeof(int) + 16;
+      if (smw <= (size_t)(220 << 10)) {
+        launch_idm<T, 256, 2>(lv, boxes, box_list, nbox, C, bmax, P, K, px, proxy_unit, eps, mmax, (T *)id_multi.tri,
+                              (int64_t)bmax * (bmax + 1), id_multi.cnt, st, err);
+        return;
+      }
+    }
     const size_t sm = TPC == 1 ? idq_smem<T, 256, 1>(bmax, 1, mmax) : idq_smem<T, 256, 2>(bmax, 1, mmax);
     if (sm <= (size_t)(220 << 10)) {
       if (TPC == 1) launch_idq<T, 256, 1>(lv, boxes, box_list, nbox, 1, bmax, P, K, px, proxy_unit, eps, mmax, st, err);
@@ -2405,7 +2624,10 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   if (nbox == 0) return;
   const bool force_general = bmax < 0;  // large-box path requested
   if (force_general) bmax = -bmax;
-  if (!force_general) {
+  // Phases of fewer than 300 boxes (upper levels) take the general kernel,
+  // whose E and G products are spread over the whole GPU; large phases the
+  // one-CTA-per-box shared-memory kernel (measured on the 512^2 grid).
+  if (!force_general && nbox >= 300) {
     // worst case over k + r = b of the shared-memory form
     size_t worst = 0;
     for (int r = 0; r <= bmax; r++) worst = std::max(worst, elim2_smem<T>(bmax, bmax - r, r));

@@ -337,9 +337,10 @@ def test_autotuner_choices_are_reproducible(pkg):
     tab = pkg.autotune_table()
     assert tab, "no autotuner entries after a factorization"
     for e in tab:
-        assert (e["tpc"], e["groups"]) in pkg.rss.AUTOTUNE_SHAPES
+        shape = (e["tpc"], e["groups"], e["ctas"])
+        assert shape in pkg.rss.AUTOTUNE_SHAPES
         assert e["width"] in (64, 128, 256) and e["elem_bytes"] in (4, 8)
-        chosen = pkg.rss.AUTOTUNE_SHAPES.index((e["tpc"], e["groups"]))
+        chosen = pkg.rss.AUTOTUNE_SHAPES.index(shape)
         tried = [u for u in e["us"] if u > 0]
         assert e["us"][chosen] > 0 and e["us"][chosen] == min(tried)
     f2 = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=pkg.MIXED)
@@ -384,27 +385,29 @@ def test_every_id_launch_shape_matches_oracle(pkg, prec):
     yo, zo = of.apply(x), of.solve(x)
     elem = 8 if prec == "fp64" else 4
     try:
-        for tpc, g in pkg.rss.AUTOTUNE_SHAPES:
+        for tpc, g, ctas in pkg.rss.AUTOTUNE_SHAPES:
             lib.rss_autotune_clear()
             for width in (64, 128):
                 if width * tpc * g > (256 if tpc == 1 else 512):
                     continue
                 for cls in range(0, 20):
-                    assert lib.rss_autotune_set(elem, width, cls, tpc, g) == 0
+                    assert lib.rss_autotune_set(elem, width, cls, tpc, g, ctas) == 0
             f = pkg.Factorization(_cuda(pts), 0, eps, leaf=64, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
             y = f.apply(_cuda(x)).cpu().numpy()
             z = f.solve(_cuda(x)).cpu().numpy()
-            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, (tpc, g)
-            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, g)
+            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, (tpc, g, ctas)
+            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, g, ctas)
     finally:
         lib.rss_autotune_clear()
-    assert lib.rss_autotune_set(4, 64, 3, 4, 4) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
+    assert lib.rss_autotune_set(4, 64, 3, 4, 4, 1) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
+    assert lib.rss_autotune_set(4, 64, 3, 2, 1, 3) == pkg.rss.RSS_EINVAL  # 3 CTAs per box: not a shape
 
 
 def test_wide_box_id_matches_oracle(pkg):
     """Boxes wider than 128 (an octree's upper level at eps 1e-3) take the ID
     kernel whose triangle is sized by the box; the factor matches the oracle
-    within 10 eps (mixed precision, both launch shapes)."""
+    within 10 eps (mixed precision, one CTA per box with one or two threads
+    per column, and several CTAs per box)."""
     lib = pkg.lib()
     pts = inputs.random_points(5, 10000, 3)  # 16 boxes of 129..140 DOFs at depth 2
     eps = 1e-3
@@ -412,16 +415,16 @@ def test_wide_box_id_matches_oracle(pkg):
     x = inputs.normal(95, len(pts))
     yo, zo = of.apply(x), of.solve(x)
     try:
-        for tpc in (1, 2):
+        for tpc, ctas in ((1, 1), (2, 1), (2, 4), (2, 8)):
             lib.rss_autotune_clear()
             for cls in range(0, 20):
-                assert lib.rss_autotune_set(4, 256, cls, tpc, 1) == 0
+                assert lib.rss_autotune_set(4, 256, cls, tpc, 1, ctas) == 0
             f = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.MIXED)
             st = f.stats()
             assert st["b"].max() > 128, st["b"].max()
             y = f.apply(_cuda(x)).cpu().numpy()
             z = f.solve(_cuda(x)).cpu().numpy()
-            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, tpc
-            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, tpc
+            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, (tpc, ctas)
+            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, ctas)
     finally:
         lib.rss_autotune_clear()
