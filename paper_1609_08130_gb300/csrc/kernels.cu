@@ -2211,7 +2211,7 @@ __host__ __device__ inline size_t elim2_smem(int b, int k, int r) {
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
-                                              int64_t sstride, Overflow<T> ovf, int *err) {
+                                              int64_t sstride, Overflow<T> ovf, int *err, int split, int C) {
   constexpr int CH = ElimChunk<T>::CH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nact[27], s_nn, s_ok;
@@ -2219,7 +2219,10 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   __shared__ int s_ld_in[27];
   __shared__ int64_t s_rb[ElimChunk<T>::CH], s_cb[ElimChunk<T>::CH];
   __shared__ int s_rl[ElimChunk<T>::CH];
-  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  // C CTAs per box (split mode only): CTA 0 also does the LU, X_RR^{-1} and
+  // the box's records; every CTA forms its share of the chunks of J
+  const int q = blockIdx.x / C, cta = blockIdx.x % C;
+  FBox<T> &fb = boxes[box_list[q]];
   const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncode3 = dim == 3 ? 27 : 9;
@@ -2262,7 +2265,7 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     }
     s_nstart[nn] = acc;
     s_nn = nn;
-    s_ok = acc <= fb.njmax ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
+    s_ok = (acc <= fb.njmax && cta == 0) ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
   }
   for (int q = tid; q < b; q += NT) sloc[q] = fb.loc[q];
   for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
@@ -2289,11 +2292,13 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       loc = lv.act_idx[s_nact[q] + (a - s_nstart[q])];
       g = lv.cell_dofs[s_nact[q] + loc];
     }
-    fb.J[a] = g;
-    fb.Jnb[a] = code;
-    fb.Jloc[a] = loc;
+    if (cta == 0) {
+      fb.J[a] = g;
+      fb.Jnb[a] = code;
+      fb.Jloc[a] = loc;
+    }
   }
-  if (tid == 0) fb.nj = nj;
+  if (tid == 0 && cta == 0) fb.nj = nj;
   // stage A_BB in (S|R) order
   const T *Aii = lv.pool + s_off_in[center];
   for (int e = tid; e < b * b; e += NT) {
@@ -2330,6 +2335,7 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     smem_gemm<T>(r, r, k, XRS, 1, r, Ts, 1, k, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
   }
   __syncthreads();
+  if (cta == 0) {
   // LU with partial pivoting by warp 0 (largest |entry|, ties to the lowest row)
   if (warp == 0) {
     for (int i = lane; i < r; i += 32) spiv[i] = i;
@@ -2442,15 +2448,26 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += NT) fb.Xi[e] = Xi[(e % r) + (size_t)(e / r) * ldx];
-  T *Xrj_out = scratch + (int64_t)blockIdx.x * sstride + (int64_t)nj * r;  // r x nj, for the Schur update
-  for (int a0 = 0; a0 < nj; a0 += CH) {
+  }  // cta == 0
+  T *Xrj_out = scratch + (int64_t)q * sstride + (int64_t)nj * r;  // r x nj, for the Schur update
+  for (int a0 = cta * CH; a0 < nj; a0 += C * CH) {
     const int na = min(CH, nj - a0);
     // raw rows A(J_a, B) and columns A(B, J_a) of the chunk (S rows come from
     // X_SR / X_RS); the row / column bases of the chunk are resolved first so
     // the element loads below are independent of one another
     if (tid < na) {
+      // (code, local index) of J entry a, as in the J lists above
       const int a = a0 + tid;
-      const int code = fb.Jnb[a], la = fb.Jloc[a];
+      int code, la;
+      if (a < k) {
+        code = center;
+        la = sloc[a];
+      } else {
+        int q2 = 0;
+        while (s_nstart[q2 + 1] <= a) q2++;
+        code = s_ncode[q2];
+        la = lv.act_idx[s_nact[q2] + (a - s_nstart[q2])];
+      }
       s_rb[tid] = s_off_in[code] + la;
       s_rl[tid] = s_ld_in[code];
       s_cb[tid] = s_off_out[code] + (int64_t)la * b;
@@ -2511,6 +2528,16 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       int ri = e % r, al = e / r;
       Xrj_out[ri + (int64_t)(a0 + al) * r] = rawC[(k + ri) + al * ldb];
     }
+    if (split) {
+      // X_JR chunk to the scratch (nj x r, ld nj); E and G follow in k_elim_gemm
+      T *Xjr = scratch + (int64_t)q * sstride;
+      for (int e = tid; e < na * r; e += NT) {
+        const int al = e % na, ri = e / na;
+        Xjr[(a0 + al) + (int64_t)ri * nj] = rawJ[al + (k + ri) * (CH + 1)];
+      }
+      __syncthreads();
+      continue;
+    }
     // E chunk = X_JR chunk * X_RR^{-1};  G chunk = X_RR^{-1} * X_RJ chunk
     {
       T *Eo = fb.E, *Go = fb.G;
@@ -2525,6 +2552,7 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     __syncthreads();
   }
   // the box's active DOFs are now its skeleton, kept in ascending order
+  if (cta != 0) return;
   const int64_t coff = lv.cell_dof_off[c];
   for (int s1 = tid; s1 < k; s1 += NT) {
     int v = sloc[s1], rank = 0;
@@ -2624,18 +2652,27 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   if (nbox == 0) return;
   const bool force_general = bmax < 0;  // large-box path requested
   if (force_general) bmax = -bmax;
-  // Phases of fewer than 300 boxes (upper levels) take the general kernel,
-  // whose E and G products are spread over the whole GPU; large phases the
-  // one-CTA-per-box shared-memory kernel (measured on the 512^2 grid).
-  if (!force_general && nbox >= 300) {
+  // Phases of fewer than 300 boxes (upper levels) leave X_JR and X_RJ in the
+  // scratch and form E and G in k_elim_gemm, spread over the whole GPU;
+  // large phases form them in the one-CTA-per-box kernel (measured on the
+  // 512^2 grid).
+  const int split = nbox < 300 ? 1 : 0;
+  const int C = split ? std::min(8, std::max(1, (300 + nbox - 1) / nbox)) : 1;  // CTAs per box
+  const int tr = (bmax + 63) / 64, tn = (std::max(njmax, 1) + 63) / 64;
+  if (!force_general) {
     // worst case over k + r = b of the shared-memory form
     size_t worst = 0;
     for (int r = 0; r <= bmax; r++) worst = std::max(worst, elim2_smem<T>(bmax, bmax - r, r));
     // the warp LU keeps at most four pivot-row entries per lane: r <= 128
     if (worst <= (size_t)(220 << 10) && bmax <= 128) {
       cudaFuncSetAttribute(k_elim2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)worst);
-      k_elim2<T><<<nbox, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, ovf, err);
+      k_elim2<T><<<nbox * C, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, ovf, err, split, C);
       count_launch();
+      if (split) {
+        k_elim_gemm<T><<<dim3(nbox, 2 * tn * tr), NT, 0, st>>>(boxes, box_list, scratch, scratch_stride, tn * tr, tr,
+                                                                 tn);
+        count_launch();
+      }
       return;
     }
   }
@@ -2649,7 +2686,6 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   k_elim<T><<<nbox, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
                                                     use_smem ? 1 : 0, ovf, err);
   // E and G: tiles of 64 x 64 over nj x r (E) and r x nj (G), nj <= njmax, r <= bmax
-  const int tr = (bmax + 63) / 64, tn = (std::max(njmax, 1) + 63) / 64;
   const int tiles_e = tn * tr;  // E: nj x r
   const int tiles_g = tr * tn;  // G: r x nj
   k_elim_gemm<T><<<dim3(nbox, tiles_e + tiles_g), NT, 0, st>>>(boxes, box_list, scratch, scratch_stride, tiles_e,
