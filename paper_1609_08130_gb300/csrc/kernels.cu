@@ -2708,6 +2708,11 @@ __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> lv, const FBox<T> *box
   __shared__ T Es[SK][ST + 1];
   __shared__ T Gs[SK][ST + 1];
   __shared__ int s_cell3[27];
+  // scatter tables of the tile: 3^d code and local index of its rows and
+  // columns of J, the pool offset of the pair block (row cell, column cell)
+  // for every pair of codes, and the leading dimension of each row cell
+  __shared__ int s_rc[ST], s_rl[ST], s_cc[ST], s_cl[ST], s_ld[27];
+  __shared__ int64_t s_po[27 * 27];
   const int bi = blockIdx.x / (tiles1 * tiles1);
   const int tt = blockIdx.x % (tiles1 * tiles1);
   const FBox<T> &fb = boxes[box_list[bi]];
@@ -2716,10 +2721,29 @@ __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> lv, const FBox<T> *box
   if (a0 >= nj || c0 >= nj || r == 0) return;
   const T *Xrj = scratch + (int64_t)bi * sstride + (int64_t)nj * r;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  if (tid < (dim == 3 ? 27 : 9)) {
+  const int nc3 = dim == 3 ? 27 : 9;
+  if (tid < nc3) {
     int dx, dy, dz;
     decode3(tid, dim, dx, dy, dz);
-    s_cell3[tid] = lv.cell_nbr[(int64_t)fb.cell * lv.NB + code5(dx, dy, dz, dim)];
+    const int cl = lv.cell_nbr[(int64_t)fb.cell * lv.NB + code5(dx, dy, dz, dim)];
+    s_cell3[tid] = cl;
+    s_ld[tid] = cl >= 0 ? lv.cell_b[cl] : 0;
+  }
+  if (tid < ST) {
+    const int a = a0 + tid, cc = c0 + tid;
+    s_rc[tid] = a < nj ? fb.Jnb[a] : 0;
+    s_rl[tid] = a < nj ? fb.Jloc[a] : 0;
+    s_cc[tid] = cc < nj ? fb.Jnb[cc] : 0;
+    s_cl[tid] = cc < nj ? fb.Jloc[cc] : 0;
+  }
+  __syncthreads();
+  for (int e = tid; e < nc3 * nc3; e += NT) {
+    const int ra = e / nc3, rc = e % nc3;
+    const int ca = s_cell3[ra];
+    int adx, ady, adz, cdx, cdy, cdz;
+    decode3(ra, dim, adx, ady, adz);
+    decode3(rc, dim, cdx, cdy, cdz);
+    s_po[e] = ca >= 0 ? lv.pair_off[(int64_t)ca * lv.NB + code5(cdx - adx, cdy - ady, cdz - adz, dim)] : -1;
   }
   T acc[4][4];
 #pragma unroll
@@ -2752,21 +2776,16 @@ __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> lv, const FBox<T> *box
   }
 #pragma unroll
   for (int y = 0; y < 4; y++) {
-    int cc = c0 + ty + 16 * y;
-    if (cc >= nj) continue;
-    int codec = fb.Jnb[cc], lc = fb.Jloc[cc];
-    int cdx, cdy, cdz;
-    decode3(codec, dim, cdx, cdy, cdz);
+    const int jc = ty + 16 * y;
+    if (c0 + jc >= nj) continue;
+    const int codec = s_cc[jc], lc = s_cl[jc];
 #pragma unroll
     for (int x = 0; x < 4; x++) {
-      int a = a0 + tx + 16 * x;
-      if (a >= nj) continue;
-      int codea = fb.Jnb[a], la = fb.Jloc[a];
-      int adx, ady, adz;
-      decode3(codea, dim, adx, ady, adz);
-      int ca = s_cell3[codea];
-      int64_t off = lv.pair_off[(int64_t)ca * lv.NB + code5(cdx - adx, cdy - ady, cdz - adz, dim)];
-      lv.pool[off + la + (int64_t)lc * lv.cell_b[ca]] -= acc[x][y];
+      const int ia = tx + 16 * x;
+      if (a0 + ia >= nj) continue;
+      const int codea = s_rc[ia];
+      const int64_t off = s_po[codea * nc3 + codec];
+      lv.pool[off + s_rl[ia] + (int64_t)lc * s_ld[codea]] -= acc[x][y];
     }
   }
 }
