@@ -152,9 +152,16 @@ static void staged_h2d(void *dst, const void *src, size_t bytes, cudaStream_t st
   S.off += need;
 }
 
+// Small arrays go through the staging ring; large ones are copied from the
+// pageable vector directly (the copy has left the vector when the call
+// returns, and on this platform it runs near memory speed, faster than a
+// host copy into the ring first).
 template <typename U> static void upload(DBuf &d, const std::vector<U> &h, cudaStream_t st) {
-  d.alloc(h.size() * sizeof(U), st);
-  if (!h.empty()) staged_h2d(d.p, h.data(), h.size() * sizeof(U), st);
+  const size_t nb = h.size() * sizeof(U);
+  d.alloc(nb, st);
+  if (nb == 0) return;
+  if (nb <= ((size_t)256 << 10)) staged_h2d(d.p, h.data(), nb, st);
+  else CK(cudaMemcpyAsync(d.p, h.data(), nb, cudaMemcpyHostToDevice, st));
 }
 
 // ---------------------------------------------------------------------------
@@ -173,7 +180,7 @@ class HostPool {
   int size() const { return (int)th_.size() + 1; }
   void parallel_for(int64_t n, const std::function<void(int64_t)> &f) {
     if (n <= 0) return;
-    if (n == 1 || th_.empty()) {
+    if (n == 1 || th_.empty() || in_job()) {  // nested calls run inline
       for (int64_t i = 0; i < n; i++) f(i);
       return;
     }
@@ -204,7 +211,12 @@ class HostPool {
       th_.back().detach();
     }
   }
+  static bool &in_job() {
+    static thread_local bool f = false;
+    return f;
+  }
   void run() {
+    in_job() = true;
     for (;;) {
       const int64_t i = next_.fetch_add(1);
       if (i >= njob_) break;
@@ -215,6 +227,7 @@ class HostPool {
         if (!err_) err_ = std::current_exception();
       }
     }
+    in_job() = false;
   }
   void worker() {
     uint64_t seen = 0;
@@ -410,53 +423,106 @@ static void build_tree(HTree &T, const double *pts_host) {
   for (int64_t i = 0; i < n; i++) T.perm[i] = i;
   radix_sort_by_key(ks, T.perm, dim * D0);  // stable: equal keys keep index order
   for (int64_t p = 0; p < n; p++) ks[p] = kf[T.perm[p]];
-  T.maxdepth = 0;
   struct Frame {
     int64_t lo, hi;
     int depth, parent;
     int c[3];
   };
-  std::vector<Frame> stack, ch;
-  std::vector<std::pair<uint64_t, int64_t>> tmp;
+  struct NodeVec {
+    std::vector<int> depth, parent, coord, task;
+    std::vector<int64_t> start, count;
+    int maxdepth = 0;
+  };
+  // children of a node that splits, in child order (its range re-sorted on
+  // the full key first at depth D0)
+  auto split = [&](const Frame &f, int pid, std::vector<std::pair<uint64_t, int64_t>> &tmp, std::vector<Frame> &ch) {
+    if (f.depth == D0) {
+      // order below D0 on the full key (ties by original index)
+      tmp.resize(f.hi - f.lo);
+      for (int64_t p = f.lo; p < f.hi; p++) tmp[p - f.lo] = {ks[p], T.perm[p]};
+      std::sort(tmp.begin(), tmp.end());
+      for (int64_t p = f.lo; p < f.hi; p++) ks[p] = tmp[p - f.lo].first, T.perm[p] = tmp[p - f.lo].second;
+    }
+    // split [lo,hi) by the dim bits of depth f.depth+1 (the keys of the range
+    // are sorted on those bits: binary search each boundary)
+    const int shift = dim * (MAXD - f.depth - 1);
+    const uint64_t mask = (1u << dim) - 1;
+    ch.clear();
+    int64_t p = f.lo;
+    while (p < f.hi) {
+      const uint64_t grp = (ks[p] >> shift) & mask;
+      const int64_t q = std::upper_bound(ks.begin() + p, ks.begin() + f.hi, grp,
+                                         [&](uint64_t g, uint64_t k) { return g < ((k >> shift) & mask); }) -
+                        ks.begin();
+      Frame cf{p, q, f.depth + 1, pid, {0, 0, 0}};
+      for (int d = 0; d < dim; d++) cf.c[d] = 2 * f.c[d] + (int)((grp >> d) & 1);
+      ch.push_back(cf);
+      p = q;
+    }
+  };
+  // pre-order build from `stack` into V; with `deferred`, a node of depth
+  // stop_depth that splits is recorded but its subtree is deferred (V.task)
+  auto grow = [&](NodeVec &V, std::vector<Frame> &stack, int stop_depth, std::vector<Frame> *deferred) {
+    std::vector<Frame> ch;
+    std::vector<std::pair<uint64_t, int64_t>> tmp;
+    while (!stack.empty()) {
+      Frame f = stack.back();
+      stack.pop_back();
+      const int id = (int)V.depth.size();
+      V.depth.push_back(f.depth);
+      V.parent.push_back(f.parent);
+      for (int d = 0; d < 3; d++) V.coord.push_back(f.c[d]);
+      V.start.push_back(f.lo);
+      V.count.push_back(f.hi - f.lo);
+      V.task.push_back(-1);
+      V.maxdepth = std::max(V.maxdepth, f.depth);
+      if (f.hi - f.lo > T.leaf && f.depth < MAXD) {
+        if (deferred && f.depth == stop_depth) {
+          V.task.back() = (int)deferred->size();
+          deferred->push_back(f);
+          continue;
+        }
+        split(f, id, tmp, ch);
+        for (int i = (int)ch.size() - 1; i >= 0; i--) stack.push_back(ch[i]);  // pre-order
+      } else {
+        // a leaf keeps its points in original order
+        std::sort(T.perm.begin() + f.lo, T.perm.begin() + f.hi);
+      }
+    }
+  };
+  // the top of the tree sequentially; for large inputs the subtrees below
+  // depth DP on the host pool, then spliced in pre-order
+  const int DP = n >= ((int64_t)1 << 17) ? (dim == 2 ? 3 : 2) : -1;
+  NodeVec top;
+  std::vector<Frame> deferred, stack;
   stack.push_back({0, n, 0, -1, {0, 0, 0}});
-  while (!stack.empty()) {
-    Frame f = stack.back();
-    stack.pop_back();
-    int id = (int)T.depth.size();
-    T.depth.push_back(f.depth);
-    T.parent.push_back(f.parent);
-    for (int d = 0; d < 3; d++) T.coord.push_back(f.c[d]);
-    T.start.push_back(f.lo);
-    T.count.push_back(f.hi - f.lo);
-    T.maxdepth = std::max(T.maxdepth, f.depth);
-    if (f.hi - f.lo > T.leaf && f.depth < MAXD) {
-      if (f.depth == D0) {
-        // order below D0 on the full key (ties by original index)
-        tmp.resize(f.hi - f.lo);
-        for (int64_t p = f.lo; p < f.hi; p++) tmp[p - f.lo] = {ks[p], T.perm[p]};
-        std::sort(tmp.begin(), tmp.end());
-        for (int64_t p = f.lo; p < f.hi; p++) ks[p] = tmp[p - f.lo].first, T.perm[p] = tmp[p - f.lo].second;
-      }
-      // children: split [lo,hi) by the dim bits of depth f.depth+1 (the keys
-      // of the range are sorted on those bits: binary search each boundary)
-      const int shift = dim * (MAXD - f.depth - 1);
-      const uint64_t mask = (1u << dim) - 1;
-      ch.clear();
-      int64_t p = f.lo;
-      while (p < f.hi) {
-        const uint64_t grp = (ks[p] >> shift) & mask;
-        const int64_t q = std::upper_bound(ks.begin() + p, ks.begin() + f.hi, grp,
-                                           [&](uint64_t g, uint64_t k) { return g < ((k >> shift) & mask); }) -
-                          ks.begin();
-        Frame cf{p, q, f.depth + 1, id, {0, 0, 0}};
-        for (int d = 0; d < dim; d++) cf.c[d] = 2 * f.c[d] + (int)((grp >> d) & 1);
-        ch.push_back(cf);
-        p = q;
-      }
-      for (int i = (int)ch.size() - 1; i >= 0; i--) stack.push_back(ch[i]);  // pre-order
-    } else {
-      // a leaf keeps its points in original order
-      std::sort(T.perm.begin() + f.lo, T.perm.begin() + f.hi);
+  grow(top, stack, DP, DP >= 0 ? &deferred : nullptr);
+  std::vector<NodeVec> sub(deferred.size());
+  HostPool::get().parallel_for((int64_t)deferred.size(), [&](int64_t t) {
+    std::vector<Frame> st2, ch;
+    std::vector<std::pair<uint64_t, int64_t>> tmp;
+    split(deferred[t], -1, tmp, ch);  // -1: child of the deferred node
+    for (int i = (int)ch.size() - 1; i >= 0; i--) st2.push_back(ch[i]);
+    grow(sub[t], st2, -1, nullptr);
+  });
+  std::vector<int> top2g(top.depth.size());
+  T.maxdepth = top.maxdepth;
+  auto append = [&](const NodeVec &V, int j, int parent) {
+    T.depth.push_back(V.depth[j]);
+    T.parent.push_back(parent);
+    for (int d = 0; d < 3; d++) T.coord.push_back(V.coord[3 * j + d]);
+    T.start.push_back(V.start[j]);
+    T.count.push_back(V.count[j]);
+  };
+  for (size_t i = 0; i < top.depth.size(); i++) {
+    const int gid = (int)T.depth.size();
+    top2g[i] = gid;
+    append(top, (int)i, top.parent[i] < 0 ? -1 : top2g[top.parent[i]]);
+    if (top.task[i] >= 0) {
+      const NodeVec &V = sub[top.task[i]];
+      const int base = (int)T.depth.size();
+      for (size_t j = 0; j < V.depth.size(); j++) append(V, (int)j, V.parent[j] < 0 ? gid : base + V.parent[j]);
+      T.maxdepth = std::max(T.maxdepth, V.maxdepth);
     }
   }
   T.x.resize((size_t)n * dim);
@@ -548,32 +614,64 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   // = floor(v 2^t) (clamping included), and the Morton key drops dim bits per level
   const int ksh = dim * (20 - t), csh = 20 - t;
   std::vector<uint64_t> dk(na);
-  bool sorted = true;
-  for (size_t q = 0; q < na; q++) {
-    dk[q] = T.key[active[q]] >> ksh;
-    if (q && dk[q] < dk[q - 1]) sorted = false;
-  }
-  std::vector<int> cid(na);
-  if (sorted) {
+  std::atomic<bool> unsorted{false};
+  parallel_range((int64_t)na, (int64_t)1 << 15, [&](int64_t lo, int64_t hi) {
+    for (int64_t q = lo; q < hi; q++) dk[q] = T.key[active[q]] >> ksh;
+    for (int64_t q = std::max<int64_t>(lo, 1); q < hi; q++)
+      if (dk[q] < dk[q - 1]) unsorted = true;
+  });
+  for (int64_t q0 = 1; q0 < (int64_t)na; q0++)  // chunk boundaries and anything missed
+    if (dk[q0] < dk[q0 - 1]) {
+      unsorted = true;
+      break;
+    }
+  const bool sorted = !unsorted;
+  std::vector<int> cid;
+  if (sorted && na >= ((size_t)1 << 16)) {
+    // cells are runs of the (tree-ordered) active list: cell c holds
+    // active[start_c .. start_{c+1}) in order
+    std::vector<int64_t> starts;
+    starts.reserve(na / 8 + 1);
+    for (size_t q = 0; q < na; q++)
+      if (q == 0 || dk[q] != dk[q - 1]) starts.push_back((int64_t)q);
+    L.ncell = (int)starts.size();
+    L.key.resize(L.ncell);
+    L.cell_b.resize(L.ncell);
+    L.cell_dof_off.resize(L.ncell + 1);
+    L.cell_coord.assign(3 * (size_t)L.ncell, 0);
+    L.cell_dofs.assign(active.begin(), active.end());
+    L.cell_dof_off[L.ncell] = (int64_t)na;
+    parallel_range(L.ncell, 4096, [&](int64_t c0, int64_t c1) {
+      for (int64_t c = c0; c < c1; c++) {
+        const int64_t q = starts[c], e = c + 1 < L.ncell ? starts[c + 1] : (int64_t)na;
+        L.key[c] = dk[q];
+        L.cell_b[c] = (int)(e - q);
+        L.cell_dof_off[c] = q;
+        for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = T.c20[active[q] * dim + d] >> csh;
+      }
+    });
+  } else if (sorted) {
+    cid.resize(na);
     // cells are runs of the (tree-ordered) active list: no sort needed
     for (size_t q = 0; q < na; q++) {
       if (q == 0 || dk[q] != dk[q - 1]) L.key.push_back(dk[q]);
       cid[q] = (int)L.key.size() - 1;
     }
   } else {
+    cid.resize(na);
     L.key = dk;
     std::sort(L.key.begin(), L.key.end());
     L.key.erase(std::unique(L.key.begin(), L.key.end()), L.key.end());
     for (size_t q = 0; q < na; q++) cid[q] = find_key(L.key, dk[q]);
   }
-  L.ncell = (int)L.key.size();
-  L.cell_b.assign(L.ncell, 0);
-  for (size_t q = 0; q < na; q++) L.cell_b[cid[q]]++;
-  L.cell_dof_off.assign(L.ncell + 1, 0);
-  for (int c = 0; c < L.ncell; c++) L.cell_dof_off[c + 1] = L.cell_dof_off[c] + L.cell_b[c];
-  L.cell_dofs.resize(na);
-  L.cell_coord.assign(3 * L.ncell, 0);
-  {
+  if (!cid.empty()) {
+    L.ncell = (int)L.key.size();
+    L.cell_b.assign(L.ncell, 0);
+    for (size_t q = 0; q < na; q++) L.cell_b[cid[q]]++;
+    L.cell_dof_off.assign(L.ncell + 1, 0);
+    for (int c = 0; c < L.ncell; c++) L.cell_dof_off[c + 1] = L.cell_dof_off[c] + L.cell_b[c];
+    L.cell_dofs.resize(na);
+    L.cell_coord.assign(3 * L.ncell, 0);
     std::vector<int64_t> fill(L.cell_dof_off.begin(), L.cell_dof_off.end() - 1);
     for (size_t q = 0; q < na; q++) {
       int c = cid[q];
@@ -581,6 +679,9 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
         for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = T.c20[active[q] * dim + d] >> csh;
       L.cell_dofs[fill[c]++] = active[q];
     }
+  } else if (na == 0) {
+    L.ncell = 0;
+    L.cell_dof_off.assign(1, 0);
   }
   L.cell_nbr.assign((size_t)L.ncell * L.NB, -1);
   L.pair_off.assign((size_t)L.ncell * L.NB, -1);
@@ -591,11 +692,13 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   std::vector<int> dense;
   if (grid_cells <= ((int64_t)1 << 24)) {
     dense.assign(grid_cells, -1);
-    for (int c = 0; c < L.ncell; c++) {
-      int64_t lin = 0, mul = 1;
-      for (int d = 0; d < dim; d++) lin += (int64_t)L.cell_coord[3 * c + d] * mul, mul *= side;
-      dense[lin] = c;
-    }
+    parallel_range(L.ncell, 8192, [&](int64_t c0, int64_t c1) {
+      for (int64_t c = c0; c < c1; c++) {
+        int64_t lin = 0, mul = 1;
+        for (int d = 0; d < dim; d++) lin += (int64_t)L.cell_coord[3 * c + d] * mul, mul *= side;
+        dense[lin] = (int)c;  // distinct cells, distinct entries
+      }
+    });
   }
   auto lookup = [&](const int64_t *p) -> int {
     if (!dense.empty()) {
@@ -605,26 +708,44 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
     }
     return find_key(L.key, morton_fast(p, dim));
   };
-  int64_t off = 0;
+  // neighbours at Chebyshev distance <= 2, then the pair-block offsets: a
+  // cell's blocks in code order, cells in order
+  std::vector<int64_t> psum(L.ncell + 1, 0);
+  parallel_range(L.ncell, 2048, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; c++) {
+      int64_t tot = 0;
+      int lim = dim == 3 ? 2 : 0;
+      for (int dz = -lim; dz <= lim; dz++)
+        for (int dy = -2; dy <= 2; dy++)
+          for (int dx = -2; dx <= 2; dx++) {
+            int64_t p[3] = {L.cell_coord[3 * c] + dx, L.cell_coord[3 * c + 1] + dy, L.cell_coord[3 * c + 2] + dz};
+            bool ok = true;
+            for (int d = 0; d < dim; d++) ok = ok && p[d] >= 0 && p[d] < side;
+            if (!ok) continue;
+            int nb = lookup(p);
+            if (nb < 0) continue;
+            L.cell_nbr[(size_t)c * L.NB + code5(dx, dy, dz, dim)] = nb;
+            tot += (int64_t)L.cell_b[c] * L.cell_b[nb];
+          }
+      psum[c + 1] = tot;
+    }
+  });
   for (int c = 0; c < L.ncell; c++) {
+    psum[c + 1] += psum[c];
     L.bmax = std::max(L.bmax, L.cell_b[c]);
-    int lim = dim == 3 ? 2 : 0;
-    for (int dz = -lim; dz <= lim; dz++)
-      for (int dy = -2; dy <= 2; dy++)
-        for (int dx = -2; dx <= 2; dx++) {
-          int64_t p[3] = {L.cell_coord[3 * c] + dx, L.cell_coord[3 * c + 1] + dy, L.cell_coord[3 * c + 2] + dz};
-          bool ok = true;
-          for (int d = 0; d < dim; d++) ok = ok && p[d] >= 0 && p[d] < side;
-          if (!ok) continue;
-          int nb = lookup(p);
-          if (nb < 0) continue;
-          int code = code5(dx, dy, dz, dim);
-          L.cell_nbr[(size_t)c * L.NB + code] = nb;
-          L.pair_off[(size_t)c * L.NB + code] = off;
-          off += (int64_t)L.cell_b[c] * L.cell_b[nb];
-        }
   }
-  L.pool_elems = off;
+  parallel_range(L.ncell, 2048, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; c++) {
+      int64_t off = psum[c];
+      for (int code = 0; code < L.NB; code++) {
+        const int nb = L.cell_nbr[(size_t)c * L.NB + code];
+        if (nb < 0) continue;
+        L.pair_off[(size_t)c * L.NB + code] = off;
+        off += (int64_t)L.cell_b[c] * L.cell_b[nb];
+      }
+    }
+  });
+  L.pool_elems = psum[L.ncell];
   for (int node : T.level[t]) {
     int64_t p[3] = {T.coord[3 * node], T.coord[3 * node + 1], T.coord[3 * node + 2]};
     int c = find_key(L.key, morton_fast(p, dim));
@@ -856,20 +977,29 @@ template <typename T> static void detect_grid(Factor<T> &F) {
   for (int d = 0; d < dim; d++) tot *= s;
   if (tot != n || (s & (s - 1)) != 0 || 2 * s > 2048) return;
   std::vector<int64_t> gi(n);
-  std::vector<char> seen(n, 0);
-  for (int64_t g = 0; g < n; g++) {
-    int64_t lin = 0, mul = 1;
-    for (int d = 0; d < dim; d++) {
-      double v = T_.x[g * dim + d] * (double)s - 0.5;
-      double iv = nearbyint(v);
-      if (v != iv || iv < 0 || iv >= (double)s) return;
-      lin += (int64_t)iv * mul;
-      mul *= s;
+  std::vector<unsigned char> seen(n, 0);
+  std::atomic<bool> bad{false};
+  parallel_range(n, (int64_t)1 << 15, [&](int64_t lo, int64_t hi) {
+    for (int64_t g = lo; g < hi && !bad.load(std::memory_order_relaxed); g++) {
+      int64_t lin = 0, mul = 1;
+      for (int d = 0; d < dim; d++) {
+        double v = T_.x[g * dim + d] * (double)s - 0.5;
+        double iv = nearbyint(v);
+        if (v != iv || iv < 0 || iv >= (double)s) {
+          bad = true;
+          return;
+        }
+        lin += (int64_t)iv * mul;
+        mul *= s;
+      }
+      if (__atomic_exchange_n(&seen[lin], (unsigned char)1, __ATOMIC_RELAXED)) {  // a cell used twice
+        bad = true;
+        return;
+      }
+      gi[T_.perm[g]] = lin;
     }
-    if (seen[lin]) return;
-    seen[lin] = 1;
-    gi[T_.perm[g]] = lin;
-  }
+  });
+  if (bad) return;
   F.grid_side = (int)s;
   F.grid_index.swap(gi);
 }
