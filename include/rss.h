@@ -287,8 +287,7 @@ rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *ra
  * that keep 32 (FP32) or 16 (FP64) rows of every panel, a box's rows over
  * fold groups of one CTA or over several CTAs, whose triangles are merged by
  * a tree; more threads per box mean fewer sequential steps per box, fewer
- * fit more boxes per SM.  Several CTAs per box are tried for phases of at
- * most 256 boxes.  The first colour phase that meets a key times every
+ * fit more boxes per SM.  The first colour phase that meets a key times every
  * candidate on its own boxes (the ID launch is idempotent), keeps the
  * fastest for the rest of the process and re-runs it, so factorizations with
  * the same key compute the same result.  Disabled per factorization by

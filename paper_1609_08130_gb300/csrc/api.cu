@@ -1089,7 +1089,7 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
     for (int ci = 0; ci < kNShapes; ci++) {
       const int tpc = kTuneShapes[ci][0], g = kTuneShapes[ci][1], ctas = kTuneShapes[ci][2];
       if (!shape_fits(width, tpc, g)) continue;  // the kernels' thread limits
-      if (ctas > 1 && (nbox > 256 || (width == 256 && tpc != 2))) continue;  // several CTAs per box: small phases
+      if (ctas > 1 && width == 256 && tpc != 2) continue;  // the widest class: two threads per column
       set_id_groups(shape_hint(ci));
       float ms = 0.f;
       for (int rep = 0; rep < 2; rep++) {  // the second launch is timed
@@ -1575,12 +1575,12 @@ template <typename T> static void run_factor(Factor<T> &F) {
     if (!id_smem) grow(gid, (size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
     int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32 + elim_ws_elems<T>(H.bmax);
     grow(gel, (size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
-    // the multi-CTA ID's triangle slots (8 CTAs per box of a phase of up to
-    // 256 boxes) and tree-node counters
+    // the multi-CTA ID's triangle slots (8 CTAs per box of the largest
+    // phase) and tree-node counters
     IdMultiScratch ims{};
     if (H.bmax <= 256 && !large) {
       const int64_t se = H.bmax <= 64 ? 64 * 65 : H.bmax <= 128 ? 128 * 129 : (int64_t)H.bmax * (H.bmax + 1);
-      const int64_t slots = 8 * (int64_t)std::min(std::max(maxphase, 1), 256);
+      const int64_t slots = 8 * (int64_t)std::max(maxphase, 1);
       grow(gtri, (size_t)(slots * se) * sizeof(T), st, 1);
       grow(gcnt, sizeof(int) * (size_t)slots * 8, st, 1);
       CK(cudaMemsetAsync(gcnt.p, 0, sizeof(int) * (size_t)slots * 8, st));
