@@ -1935,14 +1935,18 @@ __device__ bool claim_storage(FBox<T> &fb, int nj, const Overflow<T> &ov, int *e
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
                                              int64_t sstride, int64_t ws_off, int use_smem, Overflow<T> ovf,
-                                             int *err) {
+                                             int *err, int C) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nn;
   __shared__ int64_t s_off_in[27], s_off_out[27];
   __shared__ int s_ld_in[27];
   __shared__ int s_pivrow, s_ok;
 
-  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  // C CTAs per box (shared-memory workspace only): every CTA forms its share
+  // of the rows of X_JR and columns of X_RJ; CTA 0 also forms the S columns
+  // of X_RJ (the X_RS its LU needs), the LU, X_RR^{-1} and the box's records
+  const int q = blockIdx.x / C, cta = blockIdx.x % C;
+  FBox<T> &fb = boxes[box_list[q]];
   const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
   const int ncode3 = dim == 3 ? 27 : 9;
@@ -1950,7 +1954,7 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
 
   // Ts (k x r, ld k), LU (r x r, ld r+1), loc (b ints), piv (r ints): in
   // shared memory, or for large boxes in this box's global workspace
-  T *Ts = use_smem ? reinterpret_cast<T *>(smem_raw) : scratch + (int64_t)blockIdx.x * sstride + ws_off;
+  T *Ts = use_smem ? reinterpret_cast<T *>(smem_raw) : scratch + (int64_t)q * sstride + ws_off;
   const int ldl = r + 1;
   T *LU = Ts + (int64_t)k * r;
   int *sloc = reinterpret_cast<int *>(LU + (int64_t)r * ldl);
@@ -1978,9 +1982,9 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
     }
     s_nstart[nn] = acc;
     s_nn = nn;
-    s_ok = acc <= fb.njmax ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
+    s_ok = (acc <= fb.njmax && cta == 0) ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
   }
-  for (int q = tid; q < b; q += NT) sloc[q] = fb.loc[q];
+  for (int q2 = tid; q2 < b; q2 += NT) sloc[q2] = fb.loc[q2];
   for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
   __syncthreads();
   if (!s_ok) return;
@@ -2006,21 +2010,36 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
       loc = lv.act_idx[lv.cell_dof_off[nb] + (a - s_nstart[q])];
       g = lv.cell_dofs[lv.cell_dof_off[nb] + loc];
     }
-    fb.J[a] = g;
-    fb.Jnb[a] = code;
-    fb.Jloc[a] = loc;
+    if (cta == 0) {
+      fb.J[a] = g;
+      fb.Jnb[a] = code;
+      fb.Jloc[a] = loc;
+    }
   }
-  if (tid == 0) fb.nj = nj;
+  if (tid == 0 && cta == 0) fb.nj = nj;
   __syncthreads();
+  // (3^d code, local index) of J entry a, as in the J lists above
+  auto jinfo = [&](int a, int &code, int &la) {
+    if (a < k) {
+      code = center;
+      la = sloc[a];
+    } else {
+      int q2 = 0;
+      while (s_nstart[q2 + 1] <= a) q2++;
+      code = s_ncode[q2];
+      la = lv.act_idx[lv.cell_dof_off[s_ncell[code]] + (a - s_nstart[q2])];
+    }
+  };
 
-  T *Ep = scratch + (int64_t)blockIdx.x * sstride;  // X_JR, nj x r col-major (ld nj)
+  T *Ep = scratch + (int64_t)q * sstride;  // X_JR, nj x r col-major (ld nj)
   T *Gp = Ep + (int64_t)nj * r;                      // X_RJ, r x nj col-major (ld r)
   const T *pool = lv.pool;
   const T *Aii = pool + s_off_in[center];            // block (c, c), ld b
 
   // X_JR = A_JR - A_JS T   (L_T applied from the right)
-  for (int a = tid; a < nj; a += NT) {
-    int code = fb.Jnb[a], la = fb.Jloc[a];
+  for (int a = cta * NT + tid; a < nj; a += C * NT) {
+    int code, la;
+    jinfo(a, code, la);
     const T *Ab = pool + s_off_in[code];
     int64_t ld = s_ld_in[code];
     const T *row = Ab + la;
@@ -2039,17 +2058,23 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
         if (r0 + u < r) Ep[a + (int64_t)(r0 + u) * nj] = acc[u];
     }
   }
-  // X_RJ = A_RJ - T^T A_SJ  (U_T applied from the left); one warp per column
-  for (int a = warp; a < nj; a += nwarp) {
-    int code = fb.Jnb[a], la = fb.Jloc[a];
+  // X_RJ = A_RJ - T^T A_SJ  (U_T applied from the left); one warp per column:
+  // the S columns by CTA 0, the others shared by all CTAs
+  auto xrj_col = [&](int a) {
+    int code, la;
+    jinfo(a, code, la);
     const T *col = pool + s_off_out[code] + (int64_t)la * b;  // column la of block (c, nb)
     for (int ri = lane; ri < r; ri += 32) {
       T acc = col[sloc[k + ri]];
       for (int s = 0; s < k; s++) acc -= Ts[s + (int64_t)ri * k] * col[sloc[s]];
       Gp[ri + (int64_t)a * r] = acc;
     }
-  }
+  };
+  if (cta == 0)
+    for (int a = warp; a < k; a += nwarp) xrj_col(a);
+  for (int a = k + cta * nwarp + warp; a < nj; a += C * nwarp) xrj_col(a);
   __syncthreads();
+  if (cta != 0) return;
   // X_RR = A_RR - T^T A_SR - X_RS T   (X_RS = first k columns of X_RJ)
   for (int e = tid; e < r * r; e += NT) {
     int ri = e / r, rj = e % r;
@@ -2683,8 +2708,10 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   // the global workspace sits after the X_JR / X_RJ scratch of the box
   const int64_t ws_off = scratch_stride - elim_ws_elems<T>(bmax);
   if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_elim<T><<<nbox, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
-                                                    use_smem ? 1 : 0, ovf, err);
+  // several CTAs per box for small phases (shared-memory workspace only)
+  const int Cg = use_smem ? std::min(8, std::max(1, (300 + nbox - 1) / nbox)) : 1;
+  k_elim<T><<<nbox * Cg, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
+                                                         use_smem ? 1 : 0, ovf, err, Cg);
   // E and G: tiles of 64 x 64 over nj x r (E) and r x nj (G), nj <= njmax, r <= bmax
   const int tiles_e = tn * tr;  // E: nj x r
   const int tiles_g = tr * tn;  // G: r x nj
