@@ -183,7 +183,7 @@ def run_reference(args, rank, world):
 # valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
     "id": {"bytes_per_launch": 21.28e6,
-           "kernels_sha256": "334c36865b70af698abb1b5e3418905ed44c31b3f3bdd84d708427e18e106af9"},
+           "kernels_sha256": "c2bcd2bc09582b915102e46c9b838d63577b8a6189488b78f3ce047aa02724a3"},
 }
 
 
