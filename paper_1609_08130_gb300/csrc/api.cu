@@ -1578,7 +1578,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     // the multi-CTA ID's triangle slots (8 CTAs per box of the largest
     // phase) and tree-node counters
     IdMultiScratch ims{};
-    if (H.bmax <= 256 && !large) {
+    if (H.bmax <= 512 && !large) {
       const int64_t se = H.bmax <= 64 ? 64 * 65 : H.bmax <= 128 ? 128 * 129 : (int64_t)H.bmax * (H.bmax + 1);
       const int64_t slots = 8 * (int64_t)std::max(maxphase, 1);
       grow(gtri, (size_t)(slots * se) * sizeof(T), st, 1);

@@ -1584,7 +1584,7 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
 // The CTA that completes the root runs the pivoted QR and writes the ID.
 // No CTA waits for another.
 // ---------------------------------------------------------------------------
-template <typename T, int NC, int TPC>
+template <typename T, int NC, int TPC, bool GLOB>
 __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int C, Points P,
                                              KernelParams K, ProxyParams px, const double *proxy_unit, double eps,
                                              int ring_max, T *tri, int64_t tstride, int *cnt, int *err) {
@@ -1594,6 +1594,7 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
   constexpr int GT = NC * TPC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ocode[125], s_obase[126], s_no, s_second;
+  __shared__ int64_t s_pbase[125], s_abase[125];  // GLOB: each ring cell's pair block and active list
   __shared__ IdqShared<T, NC, TPC> s_sh;
   const int tid = threadIdx.x, lt = tid;
   const int col = lt / TPC, part = lt % TPC;
@@ -1601,11 +1602,15 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
   FBox<T> &fb = boxes[box_list[bq]];
   const int c = fb.cell, b = fb.b, dim = lv.dim;
   const int TR = NC > 128 ? b : NC, LDR = TR + 1;
-  T *R = reinterpret_cast<T *>(smem_raw);
-  const size_t tri_bytes = (((size_t)TR * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  // the triangle in shared memory, or (GLOB: boxes too wide for it) in this
+  // CTA's slot of `tri`, where it stays L2-resident: the fold touches one row
+  // of it per reflector step
+  T *slots = tri + (int64_t)bq * C * tstride;
+  T *R = GLOB ? slots + (int64_t)chunk * tstride : reinterpret_cast<T *>(smem_raw);
+  const size_t tri_bytes = GLOB ? 0 : (((size_t)TR * LDR * sizeof(T)) + 15) & ~(size_t)15;
   T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes);
   int64_t *s_rowsrc = reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)2 * VS * sizeof(T) + 15) & ~(size_t)15));
-  int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
+  int *perm = reinterpret_cast<int *>(s_rowsrc + (GLOB ? 0 : ring_max));
 
   for (int e = lt; e < TR * LDR; e += GT) R[e] = (T)0;
   if (tid < 32) {
@@ -1647,15 +1652,35 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
     if (tid == 0) set_err(err, DERR_INTERNAL);
     return;  // every CTA of the box sees the same nO: the box's tree is abandoned whole
   }
-  for (int q = 0; q < no; q++) {
-    const int code = s_ocode[q];
-    const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
-    const int64_t abase = lv.cell_dof_off[nb];
-    const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
-    for (int t = tid; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
-      s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+  if (GLOB) {
+    for (int q = tid; q < no; q += blockDim.x) {
+      const int code = s_ocode[q];
+      s_abase[q] = lv.cell_dof_off[lv.cell_nbr[(int64_t)c * lv.NB + code]];
+      s_pbase[q] = lv.pair_off[(int64_t)c * lv.NB + code];
+    }
+  } else {
+    for (int q = 0; q < no; q++) {
+      const int code = s_ocode[q];
+      const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+      const int64_t abase = lv.cell_dof_off[nb];
+      const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
+      for (int t = tid; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
+        s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+    }
   }
   __syncthreads();
+  // pool offset of ring row `row` (< nO): the table, or (GLOB) its ring cell
+  // by binary search over the cells' first rows
+  auto rowsrc = [&](int row) -> int64_t {
+    if (!GLOB) return s_rowsrc[row];
+    int lo = 0, hi = no - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_obase[mid] <= row) lo = mid;
+      else hi = mid - 1;
+    }
+    return s_pbase[lo] + (int64_t)lv.act_idx[s_abase[lo] + (row - s_obase[lo])] * b;
+  };
   const int m = nO + px.np;
   const int64_t coff = lv.cell_dof_off[c];
   const double D = ldexp(1.0, -lv.t);
@@ -1679,7 +1704,7 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
       T v = (T)0;
       if (col < b) {
         if (row < nO) {
-          v = lv.pool[s_rowsrc[row] + col];
+          v = lv.pool[rowsrc(row) + col];
         } else if (row < m) {
           const int pm = row - nO;
           double r2 = 0.0;
@@ -1695,14 +1720,15 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
     }
     fold_group_q<T, PR, TPC>(pan, R, LDR, b, col, part, vbuf, 1, GT);
   }
-  T *slots = tri + (int64_t)bq * C * tstride;
   int cur = chunk;  // first slot of the subtree this CTA carries
   for (int L = 1; L < C; L <<= 1) {
     const int ls = cur & ~(2 * L - 1), rs = ls + L;
     if (rs >= C) continue;  // no right partner at this level: carry the subtree up
     // publish this subtree's triangle, then count arrivals at the node
-    T *mine = slots + (int64_t)cur * tstride;
-    for (int e = lt; e < TR * LDR; e += GT) mine[e] = R[e];
+    if (!GLOB) {
+      T *mine = slots + (int64_t)cur * tstride;
+      for (int e = lt; e < TR * LDR; e += GT) mine[e] = R[e];
+    }
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -1714,9 +1740,13 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
     __syncthreads();
     if (!s_second) return;
     __threadfence();
-    if (cur != ls) {  // came from the right: the left triangle into shared memory
-      const T *left = slots + (int64_t)ls * tstride;
-      for (int e = lt; e < TR * LDR; e += GT) R[e] = __ldcg(left + e);
+    if (cur != ls) {  // came from the right: continue on the left triangle
+      T *left = slots + (int64_t)ls * tstride;
+      if (GLOB) {
+        R = left;
+      } else {
+        for (int e = lt; e < TR * LDR; e += GT) R[e] = __ldcg(left + e);
+      }
       __syncthreads();
     }
     const T *right = slots + (int64_t)rs * tstride;
@@ -1735,18 +1765,23 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
   idq_finish<T, NC, TPC>(R, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
 }
 
-template <typename T, int NC, int TPC>
+template <typename T, int NC, int TPC, bool GLOB = false>
+static size_t idm_smem(int bmax, int ring_max) {
+  constexpr int PR = IdwRows<T>::PR * TPC;
+  const int TR = NC > 128 ? bmax : NC;
+  return (GLOB ? 0 : ((((size_t)TR * (TR + 1) * sizeof(T)) + 15) & ~(size_t)15)) +
+         ((((size_t)2 * (PR + 4) * sizeof(T)) + 15) & ~(size_t)15) + (GLOB ? 0 : (size_t)ring_max * sizeof(int64_t)) +
+         (size_t)NC * sizeof(int) + 16;
+}
+
+template <typename T, int NC, int TPC, bool GLOB = false>
 static void launch_idm(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int C, int bmax,
                        const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
                        double eps, int ring_max, T *tri, int64_t tstride, int *cnt, cudaStream_t st, int *err) {
-  constexpr int PR = IdwRows<T>::PR * TPC;
-  const int TR = NC > 128 ? bmax : NC;
-  const size_t smem = ((((size_t)TR * (TR + 1) * sizeof(T)) + 15) & ~(size_t)15) +
-                      ((((size_t)2 * (PR + 4) * sizeof(T)) + 15) & ~(size_t)15) + (size_t)ring_max * sizeof(int64_t) +
-                      (size_t)NC * sizeof(int) + 16;
-  cudaFuncSetAttribute(k_idm<T, NC, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_idm<T, NC, TPC><<<nbox * C, NC * TPC, smem, st>>>(lv, boxes, box_list, C, P, K, px, proxy_unit, eps, ring_max,
-                                                      tri, tstride, cnt, err);
+  const size_t smem = idm_smem<T, NC, TPC, GLOB>(bmax, ring_max);
+  cudaFuncSetAttribute(k_idm<T, NC, TPC, GLOB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idm<T, NC, TPC, GLOB><<<nbox * C, NC * TPC, smem, st>>>(lv, boxes, box_list, C, P, K, px, proxy_unit, eps,
+                                                            ring_max, tri, tstride, cnt, err);
   count_launch();
 }
 
@@ -1881,6 +1916,18 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     if (sm <= (size_t)(220 << 10)) {
       if (TPC == 1) launch_idq<T, 256, 1>(lv, boxes, box_list, nbox, 1, bmax, P, K, px, proxy_unit, eps, mmax, st, err);
       else launch_idq<T, 256, 2>(lv, boxes, box_list, nbox, 1, bmax, P, K, px, proxy_unit, eps, mmax, st, err);
+      return;
+    }
+  }
+  if (bmax <= 512 && !force_general) {
+    // boxes too wide for a shared-memory triangle: several CTAs per box
+    // with their triangles in global (L2-resident) slots
+    const int C = (id_groups_hint >> 8) > 1 ? (id_groups_hint >> 8) : 8;
+    if (id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots &&
+        (int64_t)bmax * (bmax + 1) <= id_multi.slot_elems &&
+        idm_smem<T, 512, 1, true>(bmax, mmax) <= (size_t)(220 << 10)) {
+      launch_idm<T, 512, 1, true>(lv, boxes, box_list, nbox, C, bmax, P, K, px, proxy_unit, eps, mmax,
+                                  (T *)id_multi.tri, (int64_t)bmax * (bmax + 1), id_multi.cnt, st, err);
       return;
     }
   }

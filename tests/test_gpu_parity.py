@@ -428,3 +428,23 @@ def test_wide_box_id_matches_oracle(pkg):
             assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, ctas)
     finally:
         lib.rss_autotune_clear()
+
+
+def test_id_with_triangles_in_global_memory(pkg):
+    """Boxes too wide for a shared-memory triangle (FP64, 197 DOFs at depth
+    2 of a 3D octree at eps 1e-6) take the several-CTAs-per-box ID with its
+    triangles in global memory.  Checked against the exact operator (the
+    FP64 direct sum, itself checked against the oracle): apply and solve
+    within 10 eps, and against the one-CTA-per-box kernels (forced large-box
+    path) within the same bound."""
+    pts = inputs.random_points(5, 10000, 3)
+    eps = 1e-6
+    f = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.FP64)
+    assert f.stats()["b"].max() > 165
+    x = _cuda(inputs.rhs(96, len(pts), 2))
+    ax = f.matvec(x)
+    assert float(torch.linalg.norm(f.apply(x) - ax) / torch.linalg.norm(ax)) <= 10 * eps
+    z = f.solve(x)
+    assert float(torch.linalg.norm(f.matvec(z) - x) / torch.linalg.norm(x)) <= 10 * eps
+    g = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.FP64, flags=pkg.rss.FLAG_LARGE_BOX_PATH)
+    assert float(torch.linalg.norm(g.solve(x) - z) / torch.linalg.norm(z)) <= 10 * eps
