@@ -2000,12 +2000,15 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
   const int center = code3(0, 0, 0, dim);
 
   // Ts (k x r, ld k), LU (r x r, ld r+1), loc (b ints), piv (r ints): in
-  // shared memory, or for large boxes in this box's global workspace
-  T *Ts = use_smem ? reinterpret_cast<T *>(smem_raw) : scratch + (int64_t)q * sstride + ws_off;
+  // shared memory, or for large boxes in this box's global workspace, where
+  // T and loc are read from the box's records in place (every CTA of the box
+  // reads them; only CTA 0 writes the LU and pivots)
+  T *ws = use_smem ? reinterpret_cast<T *>(smem_raw) : scratch + (int64_t)q * sstride + ws_off;
   const int ldl = r + 1;
-  T *LU = Ts + (int64_t)k * r;
-  int *sloc = reinterpret_cast<int *>(LU + (int64_t)r * ldl);
-  int *spiv = sloc + b;
+  const T *Ts = use_smem ? ws : fb.Tm;
+  T *LU = ws + (int64_t)k * r;
+  int *sloc = use_smem ? reinterpret_cast<int *>(LU + (int64_t)r * ldl) : fb.loc;
+  int *spiv = reinterpret_cast<int *>(LU + (int64_t)r * ldl) + b;
 
   if (tid == 0) {
     int nn = 0, acc = k;
@@ -2031,8 +2034,10 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
     s_nn = nn;
     s_ok = (acc <= fb.njmax && cta == 0) ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
   }
-  for (int q2 = tid; q2 < b; q2 += NT) sloc[q2] = fb.loc[q2];
-  for (int e = tid; e < k * r; e += NT) Ts[e] = fb.Tm[e];
+  if (use_smem) {
+    for (int q2 = tid; q2 < b; q2 += NT) sloc[q2] = fb.loc[q2];
+    for (int e = tid; e < k * r; e += NT) ws[e] = fb.Tm[e];
+  }
   __syncthreads();
   if (!s_ok) return;
   const int nn = s_nn;
@@ -2755,8 +2760,8 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   // the global workspace sits after the X_JR / X_RJ scratch of the box
   const int64_t ws_off = scratch_stride - elim_ws_elems<T>(bmax);
   if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  // several CTAs per box for small phases (shared-memory workspace only)
-  const int Cg = use_smem ? std::min(8, std::max(1, (300 + nbox - 1) / nbox)) : 1;
+  // several CTAs per box for small phases
+  const int Cg = force_general ? 1 : std::min(8, std::max(1, (300 + nbox - 1) / nbox));
   k_elim<T><<<nbox * Cg, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
                                                          use_smem ? 1 : 0, ovf, err, Cg);
   // E and G: tiles of 64 x 64 over nj x r (E) and r x nj (G), nj <= njmax, r <= bmax
