@@ -1982,16 +1982,17 @@ __device__ bool claim_storage(FBox<T> &fb, int nj, const Overflow<T> &ov, int *e
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
                                              int64_t sstride, int64_t ws_off, int use_smem, Overflow<T> ovf,
-                                             int *err, int C) {
+                                             int *err, int C, int form_only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nn;
   __shared__ int64_t s_off_in[27], s_off_out[27];
   __shared__ int s_ld_in[27];
   __shared__ int s_pivrow, s_ok;
 
-  // C CTAs per box (shared-memory workspace only): every CTA forms its share
-  // of the rows of X_JR and columns of X_RJ; CTA 0 also forms the S columns
-  // of X_RJ (the X_RS its LU needs), the LU, X_RR^{-1} and the box's records
+  // C CTAs per box: every CTA forms its share of the rows of X_JR and columns
+  // of X_RJ; CTA 0 also forms the S columns of X_RJ (the X_RS its LU needs)
+  // and, unless form_only (X_RR, its LU and inverse then follow in
+  // k_elim_xrr and k_elim_lu), the LU, X_RR^{-1} and the box's records
   const int q = blockIdx.x / C, cta = blockIdx.x % C;
   FBox<T> &fb = boxes[box_list[q]];
   const int c = fb.cell, b = fb.b, k = fb.k, r = fb.r, dim = lv.dim;
@@ -2126,7 +2127,7 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
     for (int a = warp; a < k; a += nwarp) xrj_col(a);
   for (int a = k + cta * nwarp + warp; a < nj; a += C * nwarp) xrj_col(a);
   __syncthreads();
-  if (cta != 0) return;
+  if (cta != 0 || form_only) return;
   // X_RR = A_RR - T^T A_SR - X_RS T   (X_RS = first k columns of X_RJ)
   for (int e = tid; e < r * r; e += NT) {
     int ri = e / r, rj = e % r;
@@ -2723,6 +2724,343 @@ __global__ void __launch_bounds__(NT) k_elim_gemm(const FBox<T> *boxes, const in
   }
 }
 
+// X_RR = A_RR - T^T A_SR - X_RS T (Sec. 3.1) for the boxes of a phase whose
+// elimination runs in k_elim_lu, one 64 x 64 tile of X_RR per CTA: a GEMM of
+// inner dimension 2k with A' = [T^T | X_RS] (r x 2k) and B' = [A_SR ; T]
+// (2k x r), subtracted from A_RR.  X_RS is the first k columns of X_RJ in the
+// box's scratch (formed by k_elim); X_RR goes to the box's workspace,
+// column-major with leading dimension r.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_elim_xrr(LevelDev<T> lv, const FBox<T> *boxes, const int *box_list,
+                                                 T *scratch, int64_t sstride, int64_t ws_off, int tcols) {
+  __shared__ T As[16][64 + 1];
+  __shared__ T Bs[16][64 + 1];
+  const int q = blockIdx.x;
+  const FBox<T> &fb = boxes[box_list[q]];
+  const int r = fb.r, k = fb.k, b = fb.b, nj = fb.nj;
+  const int i0 = (blockIdx.y / tcols) * 64, j0 = (blockIdx.y % tcols) * 64;
+  if (r == 0 || i0 >= r || j0 >= r) return;
+  const T *Xrj = scratch + (int64_t)q * sstride + (int64_t)nj * r;
+  T *M = scratch + (int64_t)q * sstride + ws_off;
+  const int center = code5(0, 0, 0, lv.dim);
+  const int self = lv.cell_nbr[(int64_t)fb.cell * lv.NB + center];
+  const T *Aii = lv.pool + lv.pair_off[(int64_t)self * lv.NB + center];  // block (c, c), ld b
+  const int *loc = fb.loc;
+  const T *Tm = fb.Tm;
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int y = 0; y < 4; y++) acc[x][y] = (T)0;
+  for (int l0 = 0; l0 < 2 * k; l0 += 16) {
+    for (int e = tid; e < 16 * 64; e += NT) {
+      {
+        const int ii = e % 64, l = l0 + e / 64, ri = i0 + ii;
+        T av = (T)0;
+        if (ri < r && l < 2 * k) av = l < k ? Tm[l + (int64_t)ri * k] : Xrj[ri + (int64_t)(l - k) * r];
+        As[e / 64][ii] = av;
+      }
+      {
+        const int l2 = e % 16, jj = e / 16, l = l0 + l2, rj = j0 + jj;
+        T bv = (T)0;
+        if (rj < r && l < 2 * k)
+          bv = l < k ? Aii[loc[l] + (int64_t)loc[k + rj] * b] : Tm[(l - k) + (int64_t)rj * k];
+        Bs[l2][jj] = bv;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) av[x] = As[u][ti + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; y++) bv[y] = Bs[u][tj + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++) acc[x][y] += av[x] * bv[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < 4; y++) {
+    const int rj = j0 + tj + 16 * y;
+    if (rj >= r) continue;
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      const int ri = i0 + ti + 16 * x;
+      if (ri < r) M[ri + (int64_t)rj * r] = Aii[loc[k + ri] + (int64_t)loc[k + rj] * b] - acc[x][y];
+    }
+  }
+}
+
+// (value, index) argmax over a warp: largest value, ties to the lowest index
+template <typename T> __device__ __forceinline__ void warp_argmax(T &best, int &bi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+}
+
+constexpr int NLU = 1024;  // threads of k_elim_lu
+
+template <typename T> size_t elim_lu_smem(int r, int nbp) {
+  return 2 * (size_t)nbp * r * sizeof(T) + (size_t)r * sizeof(int) + 16;
+}
+
+// LU with partial pivoting of X_RR (largest |entry|, ties to the lowest row;
+// X_RR = P^T L U), X_RR^{-1} = U^{-1} L^{-1} P and the box's skeleton list,
+// one CTA of 1024 threads per box, for boxes too wide for k_elim's
+// shared-memory form.  Blocked right-looking LU with panels of NBP columns:
+// the panel is factored in shared memory (a block-wide argmax per column),
+// its row interchanges are applied to the other columns, U12 = L11^{-1} A12
+// by one thread per column, and A22 -= L21 U12 with each lane accumulating a
+// 4 x 4 block.  X_RR^{-1} by blocked forward and back substitution on the
+// columns of the identity, NBP rows at a time, the block rows of L and U
+// staged in shared memory.  X_RR (column-major, ld r) is in the workspace.
+template <typename T, int NBP>
+__global__ void __launch_bounds__(NLU) k_elim_lu(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
+                                                 int64_t sstride, int64_t ws_off, int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T s_bv[32];
+  __shared__ int s_bi[32], s_p, s_swp[NBP];
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int r = fb.r, k = fb.k, c = fb.cell;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T *M = scratch + (int64_t)blockIdx.x * sstride + ws_off;
+  T *P = reinterpret_cast<T *>(smem_raw);  // panel: P[jj * r + i], rows i in [j0, r)
+  T *U = P + (int64_t)NBP * r;              // U12: U[t * r + column]
+  int *perm = reinterpret_cast<int *>(U + (int64_t)NBP * r);
+  if (r > 0) {
+    for (int i = tid; i < r; i += NLU) perm[i] = i;
+    for (int j0 = 0; j0 < r; j0 += NBP) {
+      const int nb = min(NBP, r - j0), h = r - j0;
+      for (int e = tid; e < nb * h; e += NLU) {
+        const int jj = e / h, i = j0 + e % h;
+        P[jj * r + i] = M[i + (int64_t)(j0 + jj) * r];
+      }
+      __syncthreads();
+      for (int jj = 0; jj < nb; jj++) {
+        const int j = j0 + jj;
+        T best = (T)-1;
+        int bi = r;
+        for (int i = j + tid; i < r; i += NLU) {
+          const T v = fabs(P[jj * r + i]);
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
+        warp_argmax(best, bi);
+        if (lane == 0) {
+          s_bv[warp] = best;
+          s_bi[warp] = bi;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          best = s_bv[lane];
+          bi = s_bi[lane];
+          warp_argmax(best, bi);
+          if (lane == 0) {
+            if (bi >= r) {  // NaN column: keep the diagonal, report
+              bi = j;
+              set_err(err, DERR_NUMERIC);
+            }
+            if (best == (T)0) set_err(err, DERR_NUMERIC);
+            s_p = bi;
+            s_swp[jj] = bi;
+          }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != j) {
+          if (tid < nb) {
+            const T t0 = P[tid * r + j];
+            P[tid * r + j] = P[tid * r + p];
+            P[tid * r + p] = t0;
+          }
+          if (tid == NLU - 1) {
+            const int tp = perm[j];
+            perm[j] = perm[p];
+            perm[p] = tp;
+          }
+          __syncthreads();
+        }
+        const T d = P[jj * r + j];
+        for (int i = j + 1 + tid; i < r; i += NLU) P[jj * r + i] /= d;
+        __syncthreads();
+        const int rows = r - j - 1, cols = nb - jj - 1;
+        for (int e = tid; e < rows * cols; e += NLU) {
+          const int i = j + 1 + e % rows, cc = jj + 1 + e / rows;
+          P[cc * r + i] -= P[jj * r + i] * P[cc * r + j];
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < nb * h; e += NLU) {
+        const int jj = e / h, i = j0 + e % h;
+        M[i + (int64_t)(j0 + jj) * r] = P[jj * r + i];
+      }
+      // the panel's row interchanges, in order, on the columns outside it
+      for (int cc = tid; cc < r; cc += NLU) {
+        if (cc >= j0 && cc < j0 + nb) continue;
+        T *col = M + (int64_t)cc * r;
+        for (int jj = 0; jj < nb; jj++) {
+          const int p = s_swp[jj], j = j0 + jj;
+          if (p != j) {
+            const T t0 = col[j];
+            col[j] = col[p];
+            col[p] = t0;
+          }
+        }
+      }
+      __syncthreads();
+      const int c0 = j0 + nb, nc = r - c0;
+      if (nc > 0) {
+        // U12 = L11^{-1} A12, one thread per column right of the panel
+        for (int cc = c0 + tid; cc < r; cc += NLU) {
+          T u[NBP];
+          T *col = M + (int64_t)cc * r + j0;
+#pragma unroll
+          for (int t = 0; t < NBP; t++) u[t] = t < nb ? col[t] : (T)0;
+#pragma unroll
+          for (int t = 1; t < NBP; t++)
+            if (t < nb) {
+              T a = u[t];
+#pragma unroll
+              for (int t2 = 0; t2 < t; t2++) a -= P[t2 * r + j0 + t] * u[t2];
+              u[t] = a;
+            }
+#pragma unroll
+          for (int t = 0; t < NBP; t++)
+            if (t < nb) {
+              col[t] = u[t];
+              U[t * r + cc] = u[t];
+            }
+        }
+        __syncthreads();
+        // A22 -= L21 U12: a warp takes 128 rows x 4 columns, a lane rows
+        // lane + 32x (x < 4) of them
+        const int ublk = (nc + 127) / 128, cblk = (nc + 3) / 4;
+        for (int w = warp; w < ublk * cblk; w += NLU / 32) {
+          const int ib = c0 + (w % ublk) * 128 + lane, cb = c0 + (w / ublk) * 4;
+          T acc[4][4];
+#pragma unroll
+          for (int x = 0; x < 4; x++)
+#pragma unroll
+            for (int y = 0; y < 4; y++) acc[x][y] = (T)0;
+          for (int t = 0; t < nb; t++) {
+            T lv4[4], uv[4];
+#pragma unroll
+            for (int x = 0; x < 4; x++) lv4[x] = ib + 32 * x < r ? P[t * r + ib + 32 * x] : (T)0;
+#pragma unroll
+            for (int y = 0; y < 4; y++) uv[y] = cb + y < r ? U[t * r + cb + y] : (T)0;
+#pragma unroll
+            for (int x = 0; x < 4; x++)
+#pragma unroll
+              for (int y = 0; y < 4; y++) acc[x][y] += lv4[x] * uv[y];
+          }
+#pragma unroll
+          for (int y = 0; y < 4; y++) {
+            if (cb + y >= r) continue;
+#pragma unroll
+            for (int x = 0; x < 4; x++)
+              if (ib + 32 * x < r) M[ib + 32 * x + (int64_t)(cb + y) * r] -= acc[x][y];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // the factors, row-major as the sweeps read them
+    for (int e = tid; e < r * r; e += NLU) fb.LU[e] = M[e / r + (int64_t)(e % r) * r];
+    for (int i = tid; i < r; i += NLU) fb.piv[i] = perm[i];
+    // X_RR^{-1} = U^{-1} L^{-1} P: column perm[i] of it is U^{-1} L^{-1} e_i.
+    // Forward: w = L^{-1} e_i, NBP rows at a time, rows m0.. of L in P
+    T *Xi = fb.Xi;
+    for (int m0 = 0; m0 < r; m0 += NBP) {
+      const int nb = min(NBP, r - m0);
+      for (int e = tid; e < NBP * (m0 + nb); e += NLU) {
+        const int t = e % NBP, l = e / NBP;
+        P[t + l * NBP] = t < nb ? M[m0 + t + (int64_t)l * r] : (T)0;
+      }
+      __syncthreads();
+      for (int i = tid; i < r; i += NLU) {
+        T *w = Xi + (int64_t)perm[i] * r;
+        T acc[NBP];
+#pragma unroll
+        for (int t = 0; t < NBP; t++) acc[t] = m0 + t == i ? (T)1 : (T)0;
+        // from the warp's first column on (w[l] = 0 for l < i): the same l
+        // in every lane, so the reads of P are broadcasts
+        for (int l = i - lane; l < m0; l++) {
+          const T wl = w[l];
+#pragma unroll
+          for (int t = 0; t < NBP; t++) acc[t] -= P[t + l * NBP] * wl;
+        }
+#pragma unroll
+        for (int t = 1; t < NBP; t++)
+          if (t < nb) {
+            T a = acc[t];
+#pragma unroll
+            for (int t2 = 0; t2 < t; t2++) a -= P[t + (m0 + t2) * NBP] * acc[t2];
+            acc[t] = a;
+          }
+#pragma unroll
+        for (int t = 0; t < NBP; t++)
+          if (t < nb) w[m0 + t] = m0 + t < i ? (T)0 : acc[t];
+      }
+      __syncthreads();
+    }
+    // Back: z = U^{-1} w, from the last block of rows up
+    for (int m0 = ((r - 1) / NBP) * NBP; m0 >= 0; m0 -= NBP) {
+      const int nb = min(NBP, r - m0);
+      for (int e = tid; e < NBP * (r - m0); e += NLU) {
+        const int t = e % NBP, l = m0 + e / NBP;
+        P[t + (l - m0) * NBP] = t < nb ? M[m0 + t + (int64_t)l * r] : (T)0;
+      }
+      __syncthreads();
+      for (int i = tid; i < r; i += NLU) {
+        T *w = Xi + (int64_t)perm[i] * r;
+        T acc[NBP];
+#pragma unroll
+        for (int t = 0; t < NBP; t++) acc[t] = t < nb ? w[m0 + t] : (T)0;
+        for (int l = m0 + nb; l < r; l++) {
+          const T zl = w[l];
+#pragma unroll
+          for (int t = 0; t < NBP; t++) acc[t] -= P[t + (l - m0) * NBP] * zl;
+        }
+#pragma unroll
+        for (int t = NBP - 1; t >= 0; t--) {
+          if (t >= nb) continue;
+          T a = acc[t];
+#pragma unroll
+          for (int t2 = t + 1; t2 < NBP; t2++)
+            if (t2 < nb) a -= P[t + t2 * NBP] * acc[t2];
+          acc[t] = a / P[t + t * NBP];
+        }
+#pragma unroll
+        for (int t = 0; t < NBP; t++)
+          if (t < nb) w[m0 + t] = acc[t];
+      }
+      __syncthreads();
+    }
+  }
+  // the box's active DOFs are now its skeleton, kept in ascending order
+  const int64_t coff = lv.cell_dof_off[c];
+  for (int s = tid; s < k; s += NLU) {
+    const int v = fb.loc[s];
+    int rank = 0;
+    for (int s2 = 0; s2 < k; s2++) rank += fb.loc[s2] < v;
+    lv.act_idx[coff + rank] = v;
+  }
+  if (tid == 0) lv.act_cnt[c] = k;
+}
+
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
                  int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err, int njmax) {
@@ -2760,13 +3098,39 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
   // the global workspace sits after the X_JR / X_RJ scratch of the box
   const int64_t ws_off = scratch_stride - elim_ws_elems<T>(bmax);
   if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int tiles_e = tn * tr;  // E: nj x r
+  const int tiles_g = tr * tn;  // G: r x nj
+  if (!use_smem && !force_general) {
+    // wide boxes: X_JR and X_RJ over up to 64 CTAs per box, X_RR as tiles,
+    // the LU and X_RR^{-1} blocked in one 1024-thread CTA per box
+    int nbp = sizeof(T) == 4 ? 32 : 16;
+    while (nbp > 8 && elim_lu_smem<T>(bmax, nbp) > (size_t)(220 << 10)) nbp /= 2;
+    const size_t lsm = elim_lu_smem<T>(bmax, nbp);
+    if (lsm <= (size_t)(220 << 10)) {
+      const int Cb = std::min(64, std::max(1, (1216 + nbox - 1) / nbox));
+      k_elim<T><<<nbox * Cb, NT, 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, 0, ovf, err, Cb, 1);
+      k_elim_xrr<T><<<dim3(nbox, tr * tr), NT, 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, tr);
+      if (nbp == 8) {
+        cudaFuncSetAttribute(k_elim_lu<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
+        k_elim_lu<T, 8><<<nbox, NLU, lsm, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, err);
+      } else if (nbp == 16) {
+        cudaFuncSetAttribute(k_elim_lu<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
+        k_elim_lu<T, 16><<<nbox, NLU, lsm, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, err);
+      } else {
+        cudaFuncSetAttribute(k_elim_lu<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
+        k_elim_lu<T, 32><<<nbox, NLU, lsm, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, err);
+      }
+      k_elim_gemm<T><<<dim3(nbox, tiles_e + tiles_g), NT, 0, st>>>(boxes, box_list, scratch, scratch_stride,
+                                                                    tiles_e, tr, tn);
+      count_launch(4);
+      return;
+    }
+  }
   // several CTAs per box for small phases
   const int Cg = force_general ? 1 : std::min(8, std::max(1, (300 + nbox - 1) / nbox));
   k_elim<T><<<nbox * Cg, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
-                                                         use_smem ? 1 : 0, ovf, err, Cg);
+                                                         use_smem ? 1 : 0, ovf, err, Cg, 0);
   // E and G: tiles of 64 x 64 over nj x r (E) and r x nj (G), nj <= njmax, r <= bmax
-  const int tiles_e = tn * tr;  // E: nj x r
-  const int tiles_g = tr * tn;  // G: r x nj
   k_elim_gemm<T><<<dim3(nbox, tiles_e + tiles_g), NT, 0, st>>>(boxes, box_list, scratch, scratch_stride, tiles_e,
                                                               tr, tn);
   count_launch(2);

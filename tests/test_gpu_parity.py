@@ -448,3 +448,30 @@ def test_id_with_triangles_in_global_memory(pkg):
     assert float(torch.linalg.norm(f.matvec(z) - x) / torch.linalg.norm(x)) <= 10 * eps
     g = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.FP64, flags=pkg.rss.FLAG_LARGE_BOX_PATH)
     assert float(torch.linalg.norm(g.solve(x) - z) / torch.linalg.norm(z)) <= 10 * eps
+
+
+def test_blocked_elimination_of_wide_boxes(pkg):
+    """Boxes of 448 DOFs (depth 2 of the 32^3 octree at eps 1e-6, FP32
+    factor) are too wide for the shared-memory elimination: X_RR is formed
+    as tiles over many CTAs and its LU and inverse are blocked in one CTA
+    per box, with ragged last panels (r = 333..345).  The factor applies the
+    exact operator (FP64 direct sum) within 10 eps, and the FP64 refinement
+    it preconditions reaches 1e-10, the residual checked by the oracle's
+    direct sum on sampled rows."""
+    pts = inputs.grid_points(32, 3)
+    n = len(pts)
+    eps = 1e-6
+    f = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.MIXED)
+    st = f.stats()
+    assert st["b"].max() > 212
+    x = _cuda(inputs.rhs(97, n, 2))
+    ax = f.matvec(x)
+    err = float(torch.linalg.norm(f.apply(x).double() - ax) / torch.linalg.norm(ax))
+    assert err <= 10 * eps, err
+    b = inputs.rhs(98, n, 1)
+    z, iters, rel = f.solve_refined(_cuda(b), tol=1e-10, maxit=20)
+    assert rel <= 1e-10 and iters <= 5, (rel, iters)
+    z = z.cpu().numpy()
+    rows = (inputs.splitmix64(19, 48) % np.uint64(n)).astype(np.int64)
+    res = b[:, rows] - oracle.matvec(pts, 1, z, rows=rows)
+    assert np.abs(res).max() <= 1e-9 * np.abs(b).max()
