@@ -1717,9 +1717,11 @@ template <typename T> static void run_factor(Factor<T> &F) {
     double fl = 0;
     for (int tn : F.h_tn) fl += 2.0 / 3.0 * (double)tn * tn * tn;
     int pi = F.prof.begin(KC_TOPLU, st, 0, 0, 0, 2.0 * (double)F.h_loff[np] * sizeof(T), fl);
-    if (np == 1)
-      launch_dense_lu<T>(ptr<T>(F.d_topLU), F.ntop, ptr<int>(F.d_toppiv), st, ptr<int>(F.d_err));
-    else
+    DBuf d_panel;  // column-major copy of the current panel
+    if (np == 1) {
+      d_panel.alloc((size_t)F.ntop * 32 * sizeof(T), st, 1);
+      launch_dense_lu<T>(ptr<T>(F.d_topLU), F.ntop, ptr<int>(F.d_toppiv), ptr<T>(d_panel), st, ptr<int>(F.d_err));
+    } else
       launch_lu_batched<T>(ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_toff),
                            ptr<int>(F.d_tn), np, st, ptr<int>(F.d_err));
     check_launch("top lu");

@@ -109,7 +109,7 @@ template <typename T>
 void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_list, int nbox,
                   int njmax, const T *scratch, int64_t scratch_stride, cudaStream_t st);
 template <typename T>
-void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err);
+void launch_dense_lu(T *A, int n, int *piv, T *W, cudaStream_t st, int *err);
 
 // Sweeps over the factor (kernels.cu).  v: tree-order working vector,
 // layout v[g * nrhs + c].

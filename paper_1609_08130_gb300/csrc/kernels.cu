@@ -1981,9 +1981,8 @@ __device__ bool claim_storage(FBox<T> &fb, int nj, const Overflow<T> &ov, int *e
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, T *scratch,
-                                             int64_t sstride, int64_t ws_off, int use_smem, Overflow<T> ovf,
-                                             int *err, int C, int form_only) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                             int64_t sstride, int64_t ws_off, Overflow<T> ovf, int *err, int C,
+                                             int form_only) {
   __shared__ int s_ncode[27], s_ncell[27], s_nstart[28], s_nn;
   __shared__ int64_t s_off_in[27], s_off_out[27];
   __shared__ int s_ld_in[27];
@@ -2000,16 +1999,14 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
   const int ncode3 = dim == 3 ? 27 : 9;
   const int center = code3(0, 0, 0, dim);
 
-  // Ts (k x r, ld k), LU (r x r, ld r+1), loc (b ints), piv (r ints): in
-  // shared memory, or for large boxes in this box's global workspace, where
-  // T and loc are read from the box's records in place (every CTA of the box
-  // reads them; only CTA 0 writes the LU and pivots)
-  T *ws = use_smem ? reinterpret_cast<T *>(smem_raw) : scratch + (int64_t)q * sstride + ws_off;
+  // T (k x r, ld k) and loc (b ints) read from the box's records in place
+  // (every CTA of the box reads them); the LU (r x r, ld r+1) and the pivots
+  // (r ints) in this box's global workspace, written by CTA 0 only
+  T *LU = scratch + (int64_t)q * sstride + ws_off;
   const int ldl = r + 1;
-  const T *Ts = use_smem ? ws : fb.Tm;
-  T *LU = ws + (int64_t)k * r;
-  int *sloc = use_smem ? reinterpret_cast<int *>(LU + (int64_t)r * ldl) : fb.loc;
-  int *spiv = reinterpret_cast<int *>(LU + (int64_t)r * ldl) + b;
+  const T *Ts = fb.Tm;
+  const int *sloc = fb.loc;
+  int *spiv = reinterpret_cast<int *>(LU + (int64_t)r * ldl);
 
   if (tid == 0) {
     int nn = 0, acc = k;
@@ -2034,10 +2031,6 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
     s_nstart[nn] = acc;
     s_nn = nn;
     s_ok = (acc <= fb.njmax && cta == 0) ? claim_storage(fb, acc, ovf, err) : 1;  // acc > njmax: reported below
-  }
-  if (use_smem) {
-    for (int q2 = tid; q2 < b; q2 += NT) sloc[q2] = fb.loc[q2];
-    for (int e = tid; e < k * r; e += NT) ws[e] = fb.Tm[e];
   }
   __syncthreads();
   if (!s_ok) return;
@@ -2647,8 +2640,9 @@ template int64_t elim_smem_bytes<float>(int, int, int);
 template int64_t elim_smem_bytes<double>(int, int, int);
 
 // Elements of T the large-box elimination needs per box beyond X_JR / X_RJ.
+// k_elim's LU (r x (r+1)) and pivots, or k_elim_lu's X_RR (r x r), r <= bmax
 template <typename T> int64_t elim_ws_elems(int bmax) {
-  return (int64_t)bmax * bmax / 4 + (int64_t)bmax * (bmax + 1) + 2 * (int64_t)bmax + 64;
+  return (int64_t)bmax * (bmax + 1) + (int64_t)bmax + 64;
 }
 template int64_t elim_ws_elems<float>(int);
 template int64_t elim_ws_elems<double>(int);
@@ -3091,24 +3085,21 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
       return;
     }
   }
-  // worst case over k + r = b: k r <= b^2/4, r <= b
-  size_t smem = (size_t)bmax * bmax / 4 * sizeof(T) + (size_t)bmax * (bmax + 1) * sizeof(T) +
-                (size_t)2 * bmax * sizeof(int) + 64;
-  const bool use_smem = smem <= (size_t)(220 << 10) && !force_general;
   // the global workspace sits after the X_JR / X_RJ scratch of the box
   const int64_t ws_off = scratch_stride - elim_ws_elems<T>(bmax);
-  if (use_smem) cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int tiles_e = tn * tr;  // E: nj x r
   const int tiles_g = tr * tn;  // G: r x nj
-  if (!use_smem && !force_general) {
-    // wide boxes: X_JR and X_RJ over up to 64 CTAs per box, X_RR as tiles,
-    // the LU and X_RR^{-1} blocked in one 1024-thread CTA per box
+  if (!force_general) {
+    // boxes wider than k_elim2 takes: X_JR and X_RJ over up to 64 CTAs per
+    // box, X_RR as tiles, the LU and X_RR^{-1} blocked in one 1024-thread CTA
+    // per box (3D 32^3 grid: 83 -> 26 ms at eps 1e-3, b ~ 200, and
+    // 1063 -> 152 ms at eps 1e-6, b = 448, against k_elim)
     int nbp = sizeof(T) == 4 ? 32 : 16;
     while (nbp > 8 && elim_lu_smem<T>(bmax, nbp) > (size_t)(220 << 10)) nbp /= 2;
     const size_t lsm = elim_lu_smem<T>(bmax, nbp);
     if (lsm <= (size_t)(220 << 10)) {
       const int Cb = std::min(64, std::max(1, (1216 + nbox - 1) / nbox));
-      k_elim<T><<<nbox * Cb, NT, 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, 0, ovf, err, Cb, 1);
+      k_elim<T><<<nbox * Cb, NT, 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, ovf, err, Cb, 1);
       k_elim_xrr<T><<<dim3(nbox, tr * tr), NT, 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, tr);
       if (nbp == 8) {
         cudaFuncSetAttribute(k_elim_lu<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
@@ -3126,10 +3117,11 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
       return;
     }
   }
-  // several CTAs per box for small phases
+  // one CTA per box, everything in k_elim (the forced large-box path, kept
+  // as the plain form the other paths are checked against, and boxes too
+  // wide for k_elim_lu's shared memory)
   const int Cg = force_general ? 1 : std::min(8, std::max(1, (300 + nbox - 1) / nbox));
-  k_elim<T><<<nbox * Cg, NT, use_smem ? smem : 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off,
-                                                         use_smem ? 1 : 0, ovf, err, Cg, 0);
+  k_elim<T><<<nbox * Cg, NT, 0, st>>>(lv, boxes, box_list, scratch, scratch_stride, ws_off, ovf, err, Cg, 0);
   // E and G: tiles of 64 x 64 over nj x r (E) and r x nj (G), nj <= njmax, r <= bmax
   k_elim_gemm<T><<<dim3(nbox, tiles_e + tiles_g), NT, 0, st>>>(boxes, box_list, scratch, scratch_stride, tiles_e,
                                                               tr, tn);
@@ -3248,30 +3240,35 @@ void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_li
 
 constexpr int LB = 32;
 
+// Panel of nb <= LB columns at kb (rows kb..n-1), factored with partial
+// pivoting (largest |entry|, ties to the lowest row) in a column-major copy W,
+// so that the argmax, the scaling and the rank-1 updates read consecutive
+// addresses; the panel's row interchanges are then applied to the other
+// columns of A and to the permutation.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, int *err) {
+__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, T *W, int *err) {
   __shared__ T s_val[32];
   __shared__ int s_idx[32];
+  __shared__ int s_swp[LB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x / 32;
-  for (int j = kb; j < kb + nb; j++) {
+  const int h = n - kb;  // panel rows kb..n-1; W column-major, ld h
+  for (int e = tid; e < h * nb; e += blockDim.x) {
+    const int i = e / nb, jj = e % nb;
+    W[(int64_t)jj * h + i] = A[(int64_t)(kb + i) * n + kb + jj];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nb; jj++) {
+    T *wc = W + (int64_t)jj * h;
     T best = (T)-1;
-    int bi = n;
-    for (int i = j + tid; i < n; i += blockDim.x) {
-      T v = fabs(A[(int64_t)i * n + j]);
+    int bi = h;
+    for (int i = jj + tid; i < h; i += blockDim.x) {
+      const T v = fabs(wc[i]);
       if (v > best) {
         best = v;
         bi = i;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
+    warp_argmax(best, bi);
     if (lane == 0) {
       s_val[warp] = best;
       s_idx[warp] = bi;
@@ -3279,47 +3276,59 @@ __global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, 
     __syncthreads();
     if (warp == 0) {
       best = lane < nwarp ? s_val[lane] : (T)-1;
-      bi = lane < nwarp ? s_idx[lane] : n;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) {
-          best = ov;
-          bi = oi;
-        }
-      }
+      bi = lane < nwarp ? s_idx[lane] : h;
+      warp_argmax(best, bi);
       if (lane == 0) {
-        if (bi >= n) {
-          bi = j;
+        if (bi >= h) {  // NaN column: keep the diagonal, report
+          bi = jj;
           set_err(err, DERR_NUMERIC);
         }
-        s_idx[0] = bi;
         if (best == (T)0) set_err(err, DERR_NUMERIC);
+        s_idx[0] = bi;
+        s_swp[jj] = bi;
       }
     }
     __syncthreads();
     const int p = s_idx[0];
-    if (p != j) {
-      for (int cc = tid; cc < n; cc += blockDim.x) {
-        T t0 = A[(int64_t)j * n + cc];
-        A[(int64_t)j * n + cc] = A[(int64_t)p * n + cc];
-        A[(int64_t)p * n + cc] = t0;
+    if (p != jj) {
+      if (tid < nb) {
+        const T t0 = W[(int64_t)tid * h + jj];
+        W[(int64_t)tid * h + jj] = W[(int64_t)tid * h + p];
+        W[(int64_t)tid * h + p] = t0;
       }
-      if (tid == 0) {
-        int tp = piv[j];
-        piv[j] = piv[p];
-        piv[p] = tp;
-      }
+      __syncthreads();
+    }
+    const T d = wc[jj];
+    for (int i = jj + 1 + tid; i < h; i += blockDim.x) wc[i] /= d;
+    __syncthreads();
+    const int rows = h - jj - 1, cols = nb - jj - 1;
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+      const int i = jj + 1 + e % rows, cc = jj + 1 + e / rows;
+      W[(int64_t)cc * h + i] -= wc[i] * W[(int64_t)cc * h + jj];
     }
     __syncthreads();
-    const T d = A[(int64_t)j * n + j];
-    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
-      T l = A[(int64_t)i * n + j] / d;
-      A[(int64_t)i * n + j] = l;
-      for (int cc = j + 1; cc < kb + nb; cc++) A[(int64_t)i * n + cc] -= l * A[(int64_t)j * n + cc];
+  }
+  for (int e = tid; e < h * nb; e += blockDim.x) {
+    const int i = e / nb, jj = e % nb;
+    A[(int64_t)(kb + i) * n + kb + jj] = W[(int64_t)jj * h + i];
+  }
+  // the panel's row interchanges, in order, on the columns outside it (each
+  // thread keeps its columns for every interchange) and on the permutation
+  for (int jj = 0; jj < nb; jj++) {
+    const int p = s_swp[jj];
+    if (p == jj) continue;
+    T *rj = A + (int64_t)(kb + jj) * n, *rp = A + (int64_t)(kb + p) * n;
+    for (int cc = tid; cc < n; cc += blockDim.x) {
+      if (cc >= kb && cc < kb + nb) continue;
+      const T t0 = rj[cc];
+      rj[cc] = rp[cc];
+      rp[cc] = t0;
     }
-    __syncthreads();
+    if (tid == 0) {
+      const int tp = piv[kb + jj];
+      piv[kb + jj] = piv[kb + p];
+      piv[kb + p] = tp;
+    }
   }
 }
 
@@ -3372,12 +3381,12 @@ template <typename T> __global__ void k_iota(int *p, int n) {
   if (i < n) p[i] = i;
 }
 
-template <typename T> void launch_dense_lu(T *A, int n, int *piv, cudaStream_t st, int *err) {
+template <typename T> void launch_dense_lu(T *A, int n, int *piv, T *W, cudaStream_t st, int *err) {
   if (n <= 0) return;
   k_iota<T><<<(n + 255) / 256, 256, 0, st>>>(piv, n); count_launch();
   for (int kb = 0; kb < n; kb += LB) {
     int nb = min(LB, n - kb);
-    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, err); count_launch();
+    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, W, err); count_launch();
     int rem = n - kb - nb;
     if (rem > 0) {
       k_lu_trsm<T><<<(rem + 127) / 128, 128, 0, st>>>(A, n, kb, nb); count_launch();
@@ -4045,7 +4054,7 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
                                const Overflow<T> &, cudaStream_t, int *, int);                                \
   template void launch_schur<T>(const LevelDev<T> &, const FBox<T> *, const int *, int, int, const T *, int64_t, \
                                 cudaStream_t);                                                                \
-  template void launch_dense_lu<T>(T *, int, int *, cudaStream_t, int *);                                     \
+  template void launch_dense_lu<T>(T *, int, int *, T *, cudaStream_t, int *);                                     \
   template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t);            \
   template void launch_sweep_chunks<T>(int, const FBox<T> *, const int *, const int *, int, T *, int, int, int *, \
                                        T *, const int64_t *, cudaStream_t);                                  \
