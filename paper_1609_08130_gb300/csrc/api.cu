@@ -1576,11 +1576,11 @@ template <typename T> static void run_factor(Factor<T> &F) {
     int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32 + elim_ws_elems<T>(H.bmax);
     grow(gel, (size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
     // the multi-CTA ID's triangle slots (8 CTAs per box of the largest
-    // phase) and tree-node counters
+    // phase, 16 for boxes wider than 256) and tree-node counters
     IdMultiScratch ims{};
     if (H.bmax <= 512 && !large) {
       const int64_t se = H.bmax <= 64 ? 64 * 65 : H.bmax <= 128 ? 128 * 129 : (int64_t)H.bmax * (H.bmax + 1);
-      const int64_t slots = 8 * (int64_t)std::max(maxphase, 1);
+      const int64_t slots = (H.bmax > 256 ? 16 : 8) * (int64_t)std::max(maxphase, 1);
       grow(gtri, (size_t)(slots * se) * sizeof(T), st, 1);
       grow(gcnt, sizeof(int) * (size_t)slots * 8, st, 1);
       CK(cudaMemsetAsync(gcnt.p, 0, sizeof(int) * (size_t)slots * 8, st));
@@ -1719,7 +1719,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     int pi = F.prof.begin(KC_TOPLU, st, 0, 0, 0, 2.0 * (double)F.h_loff[np] * sizeof(T), fl);
     DBuf d_panel;  // column-major copy of the current panel
     if (np == 1) {
-      d_panel.alloc((size_t)F.ntop * 32 * sizeof(T), st, 1);
+      d_panel.alloc((size_t)F.ntop * 32 * sizeof(T) + 32 * sizeof(int), st, 1);  // + the interchanges
       launch_dense_lu<T>(ptr<T>(F.d_topLU), F.ntop, ptr<int>(F.d_toppiv), ptr<T>(d_panel), st, ptr<int>(F.d_err));
     } else
       launch_lu_batched<T>(ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_toff),

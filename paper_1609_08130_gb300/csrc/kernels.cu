@@ -1922,7 +1922,7 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   if (bmax <= 512 && !force_general) {
     // boxes too wide for a shared-memory triangle: several CTAs per box
     // with their triangles in global (L2-resident) slots
-    const int C = (id_groups_hint >> 8) > 1 ? (id_groups_hint >> 8) : 8;
+    const int C = (id_groups_hint >> 8) > 1 ? (id_groups_hint >> 8) : 16;  // 8: 904 ms, 16: 827 ms (3D 32^3, 1e-6)
     if (id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots &&
         (int64_t)bmax * (bmax + 1) <= id_multi.slot_elems &&
         idm_smem<T, 512, 1, true>(bmax, mmax) <= (size_t)(220 << 10)) {
@@ -3243,13 +3243,16 @@ constexpr int LB = 32;
 // Panel of nb <= LB columns at kb (rows kb..n-1), factored with partial
 // pivoting (largest |entry|, ties to the lowest row) in a column-major copy W,
 // so that the argmax, the scaling and the rank-1 updates read consecutive
-// addresses; the panel's row interchanges are then applied to the other
-// columns of A and to the permutation.
+// addresses; each thread loads all of a row's panel entries before it
+// updates them.  The row interchanges go to swp (local rows) and to the
+// permutation; k_lu_trsm applies them to the other columns.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, T *W, int *err) {
+__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, T *W, int *swp,
+                                                   int *err) {
+  constexpr int CH = sizeof(T) == 4 ? 16 : 8;  // panel entries a thread holds at once
   __shared__ T s_val[32];
   __shared__ int s_idx[32];
-  __shared__ int s_swp[LB];
+  __shared__ T s_prow[LB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x / 32;
   const int h = n - kb;  // panel rows kb..n-1; W column-major, ld h
   for (int e = tid; e < h * nb; e += blockDim.x) {
@@ -3285,26 +3288,37 @@ __global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, 
         }
         if (best == (T)0) set_err(err, DERR_NUMERIC);
         s_idx[0] = bi;
-        s_swp[jj] = bi;
+        swp[jj] = bi;
+        const int tp = piv[kb + jj];
+        piv[kb + jj] = piv[kb + bi];
+        piv[kb + bi] = tp;
       }
     }
     __syncthreads();
     const int p = s_idx[0];
-    if (p != jj) {
-      if (tid < nb) {
-        const T t0 = W[(int64_t)tid * h + jj];
-        W[(int64_t)tid * h + jj] = W[(int64_t)tid * h + p];
-        W[(int64_t)tid * h + p] = t0;
+    if (tid < nb) {  // interchange rows jj and p of the panel; keep row jj
+      const T vj = W[(int64_t)tid * h + jj], vp = W[(int64_t)tid * h + p];
+      if (p != jj) {
+        W[(int64_t)tid * h + jj] = vp;
+        W[(int64_t)tid * h + p] = vj;
       }
-      __syncthreads();
+      s_prow[tid] = p != jj ? vp : vj;
     }
-    const T d = wc[jj];
-    for (int i = jj + 1 + tid; i < h; i += blockDim.x) wc[i] /= d;
     __syncthreads();
-    const int rows = h - jj - 1, cols = nb - jj - 1;
-    for (int e = tid; e < rows * cols; e += blockDim.x) {
-      const int i = jj + 1 + e % rows, cc = jj + 1 + e / rows;
-      W[(int64_t)cc * h + i] -= wc[i] * W[(int64_t)cc * h + jj];
+    const T d = s_prow[jj];
+    for (int i = jj + 1 + tid; i < h; i += blockDim.x) {
+      const T l = wc[i] / d;
+      wc[i] = l;
+      T *wi = W + i;  // row i of the panel: wi[c * h], c < LB (n * LB < 2^31)
+      for (int c0 = jj + 1; c0 < nb; c0 += CH) {
+        T v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; u++)
+          if (c0 + u < nb) v[u] = wi[(c0 + u) * h];
+#pragma unroll
+        for (int u = 0; u < CH; u++)
+          if (c0 + u < nb) wi[(c0 + u) * h] = v[u] - l * s_prow[c0 + u];
+      }
     }
     __syncthreads();
   }
@@ -3312,30 +3326,22 @@ __global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, 
     const int i = e / nb, jj = e % nb;
     A[(int64_t)(kb + i) * n + kb + jj] = W[(int64_t)jj * h + i];
   }
-  // the panel's row interchanges, in order, on the columns outside it (each
-  // thread keeps its columns for every interchange) and on the permutation
-  for (int jj = 0; jj < nb; jj++) {
-    const int p = s_swp[jj];
-    if (p == jj) continue;
-    T *rj = A + (int64_t)(kb + jj) * n, *rp = A + (int64_t)(kb + p) * n;
-    for (int cc = tid; cc < n; cc += blockDim.x) {
-      if (cc >= kb && cc < kb + nb) continue;
-      const T t0 = rj[cc];
-      rj[cc] = rp[cc];
-      rp[cc] = t0;
-    }
-    if (tid == 0) {
-      const int tp = piv[kb + jj];
-      piv[kb + jj] = piv[kb + p];
-      piv[kb + p] = tp;
-    }
-  }
 }
 
-// U12 = L11^{-1} A12 for the columns right of the panel (one thread per column)
-template <typename T> __global__ void k_lu_trsm(T *A, int n, int kb, int nb) {
-  int cc = kb + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (cc >= n) return;
+// The panel's row interchanges (swp, in order) on every column outside it,
+// then U12 = L11^{-1} A12 for the columns right of it; one thread per column
+template <typename T> __global__ void k_lu_trsm(T *A, int n, int kb, int nb, const int *swp) {
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc >= n || (cc >= kb && cc < kb + nb)) return;
+  for (int jj = 0; jj < nb; jj++) {
+    const int p = swp[jj];
+    if (p != jj) {
+      const T t0 = A[(int64_t)(kb + jj) * n + cc];
+      A[(int64_t)(kb + jj) * n + cc] = A[(int64_t)(kb + p) * n + cc];
+      A[(int64_t)(kb + p) * n + cc] = t0;
+    }
+  }
+  if (cc < kb) return;
   for (int i = kb; i < kb + nb; i++) {
     T s = A[(int64_t)i * n + cc];
     for (int l = kb; l < i; l++) s -= A[(int64_t)i * n + l] * A[(int64_t)l * n + cc];
@@ -3386,10 +3392,13 @@ template <typename T> void launch_dense_lu(T *A, int n, int *piv, T *W, cudaStre
   k_iota<T><<<(n + 255) / 256, 256, 0, st>>>(piv, n); count_launch();
   for (int kb = 0; kb < n; kb += LB) {
     int nb = min(LB, n - kb);
-    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, W, err); count_launch();
+    int *swp = reinterpret_cast<int *>(W + (int64_t)n * LB);
+    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, W, swp, err); count_launch();
     int rem = n - kb - nb;
+    if (rem > 0 || kb > 0) {
+      k_lu_trsm<T><<<(n + 127) / 128, 128, 0, st>>>(A, n, kb, nb, swp); count_launch();
+    }
     if (rem > 0) {
-      k_lu_trsm<T><<<(rem + 127) / 128, 128, 0, st>>>(A, n, kb, nb); count_launch();
       dim3 g((rem + 63) / 64, (rem + 63) / 64);
       k_lu_gemm<T><<<g, NT, 0, st>>>(A, n, kb, nb); count_launch();
     }
