@@ -101,6 +101,9 @@ def workload(name: str) -> dict:
     if name == "laplace2d_grid64":            # 64x64 grid, N = 4096
         pts = grid_points(64, 2)
         return dict(name=name, pts=pts, dim=2, kind=0, eps=1e-6, leaf=64, rhs_seeds=[1])
+    if name == "laplace2d_grid256":           # 256x256 grid, N = 65536 (profiling size)
+        pts = grid_points(256, 2)
+        return dict(name=name, pts=pts, dim=2, kind=0, eps=1e-6, leaf=64, rhs_seeds=[1, 2, 3, 4])
     if name == "laplace2d_grid512":           # 512x512 grid, N = 262144
         pts = grid_points(512, 2)
         return dict(name=name, pts=pts, dim=2, kind=0, eps=1e-6, leaf=64, rhs_seeds=[1, 2, 3, 4])
