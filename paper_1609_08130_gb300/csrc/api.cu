@@ -1572,7 +1572,16 @@ template <typename T> static void run_factor(Factor<T> &F) {
     int64_t idb = id_region_bytes<T>(H.bmax, PR);
     bool id_smem = idb <= 200 * 1024 && !large;
     int64_t id_stride = (idb + sizeof(T) - 1) / sizeof(T) + 32;
-    if (!id_smem) grow(gid, (size_t)id_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
+    // boxes wider than 512 (3D upper levels at small eps): the general ID
+    // over up to 32 CTAs per box (about two CTAs per SM over the largest
+    // phase), each with its own workspace, at most 8 GB of them
+    int kid_ctas = 1;
+    if (H.bmax > 512 && !id_smem && !large) {
+      const int mp = std::max(maxphase, 1);
+      kid_ctas = std::min(32, (304 + mp - 1) / mp);
+      while (kid_ctas > 1 && (double)id_stride * sizeof(T) * mp * kid_ctas > 8e9) kid_ctas /= 2;
+    }
+    if (!id_smem) grow(gid, (size_t)id_stride * sizeof(T) * std::max(maxphase, 1) * kid_ctas, st, 1);
     int64_t el_stride = 2 * (int64_t)njmax_lvl * H.bmax + 32 + elim_ws_elems<T>(H.bmax);
     grow(gel, (size_t)el_stride * sizeof(T) * std::max(maxphase, 1), st, 1);
     // the multi-CTA ID's triangle slots (8 CTAs per box of the largest
@@ -1585,6 +1594,11 @@ template <typename T> static void run_factor(Factor<T> &F) {
       grow(gcnt, sizeof(int) * (size_t)slots * 8, st, 1);
       CK(cudaMemsetAsync(gcnt.p, 0, sizeof(int) * (size_t)slots * 8, st));
       ims = IdMultiScratch{gtri.p, se, slots, ptr<int>(gcnt)};
+    } else if (kid_ctas > 1) {
+      const int64_t slots = (int64_t)kid_ctas * std::max(maxphase, 1);
+      grow(gcnt, sizeof(int) * (size_t)slots * 8, st, 1);
+      CK(cudaMemsetAsync(gcnt.p, 0, sizeof(int) * (size_t)slots * 8, st));
+      ims = IdMultiScratch{nullptr, 0, slots, ptr<int>(gcnt), kid_ctas};
     }
     set_id_multi(ims);
     F.prof.host(KC_HOST_LEVEL, now_ms() - th0);

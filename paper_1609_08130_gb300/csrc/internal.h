@@ -94,12 +94,15 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
 // threads per column << 4 | fold groups per box (0: default).
 void set_id_groups(int G);
 // Scratch of the multi-CTA ID: triangle slots (slot_elems elements each,
-// max_slots of them) and tree-node counters (8 x slots ints, zero between
-// launches).
+// max_slots of them; none for boxes wider than 512) and tree-node counters
+// (8 x max_slots ints, zero between launches).  kid_ctas: CTAs per box of
+// the general kernel k_id (its workspaces are the level's ID scratch, which
+// then holds kid_ctas of them per box).
 struct IdMultiScratch {
   void *tri = nullptr;
   int64_t slot_elems = 0, max_slots = 0;
   int *cnt = nullptr;
+  int kid_ctas = 0;
 };
 void set_id_multi(const IdMultiScratch &m);
 template <typename T>

@@ -142,14 +142,20 @@ template <typename T> struct IdLayout {
 template <typename T>
 __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, Points P,
                                            KernelParams K, ProxyParams px, double eps, int PR, T *gscr,
-                                           int64_t gstride, int use_smem, int *err) {
+                                           int64_t gstride, int use_smem, int C, int *cnt, int *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ocell[125], s_obase[126], s_ono;
   __shared__ int64_t s_rowsrc[256];
   __shared__ T s_r11;
-  __shared__ int s_stop, s_piv, s_k;
+  __shared__ int s_stop, s_piv, s_k, s_second;
 
-  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  // C CTAs per box (global workspaces only): CTA `chunk` folds panels
+  // chunk, chunk + C, ... of the ID matrix into the triangle of its own
+  // workspace; the triangles are merged up a binary tree (at each node the
+  // second CTA to arrive, told by a counter, folds the right triangle into
+  // the left one) and the CTA left at the root pivots.
+  const int bq = blockIdx.x / C, chunk = blockIdx.x % C;
+  FBox<T> &fb = boxes[box_list[bq]];
   const int c = fb.cell, b = fb.b, dim = lv.dim;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
   IdLayout<T> lay(b, PR);
@@ -194,7 +200,43 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   double ctr[3];
   for (int d = 0; d < 3; d++) ctr[d] = (lv.cell_coord[3 * c + d] + 0.5) * D;
 
-  for (int p0 = 0; p0 < m; p0 += PR) {
+  // [R; panel] -> R, one Householder reflector per column from column j0 on
+  // (the panel's entries left of j0 are zero)
+  auto fold_panel = [&](int rows, int j0) {
+    for (int j = j0; j < b; j++) {
+      const T *pj = pan + (int64_t)j * ldp;
+      T s = (T)0;
+      for (int i = lane; i < rows; i += 32) s += pj[i] * pj[i];
+      s = warp_sum(s);
+      if (s > (T)0) {
+        T x0 = R[j + (int64_t)j * ldr];
+        T nrm2 = sqrt(x0 * x0 + s);
+        T beta = x0 >= (T)0 ? -nrm2 : nrm2;
+        T tau = (beta - x0) / beta;
+        T scl = (T)1 / (x0 - beta);
+        for (int cc = j + 1 + warp; cc < b; cc += nwarp) {
+          T *pc = pan + (int64_t)cc * ldp;
+          T d = (T)0;
+          for (int i = lane; i < rows; i += 32) d += pj[i] * pc[i];
+          d = warp_sum(d);
+          T wv = R[j + (int64_t)cc * ldr] + scl * d;
+          T f = tau * wv;
+          T fs = f * scl;
+          for (int i = lane; i < rows; i += 32) pc[i] -= fs * pj[i];
+          if (lane == 0) R[j + (int64_t)cc * ldr] -= f;
+        }
+      }
+      __syncthreads();
+      // every warp has read x0 = R_jj; now it may be replaced by beta
+      if (s > (T)0 && tid == 0) {
+        T x0 = R[j + (int64_t)j * ldr];
+        T nrm2 = sqrt(x0 * x0 + s);
+        R[j + (int64_t)j * ldr] = x0 >= (T)0 ? -nrm2 : nrm2;
+      }
+    }
+    __syncthreads();
+  };
+  for (int p0 = chunk * PR; p0 < m; p0 += C * PR) {
     const int rows = min(PR, m - p0);
     // row sources of this panel
     for (int rr = tid; rr < rows; rr += NT) {
@@ -252,39 +294,35 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
       pan[rr + (int64_t)q * ldp] = (T)0;
     }
     __syncthreads();
-    // [R; panel] -> R, one Householder reflector per column
-    for (int j = 0; j < b; j++) {
-      const T *pj = pan + (int64_t)j * ldp;
-      T s = (T)0;
-      for (int i = lane; i < rows; i += 32) s += pj[i] * pj[i];
-      s = warp_sum(s);
-      if (s > (T)0) {
-        T x0 = R[j + (int64_t)j * ldr];
-        T nrm2 = sqrt(x0 * x0 + s);
-        T beta = x0 >= (T)0 ? -nrm2 : nrm2;
-        T tau = (beta - x0) / beta;
-        T scl = (T)1 / (x0 - beta);
-        for (int cc = j + 1 + warp; cc < b; cc += nwarp) {
-          T *pc = pan + (int64_t)cc * ldp;
-          T d = (T)0;
-          for (int i = lane; i < rows; i += 32) d += pj[i] * pc[i];
-          d = warp_sum(d);
-          T wv = R[j + (int64_t)cc * ldr] + scl * d;
-          T f = tau * wv;
-          T fs = f * scl;
-          for (int i = lane; i < rows; i += 32) pc[i] -= fs * pj[i];
-          if (lane == 0) R[j + (int64_t)cc * ldr] -= f;
-        }
-      }
-      __syncthreads();
-      // every warp has read x0 = R_jj; now it may be replaced by beta
-      if (s > (T)0 && tid == 0) {
-        T x0 = R[j + (int64_t)j * ldr];
-        T nrm2 = sqrt(x0 * x0 + s);
-        R[j + (int64_t)j * ldr] = x0 >= (T)0 ? -nrm2 : nrm2;
-      }
+    fold_panel(rows, 0);
+  }
+  int cur = chunk;  // first workspace of the subtree this CTA carries
+  for (int L = 1; L < C; L <<= 1) {
+    const int ls = cur & ~(2 * L - 1), rs = ls + L;
+    if (rs >= C) continue;  // no right partner at this level: carry the subtree up
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      int *node = cnt + ((int64_t)bq * 8 + (31 - __clz(L))) * C + ls;
+      const int seen = atomicAdd(node, 1);
+      s_second = seen == 1;
+      if (seen == 1) *node = 0;  // reset for the next launch
     }
     __syncthreads();
+    if (!s_second) return;
+    __threadfence();
+    if (cur != ls) R = gscr + ((int64_t)bq * C + ls) * gstride + lay.oR;  // continue on the left triangle
+    const T *Rr = gscr + ((int64_t)bq * C + rs) * gstride + lay.oR;
+    for (int p0 = 0; p0 < b; p0 += PR) {  // rows p0.. of the right triangle are zero left of column p0
+      const int rows = min(PR, b - p0);
+      for (int e = tid; e < PR * b; e += NT) {
+        const int rr = e % PR, q = e / PR;
+        pan[rr + (int64_t)q * ldp] = rr < rows ? __ldcg(Rr + (p0 + rr) + (int64_t)q * ldr) : (T)0;
+      }
+      __syncthreads();
+      fold_panel(rows, p0);
+    }
+    cur = ls;
   }
 
   // Greedy column-pivoted QR of the b x b triangle (Definition 2.1 and the
@@ -1936,8 +1974,14 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   size_t smem = use_smem ? (size_t)lay.bytes : 0;
   if (use_smem)
     cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_id<T><<<nbox, NT, smem, st>>>(lv, boxes, box_list, P, K, px, eps, PR, gscratch, gscratch_stride,
-                                  use_smem ? 1 : 0, err); count_launch();
+  // several CTAs per box (workspaces in global memory, the level's
+  // scratch holding C of them per box), one for the forced large-box path
+  int C = 1;
+  if (!use_smem && !force_general && id_multi.kid_ctas > 1 && id_multi.cnt &&
+      (int64_t)nbox * id_multi.kid_ctas <= id_multi.max_slots)
+    C = id_multi.kid_ctas;
+  k_id<T><<<nbox * C, NT, smem, st>>>(lv, boxes, box_list, P, K, px, eps, PR, gscratch, gscratch_stride,
+                                      use_smem ? 1 : 0, C, id_multi.cnt, err); count_launch();
 }
 
 template <typename T> int64_t id_region_bytes(int b, int PR) { return IdLayout<T>(b, PR).bytes; }

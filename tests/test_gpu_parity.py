@@ -475,3 +475,23 @@ def test_blocked_elimination_of_wide_boxes(pkg):
     rows = (inputs.splitmix64(19, 48) % np.uint64(n)).astype(np.int64)
     res = b[:, rows] - oracle.matvec(pts, 1, z, rows=rows)
     assert np.abs(res).max() <= 1e-9 * np.abs(b).max()
+
+
+def test_general_id_over_several_ctas(pkg):
+    """Boxes wider than 512 (2D random points, leaf 600: leaves of ~520-600
+    DOFs at depth 3) take the general ID kernel over several CTAs per box,
+    each folding a share of the ID matrix's panels into its own triangle,
+    merged up a tree.  FP64: apply and solve within 10 eps of the exact
+    operator (FP64 direct sum), and the solve within 10 eps of the forced
+    one-CTA-per-box path."""
+    pts = inputs.random_points(41, 36000, 2)
+    eps = 1e-6
+    f = pkg.Factorization(_cuda(pts), 0, eps, leaf=600, prec=pkg.FP64)
+    assert f.stats()["b"].max() > 512
+    x = _cuda(inputs.rhs(99, len(pts), 2))
+    ax = f.matvec(x)
+    assert float(torch.linalg.norm(f.apply(x) - ax) / torch.linalg.norm(ax)) <= 10 * eps
+    z = f.solve(x)
+    assert float(torch.linalg.norm(f.matvec(z) - x) / torch.linalg.norm(x)) <= 10 * eps
+    g = pkg.Factorization(_cuda(pts), 0, eps, leaf=600, prec=pkg.FP64, flags=pkg.rss.FLAG_LARGE_BOX_PATH)
+    assert float(torch.linalg.norm(g.solve(x) - z) / torch.linalg.norm(z)) <= 10 * eps
