@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ocell[125], s_obase[126], s_ono;
   __shared__ int64_t s_rowsrc[256];
-  __shared__ T s_r11;
+  __shared__ T s_r11, s_hh[3];
   __shared__ int s_stop, s_piv, s_k, s_second;
 
   // C CTAs per box (global workspaces only): CTA `chunk` folds panels
@@ -161,7 +161,9 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   IdLayout<T> lay(b, PR);
   T *base = use_smem ? reinterpret_cast<T *>(smem_raw) : gscr + (int64_t)blockIdx.x * gstride;
   T *R = base + lay.oR;
-  T *pan = base + lay.oP;
+  // the panel: in this CTA's workspace, or with several CTAs per box in
+  // shared memory (PR x b, the launch sizes PR to fit)
+  T *pan = C > 1 ? reinterpret_cast<T *>(smem_raw) : base + lay.oP;
   T *nrm = base + lay.oN;
   int *perm = reinterpret_cast<int *>(base + lay.oPerm);
   const int ldr = lay.ldr, ldp = lay.ldp;
@@ -201,8 +203,57 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   for (int d = 0; d < 3; d++) ctr[d] = (lv.cell_coord[3 * c + d] + 0.5) * D;
 
   // [R; panel] -> R, one Householder reflector per column from column j0 on
-  // (the panel's entries left of j0 are zero)
+  // (the panel's entries left of j0 are zero).  Several CTAs per box: warp 0
+  // forms reflector j, then each thread updates its columns of the panel
+  // (shared memory, lanes on consecutive columns) and of row j of R.  One
+  // CTA per box: each warp updates its columns with warp-wide dot products.
   auto fold_panel = [&](int rows, int j0) {
+    if (C > 1) {
+      for (int j = j0; j < b; j++) {
+        const T *pj = pan + (int64_t)j * ldp;
+        if (warp == 0) {
+          T s = (T)0;
+          for (int i = lane; i < rows; i += 32) s += pj[i] * pj[i];
+          s = warp_sum(s);
+          if (lane == 0) {
+            if (s > (T)0) {
+              const T x0 = R[j + (int64_t)j * ldr];
+              const T nrm2 = sqrt(x0 * x0 + s);
+              const T beta = x0 >= (T)0 ? -nrm2 : nrm2;
+              s_hh[0] = (beta - x0) / beta;
+              s_hh[1] = (T)1 / (x0 - beta);
+              s_hh[2] = (T)1;
+              R[j + (int64_t)j * ldr] = beta;  // no other thread reads R_jj
+            } else {
+              s_hh[2] = (T)0;
+            }
+          }
+        }
+        __syncthreads();
+        if (s_hh[2] != (T)0) {
+          const T tau = s_hh[0], scl = s_hh[1];
+          for (int cc = j + 1 + tid; cc < b; cc += NT) {
+            T *pc = pan + (int64_t)cc * ldp;
+            const T rj = R[j + (int64_t)cc * ldr];
+            T d0 = (T)0, d1 = (T)0, d2 = (T)0, d3 = (T)0;
+            int i = 0;
+            for (; i + 3 < rows; i += 4) {
+              d0 += pj[i] * pc[i];
+              d1 += pj[i + 1] * pc[i + 1];
+              d2 += pj[i + 2] * pc[i + 2];
+              d3 += pj[i + 3] * pc[i + 3];
+            }
+            for (; i < rows; i++) d0 += pj[i] * pc[i];
+            const T f = tau * (rj + scl * ((d0 + d1) + (d2 + d3)));
+            const T fs = f * scl;
+            for (i = 0; i < rows; i++) pc[i] -= fs * pj[i];
+            R[j + (int64_t)cc * ldr] = rj - f;
+          }
+        }
+        __syncthreads();
+      }
+      return;
+    }
     for (int j = j0; j < b; j++) {
       const T *pj = pan + (int64_t)j * ldp;
       T s = (T)0;
@@ -1980,6 +2031,18 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   if (!use_smem && !force_general && id_multi.kid_ctas > 1 && id_multi.cnt &&
       (int64_t)nbox * id_multi.kid_ctas <= id_multi.max_slots)
     C = id_multi.kid_ctas;
+  if (C > 1) {  // the panel in shared memory: PR rows (ld PR + 1) x bmax columns
+    PR = sizeof(T) == 4 ? 32 : 16;
+    while (PR > 8 && (size_t)(PR + 1) * bmax * sizeof(T) > (size_t)(200 << 10)) PR /= 2;
+    smem = (size_t)(PR + 1) * bmax * sizeof(T) + 16;
+    if (smem > (size_t)(220 << 10)) {  // too wide even for 8-row panels: one CTA per box
+      C = 1;
+      PR = bmax <= 80 ? 128 : 64;
+      smem = 0;
+    } else {
+      cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+  }
   k_id<T><<<nbox * C, NT, smem, st>>>(lv, boxes, box_list, P, K, px, eps, PR, gscratch, gscratch_stride,
                                       use_smem ? 1 : 0, C, id_multi.cnt, err); count_launch();
 }
