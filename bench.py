@@ -182,8 +182,8 @@ def run_reference(args, rank, world):
 # capture of the full-size default workload (profiles/id_dram_laplace2d_grid512.md),
 # valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    "id": {"bytes_per_launch": 21.26e6,
-           "kernels_sha256": "87bb4cd0b585426b6de2faa6ccaf7c3070263972981521afb97346793c492d22"},
+    "id": {"bytes_per_launch": 21.34e6,
+           "kernels_sha256": "531ee677391e5cd9fc08f94155cb727cc3224f12ce19566ce7780cf3bd0731fd"},
 }
 
 
