@@ -988,10 +988,12 @@ template <> __device__ __forceinline__ void load_vec<double, 16>(double (&v)[16]
 // one vector load, a dot product and an update of its own column.
 template <typename T, int PR>
 __device__ __forceinline__ void fold_group(T (&pan)[PR], T *R, int ldr, int b, int col, T *vbuf, int bar_id,
-                                           int nthr) {
+                                           int nthr, int j0 = 0) {
   constexpr int VS = PR + 4;
-  if (col == 0 && b > 0) publish_reflector<T, PR>(vbuf, pan, R[0]);
-  for (int j = 0; j < b; j++) {
+  // j0 > 0: the panel is zero left of column j0 (rows j0.. of a triangle),
+  // so the reflectors of the columns before it would change nothing
+  if (col == j0 && j0 < b) publish_reflector<T, PR>(vbuf + (j0 & 1) * VS, pan, R[j0 * ldr + j0]);
+  for (int j = j0; j < b; j++) {
     group_bar(bar_id, nthr);
     const T *vb = vbuf + (j & 1) * VS;
     T *vn = vbuf + ((j + 1) & 1) * VS;
@@ -1147,7 +1149,7 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
         T pan[PR];
 #pragma unroll
         for (int i = 0; i < PR; i++) pan[i] = (p0 + i < b && col < b) ? Ro[(p0 + i) * LDR + col] : (T)0;
-        fold_group<T, PR>(pan, Rg, LDR, b, col, vbuf, bar_id, NC);
+        fold_group<T, PR>(pan, Rg, LDR, b, col, vbuf, bar_id, NC, p0);
       }
     }
   }
@@ -1352,10 +1354,11 @@ __device__ __forceinline__ void publish_part(T *dst, const T (&pan)[PR / TPC], T
 
 template <typename T, int PR, int TPC>
 __device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, int b, int col, int part, T *vbuf,
-                                             int bar_id, int nthr) {
+                                             int bar_id, int nthr, int j0 = 0) {
   constexpr int VS = PR + 4, RPT = PR / TPC;
-  if (col == 0 && b > 0) publish_part<T, PR, TPC>(vbuf, pan, R[0], part);
-  for (int j = 0; j < b; j++) {
+  // j0 > 0: the panel is zero left of column j0 (rows j0.. of a triangle)
+  if (col == j0 && j0 < b) publish_part<T, PR, TPC>(vbuf + (j0 & 1) * VS, pan, R[j0 * ldr + j0], part);
+  for (int j = j0; j < b; j++) {
     group_bar(bar_id, nthr);
     const T *vb = vbuf + (j & 1) * VS;
     T *vn = vbuf + ((j + 1) & 1) * VS;
@@ -1653,7 +1656,7 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
           const int row = p0 + part * RPT + i;
           pan[i] = (row < b && col < b) ? Ro[row * LDR + col] : (T)0;
         }
-        fold_group_q<T, PR, TPC>(pan, Rg, LDR, b, col, part, vbuf, bar_id, GT);
+        fold_group_q<T, PR, TPC>(pan, Rg, LDR, b, col, part, vbuf, bar_id, GT, p0);
       }
     }
   }
@@ -1846,7 +1849,7 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
         const int row = p0 + part * RPT + i;
         pan[i] = (row < b && col < b) ? __ldcg(right + row * LDR + col) : (T)0;
       }
-      fold_group_q<T, PR, TPC>(pan, R, LDR, b, col, part, vbuf, 1, GT);
+      fold_group_q<T, PR, TPC>(pan, R, LDR, b, col, part, vbuf, 1, GT, p0);
     }
     cur = ls;
   }
