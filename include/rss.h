@@ -70,9 +70,11 @@ typedef struct {
                           (see rss_mlp_create); borrowed for the call only */
 } rss_options;
 
-/* Route every box through the large-box kernels (global-memory workspaces),
- * which otherwise run only when a box is too large for shared memory.  The
- * result is the same factorization; used to test that path on small cases. */
+/* Route every box through the plain one-CTA-per-box kernels with
+ * global-memory workspaces (the general ID and elimination), which otherwise
+ * run only for boxes too wide for the other forms, and then over several
+ * CTAs per box.  The result is the same factorization up to rounding; the
+ * tests compare the other paths with it. */
 #define RSS_FLAG_LARGE_BOX_PATH 1
 /* Use the built-in launch shapes instead of the autotuner's choices (see
  * rss_autotune_table). */
