@@ -193,6 +193,16 @@ rss_status rss_solve_refined(const rss_factorization *f, const double *b, double
  * pairs otherwise.  Device buffers, n x nrhs column-major. */
 rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs);
 
+/* rss_logdet -- log |det F| of the factorization F ~ A (Sec. 3.3, the
+ * determinant by-product: the factors U_T, L_T and the elimination's unit
+ * triangular factors have determinant 1, so det F is the product of the
+ * determinants of every box's X_RR and of the top block).  Computed as the
+ * sum of log |U_jj| over the LU factors the factorization stores, in
+ * double.  logabs: HOST array, one entry per problem (1 for rss_factor,
+ * nprob for rss_factor_batched).  Synchronous.  RSS_EINVAL for a NULL
+ * argument. */
+rss_status rss_logdet(const rss_factorization *f, double *logabs);
+
 /* rss_stats -- factor statistics into a HOST int64 array:
  *   [0] number of skeletonized boxes  [1] top-block size  [2] factor bytes
  *   [3] maxdepth                      [4] n               [5] precision

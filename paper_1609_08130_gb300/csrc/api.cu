@@ -831,6 +831,7 @@ struct FactorBase {
 };
 
 template <typename T> struct Factor : FactorBase {
+  using value_type = T;
   // one or more independent problems, DOFs concatenated in problem order
   std::vector<HTree> trees;
   std::vector<int64_t> pdof;  // DOF offset of each problem (nprob + 1)
@@ -2130,17 +2131,29 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
   CK(cudaStreamSynchronize(st));
 }
 
+// Columns in chunks small enough for the sweep kernels' shared-memory
+// vectors (3 b x columns entries of the widest box within 200 KB); calls of
+// up to 4 columns on factors of boxes up to ~2000 wide are one chunk.
+template <typename T> static void sweeps_chunked(const Factor<T> &F, const double *in, double *out, int nrhs,
+                                                 bool solve) {
+  int bm = 1;
+  for (const auto &p : F.phases) bm = std::max(bm, p.bmax);
+  const int cmax = (int)std::max<size_t>(1, std::min<size_t>(nrhs, (size_t)(200 << 10) / ((size_t)3 * bm * sizeof(T))));
+  for (int c0 = 0; c0 < nrhs; c0 += cmax)
+    do_sweeps(F, in + (size_t)c0 * F.n, out + (size_t)c0 * F.n, std::min(cmax, nrhs - c0), solve);
+}
+
 static rss_status sweep_entry(const rss_factorization *f, const double *in, double *out, int nrhs, bool solve) {
   return guard([&] {
     if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "bad arguments"};
     if (f->impl->prec == RSS_FP64) {
       auto &F = static_cast<const Factor<double> &>(*f->impl);
       if (F.n > 0 && (!in || !out)) throw Fail{RSS_EINVAL, "NULL vector"};
-      do_sweeps(F, in, out, nrhs, solve);
+      sweeps_chunked(F, in, out, nrhs, solve);
     } else {
       auto &F = static_cast<const Factor<float> &>(*f->impl);
       if (F.n > 0 && (!in || !out)) throw Fail{RSS_EINVAL, "NULL vector"};
-      do_sweeps(F, in, out, nrhs, solve);
+      sweeps_chunked(F, in, out, nrhs, solve);
     }
   });
 }
@@ -2396,6 +2409,41 @@ rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, in
       if (F.n > 0 && (!x || !y)) throw Fail{RSS_EINVAL, "NULL vector"};
       if (F.n > 0) apply_A(F, x, y, nrhs);
       CK(cudaStreamSynchronize(F.st));
+    };
+    if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
+    else run(static_cast<const Factor<float> &>(*f->impl));
+  });
+}
+
+rss_status rss_logdet(const rss_factorization *f, double *logabs) {
+  return guard([&] {
+    if (!f || !f->impl || !logabs) throw Fail{RSS_EINVAL, "rss_logdet: bad arguments"};
+    auto run = [&](const auto &F) {
+      using T = typename std::remove_reference_t<decltype(F)>::value_type;
+      const int nbox = (int)F.h_boxes.size(), np = F.nprob;
+      DBuf part, first;
+      part.alloc(sizeof(double) * ((size_t)nbox + np) + 16, F.st);
+      first.alloc(sizeof(int64_t) * (size_t)nbox + 16, F.st);
+      launch_logdet<T>(ptr<FBox<T>>(F.d_boxes), nbox, F.ntop > 0 ? ptr<T>(F.d_topLU) : nullptr,
+                       ptr<int64_t>(F.d_loff), ptr<int>(F.d_tn), F.ntop > 0 ? np : 0, ptr<double>(part),
+                       ptr<int64_t>(first), F.st);
+      check_launch("logdet");
+      std::vector<double> hp((size_t)nbox + np, 0.0);
+      std::vector<int64_t> hf(nbox);
+      if (nbox > 0)
+        CK(cudaMemcpyAsync(hf.data(), first.p, sizeof(int64_t) * nbox, cudaMemcpyDeviceToHost, F.st));
+      CK(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * (nbox + (F.ntop > 0 ? np : 0)),
+                         cudaMemcpyDeviceToHost, F.st));
+      CK(cudaStreamSynchronize(F.st));
+      // boxes in factor order, then the top block, per problem
+      for (int p = 0; p < np; p++) logabs[p] = 0.0;
+      for (int q = 0; q < nbox; q++) {
+        if (hf[q] < 0) continue;
+        const int p = (int)(std::upper_bound(F.pdof.begin(), F.pdof.end(), hf[q]) - F.pdof.begin()) - 1;
+        if (p >= 0 && p < np) logabs[p] += hp[q];
+      }
+      if (F.ntop > 0)
+        for (int p = 0; p < np; p++) logabs[p] += hp[(size_t)nbox + p];
     };
     if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
     else run(static_cast<const Factor<float> &>(*f->impl));

@@ -113,6 +113,11 @@ void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_li
                   int njmax, const T *scratch, int64_t scratch_stride, cudaStream_t st);
 template <typename T>
 void launch_dense_lu(T *A, int n, int *piv, T *W, cudaStream_t st, int *err);
+// Per-box sums of log|U_jj| (part[0..nbox), and a DOF id of each box in
+// first[]) and per-problem sums over the top blocks' LU (part[nbox..)).
+template <typename T>
+void launch_logdet(const FBox<T> *boxes, int nbox, const T *topLU, const int64_t *loff, const int *tn, int nprob,
+                   double *part, int64_t *first, cudaStream_t st);
 
 // Sweeps over the factor (kernels.cu).  v: tree-order working vector,
 // layout v[g * nrhs + c].

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "librss.so")
-SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu"]
+SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu", "logdet.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -86,6 +86,7 @@ _SIGS = {
     "rss_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rss_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rss_logdet": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rss_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_mlp_create": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "rss_mlp_params": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -298,6 +299,13 @@ class Factorization:
     def matvec(self, x):
         """Exact FP64 A x by direct summation."""
         return self._call(lib().rss_matvec, x)
+
+    def logdet(self):
+        """rss_logdet: log|det F| per problem (numpy float64 array)."""
+        import numpy as np
+        out = np.zeros(len(getattr(self, "sizes", [self.n])), dtype=np.float64)
+        _check(lib().rss_logdet(self.h, C.c_void_p(out.ctypes.data)))
+        return out
 
     def stats(self) -> dict:
         import numpy as np

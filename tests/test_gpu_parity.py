@@ -495,3 +495,38 @@ def test_general_id_over_several_ctas(pkg):
     assert float(torch.linalg.norm(f.matvec(z) - x) / torch.linalg.norm(x)) <= 10 * eps
     g = pkg.Factorization(_cuda(pts), 0, eps, leaf=600, prec=pkg.FP64, flags=pkg.rss.FLAG_LARGE_BOX_PATH)
     assert float(torch.linalg.norm(g.solve(x) - z) / torch.linalg.norm(z)) <= 10 * eps
+
+
+def test_logdet_exact_limit(pkg):
+    """eps -> 0: log|det F| from the stored LU factors equals log|det A| of the
+    dense matrix (Sec. 3.3: the triangular factors have unit determinant)."""
+    pts = inputs.grid_points(32, 2)
+    f = pkg.Factorization(_cuda(pts), 0, 1e-14, leaf=16)
+    _, ld = np.linalg.slogdet(oracle.dense_matrix(pts, 0))
+    got = f.logdet()
+    assert got.shape == (1,)
+    assert abs(got[0] - ld) <= 1e-9 * max(1.0, abs(ld)), (got[0], ld)
+
+
+def test_logdet_is_that_of_the_factor(pkg):
+    """At eps 1e-6 (FP64) the value is log|det F| of the operator the factor
+    applies: F formed column by column by rss_apply on the identity, then a
+    dense LU."""
+    pts = inputs.grid_points(32, 2)
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=16)
+    Fd = f.apply(torch.eye(n, dtype=torch.float64, device="cuda")).cpu().numpy().T
+    _, ld = np.linalg.slogdet(Fd)
+    assert abs(f.logdet()[0] - ld) <= 1e-9 * max(1.0, abs(ld)), (f.logdet()[0], ld)
+
+
+def test_logdet_batched_per_problem(pkg):
+    """Batched handle, eps -> 0: one value per problem, each log|det A_p| of
+    that problem's dense matrix (w = 1/N_p)."""
+    probs = _batched_case(count=3, cap=2000)
+    f = pkg.Factorization.batched([_cuda(p) for p in probs], 0, 1e-14, leaf=64)
+    got = f.logdet()
+    assert got.shape == (len(probs),)
+    for i, pts in enumerate(probs):
+        _, ld = np.linalg.slogdet(oracle.dense_matrix(pts, 0))
+        assert abs(got[i] - ld) <= 1e-9 * max(1.0, abs(ld)), (i, got[i], ld)
