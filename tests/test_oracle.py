@@ -356,3 +356,21 @@ def test_degenerate_sizes():
     tr0 = oracle.Tree(np.zeros((0, 2)), 64)
     f0 = oracle.Factor(tr0, 0, 1e-6, w=1.0)
     assert f0.ntop == 0
+
+
+def test_logdet_is_that_of_the_factor():
+    """At eps > 0 the oracle's log det (sum of log |U_jj| over the boxes' and
+    the top block's LU) is log |det F| of the operator it applies: F formed
+    column by column from apply() on the identity, then a dense LU.  A
+    missing box, a wrong diagonal or a dropped top block moves it."""
+    pts = inputs.grid_points(16, 2)
+    n = len(pts)
+    f = oracle.Factor(oracle.Tree(pts, 16), 0, 1e-4)
+    Fd = np.stack([f.apply(np.eye(n)[:, c].copy()) for c in range(n)], axis=1)
+    sign, ld = np.linalg.slogdet(Fd)
+    assert sign != 0
+    assert abs(f.logdet() - ld) <= 1e-10 * max(1.0, abs(ld)), (f.logdet(), ld)
+    # the compression is real: F is not A, and neither is its determinant
+    _, lda = np.linalg.slogdet(oracle.dense_matrix(pts, 0))
+    assert np.linalg.norm(Fd - oracle.dense_matrix(pts, 0)) > 1e-9
+    assert abs(lda - ld) < 1e-2
