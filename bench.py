@@ -50,6 +50,26 @@ def load_peaks():
         return dict(hbm=6800.0, bf16=1900.0, src="fallback", sm_mhz=2070.0)
 
 
+# kernel classes bound by moving bytes; the others (ID, elimination, top LU)
+# by FP32 / FP64 arithmetic latency and throughput
+HBM_CLASSES = {"schur", "sweep", "assemble", "permute", "top_solve", "refine_op"}
+
+
+def class_roofline(cls: str, d: dict, peaks: dict, prec: str):
+    """Achieved rate of one kernel class against its bound: its algorithmic
+    bytes (HBM-bound classes) or flops (the others) over its CUDA-event time
+    in the timed steps; None for a class that took no time."""
+    s = d["ms"] / 1e3
+    if s <= 0:
+        return None
+    if cls in HBM_CLASSES:
+        a = d["bytes"] / s / 1e9
+        return {"bound": "hbm", "achieved": a, "peak": peaks["hbm"], "unit": "GB/s", "frac": a / peaks["hbm"]}
+    pk = alu_peak_tflops(prec, peaks["sm_mhz"])
+    a = d["flops"] / s / 1e12
+    return {"bound": "alu", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk}
+
+
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     """The slowest rank's figure (all-reduce MAX over the process group);
     x itself with a single process."""
@@ -341,24 +361,15 @@ def main():
     gpu_classes = {k: v for k, v in prof_tot.items() if not k.startswith("host_")}
     dom = max(gpu_classes.items(), key=lambda kv: kv[1]["ms"])
     cls, d = dom
-    per_launch_s = d["ms"] / 1e3 / max(d["launches"], 1)
-    hbm_classes = {"schur", "sweep", "assemble", "permute", "top_solve", "refine_op"}
-    if cls in hbm_classes:
-        achieved = d["bytes"] / max(d["launches"], 1) / per_launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm"], "traffic": None}
-    else:
-        achieved = d["flops"] / max(d["launches"], 1) / per_launch_s / 1e12
-        pk = alu_peak_tflops(args.prec, peaks["sm_mhz"])
-        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "traffic": None}
+    roof = class_roofline(cls, d, peaks, args.prec)
     roof["traffic"] = ncu_traffic(cls)
     roof["kernel"] = cls
     roof["peak_source"] = ("of measured (MEASURED_PEAKS.json)" if roof["bound"] == "hbm" and peaks["src"] == "measured"
                            else "derived from unit counts and max SM clock" if roof["bound"] == "alu"
                            else "of fallback")
     gsum = max(sum(t["ms"] for t in gpu_classes.values()), 1e-9)
-    roof["classes"] = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps, "share": v["ms"] / gsum}
+    roof["classes"] = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps, "share": v["ms"] / gsum,
+                           "roofline": class_roofline(k, v, peaks, args.prec)}
                        for k, v in sorted(gpu_classes.items(), key=lambda kv: -kv[1]["ms"])}
     roof["host_ms_per_step"] = {k: v["ms"] / args.steps for k, v in prof_tot.items() if k.startswith("host_")}
 

@@ -55,3 +55,20 @@ def test_single_process_keeps_its_time():
 
     assert bench.max_over_ranks(17.0) == 17.0
     assert bench.job_points_per_s(1, 4096, 2.0) == pytest.approx(4096 / 0.002)
+
+
+def test_class_roofline_arithmetic():
+    """Per-class roofline figures from a class's algorithmic bytes / flops
+    and its time: HBM-bound classes in GB/s against the copy peak, the
+    others in TFLOP/s against the derived FP32 peak; no time, no figure."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    peaks = {"hbm": 6800.0, "sm_mhz": 2070.0}
+    r = bench.class_roofline("schur", {"ms": 2.0, "bytes": 6.8e9, "flops": 0.0, "launches": 5}, peaks, "mixed")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(3400.0) and r["frac"] == pytest.approx(0.5)
+    r = bench.class_roofline("id", {"ms": 10.0, "bytes": 0.0, "flops": 1e11, "launches": 9}, peaks, "mixed")
+    pk = bench.alu_peak_tflops("mixed", 2070.0)
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(10.0) and r["frac"] == pytest.approx(10.0 / pk)
+    assert bench.class_roofline("elim", {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "launches": 0}, peaks, "mixed") is None
