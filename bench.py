@@ -275,8 +275,11 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # first-kind workloads carry their diagonal and off-diagonal weight
+    matrix = {k: w[k] for k in ("diag", "weight") if k in w}
+
     def step(profile=False, p=prec):
-        f = pkg.Factorization(pts, w["kind"], w["eps"], leaf=w["leaf"], prec=p, profile=profile)
+        f = pkg.Factorization(pts, w["kind"], w["eps"], leaf=w["leaf"], prec=p, profile=profile, **matrix)
         x, iters, rel = f.solve_refined(b, tol=args.tol, maxit=10)
         return f, x, iters, rel
 
@@ -328,7 +331,7 @@ def main():
         t0.record(stream)
         pd = pts_pin.to("cuda", non_blocking=True)
         bd = b_pin.to("cuda", non_blocking=True)
-        fe = pkg.Factorization(pd, w["kind"], w["eps"], leaf=w["leaf"], prec=prec)
+        fe = pkg.Factorization(pd, w["kind"], w["eps"], leaf=w["leaf"], prec=prec, **matrix)
         xe, _, _ = fe.solve_refined(bd, tol=args.tol, maxit=10)
         x_pin.copy_(xe, non_blocking=True)
         t1.record(stream)

@@ -24,6 +24,8 @@ Workloads (all synthetic, shaped like the numerical examples of Sec. 4):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -95,12 +97,45 @@ def rhs(seed: int, n: int, nrhs: int = 1) -> np.ndarray:
 # with K_ii := 0 (second-kind form), w = 1/N.
 # ---------------------------------------------------------------------------
 
+def cell_self_integral(kind: int, h: float) -> float:
+    """Diagonal entry of the first-kind discretisations of Sec. 4 (Examples
+    1 and 2): piecewise-constant collocation on a grid of side h gives
+    K_ij = h^d K(x_i - x_j) off the diagonal and K_ii = the integral of K
+    over the cell [-h/2, h/2]^d around the collocation point.  Closed forms
+    (a = h/2), by scaling the integral over the unit square / cube:
+      2D, K = -log|z| / (2 pi):
+        int_[0,1]^2 log(x^2 + y^2) = log 2 + pi/2 - 3, so
+        int_[-a,a]^2 log|z| = 2 a^2 (2 log a + log 2 + pi/2 - 3);
+      3D, K = 1 / (4 pi |z|):
+        int_[0,1]^3 1/|z| = (3/2) log((sqrt 3 + 1)/(sqrt 3 - 1)) - pi/4, so
+        int_[-a,a]^3 1/|z| = 8 a^2 times that.
+    The paper approximates these integrals adaptively; the closed forms are
+    the values that quadrature converges to."""
+    a = 0.5 * h
+    if kind == 0:
+        return -(2.0 * a * a * (2.0 * math.log(a) + math.log(2.0) + 0.5 * math.pi - 3.0)) / (2.0 * math.pi)
+    if kind == 1:
+        c = 1.5 * math.log((math.sqrt(3.0) + 1.0) / (math.sqrt(3.0) - 1.0)) - 0.25 * math.pi
+        return 8.0 * a * a * c / (4.0 * math.pi)
+    raise ValueError(kind)
+
+
 def workload(name: str) -> dict:
     """Named synthetic workloads.  Returns a dict with points, kernel, eps,
     leaf size, rhs seeds.  Points are float64, shape (n, dim)."""
     if name == "laplace2d_grid64":            # 64x64 grid, N = 4096
         pts = grid_points(64, 2)
         return dict(name=name, pts=pts, dim=2, kind=0, eps=1e-6, leaf=64, rhs_seeds=[1])
+    if name == "laplace2d_grid64_first_kind":  # Example 1 as in the paper: first kind, N = 4096
+        pts = grid_points(64, 2)
+        h = 1.0 / 64
+        return dict(name=name, pts=pts, dim=2, kind=0, eps=1e-6, leaf=64, rhs_seeds=[1],
+                    diag=cell_self_integral(0, h), weight=h * h)
+    if name == "laplace3d_grid16_first_kind":  # Example 2 as in the paper: first kind, N = 4096
+        pts = grid_points(16, 3)
+        h = 1.0 / 16
+        return dict(name=name, pts=pts, dim=3, kind=1, eps=1e-3, leaf=64, rhs_seeds=[1],
+                    diag=cell_self_integral(1, h), weight=h ** 3)
     if name == "laplace2d_grid256":           # 256x256 grid, N = 65536 (profiling size)
         pts = grid_points(256, 2)
         return dict(name=name, pts=pts, dim=2, kind=0, eps=1e-6, leaf=64, rhs_seeds=[1, 2, 3, 4])

@@ -374,3 +374,66 @@ def test_logdet_is_that_of_the_factor():
     _, lda = np.linalg.slogdet(oracle.dense_matrix(pts, 0))
     assert np.linalg.norm(Fd - oracle.dense_matrix(pts, 0)) > 1e-9
     assert abs(lda - ld) < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# first-kind workloads as in Sec. 4 (Examples 1 and 2)
+# ---------------------------------------------------------------------------
+
+def test_cell_self_integral_closed_forms():
+    """The closed forms of the cell integrals against an independent route:
+    cutting the unit square into two triangles (the unit cube into three
+    pyramids) about the singular corner leaves smooth integrals, done by
+    adaptive quadrature.  Square: int log(x^2+y^2) = -1 + int_0^1 log(1+s^2) ds.
+    Cube: int 1/|z| = (3/2) int_[0,1]^2 (1+s^2+t^2)^(-1/2) ds dt."""
+    from scipy import integrate
+    sq = -1.0 + integrate.quad(lambda s: math.log1p(s * s), 0.0, 1.0, epsabs=1e-14, epsrel=1e-14)[0]
+    cube = 1.5 * integrate.dblquad(lambda t, s: 1.0 / math.sqrt(1.0 + s * s + t * t), 0.0, 1.0, 0.0, 1.0,
+                                   epsabs=1e-13, epsrel=1e-13)[0]
+    for h in (1.0 / 64, 1.0 / 512, 0.3):
+        a = 0.5 * h
+        # [-a,a]^2 = four copies of [0,a]^2; log|z| = log(z^2)/2; scale by a^2
+        want2 = -(4.0 * a * a * 0.5 * (sq + 2.0 * math.log(a))) / (2.0 * math.pi)
+        assert inputs.cell_self_integral(0, h) == pytest.approx(want2, rel=1e-12)
+        want3 = 8.0 * a * a * cube / (4.0 * math.pi)
+        assert inputs.cell_self_integral(1, h) == pytest.approx(want3, rel=1e-12)
+
+
+def _first_kind(side, dim):
+    pts = inputs.grid_points(side, dim)
+    h = 1.0 / side
+    kind = 0 if dim == 2 else 1
+    return pts, kind, inputs.cell_self_integral(kind, h), h ** dim
+
+
+def test_first_kind_exact_limit():
+    """eps -> 0 on the first-kind matrix (diagonal = cell integral, off the
+    diagonal h^d K): exact block elimination, F = A and the dense solve."""
+    pts, kind, d, w = _first_kind(24, 2)
+    n = len(pts)
+    A = oracle.dense_matrix(pts, kind, diag=d, w=w)
+    f = oracle.Factor(oracle.Tree(pts, 64), kind, 1e-14, diag=d, w=w)
+    x = inputs.normal(11, n)
+    assert np.linalg.norm(f.apply(x) - A @ x) / np.linalg.norm(A @ x) < 1e-12
+    b = inputs.normal(12, n)
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(f.solve(b) - xs) / np.linalg.norm(xs) < 1e-10
+
+
+@pytest.mark.parametrize("side,dim,eps", [(32, 2, 1e-6), (32, 2, 1e-3), (12, 3, 1e-3)])
+def test_first_kind_accuracy(side, dim, eps):
+    """The paper's examples are first kind and its tables show e_a = O(eps)
+    (Tables 2 and 4): the apply error stays below eps; the solve error obeys
+    the first-order perturbation bound ||F^{-1} - A^{-1}|| <= ||A^{-1}|| ||A - F|| ||F^{-1}||,
+    i.e. at most 2 cond(A) e_a in relative terms."""
+    pts, kind, d, w = _first_kind(side, dim)
+    n = len(pts)
+    A = oracle.dense_matrix(pts, kind, diag=d, w=w)
+    f = oracle.Factor(oracle.Tree(pts, 64 if dim == 2 else 27), kind, eps, diag=d, w=w)
+    x = inputs.normal(13, n)
+    Ax = A @ x
+    ea = np.linalg.norm(f.apply(x) - Ax) / np.linalg.norm(Ax)
+    assert ea < eps
+    es = np.linalg.norm(f.solve(Ax) - x) / np.linalg.norm(x)
+    assert es <= 2.0 * np.linalg.cond(A) * max(ea, 1e-15)
+    assert sum(b["r"] for b in f.boxes()) > n // 8  # compression happened
