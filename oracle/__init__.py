@@ -5,8 +5,9 @@ and by the benchmark's CPU-baseline leg.  The product library never imports,
 links or runs anything here.
 
 Every routine follows the paper step by step (strong recursive
-skeletonization, Algorithm 1, Sec. 3); see the header of ``rss_oracle.c``
-for the readings taken where the paper is silent.
+skeletonization, Algorithm 1, Sec. 3; the hybrid RS-WS, Algorithm 2,
+Sec. 3.4); see the header of ``rss_oracle.c`` for the readings taken where
+the paper is silent.
 """
 from __future__ import annotations
 
@@ -61,7 +62,7 @@ def _setup(L):
     L.orc_lu.argtypes = [_dp, C.c_int, _ip]
     L.orc_factor.restype = C.c_void_p
     L.orc_factor.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
-                             C.c_double, C.c_int]
+                             C.c_double, C.c_int, C.c_int]
     L.orc_factor_free.argtypes = [C.c_void_p]
     L.orc_factor_info.restype = C.c_int64
     L.orc_factor_info.argtypes = [C.c_void_p, C.c_int]
@@ -178,16 +179,17 @@ def lu(A: np.ndarray):
 # ---------------------------------------------------------------------------
 
 class Factor:
-    """RS-S factor of A = diag*I + w*K on the tree's points (Algorithm 1)."""
+    """RS-S factor of A = diag*I + w*K on the tree's points (Algorithm 1);
+    hybrid=True: the RS-WS factor (Sec. 3.4, Algorithm 2)."""
 
     def __init__(self, tree: Tree, kind: int, eps: float, diag: float = 1.0, w: float | None = None,
-                 nproxy: int = 0, radius: float = 2.5, check: bool = False):
+                 nproxy: int = 0, radius: float = 2.5, check: bool = False, hybrid: bool = False):
         self.tree = tree
         self.kind = kind
         self.diag = diag
         self.w = (1.0 / tree.n) if w is None else w
         self.eps = eps
-        self.h = lib().orc_factor(tree.h, kind, diag, self.w, eps, nproxy, radius, int(check))
+        self.h = lib().orc_factor(tree.h, kind, diag, self.w, eps, nproxy, radius, int(check), int(hybrid))
         L = lib()
         self.nbox = L.orc_factor_info(self.h, 0)
         self.ntop = L.orc_factor_info(self.h, 1)
@@ -200,9 +202,9 @@ class Factor:
             self.h = None
 
     def box(self, i: int) -> dict:
-        v = np.empty(8, np.int32)
+        v = np.empty(9, np.int32)
         lib().orc_factor_box(self.h, i, _i(v))
-        return dict(zip(["node", "depth", "b", "k", "r", "nj", "nnear", "nring"], map(int, v)))
+        return dict(zip(["node", "depth", "b", "k", "r", "nj", "nnear", "nring", "weak"], map(int, v)))
 
     def boxes(self) -> list:
         return [self.box(i) for i in range(self.nbox)]

@@ -34,6 +34,12 @@
  *     proxy rows scaled by w like the matrix entries;
  *   - ID matrix: [A_OB; A_BO^T; w K(Gamma,B); w K(B,Gamma)^T] (Eq. 3.1 with
  *     the proxy replacement of Eq. 3.6, both halves kept);
+ *   - hybrid (RS-WS, Sec. 3.4, Algorithm 2): a weak step compresses the
+ *     box's interactions with its whole complement, [A_XB; A_BX^T; proxy
+ *     rows] with X = N u O (the cells inside the proxy surface), drops every
+ *     coupling of R outside the box and eliminates R against J = S; each
+ *     depth runs a weak pass over its boxes, then the strong pass; a last
+ *     weak pass runs at depth 1 (the paper's practice);
  *   - ID by Householder QR with greedy column pivoting, pivot = largest
  *     trailing column norm, recomputed every step, ties to the lowest
  *     column; rank k = #{j : |R_jj| > eps |R_11|}; T = R11^{-1} R12;
@@ -480,6 +486,7 @@ static void lu_mult(const double *LU, const int *piv, int n, const double *x, do
 
 typedef struct {
   int node, depth, b, k, r, nj, nnear, nring;
+  int weak;           /* 1: weak skeletonization (RS-WS, Sec. 3.4): J = S */
   int64_t *S, *R, *J; /* tree-order DOF ids: S in pivot order, J = [S; N] */
   double *T;          /* k x r column-major (ld k) */
   double *LU;         /* r x r row-major */
@@ -522,9 +529,15 @@ static void proxy_points(int dim, int np, double radius, int t, const int *coord
   }
 }
 
-/* Factor.  check != 0 turns on the Theorem 3.1 / Corollary 3.2 checks. */
+/* Factor.  check != 0 turns on the Theorem 3.1 / Corollary 3.2 checks.
+ * hybrid != 0: RS-WS (Sec. 3.4, Algorithm 2): at every depth, first weak
+ * skeletonization of each box (its interactions with the whole complement
+ * compressed: the cells inside the proxy surface explicitly, the rest
+ * through the proxy points), then strong skeletonization of what stays
+ * active; plus a last weak pass at depth 1, where no strong step is
+ * possible, as the paper does in practice. */
 void *orc_factor(void *th, int kind, double diag, double w, double eps, int nproxy,
-                 double radius, int check) {
+                 double radius, int check, int hybrid) {
   otree *T = th;
   int64_t n = T->n;
   int dim = T->dim;
@@ -552,7 +565,7 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
   int cap = 16;
   F->box = malloc(sizeof(obox) * cap);
 
-  for (int t = T->maxdepth; t >= 2; t--) {
+  for (int t = T->maxdepth; t >= (hybrid ? 1 : 2); t--) {
     int64_t *cell = cells_at(T, t);
     int nb = orc_tree_level_boxes(T, t, order);
     if (check) {
@@ -571,6 +584,9 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
         }
       }
     }
+    /* pass 0: weak skeletonization (RS-WS only); pass 1: strong (depths >= 2) */
+    for (int pass = hybrid ? 0 : 1; pass <= (t >= 2 ? 1 : 0); pass++) {
+    const int weak = pass == 0;
     for (int q = 0; q < nb; q++) {
       int node = order[q];
       int64_t bc[3] = {T->coord[3 * node], T->coord[3 * node + 1], T->coord[3 * node + 2]};
@@ -596,18 +612,24 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
           }
       }
       int b = (int)nbB;
-      /* ID matrix [A_OB; A_BO^T; w K(Gamma,B); w K(B,Gamma)^T], column-major */
-      int m = (int)(2 * nO + 2 * nproxy);
+      /* ID matrix [A_XB; A_BX^T; w K(Gamma,B); w K(B,Gamma)^T], column-major,
+       * with X the cells inside the proxy surface that the step compresses:
+       * strong: the ring O (Eq. 3.7); weak: N and O (the whole complement) */
+      int64_t nX = weak ? nN + nO : nO;
+      int m = (int)(2 * nX + 2 * nproxy);
       double *M = malloc(sizeof(double) * (size_t)m * b);
       proxy_points(dim, nproxy, radius, t, T->coord + 3 * node, yp);
       for (int c = 0; c < b; c++) {
         int64_t j = Bl[c];
         double *col = M + (size_t)c * m;
-        for (int64_t o = 0; o < nO; o++) col[o] = A[Ol[o] * n + j];
-        for (int64_t o = 0; o < nO; o++) col[nO + o] = A[j * n + Ol[o]];
+        for (int64_t o = 0; o < nX; o++) {
+          int64_t g = weak && o < nN ? Nl[o] : Ol[weak ? o - nN : o];
+          col[o] = A[g * n + j];
+          col[nX + o] = A[j * n + g];
+        }
         for (int p = 0; p < nproxy; p++) {
-          col[2 * nO + p] = w * kfun(kind, dim, yp + dim * p, T->x + j * dim);
-          col[2 * nO + nproxy + p] = w * kfun(kind, dim, T->x + j * dim, yp + dim * p);
+          col[2 * nX + p] = w * kfun(kind, dim, yp + dim * p, T->x + j * dim);
+          col[2 * nX + nproxy + p] = w * kfun(kind, dim, T->x + j * dim, yp + dim * p);
         }
       }
       int *perm = malloc(sizeof(int) * b);
@@ -623,12 +645,13 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
       obox *bx = &F->box[F->nbox++];
       memset(bx, 0, sizeof(obox));
       bx->node = node;
+      bx->weak = weak;
       bx->depth = t;
       bx->b = b;
       bx->k = k;
       bx->r = r;
-      bx->nnear = (int)nN;
-      bx->nring = (int)nO;
+      bx->nnear = weak ? 0 : (int)nN;
+      bx->nring = (int)nX;
       bx->S = malloc(sizeof(int64_t) * (k + 1));
       bx->R = malloc(sizeof(int64_t) * (r + 1));
       for (int i = 0; i < k; i++) bx->S[i] = Bl[perm[i]];
@@ -639,11 +662,12 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
       free(perm);
       int64_t *S = bx->S, *R = bx->R;
 
-      /* C = B u N: the rows / columns the operators U_T, L_T touch */
-      int64_t nC = nbB + nN;
+      /* C: the rows / columns the operators U_T, L_T touch, B u N (strong);
+       * B (weak: R's couplings outside the box are dropped below) */
+      int64_t nC = weak ? nbB : nbB + nN;
       int64_t *C = malloc(sizeof(int64_t) * (nC + 1));
       memcpy(C, Bl, sizeof(int64_t) * nbB);
-      memcpy(C + nbB, Nl, sizeof(int64_t) * nN);
+      if (!weak) memcpy(C + nbB, Nl, sizeof(int64_t) * nN);
       const double *Tk = bx->T;
       /* U_T from the left: rows R -= T^T rows S (Sec. 3.1) */
       for (int ri = 0; ri < r; ri++)
@@ -659,22 +683,24 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
           for (int si = 0; si < k; si++) s += A[C[c] * n + S[si]] * Tk[(size_t)ri * k + si];
           A[C[c] * n + R[ri]] -= s;
         }
-      /* The compressed far-field blocks X_RF, X_FR are dropped (set to 0). */
+      /* The compressed blocks are dropped (set to 0): X_RF, X_FR for the far
+       * field (strong), every coupling of R outside the box (weak). */
       for (int ri = 0; ri < r; ri++)
         for (int64_t g = 0; g < n; g++) {
           if (!active[g]) continue;
           int dist = cheb(cell + 3 * g, bc, dim);
-          if (dist >= 2) {
+          if (dist >= (weak ? 1 : 2)) {
             A[R[ri] * n + g] = 0.0;
             A[g * n + R[ri]] = 0.0;
           }
         }
-      /* Block elimination with I = R, J = S u N (Sec. 2.1, Eq. 3.4) */
-      int nj = (int)(k + nN);
+      /* Block elimination with I = R, J = S u N (Sec. 2.1, Eq. 3.4); J = S
+       * after a weak step */
+      int nj = (int)(weak ? k : k + nN);
       bx->nj = nj;
       bx->J = malloc(sizeof(int64_t) * (nj + 1));
       memcpy(bx->J, S, sizeof(int64_t) * k);
-      memcpy(bx->J + k, Nl, sizeof(int64_t) * nN);
+      if (!weak) memcpy(bx->J + k, Nl, sizeof(int64_t) * nN);
       int64_t *J = bx->J;
       bx->LU = malloc(sizeof(double) * ((size_t)r * r + 1));
       bx->piv = malloc(sizeof(int) * (r + 1));
@@ -709,6 +735,7 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
         }
       for (int ri = 0; ri < r; ri++) active[R[ri]] = 0;
       free(C);
+    }
     }
     free(cell);
   }
@@ -771,11 +798,11 @@ int64_t orc_factor_info(void *h, int what) {
 }
 
 /* info8 = {node, depth, b, k, r, nj, nnear, nring} */
-void orc_factor_box(void *h, int i, int *info8) {
+void orc_factor_box(void *h, int i, int *info9) {
   ofactor *F = h;
   obox *b = &F->box[i];
-  int v[8] = {b->node, b->depth, b->b, b->k, b->r, b->nj, b->nnear, b->nring};
-  memcpy(info8, v, sizeof(v));
+  int v[9] = {b->node, b->depth, b->b, b->k, b->r, b->nj, b->nnear, b->nring, b->weak};
+  memcpy(info9, v, sizeof(v));
 }
 
 /* Copies S (k), R (r), J (nj) ids and T (k x r col-major), E (nj x r row-major),

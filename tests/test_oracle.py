@@ -437,3 +437,85 @@ def test_first_kind_accuracy(side, dim, eps):
     es = np.linalg.norm(f.solve(Ax) - x) / np.linalg.norm(x)
     assert es <= 2.0 * np.linalg.cond(A) * max(ea, 1e-15)
     assert sum(b["r"] for b in f.boxes()) > n // 8  # compression happened
+
+
+# ---------------------------------------------------------------------------
+# RS-WS, the hybrid factorization (Sec. 3.4, Algorithm 2)
+# ---------------------------------------------------------------------------
+
+def _stored_entries(f):
+    """Entries of T, LU(X_RR), E and G over the boxes, plus the top LU."""
+    return sum(b["k"] * b["r"] + b["r"] ** 2 + 2 * b["nj"] * b["r"] for b in f.boxes()) + f.ntop ** 2
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d_12", "random2d"])
+def test_hybrid_exact_limit(case):
+    """eps -> 0: weak and strong steps are exact block eliminations, so the
+    RS-WS factor reproduces A, its solve the dense solve and its log det
+    log |det A|.  (3D: a 12^3 grid with leaves of 27 points, three levels.)"""
+    if case == "grid3d_12":
+        pts, kind, leaf = inputs.grid_points(12, 3), 1, 27
+    else:
+        (pts, kind), leaf = _problem(case), 64
+    n = len(pts)
+    f = oracle.Factor(oracle.Tree(pts, leaf), kind, 1e-14, hybrid=True)
+    assert f.info == 0
+    A = oracle.dense_matrix(pts, kind)
+    x = inputs.normal(3, n)
+    assert np.linalg.norm(f.apply(x) - A @ x) / np.linalg.norm(A @ x) < 1e-12
+    b = inputs.normal(4, n)
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(f.solve(b) - xs) / np.linalg.norm(xs) < 1e-11
+    _, ld = np.linalg.slogdet(A)
+    assert abs(f.logdet() - ld) < 1e-9 * max(1.0, abs(ld))
+
+
+def test_hybrid_schedule_and_invariants():
+    """Algorithm 2's order: at each depth >= 2 a weak pass over every box, then
+    a strong pass over the same boxes; a last weak pass at depth 1.  A weak
+    step eliminates R against S only (|J| = k).  The weak steps change no
+    block outside a box, so Theorem 3.1 / Corollary 3.2 still hold at every
+    strong step, and the end result is block diagonal (checked on the whole
+    matrix by the oracle's check mode)."""
+    pts, kind = _problem("grid2d")
+    tr = oracle.Tree(pts, 64)
+    f = oracle.Factor(tr, kind, 1e-6, hybrid=True, check=True)
+    assert f.violations == 0
+    boxes = f.boxes()
+    seq = [(b["depth"], b["weak"]) for b in boxes]
+    depths = sorted({d for d, _ in seq}, reverse=True)
+    assert depths[-1] == 1 and all(w == 1 for d, w in seq if d == 1)
+    pos = 0
+    for d in depths:
+        run = [w for dd, w in seq[pos:] if dd == d]
+        nb = len(run)
+        pos += nb
+        if d >= 2:
+            half = nb // 2
+            assert run == [1] * half + [0] * half
+    for b in boxes:
+        if b["weak"]:
+            assert b["nj"] == b["k"] and b["nnear"] == 0
+    # the strong-only factor of the same tree, for contrast: no weak steps
+    g = oracle.Factor(tr, kind, 1e-6)
+    assert not any(b["weak"] for b in g.boxes())
+
+
+@pytest.mark.parametrize("case,eps", [("grid2d", 1e-6), ("grid3d", 1e-3), ("random2d", 1e-6)])
+def test_hybrid_accuracy_and_storage(case, eps):
+    """RS-WS keeps e_a = O(eps) (the paper's tables) and, as the paper finds
+    for its examples, stores less than RS-S: its near-field compression
+    shrinks the boxes' J and the top block."""
+    pts, kind = _problem(case)
+    n = len(pts)
+    tr = oracle.Tree(pts, 64)
+    A = oracle.dense_matrix(pts, kind)
+    x = inputs.normal(6, n)
+    Ax = A @ x
+    h = oracle.Factor(tr, kind, eps, hybrid=True)
+    ea = np.linalg.norm(h.apply(x) - Ax) / np.linalg.norm(Ax)
+    assert ea < eps
+    assert np.linalg.norm(h.solve(Ax) - x) / np.linalg.norm(x) < 10 * eps
+    s = oracle.Factor(tr, kind, eps)
+    assert _stored_entries(h) < _stored_entries(s)
+    assert h.ntop < s.ntop
