@@ -220,11 +220,15 @@ static uint64_t morton(const int *c, int dim) {
   return m;
 }
 
+/* Colour of a cell: sum_d (c_d mod base) base^d; base 3 (the boxes of a
+ * colour are >= 3 cells apart) except while a factorization with the 2^d
+ * schedule orders its levels. */
+static int g_colour_base = 3;
 static int colour(const int *c, int dim) {
   int col = 0, mul = 1;
   for (int d = 0; d < dim; d++) {
-    col += (c[d] % 3) * mul;
-    mul *= 3;
+    col += (c[d] % g_colour_base) * mul;
+    mul *= g_colour_base;
   }
   return col;
 }
@@ -530,6 +534,16 @@ static void proxy_points(int dim, int np, double radius, int t, const int *coord
 }
 
 /* Factor.  check != 0 turns on the Theorem 3.1 / Corollary 3.2 checks.
+ * schedule: 0 one box after another in colour order (3^d colours); 1 and 2
+ * a colour phase as a parallel machine runs it, with 3^d (1) or 2^d (2)
+ * colours (Sec. 5): every box of the phase builds its lists and its ID
+ * matrix from the state at the start of the phase.  The rest of a box's
+ * step reads only its own rows / columns and its neighbours', which no
+ * other box of the phase writes except through the additive Schur updates
+ * of shared near-field blocks, so running those parts one box after
+ * another equals the parallel phase up to the order of those additions.
+ * With 3^d colours no box of a phase is within two cells of another, so
+ * schedule 1 gives the same factor as schedule 0.
  * hybrid != 0: RS-WS (Sec. 3.4, Algorithm 2): at every depth, first weak
  * skeletonization of each box (its interactions with the whole complement
  * compressed: the cells inside the proxy surface explicitly, the rest
@@ -537,7 +551,7 @@ static void proxy_points(int dim, int np, double radius, int t, const int *coord
  * active; plus a last weak pass at depth 1, where no strong step is
  * possible, as the paper does in practice. */
 void *orc_factor(void *th, int kind, double diag, double w, double eps, int nproxy,
-                 double radius, int check, int hybrid) {
+                 double radius, int check, int hybrid, int schedule) {
   otree *T = th;
   int64_t n = T->n;
   int dim = T->dim;
@@ -564,10 +578,15 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
   double *yp = malloc(sizeof(double) * 3 * nproxy);
   int cap = 16;
   F->box = malloc(sizeof(obox) * cap);
+  /* phase-start state for the parallel schedules */
+  double *A0 = schedule ? malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1)) : NULL;
+  char *active0 = schedule ? malloc(n > 0 ? n : 1) : NULL;
 
   for (int t = T->maxdepth; t >= (hybrid ? 1 : 2); t--) {
     int64_t *cell = cells_at(T, t);
+    g_colour_base = schedule == 2 ? 2 : 3;
     int nb = orc_tree_level_boxes(T, t, order);
+    g_colour_base = 3;
     if (check) {
       /* Corollary 3.2: at the start of a level, every far-field entry of
        * every box of this level equals the original kernel entry. */
@@ -590,12 +609,29 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
     for (int q = 0; q < nb; q++) {
       int node = order[q];
       int64_t bc[3] = {T->coord[3 * node], T->coord[3 * node + 1], T->coord[3 * node + 2]};
+      /* parallel schedules: the state at the start of the colour phase */
+      const int par = schedule && !weak;
+      if (par) {
+        const int base = schedule == 2 ? 2 : 3;
+        int newphase = q == 0;
+        if (!newphase) {
+          g_colour_base = base;
+          newphase = colour(T->coord + 3 * node, dim) != colour(T->coord + 3 * order[q - 1], dim);
+          g_colour_base = 3;
+        }
+        if (newphase) {
+          memcpy(A0, A, sizeof(double) * (size_t)n * (size_t)n);
+          memcpy(active0, active, (size_t)n);
+        }
+      }
+      const double *Ar = par ? A0 : A;
+      const char *act = par ? active0 : active;
       /* B: active DOFs of the box; N / O / P by cell distance (Fig. 2) */
       int64_t nbB = 0, nN = 0, nO = 0, nP = 0;
       for (int64_t g = T->start[node]; g < T->start[node] + T->count[node]; g++)
-        if (active[g]) Bl[nbB++] = g;
+        if (act[g]) Bl[nbB++] = g;
       for (int64_t g = 0; g < n; g++) {
-        if (!active[g]) continue;
+        if (!act[g]) continue;
         int dist = cheb(cell + 3 * g, bc, dim);
         if (dist == 1) Nl[nN++] = g;
         else if (dist == 2) Ol[nO++] = g;
@@ -603,10 +639,13 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
       }
       if (nbB == 0) continue;
       if (check) {
-        /* Theorem 3.1: interactions between B and P are still original. */
+        /* Theorem 3.1: interactions between B and P are still original (P
+         * DOFs eliminated earlier in a parallel phase are decoupled, not
+         * part of the remaining matrix) */
         for (int64_t a = 0; a < nbB; a++)
           for (int64_t p = 0; p < nP; p++) {
             int64_t i = Bl[a], j = Pl[p];
+            if (!active[j]) continue;
             if (A[i * n + j] != entry(&F->kn, T->x, i, j)) F->violations++;
             if (A[j * n + i] != entry(&F->kn, T->x, j, i)) F->violations++;
           }
@@ -624,8 +663,8 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
         double *col = M + (size_t)c * m;
         for (int64_t o = 0; o < nX; o++) {
           int64_t g = weak && o < nN ? Nl[o] : Ol[weak ? o - nN : o];
-          col[o] = A[g * n + j];
-          col[nX + o] = A[j * n + g];
+          col[o] = Ar[g * n + j];
+          col[nX + o] = Ar[j * n + g];
         }
         for (int p = 0; p < nproxy; p++) {
           col[2 * nX + p] = w * kfun(kind, dim, yp + dim * p, T->x + j * dim);
@@ -770,6 +809,7 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
   }
 
   free(A); free(active); free(Bl); free(Nl); free(Ol); free(Pl); free(order); free(yp);
+  free(A0); free(active0);
   return F;
 }
 

@@ -519,3 +519,50 @@ def test_hybrid_accuracy_and_storage(case, eps):
     s = oracle.Factor(tr, kind, eps)
     assert _stored_entries(h) < _stored_entries(s)
     assert h.ntop < s.ntop
+
+
+# ---------------------------------------------------------------------------
+# colour phases run in parallel (Sec. 5)
+# ---------------------------------------------------------------------------
+
+def _schedule_problems():
+    return [(inputs.grid_points(32, 2), 0, 1e-6, 64), (inputs.random_points(21, 3000, 2), 0, 1e-6, 64),
+            (inputs.grid_points(12, 3), 1, 1e-3, 27)]
+
+
+def test_parallel_phases_with_3d_colours_equal_the_sequential_factor():
+    """With 3^d colours the boxes of a phase are >= 3 cells apart, so a phase
+    whose boxes all start from the phase-start state (as the GPU runs it)
+    gives exactly the factor of one box after another: apply and solve agree
+    bit for bit, and the invariants hold."""
+    for pts, kind, eps, leaf in _schedule_problems():
+        tr = oracle.Tree(pts, leaf)
+        x = inputs.normal(17, len(pts))
+        f0 = oracle.Factor(tr, kind, eps, schedule=0)
+        f1 = oracle.Factor(tr, kind, eps, schedule=1, check=True)
+        assert f1.violations == 0
+        assert np.array_equal(f0.apply(x), f1.apply(x))
+        assert np.array_equal(f0.solve(x), f1.solve(x))
+
+
+def test_parallel_phases_with_2d_colours():
+    """The paper's 2^d colouring (Sec. 5): same-phase boxes can be two cells
+    apart, so a box's ring holds DOFs another box of the phase eliminates;
+    run in parallel, the factor differs from the one-after-another order but
+    is as valid: exact as eps -> 0, e_a < eps, Theorem 3.1 / Corollary 3.2
+    and the final block-diagonal form hold."""
+    for pts, kind, eps, leaf in _schedule_problems():
+        n = len(pts)
+        tr = oracle.Tree(pts, leaf)
+        A = oracle.dense_matrix(pts, kind)
+        x = inputs.normal(18, n)
+        Ax = A @ x
+        f2 = oracle.Factor(tr, kind, eps, schedule=2, check=True)
+        assert f2.violations == 0 and f2.info == 0
+        ea = np.linalg.norm(f2.apply(x) - Ax) / np.linalg.norm(Ax)
+        assert ea < eps
+        assert np.linalg.norm(f2.solve(Ax) - x) / np.linalg.norm(x) < 10 * eps
+        f0 = oracle.Factor(tr, kind, eps, schedule=0)
+        assert not np.array_equal(f0.apply(x), f2.apply(x))
+        fe = oracle.Factor(tr, kind, 1e-14, schedule=2)
+        assert np.linalg.norm(fe.apply(x) - Ax) / np.linalg.norm(Ax) < 1e-12
