@@ -69,6 +69,9 @@ def _setup(L):
     L.orc_factor_box.argtypes = [C.c_void_p, C.c_int, _ip]
     L.orc_factor_box_data.argtypes = [C.c_void_p, C.c_int, _lp, _lp, _lp, _dp, _dp, _dp]
     L.orc_factor_top.argtypes = [C.c_void_p, _lp]
+    L.orc_sqrt_prepare.restype = C.c_int
+    L.orc_sqrt_prepare.argtypes = [C.c_void_p]
+    L.orc_sqrt_apply.argtypes = [C.c_void_p, _dp, _dp, C.c_int, C.c_int]
     L.orc_logdet.restype = C.c_double
     L.orc_logdet.argtypes = [C.c_void_p]
     L.orc_apply.argtypes = [C.c_void_p, _dp, _dp, C.c_int]
@@ -231,6 +234,19 @@ class Factor:
         t = np.empty(max(self.ntop, 1), np.int64)
         lib().orc_factor_top(self.h, _l(t))
         return t[: self.ntop]
+
+    def sqrt_apply(self, x: np.ndarray, transpose: bool = False) -> np.ndarray:
+        """Generalized square root (positive definite K): F^{1/2} x, or
+        (F^{1/2})^T x with transpose=True; F = F^{1/2} (F^{1/2})^T.  Raises
+        ValueError when a diagonal block is not positive definite."""
+        L = lib()
+        st = L.orc_sqrt_prepare(self.h)
+        if st:
+            raise ValueError(f"block {st - 1} of D is not positive definite")
+        x, one = self._vec(x)
+        y = np.empty_like(x)
+        L.orc_sqrt_apply(self.h, _d(x), _d(y), x.shape[0] if x.ndim == 2 else 1, int(transpose))
+        return y[0] if one else y
 
     def logdet(self) -> float:
         return lib().orc_logdet(self.h)

@@ -509,6 +509,7 @@ typedef struct {
   int64_t *top;
   double *LUtop;
   int *pivtop;
+  double **chol;      /* Cholesky factors of the X_RR blocks and the top (orc_sqrt_prepare) */
   int64_t violations; /* Theorem 3.1 / Corollary 3.2 violations seen */
   int info;           /* nonzero: zero pivot met */
 } ofactor;
@@ -821,6 +822,10 @@ void orc_factor_free(void *h) {
     free(b->S); free(b->R); free(b->J); free(b->T); free(b->LU); free(b->piv);
     free(b->E); free(b->G);
   }
+  if (F->chol) {
+    for (int i = 0; i <= F->nbox; i++) free(F->chol[i]);
+    free(F->chol);
+  }
   free(F->box); free(F->top); free(F->LUtop); free(F->pivtop);
   free(F);
 }
@@ -1009,6 +1014,119 @@ void orc_solve(void *h, const double *bvec, double *x, int nrhs) {
     }
   }
   from_tree(F, v, x, nrhs);
+  free(v);
+}
+
+/* Generalized square root (the remark after Eq. 3.11): for positive definite
+ * K the factors are symmetric (V_i = W_i^T), and with D = L L^T by
+ * Cholesky blocks, F^{1/2} = (prod V_i) P_t L satisfies F = F^{1/2}
+ * (F^{1/2})^T.  X_RR of each box is rebuilt from its stored LU and pivots
+ * (row piv[i] of X_RR is row i of L U), then factored by Cholesky; the top
+ * block likewise.  Returns 0, or 1 + the index of the first block that is
+ * not positive definite (the factors are then left unset). */
+static int chol_from_lu(const double *LU, const int *piv, int r, double *C) {
+  double *X = malloc(sizeof(double) * ((size_t)r * r + 1));
+  for (int i = 0; i < r; i++)
+    for (int j = 0; j < r; j++) {
+      double s = 0.0;
+      for (int l = 0; l <= (i < j ? i : j); l++) s += (l == i ? 1.0 : LU[(size_t)i * r + l]) * LU[(size_t)l * r + j];
+      X[(size_t)piv[i] * r + j] = s;
+    }
+  /* lower Cholesky factor, row-major, of the symmetric part */
+  int ok = 1;
+  for (int j = 0; j < r && ok; j++) {
+    double d = 0.5 * (X[(size_t)j * r + j] + X[(size_t)j * r + j]);
+    for (int l = 0; l < j; l++) d -= C[(size_t)j * r + l] * C[(size_t)j * r + l];
+    if (!(d > 0.0)) {
+      ok = 0;
+      break;
+    }
+    C[(size_t)j * r + j] = sqrt(d);
+    for (int i = j + 1; i < r; i++) {
+      double s = 0.5 * (X[(size_t)i * r + j] + X[(size_t)j * r + i]);
+      for (int l = 0; l < j; l++) s -= C[(size_t)i * r + l] * C[(size_t)j * r + l];
+      C[(size_t)i * r + j] = s / C[(size_t)j * r + j];
+    }
+    for (int i = 0; i < j; i++) C[(size_t)i * r + j] = 0.0;
+  }
+  free(X);
+  return ok;
+}
+
+int orc_sqrt_prepare(void *h) {
+  ofactor *F = h;
+  if (F->chol) return 0;
+  double **C = calloc((size_t)F->nbox + 1, sizeof(double *));
+  for (int i = 0; i <= F->nbox; i++) {
+    int r = i < F->nbox ? F->box[i].r : F->ntop;
+    const double *LU = i < F->nbox ? F->box[i].LU : F->LUtop;
+    const int *piv = i < F->nbox ? F->box[i].piv : F->pivtop;
+    C[i] = calloc((size_t)r * r + 1, sizeof(double));
+    if (!chol_from_lu(LU, piv, r, C[i])) {
+      for (int q = 0; q <= i; q++) free(C[q]);
+      free(C);
+      return i + 1;
+    }
+  }
+  F->chol = C;
+  return 0;
+}
+
+/* y = F^{1/2} x (trans = 0) or (F^{1/2})^T x (trans = 1); orc_sqrt_prepare
+ * first.  x, y: n x nrhs column-major in the caller's point order. */
+void orc_sqrt_apply(void *h, const double *x, double *y, int nrhs, int trans) {
+  ofactor *F = h;
+  int64_t n = F->T->n;
+  double *v = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * nrhs);
+  to_tree(F, x, v, nrhs);
+  for (int c = 0; c < nrhs; c++) {
+    double *vc = v + (size_t)c * n;
+    if (trans) { /* the W product, as in orc_apply */
+      for (int i = 0; i < F->nbox; i++) {
+        obox *b = &F->box[i];
+        for (int si = 0; si < b->k; si++) {
+          double s = 0.0;
+          for (int ri = 0; ri < b->r; ri++) s += b->T[(size_t)ri * b->k + si] * vc[b->R[ri]];
+          vc[b->S[si]] += s;
+        }
+        for (int ri = 0; ri < b->r; ri++) {
+          double s = 0.0;
+          for (int a = 0; a < b->nj; a++) s += b->G[(size_t)ri * b->nj + a] * vc[b->J[a]];
+          vc[b->R[ri]] += s;
+        }
+      }
+    }
+    /* the Cholesky blocks: L (trans = 0) or L^T (trans = 1) */
+    for (int i = 0; i <= F->nbox; i++) {
+      int r = i < F->nbox ? F->box[i].r : F->ntop;
+      const int64_t *ids = i < F->nbox ? F->box[i].R : F->top;
+      const double *L = F->chol[i];
+      double *t = malloc(sizeof(double) * (r + 1));
+      for (int a = 0; a < r; a++) {
+        double s = 0.0;
+        for (int l = 0; l < r; l++) s += (trans ? L[(size_t)l * r + a] : L[(size_t)a * r + l]) * vc[ids[l]];
+        t[a] = s;
+      }
+      for (int a = 0; a < r; a++) vc[ids[a]] = t[a];
+      free(t);
+    }
+    if (!trans) { /* the V product, as in orc_apply */
+      for (int i = F->nbox - 1; i >= 0; i--) {
+        obox *b = &F->box[i];
+        for (int a = 0; a < b->nj; a++) {
+          double s = 0.0;
+          for (int ri = 0; ri < b->r; ri++) s += b->E[(size_t)a * b->r + ri] * vc[b->R[ri]];
+          vc[b->J[a]] += s;
+        }
+        for (int ri = 0; ri < b->r; ri++) {
+          double s = 0.0;
+          for (int si = 0; si < b->k; si++) s += b->T[(size_t)ri * b->k + si] * vc[b->S[si]];
+          vc[b->R[ri]] += s;
+        }
+      }
+    }
+  }
+  from_tree(F, v, y, nrhs);
   free(v);
 }
 

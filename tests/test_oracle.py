@@ -566,3 +566,40 @@ def test_parallel_phases_with_2d_colours():
         assert not np.array_equal(f0.apply(x), f2.apply(x))
         fe = oracle.Factor(tr, kind, 1e-14, schedule=2)
         assert np.linalg.norm(fe.apply(x) - Ax) / np.linalg.norm(Ax) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# generalized square root (the remark after Eq. 3.11)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("hybrid", [False, True])
+def test_square_root_reproduces_the_factor(hybrid):
+    """K positive definite (second kind here: eigenvalues near 1): with the
+    Cholesky blocks of D, F^{1/2} (F^{1/2})^T applies F itself, for RS-S and
+    RS-WS alike."""
+    for pts, kind, eps, leaf in _schedule_problems():
+        f = oracle.Factor(oracle.Tree(pts, leaf), kind, eps, hybrid=hybrid)
+        x = inputs.normal(19, len(pts))
+        Fx = f.apply(x)
+        SSx = f.sqrt_apply(f.sqrt_apply(x, transpose=True))
+        assert np.linalg.norm(SSx - Fx) / np.linalg.norm(Fx) < 1e-13
+
+
+def test_square_root_exact_limit():
+    """eps -> 0: F = A, so F^{1/2} is a square root of A up to an orthogonal
+    factor (the paper's remark): ||(F^{1/2})^T x||^2 = x^T A x."""
+    for pts, kind, _, leaf in _schedule_problems():
+        f = oracle.Factor(oracle.Tree(pts, leaf), kind, 1e-14)
+        A = oracle.dense_matrix(pts, kind)
+        x = inputs.normal(20, len(pts))
+        q = float(np.sum(f.sqrt_apply(x, transpose=True) ** 2))
+        assert q == pytest.approx(float(x @ A @ x), rel=1e-12)
+
+
+def test_square_root_needs_a_definite_matrix():
+    """A negative definite matrix (diagonal -1, small off-diagonal) has no
+    real Cholesky blocks: the square root is refused, not silently wrong."""
+    pts = inputs.grid_points(32, 2)
+    f = oracle.Factor(oracle.Tree(pts, 64), 0, 1e-6, diag=-1.0)
+    with pytest.raises(ValueError):
+        f.sqrt_apply(inputs.normal(21, len(pts)))
