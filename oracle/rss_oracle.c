@@ -136,7 +136,7 @@ static void split(otree *T, const double *pts, int64_t *idx, int64_t *tmp, int n
     for (int d = 0; d < T->dim; d++) ch |= (int)(cellc(p[d], t + 1) & 1) << d;
     cnt[ch]++;
   }
-  int64_t off[8];
+  int64_t off[8] = {0};
   int64_t acc = s;
   for (int ch = 0; ch < nch; ch++) {
     off[ch] = acc;
