@@ -62,7 +62,7 @@ def _setup(L):
     L.orc_lu.argtypes = [_dp, C.c_int, _ip]
     L.orc_factor.restype = C.c_void_p
     L.orc_factor.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
-                             C.c_double, C.c_int, C.c_int, C.c_int]
+                             C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
     L.orc_factor_free.argtypes = [C.c_void_p]
     L.orc_factor_info.restype = C.c_int64
     L.orc_factor_info.argtypes = [C.c_void_p, C.c_int]
@@ -185,18 +185,19 @@ class Factor:
     """RS-S factor of A = diag*I + w*K on the tree's points (Algorithm 1);
     hybrid=True: the RS-WS factor (Sec. 3.4, Algorithm 2).  schedule: 0 one
     box after another; 1 / 2 each colour phase as a parallel machine runs it,
-    with 3^d / 2^d colours (Sec. 5; see ``orc_factor``)."""
+    with 3^d / 2^d colours (Sec. 5; see ``orc_factor``).  cholesky=True:
+    X_RR and the top block by Cholesky (positive definite K) and G = E^T."""
 
     def __init__(self, tree: Tree, kind: int, eps: float, diag: float = 1.0, w: float | None = None,
                  nproxy: int = 0, radius: float = 2.5, check: bool = False, hybrid: bool = False,
-                 schedule: int = 0):
+                 schedule: int = 0, cholesky: bool = False):
         self.tree = tree
         self.kind = kind
         self.diag = diag
         self.w = (1.0 / tree.n) if w is None else w
         self.eps = eps
         self.h = lib().orc_factor(tree.h, kind, diag, self.w, eps, nproxy, radius, int(check), int(hybrid),
-                                  int(schedule))
+                                  int(schedule), int(cholesky))
         L = lib()
         self.nbox = L.orc_factor_info(self.h, 0)
         self.ntop = L.orc_factor_info(self.h, 1)

@@ -423,6 +423,37 @@ int orc_lu(double *A, int n, int *piv) {
 }
 
 /* Solve (P^T L U) X = B for X, B n x nrhs column-major (overwritten). */
+/* Cholesky X = L L^T of a symmetric positive definite X (n x n, row-major,
+ * symmetric part used), stored in the LU layout so that every LU routine
+ * applies it: unit lower L D^{-1} below the diagonal, U = D L^T on and above
+ * it (D = diag(L)), identity pivots.  Returns 0, or j+1 if the leading
+ * block of order j+1 is not positive definite. */
+static int chol_as_lu(double *X, int n, int *piv) {
+  for (int i = 0; i < n; i++) piv[i] = i;  /* valid even when it fails */
+  double *L = calloc((size_t)n * n + 1, sizeof(double));
+  for (int j = 0; j < n; j++) {
+    double d = X[(size_t)j * n + j];
+    for (int l = 0; l < j; l++) d -= L[(size_t)j * n + l] * L[(size_t)j * n + l];
+    if (!(d > 0.0)) {
+      free(L);
+      return j + 1;
+    }
+    L[(size_t)j * n + j] = sqrt(d);
+    for (int i = j + 1; i < n; i++) {
+      double s = 0.5 * (X[(size_t)i * n + j] + X[(size_t)j * n + i]);
+      for (int l = 0; l < j; l++) s -= L[(size_t)i * n + l] * L[(size_t)j * n + l];
+      L[(size_t)i * n + j] = s / L[(size_t)j * n + j];
+    }
+  }
+  for (int i = 0; i < n; i++) {
+    for (int j = 0; j < n; j++)
+      X[(size_t)i * n + j] = i > j ? L[(size_t)i * n + j] / L[(size_t)j * n + j]
+                                   : L[(size_t)j * n + i] * L[(size_t)i * n + i];
+  }
+  free(L);
+  return 0;
+}
+
 static void lu_solve(const double *LU, const int *piv, int n, double *B, int nrhs) {
   double *y = malloc(sizeof(double) * (n > 0 ? n : 1));
   for (int c = 0; c < nrhs; c++) {
@@ -552,7 +583,7 @@ static void proxy_points(int dim, int np, double radius, int t, const int *coord
  * active; plus a last weak pass at depth 1, where no strong step is
  * possible, as the paper does in practice. */
 void *orc_factor(void *th, int kind, double diag, double w, double eps, int nproxy,
-                 double radius, int check, int hybrid, int schedule) {
+                 double radius, int check, int hybrid, int schedule, int chol) {
   otree *T = th;
   int64_t n = T->n;
   int dim = T->dim;
@@ -746,21 +777,29 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
       bx->piv = malloc(sizeof(int) * (r + 1));
       for (int i = 0; i < r; i++)
         for (int j = 0; j < r; j++) bx->LU[(size_t)i * r + j] = A[R[i] * n + R[j]];
-      int info = orc_lu(bx->LU, r, bx->piv);
+      /* LU with partial pivoting, or Cholesky for positive definite K
+       * (Sec. 4: the paper's choice for its diagonal blocks) */
+      int info = chol ? chol_as_lu(bx->LU, r, bx->piv) : orc_lu(bx->LU, r, bx->piv);
       if (info && !F->info) F->info = info;
       bx->E = malloc(sizeof(double) * ((size_t)nj * r + 1));
       bx->G = malloc(sizeof(double) * ((size_t)r * nj + 1));
       for (int a = 0; a < nj; a++)
         for (int ri = 0; ri < r; ri++) bx->E[(size_t)a * r + ri] = A[J[a] * n + R[ri]];
       lu_solve_right(bx->LU, bx->piv, r, bx->E, nj);
-      /* G column-major scratch (r x nj), then stored row-major */
-      double *Gc = malloc(sizeof(double) * ((size_t)r * nj + 1));
-      for (int a = 0; a < nj; a++)
-        for (int ri = 0; ri < r; ri++) Gc[(size_t)a * r + ri] = A[R[ri] * n + J[a]];
-      lu_solve(bx->LU, bx->piv, r, Gc, nj);
-      for (int ri = 0; ri < r; ri++)
-        for (int a = 0; a < nj; a++) bx->G[(size_t)ri * nj + a] = Gc[(size_t)a * r + ri];
-      free(Gc);
+      if (chol) {
+        /* symmetric K: G = E^T (Sec. 3.3.3, V_i = W_i^T); only E is needed */
+        for (int ri = 0; ri < r; ri++)
+          for (int a = 0; a < nj; a++) bx->G[(size_t)ri * nj + a] = bx->E[(size_t)a * r + ri];
+      } else {
+        /* G column-major scratch (r x nj), then stored row-major */
+        double *Gc = malloc(sizeof(double) * ((size_t)r * nj + 1));
+        for (int a = 0; a < nj; a++)
+          for (int ri = 0; ri < r; ri++) Gc[(size_t)a * r + ri] = A[R[ri] * n + J[a]];
+        lu_solve(bx->LU, bx->piv, r, Gc, nj);
+        for (int ri = 0; ri < r; ri++)
+          for (int a = 0; a < nj; a++) bx->G[(size_t)ri * nj + a] = Gc[(size_t)a * r + ri];
+        free(Gc);
+      }
       /* Schur complement A_JJ -= E A_RJ, then decouple R */
       for (int a = 0; a < nj; a++)
         for (int c = 0; c < nj; c++) {
@@ -793,7 +832,7 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
   F->pivtop = malloc(sizeof(int) * (nt + 1));
   for (int64_t i = 0; i < nt; i++)
     for (int64_t j = 0; j < nt; j++) F->LUtop[i * nt + j] = A[F->top[i] * n + F->top[j]];
-  int info = orc_lu(F->LUtop, (int)nt, F->pivtop);
+  int info = chol ? chol_as_lu(F->LUtop, (int)nt, F->pivtop) : orc_lu(F->LUtop, (int)nt, F->pivtop);
   if (info && !F->info) F->info = info;
 
   if (check) {

@@ -603,3 +603,36 @@ def test_square_root_needs_a_definite_matrix():
     f = oracle.Factor(oracle.Tree(pts, 64), 0, 1e-6, diag=-1.0)
     with pytest.raises(ValueError):
         f.sqrt_apply(inputs.normal(21, len(pts)))
+
+
+def test_cholesky_variant():
+    """Positive definite K: X_RR and the top block by Cholesky (the paper's
+    choice for D in that case) give the factor of the LU variant up to
+    rounding and the same log det; G = E^T exactly (one of the two need be
+    stored); eps -> 0 is still exact; invariants hold."""
+    for pts, kind, eps, leaf in _schedule_problems():
+        n = len(pts)
+        tr = oracle.Tree(pts, leaf)
+        A = oracle.dense_matrix(pts, kind)
+        x = inputs.normal(22, n)
+        fl = oracle.Factor(tr, kind, eps)
+        fc = oracle.Factor(tr, kind, eps, cholesky=True, check=True)
+        assert fc.info == 0 and fc.violations == 0
+        yl = fl.apply(x)
+        assert np.linalg.norm(fc.apply(x) - yl) / np.linalg.norm(yl) < 1e-12
+        assert abs(fc.logdet() - fl.logdet()) < 1e-10 * max(1.0, abs(fl.logdet()))
+        for i in range(fc.nbox):
+            d = fc.box_data(i)
+            assert np.array_equal(d["G"], d["E"].T)
+        fe = oracle.Factor(tr, kind, 1e-14, cholesky=True)
+        Ax = A @ x
+        assert np.linalg.norm(fe.apply(x) - Ax) / np.linalg.norm(Ax) < 1e-12
+        assert np.linalg.norm(fe.solve(Ax) - x) / np.linalg.norm(x) < 1e-11
+
+
+def test_cholesky_refuses_an_indefinite_block():
+    """A negative definite matrix: the first Cholesky block fails and the
+    factor reports it (info != 0) instead of storing garbage."""
+    pts = inputs.grid_points(32, 2)
+    f = oracle.Factor(oracle.Tree(pts, 64), 0, 1e-6, diag=-1.0, cholesky=True)
+    assert f.info != 0
