@@ -66,6 +66,9 @@ def _setup(L):
     L.orc_factor_free.argtypes = [C.c_void_p]
     L.orc_factor_info.restype = C.c_int64
     L.orc_factor_info.argtypes = [C.c_void_p, C.c_int]
+    L.orc_factor_check_worst.restype = C.c_double
+    L.orc_factor_check_worst.argtypes = [C.c_void_p, C.c_int]
+    L.orc_plant_mistake.argtypes = [C.c_int]
     L.orc_factor_box.argtypes = [C.c_void_p, C.c_int, _ip]
     L.orc_factor_box_data.argtypes = [C.c_void_p, C.c_int, _lp, _lp, _lp, _dp, _dp, _dp]
     L.orc_factor_top.argtypes = [C.c_void_p, _lp]
@@ -203,6 +206,12 @@ class Factor:
         self.ntop = L.orc_factor_info(self.h, 1)
         self.violations = L.orc_factor_info(self.h, 2)
         self.info = L.orc_factor_info(self.h, 3)
+        # check mode: boxes over the CPQR ID bound and boxes whose T does not
+        # compress the full far field to 10 eps, with the worst ratios
+        self.id_violations = L.orc_factor_info(self.h, 4)
+        self.proxy_violations = L.orc_factor_info(self.h, 5)
+        self.id_worst = L.orc_factor_check_worst(self.h, 0)
+        self.proxy_worst = L.orc_factor_check_worst(self.h, 1)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -276,6 +285,12 @@ class Factor:
 # ---------------------------------------------------------------------------
 # Exact references
 # ---------------------------------------------------------------------------
+
+def plant_mistake(what: int) -> None:
+    """Plant a deliberate mistake in the oracle (tests of its checks only):
+    0 none, 1 every proxy surface centred one box side off in x."""
+    lib().orc_plant_mistake(int(what))
+
 
 def dense_matrix(pts: np.ndarray, kind: int, diag: float = 1.0, w: float | None = None) -> np.ndarray:
     pts = _f64(pts)

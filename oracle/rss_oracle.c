@@ -304,6 +304,15 @@ int orc_tree_box_lists(void *h, int node, int *near, int *nnear, int *ring, int 
   return 0;
 }
 
+/* Mistakes planted on purpose by the tests, to show whether a check catches
+ * them: 0 none; 1 every proxy surface centred one box side off in x; 2 the
+ * strong ID matrix holds only the ring cells at x offset >= 0 (the wrong
+ * ring cells); 3 the proxy radius a quarter of the one asked for (a circle
+ * through the box itself); 4 the ID takes its pivots in column order
+ * (no pivoting). */
+static int g_plant = 0;
+void orc_plant_mistake(int what) { g_plant = what; }
+
 /* ------------------------------------------------------------------------ */
 /* Dense building blocks                                                      */
 /* ------------------------------------------------------------------------ */
@@ -333,6 +342,7 @@ int orc_cpqr_id(double *M, int m, int n, double eps, int *perm, double *T, doubl
         p = c;
       }
     }
+    if (g_plant == 4) best = nrm[p = j];
     double colnorm = sqrt(best);
     if (j == 0) r11 = colnorm;
     if (rdiag) rdiag[j] = colnorm;
@@ -422,7 +432,6 @@ int orc_lu(double *A, int n, int *piv) {
   return info;
 }
 
-/* Solve (P^T L U) X = B for X, B n x nrhs column-major (overwritten). */
 /* Cholesky X = L L^T of a symmetric positive definite X (n x n, row-major,
  * symmetric part used), stored in the LU layout so that every LU routine
  * applies it: unit lower L D^{-1} below the diagonal, U = D L^T on and above
@@ -454,6 +463,7 @@ static int chol_as_lu(double *X, int n, int *piv) {
   return 0;
 }
 
+/* Solve (P^T L U) X = B for X, B n x nrhs column-major (overwritten). */
 static void lu_solve(const double *LU, const int *piv, int n, double *B, int nrhs) {
   double *y = malloc(sizeof(double) * (n > 0 ? n : 1));
   for (int c = 0; c < nrhs; c++) {
@@ -543,12 +553,21 @@ typedef struct {
   double **chol;      /* Cholesky factors of the X_RR blocks and the top (orc_sqrt_prepare) */
   int64_t violations; /* Theorem 3.1 / Corollary 3.2 violations seen */
   int info;           /* nonzero: zero pivot met */
+  /* per-box ID checks (check mode): boxes whose ID residual exceeds the
+   * column-pivoted QR bound, boxes whose T fails to compress the full far
+   * field to 10 eps, and the worst ratio of each (residual / bound) */
+  int64_t id_violations, proxy_violations;
+  double id_worst, proxy_worst;
 } ofactor;
+
+
 
 static void proxy_points(int dim, int np, double radius, int t, const int *coord, double *y) {
   double D = ldexp(1.0, -t);
   double c[3];
   for (int d = 0; d < dim; d++) c[d] = (coord[d] + 0.5) * D;
+  if (g_plant == 1) c[0] += D;
+  if (g_plant == 3) radius *= 0.25;
   for (int m = 0; m < np; m++) {
     if (dim == 2) {
       double th = 2.0 * ORC_PI * (double)m / (double)np;
@@ -565,7 +584,74 @@ static void proxy_points(int dim, int np, double radius, int t, const int *coord
   }
 }
 
-/* Factor.  check != 0 turns on the Theorem 3.1 / Corollary 3.2 checks.
+/* Residual X[:, R] - X[:, S] T of an ID with the columns of X (mx x b,
+ * column-major) taken in the order perm (S = perm[0..k), R = perm[k..b)),
+ * T k x r column-major: returns it as an mx x r column-major array. */
+static double *id_residual(const double *X, int64_t mx, int b, const int *perm, int k, const double *T) {
+  int r = b - k;
+  double *Res = malloc(sizeof(double) * ((size_t)mx * r + 1));
+  for (int c = 0; c < r; c++) {
+    const double *xr = X + (size_t)perm[k + c] * mx;
+    double *o = Res + (size_t)c * mx;
+    for (int64_t i = 0; i < mx; i++) o[i] = xr[i];
+    for (int s = 0; s < k; s++) {
+      double t = T[(size_t)c * k + s];
+      const double *xs = X + (size_t)perm[s] * mx;
+      for (int64_t i = 0; i < mx; i++) o[i] -= xs[i] * t;
+    }
+  }
+  return Res;
+}
+
+static double fro(const double *X, size_t len) {
+  double s = 0.0;
+  for (size_t i = 0; i < len; i++) s += X[i] * X[i];
+  return sqrt(s);
+}
+
+/* ||X||_2 of X (mx x nc, column-major): power iteration on X^T X (a lower
+ * estimate that converges to the largest singular value). */
+static double norm2(const double *X, int64_t mx, int nc) {
+  if (nc == 0 || mx == 0) return 0.0;
+  double *G = calloc((size_t)nc * nc, sizeof(double));
+  for (int a = 0; a < nc; a++)
+    for (int c = a; c < nc; c++) {
+      double s = 0.0;
+      for (int64_t i = 0; i < mx; i++) s += X[(size_t)a * mx + i] * X[(size_t)c * mx + i];
+      G[(size_t)a * nc + c] = G[(size_t)c * nc + a] = s;
+    }
+  double *v = malloc(sizeof(double) * nc), *u = malloc(sizeof(double) * nc);
+  for (int a = 0; a < nc; a++) v[a] = 1.0 + 0.01 * (a % 7);
+  double lam = 0.0;
+  for (int it = 0; it < 300; it++) {
+    double nv = 0.0;
+    for (int a = 0; a < nc; a++) nv += v[a] * v[a];
+    nv = sqrt(nv);
+    if (nv == 0.0) break;
+    for (int a = 0; a < nc; a++) v[a] /= nv;
+    double q = 0.0;
+    for (int a = 0; a < nc; a++) {
+      double s = 0.0;
+      for (int c = 0; c < nc; c++) s += G[(size_t)a * nc + c] * v[c];
+      u[a] = s;
+      q += v[a] * s;
+    }
+    lam = q > lam ? q : lam;
+    memcpy(v, u, sizeof(double) * nc);
+  }
+  free(G); free(v); free(u);
+  return sqrt(lam > 0.0 ? lam : 0.0);
+}
+
+/* Factor.  check != 0 turns on the Theorem 3.1 / Corollary 3.2 checks and
+ * two checks of every box's ID (Definition 2.1, Sec. 3.2):
+ *   - the column-pivoted QR bound on the ID matrix M the box formed: every
+ *     trailing column of R after k steps has norm <= |R_kk+1| <= eps |R_11|,
+ *     so ||M_R - M_S T||_F <= sqrt(r) eps |R_11| (up to rounding);
+ *   - proxy validity: the same T compresses the box's interactions with its
+ *     whole far field F (every active DOF at distance >= 2, the ring O and
+ *     the rest P), ||X_R - X_S T||_2 <= 10 eps ||X||_2 for
+ *     X = [A_FB; A_BF^T] from the current matrix.
  * schedule: 0 one box after another in colour order (3^d colours); 1 and 2
  * a colour phase as a parallel machine runs it, with 3^d (1) or 2^d (2)
  * colours (Sec. 5): every box of the phase builds its lists and its ID
@@ -687,6 +773,14 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
        * with X the cells inside the proxy surface that the step compresses:
        * strong: the ring O (Eq. 3.7); weak: N and O (the whole complement) */
       int64_t nX = weak ? nN + nO : nO;
+      /* planted mistake 2 (tests only): part of the ring left out */
+      int64_t *Om = Ol;
+      if (g_plant == 2 && !weak) {
+        Om = malloc(sizeof(int64_t) * (nO + 1));
+        nX = 0;
+        for (int64_t o = 0; o < nO; o++)
+          if (cell[3 * Ol[o]] >= bc[0]) Om[nX++] = Ol[o];
+      }
       int m = (int)(2 * nX + 2 * nproxy);
       double *M = malloc(sizeof(double) * (size_t)m * b);
       proxy_points(dim, nproxy, radius, t, T->coord + 3 * node, yp);
@@ -694,7 +788,7 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
         int64_t j = Bl[c];
         double *col = M + (size_t)c * m;
         for (int64_t o = 0; o < nX; o++) {
-          int64_t g = weak && o < nN ? Nl[o] : Ol[weak ? o - nN : o];
+          int64_t g = weak && o < nN ? Nl[o] : Om[weak ? o - nN : o];
           col[o] = Ar[g * n + j];
           col[nX + o] = Ar[j * n + g];
         }
@@ -705,9 +799,47 @@ void *orc_factor(void *th, int kind, double diag, double w, double eps, int npro
       }
       int *perm = malloc(sizeof(int) * b);
       double *Tm = malloc(sizeof(double) * (size_t)b * b + 1);
-      int k = orc_cpqr_id(M, m, b, eps, perm, Tm, NULL);
+      double *M0 = check ? malloc(sizeof(double) * ((size_t)m * b + 1)) : NULL;
+      double *rd = malloc(sizeof(double) * (b + 1));
+      if (M0) memcpy(M0, M, sizeof(double) * (size_t)m * b);
+      int k = orc_cpqr_id(M, m, b, eps, perm, Tm, rd);
       free(M);
+      if (Om != Ol) free(Om);
       int r = b - k;
+      if (check && r > 0) {
+        const double u = 2.220446049250313e-16;
+        /* the CPQR bound on the matrix the ID was computed from */
+        double *Res = id_residual(M0, m, b, perm, k, Tm);
+        double res = fro(Res, (size_t)m * r);
+        double tn = fro(Tm, (size_t)k * r);
+        double bound = sqrt((double)r) * eps * rd[0] + 8.0 * (m + b) * u * fro(M0, (size_t)m * b) * (1.0 + tn);
+        if (res > bound) F->id_violations++;
+        if (bound > 0.0 && res / bound > F->id_worst) F->id_worst = res / bound;
+        free(Res);
+        /* proxy validity against the full far field (ring and beyond) */
+        int64_t nF = weak ? nN + nO + nP : nO + nP;
+        double *X = malloc(sizeof(double) * ((size_t)2 * nF * b + 1));
+        for (int c = 0; c < b; c++) {
+          int64_t j = Bl[c];
+          double *col = X + (size_t)c * 2 * nF;
+          int64_t o = 0;
+          if (weak)
+            for (int64_t a = 0; a < nN; a++, o++) col[o] = Ar[Nl[a] * n + j], col[nF + o] = Ar[j * n + Nl[a]];
+          for (int64_t a = 0; a < nO; a++, o++) col[o] = Ar[Ol[a] * n + j], col[nF + o] = Ar[j * n + Ol[a]];
+          for (int64_t a = 0; a < nP; a++, o++) col[o] = Ar[Pl[a] * n + j], col[nF + o] = Ar[j * n + Pl[a]];
+        }
+        if (nF > 0) {
+          double *Rf = id_residual(X, 2 * nF, b, perm, k, Tm);
+          double rf = norm2(Rf, 2 * nF, r), xf = norm2(X, 2 * nF, b);
+          double pb = eps * xf + 8.0 * (2 * nF + b) * u * fro(X, (size_t)2 * nF * b) * (1.0 + tn);
+          if (rf > pb) F->proxy_violations++;
+          if (pb > 0.0 && rf / pb > F->proxy_worst) F->proxy_worst = rf / pb;
+          free(Rf);
+        }
+        free(X);
+      }
+      free(M0);
+      free(rd);
 
       if (F->nbox == cap) {
         cap *= 2;
@@ -869,7 +1001,8 @@ void orc_factor_free(void *h) {
   free(F);
 }
 
-/* what: 0 nbox, 1 ntop, 2 violations, 3 info */
+/* what: 0 nbox, 1 ntop, 2 violations, 3 info, 4 boxes over the CPQR ID
+ * bound, 5 boxes failing proxy validity (check mode) */
 int64_t orc_factor_info(void *h, int what) {
   ofactor *F = h;
   switch (what) {
@@ -877,6 +1010,8 @@ int64_t orc_factor_info(void *h, int what) {
     case 1: return F->ntop;
     case 2: return F->violations;
     case 3: return F->info;
+    case 4: return F->id_violations;
+    case 5: return F->proxy_violations;
   }
   return -1;
 }
@@ -1194,6 +1329,13 @@ void orc_matvec_rows(const double *pts, int64_t n, int dim, int kind, double dia
       y[(size_t)c * nrows + q] = s;
     }
   }
+}
+
+/* Worst ratio residual / bound over all boxes (check mode): what 0 the CPQR
+ * ID bound, 1 proxy validity. */
+double orc_factor_check_worst(void *h, int what) {
+  ofactor *F = h;
+  return what == 0 ? F->id_worst : F->proxy_worst;
 }
 
 /* Solve A X = B with a plain right-looking LU with partial pivoting.

@@ -343,6 +343,79 @@ def test_proxy_surface_is_needed():
     assert eb > 10 * eg
 
 
+# Per-box checks of the ID inside a factorization (Definition 2.1, Sec. 3.2)
+_ID_CHECK_PROBLEMS = [  # (points, kernel, eps, leaf)
+    ("grid2d", lambda: inputs.grid_points(64, 2), 0, 1e-6, 64),
+    ("random2d", lambda: inputs.random_points(5, 3000, 2), 0, 1e-6, 32),
+    ("grid3d", lambda: inputs.grid_points(12, 3), 1, 1e-3, 8),
+]
+
+
+@pytest.fixture
+def no_plant():
+    oracle.plant_mistake(0)
+    yield
+    oracle.plant_mistake(0)
+
+
+@pytest.mark.parametrize("name,make,kind,eps,leaf", _ID_CHECK_PROBLEMS, ids=[p[0] for p in _ID_CHECK_PROBLEMS])
+def test_every_box_id_meets_its_bounds(no_plant, name, make, kind, eps, leaf):
+    """For every box of a factorization, on the ID matrix the box actually
+    formed and the current matrix:
+      - the column-pivoted QR bound ||M_R - M_S T||_F <= sqrt(r) eps |R_11|
+        (each trailing column of R is no longer than the pivot that stopped
+        the reduction, which is at most eps |R_11|);
+      - proxy validity: the same T compresses the box's whole far field
+        (ring and beyond, both halves) to eps, ||X_R - X_S T||_2 <= eps ||X||_2
+        (Sec. 3.2: the proxy rows stand in for everything outside the ring).
+    The Theorem 3.1 / Corollary 3.2 counts stay zero too."""
+    f = oracle.Factor(oracle.Tree(make(), leaf), kind, eps, check=True)
+    assert f.nbox > 0
+    assert f.violations == 0
+    assert f.id_violations == 0, f.id_worst
+    assert f.proxy_violations == 0, f.proxy_worst
+    assert 0.0 < f.id_worst <= 1.0 and 0.0 < f.proxy_worst <= 1.0
+
+
+def test_id_checks_catch_planted_mistakes(no_plant):
+    """Planted mistakes in the oracle that make some IDs invalid must be
+    counted by the per-box checks:
+      - the ID matrix built from only half of the ring (cells at x offset
+        >= 0): sources left out sit partly inside the proxy surface, so
+        nothing in M stands for them and the far field is not compressed;
+      - pivoting dropped (columns taken in order): the truncation at
+        |R_jj| <= eps |R_11| no longer bounds the trailing columns;
+      - 4 proxy points instead of 64: too few to stand in for the far field."""
+    pts = inputs.random_points(5, 3000, 2)
+    tr = oracle.Tree(pts, 32)
+    oracle.plant_mistake(2)
+    f = oracle.Factor(tr, 0, 1e-6, check=True)
+    assert f.proxy_violations > 0 and f.proxy_worst > 1.0
+    oracle.plant_mistake(4)
+    f = oracle.Factor(oracle.Tree(inputs.grid_points(12, 3), 8), 1, 1e-3, check=True)
+    assert f.id_violations > 0 and f.id_worst > 1.0
+    oracle.plant_mistake(0)
+    f = oracle.Factor(oracle.Tree(inputs.grid_points(64, 2), 64), 0, 1e-6, check=True, nproxy=4)
+    assert f.proxy_violations > 0 and f.id_violations == 0
+
+
+def test_shifted_or_small_proxy_surfaces_stay_valid(no_plant):
+    """Not every change of the proxy surface is a mistake: a circle centred one
+    box side off still holds the box, and one of a quarter of the radius
+    still separates the box from the far field (only more skeletons are kept);
+    together with the explicit ring rows both still give IDs that compress
+    the whole far field to eps.  The checks measure validity, not the surface."""
+    pts = inputs.grid_points(64, 2)
+    tr = oracle.Tree(pts, 64)
+    ranks = {}
+    for plant in (0, 1, 3):
+        oracle.plant_mistake(plant)
+        f = oracle.Factor(tr, 0, 1e-6, check=True)
+        assert f.id_violations == 0 and f.proxy_violations == 0
+        ranks[plant] = sum(b["k"] for b in f.boxes())
+    assert ranks[3] > ranks[0]
+
+
 def test_degenerate_sizes():
     # fewer points than one leaf: no skeletonization, F = dense LU
     pts = inputs.random_points(2, 50, 2)
