@@ -79,6 +79,22 @@ typedef struct {
 /* Use the built-in launch shapes instead of the autotuner's choices (see
  * rss_autotune_table). */
 #define RSS_FLAG_NO_AUTOTUNE 2
+/* The paper's parallel schedule with 2^dim colours per level (Sec. 5: boxes
+ * of one colour are two or more cells apart) instead of the default 3^dim
+ * colours.  Boxes of one colour phase are skeletonized at once from the
+ * state at the phase start: each one's ID sees the other boxes of the phase
+ * still whole in its ring, and two boxes may share near-field blocks, whose
+ * Schur-complement updates (and the solve's and apply's updates of shared
+ * near-field entries) are added atomically.  The result is a different but
+ * equally valid factorization, with 2^dim instead of 3^dim phases per level;
+ * the order of the atomic additions makes it reproducible only up to
+ * rounding.  rss_tree_query keeps reporting the 3^dim order. */
+#define RSS_FLAG_COLOUR_2D 4
+/* Run the FP32 factor's Schur-complement updates on the FP32 SIMT units
+ * instead of the tensor cores (which use a three-product TF32 split that
+ * keeps FP32 accuracy); the same factorization up to rounding.  For
+ * comparisons; the FP64 factor always uses FP64 SIMT arithmetic. */
+#define RSS_FLAG_NO_TENSOR_CORES 8
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;
@@ -152,17 +168,20 @@ rss_status rss_solve(const rss_factorization *f, const double *b, double *x, int
  * that keep a fixed memory budget inside a hot loop and cannot afford an
  * allocation's cost or failure there.  rss_solve may allocate a working
  * vector on its first use with a given number of right-hand sides; this
- * variant never does.  The paper has no counterpart: it is an operational
- * variant of the solve of Eq. 3.11.
+ * variant never does.  The paper has no counterpart to this entry point.
  *   Working space is one fixed 16 MiB array in device memory that exists
  *   once per device from the moment the library is loaded until the process
- *   exits.  It must hold the n x nrhs working vector plus 2 * ntop * nrhs
- *   entries for the top block, in the factor's precision (4 bytes for a
- *   RSS_MIXED factor, 8 for RSS_FP64); larger requests return RSS_EINVAL
- *   without doing any work.  Nothing in it needs to start at zero: every
- *   call overwrites what it reads.
+ *   exits.  The columns are solved in passes (as rss_solve does, at most as
+ *   many columns as the sweep kernels' shared memory takes, and fewer if the
+ *   array needs it); a pass of c columns keeps n x c plus 2 * ntop * c
+ *   entries there, in the factor's precision (4 bytes for a RSS_MIXED
+ *   factor, 8 for RSS_FP64).  If a single column does not fit (about 4.19 M
+ *   points for RSS_MIXED, 2.09 M for RSS_FP64, less twice the top-block
+ *   size), the call returns RSS_EINVAL without doing any work.  Nothing in
+ *   the array needs to start at zero: every pass overwrites what it reads.
  *   The first call made with a given device current looks up the array's
- *   device address (cudaGetSymbolAddress); make that first call before any
+ *   device address (cudaGetSymbolAddress) and raises the sweep kernels'
+ *   shared-memory limits on that device; make that first call before any
  *   stream capture begins.
  *   Every call uses the same array: calls whose work overlaps on the GPU
  *   (different streams, different host threads) race and give wrong
@@ -186,6 +205,23 @@ rss_status rss_solve_noalloc(const rss_factorization *f, const double *b, double
  * (x then holds the last iterate). */
 rss_status rss_solve_refined(const rss_factorization *f, const double *b, double *x, int nrhs, double tol,
                              int maxit, int *iters, double *relres);
+
+/* rss_solve_cg -- solve A x = b to a relative residual
+ * max_c ||b_c - A x_c|| / ||b_c|| <= tol by conjugate gradients
+ * preconditioned with the factor, the paper's iterative solver for its
+ * examples (Sec. 4; A and F are symmetric for these kernels, V_i = W_i^T):
+ * x0 = F^{-1} b, FP64 vectors and residuals with the exact operator
+ * (rss_matvec), z = F^{-1} r as preconditioner (FP32 for a RSS_MIXED factor;
+ * beta in the flexible Polak-Ribiere form, which tolerates the FP32 factor's
+ * small asymmetry).  The true residual is checked when the recurrence
+ * residual meets tol, and CG restarts from x if it does not.
+ *   b, x: device, n x nrhs column-major, may not alias.  maxit: iterations
+ *   (>= 0).  iters (may be NULL): iterations taken; relres (may be NULL):
+ *   final true relative residual (max over columns).
+ * Errors: RSS_EINVAL; RSS_ENOTCONV when tol is not met within maxit
+ * (x then holds the last iterate). */
+rss_status rss_solve_cg(const rss_factorization *f, const double *b, double *x, int nrhs, double tol, int maxit,
+                        int *iters, double *relres);
 
 /* rss_matvec -- y = A x in FP64 with the exact operator being factored:
  * an FFT convolution when the points are the cell centres of an s^dim grid

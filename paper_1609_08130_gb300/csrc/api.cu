@@ -18,6 +18,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -381,11 +382,14 @@ struct HTree {
   std::vector<std::vector<int>> level;  // boxes per depth, elimination order
 };
 
-static int colour_of(const int *c, int dim) {
+// Colour of a cell: sum_d (c_d mod base) base^d.  Base 3 (the default) puts
+// same-colour cells >= 3 apart; base 2 is the paper's schedule (Sec. 5),
+// same-colour cells >= 2 apart.
+static int colour_of(const int *c, int dim, int base = 3) {
   int col = 0, mul = 1;
   for (int d = 0; d < dim; d++) {
-    col += (c[d] % 3) * mul;
-    mul *= 3;
+    col += (c[d] % base) * mul;
+    mul *= base;
   }
   return col;
 }
@@ -603,7 +607,7 @@ static int find_key(const std::vector<uint64_t> &keys, uint64_t k) {
   return (int)(it - keys.begin());
 }
 
-static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &active) {
+static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &active, int cbase = 3) {
   HLevel L;
   L.t = t;
   L.dim = T.dim;
@@ -752,7 +756,27 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
     if (c < 0) continue;  // every DOF of the box has become inactive
     L.box_cell.push_back(c);
     L.box_node.push_back(node);
-    L.box_colour.push_back(colour_of(&T.coord[3 * node], dim));
+    L.box_colour.push_back(colour_of(&T.coord[3 * node], dim, cbase));
+  }
+  if (cbase != 3) {
+    // colour-major with cbase^dim colours, Morton order within a colour
+    const int nb = (int)L.box_cell.size();
+    std::vector<int> ord(nb);
+    std::vector<uint64_t> mk(nb);
+    for (int q = 0; q < nb; q++) {
+      ord[q] = q;
+      const int node = L.box_node[q];
+      const int64_t p[3] = {T.coord[3 * node], T.coord[3 * node + 1], T.coord[3 * node + 2]};
+      mk[q] = morton_fast(p, dim);
+    }
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+      return L.box_colour[a] != L.box_colour[b] ? L.box_colour[a] < L.box_colour[b] : mk[a] < mk[b];
+    });
+    std::vector<int> bc(nb), bn(nb), bcol(nb);
+    for (int q = 0; q < nb; q++) bc[q] = L.box_cell[ord[q]], bn[q] = L.box_node[ord[q]], bcol[q] = L.box_colour[ord[q]];
+    L.box_cell.swap(bc);
+    L.box_node.swap(bn);
+    L.box_colour.swap(bcol);
   }
   return L;
 }
@@ -764,6 +788,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
 struct Phase {
   int first, count, bmax, njmax;
   int wfirst = 0, wcount = 0;  // solve-sweep work items (box, chunk of J)
+  int shared = 0;              // 1: boxes of the phase may share near DOFs (2^d colours)
 };
 
 // Per-kernel-class timing with CUDA events on the launching stream, plus the
@@ -1315,6 +1340,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
     check_launch("assemble");
   };
 
+  // colours per level: 3^d (same-colour boxes share nothing) or the paper's 2^d
+  const int cbase = (F.flags & RSS_FLAG_COLOUR_2D) ? 2 : 3;
   std::unordered_map<int64_t, int> child_b;  // (problem, node) -> sum of its children's b
   DBuf gid, gel, gtri, gcnt;                 // per-phase ID and elimination scratch, grown as needed
   if (F.mlp) F.d_ovf_used.alloc(sizeof(unsigned long long), st);
@@ -1329,13 +1356,13 @@ template <typename T> static void run_factor(Factor<T> &F) {
     std::vector<int> cell_base(np + 1, 0);
     if (np == 1) {
       if (F.trees[0].maxdepth >= t && !active[0].empty()) {
-        H = build_level(F.trees[0], t, active[0]);
+        H = build_level(F.trees[0], t, active[0], cbase);
         box_prob.assign(H.box_cell.size(), 0);
       }
     } else {
       std::vector<HLevel> Hs(np);
       HostPool::get().parallel_for(np, [&](int64_t p) {
-        if (F.trees[p].maxdepth >= t && !active[p].empty()) Hs[p] = build_level(F.trees[p], t, active[p]);
+        if (F.trees[p].maxdepth >= t && !active[p].empty()) Hs[p] = build_level(F.trees[p], t, active[p], cbase);
       });
       size_t nc = 0, nd = 0, nbx = 0;
       for (int p = 0; p < np; p++) nc += Hs[p].ncell, nd += Hs[p].cell_dofs.size(), nbx += Hs[p].box_cell.size();
@@ -1405,6 +1432,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       check_launch("level_maps");
     }
     LevelDev<T> view = D->view(H, ptr<int>(d_dof_cell[slot]), ptr<int>(d_dof_loc[slot]));
+    view.shared = cbase == 2;
     if (have_prev) {
       LevelDev<T> pv = prevD->view(prevH, ptr<int>(d_dof_cell[prev_slot]), ptr<int>(d_dof_loc[prev_slot]));
       assemble_pairs(H, *D, &pv);
@@ -1619,10 +1647,18 @@ template <typename T> static void run_factor(Factor<T> &F) {
       check_launch("elim");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_SCHUR, st, base + p.first, p.second);
-      launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
+      if constexpr (std::is_same<T, float>::value) {
+        if (!(F.flags & RSS_FLAG_NO_TENSOR_CORES))
+          launch_schur_tc(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st,
+                          ptr<int>(F.d_err));
+        else
+          launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
+      } else {
+        launch_schur<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, njmax_lvl, ptr<T>(gel), el_stride, st);
+      }
       check_launch("schur");
       F.prof.end(pi, st);
-      F.phases.push_back({base + p.first, p.second, H.bmax, large ? -njmax_lvl : njmax_lvl, 0, 0});
+      F.phases.push_back({base + p.first, p.second, H.bmax, large ? -njmax_lvl : njmax_lvl, 0, 0, cbase == 2});
     }
     set_id_multi(IdMultiScratch{});
     // ranks of this level -> active DOFs of the next
@@ -1795,10 +1831,11 @@ static void sweep_phase(const Factor<T> &F, int mode, const Phase &p, T *v, int 
   const bool solve = mode == SWEEP_SOLVE_FWD || mode == SWEEP_SOLVE_BWD;
   if (solve && nrhs <= 4 && p.njmax >= 0 && sweep_chunk_smem(p.bmax, nrhs, sizeof(T)) <= (size_t)(200 << 10)) {
     launch_sweep_chunks<T>(mode, ptr<FBox<T>>(F.d_boxes), ptr<int>(F.d_wbox) + p.wfirst, ptr<int>(F.d_wchunk) + p.wfirst,
-                           p.wcount, v, nrhs, p.bmax, ptr<int>(F.d_wcnt), ptr<T>(F.d_pbuf), ptr<int64_t>(F.d_poff), st);
+                           p.wcount, v, nrhs, p.bmax, ptr<int>(F.d_wcnt), ptr<T>(F.d_pbuf), ptr<int64_t>(F.d_poff), st,
+                           p.shared);
     return;
   }
-  launch_sweep<T>(mode, ptr<FBox<T>>(F.d_boxes), p.first, p.count, v, nrhs, p.bmax, p.njmax, st);
+  launch_sweep<T>(mode, ptr<FBox<T>>(F.d_boxes), p.first, p.count, v, nrhs, p.bmax, p.njmax, st, p.shared);
 }
 
 // Every launch of one application of F (Eq. 3.10) or F^{-1} (Eq. 3.11) on
@@ -2078,6 +2115,112 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
   return ok;
 }
 
+// Conjugate gradients on A x = b preconditioned by the factor (the paper's
+// solver for its examples, Sec. 4: F is symmetric for symmetric kernels,
+// V_i = W_i^T).  FP64 vectors and residual operator; the preconditioner is
+// the factor's solve (FP32 for the mixed factor, whose rounding makes it not
+// quite symmetric, hence the flexible (Polak-Ribiere) form of beta).  All
+// right-hand sides advance in lock step; a column whose residual is met, or
+// whose curvature p^T A p is not positive, stops moving.  The recurrence
+// residual decides when to stop; the true residual b - A x is then checked,
+// and CG restarts from x if it is not met (within maxit iterations in all).
+template <typename T>
+static bool pcg(const Factor<T> &F, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
+                double *relres) {
+  cudaStream_t st = F.st;
+  const int64_t n = F.n, nn = n * nrhs;
+  DBuf R2, Z, P, Q, part, dres;
+  R2.alloc(sizeof(double) * nn * 2, st);
+  Z.alloc(sizeof(double) * nn, st);
+  P.alloc(sizeof(double) * nn, st);
+  Q.alloc(sizeof(double) * nn, st);
+  part.alloc(sizeof(double) * 2 * nrhs * 240, st);
+  dres.alloc(sizeof(double) * 2 * nrhs * 2, st);
+  double *r = ptr<double>(R2), *rold = r + nn, *z = ptr<double>(Z), *p = ptr<double>(P), *q = ptr<double>(Q);
+  double *dd = ptr<double>(dres), *dc = dd + 2 * nrhs;
+  auto dots = [&](const double *Vb, int nv, const double *vec, std::vector<double> &out) {
+    multidot(Vb, nn, nv, vec, n, nrhs, ptr<double>(part), dd, st);
+    check_launch("multidot");
+    out.resize((size_t)nv * nrhs);
+    CK(cudaMemcpyAsync(out.data(), dd, sizeof(double) * nv * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  };
+  auto comb = [&](double *y, double alpha, const double *Vb, const std::vector<double> &coef) {
+    staged_h2d(dc, coef.data(), sizeof(double) * nrhs, st);
+    combine(y, alpha, Vb, nn, 1, dc, n, nrhs, st);
+    check_launch("combine");
+  };
+  auto copy = [&](double *dst, const double *src) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+  };
+  std::vector<double> bn, tmp;
+  dots(b, 1, b, bn);
+  for (auto &v : bn) v = v > 0 ? sqrt(v) : 1.0;
+  // x0 = F^{-1} b
+  do_sweeps(F, b, x, nrhs, true, false);
+  int inner = 0;
+  double rel = 0;
+  bool ok = false;
+  while (true) {
+    // true residual r = b - A x
+    apply_A(F, x, q, nrhs);
+    copy(r, b);
+    comb(r, 1.0, q, std::vector<double>(nrhs, -1.0));
+    dots(r, 1, r, tmp);
+    rel = 0;
+    for (int c = 0; c < nrhs; c++) rel = std::max(rel, sqrt(std::max(tmp[c], 0.0)) / bn[c]);
+    if (rel <= tol) {
+      ok = true;
+      break;
+    }
+    if (inner >= maxit) break;
+    std::vector<char> live(nrhs);
+    for (int c = 0; c < nrhs; c++) live[c] = sqrt(std::max(tmp[c], 0.0)) / bn[c] > tol;
+    do_sweeps(F, r, z, nrhs, true, false);  // z = F^{-1} r
+    copy(p, z);
+    std::vector<double> rz;
+    dots(r, 1, z, rz);
+    while (inner < maxit) {
+      apply_A(F, p, q, nrhs);  // q = A p
+      std::vector<double> pq, alpha(nrhs, 0.0);
+      dots(p, 1, q, pq);
+      for (int c = 0; c < nrhs; c++) {
+        if (live[c] && pq[c] > 0 && rz[c] > 0) alpha[c] = rz[c] / pq[c];
+        else live[c] = 0;
+      }
+      comb(x, 1.0, p, alpha);
+      copy(rold, r);
+      for (auto &a : alpha) a = -a;
+      comb(r, 1.0, q, alpha);
+      inner++;
+      dots(r, 1, r, tmp);
+      double rr = 0;
+      for (int c = 0; c < nrhs; c++) {
+        const double rc = sqrt(std::max(tmp[c], 0.0)) / bn[c];
+        if (rc <= tol) live[c] = 0;
+        rr = std::max(rr, rc);
+      }
+      if (rr <= tol) break;
+      do_sweeps(F, r, z, nrhs, true, false);
+      std::vector<double> zr, beta(nrhs, 0.0);
+      dots(r, 2, z, zr);  // zr[2c] = r.z, zr[2c+1] = r_old.z
+      for (int c = 0; c < nrhs; c++) {
+        if (live[c] && rz[c] > 0) beta[c] = (zr[2 * c] - zr[2 * c + 1]) / rz[c];
+        rz[c] = zr[2 * c];
+      }
+      // p = z + beta p (q is free until the next product)
+      copy(q, z);
+      comb(q, 1.0, p, beta);
+      std::swap(p, q);
+    }
+  }
+  if (iters) *iters = inner;
+  if (relres) *relres = rel;
+  CK(cudaStreamSynchronize(st));
+  prof_collect(F);
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free solve.  Its working vectors live in one fixed file-scope
 // device array instead of memory allocated per factor: every device that
@@ -2091,7 +2234,9 @@ static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[256];
 
 // Device address of the scratch array for the current device, looked up on
-// the first call made with that device current.
+// the first call made with that device current.  The same first call raises
+// the sweep kernels' shared-memory limits on that device, so that no later
+// call has to (a later call may be running under stream capture).
 static void *noalloc_scratch() {
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -2104,30 +2249,47 @@ static void *noalloc_scratch() {
       cudaGetLastError();
       throw Fail{RSS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)};
     }
+    sweep_kernel_attributes();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) throw Fail{RSS_ECUDA, std::string("sweep kernel attributes: ") + cudaGetErrorString(e)};
     g_noalloc_ptr[dev] = p;
   }
   return g_noalloc_ptr[dev];
 }
 
+// Columns per pass of the sweep kernels: few enough for their shared-memory
+// vectors (3 b x columns entries of the widest box within 200 KB).
+template <typename T> static int sweep_columns(const Factor<T> &F, int nrhs) {
+  int bm = 1;
+  for (const auto &p : F.phases) bm = std::max(bm, p.bmax);
+  return (int)std::max<size_t>(1, std::min<size_t>(nrhs, (size_t)(200 << 10) / ((size_t)3 * bm * sizeof(T))));
+}
+
+// The solve of Eq. 3.11 in passes of at most `c` columns, each pass with its
+// n x c working vector and 2 x ntop x c top-block entries in the fixed array.
 template <typename T>
 static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nrhs) {
-  const size_t vbytes = (((size_t)F.n * nrhs * sizeof(T)) + 255) & ~(size_t)255;
-  const size_t tbytes = (size_t)2 * F.ntop * nrhs * sizeof(T);
-  if (vbytes + tbytes > NOALLOC_SCRATCH_BYTES)
-    throw Fail{RSS_EINVAL, "rss_solve_noalloc: n * nrhs too large for the fixed 16 MiB scratch"};
+  auto vbytes = [&](int c) { return (((size_t)F.n * c * sizeof(T)) + 255) & ~(size_t)255; };
+  auto tbytes = [&](int c) { return (size_t)2 * F.ntop * c * sizeof(T); };
+  int c = sweep_columns(F, nrhs);
+  while (c > 0 && vbytes(c) + tbytes(c) > NOALLOC_SCRATCH_BYTES) c--;
+  if (c < 1) throw Fail{RSS_EINVAL, "rss_solve_noalloc: one column of n entries exceeds the fixed 16 MiB scratch"};
   unsigned char *base = static_cast<unsigned char *>(noalloc_scratch());
   T *v = reinterpret_cast<T *>(base);
-  T *topwork = reinterpret_cast<T *>(base + vbytes);
+  T *topwork = reinterpret_cast<T *>(base + vbytes(c));
   cudaStream_t st = F.st;
-  launch_permute<T>(0, ptr<int64_t>(F.d_perm), b, v, nullptr, F.n, nrhs, st);
-  const FBox<T> *bx = ptr<FBox<T>>(F.d_boxes);
-  for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_SOLVE_FWD, p, v, nrhs, st);
-  launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
-                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, topwork, st);
-  for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it)
-    sweep_phase<T>(F, SWEEP_SOLVE_BWD, *it, v, nrhs, st);
-  launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, x, F.n, nrhs, st);
-  check_launch("rss_solve_noalloc");
+  for (int c0 = 0; c0 < nrhs; c0 += c) {
+    const int nc = std::min(c, nrhs - c0);
+    const double *bc = b + (size_t)c0 * F.n;
+    double *xc = x + (size_t)c0 * F.n;
+    launch_permute<T>(0, ptr<int64_t>(F.d_perm), bc, v, nullptr, F.n, nc, st);
+    for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_SOLVE_FWD, p, v, nc, st);
+    launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
+                  ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nc, topwork, st);
+    for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) sweep_phase<T>(F, SWEEP_SOLVE_BWD, *it, v, nc, st);
+    launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, xc, F.n, nc, st);
+    check_launch("rss_solve_noalloc");
+  }
   CK(cudaStreamSynchronize(st));
 }
 
@@ -2136,9 +2298,7 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
 // up to 4 columns on factors of boxes up to ~2000 wide are one chunk.
 template <typename T> static void sweeps_chunked(const Factor<T> &F, const double *in, double *out, int nrhs,
                                                  bool solve) {
-  int bm = 1;
-  for (const auto &p : F.phases) bm = std::max(bm, p.bmax);
-  const int cmax = (int)std::max<size_t>(1, std::min<size_t>(nrhs, (size_t)(200 << 10) / ((size_t)3 * bm * sizeof(T))));
+  const int cmax = sweep_columns(F, nrhs);
   for (int c0 = 0; c0 < nrhs; c0 += cmax)
     do_sweeps(F, in + (size_t)c0 * F.n, out + (size_t)c0 * F.n, std::min(cmax, nrhs - c0), solve);
 }
@@ -2374,6 +2534,25 @@ rss_status rss_solve_refined(const rss_factorization *f, const double *b, double
   });
   if (stt == RSS_OK && !ok) {
     g_last_error = "rss_solve_refined: tolerance not reached";
+    return RSS_ENOTCONV;
+  }
+  return stt;
+}
+
+rss_status rss_solve_cg(const rss_factorization *f, const double *b, double *x, int nrhs, double tol, int maxit,
+                        int *iters, double *relres) {
+  bool ok = false;
+  rss_status stt = guard([&] {
+    if (!f || !f->impl || nrhs < 1 || !(tol > 0) || maxit < 0) throw Fail{RSS_EINVAL, "rss_solve_cg: bad arguments"};
+    auto run = [&](const auto &F) {
+      if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
+      ok = F.n == 0 || pcg(F, b, x, nrhs, tol, maxit, iters, relres);
+    };
+    if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
+    else run(static_cast<const Factor<float> &>(*f->impl));
+  });
+  if (stt == RSS_OK && !ok) {
+    g_last_error = "rss_solve_cg: tolerance not reached";
     return RSS_ENOTCONV;
   }
   return stt;

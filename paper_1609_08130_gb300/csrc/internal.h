@@ -60,6 +60,8 @@ template <typename T> struct LevelDev {
   const int *dof_cell;          // [n] cell of each active DOF at this level
   const int *dof_loc;           // [n] local index of each active DOF
   T *pool;
+  int shared;                   // 1: boxes of one phase may share pair blocks
+                                // (2^d colours): Schur updates add atomically
 };
 
 // A list of dense blocks to assemble: block q has rows row_ids[row_off[q] ..
@@ -111,6 +113,11 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
 template <typename T>
 void launch_schur(const LevelDev<T> &lv, const FBox<T> *boxes, const int *box_list, int nbox,
                   int njmax, const T *scratch, int64_t scratch_stride, cudaStream_t st);
+// The FP32 factor's Schur update on the tensor cores (schur_tc.cu): the same
+// arguments as launch_schur plus the device error word (a bounded wait that
+// gives up records DERR_INTERNAL).
+void launch_schur_tc(const LevelDev<float> &lv, const FBox<float> *boxes, const int *box_list, int nbox, int njmax,
+                     const float *scratch, int64_t scratch_stride, cudaStream_t st, int *err);
 template <typename T>
 void launch_dense_lu(T *A, int n, int *piv, T *W, cudaStream_t st, int *err);
 // Per-box sums of log|U_jj| (part[0..nbox), and a DOF id of each box in
@@ -121,9 +128,11 @@ void launch_logdet(const FBox<T> *boxes, int nbox, const T *topLU, const int64_t
 
 // Sweeps over the factor (kernels.cu).  v: tree-order working vector,
 // layout v[g * nrhs + c].
+// shared != 0: boxes of the phase may share near DOFs (2^d colours), whose
+// updates are then atomic additions.
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax,
-                  int njmax, cudaStream_t st);
+                  int njmax, cudaStream_t st, int shared = 0);
 // Solve sweeps over work items (box, chunk of SWEEP_CHUNK rows of J) for
 // nrhs <= 4; cnt: per-box counters (zero between launches); pbuf/poff: the
 // backward sweep's per-box partial sums (ceil(nj / SWEEP_CHUNK) x r x 4
@@ -131,8 +140,11 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
 constexpr int SWEEP_CHUNK = 128;
 template <typename T>
 void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const int *wchunk, int nwork, T *v,
-                         int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st);
+                         int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st,
+                         int shared = 0);
 size_t sweep_chunk_smem(int bmax, int nrhs, int elem);
+// Set the shared-memory attributes of every sweep kernel on the current device.
+void sweep_kernel_attributes();
 template <typename T>
 void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, const int64_t *top, const int64_t *toff,
                 const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st);

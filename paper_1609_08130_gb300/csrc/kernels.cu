@@ -3330,7 +3330,9 @@ __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> lv, const FBox<T> *box
       if (a0 + ia >= nj) continue;
       const int codea = s_rc[ia];
       const int64_t off = s_po[codea * nc3 + codec];
-      lv.pool[off + s_rl[ia] + (int64_t)lc * s_ld[codea]] -= acc[x][y];
+      T *dst = lv.pool + off + s_rl[ia] + (int64_t)lc * s_ld[codea];
+      if (lv.shared) atomicAdd(dst, -acc[x][y]);  // pair blocks other boxes of the phase update too
+      else *dst -= acc[x][y];
     }
   }
 }
@@ -3545,7 +3547,8 @@ __device__ void warp_lu_solve(const T *LU, const int *piv, int r, T *x, T *tmp, 
 #define VJ(a, c) (jsh ? vJ[(a) * nrhs + (c)] : v[fb.J[a] * nrhs + (c)])
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, int first, T *v, int nrhs, int jsh) {
+__global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, int first, T *v, int nrhs, int jsh,
+                                              int shared) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FBox<T> &fb = boxes[first + blockIdx.x];
   const int k = fb.k, r = fb.r, nj = fb.nj;
@@ -3576,7 +3579,8 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
       int a = e % nj, c = e / nj;
       T acc = (T)0;
       for (int ri = 0; ri < r; ri++) acc += fb.E[a + (int64_t)ri * nj] * tmp[ri * nrhs + c];
-      v[fb.J[a] * nrhs + c] -= acc;
+      if (shared) atomicAdd(v + fb.J[a] * nrhs + c, -acc);  // near DOFs other boxes of the phase update too
+      else v[fb.J[a] * nrhs + c] -= acc;
     }
     // D^{-1} on R (v_R is final for this box): x_R = X_RR^{-1} v_R
     for (int e = tid; e < r * nrhs; e += NT) {
@@ -3647,6 +3651,10 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
       int a = e % nj, c = e / nj;
       T acc = (T)0;
       for (int ri = 0; ri < r; ri++) acc += fb.E[a + (int64_t)ri * nj] * vR[ri * nrhs + c];
+      if (shared && a >= k) {
+        atomicAdd(v + fb.J[a] * nrhs + c, acc);  // near DOFs other boxes of the phase update too
+        continue;
+      }
       T nv = v[fb.J[a] * nrhs + c] + acc;
       v[fb.J[a] * nrhs + c] = nv;
       if (a < k) vS[a * nrhs + c] = nv;  // S is the head of J
@@ -3679,7 +3687,7 @@ __device__ __forceinline__ void sweep_gather(const FBox<T> &fb, const T *v, T *v
 // chunk of J; the last CTA of the box: v_S -= E_S tmp, v_R = X_RR^{-1} tmp.
 template <typename T, int NR>
 __global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const int *wbox, const int *wchunk, T *v,
-                                                  int *cnt) {
+                                                  int *cnt, int shared) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
   const int bi = wbox[blockIdx.x], ch = wchunk[blockIdx.x];
@@ -3741,8 +3749,13 @@ __global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const in
     erow(a, a < nj, acc);
     if (mine && (tid & 1) == 0) {
       T *vg = v + fb.J[a] * NR;
+      if (shared) {  // near DOFs other boxes of the phase update too
 #pragma unroll
-      for (int c = 0; c < NR; c++) vg[c] -= acc[c];
+        for (int c = 0; c < NR; c++) atomicAdd(vg + c, -acc[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NR; c++) vg[c] -= acc[c];
+      }
     }
   }
   __syncthreads();
@@ -3888,7 +3901,7 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
 
 template <typename T>
 void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const int *wchunk, int nwork, T *v,
-                         int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st) {
+                         int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st, int shared) {
   if (nwork == 0) return;
   const size_t smem = ((size_t)4 * bmax + NT) * nrhs * sizeof(T) + 64;
   constexpr int SMAX = (200 << 10) + 64;  // callers keep smem within this
@@ -3896,7 +3909,7 @@ void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const 
   case NRV:                                                                                                \
     if (mode == SWEEP_SOLVE_FWD) {                                                                         \
       if (!capturing(st)) cudaFuncSetAttribute(k_sweep_fwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX); \
-      k_sweep_fwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt);                           \
+      k_sweep_fwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt, shared);                           \
     } else {                                                                                               \
       if (!capturing(st)) cudaFuncSetAttribute(k_sweep_bwd<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX); \
       k_sweep_bwd<T, NRV><<<nwork, NT, smem, st>>>(boxes, wbox, wchunk, v, cnt, pbuf, poff);               \
@@ -3916,7 +3929,7 @@ size_t sweep_chunk_smem(int bmax, int nrhs, int elem) { return ((size_t)4 * bmax
 
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax, int njmax,
-                  cudaStream_t st) {
+                  cudaStream_t st, int shared) {
   if (count == 0) return;
   const bool force_general = njmax < 0;  // large-box path requested
   if (force_general) njmax = -njmax;
@@ -3927,7 +3940,23 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
     smem = (size_t)3 * bmax * nrhs * sizeof(T) + 64;
   }
   if (!capturing(st)) cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (200 << 10) + 64);
-  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs, jsh); count_launch();
+  k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs, jsh, shared); count_launch();
+}
+
+// Raise the dynamic shared-memory limit of every sweep kernel on the current
+// device (both element types, every right-hand-side count of the chunked
+// forms), so that later launches need no attribute call, for instance while a
+// stream is being captured.
+void sweep_kernel_attributes() {
+  constexpr int SMAX = (200 << 10) + 64;
+  cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX);
+  cudaFuncSetAttribute(k_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX);
+#define RSS_SWEEP_ATTR(TT, NRV)                                                                   \
+  cudaFuncSetAttribute(k_sweep_fwd<TT, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX); \
+  cudaFuncSetAttribute(k_sweep_bwd<TT, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMAX);
+  RSS_SWEEP_ATTR(float, 1) RSS_SWEEP_ATTR(float, 2) RSS_SWEEP_ATTR(float, 3) RSS_SWEEP_ATTR(float, 4)
+  RSS_SWEEP_ATTR(double, 1) RSS_SWEEP_ATTR(double, 2) RSS_SWEEP_ATTR(double, 3) RSS_SWEEP_ATTR(double, 4)
+#undef RSS_SWEEP_ATTR
 }
 
 // Top blocks of one or more problems (Sec. 3.3.3): problem p has tn[p] DOFs
@@ -4174,9 +4203,9 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
   template void launch_schur<T>(const LevelDev<T> &, const FBox<T> *, const int *, int, int, const T *, int64_t, \
                                 cudaStream_t);                                                                \
   template void launch_dense_lu<T>(T *, int, int *, T *, cudaStream_t, int *);                                     \
-  template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t);            \
+  template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t, int);       \
   template void launch_sweep_chunks<T>(int, const FBox<T> *, const int *, const int *, int, T *, int, int, int *, \
-                                       T *, const int64_t *, cudaStream_t);                                  \
+                                       T *, const int64_t *, cudaStream_t, int);                             \
   template void launch_top<T>(int, const T *, const int64_t *, const int *, const int64_t *, const int64_t *,     \
                              const int *, int, int, T *, int, T *, cudaStream_t);                            \
   template void launch_lu_batched<T>(T *, const int64_t *, int *, const int64_t *, const int *, int, cudaStream_t, \

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "librss.so")
-SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu", "logdet.cu"]
+SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu", "logdet.cu", "schur_tc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -25,6 +25,8 @@ LAPLACE2D_LOG, LAPLACE3D_INV = 0, 1
 FP64, MIXED = 0, 1
 FLAG_LARGE_BOX_PATH = 1
 FLAG_NO_AUTOTUNE = 2
+FLAG_COLOUR_2D = 4
+FLAG_NO_TENSOR_CORES = 8
 
 
 def _nvcc():
@@ -37,7 +39,7 @@ def _nvcc():
 def build(force: bool = False) -> str:
     """Compile librss.so in-tree for sm_103a (translation units in parallel)."""
     srcs = [os.path.join(_CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(_CSRC, h) for h in ("common.cuh", "internal.h")] + \
+    deps = srcs + [os.path.join(_CSRC, h) for h in ("common.cuh", "internal.h", "tc.cuh")] + \
         [os.path.join(_INC, "rss.h")]
     if not force and os.path.exists(LIB_PATH) and \
             os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
@@ -82,6 +84,8 @@ _SIGS = {
     "rss_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rss_solve_cg": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
+                               C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rss_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -292,6 +296,18 @@ class Factorization:
         rr = C.c_double(0.0)
         st = lib().rss_solve_refined(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), b.shape[0],
                                      tol, maxit, C.byref(it), C.byref(rr))
+        if check or st != RSS_ENOTCONV:
+            _check(st)
+        return (x[0] if one else x), it.value, rr.value
+
+    def solve_cg(self, b, tol: float = 1e-10, maxit: int = 50, check: bool = True):
+        """Conjugate gradients on A x = b preconditioned with the factor.
+        Returns (x, iterations, final relative residual)."""
+        b, one, x = self._vec(b)
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        st = lib().rss_solve_cg(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), b.shape[0], tol, maxit,
+                                C.byref(it), C.byref(rr))
         if check or st != RSS_ENOTCONV:
             _check(st)
         return (x[0] if one else x), it.value, rr.value
