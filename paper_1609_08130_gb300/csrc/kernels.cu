@@ -1028,6 +1028,199 @@ __device__ __forceinline__ void fold_group(T (&pan)[PR], T *R, int ldr, int b, i
   group_bar(bar_id, nthr);
 }
 
+template <int TPC> __device__ __forceinline__ unsigned col_mask() {
+  return TPC == 1 ? 0xffffffffu : (((1u << TPC) - 1u) << ((threadIdx.x & 31) & ~(TPC - 1)));
+}
+template <typename T, int TPC> __device__ __forceinline__ T col_sum(T v) {
+  const unsigned m = col_mask<TPC>();
+#pragma unroll
+  for (int o = 1; o < TPC; o <<= 1) v += __shfl_xor_sync(m, v, o);
+  return v;
+}
+
+// Greedy column-pivoted QR of the box's b x b triangle R (row-major, ld
+// LDR; GT = NC x TPC threads of the calling group, column `col` split over
+// its TPC threads), T = R11^{-1} R12 and the box's ID outputs (Definition
+// 2.1, with the pivot and truncation rule of the ID: largest trailing column
+// norm, ties to the lowest column, k = #{j : |R_jj| > eps |R_11|}).
+//   - Columns are not moved: each thread keeps the logical position of its
+//     physical column, and the pivot's owner computes the reflector from its
+//     own column, so a step costs two barriers (argmax, reflector).
+//   - Trailing column norms are downdated (||x||^2 -= R_jc^2) and recomputed
+//     from the column when they have lost half their digits (LAPACK's
+//     safeguard); the pivot's own norm and the stopping test always use the
+//     exact trailing norm.  In exact arithmetic the pivots are those of the
+//     recomputed norms.
+//   - T is formed in place (R12 := R11^{-1} R12) by back substitution, one
+//     row of R11 per barrier with the updates spread over all threads, and
+//     copied out coalesced.
+template <typename T, int NC, int TPC> struct IdqShared {
+  T red_v[16];
+  int red_i[16], red_l[16];
+  T hh[4];
+  int lp[NC];  // physical column at each logical position
+  int stop, k;
+  T r11;
+};
+
+template <typename T, int NC, int TPC>
+__device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShared<T, NC, TPC> &sh, FBox<T> &fb,
+                           const LevelDev<T> &lv, int64_t coff, int nO) {
+  constexpr int GT = NC * TPC;
+  constexpr int NW = GT / 32;
+  const int tid = threadIdx.x, lt = tid % GT, col = lt / TPC, part = lt % TPC;
+  const int lane = tid & 31, wid = tid >> 5;
+  // half the digits of T: recompute a norm once it has dropped below that
+  const T tol = sizeof(T) == 4 ? (T)2.4e-4 : (T)1.5e-8;
+  const bool own = col < b;
+  int mylog = col;  // logical position of this thread's physical column
+  // downdated and last exact trailing norms^2 of this thread's column
+  T nrm = (T)0, nrm0 = (T)0;
+  if (lt < b) perm[lt] = lt;
+  if (own) {
+    T a0 = (T)0;
+    for (int i = part; i < b; i += TPC) a0 += R[i * LDR + col] * R[i * LDR + col];
+    nrm = nrm0 = col_sum<T, TPC>(a0);
+  }
+  if (tid == 0) sh.k = b;
+  // (largest norm, lowest logical position) over this warp's active columns
+  auto warp_argmax = [&](int j) {
+    T best = (T)-1;
+    int bi = b, bl = b;
+    if (own && part == 0 && mylog >= j) {
+      best = nrm;
+      bi = col;
+      bl = mylog;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(FULL, best, o);
+      const int oi = __shfl_xor_sync(FULL, bi, o), ol = __shfl_xor_sync(FULL, bl, o);
+      if (ov > best || (ov == best && ol < bl)) {
+        best = ov;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    if (lane == 0) {
+      sh.red_v[wid] = best;
+      sh.red_i[wid] = bi;
+      sh.red_l[wid] = bl;
+    }
+  };
+  group_bar(1, GT);
+  warp_argmax(0);
+  group_bar(1, GT);
+  int j = 0;
+  for (; j < b; j++) {
+    // the pivot: every thread reduces the warps' candidates the same way
+    T best = sh.red_v[0];
+    int pc = sh.red_i[0], pl = sh.red_l[0];
+    for (int u = 1; u < NW; u++)
+      if (sh.red_v[u] > best || (sh.red_v[u] == best && sh.red_l[u] < pl)) {
+        best = sh.red_v[u];
+        pc = sh.red_i[u];
+        pl = sh.red_l[u];
+      }
+    if (pc >= b) {  // no valid candidate (all norms NaN): stop
+      if (tid == 0) sh.k = j;
+      break;
+    }
+    if (col == pc) {
+      // exact trailing norm of the pivot column, the stopping test and the
+      // reflector (v = [1; R_(j+1..),pc scl], H = I - tau v v^T)
+      T a0 = (T)0;
+      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + pc] * R[i * LDR + pc];
+      const T sacc = col_sum<T, TPC>(a0);
+      if (part == 0) {
+        const T x0 = R[j * LDR + pc];
+        const T cn = sqrt(x0 * x0 + sacc);
+        if (j == 0) sh.r11 = cn;
+        const T r11 = j == 0 ? cn : sh.r11;
+        sh.stop = (r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
+        if (sacc > (T)0) {
+          const T beta = x0 >= (T)0 ? -cn : cn;
+          sh.hh[1] = beta;
+          sh.hh[2] = (beta - x0) / beta;
+          sh.hh[3] = (T)1 / (x0 - beta);
+        } else {
+          sh.hh[2] = (T)0;  // tau = 0: nothing below the diagonal
+        }
+      }
+    }
+    // logical swap of positions j and pl (no data moves)
+    if (mylog == j) mylog = pl;
+    if (col == pc) mylog = j;
+    if (tid == 0) {
+      const int tp = perm[j];
+      perm[j] = perm[pl];
+      perm[pl] = tp;
+    }
+    group_bar(1, GT);
+    if (sh.stop) {
+      if (tid == 0) sh.k = j;
+      break;
+    }
+    const T tau = sh.hh[2];
+    if (own && mylog > j) {
+      T rjc = R[j * LDR + col];
+      if (tau != (T)0) {
+        const T scl = sh.hh[3];
+        T a0 = (T)0;
+        for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + pc] * R[i * LDR + col];
+        const T d = col_sum<T, TPC>(a0);
+        const T f = tau * (rjc + scl * d);
+        const T fs = f * scl;
+        for (int i = j + 1 + part; i < b; i += TPC) R[i * LDR + col] -= fs * R[i * LDR + pc];
+        rjc -= f;
+        if (part == 0) R[j * LDR + col] = rjc;
+      }
+      // row j leaves the trailing block of this column
+      nrm -= rjc * rjc;
+      if (!(nrm > tol * nrm0)) {
+        T a0 = (T)0;
+        for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + col] * R[i * LDR + col];
+        nrm = nrm0 = col_sum<T, TPC>(a0);
+      }
+    }
+    if (col == pc && part == 0 && tau != (T)0) R[j * LDR + pc] = sh.hh[1];
+    warp_argmax(j + 1);
+    group_bar(1, GT);
+  }
+  group_bar(1, GT);
+  const int k = sh.k;
+  const int r = b - k;
+  if (own && part == 0) sh.lp[mylog] = col;
+  group_bar(1, GT);
+  // R12 := R11^{-1} R12 (columns of R12 are the logical positions k.. b-1)
+  for (int i = k - 1; i >= 0; i--) {
+    const int pi = sh.lp[i];
+    const T inv = (T)1 / R[i * LDR + pi];
+    for (int c = lt; c < r; c += GT) R[i * LDR + sh.lp[k + c]] *= inv;
+    group_bar(1, GT);
+    for (int e = lt; e < i * r; e += GT) {
+      const int l = e / r, c = e % r;
+      const int pcol = sh.lp[k + c];
+      R[l * LDR + pcol] -= R[l * LDR + pi] * R[i * LDR + pcol];
+    }
+    group_bar(1, GT);
+  }
+  // T (k x r, column-major, ld k)
+  for (int e = lt; e < k * r; e += GT) {
+    const int i = e % k, c = e / k;
+    fb.Tm[e] = R[i * LDR + sh.lp[k + c]];
+  }
+  if (lt < b) {
+    fb.loc[lt] = perm[lt];
+    fb.ids[lt] = lv.cell_dofs[coff + perm[lt]];
+  }
+  if (tid == 0) {
+    fb.k = k;
+    fb.r = r;
+    fb.no = nO;
+  }
+}
+
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
                                              Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
@@ -1037,10 +1230,7 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
   constexpr int VS = PR + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ocode[125], s_obase[126], s_no;
-  __shared__ T s_red_v[8];
-  __shared__ int s_red_i[8];
-  __shared__ T s_hh[4];  // x0, beta, tau, scl of the current CPQR step
-  __shared__ int s_stop, s_piv, s_k;
+  __shared__ IdqShared<T, NC, 1> s_sh;
   const int tid = threadIdx.x;
   const int grp = tid / NC, col = tid % NC;
   const int bar_id = 1 + grp;
@@ -1155,154 +1345,7 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
   }
   __syncthreads();
   if (grp != 0) return;
-  // greedy column-pivoted QR of the triangle, one column per thread
-  T *R = Rg;
-  const int lane = tid & 31, wid = tid >> 5;
-  constexpr int NW = NC / 32;
-  if (col < b) perm[col] = col;
-  if (tid == 0) s_k = b;
-  T r11 = (T)0;
-  for (int j = 0; j < b; j++) {
-    T best = (T)-1;
-    int bi = b;
-    if (col >= j && col < b) {
-      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-      int i = j;
-      for (; i + 3 < b; i += 4) {
-        const T x0 = R[i * LDR + col], x1 = R[(i + 1) * LDR + col];
-        const T x2 = R[(i + 2) * LDR + col], x3 = R[(i + 3) * LDR + col];
-        a0 += x0 * x0;
-        a1 += x1 * x1;
-        a2 += x2 * x2;
-        a3 += x3 * x3;
-      }
-      for (; i < b; i++) a0 += R[i * LDR + col] * R[i * LDR + col];
-      best = (a0 + a1) + (a2 + a3);
-      bi = col;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T ov = __shfl_xor_sync(FULL, best, o);
-      int oi = __shfl_xor_sync(FULL, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      s_red_v[wid] = best;
-      s_red_i[wid] = bi;
-    }
-    group_bar(1, NC);
-    if (tid == 0) {
-      for (int u = 1; u < NW; u++)
-        if (s_red_v[u] > best || (s_red_v[u] == best && s_red_i[u] < bi)) {
-          best = s_red_v[u];
-          bi = s_red_i[u];
-        }
-      const T cn = sqrt(best);
-      if (j == 0) r11 = cn;
-      // no valid pivot (all norms NaN) also stops
-      const int stop = (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
-      s_stop = stop;
-      s_piv = bi;
-      if (stop) s_k = j;
-    }
-    group_bar(1, NC);
-    if (s_stop) break;
-    const int p = s_piv;
-    if (p != j) {
-      for (int i = col; i < b; i += NC) {
-        T t0 = R[i * LDR + j];
-        R[i * LDR + j] = R[i * LDR + p];
-        R[i * LDR + p] = t0;
-      }
-      if (tid == 0) {
-        int tp = perm[j];
-        perm[j] = perm[p];
-        perm[p] = tp;
-      }
-    }
-    group_bar(1, NC);
-    if (col == j) {
-      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-      int i = j + 1;
-      for (; i + 3 < b; i += 4) {
-        const T x0 = R[i * LDR + j], x1 = R[(i + 1) * LDR + j], x2 = R[(i + 2) * LDR + j], x3 = R[(i + 3) * LDR + j];
-        a0 += x0 * x0;
-        a1 += x1 * x1;
-        a2 += x2 * x2;
-        a3 += x3 * x3;
-      }
-      for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + j];
-      const T sacc = (a0 + a1) + (a2 + a3);
-      const T x0 = R[j * LDR + j];
-      if (sacc > (T)0) {
-        const T nrm = sqrt(x0 * x0 + sacc);
-        const T beta = x0 >= (T)0 ? -nrm : nrm;
-        s_hh[0] = x0;
-        s_hh[1] = beta;
-        s_hh[2] = (beta - x0) / beta;
-        s_hh[3] = (T)1 / (x0 - beta);
-      } else {
-        s_hh[2] = (T)0;  // tau = 0: no reflection
-      }
-    }
-    group_bar(1, NC);
-    const T tau = s_hh[2];
-    if (tau != (T)0 && col > j && col < b) {
-      const T scl = s_hh[3];
-      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-      int i = j + 1;
-      for (; i + 3 < b; i += 4) {
-        a0 += R[i * LDR + j] * R[i * LDR + col];
-        a1 += R[(i + 1) * LDR + j] * R[(i + 1) * LDR + col];
-        a2 += R[(i + 2) * LDR + j] * R[(i + 2) * LDR + col];
-        a3 += R[(i + 3) * LDR + j] * R[(i + 3) * LDR + col];
-      }
-      for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + col];
-      const T d = (a0 + a1) + (a2 + a3);
-      const T f = tau * (R[j * LDR + col] + scl * d);
-      const T fs = f * scl;
-      R[j * LDR + col] -= f;
-      int i2 = j + 1;
-      for (; i2 + 3 < b; i2 += 4) {
-        const T y0 = R[i2 * LDR + col], y1 = R[(i2 + 1) * LDR + col];
-        const T y2 = R[(i2 + 2) * LDR + col], y3 = R[(i2 + 3) * LDR + col];
-        const T z0 = R[i2 * LDR + j], z1 = R[(i2 + 1) * LDR + j];
-        const T z2 = R[(i2 + 2) * LDR + j], z3 = R[(i2 + 3) * LDR + j];
-        R[i2 * LDR + col] = y0 - fs * z0;
-        R[(i2 + 1) * LDR + col] = y1 - fs * z1;
-        R[(i2 + 2) * LDR + col] = y2 - fs * z2;
-        R[(i2 + 3) * LDR + col] = y3 - fs * z3;
-      }
-      for (; i2 < b; i2++) R[i2 * LDR + col] -= fs * R[i2 * LDR + j];
-    }
-    group_bar(1, NC);
-    if (tau != (T)0 && col == j) R[j * LDR + j] = s_hh[1];
-    group_bar(1, NC);
-  }
-  group_bar(1, NC);
-  const int k = s_k;
-  const int r = b - k;
-  // T = R11^{-1} R12, one thread per column
-  for (int cc = col; cc < r; cc += NC) {
-    T *tcol = fb.Tm + (int64_t)cc * k;
-    for (int i = k - 1; i >= 0; i--) {
-      T sacc = R[i * LDR + k + cc];
-      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
-      tcol[i] = sacc / R[i * LDR + i];
-    }
-  }
-  if (col < b) {
-    fb.loc[col] = perm[col];
-    fb.ids[col] = lv.cell_dofs[coff + perm[col]];
-  }
-  if (tid == 0) {
-    fb.k = k;
-    fb.r = r;
-    fb.no = nO;
-  }
+  idq_finish<T, NC, 1>(Rg, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
 }
 
 // ---------------------------------------------------------------------------
@@ -1314,16 +1357,6 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
 // fewer sequential steps.  The reflectors, the triangle and the greedy
 // pivoting are those of k_idc; only the order of partial sums differs.
 // ---------------------------------------------------------------------------
-
-template <int TPC> __device__ __forceinline__ unsigned col_mask() {
-  return TPC == 1 ? 0xffffffffu : (((1u << TPC) - 1u) << ((threadIdx.x & 31) & ~(TPC - 1)));
-}
-template <typename T, int TPC> __device__ __forceinline__ T col_sum(T v) {
-  const unsigned m = col_mask<TPC>();
-#pragma unroll
-  for (int o = 1; o < TPC; o <<= 1) v += __shfl_xor_sync(m, v, o);
-  return v;
-}
 
 // The TPC threads of the owner column publish [v (PR entries) | tau | scl |
 // beta | flag] for the next reflector; see publish_reflector.
@@ -1390,143 +1423,6 @@ __device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, 
     }
   }
   group_bar(bar_id, nthr);
-}
-
-// Greedy column-pivoted QR of the box's triangle R (rows x ld LDR, GT = NC x
-// TPC threads of the calling group, column `col` split over its TPC
-// threads), T = R11^{-1} R12 and the box's ID outputs (Definition 2.1).
-template <typename T, int NC, int TPC> struct IdqShared {
-  T red_v[16];
-  int red_i[16];
-  T hh[4];
-  int stop, piv, k;
-};
-
-template <typename T, int NC, int TPC>
-__device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShared<T, NC, TPC> &sh, FBox<T> &fb,
-                           const LevelDev<T> &lv, int64_t coff, int nO) {
-  constexpr int GT = NC * TPC;
-  const int tid = threadIdx.x, lt = tid % GT, col = lt / TPC, part = lt % TPC;
-  T *s_red_v = sh.red_v;
-  int *s_red_i = sh.red_i;
-  T *s_hh = sh.hh;
-  int &s_stop = sh.stop, &s_piv = sh.piv, &s_k = sh.k;
-  const int lane = tid & 31, wid = tid >> 5;
-  constexpr int NW = GT / 32;
-  if (lt < b) perm[lt] = lt;
-  if (tid == 0) s_k = b;
-  T r11 = (T)0;
-  for (int j = 0; j < b; j++) {
-    T best = (T)-1;
-    int bi = b;
-    {
-      T a0 = (T)0;
-      if (col >= j && col < b)
-        for (int i = j + part; i < b; i += TPC) a0 += R[i * LDR + col] * R[i * LDR + col];
-      a0 = col_sum<T, TPC>(a0);
-      if (col >= j && col < b && part == 0) {
-        best = a0;
-        bi = col;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T ov = __shfl_xor_sync(FULL, best, o);
-      int oi = __shfl_xor_sync(FULL, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      s_red_v[wid] = best;
-      s_red_i[wid] = bi;
-    }
-    group_bar(1, GT);
-    if (tid == 0) {
-      for (int u = 1; u < NW; u++)
-        if (s_red_v[u] > best || (s_red_v[u] == best && s_red_i[u] < bi)) {
-          best = s_red_v[u];
-          bi = s_red_i[u];
-        }
-      const T cn = sqrt(best);
-      if (j == 0) r11 = cn;
-      const int stop = (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) ? 1 : 0;
-      s_stop = stop;
-      s_piv = bi;
-      if (stop) s_k = j;
-    }
-    group_bar(1, GT);
-    if (s_stop) break;
-    const int p = s_piv;
-    if (p != j) {
-      for (int i = lt; i < b; i += GT) {
-        T t0 = R[i * LDR + j];
-        R[i * LDR + j] = R[i * LDR + p];
-        R[i * LDR + p] = t0;
-      }
-      if (tid == 0) {
-        int tp = perm[j];
-        perm[j] = perm[p];
-        perm[p] = tp;
-      }
-    }
-    group_bar(1, GT);
-    if (col == j) {
-      T a0 = (T)0;
-      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + j];
-      const T sacc = col_sum<T, TPC>(a0);
-      if (part == 0) {
-        const T x0 = R[j * LDR + j];
-        if (sacc > (T)0) {
-          const T nrm = sqrt(x0 * x0 + sacc);
-          const T beta = x0 >= (T)0 ? -nrm : nrm;
-          s_hh[0] = x0;
-          s_hh[1] = beta;
-          s_hh[2] = (beta - x0) / beta;
-          s_hh[3] = (T)1 / (x0 - beta);
-        } else {
-          s_hh[2] = (T)0;
-        }
-      }
-    }
-    group_bar(1, GT);
-    const T tau = s_hh[2];
-    if (tau != (T)0 && col > j && col < b) {
-      const T scl = s_hh[3];
-      T a0 = (T)0;
-      for (int i = j + 1 + part; i < b; i += TPC) a0 += R[i * LDR + j] * R[i * LDR + col];
-      const T rjc = R[j * LDR + col];
-      const T d = col_sum<T, TPC>(a0);
-      const T f = tau * (rjc + scl * d);
-      const T fs = f * scl;
-      if (part == 0) R[j * LDR + col] = rjc - f;
-      for (int i = j + 1 + part; i < b; i += TPC) R[i * LDR + col] -= fs * R[i * LDR + j];
-    }
-    group_bar(1, GT);
-    if (tau != (T)0 && col == j && part == 0) R[j * LDR + j] = s_hh[1];
-    group_bar(1, GT);
-  }
-  group_bar(1, GT);
-  const int k = s_k;
-  const int r = b - k;
-  for (int cc = lt; cc < r; cc += GT) {
-    T *tcol = fb.Tm + (int64_t)cc * k;
-    for (int i = k - 1; i >= 0; i--) {
-      T sacc = R[i * LDR + k + cc];
-      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
-      tcol[i] = sacc / R[i * LDR + i];
-    }
-  }
-  if (lt < b) {
-    fb.loc[lt] = perm[lt];
-    fb.ids[lt] = lv.cell_dofs[coff + perm[lt]];
-  }
-  if (tid == 0) {
-    fb.k = k;
-    fb.r = r;
-    fb.no = nO;
-  }
 }
 
 template <typename T, int NC, int TPC>
