@@ -12,6 +12,8 @@ Workloads (--workload):
                        K = -log|x-y| / (2 pi), leaf <= 64, eps = 1e-6, four
                        N(0,1) right-hand sides (seeds 1..4)
   laplace2d_grid64     the same at 64 x 64 (N = 4096), one right-hand side
+  laplace2d_grid256    the same at 256 x 256 (N = 65536), four right-hand
+                       sides (a profiling size)
   laplace3d_grid32     3D Laplace, 32^3 grid (N = 32768), A = I + h^3/(4 pi r),
                        eps = 1e-3, one right-hand side
   laplace2d_batched256 256 independent 2D problems, N_p uniform in
@@ -55,8 +57,8 @@ from paper_1609_08130_gb300 import inputs  # noqa: E402
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 METRIC = "RS-S factor+solve points/s at eps=1e-6, mixed/batched vs FP64 GPU"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
-WORKLOADS = ["laplace2d_grid512", "laplace2d_grid64", "laplace3d_grid32", "laplace2d_batched256",
-             "laplace3d_grid64"]
+WORKLOADS = ["laplace2d_grid512", "laplace2d_grid64", "laplace2d_grid256", "laplace3d_grid32",
+             "laplace2d_batched256", "laplace3d_grid64"]
 
 
 def load_peaks():
@@ -195,7 +197,7 @@ def oracle_sample(name: str) -> dict:
     sides per point on a problem of at most 4096 points."""
     if name.startswith("laplace2d_grid"):
         pts = inputs.grid_points(64, 2)
-        nrhs = 4 if name == "laplace2d_grid512" else 1
+        nrhs = 1 if name == "laplace2d_grid64" else 4
         return dict(pts=[pts], kind=0, eps=1e-6, nrhs=nrhs,
                     desc=f"64x64-grid instance (N=4096) of the 2D workload, leaf 64, eps 1e-6, {nrhs} rhs")
     if name.startswith("laplace3d_grid"):
@@ -349,8 +351,8 @@ def main():
     ap.add_argument("--workload", default="laplace2d_grid512", choices=WORKLOADS)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--mlp", action="store_true", help="presize factor storage by the trained rank proposal")
-    ap.add_argument("--colours", type=int, default=3, choices=[2, 3],
-                    help="colours per dimension of the level schedule: 3 (default) or the paper's 2")
+    ap.add_argument("--colours", type=int, default=2, choices=[2, 3],
+                    help="colours per dimension of the level schedule: the paper's 2 (default) or 3")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
