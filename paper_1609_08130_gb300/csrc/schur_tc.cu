@@ -7,11 +7,13 @@
 // pair blocks of the level (one dense block per pair of cells at Chebyshev
 // distance <= 2), so the product is scattered into them.
 //
-// One CTA of 128 threads per (box, 128 rows of J): the E rows are staged
-// once in shared memory, then for every 64 columns of J the X_RJ columns are
-// staged, the tile E X_RJ is accumulated in tensor memory (M = 128, N = 64,
-// K = 8 per instruction) and the four warps read their 32 rows back and
-// subtract them from the pair blocks.  FP32 accuracy is kept by splitting
+// One CTA of 256 threads (two warpgroups) per (box, 128 rows of J): the E
+// rows are staged in shared memory, then for every 64 columns of J the X_RJ
+// columns are staged, the tile E X_RJ is accumulated in tensor memory
+// (M = 128, N = 64, K = 8 per instruction) and every warp reads 32 rows x 32
+// columns of it back (warp w: rows 32 (w mod 4) .., columns 32 (w / 4) ..)
+// and subtracts them from the pair blocks.  54 KB of shared memory per CTA
+// lets four CTAs share an SM, so many scatter loads are in flight.  FP32 accuracy is kept by splitting
 // each operand into a TF32 head and an FP32 remainder: three TF32 products
 // (head x head, head x remainder, remainder x head) per K step.
 #include "internal.h"
@@ -23,8 +25,8 @@ namespace {
 
 constexpr int TM = 128;  // rows of J per CTA (MMA M)
 constexpr int TN = 64;   // columns of J per MMA tile (MMA N)
-constexpr int KC = 64;   // K (= r) per staged chunk
-constexpr int NTC = 128; // threads: one warpgroup, thread = accumulator row
+constexpr int KC = 32;   // K (= r) per staged chunk
+constexpr int NTC = 256; // threads: two warpgroups over the accumulator's rows and column halves
 constexpr long long WAIT_POLLS = 1ll << 20;  // polls of a bounded mbarrier wait
 
 struct SchurTcSmem {
@@ -80,8 +82,9 @@ __global__ void __launch_bounds__(NTC) k_schur_tc(LevelDev<float> lv, const FBox
     decode3(rc, dim, cdx, cdy, cdz);
     s_po[e] = ca >= 0 ? lv.pair_off[(int64_t)ca * lv.NB + code5(cdx - adx, cdy - ady, cdz - adz, dim)] : -1;
   }
-  // this thread's accumulator row
-  const int a = a0 + tid;
+  // this thread's accumulator row (its warp's lane quarter) and column half
+  const int trow = (warp & 3) * 32 + (tid & 31), chalf = warp >> 2;
+  const int a = a0 + trow;
   const bool row_ok = a < nj;
   const int codea = row_ok ? fb.Jnb[a] : 0, rloc = row_ok ? fb.Jloc[a] : 0;
 
@@ -101,15 +104,17 @@ __global__ void __launch_bounds__(NTC) k_schur_tc(LevelDev<float> lv, const FBox
       const int kp = (kw + 7) & ~7;              // padded to the MMA's K = 8
       // E rows a0.. (column-major, ld nj): staged when the chunk changes
       if (c0 == 0 || nkc > 1) {
-        for (int q = 0; q < kp / 4; q++) {
+        const int ra = a0 + (tid & (TM - 1));  // rows over the first 128 threads, again for the next
+        const bool ra_ok = ra < nj;
+        for (int q = tid / TM; q < kp / 4; q += NTC / TM) {
           float hv[4], lv4[4];
 #pragma unroll
           for (int u = 0; u < 4; u++) {
             const int k = 4 * q + u;
-            const float x = (row_ok && k < kw) ? fb.E[a + (int64_t)(kc * KC + k) * nj] : 0.f;
+            const float x = (ra_ok && k < kw) ? fb.E[ra + (int64_t)(kc * KC + k) * nj] : 0.f;
             tc::split_tf32(x, hv[u], lv4[u]);
           }
-          const uint32_t o = tc::kmajor_off(tid, 4 * q, TM);
+          const uint32_t o = tc::kmajor_off(tid & (TM - 1), 4 * q, TM);
           *reinterpret_cast<float4 *>(opA_hi + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *reinterpret_cast<float4 *>(opA_lo + o) = make_float4(lv4[0], lv4[1], lv4[2], lv4[3]);
         }
@@ -167,9 +172,9 @@ __global__ void __launch_bounds__(NTC) k_schur_tc(LevelDev<float> lv, const FBox
     const int ld = s_ld[codea];
     float *pool = lv.pool + rloc;
 #pragma unroll 1
-    for (int j0 = 0; j0 < TN; j0 += 16) {
+    for (int j0 = chalf * (TN / 2); j0 < (chalf + 1) * (TN / 2); j0 += 16) {
       float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
+      tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)j0, v);
       if (row_ok) {
 #pragma unroll
         for (int j = 0; j < 16; j++) {

@@ -121,12 +121,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
   return false;
 }
 
-// Split x into a TF32 head (low 13 mantissa bits cleared) and the FP32
-// remainder, so that hi_a hi_b + hi_a lo_b + lo_a hi_b carries x_a x_b to
-// about FP32 accuracy (the lo_a lo_b term is below 2^-22 relative).
+// x rounded to the nearest TF32 value (10 explicit mantissa bits; the low 13
+// bits of the FP32 word are zero).
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Split x into a TF32 head and a TF32 remainder, both rounded to nearest:
+// x - hi is exact in FP32 and |x - hi - lo| <= 2^-24 |x|, so
+// hi_a hi_b + hi_a lo_b + lo_a hi_b carries x_a x_b to about FP32 accuracy
+// (the dropped lo_a lo_b term is below 2^-24 relative).
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  lo = x - hi;
+  hi = to_tf32(x);
+  lo = to_tf32(x - hi);
 }
 
 }  // namespace tc
