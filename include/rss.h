@@ -254,6 +254,18 @@ rss_status rss_logdet(const rss_factorization *f, double *logabs);
  * as in rss_tree_query. */
 rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes);
 
+/* rss_stats_json -- the factor's statistics as a NUL-terminated JSON
+ * document in a HOST buffer: sizes (n, problems, dim, precision, eps, colour
+ * phases per level, maxdepth, boxes, top-block size), storage (factor,
+ * reserved, used and overflow bytes; whether a rank proposal was used and
+ * whether the factorization was redone), per depth the boxes and the sums
+ * and maxima of |B|, k and |J| (the skeleton ranks of Sec. 3.3), per box in
+ * elimination order its depth, |B|, k and |J|, and the kernel-class times
+ * in milliseconds when the factor was created with options.profile.
+ * buf may be NULL to ask for the size; *nbytes in/out as in
+ * rss_tree_query (the size includes the terminating NUL). */
+rss_status rss_stats_json(const rss_factorization *f, char *buf, size_t *nbytes);
+
 /* rss_profile -- per-kernel-class totals of a factor created with
  * options.profile = 1, accumulated over rss_factor and every later
  * rss_apply / rss_solve on it, into a HOST double array of 4 * 12 entries:

@@ -317,58 +317,6 @@ static inline uint64_t morton_fast(const int64_t *c, int dim) {
                   : (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
 }
 
-// Stable LSD radix sort of idx by key (11-bit digits over the low key_bits
-// bits; a digit on which all keys agree is skipped).  Large inputs split
-// the histogram and scatter passes over the host pool.
-static void radix_sort_by_key(std::vector<uint64_t> &key, std::vector<int64_t> &idx, int key_bits) {
-  const size_t n = key.size();
-  const int RB = 11, NBK = 1 << RB;
-  const int nt = n < ((size_t)1 << 18) ? 1 : std::min(16, HostPool::get().size());
-  std::vector<uint64_t> k2(n);
-  std::vector<int64_t> i2(n);
-  std::vector<size_t> cnt((size_t)nt * NBK);
-  auto range = [&](int t, size_t &lo, size_t &hi) {
-    lo = n * t / nt;
-    hi = n * (t + 1) / nt;
-  };
-  for (int sh = 0; sh < key_bits; sh += RB) {
-    std::fill(cnt.begin(), cnt.end(), 0);
-    HostPool::get().parallel_for(nt, [&](int64_t t) {
-      size_t lo, hi;
-      range((int)t, lo, hi);
-      size_t *c = &cnt[(size_t)t * NBK];
-      for (size_t q = lo; q < hi; q++) c[(key[q] >> sh) & (NBK - 1)]++;
-    });
-    int used = 0;
-    for (int d = 0; d < NBK && used < 2; d++) {
-      size_t tot = 0;
-      for (int t = 0; t < nt; t++) tot += cnt[(size_t)t * NBK + d];
-      if (tot) used++;
-    }
-    if (used < 2) continue;
-    // exclusive offsets in (digit, thread) order
-    size_t acc = 0;
-    for (int d = 0; d < NBK; d++)
-      for (int t = 0; t < nt; t++) {
-        size_t c = cnt[(size_t)t * NBK + d];
-        cnt[(size_t)t * NBK + d] = acc;
-        acc += c;
-      }
-    HostPool::get().parallel_for(nt, [&](int64_t t) {
-      size_t lo, hi;
-      range((int)t, lo, hi);
-      size_t *c = &cnt[(size_t)t * NBK];
-      for (size_t q = lo; q < hi; q++) {
-        size_t pos = c[(key[q] >> sh) & (NBK - 1)]++;
-        k2[pos] = key[q];
-        i2[pos] = idx[q];
-      }
-    });
-    key.swap(k2);
-    idx.swap(i2);
-  }
-}
-
 struct HTree {
   uint32_t magic = MAGIC_TREE;
   int dim = 2, leaf = 64, maxdepth = 0;
@@ -394,164 +342,128 @@ static int colour_of(const int *c, int dim, int base = 3) {
   return col;
 }
 
-// Build by sorting on the depth-20 Morton key: a node of depth t is the run
-// of points sharing the key's top dim*t bits; children come out in child
-// index order because x is the lowest bit of each group.  The radix sort
-// uses only the key's top D0 levels (a few below the depth a uniform
-// distribution needs); a node that still has to split at depth D0 re-sorts
-// its range on the full key.  Points of a leaf are finally put back in
-// original order, so the result is that of a full-key sort.
-static void build_tree(HTree &T, const double *pts_host) {
+// Elimination order of every depth: colour-major with 3^d colours, Morton
+// order within a colour (nodes of a depth come in Morton order already).
+static void level_lists(HTree &T) {
   const int dim = T.dim;
-  const int64_t n = T.n;
-  const int MAXD = 20;
-  std::vector<uint64_t> kf(n);
-  std::vector<int> cc((size_t)n * dim);
-  parallel_range(n, (int64_t)1 << 16, [&](int64_t lo, int64_t hi) {
-    for (int64_t i = lo; i < hi; i++) {
-      int64_t c[3] = {0, 0, 0};
-      for (int d = 0; d < dim; d++) {
-        c[d] = cell_at(pts_host[i * dim + d], MAXD);
-        cc[(size_t)i * dim + d] = (int)c[d];
-      }
-      kf[i] = morton_fast(c, dim);
-    }
-  });
-  int D0 = 0;
-  while (D0 < MAXD && ((int64_t)T.leaf << (dim * D0)) < n) D0++;
-  D0 = std::min(MAXD, D0 + 3);
-  const int shift0 = dim * (MAXD - D0);
-  std::vector<uint64_t> ks(n);
-  for (int64_t i = 0; i < n; i++) ks[i] = kf[i] >> shift0;
-  T.perm.resize(n);
-  for (int64_t i = 0; i < n; i++) T.perm[i] = i;
-  radix_sort_by_key(ks, T.perm, dim * D0);  // stable: equal keys keep index order
-  for (int64_t p = 0; p < n; p++) ks[p] = kf[T.perm[p]];
-  struct Frame {
-    int64_t lo, hi;
-    int depth, parent;
-    int c[3];
-  };
-  struct NodeVec {
-    std::vector<int> depth, parent, coord, task;
-    std::vector<int64_t> start, count;
-    int maxdepth = 0;
-  };
-  // children of a node that splits, in child order (its range re-sorted on
-  // the full key first at depth D0)
-  auto split = [&](const Frame &f, int pid, std::vector<std::pair<uint64_t, int64_t>> &tmp, std::vector<Frame> &ch) {
-    if (f.depth == D0) {
-      // order below D0 on the full key (ties by original index)
-      tmp.resize(f.hi - f.lo);
-      for (int64_t p = f.lo; p < f.hi; p++) tmp[p - f.lo] = {ks[p], T.perm[p]};
-      std::sort(tmp.begin(), tmp.end());
-      for (int64_t p = f.lo; p < f.hi; p++) ks[p] = tmp[p - f.lo].first, T.perm[p] = tmp[p - f.lo].second;
-    }
-    // split [lo,hi) by the dim bits of depth f.depth+1 (the keys of the range
-    // are sorted on those bits: binary search each boundary)
-    const int shift = dim * (MAXD - f.depth - 1);
-    const uint64_t mask = (1u << dim) - 1;
-    ch.clear();
-    int64_t p = f.lo;
-    while (p < f.hi) {
-      const uint64_t grp = (ks[p] >> shift) & mask;
-      const int64_t q = std::upper_bound(ks.begin() + p, ks.begin() + f.hi, grp,
-                                         [&](uint64_t g, uint64_t k) { return g < ((k >> shift) & mask); }) -
-                        ks.begin();
-      Frame cf{p, q, f.depth + 1, pid, {0, 0, 0}};
-      for (int d = 0; d < dim; d++) cf.c[d] = 2 * f.c[d] + (int)((grp >> d) & 1);
-      ch.push_back(cf);
-      p = q;
-    }
-  };
-  // pre-order build from `stack` into V; with `deferred`, a node of depth
-  // stop_depth that splits is recorded but its subtree is deferred (V.task)
-  auto grow = [&](NodeVec &V, std::vector<Frame> &stack, int stop_depth, std::vector<Frame> *deferred) {
-    std::vector<Frame> ch;
-    std::vector<std::pair<uint64_t, int64_t>> tmp;
-    while (!stack.empty()) {
-      Frame f = stack.back();
-      stack.pop_back();
-      const int id = (int)V.depth.size();
-      V.depth.push_back(f.depth);
-      V.parent.push_back(f.parent);
-      for (int d = 0; d < 3; d++) V.coord.push_back(f.c[d]);
-      V.start.push_back(f.lo);
-      V.count.push_back(f.hi - f.lo);
-      V.task.push_back(-1);
-      V.maxdepth = std::max(V.maxdepth, f.depth);
-      if (f.hi - f.lo > T.leaf && f.depth < MAXD) {
-        if (deferred && f.depth == stop_depth) {
-          V.task.back() = (int)deferred->size();
-          deferred->push_back(f);
-          continue;
-        }
-        split(f, id, tmp, ch);
-        for (int i = (int)ch.size() - 1; i >= 0; i--) stack.push_back(ch[i]);  // pre-order
-      } else {
-        // a leaf keeps its points in original order
-        std::sort(T.perm.begin() + f.lo, T.perm.begin() + f.hi);
-      }
-    }
-  };
-  // the top of the tree sequentially; for large inputs the subtrees below
-  // depth DP on the host pool, then spliced in pre-order
-  const int DP = n >= ((int64_t)1 << 17) ? (dim == 2 ? 3 : 2) : -1;
-  NodeVec top;
-  std::vector<Frame> deferred, stack;
-  stack.push_back({0, n, 0, -1, {0, 0, 0}});
-  grow(top, stack, DP, DP >= 0 ? &deferred : nullptr);
-  std::vector<NodeVec> sub(deferred.size());
-  HostPool::get().parallel_for((int64_t)deferred.size(), [&](int64_t t) {
-    std::vector<Frame> st2, ch;
-    std::vector<std::pair<uint64_t, int64_t>> tmp;
-    split(deferred[t], -1, tmp, ch);  // -1: child of the deferred node
-    for (int i = (int)ch.size() - 1; i >= 0; i--) st2.push_back(ch[i]);
-    grow(sub[t], st2, -1, nullptr);
-  });
-  std::vector<int> top2g(top.depth.size());
-  T.maxdepth = top.maxdepth;
-  auto append = [&](const NodeVec &V, int j, int parent) {
-    T.depth.push_back(V.depth[j]);
-    T.parent.push_back(parent);
-    for (int d = 0; d < 3; d++) T.coord.push_back(V.coord[3 * j + d]);
-    T.start.push_back(V.start[j]);
-    T.count.push_back(V.count[j]);
-  };
-  for (size_t i = 0; i < top.depth.size(); i++) {
-    const int gid = (int)T.depth.size();
-    top2g[i] = gid;
-    append(top, (int)i, top.parent[i] < 0 ? -1 : top2g[top.parent[i]]);
-    if (top.task[i] >= 0) {
-      const NodeVec &V = sub[top.task[i]];
-      const int base = (int)T.depth.size();
-      for (size_t j = 0; j < V.depth.size(); j++) append(V, (int)j, V.parent[j] < 0 ? gid : base + V.parent[j]);
-      T.maxdepth = std::max(T.maxdepth, V.maxdepth);
-    }
-  }
-  T.x.resize((size_t)n * dim);
-  T.key.resize(n);
-  T.c20.resize((size_t)n * dim);
-  parallel_range(n, (int64_t)1 << 16, [&](int64_t lo, int64_t hi) {
-    for (int64_t g = lo; g < hi; g++) {
-      const int64_t i = T.perm[g];
-      T.key[g] = kf[i];
-      for (int d = 0; d < dim; d++) {
-        T.x[g * dim + d] = pts_host[i * dim + d];
-        T.c20[g * dim + d] = cc[(size_t)i * dim + d];
-      }
-    }
-  });
   T.level.assign(T.maxdepth + 1, {});
   for (int i = 0; i < (int)T.depth.size(); i++) T.level[T.depth[i]].push_back(i);
-  {
-    // elimination order within a depth: colour-major, Morton within a colour
-    std::vector<std::pair<int, uint64_t>> ord(T.depth.size());
-    for (size_t i = 0; i < T.depth.size(); i++) {
-      int64_t pc[3] = {T.coord[3 * i], T.coord[3 * i + 1], T.coord[3 * i + 2]};
-      ord[i] = {colour_of(&T.coord[3 * i], dim), morton_fast(pc, dim)};
+  std::vector<int> col(T.depth.size());
+  for (size_t i = 0; i < T.depth.size(); i++) col[i] = colour_of(&T.coord[3 * i], dim);
+  for (auto &lv : T.level) std::stable_sort(lv.begin(), lv.end(), [&](int a, int b) { return col[a] < col[b]; });
+}
+
+// Trees of nprob problems (device points pts[p], n[p] each) built on the GPU
+// (tree.cu) and copied to the host: one build over all problems when the
+// problem index fits above the Morton key, else one build per group.
+static void build_trees_gpu(std::vector<HTree> &trees, const double *const *pts, const int64_t *n, int nprob, int dim,
+                            int leaf, cudaStream_t st) {
+  // problems per build: dim * 20 key bits plus the problem index within 64
+  const int max_bits = 64 - dim * 20;
+  const int per_build = max_bits >= 24 ? (1 << 24) : (1 << max_bits);
+  for (int p0 = 0; p0 < nprob; p0 += per_build) {
+    const int np = std::min(per_build, nprob - p0);
+    std::vector<int64_t> pofs(np + 1, 0);
+    for (int p = 0; p < np; p++) pofs[p + 1] = pofs[p] + n[p0 + p];
+    const int64_t N = pofs[np];
+    int bits = 0;
+    while ((1 << bits) < np) bits++;
+    DBuf d_pts, d_pofs, scratch;
+    const double *P = pts[p0];
+    if (np > 1 && N > 0) {
+      d_pts.alloc(sizeof(double) * (size_t)N * dim, st, 1);
+      for (int p = 0; p < np; p++)
+        if (n[p0 + p] > 0)
+          CK(cudaMemcpyAsync(ptr<double>(d_pts) + pofs[p] * dim, pts[p0 + p], sizeof(double) * n[p0 + p] * dim,
+                             cudaMemcpyDeviceToDevice, st));
+      P = ptr<double>(d_pts);
     }
-    for (auto &lv : T.level) std::sort(lv.begin(), lv.end(), [&](int a, int b) { return ord[a] < ord[b]; });
+    upload(d_pofs, pofs, st);
+    TreeGpu G;
+    G.pts = P;
+    G.n = N;
+    G.dim = dim;
+    G.leaf = leaf;
+    G.pofs = ptr<int64_t>(d_pofs);
+    G.nprob = np;
+    G.prob_bits = bits;
+    scratch.alloc((size_t)tree_gpu_scratch_bytes(N, dim), st, 1);
+    tree_gpu_sort(G, scratch.p, st);
+    uint32_t nnode = 0;
+    CK(cudaMemcpyAsync(&nnode, G.total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    DBuf o_depth, o_parent, o_coord, o_start, o_count, o_perm, o_x, o_c20, o_key;
+    o_depth.alloc(sizeof(int) * std::max<uint32_t>(nnode, 1), st, 1);
+    o_parent.alloc(sizeof(int) * std::max<uint32_t>(nnode, 1), st, 1);
+    o_coord.alloc(sizeof(int) * 3 * std::max<uint32_t>(nnode, 1), st, 1);
+    o_start.alloc(sizeof(int64_t) * std::max<uint32_t>(nnode, 1), st, 1);
+    o_count.alloc(sizeof(int64_t) * std::max<uint32_t>(nnode, 1), st, 1);
+    o_perm.alloc(sizeof(int64_t) * std::max<int64_t>(N, 1), st, 1);
+    o_x.alloc(sizeof(double) * std::max<int64_t>(N, 1) * dim, st, 1);
+    o_c20.alloc(sizeof(int) * std::max<int64_t>(N, 1) * dim, st, 1);
+    o_key.alloc(sizeof(uint64_t) * std::max<int64_t>(N, 1), st, 1);
+    tree_gpu_nodes(G, ptr<int>(o_depth), ptr<int>(o_parent), ptr<int>(o_coord), ptr<int64_t>(o_start),
+                   ptr<int64_t>(o_count), ptr<int64_t>(o_perm), ptr<double>(o_x), ptr<int>(o_c20),
+                   ptr<uint64_t>(o_key), st);
+    check_launch("tree");
+    std::vector<int> depth(nnode), parent(nnode), coord((size_t)3 * nnode);
+    std::vector<int64_t> start(nnode), count(nnode), perm(N);
+    std::vector<double> x((size_t)N * dim);
+    std::vector<int> c20((size_t)N * dim);
+    std::vector<uint64_t> key(N);
+    auto d2h = [&](void *dst, const DBuf &src, size_t bytes) {
+      if (bytes) CK(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToHost, st));
+    };
+    d2h(depth.data(), o_depth, sizeof(int) * nnode);
+    d2h(parent.data(), o_parent, sizeof(int) * nnode);
+    d2h(coord.data(), o_coord, sizeof(int) * 3 * nnode);
+    d2h(start.data(), o_start, sizeof(int64_t) * nnode);
+    d2h(count.data(), o_count, sizeof(int64_t) * nnode);
+    d2h(perm.data(), o_perm, sizeof(int64_t) * N);
+    d2h(x.data(), o_x, sizeof(double) * N * dim);
+    d2h(c20.data(), o_c20, sizeof(int) * N * dim);
+    d2h(key.data(), o_key, sizeof(uint64_t) * N);
+    CK(cudaStreamSynchronize(st));
+    // split into the problems: a problem's nodes are contiguous (its points
+    // are, and nodes are ordered by first point)
+    int node0 = 0;
+    for (int p = 0; p < np; p++) {
+      HTree &T = trees[p0 + p];
+      T.dim = dim;
+      T.leaf = leaf;
+      T.n = n[p0 + p];
+      const int64_t off = pofs[p];
+      int node1 = node0;
+      while (node1 < (int)nnode && start[node1] < pofs[p + 1]) node1++;
+      if (T.n == 0) node1 = node0;
+      const int nn = node1 - node0;
+      T.depth.assign(depth.begin() + node0, depth.begin() + node1);
+      T.parent.resize(nn);
+      T.start.resize(nn);
+      T.count.assign(count.begin() + node0, count.begin() + node1);
+      T.coord.assign(coord.begin() + 3 * (size_t)node0, coord.begin() + 3 * (size_t)node1);
+      T.maxdepth = 0;
+      for (int i = 0; i < nn; i++) {
+        T.parent[i] = parent[node0 + i] < 0 ? -1 : parent[node0 + i] - node0;
+        T.start[i] = start[node0 + i] - off;
+        T.maxdepth = std::max(T.maxdepth, T.depth[i]);
+      }
+      if (nn == 0) {
+        // an empty problem: a root of depth 0 holding nothing
+        T.depth = {0};
+        T.parent = {-1};
+        T.coord = {0, 0, 0};
+        T.start = {0};
+        T.count = {0};
+      }
+      T.perm.resize(T.n);
+      for (int64_t g = 0; g < T.n; g++) T.perm[g] = perm[off + g] - off;
+      T.x.assign(x.begin() + off * dim, x.begin() + (off + T.n) * dim);
+      T.c20.assign(c20.begin() + off * dim, c20.begin() + (off + T.n) * dim);
+      T.key.assign(key.begin() + off, key.begin() + off + T.n);
+      level_lists(T);
+      node0 = node1;
+    }
   }
 }
 
@@ -1815,14 +1727,6 @@ template <typename F> static rss_status guard(F &&fn) {
   }
 }
 
-static void fetch_points(const double *pts, int64_t n, int dim, std::vector<double> &h, cudaStream_t st) {
-  h.resize((size_t)std::max<int64_t>(n, 1) * dim);
-  if (n > 0) {
-    CK(cudaMemcpyAsync(h.data(), pts, sizeof(double) * n * dim, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-  }
-}
-
 // One phase of a sweep: the chunked solve kernels when they apply, else the
 // one-CTA-per-box kernel (apply sweeps, more than four right-hand sides, the
 // forced large-box path).
@@ -2329,12 +2233,10 @@ rss_status rss_build_tree(const double *pts, int64_t n, int dim, int leaf_size, 
     if (!out || n < 0 || (dim != 2 && dim != 3) || leaf_size < 1 || (n > 0 && !pts))
       throw Fail{RSS_EINVAL, "rss_build_tree: bad arguments"};
     std::unique_ptr<rss_tree> tr(new rss_tree());
-    tr->t.dim = dim;
-    tr->t.leaf = leaf_size;
-    tr->t.n = n;
-    std::vector<double> h;
-    fetch_points(pts, n, dim, h, nullptr);
-    build_tree(tr->t, h.data());
+    std::vector<HTree> one(1);
+    const double *pp[1] = {pts};
+    build_trees_gpu(one, pp, &n, 1, dim, leaf_size, nullptr);
+    tr->t = std::move(one[0]);
     *out = tr.release();
   });
 }
@@ -2426,8 +2328,6 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
     const bool prof_on = o.profile != 0;
     if (o.prec != RSS_FP64 && o.prec != RSS_MIXED) throw Fail{RSS_EINVAL, "rss_factor: bad precision"};
     cudaStream_t st = (cudaStream_t)o.stream;
-    std::vector<std::vector<double>> h(nprob);
-    for (int p = 0; p < nprob; p++) fetch_points(pts[p], n[p], dim, h[p], st);
     const MlpModel *mlp = nullptr;
     if (o.mlp) {
       if (o.mlp->magic != MAGIC_MLP || !o.mlp->impl) throw Fail{RSS_EINVAL, "rss_factor: bad rank-proposal handle"};
@@ -2449,20 +2349,9 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
         F->trees[p].n = n[p];
       }
       F->n = F->pdof[nprob];
+      // the trees of every problem, built on the GPU in one pass
       double tt0 = now_ms();
-      if (nprob == 1) {
-        build_tree(F->trees[0], h[0].data());
-      } else {
-        // independent trees on host threads
-        unsigned hw = std::thread::hardware_concurrency();
-        int nt = (int)std::min<unsigned>(hw ? hw : 1, 16);
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; t++)
-          th.emplace_back([&, t] {
-            for (int p = t; p < nprob; p += nt) build_tree(F->trees[p], h[p].data());
-          });
-        for (auto &x : th) x.join();
-      }
+      build_trees_gpu(F->trees, pts, n, nprob, dim, leaf_size, st);
       F->prof.host(KC_HOST_TREE, now_ms() - tt0);
       F->K.kind = kernel.kind;
       F->K.diag = kernel.diag;
@@ -2653,6 +2542,88 @@ rss_status rss_stats(const rss_factorization *f, int64_t *buf, size_t *nbytes) {
     if (buf) {
       if (cap < need) throw Fail{RSS_EINVAL, "rss_stats: buffer too small"};
       memcpy(buf, s.data(), need);
+    }
+  });
+}
+
+rss_status rss_stats_json(const rss_factorization *f, char *buf, size_t *nbytes) {
+  return guard([&] {
+    if (!f || !f->impl || !nbytes) throw Fail{RSS_EINVAL, "rss_stats_json: bad arguments"};
+    std::string js;
+    auto num = [&](const char *key, double v, bool comma = true) {
+      char tmp[96];
+      snprintf(tmp, sizeof(tmp), "\"%s\": %.17g%s", key, v, comma ? ", " : "");
+      js += tmp;
+    };
+    auto fill = [&](const auto &F) {
+      const int64_t sz = F.prec == RSS_FP64 ? 8 : 4;
+      js += "{";
+      num("n", (double)F.n);
+      num("problems", F.nprob);
+      num("dim", F.dim);
+      js += std::string("\"precision\": \"") + (F.prec == RSS_FP64 ? "fp64" : "fp32") + "\", ";
+      num("eps", F.eps);
+      num("colours_per_level", (F.flags & RSS_FLAG_COLOUR_2D) ? (1 << F.dim) : (F.dim == 2 ? 9 : 27));
+      num("maxdepth", F.maxdepth);
+      num("boxes", (double)F.h_boxes.size());
+      num("top_block", F.ntop);
+      num("factor_bytes", (double)F.factor_bytes);
+      num("reserved_bytes", (double)(F.reserved_T * sz));
+      num("used_bytes", (double)(F.used_T * sz));
+      num("overflow_bytes", (double)(F.ovf_used * sz));
+      num("retried", F.retries);
+      num("rank_proposal", F.mlp ? 1 : 0);
+      // per depth: boxes, sum and largest of |B|, k, |J|
+      js += "\"levels\": [";
+      bool first = true;
+      for (int t = F.maxdepth; t >= 0; t--) {
+        int64_t cnt = 0, sb = 0, sk = 0, sj = 0, mb = 0, mk = 0, mj = 0;
+        for (const auto &b : F.h_boxes) {
+          if (b.depth != t) continue;
+          cnt++;
+          sb += b.b, sk += b.k, sj += b.nj;
+          mb = std::max<int64_t>(mb, b.b), mk = std::max<int64_t>(mk, b.k), mj = std::max<int64_t>(mj, b.nj);
+        }
+        if (!cnt) continue;
+        js += first ? "{" : ", {";
+        first = false;
+        num("depth", t);
+        num("boxes", (double)cnt);
+        num("b_sum", (double)sb);
+        num("k_sum", (double)sk);
+        num("nj_sum", (double)sj);
+        num("b_max", (double)mb);
+        num("k_max", (double)mk);
+        num("nj_max", (double)mj, false);
+        js += "}";
+      }
+      js += "], ";
+      // per box in elimination order: depth, |B|, k, |J|
+      const char *names[4] = {"box_depth", "box_b", "box_k", "box_nj"};
+      for (int q = 0; q < 4; q++) {
+        js += std::string("\"") + names[q] + "\": [";
+        for (size_t i = 0; i < F.h_boxes.size(); i++) {
+          const auto &b = F.h_boxes[i];
+          const int v = q == 0 ? b.depth : q == 1 ? b.b : q == 2 ? b.k : b.nj;
+          js += (i ? ", " : "") + std::to_string(v);
+        }
+        js += "], ";
+      }
+      // kernel-class times when the factor was created with profiling
+      const Prof &P = F.prof;
+      static const char *cls[KC_N] = {"assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve",
+                                      "permute", "host_tree", "host_level", "host_wait", "residual_operator"};
+      js += "\"profile_ms\": {";
+      for (int c = 0; c < KC_N; c++) num(cls[c], P.ms[c], c + 1 < KC_N);
+      js += "}}";
+    };
+    if (f->impl->prec == RSS_FP64) fill(static_cast<const Factor<double> &>(*f->impl));
+    else fill(static_cast<const Factor<float> &>(*f->impl));
+    const size_t need = js.size() + 1, cap = *nbytes;
+    *nbytes = need;
+    if (buf) {
+      if (cap < need) throw Fail{RSS_EINVAL, "rss_stats_json: buffer too small"};
+      memcpy(buf, js.c_str(), need);
     }
   });
 }

@@ -196,6 +196,30 @@ void mlp_gradient(const void *wbf, const float *X, const float *y, int64_t n, fl
 void mlp_adam(float *theta, float *m, float *v, const float *grad, void *wbf, int *step, float lr,
               cudaStream_t st);
 
+// The adaptive tree on the GPU (tree.cu).  Points of nprob problems,
+// concatenated (problem p's first point is pofs[p], device array of nprob + 1);
+// prob_bits: bits for the problem index above the 20 dim Morton key bits
+// (dim * 20 + prob_bits <= 64).  tree_gpu_sort sorts and counts the nodes
+// (total at T.total, device); tree_gpu_nodes writes the nodes in pre-order
+// (start: sorted position) and the tree-order permutation, coordinates,
+// depth-20 cells and Morton keys.
+struct TreeGpu {
+  const double *pts = nullptr;
+  int64_t n = 0;
+  int dim = 2, leaf = 64;
+  const int64_t *pofs = nullptr;
+  int nprob = 1, prob_bits = 0;
+  uint64_t *k0 = nullptr, *k1 = nullptr, *mkey = nullptr;
+  int64_t *i0 = nullptr, *i1 = nullptr;
+  int *c20 = nullptr, *c20s = nullptr, *Lp = nullptr;
+  uint32_t *nd = nullptr, *hist = nullptr, *total = nullptr;
+  int64_t nblk = 0;
+};
+int64_t tree_gpu_scratch_bytes(int64_t n, int dim);
+void tree_gpu_sort(TreeGpu &T, void *scratch, cudaStream_t st);
+void tree_gpu_nodes(const TreeGpu &T, int *depth, int *parent, int *coord, int64_t *start, int64_t *count,
+                    int64_t *perm, double *x, int *c20t, uint64_t *keyt, cudaStream_t st);
+
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n = 1);
 long long launches_total();

@@ -1,0 +1,349 @@
+// tree.cu -- the adaptive 2^d-tree of the factorization (Sec. 3: boxes are
+// split until every leaf holds at most leaf_size points; Sec. 4: refined to
+// n_occ points per leaf) built on the GPU.
+//
+// The tree is the one a recursive split produces: root [0,1]^d, a node of
+// depth t splits iff it holds more than leaf_size points and t < 20; the
+// integer cell of coordinate v at depth t is floor(v 2^t) clamped to
+// [0, 2^t - 1]; child index sum_d bit_d << d; DOFs in stable pre-order
+// (children ascending, points of a leaf in original order); nodes numbered
+// in pre-order.  It is computed without recursion:
+//   1. every point's depth-20 cell and Morton key (x in the lowest bit of each
+//      group of d bits, a problem index above the 20 d key bits when several
+//      problems share the build);
+//   2. a stable LSD radix sort of (key, index) -- a depth-t node is a run of
+//      points sharing the key's top d t bits, and the runs come out in child
+//      order;
+//   3. a point's leaf depth L is the first depth at which its run holds at
+//      most leaf_size points (or 20): found by bisection on the depth, each
+//      run's extent by binary search in the sorted keys;
+//   4. a node of depth t starts at point p iff p starts a depth-t run and
+//      t <= L(p); the depths at which p starts a run are t_b(p) .. 20, t_b
+//      given by the highest bit where p's key differs from its predecessor's,
+//      so p starts nodes at depths t_b(p) .. L(p), and pre-order numbering is
+//      the order of (start, depth): an exclusive scan of the per-point node
+//      counts;
+//   5. within a leaf shallower than 20, the points are put back in original
+//      order (a rank sort of at most leaf_size indices).
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "internal.h"
+
+namespace rss {
+
+namespace {
+
+constexpr int RS_T = 256;              // threads per radix-sort block
+constexpr int RS_ITEMS = 8;            // sub-tiles of RS_T keys per block
+constexpr int RS_TILE = RS_T * RS_ITEMS;
+constexpr int MAXD = 20;               // maximum depth of the tree
+
+__device__ __forceinline__ uint64_t spread2(uint64_t x) {
+  x &= 0x1fffffULL;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffULL;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffULL;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+  x = (x | (x << 2)) & 0x3333333333333333ULL;
+  x = (x | (x << 1)) & 0x5555555555555555ULL;
+  return x;
+}
+__device__ __forceinline__ uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffULL;
+  x = (x | (x << 32)) & 0x001f00000000ffffULL;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffULL;
+  x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+  x = (x | (x << 2)) & 0x1249249249249249ULL;
+  return x;
+}
+
+// Depth-20 cells, Morton keys and point indices.  pofs (nprob + 1 entries)
+// gives each problem's first point; the problem index goes above the key.
+__global__ void k_tree_keys(const double *__restrict__ pts, int64_t n, int dim, const int64_t *__restrict__ pofs,
+                            int nprob, uint64_t *__restrict__ key, uint64_t *__restrict__ mkey,
+                            int64_t *__restrict__ idx, int *__restrict__ c20) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = nprob;  // problem of point i: last p with pofs[p] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pofs[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  uint64_t c[3] = {0, 0, 0};
+  const double m = (double)(1 << MAXD);
+  for (int d = 0; d < dim; d++) {
+    int64_t v = (int64_t)floor(pts[i * dim + d] * m);
+    v = v < 0 ? 0 : (v > (1 << MAXD) - 1 ? (1 << MAXD) - 1 : v);
+    c[d] = (uint64_t)v;
+    c20[i * dim + d] = (int)v;
+  }
+  const uint64_t mk = dim == 2 ? (spread2(c[0]) | (spread2(c[1]) << 1))
+                               : (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
+  mkey[i] = mk;
+  key[i] = ((uint64_t)lo << (dim * MAXD)) | mk;
+  idx[i] = i;
+}
+
+// Radix sort pass, part 1: per block, the counts of the 8-bit digit at
+// `shift` over its tile, stored digit-major (digit * nblk + block).
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *__restrict__ key, int64_t n, int shift,
+                                                  uint32_t *__restrict__ hist, int nblk) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+  for (int it = 0; it < RS_ITEMS; it++) {
+    const int64_t e = t0 + it * RS_T + threadIdx.x;
+    if (e < n) atomicAdd(&h[(key[e] >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// In-place exclusive scan of len counts by one block of 1024 threads (each
+// scans a contiguous share, the shares' totals are scanned in shared
+// memory).  total (may be NULL) receives the sum.
+__global__ void __launch_bounds__(1024) k_scan_excl(uint32_t *a, int64_t len, uint32_t *total) {
+  __shared__ uint32_t s[1024];
+  const int64_t per = (len + 1023) / 1024;
+  const int64_t lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
+  uint32_t sum = 0;
+  for (int64_t i = lo; i < hi; i++) sum += a[i];
+  s[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
+    __syncthreads();
+    s[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = s[threadIdx.x] - sum;
+  for (int64_t i = lo; i < hi; i++) {
+    const uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  if (total && threadIdx.x == 1023) *total = s[1023];
+}
+
+// Radix sort pass, part 2: stable scatter.  Each block walks its tile in
+// sub-tiles of RS_T keys in index order; a key's position is its digit's
+// offset for the block, plus the keys with that digit in earlier sub-tiles,
+// earlier warps and earlier lanes of its warp.
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict__ kin, const int64_t *__restrict__ iin,
+                                                     uint64_t *__restrict__ kout, int64_t *__restrict__ iout, int64_t n,
+                                                     int shift, const uint32_t *__restrict__ offs, int nblk) {
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t wcnt[RS_T / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  base[tid] = offs[(int64_t)tid * nblk + blockIdx.x];
+  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+  for (int it = 0; it < RS_ITEMS; it++) {
+    for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
+    __syncthreads();
+    const int64_t e = t0 + it * RS_T + tid;
+    const bool ok = e < n;
+    const uint64_t k = ok ? kin[e] : 0;
+    const int64_t ix = ok ? iin[e] : 0;
+    const int dig = ok ? (int)((k >> shift) & 255) : 256 + lane;  // absent keys: a digit of their own
+    const unsigned peers = __match_any_sync(0xffffffffu, dig);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (ok && rank == 0) wcnt[warp][dig] = __popc(peers);
+    __syncthreads();
+    if (ok) {
+      uint32_t pos = base[dig] + (uint32_t)rank;
+      for (int w = 0; w < warp; w++) pos += wcnt[w][dig];
+      kout[pos] = k;
+      iout[pos] = ix;
+    }
+    __syncthreads();
+    uint32_t s = 0;
+    for (int w = 0; w < RS_T / 32; w++) s += wcnt[w][tid];
+    base[tid] += s;
+    __syncthreads();
+  }
+}
+
+// First position q in [0, n) with (key[q] >> sh) >= P, and the first with > P.
+__device__ __forceinline__ int64_t prefix_lower(const uint64_t *key, int64_t n, uint64_t P, int sh) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((key[mid] >> sh) < P) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t prefix_upper(const uint64_t *key, int64_t n, uint64_t P, int sh) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((key[mid] >> sh) <= P) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// First depth at which sorted point p starts a run (0 for the first point of
+// a problem; 21: never, its key equals its predecessor's).
+__device__ __forceinline__ int run_start_depth(const uint64_t *key, int64_t p, int dim) {
+  if (p == 0) return 0;
+  const uint64_t x = key[p] ^ key[p - 1];
+  if (x == 0) return MAXD + 1;
+  const int hb = 63 - __clzll((long long)x);
+  const int t = MAXD - hb / dim;
+  return t < 0 ? 0 : t;
+}
+
+// Leaf depth of every sorted point, and the number of nodes each starts.
+__global__ void k_tree_depths(const uint64_t *__restrict__ key, int64_t n, int dim, int leaf, int *__restrict__ L,
+                              uint32_t *__restrict__ nd) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int lo = 0, hi = MAXD;  // first depth whose run holds <= leaf points, or 20
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int sh = dim * (MAXD - mid);
+    const uint64_t P = key[p] >> sh;
+    const int64_t cnt = prefix_upper(key, n, P, sh) - prefix_lower(key, n, P, sh);
+    if (cnt <= leaf) hi = mid;
+    else lo = mid + 1;
+  }
+  L[p] = lo;
+  const int tb = run_start_depth(key, p, dim);
+  nd[p] = tb <= lo ? (uint32_t)(lo - tb + 1) : 0u;
+}
+
+// The nodes (pre-order ids = exclusive scan of the per-point counts): depth,
+// parent, coordinates, first point and count.  Points are sorted positions;
+// prob_first (per problem) turns them into positions within the problem.
+__global__ void k_tree_nodes(const uint64_t *__restrict__ key, const int *__restrict__ c20s, int64_t n, int dim,
+                             const int *__restrict__ L, const uint32_t *__restrict__ base, int *__restrict__ depth,
+                             int *__restrict__ parent, int *__restrict__ coord, int64_t *__restrict__ start,
+                             int64_t *__restrict__ count) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int tb = run_start_depth(key, p, dim), lp = L[p];
+  for (int t = tb; t <= lp; t++) {
+    const int id = (int)base[p] + (t - tb);
+    const int sh = dim * (MAXD - t);
+    depth[id] = t;
+    start[id] = p;
+    count[id] = prefix_upper(key, n, key[p] >> sh, sh) - p;
+    for (int d = 0; d < 3; d++) coord[3 * id + d] = d < dim ? (c20s[p * dim + d] >> (MAXD - t)) : 0;
+    if (t > tb) {
+      parent[id] = id - 1;  // the parent starts at the same point
+    } else if (t == 0) {
+      parent[id] = -1;
+    } else {
+      const int shp = dim * (MAXD - t + 1);
+      const int64_t s = prefix_lower(key, n, key[p] >> shp, shp);
+      parent[id] = (int)base[s] + (t - 1 - run_start_depth(key, s, dim));
+    }
+  }
+}
+
+// Points of a leaf shallower than 20 back in original order; deeper leaves
+// (equal keys) already are, by the stable sort.
+__global__ void k_tree_leaf_order(const uint64_t *__restrict__ key, const int64_t *__restrict__ idx, int64_t n,
+                                  int dim, const int *__restrict__ L, int64_t *__restrict__ perm) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int lp = L[p];
+  if (lp >= MAXD) {
+    perm[p] = idx[p];
+    return;
+  }
+  const int sh = dim * (MAXD - lp);
+  const uint64_t P = key[p] >> sh;
+  const int64_t s = prefix_lower(key, n, P, sh), e = prefix_upper(key, n, P, sh);
+  const int64_t me = idx[p];
+  int64_t rank = 0;
+  for (int64_t q = s; q < e; q++) rank += idx[q] < me;
+  perm[s + rank] = me;
+}
+
+// Tree-order copies: coordinates, depth-20 cells and Morton keys.
+__global__ void k_tree_gather(const double *__restrict__ pts, const int *__restrict__ c20, const uint64_t *__restrict__ mkey,
+                              const int64_t *__restrict__ perm, int64_t n, int dim, double *__restrict__ x,
+                              int *__restrict__ c20t, uint64_t *__restrict__ keyt) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int64_t i = perm[g];
+  for (int d = 0; d < dim; d++) {
+    x[g * dim + d] = pts[i * dim + d];
+    c20t[g * dim + d] = c20[i * dim + d];
+  }
+  keyt[g] = mkey[i];
+}
+
+__global__ void k_tree_sorted_cells(const int *__restrict__ c20, const int64_t *__restrict__ idx, int64_t n, int dim,
+                                    int *__restrict__ c20s) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int64_t i = idx[p];
+  for (int d = 0; d < dim; d++) c20s[p * dim + d] = c20[i * dim + d];
+}
+
+inline unsigned nb256(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+int64_t tree_gpu_scratch_bytes(int64_t n, int dim) {
+  const int64_t nblk = (n + RS_TILE - 1) / RS_TILE;
+  auto r16 = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
+  return 3 * r16(8 * n) + 2 * r16(8 * n) + 2 * r16(4 * n * dim) + 2 * r16(4 * n) + r16(4 * 256 * nblk) + 16 + 64;
+}
+
+void tree_gpu_sort(TreeGpu &T, void *scratch, cudaStream_t st) {
+  unsigned char *w = static_cast<unsigned char *>(scratch);
+  auto take = [&](int64_t bytes) {
+    void *r = w;
+    w += (bytes + 15) & ~(int64_t)15;
+    return r;
+  };
+  const int64_t n = T.n;
+  const int dim = T.dim;
+  T.k0 = (uint64_t *)take(8 * n);
+  T.k1 = (uint64_t *)take(8 * n);
+  T.mkey = (uint64_t *)take(8 * n);
+  T.i0 = (int64_t *)take(8 * n);
+  T.i1 = (int64_t *)take(8 * n);
+  T.c20 = (int *)take(4 * n * dim);
+  T.c20s = (int *)take(4 * n * dim);
+  T.Lp = (int *)take(4 * n);
+  T.nd = (uint32_t *)take(4 * n);
+  T.nblk = (n + RS_TILE - 1) / RS_TILE;
+  T.hist = (uint32_t *)take(4 * 256 * T.nblk);
+  T.total = (uint32_t *)take(16);
+  cudaMemsetAsync(T.total, 0, sizeof(uint32_t), st);
+  if (n == 0) return;
+  k_tree_keys<<<nb256(n), 256, 0, st>>>(T.pts, n, dim, T.pofs, T.nprob, T.k0, T.mkey, T.i0, T.c20); count_launch();
+  const int bits = dim * MAXD + T.prob_bits;
+  for (int sh = 0; sh < bits; sh += 8) {
+    k_rs_hist<<<(unsigned)T.nblk, RS_T, 0, st>>>(T.k0, n, sh, T.hist, (int)T.nblk); count_launch();
+    k_scan_excl<<<1, 1024, 0, st>>>(T.hist, 256 * T.nblk, nullptr); count_launch();
+    k_rs_scatter<<<(unsigned)T.nblk, RS_T, 0, st>>>(T.k0, T.i0, T.k1, T.i1, n, sh, T.hist, (int)T.nblk);
+    count_launch();
+    std::swap(T.k0, T.k1);
+    std::swap(T.i0, T.i1);
+  }
+  k_tree_depths<<<nb256(n), 256, 0, st>>>(T.k0, n, dim, T.leaf, T.Lp, T.nd); count_launch();
+  k_scan_excl<<<1, 1024, 0, st>>>(T.nd, n, T.total); count_launch();
+}
+
+void tree_gpu_nodes(const TreeGpu &T, int *depth, int *parent, int *coord, int64_t *start, int64_t *count,
+                    int64_t *perm, double *x, int *c20t, uint64_t *keyt, cudaStream_t st) {
+  const int64_t n = T.n;
+  if (n == 0) return;
+  k_tree_sorted_cells<<<nb256(n), 256, 0, st>>>(T.c20, T.i0, n, T.dim, T.c20s); count_launch();
+  k_tree_nodes<<<nb256(n), 256, 0, st>>>(T.k0, T.c20s, n, T.dim, T.Lp, T.nd, depth, parent, coord, start, count);
+  count_launch();
+  k_tree_leaf_order<<<nb256(n), 256, 0, st>>>(T.k0, T.i0, n, T.dim, T.Lp, perm); count_launch();
+  k_tree_gather<<<nb256(n), 256, 0, st>>>(T.pts, T.c20, T.mkey, perm, n, T.dim, x, c20t, keyt); count_launch();
+}
+
+}  // namespace rss

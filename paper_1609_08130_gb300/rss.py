@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "librss.so")
-SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu", "logdet.cu", "schur_tc.cu"]
+SOURCES = ["api.cu", "kernels.cu", "refine.cu", "mlp.cu", "logdet.cu", "schur_tc.cu", "tree.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -91,6 +91,7 @@ _SIGS = {
                                     C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rss_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_logdet": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rss_stats_json": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_size_t)]),
     "rss_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_mlp_create": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "rss_mlp_params": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -336,6 +337,15 @@ class Factorization:
                     overflow_bytes=int(buf[8]), retried=int(buf[9]), proposal=int(buf[10]),
                     depth=boxes[:, 0].copy(), b=boxes[:, 1].copy(), k=boxes[:, 2].copy(),
                     nj=boxes[:, 3].copy(), rres=boxes[:, 4].copy(), njres=boxes[:, 5].copy())
+
+    def stats_json(self) -> dict:
+        """rss_stats_json, parsed."""
+        import json
+        nb = C.c_size_t(0)
+        _check(lib().rss_stats_json(self.h, None, C.byref(nb)))
+        buf = C.create_string_buffer(nb.value)
+        _check(lib().rss_stats_json(self.h, buf, C.byref(nb)))
+        return json.loads(buf.value.decode())
 
     def box_features(self):
         """rss_box_features: (features (nbox, 16) float32, ranks (nbox,) int32)."""
