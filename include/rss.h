@@ -95,6 +95,12 @@ typedef struct {
  * keeps FP32 accuracy); the same factorization up to rounding.  For
  * comparisons; the FP64 factor always uses FP64 SIMT arithmetic. */
 #define RSS_FLAG_NO_TENSOR_CORES 8
+/* Symmetric storage: both kernels are symmetric, so G = X_RR^{-1} X_RJ is
+ * E^T (E = X_JR X_RR^{-1}; Sec. 3.3, V_i = W_i^T) and only E is kept: the
+ * boxes' factor storage drops by |J| r entries each (the largest share),
+ * and the sweeps read E transposed where they read G.  The same
+ * factorization up to rounding. */
+#define RSS_FLAG_SYMMETRIC_STORAGE 16
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;
@@ -222,6 +228,19 @@ rss_status rss_solve_refined(const rss_factorization *f, const double *b, double
  * (x then holds the last iterate). */
 rss_status rss_solve_cg(const rss_factorization *f, const double *b, double *x, int nrhs, double tol, int maxit,
                         int *iters, double *relres);
+
+/* rss_sqrt_apply -- y = F^{1/2} x (transpose = 0) or y = (F^{1/2})^T x
+ * (transpose = 1), the generalized square root of the remark after
+ * Eq. 3.11: for symmetric positive definite A the factor is F = V D V^T
+ * (W = V^T), and with D = C C^T (C the block lower triangular Cholesky
+ * factors of every box's X_RR and of the top blocks) F^{1/2} = V C, so that
+ * F = F^{1/2} (F^{1/2})^T.  The Cholesky factors are rebuilt from the stored
+ * LU factors on the first call (X = P^T L U, then the factor of its
+ * symmetric part) and kept with the factorization.  x, y: device, n x nrhs
+ * column-major, may not alias.  Errors: RSS_EINVAL (bad arguments, a top
+ * block larger than 4096); RSS_ENUMERIC when a diagonal block is not
+ * positive definite (A is not). */
+rss_status rss_sqrt_apply(const rss_factorization *f, const double *x, double *y, int nrhs, int transpose);
 
 /* rss_matvec -- y = A x in FP64 with the exact operator being factored:
  * an FFT convolution when the points are the cell centres of an s^dim grid

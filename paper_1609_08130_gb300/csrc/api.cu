@@ -456,11 +456,18 @@ static void build_trees_gpu(std::vector<HTree> &trees, const double *const *pts,
         T.start = {0};
         T.count = {0};
       }
-      T.perm.resize(T.n);
-      for (int64_t g = 0; g < T.n; g++) T.perm[g] = perm[off + g] - off;
-      T.x.assign(x.begin() + off * dim, x.begin() + (off + T.n) * dim);
-      T.c20.assign(c20.begin() + off * dim, c20.begin() + (off + T.n) * dim);
-      T.key.assign(key.begin() + off, key.begin() + off + T.n);
+      if (np == 1) {  // the whole build is this problem's
+        T.perm.swap(perm);
+        T.x.swap(x);
+        T.c20.swap(c20);
+        T.key.swap(key);
+      } else {
+        T.perm.resize(T.n);
+        for (int64_t g = 0; g < T.n; g++) T.perm[g] = perm[off + g] - off;
+        T.x.assign(x.begin() + off * dim, x.begin() + (off + T.n) * dim);
+        T.c20.assign(c20.begin() + off * dim, c20.begin() + (off + T.n) * dim);
+        T.key.assign(key.begin() + off, key.begin() + off + T.n);
+      }
       level_lists(T);
       node0 = node1;
     }
@@ -794,6 +801,11 @@ template <typename T> struct Factor : FactorBase {
   std::vector<int64_t> h_toff, h_loff;
   DBuf d_top, d_topLU, d_toppiv, d_tn, d_toff, d_loff;
   mutable DBuf d_work, d_topwork;
+  // Cholesky factors of the diagonal blocks for the generalized square root
+  // (rss_sqrt_apply), built on its first use
+  mutable DBuf d_chol, d_coff, d_cerr;
+  mutable bool chol_ready = false;
+  mutable int chol_rmax = 0;
   mutable int work_nrhs = 0, work_gen = 0;
   // solve sweeps captured in a CUDA graph, one per nrhs <= 4, replayed with
   // fixed input/output buffers (options.use_graphs)
@@ -1254,6 +1266,9 @@ template <typename T> static void run_factor(Factor<T> &F) {
 
   // colours per level: 3^d (same-colour boxes share nothing) or the paper's 2^d
   const int cbase = (F.flags & RSS_FLAG_COLOUR_2D) ? 2 : 3;
+  // symmetric storage: the kernels are symmetric, so G = E^T (Sec. 3.3) and
+  // only E is kept
+  const bool symm = (F.flags & RSS_FLAG_SYMMETRIC_STORAGE) != 0;
   std::unordered_map<int64_t, int> child_b;  // (problem, node) -> sum of its children's b
   DBuf gid, gel, gtri, gcnt;                 // per-phase ID and elimination scratch, grown as needed
   if (F.mlp) F.d_ovf_used.alloc(sizeof(unsigned long long), st);
@@ -1442,7 +1457,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       const size_t b = H.cell_b[H.box_cell[q]], nj = njmaxv[q], rr = rres[q], njr = njres[q];
       sz_i64 += b + nj;
       sz_i32 += b + 2 * nj + b;
-      sz_T += b * b / 4 + 1 + 2 * rr * rr + 2 * njr * rr;
+      sz_T += b * b / 4 + 1 + 2 * rr * rr + (symm ? 1 : 2) * njr * rr;
     }
     int64_t *p64 = (int64_t *)F.alloc_store(sz_i64 * sizeof(int64_t));
     int *p32 = (int *)F.alloc_store(sz_i32 * sizeof(int));
@@ -1477,8 +1492,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
       pT += (size_t)rr * rr;
       fb.E = pT;
       pT += (size_t)njr * rr;
-      fb.G = pT;
-      pT += (size_t)njr * rr;
+      fb.G = symm ? nullptr : pT;  // symmetric storage: G = E^T is not kept
+      if (!symm) pT += (size_t)njr * rr;
       F.h_boxes.push_back(fb);
     }
     F.feats.insert(F.feats.end(), fx.begin(), fx.end());
@@ -1594,7 +1609,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     child_b.clear();
     for (int q = 0; q < nb; q++) {
       const FBox<T> &fb = F.h_boxes[base + q];
-      F.used_T += (int64_t)fb.k * fb.r + 2 * (int64_t)fb.r * fb.r + 2 * (int64_t)fb.nj * fb.r;
+      F.used_T += (int64_t)fb.k * fb.r + 2 * (int64_t)fb.r * fb.r + (symm ? 1 : 2) * (int64_t)fb.nj * fb.r;
       const HTree &Tp = F.trees[box_prob[q]];
       const int par = Tp.parent[H.box_node[q]];
       if (par >= 0) child_b[((int64_t)box_prob[q] << 32) | (uint32_t)par] += fb.b;
@@ -2125,6 +2140,87 @@ static bool pcg(const Factor<T> &F, const double *b, double *x, int nrhs, double
   return ok;
 }
 
+// Columns per pass of the sweep kernels: few enough for their shared-memory
+// vectors (3 b x columns entries of the widest box within 200 KB).
+template <typename T> static int sweep_columns(const Factor<T> &F, int nrhs) {
+  int bm = 1;
+  for (const auto &p : F.phases) bm = std::max(bm, p.bmax);
+  return (int)std::max<size_t>(1, std::min<size_t>(nrhs, (size_t)(200 << 10) / ((size_t)3 * bm * sizeof(T))));
+}
+
+// Generalized square root (the remark after Eq. 3.11): for symmetric
+// positive definite A the factor is F = V D W with W = V^T, so with
+// D = C C^T (C block lower triangular, the Cholesky factors of the X_RR
+// blocks and of the top blocks) F^{1/2} = V C satisfies
+// F = F^{1/2} (F^{1/2})^T.  y = V C x applies C on every block's DOFs, then
+// the apply's backward sweeps (the V product); (F^{1/2})^T x = C^T W x runs
+// the apply's forward sweeps without D (the W product), then C^T.  The
+// factors C are rebuilt once from the stored LU factors (X = P^T L U, then
+// the Cholesky factor of its symmetric part).
+template <typename T> static void chol_prepare(const Factor<T> &F) {
+  if (F.chol_ready) return;
+  cudaStream_t st = F.st;
+  const int nbox = (int)F.h_boxes.size(), np = F.nprob;
+  std::vector<int64_t> coff(nbox + np + 1, 0);
+  int rmax = 1;
+  for (int q = 0; q < nbox; q++) {
+    const int r = F.h_boxes[q].r;
+    coff[q + 1] = coff[q] + (int64_t)r * r;
+    rmax = std::max(rmax, r);
+  }
+  for (int p = 0; p < np; p++) {
+    const int t = F.ntop > 0 ? F.h_tn[p] : 0;
+    if (t > 4096) throw Fail{RSS_EINVAL, "rss_sqrt_apply: top block larger than 4096"};
+    coff[nbox + p + 1] = coff[nbox + p] + (int64_t)t * t;
+    rmax = std::max(rmax, t);
+  }
+  upload(F.d_coff, coff, st);
+  F.d_chol.alloc(sizeof(T) * std::max<int64_t>(coff.back(), 1), st);
+  F.d_cerr.alloc(sizeof(int), st);
+  CK(cudaMemsetAsync(F.d_cerr.p, 0, sizeof(int), st));
+  launch_chol_from_lu<T>(ptr<FBox<T>>(F.d_boxes), nbox, F.ntop > 0 ? ptr<T>(F.d_topLU) : nullptr,
+                         ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn),
+                         F.ntop > 0 ? np : 0, ptr<T>(F.d_chol), ptr<int64_t>(F.d_coff), ptr<int>(F.d_cerr), st);
+  check_launch("cholesky factors");
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, F.d_cerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (e) throw Fail{RSS_ENUMERIC, "rss_sqrt_apply: a diagonal block of D is not positive definite"};
+  F.chol_rmax = rmax;
+  F.chol_ready = true;
+}
+
+template <typename T>
+static void sqrt_apply(const Factor<T> &F, const double *x, double *y, int nrhs, int trans) {
+  chol_prepare(F);
+  cudaStream_t st = F.st;
+  const int nbox = (int)F.h_boxes.size(), np = F.ntop > 0 ? F.nprob : 0;
+  // columns per pass: the sweeps' limit, and the block vectors within 200 KB
+  int c = sweep_columns(F, nrhs);
+  while (c > 1 && (size_t)F.chol_rmax * c * sizeof(T) > (size_t)(200 << 10)) c--;
+  ensure_work(F, c);
+  T *v = ptr<T>(F.d_work);
+  for (int c0 = 0; c0 < nrhs; c0 += c) {
+    const int nc = std::min(c, nrhs - c0);
+    launch_permute<T>(0, ptr<int64_t>(F.d_perm), x + (size_t)c0 * F.n, v, nullptr, F.n, nc, st);
+    auto blocks = [&](int tr) {
+      launch_chol_apply<T>(ptr<FBox<T>>(F.d_boxes), nbox, ptr<int64_t>(F.d_top), ptr<int64_t>(F.d_toff),
+                           ptr<int>(F.d_tn), np, ptr<T>(F.d_chol), ptr<int64_t>(F.d_coff), v, nc, F.chol_rmax, tr,
+                           st);
+    };
+    if (!trans) {
+      blocks(0);
+      for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) sweep_phase<T>(F, SWEEP_APPLY_BWD, *it, v, nc, st);
+    } else {
+      for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_APPLY_W, p, v, nc, st);
+      blocks(1);
+    }
+    launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, y + (size_t)c0 * F.n, F.n, nc, st);
+    check_launch("rss_sqrt_apply");
+  }
+  CK(cudaStreamSynchronize(st));
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free solve.  Its working vectors live in one fixed file-scope
 // device array instead of memory allocated per factor: every device that
@@ -2161,13 +2257,6 @@ static void *noalloc_scratch() {
   return g_noalloc_ptr[dev];
 }
 
-// Columns per pass of the sweep kernels: few enough for their shared-memory
-// vectors (3 b x columns entries of the widest box within 200 KB).
-template <typename T> static int sweep_columns(const Factor<T> &F, int nrhs) {
-  int bm = 1;
-  for (const auto &p : F.phases) bm = std::max(bm, p.bmax);
-  return (int)std::max<size_t>(1, std::min<size_t>(nrhs, (size_t)(200 << 10) / ((size_t)3 * bm * sizeof(T))));
-}
 
 // The solve of Eq. 3.11 in passes of at most `c` columns, each pass with its
 // n x c working vector and 2 x ntop x c top-block entries in the fixed array.
@@ -2467,6 +2556,19 @@ rss_status rss_solve_noalloc(const rss_factorization *f, const double *b, double
       if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
       solve_noalloc(F, b, x, nrhs);
     }
+  });
+}
+
+rss_status rss_sqrt_apply(const rss_factorization *f, const double *x, double *y, int nrhs, int transpose) {
+  return guard([&] {
+    if (!f || !f->impl || nrhs < 1 || (transpose != 0 && transpose != 1))
+      throw Fail{RSS_EINVAL, "rss_sqrt_apply: bad arguments"};
+    auto run = [&](const auto &F) {
+      if (F.n > 0 && (!x || !y)) throw Fail{RSS_EINVAL, "NULL vector"};
+      if (F.n > 0) sqrt_apply(F, x, y, nrhs, transpose);
+    };
+    if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
+    else run(static_cast<const Factor<float> &>(*f->impl));
   });
 }
 

@@ -62,6 +62,9 @@ template <typename T> struct LevelDev {
   T *pool;
   int shared;                   // 1: boxes of one phase may share pair blocks
                                 // (2^d colours): Schur updates add atomically
+  int weak;                     // 1: weak skeletonization (RS-WS, Sec. 3.4):
+                                // the ID compresses against every cell inside
+                                // the proxy surface, J = S
 };
 
 // A list of dense blocks to assemble: block q has rows row_ids[row_off[q] ..
@@ -224,7 +227,21 @@ void tree_gpu_nodes(const TreeGpu &T, int *depth, int *parent, int *coord, int64
 void count_launch(int n = 1);
 long long launches_total();
 
-// Sweep modes.
-enum { SWEEP_SOLVE_FWD = 0, SWEEP_SOLVE_BWD = 1, SWEEP_APPLY_FWD = 2, SWEEP_APPLY_BWD = 3 };
+// Sweep modes.  SWEEP_APPLY_W: the forward apply sweep without the
+// diagonal block (the W product of the generalized square root).
+enum { SWEEP_SOLVE_FWD = 0, SWEEP_SOLVE_BWD = 1, SWEEP_APPLY_FWD = 2, SWEEP_APPLY_BWD = 3, SWEEP_APPLY_W = 4 };
+
+// Generalized square root: lower Cholesky factors of the boxes' X_RR and the
+// problems' top blocks (block q at C + coff[q], boxes first), rebuilt from
+// their LU factors; and v_B := C v_B or C^T v_B on every block's DOFs
+// (rmax: the largest block order).
+template <typename T>
+void launch_chol_from_lu(const FBox<T> *boxes, int nbox, const T *topLU, const int64_t *loff, const int *toppiv,
+                         const int64_t *toff, const int *tn, int nprob, T *C, const int64_t *coff, int *err,
+                         cudaStream_t st);
+template <typename T>
+void launch_chol_apply(const FBox<T> *boxes, int nbox, const int64_t *top, const int64_t *toff, const int *tn,
+                       int nprob, const T *C, const int64_t *coff, T *v, int nrhs, int rmax, int trans,
+                       cudaStream_t st);
 
 }  // namespace rss

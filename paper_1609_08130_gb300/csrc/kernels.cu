@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
       for (int dy = -2; dy <= 2; dy++)
         for (int dx = -2; dx <= 2; dx++) {
           int m = max(abs(dx), max(abs(dy), abs(dz)));
-          if (m != 2) continue;
+          if (m != 2 && !(lv.weak && m == 1)) continue;  // ring O; weak steps: N too
           int code = code5(dx, dy, dz, dim);
           int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
           if (nb < 0) continue;
@@ -492,417 +492,12 @@ __global__ void __launch_bounds__(NT) k_id(LevelDev<T> lv, FBox<T> *boxes, const
   }
 }
 
-// ---------------------------------------------------------------------------
-// Warp-level ID for boxes with b <= 32*CPL.  W warps share one box: each
-// folds a disjoint set of 'PR'-row panels of the ID matrix into its own b x b
-// triangle (lane l owns columns l, l+32, ...; the panel sits in registers and
-// the Householder vector is broadcast by shuffles, so no block barrier is
-// needed), the W triangles are folded into the first one, and that warp runs
-// the greedy column-pivoted QR on it.
-// ---------------------------------------------------------------------------
+constexpr unsigned FULL = 0xffffffffu;
 
+// Rows of the ID matrix a thread keeps per panel column: 32 (FP32) / 16 (FP64).
 template <typename T> struct IdwRows;
 template <> struct IdwRows<float> { static constexpr int PR = 32; };
 template <> struct IdwRows<double> { static constexpr int PR = 16; };
-
-constexpr unsigned FULL = 0xffffffffu;
-
-// Fold the PR rows held in `pan` into the triangle R (row-major, ld ldr).
-// The owner lane of column j publishes the column and its squared norm
-// through the warp's shared buffer `vbuf` (PR + 4 entries, 16-byte aligned);
-// the owner of column j+1 publishes it into the other half of the double
-// buffer as soon as its own update for step j is done, so the next step
-// starts from data already in shared memory.  The slot loop is unrolled so
-// that lanes whose columns lie left of j drop out at compile time.
-template <typename T, int PR>
-__device__ __forceinline__ void publish_col(T *dst, const T (&col)[PR]) {
-  T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
-#pragma unroll
-  for (int i = 0; i < PR; i += 4) {
-    s0 += col[i] * col[i];
-    s1 += col[i + 1] * col[i + 1];
-    s2 += col[i + 2] * col[i + 2];
-    s3 += col[i + 3] * col[i + 3];
-  }
-#pragma unroll
-  for (int i = 0; i < PR; i++) dst[i] = col[i];
-  dst[PR] = (s0 + s1) + (s2 + s3);
-}
-
-template <typename T, int CPL, int PR>
-__device__ __forceinline__ void fold_rows(T (&pan)[PR][CPL], T *R, int ldr, int b, int lane, T *vbuf) {
-  constexpr int VS = PR + 4;  // one half of the double buffer
-  if (b <= 0) return;
-  // column 0 is owned by lane 0, slot 0
-  if (lane == 0) {
-    T col[PR];
-#pragma unroll
-    for (int i = 0; i < PR; i++) col[i] = pan[i][0];
-    publish_col<T, PR>(vbuf, col);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < CPL; q++) {
-    for (int jj = 0; jj < 32; jj++) {
-      const int j = q * 32 + jj;
-      if (j >= b) break;
-      const T *vb = vbuf + (j & 1) * VS;
-      T *vn = vbuf + ((j + 1) & 1) * VS;
-      T v[PR];
-#pragma unroll
-      for (int i = 0; i < PR; i++) v[i] = vb[i];
-      const T s = vb[PR];
-      // owner of the next column (same slot unless jj == 31)
-      const int jn = j + 1;
-      const int on = jn & 31, qn = jn >> 5;
-      if (s > (T)0) {
-        const T x0 = R[j * ldr + j];
-        const T nrm = sqrt(x0 * x0 + s);
-        const T beta = x0 >= (T)0 ? -nrm : nrm;
-        const T tau = (beta - x0) / beta;
-        const T scl = (T)1 / (x0 - beta);
-#pragma unroll
-        for (int qq = q; qq < CPL; qq++) {
-          const int col = lane + 32 * qq;
-          const bool act = (qq > q ? true : lane > jj) && col < b;
-          if (act) {
-            T d[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) d[u] = (T)0;
-#pragma unroll
-            for (int i = 0; i < PR; i += 8)
-#pragma unroll
-              for (int u = 0; u < 8 && i + u < PR; u++) d[u] += v[i + u] * pan[i + u][qq];
-            const T dd = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
-            const T wv = R[j * ldr + col] + scl * dd;
-            const T f = tau * wv;
-            const T fs = f * scl;
-            R[j * ldr + col] -= f;
-#pragma unroll
-            for (int i = 0; i < PR; i++) pan[i][qq] -= fs * v[i];
-            // publish the next pivot column as soon as it is updated
-            if (jn < b && col == jn) {
-              T cn[PR];
-#pragma unroll
-              for (int i = 0; i < PR; i++) cn[i] = pan[i][qq];
-              publish_col<T, PR>(vn, cn);
-            }
-          }
-        }
-        __syncwarp();
-        if (lane == jj) R[j * ldr + j] = beta;
-      } else if (jn < b && lane == on) {
-        // nothing to annihilate: column jn is unchanged, publish it as is
-        T cn[PR];
-#pragma unroll
-        for (int i = 0; i < PR; i++) {
-          T x = pan[i][0];
-#pragma unroll
-          for (int u = 1; u < CPL; u++)
-            if (qn == u) x = pan[i][u];
-          cn[i] = x;
-        }
-        publish_col<T, PR>(vn, cn);
-      }
-      __syncwarp();
-    }
-  }
-  __syncwarp();
-}
-
-template <typename T, int CPL>
-__global__ void __launch_bounds__(128) k_idw(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int W,
-                                             Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
-                                             double eps, int ring_max, int *err) {
-  constexpr int PR = IdwRows<T>::PR;
-  constexpr int BM = 32 * CPL;        // max b
-  constexpr int LDR = BM + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wpc = blockDim.x >> 5;
-  const int bpc = wpc / W;                      // boxes per CTA
-  const int lb = warp / W, sw = warp % W;       // local box, sub-warp
-  const int qbox = blockIdx.x * bpc + lb;
-  T *Rw = reinterpret_cast<T *>(smem_raw) + (size_t)warp * BM * LDR;
-  const size_t tri_bytes = (((size_t)wpc * BM * LDR * sizeof(T) + 15) & ~(size_t)15);
-  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)warp * 2 * (PR + 4);  // column broadcast
-  int *ibase = reinterpret_cast<int *>(smem_raw + tri_bytes + (size_t)wpc * 2 * (PR + 4) * sizeof(T));
-  int *s_ocode = ibase + lb * (125 + 126 + BM + 4);
-  int *s_obase = s_ocode + 125;
-  int *perm = s_obase + 126;
-  int *s_misc = perm + BM;                      // [0] ring count, [1] k
-  // element offset in the pool of the column holding each ring row
-  int64_t *s_rowsrc = reinterpret_cast<int64_t *>(ibase + ((125 + 126 + BM + 4 + 1) & ~1));
-  const bool active = qbox < nbox;
-  FBox<T> *fbp = active ? &boxes[box_list[qbox]] : nullptr;
-  const int c = active ? fbp->cell : 0;
-  const int b = active ? fbp->b : 0;
-  const int dim = lv.dim;
-
-  for (int e = lane; e < BM * LDR; e += 32) Rw[e] = (T)0;
-  // ring O (Chebyshev distance 2) cells with active DOFs, by sub-warp 0
-  if (active && sw == 0) {
-    const int lim = dim == 3 ? 2 : 0;
-    int cnt_here = 0;
-    int no = 0, acc = 0;
-    const int ncode = dim == 3 ? 125 : 25;
-    for (int base = 0; base < ncode; base += 32) {
-      int code = base + lane;
-      int cnt = 0;
-      if (code < ncode) {
-        int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
-        int mm = max(abs(dx), max(abs(dy), abs(dz)));
-        (void)lim;
-        if (mm == 2) {
-          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
-          if (nb >= 0) cnt = lv.act_cnt[nb];
-        }
-      }
-      unsigned mask = __ballot_sync(FULL, cnt > 0);
-      // exclusive prefix of counts among flagged lanes
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-      }
-      int pos = __popc(mask & ((1u << lane) - 1));
-      if (cnt > 0) {
-        s_ocode[no + pos] = code;
-        s_obase[no + pos] = acc + incl - cnt;
-      }
-      no += __popc(mask);
-      acc += __shfl_sync(FULL, incl, 31);
-      cnt_here += cnt;
-    }
-    if (lane == 0) {
-      s_obase[no] = acc;
-      s_misc[0] = no;
-    }
-    (void)cnt_here;
-  }
-  __syncthreads();
-  if (active) {
-    // ring rows -> pool offsets, all warps of the box in parallel
-    const int no = s_misc[0];
-    const int nO = s_obase[no];
-    if (nO > ring_max) {
-      if (threadIdx.x == 0) set_err(err, DERR_INTERNAL);
-    } else {
-      for (int q = 0; q < no; q++) {
-        const int code = s_ocode[q];
-        const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
-        const int64_t abase = lv.cell_dof_off[nb];
-        const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
-        for (int t = threadIdx.x; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
-          s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
-      }
-    }
-  }
-  __syncthreads();
-  if (active && s_obase[s_misc[0]] <= ring_max) {
-    const int no = s_misc[0];
-    const int nO = s_obase[no];
-    const int m = nO + px.np;
-    const int64_t coff = lv.cell_dof_off[c];
-    const double D = ldexp(1.0, -lv.t);
-    double ctr[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) ctr[d] = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
-    const double rad = px.radius * D;
-    // own columns: positions relative to the box centre (for the proxy rows)
-    double xq[CPL][3];
-#pragma unroll
-    for (int q = 0; q < CPL; q++) {
-      int col = lane + 32 * q;
-      int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
-#pragma unroll
-      for (int d = 0; d < 3; d++) xq[q][d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr[d] : 0.0;
-    }
-    const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
-    const int npan = (m + PR - 1) / PR;
-    for (int pnl = sw; pnl < npan; pnl += W) {
-      T pan[PR][CPL];
-#pragma unroll
-      for (int i = 0; i < PR; i++) {
-        const int row = pnl * PR + i;
-        int64_t src = -1;
-        int pm = -1;
-        if (row < nO) src = s_rowsrc[row];
-        else if (row < m) pm = row - nO;
-#pragma unroll
-        for (int q = 0; q < CPL; q++) {
-          const int col = lane + 32 * q;
-          T v = (T)0;
-          if (col < b) {
-            if (src >= 0) {
-              v = lv.pool[src + col];
-            } else if (pm >= 0) {
-              double r2 = 0.0;
-#pragma unroll
-              for (int d = 0; d < 3; d++) {
-                double dd = rad * proxy_unit[3 * pm + d] - xq[q][d];
-                r2 += dd * dd;
-              }
-              v = w * kof(K.kind, (T)r2);
-            }
-          }
-          pan[i][q] = v;
-        }
-      }
-      fold_rows<T, CPL, PR>(pan, Rw, LDR, b, lane, vbuf);
-    }
-  }
-  // tree merge of the sub-warps' triangles: in round `step`, sub-warp sw
-  // (a multiple of 2*step) absorbs sub-warp sw + step
-  const bool ok_ring = active && s_obase[s_misc[0]] <= ring_max;
-  for (int step = 1; step < W; step <<= 1) {
-    __syncthreads();
-    if (ok_ring && sw % (2 * step) == 0 && sw + step < W) {
-      const T *Ro = Rw + (size_t)step * BM * LDR;
-      for (int p0 = 0; p0 < b; p0 += PR) {
-        T pan[PR][CPL];
-#pragma unroll
-        for (int i = 0; i < PR; i++)
-#pragma unroll
-          for (int q = 0; q < CPL; q++) {
-            int col = lane + 32 * q, row = p0 + i;
-            pan[i][q] = (row < b && col < b) ? Ro[row * LDR + col] : (T)0;
-          }
-        fold_rows<T, CPL, PR>(pan, Rw, LDR, b, lane, vbuf);
-      }
-    }
-  }
-  __syncthreads();
-  if (!ok_ring || sw != 0) return;
-  T *R = Rw;
-  // greedy column-pivoted QR of the triangle
-  for (int q = lane; q < b; q += 32) perm[q] = q;
-  __syncwarp();
-  T r11 = (T)0;
-  int k = b;
-  for (int j = 0; j < b; j++) {
-    T best = (T)-1;
-    int bi = b;
-#pragma unroll
-    for (int q = 0; q < CPL; q++) {
-      int col = lane + 32 * q;
-      if (col >= j && col < b) {
-        T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-        int i = j;
-        for (; i + 3 < b; i += 4) {
-          const T x0 = R[i * LDR + col], x1 = R[(i + 1) * LDR + col];
-          const T x2 = R[(i + 2) * LDR + col], x3 = R[(i + 3) * LDR + col];
-          a0 += x0 * x0;
-          a1 += x1 * x1;
-          a2 += x2 * x2;
-          a3 += x3 * x3;
-        }
-        for (; i < b; i++) a0 += R[i * LDR + col] * R[i * LDR + col];
-        const T sacc = (a0 + a1) + (a2 + a3);
-        if (sacc > best) {
-          best = sacc;
-          bi = col;
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T ov = __shfl_xor_sync(FULL, best, o);
-      int oi = __shfl_xor_sync(FULL, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    const T cn = sqrt(best);
-    if (j == 0) r11 = cn;
-    // no valid pivot (all norms NaN) also stops
-    if (bi >= b || r11 == (T)0 || !(cn > (T)eps * r11)) {
-      k = j;
-      break;
-    }
-    const int p = bi;
-    if (p != j) {
-      for (int i = lane; i < b; i += 32) {
-        T t0 = R[i * LDR + j];
-        R[i * LDR + j] = R[i * LDR + p];
-        R[i * LDR + p] = t0;
-      }
-      if (lane == 0) {
-        int tp = perm[j];
-        perm[j] = perm[p];
-        perm[p] = tp;
-      }
-    }
-    __syncwarp();
-    T sacc;
-    {
-      T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-      int i = j + 1;
-      for (; i + 3 < b; i += 4) {
-        const T x0 = R[i * LDR + j], x1 = R[(i + 1) * LDR + j], x2 = R[(i + 2) * LDR + j], x3 = R[(i + 3) * LDR + j];
-        a0 += x0 * x0;
-        a1 += x1 * x1;
-        a2 += x2 * x2;
-        a3 += x3 * x3;
-      }
-      for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + j];
-      sacc = (a0 + a1) + (a2 + a3);
-    }
-    if (sacc > (T)0) {
-      const T x0 = R[j * LDR + j];
-      const T nrm = sqrt(x0 * x0 + sacc);
-      const T beta = x0 >= (T)0 ? -nrm : nrm;
-      const T tau = (beta - x0) / beta;
-      const T scl = (T)1 / (x0 - beta);
-#pragma unroll
-      for (int q = 0; q < CPL; q++) {
-        const int col = lane + 32 * q;
-        if (col > j && col < b) {
-          T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-          int i = j + 1;
-          for (; i + 3 < b; i += 4) {
-            a0 += R[i * LDR + j] * R[i * LDR + col];
-            a1 += R[(i + 1) * LDR + j] * R[(i + 1) * LDR + col];
-            a2 += R[(i + 2) * LDR + j] * R[(i + 2) * LDR + col];
-            a3 += R[(i + 3) * LDR + j] * R[(i + 3) * LDR + col];
-          }
-          for (; i < b; i++) a0 += R[i * LDR + j] * R[i * LDR + col];
-          const T d = (a0 + a1) + (a2 + a3);
-          const T f = tau * (R[j * LDR + col] + scl * d);
-          const T fs = f * scl;
-          R[j * LDR + col] -= f;
-          for (int i = j + 1; i < b; i++) R[i * LDR + col] -= fs * R[i * LDR + j];
-        }
-      }
-      __syncwarp();
-      if (lane == 0) R[j * LDR + j] = beta;
-      __syncwarp();
-    }
-  }
-  FBox<T> &fb = *fbp;
-  const int r = b - k;
-  // T = R11^{-1} R12, one lane per column
-  for (int cc = lane; cc < r; cc += 32) {
-    T *tcol = fb.Tm + (int64_t)cc * k;
-    for (int i = k - 1; i >= 0; i--) {
-      T sacc = R[i * LDR + k + cc];
-      for (int l = i + 1; l < k; l++) sacc -= R[i * LDR + l] * tcol[l];
-      tcol[i] = sacc / R[i * LDR + i];
-    }
-  }
-  const int64_t coff = lv.cell_dof_off[c];
-  for (int q = lane; q < b; q += 32) {
-    fb.loc[q] = perm[q];
-    fb.ids[q] = lv.cell_dofs[coff + perm[q]];
-  }
-  if (lane == 0) {
-    fb.k = k;
-    fb.r = r;
-    fb.no = s_obase[s_misc[0]];
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Column-per-thread ID for boxes with b <= NC (64 or 128).  A "fold group" is
@@ -1250,7 +845,8 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
       int code = base + tid, cnt = 0;
       if (code < ncode) {
         int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
-        if (max(abs(dx), max(abs(dy), abs(dz))) == 2) {
+        const int dist = max(abs(dx), max(abs(dy), abs(dz)));
+        if (dist == 2 || (lv.weak && dist == 1)) {  // ring O; weak steps: N too
           int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
           if (nb >= 0) cnt = lv.act_cnt[nb];
         }
@@ -1461,7 +1057,8 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
       int code = base + tid, cnt = 0;
       if (code < ncode) {
         int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
-        if (max(abs(dx), max(abs(dy), abs(dz))) == 2) {
+        const int dist = max(abs(dx), max(abs(dy), abs(dz)));
+        if (dist == 2 || (lv.weak && dist == 1)) {  // ring O; weak steps: N too
           int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
           if (nb >= 0) cnt = lv.act_cnt[nb];
         }
@@ -1608,7 +1205,8 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
       int code = base + tid, cnt_ = 0;
       if (code < ncode) {
         int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
-        if (max(abs(dx), max(abs(dy), abs(dz))) == 2) {
+        const int dist = max(abs(dx), max(abs(dy), abs(dz)));
+        if (dist == 2 || (lv.weak && dist == 1)) {  // ring O; weak steps: N too
           int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
           if (nb >= 0) cnt_ = lv.act_cnt[nb];
         }
@@ -1819,24 +1417,6 @@ static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
   count_launch();
 }
 
-template <typename T, int CPL>
-static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int W,
-                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
-                       double eps, int ring_max, cudaStream_t st, int *err) {
-  constexpr int BM = 32 * CPL;
-  // one box per CTA of W warps, each warp with its own b x b triangle
-  const size_t tri = (size_t)BM * (BM + 1) * sizeof(T);
-  int wmax = (int)((200u << 10) / tri);
-  if (wmax < 1) wmax = 1;
-  if (W > wmax) W = wmax;
-  const int wpc = W;
-  size_t smem = (((size_t)wpc * tri + 15) & ~(size_t)15) + (size_t)wpc * 2 * (IdwRows<T>::PR + 4) * sizeof(T) +
-                (size_t)((125 + 126 + BM + 4 + 1) & ~1) * sizeof(int) + (size_t)ring_max * sizeof(int64_t) + 16;
-  cudaFuncSetAttribute(k_idw<T, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_idw<T, CPL><<<nbox, wpc * 32, smem, st>>>(lv, boxes, box_list, nbox, W, P, K, px, proxy_unit, eps, ring_max,
-                                              err);
-  count_launch();
-}
 
 // Launch shape of the next ID launch on this thread: fold groups per box
 // (hint & 15), threads per column ((hint >> 4) & 15; 0 or 1: k_idc) and CTAs
@@ -1964,7 +1544,8 @@ template <typename T>
 __device__ bool claim_storage(FBox<T> &fb, int nj, const Overflow<T> &ov, int *err) {
   const int r = fb.r;
   if (r <= fb.rres && (int64_t)nj * r <= (int64_t)fb.njres * fb.rres) return true;
-  const int64_t need = (2 * (int64_t)r * r + 2 * (int64_t)nj * r + 3) & ~int64_t(3);
+  const bool symm = fb.G == nullptr;  // symmetric storage: no G
+  const int64_t need = (2 * (int64_t)r * r + (symm ? 1 : 2) * (int64_t)nj * r + 3) & ~int64_t(3);
   if (ov.cap > 0) {
     const unsigned long long o = atomicAdd(ov.used, (unsigned long long)need);
     if ((int64_t)o + need <= ov.cap) {
@@ -1975,7 +1556,7 @@ __device__ bool claim_storage(FBox<T> &fb, int nj, const Overflow<T> &ov, int *e
       p += (int64_t)r * r;
       fb.E = p;
       p += (int64_t)nj * r;
-      fb.G = p;
+      fb.G = symm ? nullptr : p;
       return true;
     }
   }
@@ -2026,7 +1607,7 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
         s_off_out[code] = lv.pair_off[(int64_t)c * lv.NB + code5(dx, dy, dz, dim)];
         s_ld_in[code] = lv.cell_b[nb];
       }
-      if (code == center || nb < 0) continue;
+      if (code == center || nb < 0 || lv.weak) continue;  // weak steps: J = S
       int cnt = lv.act_cnt[nb];
       if (cnt <= 0) continue;
       s_ncode[nn] = code;
@@ -2331,7 +1912,7 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
         s_off_out[code] = lv.pair_off[(int64_t)c * lv.NB + code5(dx, dy, dz, dim)];
         s_ld_in[code] = lv.cell_b[nb];
       }
-      if (code == center || nb < 0) continue;
+      if (code == center || nb < 0 || lv.weak) continue;  // weak steps: J = S
       int cnt = lv.act_cnt[nb];
       if (cnt <= 0) continue;
       s_ncode[nn] = code;
@@ -2622,9 +2203,10 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       smem_gemm<T>(na, r, r, rawJ + (size_t)k * (CH + 1), 1, CH + 1, Xi, 1, ldx, [&](int al, int ri, T v) {
         Eo[(aa0 + al) + (int64_t)ri * njj] = v;
       });
-      smem_gemm<T>(r, na, r, Xi, 1, ldx, rawC + k, 1, ldb, [&](int ri, int al, T v) {
-        Go[ri + (int64_t)(aa0 + al) * rr] = v;
-      });
+      if (Go)  // uniform over the CTA; symmetric storage keeps no G
+        smem_gemm<T>(r, na, r, Xi, 1, ldx, rawC + k, 1, ldb, [&](int ri, int al, T v) {
+          Go[ri + (int64_t)(aa0 + al) * rr] = v;
+        });
     }
     __syncthreads();
   }
@@ -2681,6 +2263,7 @@ __global__ void __launch_bounds__(NT) k_elim_gemm(const FBox<T> *boxes, const in
     t -= tiles_e;
     tcols = tcols_g;
     m = r, n = nj, A = Xi, lda = r, B = Xrj, ldb = r, Cp = fb.G, ldc = r;
+    if (!Cp) return;  // symmetric storage keeps no G
   }
   const int i0 = (t / tcols) * 64, j0 = (t % tcols) * 64;
   if (i0 >= m || j0 >= n) return;
@@ -3438,6 +3021,12 @@ __device__ void warp_lu_solve(const T *LU, const int *piv, int r, T *x, T *tmp, 
   __syncwarp();
 }
 
+// G(ri, a) of a box: its stored G, or E(a, ri) under symmetric storage
+// (G = E^T for the symmetric kernels, Sec. 3.3).
+template <typename T> __device__ __forceinline__ T gval(const FBox<T> &fb, int ri, int a) {
+  return fb.G ? __ldg(fb.G + ri + (int64_t)a * fb.r) : __ldg(fb.E + a + (int64_t)ri * fb.nj);
+}
+
 // vJ(a, c): the J entries, from the shared copy or, for boxes whose J does
 // not fit in shared memory, straight from the vector
 #define VJ(a, c) (jsh ? vJ[(a) * nrhs + (c)] : v[fb.J[a] * nrhs + (c)])
@@ -3490,7 +3079,7 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
     for (int e = tid; e < r * nrhs; e += NT) {
       int ri = e % r, c = e / r;
       T acc = (T)0;
-      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * VJ(a, c);
+      for (int a = 0; a < nj; a++) acc += gval(fb, ri, a) * VJ(a, c);
       vR[ri * nrhs + c] -= acc;
     }
     __syncthreads();
@@ -3502,7 +3091,7 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
       v[S[q] * nrhs + c] = vS[q * nrhs + c] - acc;
     }
     for (int e = tid; e < r * nrhs; e += NT) v[Rr[e / nrhs] * nrhs + e % nrhs] = vR[e];
-  } else if (mode == SWEEP_APPLY_FWD) {
+  } else if (mode == SWEEP_APPLY_FWD || mode == SWEEP_APPLY_W) {
     // L_T^{-1}: v_S += T v_R
     for (int e = tid; e < k * nrhs; e += NT) {
       int q = e % k, c = e / k;
@@ -3523,10 +3112,14 @@ __global__ void __launch_bounds__(NT) k_sweep(int mode, const FBox<T> *boxes, in
     for (int e = tid; e < r * nrhs; e += NT) {
       int ri = e % r, c = e / r;
       T acc = (T)0;
-      for (int a = 0; a < nj; a++) acc += fb.G[ri + (int64_t)a * r] * VJ(a, c);
+      for (int a = 0; a < nj; a++) acc += gval(fb, ri, a) * VJ(a, c);
       vR[ri * nrhs + c] += acc;
     }
     __syncthreads();
+    if (mode == SWEEP_APPLY_W) {  // the W product only: v_R as it stands
+      for (int e = tid; e < r * nrhs; e += NT) v[Rr[e / nrhs] * nrhs + e % nrhs] = vR[e];
+      return;
+    }
     // D: y_R = P^T L U v_R
     for (int e = tid; e < r * nrhs; e += NT) {
       int i = e % r, c = e / r;
@@ -3733,7 +3326,7 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
         int64_t ja[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          gv[u] = __ldg(fb.G + i + (int64_t)(a + u * nch) * r);
+          gv[u] = gval(fb, i, a + u * nch);
           ja[u] = fb.J[a + u * nch];
         }
 #pragma unroll
@@ -3742,7 +3335,7 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
           for (int c = 0; c < NR; c++) acc[c] += gv[u] * v[ja[u] * NR + c];
       }
       for (; a < a1; a += nch) {
-        const T gv = __ldg(fb.G + i + (int64_t)a * r);
+        const T gv = gval(fb, i, a);
         const int64_t ja = fb.J[a];
 #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] += gv * v[ja * NR + c];
@@ -3837,6 +3430,125 @@ void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, in
   }
   if (!capturing(st)) cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (200 << 10) + 64);
   k_sweep<T><<<count, NT, smem, st>>>(mode, boxes, first, v, nrhs, jsh, shared); count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Generalized square root F^{1/2} (the remark after Eq. 3.11): Cholesky
+// factors of the diagonal blocks of D, rebuilt from their stored LU factors
+// ---------------------------------------------------------------------------
+
+// Block q of `nblk` (the boxes' X_RR, then the problems' top blocks): its LU
+// (row-major, P X = L U, row i of P X is row piv[i] of X), order r, and the
+// place of its Cholesky factor.  One CTA per block: X = P^T L U is formed in
+// C, then C := the lower Cholesky factor of (X + X^T) / 2 in place, column
+// by column (the upper triangle still holds X until it is cleared).  A block
+// that is not positive definite records DERR_NUMERIC.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_chol_from_lu(const FBox<T> *boxes, int nbox, const T *topLU,
+                                                     const int64_t *loff, const int *toppiv, const int64_t *toff,
+                                                     const int *tn, T *Call, const int64_t *coff, int *err) {
+  const int q = blockIdx.x, tid = threadIdx.x;
+  const T *LU;
+  const int *piv;
+  int r;
+  if (q < nbox) {
+    LU = boxes[q].LU;
+    piv = boxes[q].piv;
+    r = boxes[q].r;
+  } else {
+    const int p = q - nbox;
+    LU = topLU + loff[p];
+    piv = toppiv + toff[p];
+    r = tn[p];
+  }
+  if (r == 0) return;
+  T *C = Call + coff[q];
+  for (int e = tid; e < r * r; e += NT) {
+    const int i = e / r, j = e % r, m = i < j ? i : j;
+    T acc = (T)0;
+    for (int l = 0; l <= m; l++) acc += (l == i ? (T)1 : LU[(int64_t)i * r + l]) * LU[(int64_t)l * r + j];
+    C[(int64_t)piv[i] * r + j] = acc;
+  }
+  __syncthreads();
+  __shared__ T s_d;
+  for (int j = 0; j < r; j++) {
+    if (tid == 0) {
+      T d = C[(int64_t)j * r + j];
+      for (int l = 0; l < j; l++) d -= C[(int64_t)j * r + l] * C[(int64_t)j * r + l];
+      if (!(d > (T)0)) {
+        set_err(err, DERR_NUMERIC);
+        d = (T)1;  // keep going with a harmless pivot; the host reports the error
+      }
+      s_d = sqrt(d);
+      C[(int64_t)j * r + j] = s_d;
+    }
+    __syncthreads();
+    const T dj = s_d;
+    for (int i = j + 1 + tid; i < r; i += NT) {
+      T acc = (T)0.5 * (C[(int64_t)i * r + j] + C[(int64_t)j * r + i]);
+      for (int l = 0; l < j; l++) acc -= C[(int64_t)i * r + l] * C[(int64_t)j * r + l];
+      C[(int64_t)i * r + j] = acc / dj;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < r * r; e += NT) {
+    const int i = e / r, j = e % r;
+    if (i < j) C[e] = (T)0;
+  }
+}
+
+// v_B := C v_B (trans = 0) or C^T v_B (trans = 1) on every block's DOFs (a
+// box's R, a problem's top-block DOFs), C its lower Cholesky factor.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_chol_apply(const FBox<T> *boxes, int nbox, const int64_t *top,
+                                                   const int64_t *toff, const int *tn, const T *Call,
+                                                   const int64_t *coff, T *v, int nrhs, int trans) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int q = blockIdx.x, tid = threadIdx.x;
+  const int64_t *ids;
+  int r;
+  if (q < nbox) {
+    ids = boxes[q].ids + boxes[q].k;
+    r = boxes[q].r;
+  } else {
+    const int p = q - nbox;
+    ids = top + toff[p];
+    r = tn[p];
+  }
+  if (r == 0) return;
+  const T *C = Call + coff[q];
+  for (int e = tid; e < r * nrhs; e += NT) xs[e] = v[ids[e / nrhs] * nrhs + e % nrhs];
+  __syncthreads();
+  for (int e = tid; e < r * nrhs; e += NT) {
+    const int a = e / nrhs, c = e % nrhs;
+    T acc = (T)0;
+    if (!trans)
+      for (int l = 0; l <= a; l++) acc += C[(int64_t)a * r + l] * xs[l * nrhs + c];
+    else
+      for (int l = a; l < r; l++) acc += C[(int64_t)l * r + a] * xs[l * nrhs + c];
+    v[ids[a] * nrhs + c] = acc;
+  }
+}
+
+template <typename T>
+void launch_chol_from_lu(const FBox<T> *boxes, int nbox, const T *topLU, const int64_t *loff, const int *toppiv,
+                         const int64_t *toff, const int *tn, int nprob, T *C, const int64_t *coff, int *err,
+                         cudaStream_t st) {
+  if (nbox + nprob == 0) return;
+  k_chol_from_lu<T><<<nbox + nprob, NT, 0, st>>>(boxes, nbox, topLU, loff, toppiv, toff, tn, C, coff, err);
+  count_launch();
+}
+
+template <typename T>
+void launch_chol_apply(const FBox<T> *boxes, int nbox, const int64_t *top, const int64_t *toff, const int *tn,
+                       int nprob, const T *C, const int64_t *coff, T *v, int nrhs, int rmax, int trans,
+                       cudaStream_t st) {
+  if (nbox + nprob == 0) return;
+  const size_t smem = (size_t)rmax * nrhs * sizeof(T) + 16;
+  if (!capturing(st)) cudaFuncSetAttribute(k_chol_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_chol_apply<T><<<nbox + nprob, NT, smem, st>>>(boxes, nbox, top, toff, tn, C, coff, v, nrhs, trans);
+  count_launch();
 }
 
 // Raise the dynamic shared-memory limit of every sweep kernel on the current
@@ -4102,6 +3814,10 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
   template void launch_sweep<T>(int, const FBox<T> *, int, int, T *, int, int, int, cudaStream_t, int);       \
   template void launch_sweep_chunks<T>(int, const FBox<T> *, const int *, const int *, int, T *, int, int, int *, \
                                        T *, const int64_t *, cudaStream_t, int);                             \
+  template void launch_chol_from_lu<T>(const FBox<T> *, int, const T *, const int64_t *, const int *,            \
+                                       const int64_t *, const int *, int, T *, const int64_t *, int *, cudaStream_t); \
+  template void launch_chol_apply<T>(const FBox<T> *, int, const int64_t *, const int64_t *, const int *, int,     \
+                                     const T *, const int64_t *, T *, int, int, int, cudaStream_t);              \
   template void launch_top<T>(int, const T *, const int64_t *, const int *, const int64_t *, const int64_t *,     \
                              const int *, int, int, T *, int, T *, cudaStream_t);                            \
   template void launch_lu_batched<T>(T *, const int64_t *, int *, const int64_t *, const int *, int, cudaStream_t, \

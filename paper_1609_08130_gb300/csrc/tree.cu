@@ -103,30 +103,56 @@ __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *__restrict__ k
   hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-// In-place exclusive scan of len counts by one block of 1024 threads (each
-// scans a contiguous share, the shares' totals are scanned in shared
-// memory).  total (may be NULL) receives the sum.
+// In-place exclusive scan of len counts by one block of 1024 threads, 8192
+// consecutive counts at a time (8 per thread, loaded together; warp scans
+// of the threads' sums, then the warps' totals), with a running carry.
+// total (may be NULL) receives the sum.
 __global__ void __launch_bounds__(1024) k_scan_excl(uint32_t *a, int64_t len, uint32_t *total) {
-  __shared__ uint32_t s[1024];
-  const int64_t per = (len + 1023) / 1024;
-  const int64_t lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
-  uint32_t sum = 0;
-  for (int64_t i = lo; i < hi; i++) sum += a[i];
-  s[threadIdx.x] = sum;
+  constexpr int IT = 8;
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_carry = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
+  for (int64_t b0 = 0; b0 < len; b0 += 1024 * IT) {
+    const int64_t i0 = b0 + (int64_t)tid * IT;
+    uint32_t v[IT], sum = 0;
+#pragma unroll
+    for (int u = 0; u < IT; u++) {
+      v[u] = i0 + u < len ? a[i0 + u] : 0u;
+      sum += v[u];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    s[threadIdx.x] += v;
+    if (warp == 0) {
+      uint32_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t carry = s_carry;
+    const uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u);
+    uint32_t run = carry + incl - sum;
+#pragma unroll
+    for (int u = 0; u < IT; u++) {
+      if (i0 + u < len) a[i0 + u] = run;
+      run += v[u];
+    }
+    __syncthreads();
+    if (tid == 1023) s_carry = carry + incl;
     __syncthreads();
   }
-  uint32_t run = s[threadIdx.x] - sum;
-  for (int64_t i = lo; i < hi; i++) {
-    const uint32_t v = a[i];
-    a[i] = run;
-    run += v;
-  }
-  if (total && threadIdx.x == 1023) *total = s[1023];
+  if (total && tid == 0) *total = s_carry;
 }
 
 // Radix sort pass, part 2: stable scatter.  Each block walks its tile in

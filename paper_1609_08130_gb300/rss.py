@@ -27,6 +27,7 @@ FLAG_LARGE_BOX_PATH = 1
 FLAG_NO_AUTOTUNE = 2
 FLAG_COLOUR_2D = 4
 FLAG_NO_TENSOR_CORES = 8
+FLAG_SYMMETRIC_STORAGE = 16
 
 
 def _nvcc():
@@ -92,6 +93,7 @@ _SIGS = {
     "rss_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_logdet": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rss_stats_json": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_size_t)]),
+    "rss_sqrt_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "rss_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_mlp_create": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "rss_mlp_params": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -312,6 +314,13 @@ class Factorization:
         if check or st != RSS_ENOTCONV:
             _check(st)
         return (x[0] if one else x), it.value, rr.value
+
+    def sqrt_apply(self, x, transpose: bool = False):
+        """Generalized square root: F^{1/2} x, or (F^{1/2})^T x."""
+        x, one, y = self._vec(x)
+        _check(lib().rss_sqrt_apply(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0],
+                                    int(transpose)))
+        return y[0] if one else y
 
     def matvec(self, x):
         """Exact FP64 A x by direct summation."""
