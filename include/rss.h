@@ -101,6 +101,15 @@ typedef struct {
  * and the sweeps read E transposed where they read G.  The same
  * factorization up to rounding. */
 #define RSS_FLAG_SYMMETRIC_STORAGE 16
+/* The hybrid factorization RS-WS (Sec. 3.4, Algorithm 2) instead of RS-S: at
+ * every depth each box is first weakly skeletonized -- its ID compresses its
+ * interactions with every cell inside the proxy surface and, through the
+ * proxy points, the rest, and its redundant DOFs are eliminated against its
+ * skeleton alone (J = S) -- then what stays active is strongly
+ * skeletonized as in RS-S; a last weak pass runs at depth 1.  Fewer stored
+ * entries and a smaller top block, at a somewhat larger apply error.  Not
+ * with RSS_FLAG_COLOUR_2D or a rank proposal (RSS_EINVAL). */
+#define RSS_FLAG_HYBRID 32
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;

@@ -1198,10 +1198,14 @@ template <typename T> static void run_factor(Factor<T> &F) {
   }
 
   F.maxdepth = 0;
+  // box records: one per tree node of depths 2.. (RS-S); the hybrid has a
+  // weak and a strong record per node of depths 2.. and a weak one at depth 1
+  const bool hyb = (F.flags & RSS_FLAG_HYBRID) != 0;
   int nbox_total = 0;
   for (const HTree &Tp : F.trees) {
     F.maxdepth = std::max(F.maxdepth, Tp.maxdepth);
-    for (int t = 2; t <= Tp.maxdepth; t++) nbox_total += (int)Tp.level[t].size();
+    for (int t = 2; t <= Tp.maxdepth; t++) nbox_total += (hyb ? 2 : 1) * (int)Tp.level[t].size();
+    if (hyb && Tp.maxdepth >= 1) nbox_total += (int)Tp.level[1].size();
   }
   F.d_boxes.alloc(sizeof(FBox<T>) * std::max(nbox_total, 1), st);
   F.h_boxes.clear();
@@ -1272,7 +1276,19 @@ template <typename T> static void run_factor(Factor<T> &F) {
   std::unordered_map<int64_t, int> child_b;  // (problem, node) -> sum of its children's b
   DBuf gid, gel, gtri, gcnt;                 // per-phase ID and elimination scratch, grown as needed
   if (F.mlp) F.d_ovf_used.alloc(sizeof(unsigned long long), st);
-  for (int t = F.maxdepth; t >= 2; t--) {
+  // stages: (depth, weak).  RS-S: the strong step at depths maxdepth .. 2.
+  // RS-WS (Sec. 3.4, Algorithm 2): at each depth a weak pass over the boxes,
+  // then the strong pass over what stays active, and a last weak pass at
+  // depth 1.  The strong pass after a weak one rebuilds its level from the
+  // weak pass's (same depth): the near-field blocks carry over.
+  const bool hybrid = (F.flags & RSS_FLAG_HYBRID) != 0;
+  std::vector<std::pair<int, int>> stages;
+  for (int t = F.maxdepth; t >= (hybrid ? 1 : 2); t--) {
+    if (hybrid) stages.push_back({t, 1});
+    if (t >= 2) stages.push_back({t, 0});
+  }
+  for (const auto &stage : stages) {
+    const int t = stage.first, weak = stage.second;
     double th0 = now_ms();
     // this depth's cells of every problem deep enough, merged
     HLevel H;
@@ -1360,6 +1376,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     }
     LevelDev<T> view = D->view(H, ptr<int>(d_dof_cell[slot]), ptr<int>(d_dof_loc[slot]));
     view.shared = cbase == 2;
+    view.weak = weak;
     if (have_prev) {
       LevelDev<T> pv = prevD->view(prevH, ptr<int>(d_dof_cell[prev_slot]), ptr<int>(d_dof_loc[prev_slot]));
       assemble_pairs(H, *D, &pv);
@@ -1387,7 +1404,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
             int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
             if (nbc >= 0) nj += H.cell_b[nbc], nnear_cells++;
           }
-      njmaxv[q] = nj;
+      njmaxv[q] = weak ? b : nj;  // a weak step eliminates against J = S
       // DOFs of the ring inside the proxy surface, bounded by level-start counts
       int ring = 0, nring_cells = 0, lim2 = dim == 3 ? 2 : 0;
       for (int dz = -lim2; dz <= lim2; dz++)
@@ -1397,7 +1414,9 @@ template <typename T> static void run_factor(Factor<T> &F) {
             int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
             if (nbc >= 0) ring += H.cell_b[nbc], nring_cells++;
           }
-      ringv[q] = ring;
+      // rows of the ID matrix from inside the proxy surface: the ring, and
+      // for a weak step the near cells too
+      ringv[q] = weak ? ring + (nj - b) : ring;
       const HTree &Tp = F.trees[box_prob[q]];
       const int node = H.box_node[q];
       const bool leaf = !(Tp.count[node] > Tp.leaf && Tp.depth[node] < 20);
@@ -2416,6 +2435,8 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
     if (opts) o = *opts;
     const bool prof_on = o.profile != 0;
     if (o.prec != RSS_FP64 && o.prec != RSS_MIXED) throw Fail{RSS_EINVAL, "rss_factor: bad precision"};
+    if ((o.flags & RSS_FLAG_HYBRID) && ((o.flags & RSS_FLAG_COLOUR_2D) || o.mlp))
+      throw Fail{RSS_EINVAL, "rss_factor: the hybrid factorization takes neither the 2^d schedule nor a rank proposal"};
     cudaStream_t st = (cudaStream_t)o.stream;
     const MlpModel *mlp = nullptr;
     if (o.mlp) {

@@ -141,6 +141,24 @@ static void fft_nd(double2 *X, int dim, int L, int logL, const double2 *tw, int 
   }
 }
 
+// One pass of length-L transforms along axis `ax`, over the lines whose other
+// coordinates d lie below lim[d] (lines entirely outside hold zeros, or
+// results nobody reads).
+static void fft_pass(double2 *X, int dim, int L, int logL, const double2 *tw, int sign, int ax, const int64_t *lim,
+                     cudaStream_t st) {
+  size_t smem = (size_t)2 * L * sizeof(double2);
+  int64_t stride[4] = {1, 1, 1, 1};
+  for (int d = 0; d < dim; d++) stride[d + 1] = stride[d] * L;
+  int o[2] = {-1, -1}, no = 0;
+  for (int d = 0; d < dim; d++)
+    if (d != ax) o[no++] = d;
+  const int64_t lo_lim = no > 0 ? lim[o[0]] : 1, hi_lim = no > 1 ? lim[o[1]] : 1;
+  const int64_t mul = no > 0 ? stride[o[0]] : 0, mul2 = no > 1 ? stride[o[1]] : 0;
+  const int64_t lines = lo_lim * hi_lim;
+  if (lines == 0) return;
+  k_fft_lines<<<(unsigned)lines, 256, smem, st>>>(X, L, logL, stride[ax], mul, lo_lim, mul2, tw, sign); count_launch();
+}
+
 void grid_op_setup(GridOp &G, cudaStream_t st) {
   int64_t tot = 1;
   for (int d = 0; d < G.dim; d++) tot *= G.L;
@@ -156,9 +174,20 @@ void grid_op_apply(const GridOp &G, const double *x, double *y, int nrhs, cudaSt
   for (int c0 = 0; c0 < nrhs; c0 += 2) {
     cudaMemsetAsync(G.X, 0, sizeof(double2) * tot, st);
     k_pack<<<(unsigned)((G.n + 255) / 256), 256, 0, st>>>(G.X, G.gidx, x, G.n, nrhs, c0, G.dim, G.s, G.L); count_launch();
-    fft_nd(G.X, G.dim, G.L, G.logL, G.tw, -1, st);
+    // forward: the data sit in [0, s)^d, so an axis not yet transformed
+    // limits the lines to its first s coordinates
+    int64_t lim[3] = {G.s, G.s, G.s};
+    for (int ax = 0; ax < G.dim; ax++) {
+      fft_pass(G.X, G.dim, G.L, G.logL, G.tw, -1, ax, lim, st);
+      lim[ax] = G.L;
+    }
     k_mul_real<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G.X, G.C, tot, 1.0 / (double)tot); count_launch();
-    fft_nd(G.X, G.dim, G.L, G.logL, G.tw, +1, st);
+    // inverse, last axis first: only [0, s)^d is read, so an axis already
+    // transformed back limits the lines to its first s coordinates
+    for (int ax = G.dim - 1; ax >= 0; ax--) {
+      for (int d = 0; d < G.dim; d++) lim[d] = d > ax ? G.s : G.L;
+      fft_pass(G.X, G.dim, G.L, G.logL, G.tw, +1, ax, lim, st);
+    }
     k_unpack<<<(unsigned)((G.n + 255) / 256), 256, 0, st>>>(G.X, G.gidx, x, y, G.n, nrhs, c0, G.dim, G.s, G.L,
                                                              G.diag); count_launch();
   }

@@ -28,6 +28,7 @@ FLAG_NO_AUTOTUNE = 2
 FLAG_COLOUR_2D = 4
 FLAG_NO_TENSOR_CORES = 8
 FLAG_SYMMETRIC_STORAGE = 16
+FLAG_HYBRID = 32
 
 
 def _nvcc():
