@@ -508,7 +508,7 @@ def main():
 
     peaks = load_peaks()
     peaks["sms"] = torch.cuda.get_device_properties(local).multi_processor_count
-    tuned = [[e["elem_bytes"], e["width"], e["phase_class"], e["tpc"], e["groups"], e["ctas"]]
+    tuned = [[e["elem_bytes"], e["width"], e["phase_class"], e["tpc"], e["groups"], e["ctas"], e["rows"]]
              for e in pkg.autotune_table()]
     # dominant kernel class by time in the profiled pass
     gpu_classes = {k: v for k, v in prof_tot.items() if not k.startswith("host_")}
@@ -553,7 +553,8 @@ def main():
             "clocks": clk,
             "gpu_launches": int(launches),
             "autotune": {"id_shapes": tuned, "fields": ["element bytes", "box width class", "phase-size class",
-                                                        "threads per column", "fold groups", "CTAs per box"]},
+                                                        "threads per column", "fold groups", "CTAs per box",
+                                                        "panel rows per thread (units of 32 FP32 rows)"]},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -364,21 +364,26 @@ rss_status rss_mlp_train(rss_mlp *m, const float *X, const float *y, int64_t n, 
 rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *rank, int64_t nbox);
 
 /* rss_autotune_table -- the autotuner's choices so far in this process, as
- * HOST int32 records of 18: {element bytes (4 FP32 factor, 8 FP64), box-width
+ * HOST int32 records of 25: {element bytes (4 FP32 factor, 8 FP64), box-width
  * class (64, 128 or 256), phase-size class (floor(log2(boxes in the phase))),
- * chosen threads per column, fold groups per box and CTAs per box, then the
- * measured time in microseconds of the 12 candidate shapes (threads per
- * column, groups, CTAs) = (1,1,1) (1,2,1) (1,4,1) (2,1,1) (2,2,1) (2,4,1)
- * (4,1,1) (4,2,1) (2,1,4) (2,1,8) (4,1,4) (4,1,8) (0: not a candidate)}.
+ * the chosen shape (threads per column, fold groups per box, CTAs per box,
+ * panel rows per thread in units of 32 FP32 / 16 FP64 rows), then the
+ * measured time in microseconds of the 18 candidate shapes = (1,1,1,1)
+ * (1,2,1,1) (1,4,1,1) (2,1,1,1) (2,2,1,1) (2,4,1,1) (4,1,1,1) (4,2,1,1)
+ * (2,1,4,1) (2,1,8,1) (4,1,4,1) (4,1,8,1) (0,2,1,1) (0,4,1,1) (0,8,1,1)
+ * (1,1,1,2) (1,2,1,2) (1,4,1,2) (0: not a candidate)}.
  * The ID kernel (Sec. 2.2: Householder reduction of the ID matrix to a
  * triangle, then greedy column pivoting) splits each column over threads
- * that keep 32 (FP32) or 16 (FP64) rows of every panel, a box's rows over
- * fold groups of one CTA or over several CTAs, whose triangles are merged by
- * a tree; more threads per box mean fewer sequential steps per box, fewer
- * fit more boxes per SM.  The first colour phase that meets a key times every
- * candidate on its own boxes (the ID launch is idempotent), keeps the
- * fastest for the rest of the process and re-runs it, so factorizations with
- * the same key compute the same result.  Disabled per factorization by
+ * that keep 32 (FP32) or 16 (FP64) rows of every panel (twice that with two
+ * units of rows), a box's rows over fold groups of one CTA or over several
+ * CTAs, whose triangles are merged by a tree; more threads per box mean
+ * fewer sequential steps per box, fewer fit more boxes per SM.  Threads per
+ * column 0 (width class 64 only) is the warp-per-fold form: `groups` warps
+ * per box, each folding its own rows with the box's columns spread over its
+ * 32 lanes, two per lane.  The first colour phase that meets a key times
+ * every candidate on its own boxes (the ID launch is idempotent), keeps the
+ * fastest for the rest of the process and re-runs it, so factorizations
+ * with the same key compute the same result.  Disabled per factorization by
  * RSS_FLAG_NO_AUTOTUNE.  *nbytes in/out as in rss_tree_query. */
 rss_status rss_autotune_table(int32_t *buf, size_t *nbytes);
 
@@ -386,8 +391,10 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes);
  * from another run), without timing.  Errors: RSS_EINVAL for a shape that is
  * not a candidate or exceeds the kernel's thread limit (256 threads for one
  * thread per column, 512 otherwise; the 256 width class takes several CTAs
- * per box only with two threads per column). */
-rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas);
+ * per box only with two threads per column; the warp-per-fold form only the
+ * 64 width class; two units of rows only one thread per column and width
+ * classes 64 and 128). */
+rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas, int rows);
 
 /* rss_autotune_clear -- forget every choice; the next factorizations tune
  * again. */

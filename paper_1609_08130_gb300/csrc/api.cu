@@ -553,10 +553,19 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   if (sorted && na >= ((size_t)1 << 16)) {
     // cells are runs of the (tree-ordered) active list: cell c holds
     // active[start_c .. start_{c+1}) in order
+    // run starts, found per chunk and concatenated in chunk order
+    const int64_t nch = std::min<int64_t>(64, ((int64_t)na + (1 << 14) - 1) >> 14);
+    std::vector<std::vector<int64_t>> part(nch);
+    HostPool::get().parallel_for(nch, [&](int64_t h) {
+      const int64_t lo = (int64_t)na * h / nch, hi = (int64_t)na * (h + 1) / nch;
+      for (int64_t q = lo; q < hi; q++)
+        if (q == 0 || dk[q] != dk[q - 1]) part[h].push_back(q);
+    });
     std::vector<int64_t> starts;
-    starts.reserve(na / 8 + 1);
-    for (size_t q = 0; q < na; q++)
-      if (q == 0 || dk[q] != dk[q - 1]) starts.push_back((int64_t)q);
+    size_t ns = 0;
+    for (const auto &v : part) ns += v.size();
+    starts.reserve(ns);
+    for (const auto &v : part) starts.insert(starts.end(), v.begin(), v.end());
     L.ncell = (int)starts.size();
     L.key.resize(L.ncell);
     L.cell_b.resize(L.ncell);
@@ -678,19 +687,19 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
     L.box_colour.push_back(colour_of(&T.coord[3 * node], dim, cbase));
   }
   if (cbase != 3) {
-    // colour-major with cbase^dim colours, Morton order within a colour
+    // colour-major with cbase^dim colours, Morton order within a colour:
+    // nodes of one depth in pre-order are in Morton order, so the boxes
+    // sorted by node index, then a stable counting sort by colour
     const int nb = (int)L.box_cell.size();
-    std::vector<int> ord(nb);
-    std::vector<uint64_t> mk(nb);
-    for (int q = 0; q < nb; q++) {
-      ord[q] = q;
-      const int node = L.box_node[q];
-      const int64_t p[3] = {T.coord[3 * node], T.coord[3 * node + 1], T.coord[3 * node + 2]};
-      mk[q] = morton_fast(p, dim);
-    }
-    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
-      return L.box_colour[a] != L.box_colour[b] ? L.box_colour[a] < L.box_colour[b] : mk[a] < mk[b];
-    });
+    std::vector<int> byn(nb), ord(nb);
+    for (int q = 0; q < nb; q++) byn[q] = q;
+    std::sort(byn.begin(), byn.end(), [&](int a, int b) { return L.box_node[a] < L.box_node[b]; });
+    int ncol = 1;
+    for (int d = 0; d < dim; d++) ncol *= cbase;
+    std::vector<int> cstart(ncol + 1, 0);
+    for (int q = 0; q < nb; q++) cstart[L.box_colour[q] + 1]++;
+    for (int c = 0; c < ncol; c++) cstart[c + 1] += cstart[c];
+    for (int q : byn) ord[cstart[L.box_colour[q]]++] = q;
     std::vector<int> bc(nb), bn(nb), bcol(nb);
     for (int q = 0; q < nb; q++) bc[q] = L.box_cell[ord[q]], bn[q] = L.box_node[ord[q]], bcol[q] = L.box_colour[ord[q]];
     L.box_cell.swap(bc);
@@ -999,12 +1008,25 @@ static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vect
 // that key computes exactly the same thing.
 // ---------------------------------------------------------------------------
 
-// Candidate launch shapes (threads per column, fold groups per box, CTAs per box).
-constexpr int kNShapes = 12;
-static const int kTuneShapes[kNShapes][3] = {{1, 1, 1}, {1, 2, 1}, {1, 4, 1}, {2, 1, 1}, {2, 2, 1}, {2, 4, 1},
-                                             {4, 1, 1}, {4, 2, 1}, {2, 1, 4}, {2, 1, 8}, {4, 1, 4}, {4, 1, 8}};
-static bool shape_fits(int width, int tpc, int g) { return width * tpc * g <= (tpc == 1 ? 256 : 512); }
-static int shape_hint(int c) { return (kTuneShapes[c][2] << 8) | (kTuneShapes[c][0] << 4) | kTuneShapes[c][1]; }
+// Candidate launch shapes (threads per column, fold groups per box, CTAs per
+// box, panel rows per thread in units of 32 FP32 / 16 FP64 rows); threads
+// per column 0 is the warp-per-fold kernel (width class 64 only) with
+// `groups` warps per box; two units of rows only with one thread per column.
+constexpr int kNShapes = 18;
+static const int kTuneShapes[kNShapes][4] = {
+    {1, 1, 1, 1}, {1, 2, 1, 1}, {1, 4, 1, 1}, {2, 1, 1, 1}, {2, 2, 1, 1}, {2, 4, 1, 1},
+    {4, 1, 1, 1}, {4, 2, 1, 1}, {2, 1, 4, 1}, {2, 1, 8, 1}, {4, 1, 4, 1}, {4, 1, 8, 1},
+    {0, 2, 1, 1}, {0, 4, 1, 1}, {0, 8, 1, 1}, {1, 1, 1, 2}, {1, 2, 1, 2}, {1, 4, 1, 2}};
+static bool shape_fits(int width, int tpc, int g, int rows = 1) {
+  if (rows != 1 && (rows != 2 || tpc != 1 || width > 128)) return false;
+  if (tpc == 0) return width == 64 && g * 32 <= 512;
+  return width * tpc * g <= (tpc == 1 ? 256 : 512);
+}
+static int shape_hint(int c) {
+  if (kTuneShapes[c][0] == 0) return (1 << 12) | kTuneShapes[c][1];
+  return (kTuneShapes[c][3] == 2 ? 1 << 13 : 0) | (kTuneShapes[c][2] << 8) | (kTuneShapes[c][0] << 4) |
+         kTuneShapes[c][1];
+}
 struct TuneEntry {
   int shape;            // index into kTuneShapes
   float us[kNShapes];   // time of each candidate, microseconds; 0 if not a candidate
@@ -1038,7 +1060,7 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
     float best = 0.f;
     for (int ci = 0; ci < kNShapes; ci++) {
       const int tpc = kTuneShapes[ci][0], g = kTuneShapes[ci][1], ctas = kTuneShapes[ci][2];
-      if (!shape_fits(width, tpc, g)) continue;  // the kernels' thread limits
+      if (!shape_fits(width, tpc, g, kTuneShapes[ci][3])) continue;  // the kernels' thread limits
       if (ctas > 1 && width == 256 && tpc != 2) continue;  // the widest class: two threads per column
       set_id_groups(shape_hint(ci));
       float ms = 0.f;
@@ -1224,44 +1246,19 @@ template <typename T> static void run_factor(Factor<T> &F) {
   bool have_prev = false;
 
   auto assemble_pairs = [&](const HLevel &H, DLevel<T> &D, const LevelDev<T> *prev) {
-    // one entry per (cell, neighbour at distance <= 2), in cell order
-    std::vector<int64_t> first(H.ncell + 1, 0);
+    // one block per (cell, neighbour code at distance <= 2), enumerated on
+    // the device from the level's tables; codes with no neighbour are empty
     int64_t maxblk = 0;
-    for (int c = 0; c < H.ncell; c++) {
-      int cnt = 0;
-      for (int o = 0; o < H.NB; o++) {
-        const int nb = H.cell_nbr[(size_t)c * H.NB + o];
-        if (nb < 0) continue;
-        cnt++;
-        maxblk = std::max(maxblk, (int64_t)H.cell_b[c] * H.cell_b[nb]);
-      }
-      first[c + 1] = first[c] + cnt;
-    }
-    const int64_t npair = first[H.ncell];
-    std::vector<int64_t> row_off(npair), col_off(npair), out_off(npair);
-    std::vector<int> nrow(npair), ncol(npair);
-    parallel_range(H.ncell, 2048, [&](int64_t c0, int64_t c1) {
-      int64_t e = first[c0];
-      for (int64_t c = c0; c < c1; c++)
-        for (int o = 0; o < H.NB; o++) {
-          const int nb = H.cell_nbr[(size_t)c * H.NB + o];
-          if (nb < 0) continue;
-          row_off[e] = H.cell_dof_off[c];
-          col_off[e] = H.cell_dof_off[nb];
-          out_off[e] = H.pair_off[(size_t)c * H.NB + o];
-          nrow[e] = H.cell_b[c];
-          ncol[e] = H.cell_b[nb];
-          e++;
-        }
-    });
-    DBuf a, b2, c2, d2, e2;
-    upload(a, row_off, st);
-    upload(b2, col_off, st);
-    upload(c2, out_off, st);
-    upload(d2, nrow, st);
-    upload(e2, ncol, st);
-    AssembleList L{(int)row_off.size(), ptr<int64_t>(a), ptr<int64_t>(b2), ptr<int64_t>(c2),
-                   ptr<int>(d2), ptr<int>(e2), ptr<int64_t>(D.cell_dofs), ptr<int64_t>(D.cell_dofs), 0};
+    for (int c = 0; c < H.ncell; c++) maxblk = std::max(maxblk, (int64_t)H.cell_b[c]);
+    maxblk *= maxblk;
+    AssembleList L{};
+    L.nblock = H.ncell * H.NB;
+    L.row_ids = L.col_ids = ptr<int64_t>(D.cell_dofs);
+    L.cell_nbr = ptr<int>(D.cell_nbr);
+    L.cell_b = ptr<int>(D.cell_b);
+    L.cell_dof_off = ptr<int64_t>(D.cell_dof_off);
+    L.pair_off = ptr<int64_t>(D.pair_off);
+    L.NB = H.NB;
     int pi = F.prof.begin(KC_ASSEMBLE, st, 0, 0, 0, 2.0 * (double)H.pool_elems * sizeof(T), 0.0);
     launch_assemble<T>(L, ptr<T>(D.pool), prev, F.P, F.K, maxblk, st);
     F.prof.end(pi, st);
@@ -1634,13 +1631,25 @@ template <typename T> static void run_factor(Factor<T> &F) {
       if (par >= 0) child_b[((int64_t)box_prob[q] << 32) | (uint32_t)par] += fb.b;
     }
     double ta0 = now_ms();
+    // each cell's active DOFs at its offset in the problem's list (an
+    // exclusive scan of the counts), filled in parallel over cells
+    std::vector<int64_t> aoff(H.ncell + 1, 0);
+    for (int c = 0; c < H.ncell; c++) aoff[c + 1] = aoff[c] + ac[c];
+    for (int p = 0; p < np; p++)
+      if (cell_base[p + 1] > cell_base[p]) active[p].resize(aoff[cell_base[p + 1]] - aoff[cell_base[p]]);
+    std::vector<int> cell_prob(H.ncell);
+    for (int p = 0; p < np; p++)
+      for (int c = cell_base[p]; c < cell_base[p + 1]; c++) cell_prob[c] = p;
+    parallel_range(H.ncell, 256, [&](int64_t c0, int64_t c1) {
+      for (int64_t c = c0; c < c1; c++) {
+        const int p = cell_prob[c];
+        int64_t *dst = active[p].data() + (aoff[c] - aoff[cell_base[p]]);
+        for (int q = 0; q < ac[c]; q++) dst[q] = H.cell_dofs[H.cell_dof_off[c] + ai[H.cell_dof_off[c] + q]] - F.pdof[p];
+      }
+    });
     HostPool::get().parallel_for(np, [&](int64_t p) {
       if (cell_base[p + 1] == cell_base[p]) return;
       std::vector<int64_t> &act = active[p];
-      act.clear();
-      for (int c = cell_base[p]; c < cell_base[p + 1]; c++)
-        for (int q = 0; q < ac[c]; q++)
-          act.push_back(H.cell_dofs[H.cell_dof_off[c] + ai[H.cell_dof_off[c] + q]] - F.pdof[p]);
       if (!std::is_sorted(act.begin(), act.end())) std::sort(act.begin(), act.end());
     });
     F.prof.host(KC_HOST_LEVEL, now_ms() - ta0);
@@ -2942,7 +2951,7 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
         v.push_back(std::get<0>(kv.first));
         v.push_back(std::get<1>(kv.first));
         v.push_back(std::get<2>(kv.first));
-        for (int f = 0; f < 3; f++) v.push_back(kTuneShapes[kv.second.shape][f]);
+        for (int f = 0; f < 4; f++) v.push_back(kTuneShapes[kv.second.shape][f]);
         for (int c = 0; c < kNShapes; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
       }
     }
@@ -2955,13 +2964,15 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes) {
   });
 }
 
-rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas) {
+rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas, int rows) {
   return guard([&] {
     int shape = -1;
     for (int c = 0; c < kNShapes; c++)
-      if (kTuneShapes[c][0] == tpc && kTuneShapes[c][1] == groups && kTuneShapes[c][2] == ctas) shape = c;
+      if (kTuneShapes[c][0] == tpc && kTuneShapes[c][1] == groups && kTuneShapes[c][2] == ctas &&
+          kTuneShapes[c][3] == rows)
+        shape = c;
     if (shape < 0 || (elem_bytes != 4 && elem_bytes != 8) || (width != 64 && width != 128 && width != 256) ||
-        phase_class < 0 || phase_class > 40 || !shape_fits(width, tpc, groups) ||
+        phase_class < 0 || phase_class > 40 || !shape_fits(width, tpc, groups, rows) ||
         (width == 256 && ctas > 1 && tpc != 2))
       throw Fail{RSS_EINVAL, "rss_autotune_set: bad arguments"};
     std::lock_guard<std::mutex> lk(g_tune_m);

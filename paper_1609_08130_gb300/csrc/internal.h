@@ -79,6 +79,11 @@ struct AssembleList {
   const int *nrow, *ncol;
   const int64_t *row_ids, *col_ids;
   int transpose;  // 1: entry (i, j) holds A(col j, row i) (row-major A)
+  // level mode (cell_nbr set): block q is the pair (cell q / NB, neighbour
+  // code q % NB), read from the level's tables; row_off .. ncol are unused
+  const int *cell_nbr, *cell_b;
+  const int64_t *cell_dof_off, *pair_off;
+  int NB;
 };
 
 struct ProxyParams {

@@ -46,11 +46,26 @@ static bool capturing(cudaStream_t st) {
 template <typename T>
 __global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__ out, LevelDev<T> prev,
                                                  int has_prev, Points P, KernelParams K) {
-  int q = blockIdx.x;
-  int nr = L.nrow[q], nc = L.ncol[q];
-  const int64_t *rid = L.row_ids + L.row_off[q];
-  const int64_t *cid = L.col_ids + L.col_off[q];
-  T *o = out + L.out_off[q];
+  const int q = blockIdx.x;
+  int nr, nc;
+  const int64_t *rid, *cid;
+  T *o;
+  if (L.cell_nbr) {
+    const int nb = L.cell_nbr[q];
+    if (nb < 0) return;
+    const int c = q / L.NB;
+    nr = L.cell_b[c];
+    nc = L.cell_b[nb];
+    rid = L.row_ids + L.cell_dof_off[c];
+    cid = L.col_ids + L.cell_dof_off[nb];
+    o = out + L.pair_off[q];
+  } else {
+    nr = L.nrow[q];
+    nc = L.ncol[q];
+    rid = L.row_ids + L.row_off[q];
+    cid = L.col_ids + L.col_off[q];
+    o = out + L.out_off[q];
+  }
   int64_t tot = (int64_t)nr * nc;
   for (int64_t e = blockIdx.y * (int64_t)NT + threadIdx.x; e < tot; e += (int64_t)NT * gridDim.y) {
     int i = (int)(e % nr), j = (int)(e / nr);
@@ -515,23 +530,157 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Vector loads and stores of a thread's panel rows (16-byte aligned
+// addresses): float4 for FP32, double2 for FP64.
+template <typename T, int N> __device__ __forceinline__ void store_vec(T *dst, const T (&v)[N]) {
+  if constexpr (sizeof(T) == 4) {
+    static_assert(N % 4 == 0, "FP32 rows in fours");
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < N / 4; i++) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+    static_assert(N % 2 == 0, "FP64 rows in pairs");
+    double2 *d2 = reinterpret_cast<double2 *>(dst);
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) d2[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  }
+}
+template <typename T, int N> __device__ __forceinline__ void load_vec(T (&v)[N], const T *src) {
+  if constexpr (sizeof(T) == 4) {
+    static_assert(N % 4 == 0, "FP32 rows in fours");
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int i = 0; i < N / 4; i++) {
+      const float4 t = s4[i];
+      v[4 * i] = t.x;
+      v[4 * i + 1] = t.y;
+      v[4 * i + 2] = t.z;
+      v[4 * i + 3] = t.w;
+    }
+  } else {
+    static_assert(N % 2 == 0, "FP64 rows in pairs");
+    const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+      const double2 t = s2[i];
+      v[2 * i] = t.x;
+      v[2 * i + 1] = t.y;
+    }
+  }
+}
+
+// Sums and updates over a thread's panel rows.  FP32 goes through the
+// paired FMA (__ffma2_rn: two correctly rounded FMAs per instruction) with
+// the same grouping of partial sums as the scalar form, so both give the
+// same bits; FP64 stays scalar.
+//   rows_dot8:   sum_i v_i p_i over eight interleaved partial sums
+//   rows_dot2:   the same over two
+//   rows_sumsq4: sum_i p_i^2 over four
+//   rows_sumsq2: the same over two
+//   rows_axpy:   p_i -= f v_i
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+template <typename T, int N> __device__ __forceinline__ T rows_dot8(const T (&v)[N], const T (&p)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 8 == 0) {
+    float2 d[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) d[u] = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < N; i += 8)
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        d[u] = __ffma2_rn(f2(v[i + 2 * u], v[i + 2 * u + 1]), f2(p[i + 2 * u], p[i + 2 * u + 1]), d[u]);
+    return ((d[0].x + d[0].y) + (d[1].x + d[1].y)) + ((d[2].x + d[2].y) + (d[3].x + d[3].y));
+  } else {
+    T d[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) d[u] = (T)0;
+#pragma unroll
+    for (int i = 0; i < N; i += 8)
+#pragma unroll
+      for (int u = 0; u < 8 && i + u < N; u++) d[u] += v[i + u] * p[i + u];
+    return ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
+  }
+}
+template <typename T, int N> __device__ __forceinline__ T rows_dot2(const T (&v)[N], const T (&p)[N]) {
+  static_assert(N % 2 == 0, "rows in pairs");
+  if constexpr (sizeof(T) == 4) {
+    float2 d = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) d = __ffma2_rn(f2(v[i], v[i + 1]), f2(p[i], p[i + 1]), d);
+    return d.x + d.y;
+  } else {
+    T d0 = (T)0, d1 = (T)0;
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      d0 += v[i] * p[i];
+      d1 += v[i + 1] * p[i + 1];
+    }
+    return d0 + d1;
+  }
+}
+template <typename T, int N> __device__ __forceinline__ T rows_sumsq4(const T (&p)[N]) {
+  static_assert(N % 4 == 0, "rows in fours");
+  if constexpr (sizeof(T) == 4) {
+    float2 s0 = f2(0.f, 0.f), s1 = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      s0 = __ffma2_rn(f2(p[i], p[i + 1]), f2(p[i], p[i + 1]), s0);
+      s1 = __ffma2_rn(f2(p[i + 2], p[i + 3]), f2(p[i + 2], p[i + 3]), s1);
+    }
+    return (s0.x + s0.y) + (s1.x + s1.y);
+  } else {
+    T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      s0 += p[i] * p[i];
+      s1 += p[i + 1] * p[i + 1];
+      s2 += p[i + 2] * p[i + 2];
+      s3 += p[i + 3] * p[i + 3];
+    }
+    return (s0 + s1) + (s2 + s3);
+  }
+}
+template <typename T, int N> __device__ __forceinline__ T rows_sumsq2(const T (&p)[N]) {
+  static_assert(N % 2 == 0, "rows in pairs");
+  if constexpr (sizeof(T) == 4) {
+    float2 s = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) s = __ffma2_rn(f2(p[i], p[i + 1]), f2(p[i], p[i + 1]), s);
+    return s.x + s.y;
+  } else {
+    T s0 = (T)0, s1 = (T)0;
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      s0 += p[i] * p[i];
+      s1 += p[i + 1] * p[i + 1];
+    }
+    return s0 + s1;
+  }
+}
+template <typename T, int N> __device__ __forceinline__ void rows_axpy(T (&p)[N], const T (&v)[N], T f) {
+  if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+    const float2 nf = f2(-f, -f);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const float2 r = __ffma2_rn(nf, f2(v[i], v[i + 1]), f2(p[i], p[i + 1]));
+      p[i] = r.x;
+      p[i + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) p[i] -= f * v[i];
+  }
+}
+
 // The owner of column j publishes [v (PR entries) | tau | scl | beta | flag]
 // for the reflector of step j, computed from its column, its squared norm
 // and the current diagonal R[j][j]; flag = 0 means there is nothing to
 // annihilate.  Entries are padded to a multiple of four for vector loads.
 template <typename T, int PR>
 __device__ __forceinline__ void publish_reflector(T *dst, const T (&pan)[PR], T x0) {
-  T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
-#pragma unroll
-  for (int i = 0; i < PR; i += 4) {
-    s0 += pan[i] * pan[i];
-    s1 += pan[i + 1] * pan[i + 1];
-    s2 += pan[i + 2] * pan[i + 2];
-    s3 += pan[i + 3] * pan[i + 3];
-  }
-  const T s = (s0 + s1) + (s2 + s3);
-#pragma unroll
-  for (int i = 0; i < PR; i++) dst[i] = pan[i];
+  const T s = rows_sumsq4<T, PR>(pan);
+  store_vec<T, PR>(dst, pan);  // dst is 16-byte aligned: the buffers' stride is a multiple of 16 bytes
   if (s > (T)0) {
     const T nrm = sqrt(x0 * x0 + s);
     const T beta = x0 >= (T)0 ? -nrm : nrm;
@@ -541,39 +690,6 @@ __device__ __forceinline__ void publish_reflector(T *dst, const T (&pan)[PR], T 
     dst[PR + 3] = (T)1;
   } else {
     dst[PR + 3] = (T)0;
-  }
-}
-
-template <typename T, int PR> __device__ __forceinline__ void load_vec(T (&v)[PR], const T *src);
-template <typename T, int PR> __device__ __forceinline__ void store_vec(T *dst, const T (&v)[PR]);
-template <> __device__ __forceinline__ void store_vec<float, 32>(float *dst, const float (&v)[32]) {
-  float4 *d4 = reinterpret_cast<float4 *>(dst);
-#pragma unroll
-  for (int i = 0; i < 8; i++) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-}
-template <> __device__ __forceinline__ void store_vec<double, 16>(double *dst, const double (&v)[16]) {
-  double2 *d2 = reinterpret_cast<double2 *>(dst);
-#pragma unroll
-  for (int i = 0; i < 8; i++) d2[i] = make_double2(v[2 * i], v[2 * i + 1]);
-}
-template <> __device__ __forceinline__ void load_vec<float, 32>(float (&v)[32], const float *src) {
-  const float4 *s4 = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-  for (int i = 0; i < 8; i++) {
-    float4 t = s4[i];
-    v[4 * i] = t.x;
-    v[4 * i + 1] = t.y;
-    v[4 * i + 2] = t.z;
-    v[4 * i + 3] = t.w;
-  }
-}
-template <> __device__ __forceinline__ void load_vec<double, 16>(double (&v)[16], const double *src) {
-  const double2 *s2 = reinterpret_cast<const double2 *>(src);
-#pragma unroll
-  for (int i = 0; i < 8; i++) {
-    double2 t = s2[i];
-    v[2 * i] = t.x;
-    v[2 * i + 1] = t.y;
   }
 }
 
@@ -588,37 +704,27 @@ __device__ __forceinline__ void fold_group(T (&pan)[PR], T *R, int ldr, int b, i
   // j0 > 0: the panel is zero left of column j0 (rows j0.. of a triangle),
   // so the reflectors of the columns before it would change nothing
   if (col == j0 && j0 < b) publish_reflector<T, PR>(vbuf + (j0 & 1) * VS, pan, R[j0 * ldr + j0]);
-  for (int j = j0; j < b; j++) {
+  const int wlast = col | 31;  // the last column of this warp (columns of a warp are consecutive)
+  T *Rj = R + (size_t)j0 * ldr;  // row j of the triangle
+  for (int j = j0; j < b; j++, Rj += ldr) {
     group_bar(bar_id, nthr);
+    if (j > wlast) continue;  // every column of this warp is done: only the barrier
     const T *vb = vbuf + (j & 1) * VS;
-    T *vn = vbuf + ((j + 1) & 1) * VS;
-    const T flag = vb[PR + 3];
-    if (flag != (T)0) {
-      if (col > j && col < b) {
-        T v[PR];
-        load_vec<T, PR>(v, vb);
-        const T tau = vb[PR], scl = vb[PR + 1];
-        T d[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) d[u] = (T)0;
-#pragma unroll
-        for (int i = 0; i < PR; i += 8)
-#pragma unroll
-          for (int u = 0; u < 8 && i + u < PR; u++) d[u] += v[i + u] * pan[i + u];
-        const T dd = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
-        const T rj = R[j * ldr + col];
-        const T f = tau * (rj + scl * dd);
-        const T fs = f * scl;
-#pragma unroll
-        for (int i = 0; i < PR; i++) pan[i] -= fs * v[i];
-        R[j * ldr + col] = rj - f;
-        if (col == j + 1) publish_reflector<T, PR>(vn, pan, R[col * ldr + col]);
-      } else if (col == j) {
-        R[j * ldr + j] = vb[PR + 2];  // nobody reads R[j][j] again in this fold
-      }
-    } else if (col == j + 1 && col < b) {
-      publish_reflector<T, PR>(vn, pan, R[col * ldr + col]);
+    if (vb[PR + 3] != (T)0) {  // the same for the whole group
+      // every lane applies the reflector; columns at or left of j and
+      // beyond b take f = 0, which leaves their rows as they are
+      T v[PR];
+      load_vec<T, PR>(v, vb);
+      const T tau = vb[PR], scl = vb[PR + 1];
+      const bool act = col > j && col < b;
+      const T dd = rows_dot8<T, PR>(v, pan);
+      const T rj = Rj[col];
+      const T f = act ? tau * (rj + scl * dd) : (T)0;
+      rows_axpy<T, PR>(pan, v, f * scl);
+      if (act) Rj[col] = rj - f;
+      else if (col == j) Rj[col] = vb[PR + 2];  // beta; nobody reads R[j][j] again in this fold
     }
+    if (col == j + 1 && col < b) publish_reflector<T, PR>(vbuf + ((j + 1) & 1) * VS, pan, Rj[ldr + col]);
   }
   group_bar(bar_id, nthr);
 }
@@ -766,7 +872,22 @@ __device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShare
         const T d = col_sum<T, TPC>(a0);
         const T f = tau * (rjc + scl * d);
         const T fs = f * scl;
-        for (int i = j + 1 + part; i < b; i += TPC) R[i * LDR + col] -= fs * R[i * LDR + pc];
+        // eight rows at a time, loads before stores (the compiler cannot
+        // tell that column col is not column pc)
+        for (int i0 = j + 1 + part; i0 < b; i0 += 8 * TPC) {
+          T xp[8], xc[8];
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int i = i0 + u * TPC;
+            xp[u] = i < b ? R[i * LDR + pc] : (T)0;
+            xc[u] = i < b ? R[i * LDR + col] : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int i = i0 + u * TPC;
+            if (i < b) R[i * LDR + col] = xc[u] - fs * xp[u];
+          }
+        }
         rjc -= f;
         if (part == 0) R[j * LDR + col] = rjc;
       }
@@ -816,11 +937,11 @@ __device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShare
   }
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int RPT = IdwRows<T>::PR>
 __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
                                              Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
                                              double eps, int ring_max, int *err) {
-  constexpr int PR = IdwRows<T>::PR;
+  constexpr int PR = RPT;  // rows of a panel, all held by the column's thread
   constexpr int LDR = NC + 1;
   constexpr int VS = PR + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -959,13 +1080,7 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
 template <typename T, int PR, int TPC>
 __device__ __forceinline__ void publish_part(T *dst, const T (&pan)[PR / TPC], T x0, int part) {
   constexpr int RPT = PR / TPC;
-  T s0 = (T)0, s1 = (T)0;
-#pragma unroll
-  for (int i = 0; i < RPT; i += 2) {
-    s0 += pan[i] * pan[i];
-    s1 += pan[i + 1] * pan[i + 1];
-  }
-  const T s = col_sum<T, TPC>(s0 + s1);
+  const T s = col_sum<T, TPC>(rows_sumsq2<T, RPT>(pan));
   store_vec<T, RPT>(dst + part * RPT, pan);
   if (part == 0) {
     if (s > (T)0) {
@@ -997,18 +1112,11 @@ __device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, 
         T v[RPT];
         load_vec<T, RPT>(v, vb + part * RPT);  // 16-byte aligned: VS and RPT are multiples of 4 (FP32) / 2 (FP64)
         const T tau = vb[PR], scl = vb[PR + 1];
-        T d0 = (T)0, d1 = (T)0;
-#pragma unroll
-        for (int i = 0; i < RPT; i += 2) {
-          d0 += v[i] * pan[i];
-          d1 += v[i + 1] * pan[i + 1];
-        }
         const T rj = R[j * ldr + col];
-        const T dd = col_sum<T, TPC>(d0 + d1);  // also orders the read of rj before the write below
+        const T dd = col_sum<T, TPC>(rows_dot2<T, RPT>(v, pan));  // also orders the read of rj before the write below
         const T f = tau * (rj + scl * dd);
         const T fs = f * scl;
-#pragma unroll
-        for (int i = 0; i < RPT; i++) pan[i] -= fs * v[i];
+        rows_axpy<T, RPT>(pan, v, fs);
         if (part == 0) R[j * ldr + col] = rj - f;
         if (col == j + 1) publish_part<T, PR, TPC>(vn, pan, R[col * ldr + col], part);
       } else if (col == j && part == 0) {
@@ -1400,11 +1508,11 @@ static void launch_idq(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
   count_launch();
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int RPT = IdwRows<T>::PR>
 static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
                        const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
                        double eps, int ring_max, cudaStream_t st, int *err) {
-  constexpr int PR = IdwRows<T>::PR;
+  constexpr int PR = RPT;
   const size_t tri = (size_t)NC * (NC + 1) * sizeof(T);
   int gmax = (int)((190u << 10) / tri);
   if (gmax < 1) gmax = 1;
@@ -1412,15 +1520,236 @@ static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
   if (G * NC > 256) G = 256 / NC;
   size_t smem = (((size_t)G * tri + 15) & ~(size_t)15) + (((size_t)G * 2 * (PR + 4) * sizeof(T) + 15) & ~(size_t)15) +
                 (size_t)ring_max * sizeof(int64_t) + (size_t)NC * sizeof(int) + 16;
-  cudaFuncSetAttribute(k_idc<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_idc<T, NC><<<nbox, G * NC, smem, st>>>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, err);
+  cudaFuncSetAttribute(k_idc<T, NC, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idc<T, NC, RPT><<<nbox, G * NC, smem, st>>>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max,
+                                                err);
   count_launch();
 }
 
 
+// ---------------------------------------------------------------------------
+// Warp-per-fold ID for boxes with b <= 64 (k_idw).  One CTA of W warps per
+// box; warp w folds row panels w, w + W, ... of the ID matrix into its own
+// b x b triangle.  Lane l keeps columns l and l + 32 of a PR-row panel in
+// registers, the reflector of each step goes through the warp's own double
+// buffer in shared memory, and a step costs a __syncwarp instead of a
+// barrier across warps.  The reflector is loaded once for both columns, and
+// the lower column half is skipped once the step has passed it.  The warps'
+// triangles are then merged by a tree (a fold of the partner's rows, whose
+// leading zeros are skipped), and all W warps run the column-pivoted QR of
+// the merged triangle (idq_finish, W / 2 threads per column).  Reflectors,
+// triangle and pivoting are those of k_idc; only the order in which rows
+// are folded and partial sums are added differs.
+// ---------------------------------------------------------------------------
+
+// Apply the reflector (v, tau, scl) of the current step to one column: its
+// PR panel rows `p` and its entry of the triangle's current row, *rjc.
+template <typename T, int PR>
+__device__ __forceinline__ void warp_col_update(T (&p)[PR], const T (&v)[PR], T tau, T scl, T *rjc) {
+  const T dd = rows_dot8<T, PR>(v, p);
+  const T rj = *rjc;
+  const T f = tau * (rj + scl * dd);
+  const T fs = f * scl;
+  rows_axpy<T, PR>(p, v, fs);
+  *rjc = rj - f;
+}
+
+// Fold one PR-row panel (columns lane and lane + 32 in p0 and p1) into the
+// warp's triangle R, starting at column j0 (the panel is zero left of it).
+template <typename T, int PR>
+__device__ __forceinline__ void fold_warp(T (&p0)[PR], T (&p1)[PR], T *R, int ldr, int b, int lane, T *vbuf,
+                                          int j0) {
+  constexpr int VS = PR + 4;
+  const int c0 = lane, c1 = lane + 32;
+  if (j0 < b) {
+    if (j0 < 32) {
+      if (c0 == j0) publish_reflector<T, PR>(vbuf + (j0 & 1) * VS, p0, R[j0 * ldr + j0]);
+    } else if (c1 == j0) {
+      publish_reflector<T, PR>(vbuf + (j0 & 1) * VS, p1, R[j0 * ldr + j0]);
+    }
+  }
+  for (int j = j0; j < b; j++) {
+    __syncwarp();
+    const T *vb = vbuf + (j & 1) * VS;
+    T *vn = vbuf + ((j + 1) & 1) * VS;
+    if (vb[PR + 3] != (T)0) {
+      T v[PR];
+      load_vec<T, PR>(v, vb);
+      const T tau = vb[PR], scl = vb[PR + 1];
+      if (j < 31 && c0 > j && c0 < b) warp_col_update<T, PR>(p0, v, tau, scl, R + j * ldr + c0);
+      if (c1 > j && c1 < b) warp_col_update<T, PR>(p1, v, tau, scl, R + j * ldr + c1);
+      if ((j < 32 ? c0 : c1) == j) R[j * ldr + j] = vb[PR + 2];  // nobody reads R[j][j] again in this fold
+    }
+    const int jn = j + 1;
+    if (jn < b) {
+      if (jn < 32) {
+        if (c0 == jn) publish_reflector<T, PR>(vn, p0, R[jn * ldr + jn]);
+      } else if (c1 == jn) {
+        publish_reflector<T, PR>(vn, p1, R[jn * ldr + jn]);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, Points P,
+                                                KernelParams K, ProxyParams px, const double *proxy_unit, double eps,
+                                                int ring_max, int *err) {
+  constexpr int PR = IdwRows<T>::PR;
+  constexpr int LDR = 65;
+  constexpr int VS = PR + 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ocode[125], s_obase[126], s_no;
+  __shared__ IdqShared<T, 64, W / 2> s_sh;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  FBox<T> &fb = boxes[box_list[blockIdx.x]];
+  const int c = fb.cell, b = fb.b, dim = lv.dim;
+  T *R0 = reinterpret_cast<T *>(smem_raw);
+  T *Rw = R0 + (size_t)wid * 64 * LDR;
+  const size_t tri_bytes = (((size_t)W * 64 * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)wid * 2 * VS;
+  int64_t *s_rowsrc =
+      reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)W * 2 * VS * sizeof(T) + 15) & ~(size_t)15));
+  int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
+
+  for (int e = lane; e < 64 * LDR; e += 32) Rw[e] = (T)0;
+  if (tid < 32) {
+    const int ncode = dim == 3 ? 125 : 25;
+    int no = 0, acc = 0;
+    for (int base = 0; base < ncode; base += 32) {
+      int code = base + tid, cnt = 0;
+      if (code < ncode) {
+        int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+        const int dist = max(abs(dx), max(abs(dy), abs(dz)));
+        if (dist == 2 || (lv.weak && dist == 1)) {  // ring O; weak steps: N too
+          int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+          if (nb >= 0) cnt = lv.act_cnt[nb];
+        }
+      }
+      unsigned mask = __ballot_sync(FULL, cnt > 0);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, o);
+        if (tid >= o) incl += t;
+      }
+      int pos = __popc(mask & ((1u << tid) - 1));
+      if (cnt > 0) {
+        s_ocode[no + pos] = code;
+        s_obase[no + pos] = acc + incl - cnt;
+      }
+      no += __popc(mask);
+      acc += __shfl_sync(FULL, incl, 31);
+    }
+    if (tid == 0) {
+      s_obase[no] = acc;
+      s_no = no;
+    }
+  }
+  __syncthreads();
+  const int no = s_no;
+  const int nO = s_obase[no];
+  if (nO > ring_max) {
+    if (tid == 0) set_err(err, DERR_INTERNAL);
+    return;  // uniform: every thread sees the same nO
+  }
+  for (int q = 0; q < no; q++) {
+    const int code = s_ocode[q];
+    const int nb = lv.cell_nbr[(int64_t)c * lv.NB + code];
+    const int64_t abase = lv.cell_dof_off[nb];
+    const int64_t pbase = lv.pair_off[(int64_t)c * lv.NB + code];
+    for (int t = tid; t < s_obase[q + 1] - s_obase[q]; t += blockDim.x)
+      s_rowsrc[s_obase[q] + t] = pbase + (int64_t)lv.act_idx[abase + t] * b;
+  }
+  __syncthreads();
+  const int m = nO + px.np;
+  const int64_t coff = lv.cell_dof_off[c];
+  const double D = ldexp(1.0, -lv.t);
+  const double rad = px.radius * D;
+  const int c0 = lane, c1 = lane + 32;
+  double xq0[3], xq1[3];
+  {
+    const int64_t g0 = c0 < b ? lv.cell_dofs[coff + c0] : 0, g1 = c1 < b ? lv.cell_dofs[coff + c1] : 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
+      xq0[d] = (c0 < b && d < dim) ? P.x[g0 * dim + d] - ctr : 0.0;
+      xq1[d] = (c1 < b && d < dim) ? P.x[g1 * dim + d] - ctr : 0.0;
+    }
+  }
+  const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
+  const int npan = (m + PR - 1) / PR;
+  for (int pnl = wid; pnl < npan; pnl += W) {
+    T p0[PR], p1[PR];
+#pragma unroll
+    for (int i = 0; i < PR; i++) {
+      const int row = pnl * PR + i;
+      T v0 = (T)0, v1 = (T)0;
+      if (row < nO) {
+        const int64_t src = s_rowsrc[row];
+        if (c0 < b) v0 = lv.pool[src + c0];
+        if (c1 < b) v1 = lv.pool[src + c1];
+      } else if (row < m) {
+        const int pm = row - nO;
+        double r0 = 0.0, r1 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const double u = rad * proxy_unit[3 * pm + d];
+          r0 += (u - xq0[d]) * (u - xq0[d]);
+          r1 += (u - xq1[d]) * (u - xq1[d]);
+        }
+        if (c0 < b) v0 = w * kof(K.kind, (T)r0);
+        if (c1 < b) v1 = w * kof(K.kind, (T)r1);
+      }
+      p0[i] = v0;
+      p1[i] = v1;
+    }
+    fold_warp<T, PR>(p0, p1, Rw, LDR, b, lane, vbuf, 0);
+  }
+  // tree merge: in round `step`, warp w (a multiple of 2*step) absorbs w + step
+  for (int step = 1; step < W; step <<= 1) {
+    __syncthreads();
+    if (wid % (2 * step) == 0 && wid + step < W) {
+      const T *Ro = Rw + (size_t)step * 64 * LDR;
+      for (int q0 = 0; q0 < b; q0 += PR) {
+        T p0[PR], p1[PR];
+#pragma unroll
+        for (int i = 0; i < PR; i++) {
+          const int row = q0 + i;
+          p0[i] = (row < b && c0 < b) ? Ro[row * LDR + c0] : (T)0;
+          p1[i] = (row < b && c1 < b) ? Ro[row * LDR + c1] : (T)0;
+        }
+        fold_warp<T, PR>(p0, p1, Rw, LDR, b, lane, vbuf, q0);
+      }
+    }
+  }
+  __syncthreads();
+  idq_finish<T, 64, W / 2>(R0, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
+}
+
+template <typename T, int W> static size_t idw_smem(int ring_max) {
+  constexpr int PR = IdwRows<T>::PR;
+  return ((((size_t)W * 64 * 65 * sizeof(T)) + 15) & ~(size_t)15) +
+         ((((size_t)W * 2 * (PR + 4) * sizeof(T)) + 15) & ~(size_t)15) + (size_t)ring_max * sizeof(int64_t) +
+         64 * sizeof(int) + 16;
+}
+
+template <typename T, int W>
+static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, const Points &P,
+                       const KernelParams &K, const ProxyParams &px, const double *proxy_unit, double eps,
+                       int ring_max, cudaStream_t st, int *err) {
+  const size_t smem = idw_smem<T, W>(ring_max);
+  cudaFuncSetAttribute(k_idw<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idw<T, W><<<nbox, W * 32, smem, st>>>(lv, boxes, box_list, P, K, px, proxy_unit, eps, ring_max, err);
+  count_launch();
+}
+
 // Launch shape of the next ID launch on this thread: fold groups per box
-// (hint & 15), threads per column ((hint >> 4) & 15; 0 or 1: k_idc) and CTAs
-// per box (hint >> 8; more than 1: k_idm); 0: default.  Set by the host's
+// (hint & 15), threads per column ((hint >> 4) & 15; 0 or 1: k_idc), CTAs
+// per box ((hint >> 8) & 15; more than 1: k_idm), with bit 12 set the
+// warp-per-fold kernel k_idw with (hint & 15) warps, with bit 13 set (k_idc)
+// twice the panel rows per thread; 0: default.  Set by the host's
 // autotuner around a launch_id call, with the multi-CTA scratch.
 static thread_local int id_groups_hint = 0;
 static thread_local IdMultiScratch id_multi{};
@@ -1441,7 +1770,26 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     // width, phase size), else the default (enough boxes resident at once to
     // finish a large phase in one wave, more groups per box when small)
     const int NCw = bmax <= 64 ? 64 : 128;
-    int G = id_groups_hint & 15, TPC = (id_groups_hint >> 4) & 15, C = id_groups_hint >> 8;
+    if (((id_groups_hint >> 12) & 1) && bmax <= 64) {
+      // eight warps: FP32 only (eight FP64 triangles exceed shared memory);
+      // a ring too long for the row table takes the shapes below
+      const size_t lim = 220u << 10;
+      const int W = sizeof(T) == 4 || (id_groups_hint & 15) != 8 ? id_groups_hint & 15 : 4;
+      if constexpr (sizeof(T) == 4)
+        if (W == 8 && idw_smem<T, 8>(ring_max) <= lim) {
+          launch_idw<T, 8>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
+          return;
+        }
+      if (W == 2 && idw_smem<T, 2>(ring_max) <= lim) {
+        launch_idw<T, 2>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
+        return;
+      }
+      if (W != 2 && idw_smem<T, 4>(ring_max) <= lim) {
+        launch_idw<T, 4>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
+        return;
+      }
+    }
+    int G = id_groups_hint & 15, TPC = (id_groups_hint >> 4) & 15, C = (id_groups_hint >> 8) & 15;
     const int64_t ts = (int64_t)NCw * (NCw + 1);
     if (C > 1 && TPC >= 2 && id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots && ts <= id_multi.slot_elems &&
         NCw * TPC <= 512) {
@@ -1456,20 +1804,25 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     }
     if (G <= 0) G = NCw == 64 ? (nbox >= 300 ? 2 : 4) : (nbox >= 300 ? 1 : 2);
     if (TPC <= 0) TPC = 1;
+    // bit 13: one thread per column holding twice the rows of a panel
+    constexpr int R2 = 2 * IdwRows<T>::PR;
+    const bool rows2 = TPC == 1 && ((id_groups_hint >> 13) & 1);
     if (NCw == 64) {
       if (TPC == 4) launch_idq<T, 64, 4>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
       else if (TPC == 2) launch_idq<T, 64, 2>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (rows2) launch_idc<T, 64, R2>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
       else launch_idc<T, 64>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
     } else {
       if (TPC == 4) launch_idq<T, 128, 4>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
       else if (TPC == 2) launch_idq<T, 128, 2>(lv, boxes, box_list, nbox, G, bmax, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (rows2) launch_idc<T, 128, R2>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
       else launch_idc<T, 128>(lv, boxes, box_list, nbox, G, P, K, px, proxy_unit, eps, ring_max, st, err);
     }
     return;
   }
   if (bmax <= 256 && !force_general) {
     // one group per box, the triangle sized by the level's widest box
-    const int TPC = ((id_groups_hint >> 4) & 15) == 1 ? 1 : 2, C = id_groups_hint >> 8;
+    const int TPC = ((id_groups_hint >> 4) & 15) == 1 ? 1 : 2, C = (id_groups_hint >> 8) & 15;
     if (C > 1 && TPC == 2 && id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots &&
         (int64_t)bmax * (bmax + 1) <= id_multi.slot_elems) {
       const size_t smw = (((size_t)bmax * (bmax + 1) * sizeof(T) + 15) & ~(size_t)15) + 2 * (64 + 4) * sizeof(T) + 16 +
@@ -1490,7 +1843,7 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
   if (bmax <= 512 && !force_general) {
     // boxes too wide for a shared-memory triangle: several CTAs per box
     // with their triangles in global (L2-resident) slots
-    const int C = (id_groups_hint >> 8) > 1 ? (id_groups_hint >> 8) : 16;  // 8: 904 ms, 16: 827 ms (3D 32^3, 1e-6)
+    const int C = ((id_groups_hint >> 8) & 15) > 1 ? ((id_groups_hint >> 8) & 15) : 16;  // 8: 904 ms, 16: 827 ms (3D 32^3, 1e-6)
     if (id_multi.tri && (int64_t)nbox * C <= id_multi.max_slots &&
         (int64_t)bmax * (bmax + 1) <= id_multi.slot_elems &&
         idm_smem<T, 512, 1, true>(bmax, mmax) <= (size_t)(220 << 10)) {

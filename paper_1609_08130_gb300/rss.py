@@ -105,7 +105,7 @@ _SIGS = {
                                 C.POINTER(C.c_double)]),
     "rss_box_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "rss_autotune_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
-    "rss_autotune_set": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "rss_autotune_set": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "rss_autotune_clear": (None, []),
     "rss_free": (None, [C.c_void_p]),
     "rss_last_error": (C.c_char_p, []),
@@ -136,19 +136,24 @@ def kernel_launches() -> int:
 
 
 def autotune_table() -> list:
-    """rss_autotune_table: [{elem_bytes, width, phase_class, tpc, groups, ctas, us: [12 candidates]}]."""
+    """rss_autotune_table: [{elem_bytes, width, phase_class, tpc, groups, ctas, rows, us: [18 candidates]}]."""
     import numpy as np
     nb = C.c_size_t(0)
     _check(lib().rss_autotune_table(None, C.byref(nb)))
     buf = np.zeros(max(nb.value // 4, 1), dtype=np.int32)
     _check(lib().rss_autotune_table(C.c_void_p(buf.ctypes.data), C.byref(nb)))
-    recs = buf[:nb.value // 4].reshape(-1, 18)
+    rl = 7 + len(AUTOTUNE_SHAPES)
+    recs = buf[:nb.value // 4].reshape(-1, rl)
     return [dict(elem_bytes=int(r[0]), width=int(r[1]), phase_class=int(r[2]), tpc=int(r[3]), groups=int(r[4]),
-                 ctas=int(r[5]), us=[int(x) for x in r[6:18]]) for r in recs]
+                 ctas=int(r[5]), rows=int(r[6]), us=[int(x) for x in r[7:rl]]) for r in recs]
 
 
-AUTOTUNE_SHAPES = [(1, 1, 1), (1, 2, 1), (1, 4, 1), (2, 1, 1), (2, 2, 1), (2, 4, 1), (4, 1, 1), (4, 2, 1),
-                   (2, 1, 4), (2, 1, 8), (4, 1, 4), (4, 1, 8)]
+# (threads per column, fold groups, CTAs per box, panel rows per thread in
+# units of 32 FP32 / 16 FP64 rows); threads per column 0: the warp-per-fold
+# form with `groups` warps (box width class 64 only)
+AUTOTUNE_SHAPES = [(1, 1, 1, 1), (1, 2, 1, 1), (1, 4, 1, 1), (2, 1, 1, 1), (2, 2, 1, 1), (2, 4, 1, 1),
+                   (4, 1, 1, 1), (4, 2, 1, 1), (2, 1, 4, 1), (2, 1, 8, 1), (4, 1, 4, 1), (4, 1, 8, 1),
+                   (0, 2, 1, 1), (0, 4, 1, 1), (0, 8, 1, 1), (1, 1, 1, 2), (1, 2, 1, 2), (1, 4, 1, 2)]
 
 
 def _check(st: int):

@@ -337,7 +337,7 @@ def test_autotuner_choices_are_reproducible(pkg):
     tab = pkg.autotune_table()
     assert tab, "no autotuner entries after a factorization"
     for e in tab:
-        shape = (e["tpc"], e["groups"], e["ctas"])
+        shape = (e["tpc"], e["groups"], e["ctas"], e["rows"])
         assert shape in pkg.rss.AUTOTUNE_SHAPES
         assert e["width"] in (64, 128, 256) and e["elem_bytes"] in (4, 8)
         chosen = pkg.rss.AUTOTUNE_SHAPES.index(shape)
@@ -375,8 +375,9 @@ def test_graph_solve_matches_stream_solve(pkg, prec):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_every_id_launch_shape_matches_oracle(pkg, prec):
     """Each launch shape the autotuner may pick (threads per column, fold
-    groups per box), pinned for every key, gives a factor within 10 eps of
-    the oracle's."""
+    groups per box, CTAs per box, panel rows per thread; the warp-per-fold
+    form with 2, 4 or 8 warps), pinned for every key, gives a factor within
+    10 eps of the oracle's."""
     lib = pkg.lib()
     pts = inputs.random_points(93, 3000, 2)  # boxes of width class 64 and 128
     eps = 1e-6
@@ -385,22 +386,26 @@ def test_every_id_launch_shape_matches_oracle(pkg, prec):
     yo, zo = of.apply(x), of.solve(x)
     elem = 8 if prec == "fp64" else 4
     try:
-        for tpc, g, ctas in pkg.rss.AUTOTUNE_SHAPES:
+        for tpc, g, ctas, rows in pkg.rss.AUTOTUNE_SHAPES:
             lib.rss_autotune_clear()
             for width in (64, 128):
+                if tpc == 0 and width != 64:
+                    continue  # the warp-per-fold form takes boxes of width class 64 only
                 if width * tpc * g > (256 if tpc == 1 else 512):
                     continue
                 for cls in range(0, 20):
-                    assert lib.rss_autotune_set(elem, width, cls, tpc, g, ctas) == 0
+                    assert lib.rss_autotune_set(elem, width, cls, tpc, g, ctas, rows) == 0
             f = pkg.Factorization(_cuda(pts), 0, eps, leaf=64, prec=pkg.FP64 if prec == "fp64" else pkg.MIXED)
             y = f.apply(_cuda(x)).cpu().numpy()
             z = f.solve(_cuda(x)).cpu().numpy()
-            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, (tpc, g, ctas)
-            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, g, ctas)
+            assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 10 * eps, (tpc, g, ctas, rows)
+            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 10 * eps, (tpc, g, ctas, rows)
     finally:
         lib.rss_autotune_clear()
-    assert lib.rss_autotune_set(4, 64, 3, 4, 4, 1) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
-    assert lib.rss_autotune_set(4, 64, 3, 2, 1, 3) == pkg.rss.RSS_EINVAL  # 3 CTAs per box: not a shape
+    assert lib.rss_autotune_set(4, 64, 3, 4, 4, 1, 1) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
+    assert lib.rss_autotune_set(4, 64, 3, 2, 1, 3, 1) == pkg.rss.RSS_EINVAL  # 3 CTAs per box: not a shape
+    assert lib.rss_autotune_set(4, 128, 3, 0, 4, 1, 1) == pkg.rss.RSS_EINVAL  # warp per fold: width 64 only
+    assert lib.rss_autotune_set(4, 64, 3, 2, 1, 1, 2) == pkg.rss.RSS_EINVAL  # two units of rows: one thread per column
 
 
 def test_wide_box_id_matches_oracle(pkg):
@@ -418,7 +423,7 @@ def test_wide_box_id_matches_oracle(pkg):
         for tpc, ctas in ((1, 1), (2, 1), (2, 4), (2, 8)):
             lib.rss_autotune_clear()
             for cls in range(0, 20):
-                assert lib.rss_autotune_set(4, 256, cls, tpc, 1, ctas) == 0
+                assert lib.rss_autotune_set(4, 256, cls, tpc, 1, ctas, 1) == 0
             f = pkg.Factorization(_cuda(pts), 1, eps, leaf=64, prec=pkg.MIXED)
             st = f.stats()
             assert st["b"].max() > 128, st["b"].max()
