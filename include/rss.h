@@ -19,7 +19,8 @@
  *     that a factor keeps its own copy of the points.
  *   - Calls run on the stream given in rss_options (NULL: the legacy default
  *     stream) and return after their work is complete (they synchronise the
- *     stream), so outputs may be read on return.
+ *     stream), so outputs may be read on return -- unless the factor was
+ *     made with RSS_FLAG_ASYNC (see there).
  *   - Errors are reported by the return code; rss_last_error() gives a
  *     thread-local message.  No C++ exception crosses the ABI.
  */
@@ -110,6 +111,18 @@ typedef struct {
  * entries and a smaller top block, at a somewhat larger apply error.  Not
  * with RSS_FLAG_COLOUR_2D or a rank proposal (RSS_EINVAL). */
 #define RSS_FLAG_HYBRID 32
+/* Asynchronous calls.  rss_factor returns once the last level's ranks are
+ * known and the top block's LU is queued; rss_apply, rss_solve,
+ * rss_solve_noalloc, rss_sqrt_apply (after its first call) and rss_matvec
+ * return once their work is queued on the stream.  Their outputs may be
+ * read after the stream has been synchronised (by the caller, or by
+ * rss_sync).  An error the device records in that work (a zero pivot in the
+ * top block) is returned by the next call on the factor that finds the work
+ * finished, and at the latest by rss_sync.  rss_solve_refined,
+ * rss_solve_cg and rss_logdet stay synchronous (they read device results
+ * on the host).  Ignored when profiling (options.profile), which reads
+ * CUDA events after every call. */
+#define RSS_FLAG_ASYNC 64
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;
@@ -256,6 +269,12 @@ rss_status rss_sqrt_apply(const rss_factorization *f, const double *x, double *y
  * (s a power of two; exact up to FP64 rounding), direct summation over all
  * pairs otherwise.  Device buffers, n x nrhs column-major. */
 rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs);
+
+/* rss_sync -- wait for the factor's stream, then report an error the device
+ * recorded in work of an asynchronous call (RSS_FLAG_ASYNC) that no call has
+ * reported yet (RSS_ENUMERIC for a zero pivot in the top block); RSS_OK
+ * otherwise.  Each recorded error is reported once. */
+rss_status rss_sync(const rss_factorization *f);
 
 /* rss_logdet -- log |det F| of the factorization F ~ A (Sec. 3.3, the
  * determinant by-product: the factors U_T, L_T and the elimination's unit

@@ -825,9 +825,17 @@ template <typename T> struct Factor : FactorBase {
   };
   mutable SweepGraph sgraph[5];
   mutable DBuf g_in, g_out;
+  // asynchronous factors (RSS_FLAG_ASYNC): the device error flag as copied
+  // behind the last call's work, and the event that marks the copy done
+  mutable int *h_err = nullptr;
+  mutable cudaEvent_t ev_err = nullptr;
+  mutable bool err_pending = false;
+  bool async() const { return (flags & RSS_FLAG_ASYNC) != 0 && !prof.on; }
   ~Factor() {
     for (auto &g : sgraph)
       if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ev_err) cudaEventDestroy(ev_err);
+    if (h_err) cudaFreeHost(h_err);
   }
   // FP64 residual operator: FFT convolution when a single problem's points
   // are the cell centres of a regular grid, direct summation otherwise
@@ -919,6 +927,39 @@ static int check_err(DBuf &d_err, cudaStream_t st) {
   CK(cudaMemcpyAsync(&h, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return h;
+}
+
+// Asynchronous factors (RSS_FLAG_ASYNC).  A call that leaves device work
+// whose error flag nobody has read queues a copy of the flag into pinned
+// host memory behind that work, with an event (defer_err); the next call on
+// the factor reads it once the event has completed, or rss_sync waits for
+// it, and reports what the device recorded (take_deferred).
+template <typename T> static void defer_err(const T &F) {
+  if (!F.h_err) {
+    CK(cudaHostAlloc((void **)&F.h_err, sizeof(int), cudaHostAllocDefault));
+    *F.h_err = 0;
+    CK(cudaEventCreateWithFlags(&F.ev_err, cudaEventDisableTiming));
+  }
+  CK(cudaMemcpyAsync(F.h_err, F.d_err.p, sizeof(int), cudaMemcpyDeviceToHost, F.st));
+  CK(cudaEventRecord(F.ev_err, F.st));
+  F.err_pending = true;
+}
+template <typename T> static void take_deferred(const T &F, bool wait) {
+  if (!F.err_pending) return;
+  if (wait) {
+    CK(cudaEventSynchronize(F.ev_err));
+  } else {
+    const cudaError_t q = cudaEventQuery(F.ev_err);
+    if (q == cudaErrorNotReady) return;  // still running: a later call reports it
+    CK(q);
+  }
+  F.err_pending = false;
+  const int e = *F.h_err;
+  if (!e) return;
+  *F.h_err = 0;
+  CK(cudaMemsetAsync(F.d_err.p, 0, sizeof(int), F.st));
+  if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the top block (reported after an asynchronous call)"};
+  throw Fail{RSS_ECUDA, "device-side consistency check failed (reported after an asynchronous call)"};
 }
 
 // Points exactly at the cell centres ((i + 1/2) / s) of an s^dim grid, s a
@@ -1734,6 +1775,10 @@ template <typename T> static void run_factor(Factor<T> &F) {
     F.prof.end(pi, st);
   }
   prevD.reset();
+  if (F.async()) {  // the top block's LU runs on; its error flag is read by a later call
+    defer_err(F);
+    return;
+  }
   int e = check_err(F.d_err, st);
   prof_collect(F);
   if (e == DERR_NUMERIC) throw Fail{RSS_ENUMERIC, "zero pivot in the top block"};
@@ -1882,7 +1927,7 @@ static void do_sweeps(const Factor<T> &F, const double *in, double *out, int nrh
     enqueue_sweeps(F, in, out, v, nrhs, solve, st, F.prof.on);
     check_launch("sweeps");
   }
-  if (sync) {
+  if (sync && !F.async()) {
     CK(cudaStreamSynchronize(st));
     prof_collect(F);
   }
@@ -2246,7 +2291,7 @@ static void sqrt_apply(const Factor<T> &F, const double *x, double *y, int nrhs,
     launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, y + (size_t)c0 * F.n, F.n, nc, st);
     check_launch("rss_sqrt_apply");
   }
-  CK(cudaStreamSynchronize(st));
+  if (!F.async()) CK(cudaStreamSynchronize(st));
 }
 
 // ---------------------------------------------------------------------------
@@ -2311,7 +2356,7 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
     launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, xc, F.n, nc, st);
     check_launch("rss_solve_noalloc");
   }
-  CK(cudaStreamSynchronize(st));
+  if (!F.async()) CK(cudaStreamSynchronize(st));
 }
 
 // Columns in chunks small enough for the sweep kernels' shared-memory
@@ -2329,14 +2374,22 @@ static rss_status sweep_entry(const rss_factorization *f, const double *in, doub
     if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "bad arguments"};
     if (f->impl->prec == RSS_FP64) {
       auto &F = static_cast<const Factor<double> &>(*f->impl);
+      take_deferred(F, false);
       if (F.n > 0 && (!in || !out)) throw Fail{RSS_EINVAL, "NULL vector"};
       sweeps_chunked(F, in, out, nrhs, solve);
     } else {
       auto &F = static_cast<const Factor<float> &>(*f->impl);
+      take_deferred(F, false);
       if (F.n > 0 && (!in || !out)) throw Fail{RSS_EINVAL, "NULL vector"};
       sweeps_chunked(F, in, out, nrhs, solve);
     }
   });
+}
+
+// Every other entry point on a factor reads a deferred device error first.
+static void take_deferred_any(const rss_factorization *f, bool wait) {
+  if (f->impl->prec == RSS_FP64) take_deferred(static_cast<const Factor<double> &>(*f->impl), wait);
+  else take_deferred(static_cast<const Factor<float> &>(*f->impl), wait);
 }
 
 extern "C" {
@@ -2530,6 +2583,7 @@ rss_status rss_solve_refined(const rss_factorization *f, const double *b, double
   bool ok = false;
   rss_status stt = guard([&] {
     if (!f || !f->impl || nrhs < 1 || !(tol > 0) || maxit < 0) throw Fail{RSS_EINVAL, "rss_solve_refined: bad arguments"};
+    take_deferred_any(f, true);
     if (f->impl->prec == RSS_FP64) {
       auto &F = static_cast<const Factor<double> &>(*f->impl);
       if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
@@ -2552,6 +2606,7 @@ rss_status rss_solve_cg(const rss_factorization *f, const double *b, double *x, 
   bool ok = false;
   rss_status stt = guard([&] {
     if (!f || !f->impl || nrhs < 1 || !(tol > 0) || maxit < 0) throw Fail{RSS_EINVAL, "rss_solve_cg: bad arguments"};
+    take_deferred_any(f, true);
     auto run = [&](const auto &F) {
       if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
       ok = F.n == 0 || pcg(F, b, x, nrhs, tol, maxit, iters, relres);
@@ -2577,6 +2632,7 @@ rss_status rss_solve(const rss_factorization *f, const double *b, double *x, int
 rss_status rss_solve_noalloc(const rss_factorization *f, const double *b, double *x, int nrhs) {
   return guard([&] {
     if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "rss_solve_noalloc: bad arguments"};
+    take_deferred_any(f, false);
     if (f->impl->prec == RSS_FP64) {
       auto &F = static_cast<const Factor<double> &>(*f->impl);
       if (F.n > 0 && (!b || !x)) throw Fail{RSS_EINVAL, "NULL vector"};
@@ -2593,6 +2649,7 @@ rss_status rss_sqrt_apply(const rss_factorization *f, const double *x, double *y
   return guard([&] {
     if (!f || !f->impl || nrhs < 1 || (transpose != 0 && transpose != 1))
       throw Fail{RSS_EINVAL, "rss_sqrt_apply: bad arguments"};
+    take_deferred_any(f, false);
     auto run = [&](const auto &F) {
       if (F.n > 0 && (!x || !y)) throw Fail{RSS_EINVAL, "NULL vector"};
       if (F.n > 0) sqrt_apply(F, x, y, nrhs, transpose);
@@ -2605,10 +2662,23 @@ rss_status rss_sqrt_apply(const rss_factorization *f, const double *x, double *y
 rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs) {
   return guard([&] {
     if (!f || !f->impl || nrhs < 1) throw Fail{RSS_EINVAL, "rss_matvec: bad arguments"};
+    take_deferred_any(f, false);
     auto run = [&](const auto &F) {
       if (F.n > 0 && (!x || !y)) throw Fail{RSS_EINVAL, "NULL vector"};
       if (F.n > 0) apply_A(F, x, y, nrhs);
+      if (!F.async()) CK(cudaStreamSynchronize(F.st));
+    };
+    if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
+    else run(static_cast<const Factor<float> &>(*f->impl));
+  });
+}
+
+rss_status rss_sync(const rss_factorization *f) {
+  return guard([&] {
+    if (!f || !f->impl) throw Fail{RSS_EINVAL, "rss_sync: bad arguments"};
+    auto run = [&](const auto &F) {
       CK(cudaStreamSynchronize(F.st));
+      take_deferred(F, true);
     };
     if (f->impl->prec == RSS_FP64) run(static_cast<const Factor<double> &>(*f->impl));
     else run(static_cast<const Factor<float> &>(*f->impl));
@@ -2618,6 +2688,7 @@ rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, in
 rss_status rss_logdet(const rss_factorization *f, double *logabs) {
   return guard([&] {
     if (!f || !f->impl || !logabs) throw Fail{RSS_EINVAL, "rss_logdet: bad arguments"};
+    take_deferred_any(f, true);
     auto run = [&](const auto &F) {
       using T = typename std::remove_reference_t<decltype(F)>::value_type;
       const int nbox = (int)F.h_boxes.size(), np = F.nprob;

@@ -29,6 +29,7 @@ FLAG_COLOUR_2D = 4
 FLAG_NO_TENSOR_CORES = 8
 FLAG_SYMMETRIC_STORAGE = 16
 FLAG_HYBRID = 32
+FLAG_ASYNC = 64
 
 
 def _nvcc():
@@ -86,6 +87,7 @@ _SIGS = {
     "rss_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rss_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rss_sync": (C.c_int, [C.c_void_p]),
     "rss_solve_cg": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rss_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -331,6 +333,11 @@ class Factorization:
     def matvec(self, x):
         """Exact FP64 A x by direct summation."""
         return self._call(lib().rss_matvec, x)
+
+    def sync(self):
+        """rss_sync: wait for the factor's stream; raises RSSError for a
+        device error recorded by asynchronous work (FLAG_ASYNC)."""
+        _check(lib().rss_sync(self.h))
 
     def logdet(self):
         """rss_logdet: log|det F| per problem (numpy float64 array)."""

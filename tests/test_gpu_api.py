@@ -38,3 +38,49 @@ def test_stats_json_matches_stats(pkg, flags):
     leaf = [lv for lv in js["levels"] if lv["depth"] == js["maxdepth"]][0]
     assert leaf["b_sum"] == 4096
     assert js["profile_ms"]["id"] > 0 and js["profile_ms"]["schur"] > 0
+
+
+def _busy(torch):
+    """Queue some tens of milliseconds of work on the current stream."""
+    a = torch.randn(8192, 8192, device="cuda", dtype=torch.float32)
+    for _ in range(8):
+        a = (a @ a) * 1e-4
+    return a
+
+
+def test_async_calls_return_before_their_work_is_done(pkg):
+    """RSS_FLAG_ASYNC: rss_solve and rss_apply return once their work is
+    queued behind earlier work on the stream (the stream is still busy on
+    return), and give the same bits as the synchronous factor once the
+    stream is synchronised; without the flag the stream is idle on return."""
+    pts = torch.from_numpy(inputs.grid_points(128, 2)).cuda()
+    fs = pkg.Factorization(pts, 0, 1e-6, leaf=64, prec=pkg.MIXED)
+    fa = pkg.Factorization(pts, 0, 1e-6, leaf=64, prec=pkg.MIXED, flags=pkg.rss.FLAG_ASYNC)
+    fa.sync()
+    x = torch.from_numpy(inputs.rhs(3, len(pts), 2)).cuda()
+    for op in ("solve", "apply"):
+        ref = getattr(fs, op)(x)
+        _busy(torch)
+        y = getattr(fa, op)(x)
+        assert not torch.cuda.current_stream().query(), op  # still queued
+        fa.sync()
+        assert torch.equal(y, ref), op
+        _busy(torch)
+        getattr(fs, op)(x)
+        assert torch.cuda.current_stream().query(), op  # the synchronous call waited
+
+
+def test_async_factor_reports_a_device_error_later(pkg):
+    """Two points at distance exactly 1 make K = 0 (log 1 = 0); with
+    diag = 0 the matrix is zero and the top block's LU meets a zero pivot.
+    The synchronous factor returns RSS_ENUMERIC; the asynchronous one
+    returns RSS_OK and rss_sync reports RSS_ENUMERIC once."""
+    pts = torch.tensor([[0.0, 0.0], [1.0, 0.0]], dtype=torch.float64).cuda()
+    with pytest.raises(pkg.RSSError) as e:
+        pkg.Factorization(pts, 0, 1e-6, leaf=64, prec=pkg.FP64, diag=0.0)
+    assert e.value.status == pkg.rss.RSS_ENUMERIC
+    f = pkg.Factorization(pts, 0, 1e-6, leaf=64, prec=pkg.FP64, diag=0.0, flags=pkg.rss.FLAG_ASYNC)
+    with pytest.raises(pkg.RSSError) as e:
+        f.sync()
+    assert e.value.status == pkg.rss.RSS_ENUMERIC
+    f.sync()  # reported once
