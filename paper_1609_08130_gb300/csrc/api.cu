@@ -98,6 +98,15 @@ struct DBuf {
     p = nullptr;
     bytes = 0;
   }
+  // take over o's memory (o is left empty)
+  void take(DBuf &o) {
+    release();
+    p = o.p;
+    bytes = o.bytes;
+    st = o.st;
+    o.p = nullptr;
+    o.bytes = 0;
+  }
 };
 
 template <typename U> static inline U *ptr(const DBuf &b) { return static_cast<U *>(b.p); }
@@ -316,6 +325,37 @@ static inline uint64_t morton_fast(const int64_t *c, int dim) {
   return dim == 2 ? (spread2(c[0]) | (spread2(c[1]) << 1))
                   : (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
 }
+// The inverse: every dim-th bit of x from bit 0, packed.
+static inline uint64_t compact2(uint64_t x) {
+  x &= 0x5555555555555555ULL;
+  x = (x | (x >> 1)) & 0x3333333333333333ULL;
+  x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0fULL;
+  x = (x | (x >> 4)) & 0x00ff00ff00ff00ffULL;
+  x = (x | (x >> 8)) & 0x0000ffff0000ffffULL;
+  x = (x | (x >> 16)) & 0x00000000ffffffffULL;
+  return x;
+}
+static inline uint64_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ULL;
+  x = (x | (x >> 2)) & 0x10c30c30c30c30c3ULL;
+  x = (x | (x >> 4)) & 0x100f00f00f00f00fULL;
+  x = (x | (x >> 8)) & 0x001f0000ff0000ffULL;
+  x = (x | (x >> 16)) & 0x001f00000000ffffULL;
+  x = (x | (x >> 32)) & 0x00000000001fffffULL;
+  return x;
+}
+// Cell coordinates of a Morton key (x in the lowest bit of each group).
+static inline void morton_cell(uint64_t k, int dim, int *c) {
+  if (dim == 2) {
+    c[0] = (int)compact2(k);
+    c[1] = (int)compact2(k >> 1);
+    c[2] = 0;
+  } else {
+    c[0] = (int)compact3(k);
+    c[1] = (int)compact3(k >> 1);
+    c[2] = (int)compact3(k >> 2);
+  }
+}
 
 struct HTree {
   uint32_t magic = MAGIC_TREE;
@@ -353,11 +393,21 @@ static void level_lists(HTree &T) {
   for (auto &lv : T.level) std::stable_sort(lv.begin(), lv.end(), [&](int a, int b) { return col[a] < col[b]; });
 }
 
+// Tree-order points of a single problem kept on the device by a factor:
+// coordinates, the permutation (tree -> caller order) and depth-20 cells.
+struct DevTreePoints {
+  DBuf x, perm, c20;
+  bool have = false;
+};
+
 // Trees of nprob problems (device points pts[p], n[p] each) built on the GPU
 // (tree.cu) and copied to the host: one build over all problems when the
-// problem index fits above the Morton key, else one build per group.
+// problem index fits above the Morton key, else one build per group.  With
+// `keep` (a single problem), the tree-order coordinates, permutation and
+// cells stay on the device in *keep and are not copied to the host.
 static void build_trees_gpu(std::vector<HTree> &trees, const double *const *pts, const int64_t *n, int nprob, int dim,
-                            int leaf, cudaStream_t st) {
+                            int leaf, cudaStream_t st, DevTreePoints *keep = nullptr) {
+  if (nprob != 1) keep = nullptr;
   // problems per build: dim * 20 key bits plus the problem index within 64
   const int max_bits = 64 - dim * 20;
   const int per_build = max_bits >= 24 ? (1 << 24) : (1 << max_bits);
@@ -407,9 +457,9 @@ static void build_trees_gpu(std::vector<HTree> &trees, const double *const *pts,
                    ptr<uint64_t>(o_key), st);
     check_launch("tree");
     std::vector<int> depth(nnode), parent(nnode), coord((size_t)3 * nnode);
-    std::vector<int64_t> start(nnode), count(nnode), perm(N);
-    std::vector<double> x((size_t)N * dim);
-    std::vector<int> c20((size_t)N * dim);
+    std::vector<int64_t> start(nnode), count(nnode), perm(keep ? 0 : N);
+    std::vector<double> x(keep ? 0 : (size_t)N * dim);
+    std::vector<int> c20(keep ? 0 : (size_t)N * dim);
     std::vector<uint64_t> key(N);
     auto d2h = [&](void *dst, const DBuf &src, size_t bytes) {
       if (bytes) CK(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToHost, st));
@@ -419,9 +469,16 @@ static void build_trees_gpu(std::vector<HTree> &trees, const double *const *pts,
     d2h(coord.data(), o_coord, sizeof(int) * 3 * nnode);
     d2h(start.data(), o_start, sizeof(int64_t) * nnode);
     d2h(count.data(), o_count, sizeof(int64_t) * nnode);
-    d2h(perm.data(), o_perm, sizeof(int64_t) * N);
-    d2h(x.data(), o_x, sizeof(double) * N * dim);
-    d2h(c20.data(), o_c20, sizeof(int) * N * dim);
+    if (keep) {
+      keep->x.take(o_x);
+      keep->perm.take(o_perm);
+      keep->c20.take(o_c20);
+      keep->have = true;
+    } else {
+      d2h(perm.data(), o_perm, sizeof(int64_t) * N);
+      d2h(x.data(), o_x, sizeof(double) * N * dim);
+      d2h(c20.data(), o_c20, sizeof(int) * N * dim);
+    }
     d2h(key.data(), o_key, sizeof(uint64_t) * N);
     CK(cudaStreamSynchronize(st));
     // split into the problems: a problem's nodes are contiguous (its points
@@ -533,9 +590,10 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
   const int dim = T.dim;
   L.NB = dim == 2 ? 25 : 125;
   const size_t na = active.size();
-  // depth-t cell and key of a DOF from its depth-20 ones: floor(v 2^20) >> (20 - t)
-  // = floor(v 2^t) (clamping included), and the Morton key drops dim bits per level
-  const int ksh = dim * (20 - t), csh = 20 - t;
+  // depth-t key of a DOF from its depth-20 one: the Morton key drops dim
+  // bits per level, and its coordinates are floor(v 2^20) >> (20 - t) =
+  // floor(v 2^t), the DOF's depth-t cell (clamping included)
+  const int ksh = dim * (20 - t);
   std::vector<uint64_t> dk(na);
   std::atomic<bool> unsorted{false};
   parallel_range((int64_t)na, (int64_t)1 << 15, [&](int64_t lo, int64_t hi) {
@@ -579,7 +637,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
         L.key[c] = dk[q];
         L.cell_b[c] = (int)(e - q);
         L.cell_dof_off[c] = q;
-        for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = T.c20[active[q] * dim + d] >> csh;
+        morton_cell(dk[q], dim, &L.cell_coord[3 * c]);
       }
     });
   } else if (sorted) {
@@ -607,8 +665,7 @@ static HLevel build_level(const HTree &T, int t, const std::vector<int64_t> &act
     std::vector<int64_t> fill(L.cell_dof_off.begin(), L.cell_dof_off.end() - 1);
     for (size_t q = 0; q < na; q++) {
       int c = cid[q];
-      if (fill[c] == L.cell_dof_off[c])
-        for (int d = 0; d < dim; d++) L.cell_coord[3 * c + d] = T.c20[active[q] * dim + d] >> csh;
+      if (fill[c] == L.cell_dof_off[c]) morton_cell(dk[q], dim, &L.cell_coord[3 * c]);
       L.cell_dofs[fill[c]++] = active[q];
     }
   } else if (na == 0) {
@@ -798,6 +855,7 @@ template <typename T> struct Factor : FactorBase {
   int64_t n = 0;
   int dim = 2;
   DBuf d_x, d_perm, d_cell, d_off, d_err, d_proxy, d_wdof;
+  DevTreePoints dev_pts;  // a single problem's tree-order points, kept on the device
   Points P{};
   std::vector<std::unique_ptr<DBuf>> store;  // factor storage chunks
   int64_t factor_bytes = 0;
@@ -976,6 +1034,19 @@ template <typename T> static void detect_grid(Factor<T> &F) {
   int64_t tot = 1;
   for (int d = 0; d < dim; d++) tot *= s;
   if (tot != n || (s & (s - 1)) != 0 || 2 * s > 2048) return;
+  if (T_.x.empty()) {  // the points are on the device only: test them there
+    DBuf seen, bad;
+    seen.alloc(sizeof(unsigned) * (size_t)n, F.st);
+    bad.alloc(sizeof(int), F.st);
+    F.g_gidx.alloc(sizeof(int64_t) * (size_t)n, F.st);
+    CK(cudaMemsetAsync(seen.p, 0, sizeof(unsigned) * (size_t)n, F.st));
+    CK(cudaMemsetAsync(bad.p, 0, sizeof(int), F.st));
+    grid_detect(ptr<double>(F.d_x), ptr<int64_t>(F.d_perm), n, dim, s, ptr<int64_t>(F.g_gidx), ptr<unsigned>(seen),
+                ptr<int>(bad), F.st);
+    check_launch("grid detection");
+    if (check_err(bad, F.st) == 0) F.grid_side = (int)s;
+    return;
+  }
   std::vector<int64_t> gi(n);
   std::vector<unsigned char> seen(n, 0);
   std::atomic<bool> bad{false};
@@ -1181,8 +1252,24 @@ template <typename T> static void run_factor(Factor<T> &F) {
   const int64_t n = F.n;
   const int np = F.nprob;
   cudaStream_t st = F.st;
-  // points: tree order of every problem, concatenated
-  {
+  // points: tree order of every problem, concatenated (a single problem's
+  // from the tree build's device arrays)
+  if (F.dev_pts.have) {
+    const double D = ldexp(1.0, -20);
+    F.d_x.take(F.dev_pts.x);
+    F.d_perm.take(F.dev_pts.perm);
+    F.d_cell.alloc(sizeof(int) * 3 * (size_t)std::max<int64_t>(n, 1), st);
+    F.d_off.alloc(sizeof(float) * 3 * (size_t)std::max<int64_t>(n, 1), st);
+    points_setup(ptr<double>(F.d_x), ptr<int>(F.dev_pts.c20), n, dim, D, ptr<int>(F.d_cell), ptr<float>(F.d_off), st);
+    check_launch("points setup");
+    F.dev_pts.c20.release();  // stream-ordered: after the setup kernel
+    F.P.x = ptr<double>(F.d_x);
+    F.P.cell = ptr<int>(F.d_cell);
+    F.P.off = ptr<float>(F.d_off);
+    F.P.D = (float)D;
+    F.P.dim = dim;
+    F.P.wdof = nullptr;
+  } else {
     std::vector<double> x((size_t)std::max<int64_t>(n, 1) * dim);
     std::vector<int64_t> perm(std::max<int64_t>(n, 1));
     std::vector<double> wd;
@@ -1221,6 +1308,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
     F.P.D = (float)D;
     F.P.dim = dim;
     F.P.wdof = np > 1 ? ptr<double>(F.d_wdof) : nullptr;
+  }
+  {
     // direct-sum residual tiles: 256 targets of one problem against its sources
     std::vector<int64_t> ts, te, sb, se;
     for (int p = 0; p < np; p++)
@@ -1957,7 +2046,7 @@ template <typename T> static void apply_A_impl(const Factor<T> &F, const double 
       G.diag = F.K.diag;
       int64_t tot = 1;
       for (int d = 0; d < G.dim; d++) tot *= G.L;
-      upload(F.g_gidx, F.grid_index, F.st);
+      if (!F.grid_index.empty()) upload(F.g_gidx, F.grid_index, F.st);  // else detected on the device
       F.g_C.alloc(sizeof(double2) * tot, F.st);
       F.g_X.alloc(sizeof(double2) * tot, F.st);
       F.g_tw.alloc(sizeof(double2) * (G.L / 2 + 1), F.st);
@@ -2523,7 +2612,7 @@ static rss_status factor_impl(int nprob, const double *const *pts, const int64_t
       F->n = F->pdof[nprob];
       // the trees of every problem, built on the GPU in one pass
       double tt0 = now_ms();
-      build_trees_gpu(F->trees, pts, n, nprob, dim, leaf_size, st);
+      build_trees_gpu(F->trees, pts, n, nprob, dim, leaf_size, st, &F->dev_pts);
       F->prof.host(KC_HOST_TREE, now_ms() - tt0);
       F->K.kind = kernel.kind;
       F->K.diag = kernel.diag;

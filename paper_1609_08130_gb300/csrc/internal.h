@@ -227,6 +227,13 @@ int64_t tree_gpu_scratch_bytes(int64_t n, int dim);
 void tree_gpu_sort(TreeGpu &T, void *scratch, cudaStream_t st);
 void tree_gpu_nodes(const TreeGpu &T, int *depth, int *parent, int *coord, int64_t *start, int64_t *count,
                     int64_t *perm, double *x, int *c20t, uint64_t *keyt, cudaStream_t st);
+// A factor's per-point arrays (cells padded to 3 coordinates, FP32 offsets
+// from the cell corners) and the grid test of the FFT residual operator,
+// both from the tree-order points on the device.
+void points_setup(const double *x, const int *c20, int64_t n, int dim, double D, int *cell3, float *off,
+                  cudaStream_t st);
+void grid_detect(const double *x, const int64_t *perm, int64_t n, int dim, int64_t s, int64_t *gidx, unsigned *seen,
+                 int *bad, cudaStream_t st);
 
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n = 1);

@@ -372,4 +372,57 @@ void tree_gpu_nodes(const TreeGpu &T, int *depth, int *parent, int *coord, int64
   k_tree_gather<<<nb256(n), 256, 0, st>>>(T.pts, T.c20, T.mkey, perm, n, T.dim, x, c20t, keyt); count_launch();
 }
 
+// A factor's per-point arrays from the tree-order points: each point's
+// depth-20 cell padded to three coordinates, and its offset from the cell's
+// corner in FP32 (x - c 2^-20; zero in unused coordinates).
+__global__ void k_points_setup(const double *__restrict__ x, const int *__restrict__ c20, int64_t n, int dim,
+                               double D, int *__restrict__ cell3, float *__restrict__ off) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const int c = d < dim ? c20[g * dim + d] : 0;
+    cell3[3 * g + d] = c;
+    off[3 * g + d] = d < dim ? (float)(x[g * dim + d] - (double)c * D) : 0.f;
+  }
+}
+
+void points_setup(const double *x, const int *c20, int64_t n, int dim, double D, int *cell3, float *off,
+                  cudaStream_t st) {
+  if (n == 0) return;
+  k_points_setup<<<nb256(n), 256, 0, st>>>(x, c20, n, dim, D, cell3, off); count_launch();
+}
+
+// Is every point the centre ((i + 1/2) / s) of its own cell of an s^dim
+// grid?  Records each point's grid index in caller order; *bad != 0 when a
+// coordinate is off the centres or a cell is used twice (seen: n flags,
+// zeroed by the caller).
+__global__ void k_grid_detect(const double *__restrict__ x, const int64_t *__restrict__ perm, int64_t n, int dim,
+                              int64_t s, int64_t *__restrict__ gidx, unsigned *__restrict__ seen, int *bad) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  int64_t lin = 0, mul = 1;
+  for (int d = 0; d < dim; d++) {
+    const double v = x[g * dim + d] * (double)s - 0.5;
+    const double iv = nearbyint(v);
+    if (v != iv || iv < 0 || iv >= (double)s) {
+      atomicOr(bad, 1);
+      return;
+    }
+    lin += (int64_t)iv * mul;
+    mul *= s;
+  }
+  if (atomicExch(&seen[lin], 1u)) {
+    atomicOr(bad, 1);
+    return;
+  }
+  gidx[perm[g]] = lin;
+}
+
+void grid_detect(const double *x, const int64_t *perm, int64_t n, int dim, int64_t s, int64_t *gidx, unsigned *seen,
+                 int *bad, cudaStream_t st) {
+  if (n == 0) return;
+  k_grid_detect<<<nb256(n), 256, 0, st>>>(x, perm, n, dim, s, gidx, seen, bad); count_launch();
+}
+
 }  // namespace rss
