@@ -397,9 +397,9 @@ rss_status rss_box_features(const rss_factorization *f, float *feat, int32_t *ra
  * units of rows), a box's rows over fold groups of one CTA or over several
  * CTAs, whose triangles are merged by a tree; more threads per box mean
  * fewer sequential steps per box, fewer fit more boxes per SM.  Threads per
- * column 0 (width class 64 only) is the warp-per-fold form: `groups` warps
- * per box, each folding its own rows with the box's columns spread over its
- * 32 lanes, two per lane.  The first colour phase that meets a key times
+ * column 0 (width class 64 only) is the warp-per-panel form: `groups`
+ * warps per box, each folding its own panels with the box's columns spread
+ * over its 32 lanes, two per lane, the panels pipelined into one triangle.  The first colour phase that meets a key times
  * every candidate on its own boxes (the ID launch is idempotent), keeps the
  * fastest for the rest of the process and re-runs it, so factorizations
  * with the same key compute the same result.  Disabled per factorization by
@@ -410,9 +410,9 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes);
  * from another run), without timing.  Errors: RSS_EINVAL for a shape that is
  * not a candidate or exceeds the kernel's thread limit (256 threads for one
  * thread per column, 512 otherwise; the 256 width class takes several CTAs
- * per box only with two threads per column; the warp-per-fold form only the
- * 64 width class; two units of rows only one thread per column and width
- * classes 64 and 128). */
+ * per box only with two threads per column; the warp-per-panel form only
+ * the 64 width class; two units of rows only one thread per column and
+ * width classes 64 and 128). */
 rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas, int rows);
 
 /* rss_autotune_clear -- forget every choice; the next factorizations tune

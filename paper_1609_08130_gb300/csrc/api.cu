@@ -1122,8 +1122,8 @@ static void append_level(HLevel &H, const HLevel &Hp, int64_t dof_off, std::vect
 
 // Candidate launch shapes (threads per column, fold groups per box, CTAs per
 // box, panel rows per thread in units of 32 FP32 / 16 FP64 rows); threads
-// per column 0 is the warp-per-fold kernel (width class 64 only) with
-// `groups` warps per box; two units of rows only with one thread per column.
+// per column 0 is the warp-per-panel kernel with `groups` warps per box
+// (width class 64 only); two units of rows only with one thread per column.
 constexpr int kNShapes = 18;
 static const int kTuneShapes[kNShapes][4] = {
     {1, 1, 1, 1}, {1, 2, 1, 1}, {1, 4, 1, 1}, {2, 1, 1, 1}, {2, 2, 1, 1}, {2, 4, 1, 1},
@@ -1131,11 +1131,15 @@ static const int kTuneShapes[kNShapes][4] = {
     {0, 2, 1, 1}, {0, 4, 1, 1}, {0, 8, 1, 1}, {1, 1, 1, 2}, {1, 2, 1, 2}, {1, 4, 1, 2}};
 static bool shape_fits(int width, int tpc, int g, int rows = 1) {
   if (rows != 1 && (rows != 2 || tpc != 1 || width > 128)) return false;
-  if (tpc == 0) return width == 64 && g * 32 <= 512;
+  if (tpc == 0) return width == 64 && (g == 2 || g == 4 || g == 8);
   return width * tpc * g <= (tpc == 1 ? 256 : 512);
 }
 static int shape_hint(int c) {
-  if (kTuneShapes[c][0] == 0) return (1 << 12) | kTuneShapes[c][1];
+  if (kTuneShapes[c][0] == 0) {  // warps as a power of two
+    int lg = 0;
+    while ((1 << lg) < kTuneShapes[c][1]) lg++;
+    return (1 << 12) | lg;
+  }
   return (kTuneShapes[c][3] == 2 ? 1 << 13 : 0) | (kTuneShapes[c][2] << 8) | (kTuneShapes[c][0] << 4) |
          kTuneShapes[c][1];
 }

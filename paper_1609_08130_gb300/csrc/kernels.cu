@@ -1528,18 +1528,22 @@ static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
 
 
 // ---------------------------------------------------------------------------
-// Warp-per-fold ID for boxes with b <= 64 (k_idw).  One CTA of W warps per
-// box; warp w folds row panels w, w + W, ... of the ID matrix into its own
-// b x b triangle.  Lane l keeps columns l and l + 32 of a PR-row panel in
-// registers, the reflector of each step goes through the warp's own double
-// buffer in shared memory, and a step costs a __syncwarp instead of a
-// barrier across warps.  The reflector is loaded once for both columns, and
-// the lower column half is skipped once the step has passed it.  The warps'
-// triangles are then merged by a tree (a fold of the partner's rows, whose
-// leading zeros are skipped), and all W warps run the column-pivoted QR of
-// the merged triangle (idq_finish, W / 2 threads per column).  Reflectors,
-// triangle and pivoting are those of k_idc; only the order in which rows
-// are folded and partial sums are added differs.
+// Warp-per-panel ID for boxes with b <= 64 (k_idw), the panels pipelined
+// into one triangle.  One CTA of W warps per box; warp w folds row panels
+// w, w + W, ... of the ID matrix.  Lane l keeps columns l and l + 32 of a
+// PR-row panel in registers and the reflector of each step goes through the
+// warp's own buffer in shared memory (a __syncwarp, not a barrier across
+// warps, orders it).  All warps fold into the same b x b triangle: panel p
+// takes step j one iteration after panel p - 1 took it, since step j reads
+// and writes only row j of the triangle, which panel p - 1 finished at its
+// own step j.  In one iteration the warps work on different rows, a barrier
+// over the CTA separates iterations, and warp w runs W iterations behind
+// nobody: panel w starts at iteration w, panel w + W one round (max(b, W)
+// iterations) later.  No triangle per warp and no merge: ceil(panels / W)
+// rounds of b steps, then all W warps run the column-pivoted QR of the
+// triangle (idq_finish, W / 2 threads per column).  Reflectors, triangle
+// and pivoting are those of k_idc; only the order in which rows are folded
+// and partial sums are added differs.
 // ---------------------------------------------------------------------------
 
 // Apply the reflector (v, tau, scl) of the current step to one column: its
@@ -1554,66 +1558,68 @@ __device__ __forceinline__ void warp_col_update(T (&p)[PR], const T (&v)[PR], T 
   *rjc = rj - f;
 }
 
-// Fold one PR-row panel (columns lane and lane + 32 in p0 and p1) into the
-// warp's triangle R, starting at column j0 (the panel is zero left of it).
-template <typename T, int PR>
-__device__ __forceinline__ void fold_warp(T (&p0)[PR], T (&p1)[PR], T *R, int ldr, int b, int lane, T *vbuf,
-                                          int j0) {
-  constexpr int VS = PR + 4;
-  const int c0 = lane, c1 = lane + 32;
-  if (j0 < b) {
-    if (j0 < 32) {
-      if (c0 == j0) publish_reflector<T, PR>(vbuf + (j0 & 1) * VS, p0, R[j0 * ldr + j0]);
-    } else if (c1 == j0) {
-      publish_reflector<T, PR>(vbuf + (j0 & 1) * VS, p1, R[j0 * ldr + j0]);
+// Step j of a warp's panel (column lane + 32 s in slot s of p): the owner
+// of column j publishes the reflector from its column and R[j][j], then
+// every lane applies it to its columns right of j and row j of R.
+template <typename T, int PR, int NS>
+__device__ __forceinline__ void warp_step(T (&p)[NS][PR], T *R, int ldr, int b, int lane, T *vb, int j) {
+  if (lane == (j & 31)) {
+    // the owner's column j, picked from its slots with static indices (so
+    // that the panel stays in registers)
+    const int js = j >> 5;
+    T src[PR];
+#pragma unroll
+    for (int i = 0; i < PR; i++) {
+      src[i] = p[0][i];
+#pragma unroll
+      for (int sl = 1; sl < NS; sl++)
+        if (js == sl) src[i] = p[sl][i];
     }
-  }
-  for (int j = j0; j < b; j++) {
-    __syncwarp();
-    const T *vb = vbuf + (j & 1) * VS;
-    T *vn = vbuf + ((j + 1) & 1) * VS;
-    if (vb[PR + 3] != (T)0) {
-      T v[PR];
-      load_vec<T, PR>(v, vb);
-      const T tau = vb[PR], scl = vb[PR + 1];
-      if (j < 31 && c0 > j && c0 < b) warp_col_update<T, PR>(p0, v, tau, scl, R + j * ldr + c0);
-      if (c1 > j && c1 < b) warp_col_update<T, PR>(p1, v, tau, scl, R + j * ldr + c1);
-      if ((j < 32 ? c0 : c1) == j) R[j * ldr + j] = vb[PR + 2];  // nobody reads R[j][j] again in this fold
-    }
-    const int jn = j + 1;
-    if (jn < b) {
-      if (jn < 32) {
-        if (c0 == jn) publish_reflector<T, PR>(vn, p0, R[jn * ldr + jn]);
-      } else if (c1 == jn) {
-        publish_reflector<T, PR>(vn, p1, R[jn * ldr + jn]);
-      }
-    }
+    publish_reflector<T, PR>(vb, src, R[j * ldr + j]);
   }
   __syncwarp();
+  if (vb[PR + 3] != (T)0) {
+    T v[PR];
+    load_vec<T, PR>(v, vb);
+    const T tau = vb[PR], scl = vb[PR + 1];
+#pragma unroll
+    for (int sl = 0; sl < NS; sl++) {
+      const int c = lane + 32 * sl;
+      if (j < 32 * sl + 31 && c > j && c < b) warp_col_update<T, PR>(p[sl], v, tau, scl, R + j * ldr + c);
+    }
+    if (lane == (j & 31)) R[j * ldr + j] = vb[PR + 2];  // later panels read the new R[j][j]
+  }
+  __syncwarp();  // the buffer is written again at the next step
 }
 
-template <typename T, int W>
+// Rows per panel of the warp-per-panel ID: 32 (FP32) / 16 (FP64) for 64
+// columns (two per lane), half that for 128 (four per lane).
+template <typename T, int NC> struct IdpRows {
+  static constexpr int PR = NC == 64 ? IdwRows<T>::PR : IdwRows<T>::PR / 2;
+};
+
+template <typename T, int W, int NC>
 __global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, Points P,
                                                 KernelParams K, ProxyParams px, const double *proxy_unit, double eps,
                                                 int ring_max, int *err) {
-  constexpr int PR = IdwRows<T>::PR;
-  constexpr int LDR = 65;
+  constexpr int PR = IdpRows<T, NC>::PR;
+  constexpr int NS = NC / 32;  // columns per lane
+  constexpr int LDR = NC + 1;
   constexpr int VS = PR + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ocode[125], s_obase[126], s_no;
-  __shared__ IdqShared<T, 64, W / 2> s_sh;
+  __shared__ IdqShared<T, NC, W * 32 / NC> s_sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   FBox<T> &fb = boxes[box_list[blockIdx.x]];
   const int c = fb.cell, b = fb.b, dim = lv.dim;
-  T *R0 = reinterpret_cast<T *>(smem_raw);
-  T *Rw = R0 + (size_t)wid * 64 * LDR;
-  const size_t tri_bytes = (((size_t)W * 64 * LDR * sizeof(T)) + 15) & ~(size_t)15;
-  T *vbuf = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)wid * 2 * VS;
+  T *R = reinterpret_cast<T *>(smem_raw);
+  const size_t tri_bytes = (((size_t)NC * LDR * sizeof(T)) + 15) & ~(size_t)15;
+  T *vb = reinterpret_cast<T *>(smem_raw + tri_bytes) + (size_t)wid * VS;
   int64_t *s_rowsrc =
-      reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)W * 2 * VS * sizeof(T) + 15) & ~(size_t)15));
+      reinterpret_cast<int64_t *>(smem_raw + tri_bytes + (((size_t)W * VS * sizeof(T) + 15) & ~(size_t)15));
   int *perm = reinterpret_cast<int *>(s_rowsrc + ring_max);
 
-  for (int e = lane; e < 64 * LDR; e += 32) Rw[e] = (T)0;
+  for (int e = tid; e < NC * LDR; e += W * 32) R[e] = (T)0;
   if (tid < 32) {
     const int ncode = dim == 3 ? 125 : 25;
     int no = 0, acc = 0;
@@ -1667,89 +1673,87 @@ __global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, 
   const int64_t coff = lv.cell_dof_off[c];
   const double D = ldexp(1.0, -lv.t);
   const double rad = px.radius * D;
-  const int c0 = lane, c1 = lane + 32;
-  double xq0[3], xq1[3];
-  {
-    const int64_t g0 = c0 < b ? lv.cell_dofs[coff + c0] : 0, g1 = c1 < b ? lv.cell_dofs[coff + c1] : 0;
+  double xq[NS][3];
+#pragma unroll
+  for (int sl = 0; sl < NS; sl++) {
+    const int col = lane + 32 * sl;
+    const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
-      xq0[d] = (c0 < b && d < dim) ? P.x[g0 * dim + d] - ctr : 0.0;
-      xq1[d] = (c1 < b && d < dim) ? P.x[g1 * dim + d] - ctr : 0.0;
+      xq[sl][d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
     }
   }
   const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
   const int npan = (m + PR - 1) / PR;
-  for (int pnl = wid; pnl < npan; pnl += W) {
-    T p0[PR], p1[PR];
+  const int L = max(b, W);  // iterations per round of W panels
+  const int iters = ((npan + W - 1) / W) * L + W - 1;
+  T p[NS][PR];
+  for (int it = 0; it < iters; it++) {
+    group_bar(1, W * 32);
+    const int local = it - wid;
+    if (local < 0) continue;
+    const int j = local % L, pnl = wid + (local / L) * W;
+    if (pnl >= npan || j >= b) continue;
+    if (j == 0) {  // this warp's next panel
 #pragma unroll
-    for (int i = 0; i < PR; i++) {
-      const int row = pnl * PR + i;
-      T v0 = (T)0, v1 = (T)0;
-      if (row < nO) {
-        const int64_t src = s_rowsrc[row];
-        if (c0 < b) v0 = lv.pool[src + c0];
-        if (c1 < b) v1 = lv.pool[src + c1];
-      } else if (row < m) {
-        const int pm = row - nO;
-        double r0 = 0.0, r1 = 0.0;
+      for (int i = 0; i < PR; i++) {
+        const int row = pnl * PR + i;
+        if (row < nO) {
+          const int64_t src = s_rowsrc[row];
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-          const double u = rad * proxy_unit[3 * pm + d];
-          r0 += (u - xq0[d]) * (u - xq0[d]);
-          r1 += (u - xq1[d]) * (u - xq1[d]);
+          for (int sl = 0; sl < NS; sl++) {
+            const int col = lane + 32 * sl;
+            p[sl][i] = col < b ? lv.pool[src + col] : (T)0;
+          }
+        } else if (row < m) {
+          const int pm = row - nO;
+          double u[3];
+#pragma unroll
+          for (int d = 0; d < 3; d++) u[d] = rad * proxy_unit[3 * pm + d];
+#pragma unroll
+          for (int sl = 0; sl < NS; sl++) {
+            double r2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) r2 += (u[d] - xq[sl][d]) * (u[d] - xq[sl][d]);
+            p[sl][i] = lane + 32 * sl < b ? w * kof(K.kind, (T)r2) : (T)0;
+          }
+        } else {
+#pragma unroll
+          for (int sl = 0; sl < NS; sl++) p[sl][i] = (T)0;
         }
-        if (c0 < b) v0 = w * kof(K.kind, (T)r0);
-        if (c1 < b) v1 = w * kof(K.kind, (T)r1);
-      }
-      p0[i] = v0;
-      p1[i] = v1;
-    }
-    fold_warp<T, PR>(p0, p1, Rw, LDR, b, lane, vbuf, 0);
-  }
-  // tree merge: in round `step`, warp w (a multiple of 2*step) absorbs w + step
-  for (int step = 1; step < W; step <<= 1) {
-    __syncthreads();
-    if (wid % (2 * step) == 0 && wid + step < W) {
-      const T *Ro = Rw + (size_t)step * 64 * LDR;
-      for (int q0 = 0; q0 < b; q0 += PR) {
-        T p0[PR], p1[PR];
-#pragma unroll
-        for (int i = 0; i < PR; i++) {
-          const int row = q0 + i;
-          p0[i] = (row < b && c0 < b) ? Ro[row * LDR + c0] : (T)0;
-          p1[i] = (row < b && c1 < b) ? Ro[row * LDR + c1] : (T)0;
-        }
-        fold_warp<T, PR>(p0, p1, Rw, LDR, b, lane, vbuf, q0);
       }
     }
+    warp_step<T, PR, NS>(p, R, LDR, b, lane, vb, j);
   }
   __syncthreads();
-  idq_finish<T, 64, W / 2>(R0, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
+  idq_finish<T, NC, W * 32 / NC>(R, LDR, b, eps, perm, s_sh, fb, lv, coff, nO);
 }
 
-template <typename T, int W> static size_t idw_smem(int ring_max) {
-  constexpr int PR = IdwRows<T>::PR;
-  return ((((size_t)W * 64 * 65 * sizeof(T)) + 15) & ~(size_t)15) +
-         ((((size_t)W * 2 * (PR + 4) * sizeof(T)) + 15) & ~(size_t)15) + (size_t)ring_max * sizeof(int64_t) +
-         64 * sizeof(int) + 16;
+template <typename T, int W, int NC> static size_t idw_smem(int ring_max) {
+  constexpr int PR = IdpRows<T, NC>::PR;
+  return ((((size_t)NC * (NC + 1) * sizeof(T)) + 15) & ~(size_t)15) +
+         ((((size_t)W * (PR + 4) * sizeof(T)) + 15) & ~(size_t)15) + (size_t)ring_max * sizeof(int64_t) +
+         NC * sizeof(int) + 16;
 }
 
-template <typename T, int W>
-static void launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, const Points &P,
+template <typename T, int W, int NC>
+static bool launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, const Points &P,
                        const KernelParams &K, const ProxyParams &px, const double *proxy_unit, double eps,
                        int ring_max, cudaStream_t st, int *err) {
-  const size_t smem = idw_smem<T, W>(ring_max);
-  cudaFuncSetAttribute(k_idw<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_idw<T, W><<<nbox, W * 32, smem, st>>>(lv, boxes, box_list, P, K, px, proxy_unit, eps, ring_max, err);
+  const size_t smem = idw_smem<T, W, NC>(ring_max);
+  if (smem > (size_t)(220u << 10)) return false;  // a ring too long for the row table
+  cudaFuncSetAttribute(k_idw<T, W, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_idw<T, W, NC><<<nbox, W * 32, smem, st>>>(lv, boxes, box_list, P, K, px, proxy_unit, eps, ring_max, err);
   count_launch();
+  return true;
 }
 
 // Launch shape of the next ID launch on this thread: fold groups per box
 // (hint & 15), threads per column ((hint >> 4) & 15; 0 or 1: k_idc), CTAs
 // per box ((hint >> 8) & 15; more than 1: k_idm), with bit 12 set the
-// warp-per-fold kernel k_idw with (hint & 15) warps, with bit 13 set (k_idc)
-// twice the panel rows per thread; 0: default.  Set by the host's
+// warp-per-panel kernel k_idw with 2^(hint & 15) warps, with bit 13 set
+// (k_idc) twice the panel rows per thread; 0: default.  Set by the host's
 // autotuner around a launch_id call, with the multi-CTA scratch.
 static thread_local int id_groups_hint = 0;
 static thread_local IdMultiScratch id_multi{};
@@ -1770,24 +1774,13 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
     // width, phase size), else the default (enough boxes resident at once to
     // finish a large phase in one wave, more groups per box when small)
     const int NCw = bmax <= 64 ? 64 : 128;
-    if (((id_groups_hint >> 12) & 1) && bmax <= 64) {
-      // eight warps: FP32 only (eight FP64 triangles exceed shared memory);
-      // a ring too long for the row table takes the shapes below
-      const size_t lim = 220u << 10;
-      const int W = sizeof(T) == 4 || (id_groups_hint & 15) != 8 ? id_groups_hint & 15 : 4;
-      if constexpr (sizeof(T) == 4)
-        if (W == 8 && idw_smem<T, 8>(ring_max) <= lim) {
-          launch_idw<T, 8>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
-          return;
-        }
-      if (W == 2 && idw_smem<T, 2>(ring_max) <= lim) {
-        launch_idw<T, 2>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
-        return;
-      }
-      if (W != 2 && idw_smem<T, 4>(ring_max) <= lim) {
-        launch_idw<T, 4>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
-        return;
-      }
+    if (((id_groups_hint >> 12) & 1) && NCw == 64) {  // warp per panel: 2^(hint & 15) warps
+      const int W = 1 << (id_groups_hint & 15);
+      bool done = false;
+      if (W == 2) done = launch_idw<T, 2, 64>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (W == 4) done = launch_idw<T, 4, 64>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
+      else if (W == 8) done = launch_idw<T, 8, 64>(lv, boxes, box_list, nbox, P, K, px, proxy_unit, eps, ring_max, st, err);
+      if (done) return;
     }
     int G = id_groups_hint & 15, TPC = (id_groups_hint >> 4) & 15, C = (id_groups_hint >> 8) & 15;
     const int64_t ts = (int64_t)NCw * (NCw + 1);

@@ -151,11 +151,20 @@ def autotune_table() -> list:
 
 
 # (threads per column, fold groups, CTAs per box, panel rows per thread in
-# units of 32 FP32 / 16 FP64 rows); threads per column 0: the warp-per-fold
+# units of 32 FP32 / 16 FP64 rows); threads per column 0: the warp-per-panel
 # form with `groups` warps (box width class 64 only)
 AUTOTUNE_SHAPES = [(1, 1, 1, 1), (1, 2, 1, 1), (1, 4, 1, 1), (2, 1, 1, 1), (2, 2, 1, 1), (2, 4, 1, 1),
                    (4, 1, 1, 1), (4, 2, 1, 1), (2, 1, 4, 1), (2, 1, 8, 1), (4, 1, 4, 1), (4, 1, 8, 1),
                    (0, 2, 1, 1), (0, 4, 1, 1), (0, 8, 1, 1), (1, 1, 1, 2), (1, 2, 1, 2), (1, 4, 1, 2)]
+
+
+def shape_fits(width: int, tpc: int, groups: int, rows: int = 1) -> bool:
+    """Whether (tpc, groups, rows) is a candidate for a box-width class."""
+    if rows != 1 and (rows != 2 or tpc != 1 or width > 128):
+        return False
+    if tpc == 0:
+        return width == 64 and groups in (2, 4, 8)
+    return width * tpc * groups <= (256 if tpc == 1 else 512)
 
 
 def _check(st: int):

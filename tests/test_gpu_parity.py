@@ -375,7 +375,7 @@ def test_graph_solve_matches_stream_solve(pkg, prec):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_every_id_launch_shape_matches_oracle(pkg, prec):
     """Each launch shape the autotuner may pick (threads per column, fold
-    groups per box, CTAs per box, panel rows per thread; the warp-per-fold
+    groups per box, CTAs per box, panel rows per thread; the warp-per-panel
     form with 2, 4 or 8 warps), pinned for every key, gives a factor within
     10 eps of the oracle's."""
     lib = pkg.lib()
@@ -389,9 +389,7 @@ def test_every_id_launch_shape_matches_oracle(pkg, prec):
         for tpc, g, ctas, rows in pkg.rss.AUTOTUNE_SHAPES:
             lib.rss_autotune_clear()
             for width in (64, 128):
-                if tpc == 0 and width != 64:
-                    continue  # the warp-per-fold form takes boxes of width class 64 only
-                if width * tpc * g > (256 if tpc == 1 else 512):
+                if not pkg.rss.shape_fits(width, tpc, g, rows):
                     continue
                 for cls in range(0, 20):
                     assert lib.rss_autotune_set(elem, width, cls, tpc, g, ctas, rows) == 0
@@ -404,7 +402,7 @@ def test_every_id_launch_shape_matches_oracle(pkg, prec):
         lib.rss_autotune_clear()
     assert lib.rss_autotune_set(4, 64, 3, 4, 4, 1, 1) == pkg.rss.RSS_EINVAL  # 1024 threads: not a shape
     assert lib.rss_autotune_set(4, 64, 3, 2, 1, 3, 1) == pkg.rss.RSS_EINVAL  # 3 CTAs per box: not a shape
-    assert lib.rss_autotune_set(4, 128, 3, 0, 4, 1, 1) == pkg.rss.RSS_EINVAL  # warp per fold: width 64 only
+    assert lib.rss_autotune_set(4, 128, 3, 0, 4, 1, 1) == pkg.rss.RSS_EINVAL  # warp per panel: width 64 only
     assert lib.rss_autotune_set(4, 64, 3, 2, 1, 1, 2) == pkg.rss.RSS_EINVAL  # two units of rows: one thread per column
 
 
