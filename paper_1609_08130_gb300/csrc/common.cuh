@@ -17,6 +17,28 @@ enum DevErr { DERR_NONE = 0, DERR_NUMERIC = 4, DERR_INTERNAL = 7, DERR_CAPACITY 
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
+// Division by a loop-invariant divisor 1 <= d < 2^31 with a multiply-high,
+// an add and a shift (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994, Fig. 4.1): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l
+// for 0 <= n < 2^31.  The index loops that walk a matrix element by
+// element use it instead of the hardware-less integer division.
+struct FastDiv {
+  uint32_t d, m, l;
+  __device__ __forceinline__ explicit FastDiv(int dd) : d((uint32_t)dd), l(0) {
+    while (l < 31 && (1u << l) < d) l++;
+    m = (uint32_t)((((uint64_t)((1ull << l) - d)) << 32) / d) + 1u;
+  }
+  __device__ __forceinline__ int div(int n) const {
+    return (int)((__umulhi(m, (uint32_t)n) + (uint32_t)n) >> l);
+  }
+  // n = q d + r, 0 <= r < d
+  __device__ __forceinline__ void divmod(int n, int &q, int &r) const {
+    q = div(n);
+    r = n - q * (int)d;
+  }
+};
+
 // Offsets of the 5^d block around a cell: code = sum_d (delta_d + 2) 5^d.
 __host__ __device__ __forceinline__ int code5(int dx, int dy, int dz, int dim) {
   return (dx + 2) + 5 * (dy + 2) + (dim == 3 ? 25 * (dz + 2) : 0);

@@ -2179,12 +2179,19 @@ __device__ __forceinline__ void smem_gemm(int m, int n, int K, const T *A, int s
       bool cv[4];
 #pragma unroll
       for (int y = 0; y < 4; y++) cv[y] = j0 + tj + 16 * y < n;
+      // rows and columns past the matrix read row / column 0 (their
+      // products are never stored), so the loads need no predicate
+      const T *ap[2], *bp[4];
+#pragma unroll
+      for (int x = 0; x < 2; x++) ap[x] = A + (rv[x] ? (i0 + ti + 16 * x) * sai : 0);
+#pragma unroll
+      for (int y = 0; y < 4; y++) bp[y] = B + (cv[y] ? (j0 + tj + 16 * y) * sbj : 0);
       for (int l = 0; l < K; l++) {
         T a[2], bb[4];
 #pragma unroll
-        for (int x = 0; x < 2; x++) a[x] = rv[x] ? A[(i0 + ti + 16 * x) * sai + l * sal] : (T)0;
+        for (int x = 0; x < 2; x++) a[x] = ap[x][l * sal];
 #pragma unroll
-        for (int y = 0; y < 4; y++) bb[y] = cv[y] ? B[l * sbl + (j0 + tj + 16 * y) * sbj] : (T)0;
+        for (int y = 0; y < 4; y++) bb[y] = bp[y][l * sbl];
 #pragma unroll
         for (int x = 0; x < 2; x++)
 #pragma unroll
@@ -2304,24 +2311,29 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   }
   if (tid == 0 && cta == 0) fb.nj = nj;
   // stage A_BB in (S|R) order
+  const FastDiv fdb(max(b, 1)), fdr(max(r, 1)), fdk(max(k, 1));
   const T *Aii = lv.pool + s_off_in[center];
   for (int e = tid; e < b * b; e += NT) {
-    int pp = e % b, qq = e / b;
+    int pp, qq;
+    fdb.divmod(e, qq, pp);
     Ab[pp + qq * ldb] = Aii[sloc[pp] + (int64_t)sloc[qq] * b];
   }
   __syncthreads();
   // X_RS = A_RS - T^T A_SS,  X_SR = A_SR - A_SS T,  then
   // X_RR = A_RR - T^T A_SR - X_RS T (all as tiled shared-memory products)
   for (int e = tid; e < r * k; e += NT) {
-    int ri = e % r, s2 = e / r;
+    int ri, s2;
+    fdr.divmod(e, s2, ri);
     XRS[ri + s2 * r] = Ab[(k + ri) + s2 * ldb];
   }
   for (int e = tid; e < r * k; e += NT) {
-    int s2 = e % k, ri = e / k;
+    int s2, ri;
+    fdk.divmod(e, ri, s2);
     XSR[s2 + ri * k] = Ab[s2 + (k + ri) * ldb];
   }
   for (int e = tid; e < r * r; e += NT) {
-    int ri = e % r, rj = e / r;
+    int ri, rj;
+    fdr.divmod(e, rj, ri);
     LU[ri * ldl + rj] = Ab[(k + ri) + (k + rj) * ldb];
   }
   __syncthreads();
@@ -2415,7 +2427,11 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   }
   __syncthreads();
   for (int i = tid; i < r; i += NT) spinv[spiv[i]] = i;
-  for (int e = tid; e < r * r; e += NT) fb.LU[e] = LU[(e / r) * ldl + (e % r)];
+  for (int e = tid; e < r * r; e += NT) {
+    int qi, ri;
+    fdr.divmod(e, qi, ri);
+    fb.LU[e] = LU[qi * ldl + ri];
+  }
   for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
   __syncthreads();
   // X_RR^{-1} = U^{-1} L^{-1} P: column cc is U^{-1} L^{-1} e_{pinv[cc]}
@@ -2451,7 +2467,11 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     }
   }
   __syncthreads();
-  for (int e = tid; e < r * r; e += NT) fb.Xi[e] = Xi[(e % r) + (size_t)(e / r) * ldx];
+  for (int e = tid; e < r * r; e += NT) {
+    int qi, ri;
+    fdr.divmod(e, qi, ri);
+    fb.Xi[e] = Xi[ri + (size_t)qi * ldx];
+  }
   }  // cta == 0
   T *Xrj_out = scratch + (int64_t)q * sstride + (int64_t)nj * r;  // r x nj, for the Schur update
   for (int a0 = cta * CH; a0 < nj; a0 += C * CH) {
@@ -2477,41 +2497,48 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       s_cb[tid] = s_off_out[code] + (int64_t)la * b;
     }
     __syncthreads();
+    const FastDiv fdna(max(na, 1));
     for (int e0 = tid; e0 < na * b; e0 += 4 * NT) {
       T val[4];
+      int dst[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int e = e0 + u * NT;
         val[u] = (T)0;
+        dst[u] = -1;
         if (e < na * b) {
-          const int al = e % na, pp = e / na, a = a0 + al;
+          int al, pp;
+          fdna.divmod(e, pp, al);
+          const int a = a0 + al;
+          dst[u] = al + pp * (CH + 1);
           if (a < k) val[u] = pp >= k ? XSR[a + (pp - k) * k] : (T)0;
           else val[u] = lv.pool[s_rb[al] + (int64_t)sloc[pp] * s_rl[al]];
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int e = e0 + u * NT;
-        if (e < na * b) rawJ[(e % na) + (e / na) * (CH + 1)] = val[u];
-      }
+      for (int u = 0; u < 4; u++)
+        if (dst[u] >= 0) rawJ[dst[u]] = val[u];
     }
     for (int e0 = tid; e0 < na * b; e0 += 4 * NT) {
       T val[4];
+      int dst[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int e = e0 + u * NT;
         val[u] = (T)0;
+        dst[u] = -1;
         if (e < na * b) {
-          const int pp = e % b, al = e / b, a = a0 + al;
+          int pp, al;
+          fdb.divmod(e, al, pp);
+          const int a = a0 + al;
+          dst[u] = pp + al * ldb;
           if (a < k) val[u] = pp >= k ? XRS[(pp - k) + a * r] : (T)0;
           else val[u] = lv.pool[s_cb[al] + sloc[pp]];
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int e = e0 + u * NT;
-        if (e < na * b) rawC[(e % b) + (e / b) * ldb] = val[u];
-      }
+      for (int u = 0; u < 4; u++)
+        if (dst[u] >= 0) rawC[dst[u]] = val[u];
     }
     __syncthreads();
     // in place: X_JR = A_JR - A_JS T (rows a >= k);  X_RJ = A_RJ - T^T A_SJ
@@ -2529,14 +2556,16 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     }
     __syncthreads();
     for (int e = tid; e < na * r; e += NT) {
-      int ri = e % r, al = e / r;
+      int ri, al;
+      fdr.divmod(e, al, ri);
       Xrj_out[ri + (int64_t)(a0 + al) * r] = rawC[(k + ri) + al * ldb];
     }
     if (split) {
       // X_JR chunk to the scratch (nj x r, ld nj); E and G follow in k_elim_gemm
       T *Xjr = scratch + (int64_t)q * sstride;
       for (int e = tid; e < na * r; e += NT) {
-        const int al = e % na, ri = e / na;
+        int al, ri;
+        fdna.divmod(e, ri, al);
         Xjr[(a0 + al) + (int64_t)ri * nj] = rawJ[al + (k + ri) * (CH + 1)];
       }
       __syncthreads();
