@@ -396,7 +396,7 @@ static void level_lists(HTree &T) {
 // Tree-order points of a single problem kept on the device by a factor:
 // coordinates, the permutation (tree -> caller order) and depth-20 cells.
 struct DevTreePoints {
-  DBuf x, perm, c20;
+  DBuf x, perm, c20, key;
   bool have = false;
 };
 
@@ -480,6 +480,7 @@ static void build_trees_gpu(std::vector<HTree> &trees, const double *const *pts,
       d2h(c20.data(), o_c20, sizeof(int) * N * dim);
     }
     d2h(key.data(), o_key, sizeof(uint64_t) * N);
+    if (keep) keep->key.take(o_key);  // the copy above reads it first (stream order)
     CK(cudaStreamSynchronize(st));
     // split into the problems: a problem's nodes are contiguous (its points
     // are, and nodes are ordered by first point)
@@ -552,6 +553,11 @@ struct HLevel {
   int64_t pool_elems = 0;
   std::vector<int> box_cell, box_node, box_colour;
   int bmax = 0;
+  // a level built on the device: the cell tables stay there; per box its b,
+  // |J|, ID rows inside the proxy surface and near / ring cells present
+  bool on_device = false;
+  int64_t ndof = 0;
+  std::vector<int> box_b, box_nj, box_ring, box_nnc, box_nrc;
 };
 
 template <typename T> struct DLevel {
@@ -1379,12 +1385,173 @@ template <typename T> static void run_factor(Factor<T> &F) {
   int prev_slot = 0;
   bool have_prev = false;
 
+  // One problem without a rank proposal: the level lists are built on the
+  // device from a device-resident active list (the host gets the cell and
+  // pool counts and six ints per box); otherwise on the host (build_level).
+  const bool dev_lv = np == 1 && !F.mlp && F.dev_pts.key.p != nullptr;
+  DBuf d_act, d_act_next, lv_dk, lv_flag, lv_cpos, lv_cnt, lv_key, lv_grid, lv_psz, lv_tot, lv_node, lv_box;
+  DBuf lv_sact, lv_k1, lv_v1, lv_hist;  // stable sorts of unsorted lists
+  int64_t dev_na = 0;
+  bool act_unsorted = false;  // the active list came out of a level in cell order, not ascending
+  if (dev_lv) {
+    dev_na = n;
+    d_act.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1), st);
+    iota64(ptr<int64_t>(d_act), n, st);
+    check_launch("active list");
+  }
+  auto build_level_dev = [&](const HTree &Tt, int t, DLevel<T> &D) {
+    const int cbase = (F.flags & RSS_FLAG_COLOUR_2D) ? 2 : 3;  // colours per level, as below
+    HLevel L;
+    L.t = t;
+    L.dim = dim;
+    L.NB = dim == 2 ? 25 : 125;
+    L.on_device = true;
+    L.ndof = dev_na;
+    const int64_t na = dev_na;
+    grow(lv_dk, sizeof(uint64_t) * (size_t)na, st, 1);
+    grow(lv_flag, sizeof(uint32_t) * (size_t)na, st, 1);
+    grow(lv_cpos, sizeof(uint32_t) * (size_t)na, st, 1);
+    grow(lv_cnt, 64, st, 1);
+    auto sort_scratch = [&] {
+      grow(lv_sact, sizeof(int64_t) * (size_t)na, st, 1);
+      grow(lv_k1, sizeof(uint64_t) * (size_t)na, st, 1);
+      grow(lv_v1, sizeof(int64_t) * (size_t)na, st, 1);
+      grow(lv_hist, (size_t)sort_pairs_hist_bytes(na), st, 1);
+    };
+    if (act_unsorted) {  // the previous level left its survivors in cell order: ascending again
+      sort_scratch();
+      CK(cudaMemcpyAsync(lv_sact.p, d_act.p, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToDevice, st));
+      int bits = 1;
+      while (bits < 62 && ((int64_t)1 << bits) < n) bits++;
+      sort_pairs_u64(ptr<uint64_t>(lv_sact), ptr<int64_t>(d_act), ptr<uint64_t>(lv_k1), ptr<int64_t>(lv_v1),
+                     ptr<uint32_t>(lv_hist), na, bits, st);
+      act_unsorted = false;
+    }
+    CK(cudaMemsetAsync(lv_cnt.p, 0, 64, st));
+    uint32_t *cnt = ptr<uint32_t>(lv_cnt);  // [0] cells, [1] unsorted
+    level_gpu_keys(ptr<uint64_t>(F.dev_pts.key), ptr<int64_t>(d_act), na, dim * (20 - t), ptr<uint64_t>(lv_dk),
+                   cnt + 1, st);
+    level_gpu_runs(ptr<uint64_t>(lv_dk), na, ptr<uint32_t>(lv_flag), ptr<uint32_t>(lv_cpos), cnt, st);
+    check_launch("level cells");
+    uint32_t hc[2] = {0, 0};
+    CK(cudaMemcpyAsync(hc, lv_cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int64_t *act_lv = ptr<int64_t>(d_act);
+    if (hc[1]) {
+      // DOFs of leaves shallower than t are in their original order: a
+      // stable sort of (key, DOF) groups them by cell, as the host build
+      // does; the next level's list is made ascending again
+      sort_scratch();
+      CK(cudaMemcpyAsync(lv_sact.p, d_act.p, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToDevice, st));
+      sort_pairs_u64(ptr<uint64_t>(lv_dk), ptr<int64_t>(lv_sact), ptr<uint64_t>(lv_k1), ptr<int64_t>(lv_v1),
+                     ptr<uint32_t>(lv_hist), na, dim * t, st);
+      level_gpu_runs(ptr<uint64_t>(lv_dk), na, ptr<uint32_t>(lv_flag), ptr<uint32_t>(lv_cpos), cnt, st);
+      check_launch("level sort");
+      CK(cudaMemcpyAsync(hc, lv_cnt.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      act_lv = ptr<int64_t>(lv_sact);
+      act_unsorted = true;
+    }
+    L.ncell = (int)hc[0];
+    const int ncell = L.ncell;
+    const int64_t len = (int64_t)ncell * L.NB;
+    D.cell_dof_off.alloc(sizeof(int64_t) * (size_t)(ncell + 1), st);
+    D.cell_dofs.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(na, 1), st);
+    D.cell_b.alloc(sizeof(int) * (size_t)std::max(ncell, 1), st);
+    D.cell_coord.alloc(sizeof(int) * 3 * (size_t)std::max(ncell, 1), st);
+    D.cell_nbr.alloc(sizeof(int) * (size_t)std::max<int64_t>(len, 1), st);
+    D.pair_off.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(len, 1), st);
+    grow(lv_key, sizeof(uint64_t) * (size_t)std::max(ncell, 1), st, 1);
+    grow(lv_psz, sizeof(unsigned long long) * (size_t)std::max<int64_t>(len, 1), st, 1);
+    grow(lv_tot, 64, st, 1);
+    CK(cudaMemsetAsync(lv_tot.p, 0, 64, st));  // pool total, bmax
+    const int64_t side = (int64_t)1 << t;
+    int64_t grid_cells = 1;
+    for (int d = 0; d < dim; d++) grid_cells *= side;
+    const bool use_grid = grid_cells <= ((int64_t)1 << 24);
+    if (use_grid) {
+      grow(lv_grid, sizeof(int) * (size_t)grid_cells, st, 1);
+      CK(cudaMemsetAsync(lv_grid.p, 0xFF, sizeof(int) * (size_t)grid_cells, st));
+    }
+    // the tree's nodes of depth t, in the host order of build_level
+    const std::vector<int> &nodes = Tt.level[t];
+    const int nbox = (int)nodes.size();
+    std::vector<int> ncoord((size_t)3 * std::max(nbox, 1), 0);
+    for (int i = 0; i < nbox; i++)
+      for (int d = 0; d < 3; d++) ncoord[3 * (size_t)i + d] = Tt.coord[3 * (size_t)nodes[i] + d];
+    upload(lv_node, ncoord, st);
+    grow(lv_box, sizeof(int) * 6 * (size_t)std::max(nbox, 1), st, 1);
+    LevelGpu G;
+    G.act = act_lv;
+    G.na = na;
+    G.dim = dim;
+    G.NB = L.NB;
+    G.side = (int)side;
+    G.ncell = ncell;
+    G.nbox = nbox;
+    G.dk = ptr<uint64_t>(lv_dk);
+    G.flag = ptr<uint32_t>(lv_flag);
+    G.cpos = ptr<uint32_t>(lv_cpos);
+    G.node_coord = ptr<int>(lv_node);
+    G.grid = use_grid ? ptr<int>(lv_grid) : nullptr;
+    G.cell_dof_off = ptr<int64_t>(D.cell_dof_off);
+    G.cell_dofs = ptr<int64_t>(D.cell_dofs);
+    G.pair_off = ptr<int64_t>(D.pair_off);
+    G.cell_b = ptr<int>(D.cell_b);
+    G.cell_coord = ptr<int>(D.cell_coord);
+    G.cell_nbr = ptr<int>(D.cell_nbr);
+    G.cell_key = ptr<uint64_t>(lv_key);
+    G.psz = ptr<unsigned long long>(lv_psz);
+    G.pool_total = ptr<unsigned long long>(lv_tot);
+    G.bmax = reinterpret_cast<int *>(ptr<unsigned long long>(lv_tot) + 1);
+    G.box_out = ptr<int>(lv_box);
+    level_gpu_tables(G, st);
+    check_launch("level tables");
+    unsigned long long tot[2] = {0, 0};
+    std::vector<int> bo((size_t)6 * std::max(nbox, 1));
+    CK(cudaMemcpyAsync(tot, lv_tot.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    if (nbox > 0) CK(cudaMemcpyAsync(bo.data(), lv_box.p, sizeof(int) * 6 * (size_t)nbox, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    L.pool_elems = (int64_t)tot[0];
+    L.bmax = (int)(tot[1] & 0xffffffffu);
+    for (int i = 0; i < nbox; i++) {
+      const int *o = &bo[6 * (size_t)i];
+      if (o[0] < 0) continue;  // every DOF of the box has become inactive
+      L.box_cell.push_back(o[0]);
+      L.box_node.push_back(nodes[i]);
+      L.box_colour.push_back(colour_of(&Tt.coord[3 * (size_t)nodes[i]], dim, cbase));
+      L.box_b.push_back(o[1]);
+      L.box_nj.push_back(o[2]);
+      L.box_ring.push_back(o[3]);
+      L.box_nnc.push_back(o[4]);
+      L.box_nrc.push_back(o[5]);
+    }
+    if (cbase != 3) {  // as build_level: colour-major, node (Morton) order within a colour
+      const int nb = (int)L.box_cell.size();
+      std::vector<int> byn(nb), ord(nb);
+      for (int q = 0; q < nb; q++) byn[q] = q;
+      std::sort(byn.begin(), byn.end(), [&](int a, int b) { return L.box_node[a] < L.box_node[b]; });
+      int ncol = 1;
+      for (int d = 0; d < dim; d++) ncol *= cbase;
+      std::vector<int> cstart(ncol + 1, 0);
+      for (int q = 0; q < nb; q++) cstart[L.box_colour[q] + 1]++;
+      for (int c = 0; c < ncol; c++) cstart[c + 1] += cstart[c];
+      for (int q : byn) ord[cstart[L.box_colour[q]]++] = q;
+      auto perm = [&](std::vector<int> &v) {
+        std::vector<int> w(nb);
+        for (int q = 0; q < nb; q++) w[q] = v[ord[q]];
+        v.swap(w);
+      };
+      perm(L.box_cell), perm(L.box_node), perm(L.box_colour), perm(L.box_b), perm(L.box_nj), perm(L.box_ring);
+      perm(L.box_nnc), perm(L.box_nrc);
+    }
+    return L;
+  };
+
   auto assemble_pairs = [&](const HLevel &H, DLevel<T> &D, const LevelDev<T> *prev) {
     // one block per (cell, neighbour code at distance <= 2), enumerated on
     // the device from the level's tables; codes with no neighbour are empty
-    int64_t maxblk = 0;
-    for (int c = 0; c < H.ncell; c++) maxblk = std::max(maxblk, (int64_t)H.cell_b[c]);
-    maxblk *= maxblk;
+    const int64_t maxblk = (int64_t)H.bmax * H.bmax;
     AssembleList L{};
     L.nblock = H.ncell * H.NB;
     L.row_ids = L.col_ids = ptr<int64_t>(D.cell_dofs);
@@ -1428,7 +1595,13 @@ template <typename T> static void run_factor(Factor<T> &F) {
     H.NB = dim == 2 ? 25 : 125;
     std::vector<int> box_prob;
     std::vector<int> cell_base(np + 1, 0);
-    if (np == 1) {
+    std::unique_ptr<DLevel<T>> D(new DLevel<T>());
+    if (dev_lv) {
+      if (F.trees[0].maxdepth >= t && dev_na > 0) {
+        H = build_level_dev(F.trees[0], t, *D);
+        box_prob.assign(H.box_cell.size(), 0);
+      }
+    } else if (np == 1) {
       if (F.trees[0].maxdepth >= t && !active[0].empty()) {
         H = build_level(F.trees[0], t, active[0], cbase);
         box_prob.assign(H.box_cell.size(), 0);
@@ -1459,6 +1632,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     if (np == 1) cell_base[0] = 0;
     cell_base[np] = H.ncell;
     if (H.cell_dof_off.empty()) H.cell_dof_off.push_back(0);
+    if (!H.on_device) H.ndof = (int64_t)H.cell_dofs.size();
     if (H.box_cell.empty()) continue;  // no problem has boxes at this depth
     // colour-major order over all problems (stable: problem order within a colour)
     {
@@ -1466,31 +1640,29 @@ template <typename T> static void run_factor(Factor<T> &F) {
       std::vector<int> ordr(nb0);
       for (int q = 0; q < nb0; q++) ordr[q] = q;
       std::stable_sort(ordr.begin(), ordr.end(), [&](int a, int b) { return H.box_colour[a] < H.box_colour[b]; });
-      std::vector<int> bc(nb0), bn(nb0), bcol(nb0), bp(nb0);
-      for (int q = 0; q < nb0; q++) {
-        bc[q] = H.box_cell[ordr[q]];
-        bn[q] = H.box_node[ordr[q]];
-        bcol[q] = H.box_colour[ordr[q]];
-        bp[q] = box_prob[ordr[q]];
-      }
-      H.box_cell.swap(bc);
-      H.box_node.swap(bn);
-      H.box_colour.swap(bcol);
-      box_prob.swap(bp);
+      auto perm = [&](std::vector<int> &v) {
+        if (v.empty()) return;
+        std::vector<int> w(nb0);
+        for (int q = 0; q < nb0; q++) w[q] = v[ordr[q]];
+        v.swap(w);
+      };
+      perm(H.box_cell), perm(H.box_node), perm(H.box_colour), perm(box_prob);
+      perm(H.box_b), perm(H.box_nj), perm(H.box_ring), perm(H.box_nnc), perm(H.box_nrc);
     }
-    std::unique_ptr<DLevel<T>> D(new DLevel<T>());
-    upload(D->cell_b, H.cell_b, st);
-    upload(D->cell_dof_off, H.cell_dof_off, st);
-    upload(D->cell_dofs, H.cell_dofs, st);
-    upload(D->cell_coord, H.cell_coord, st);
-    upload(D->cell_nbr, H.cell_nbr, st);
-    upload(D->pair_off, H.pair_off, st);
+    if (!H.on_device) {
+      upload(D->cell_b, H.cell_b, st);
+      upload(D->cell_dof_off, H.cell_dof_off, st);
+      upload(D->cell_dofs, H.cell_dofs, st);
+      upload(D->cell_coord, H.cell_coord, st);
+      upload(D->cell_nbr, H.cell_nbr, st);
+      upload(D->pair_off, H.pair_off, st);
+    }
     D->pool.alloc((size_t)H.pool_elems * sizeof(T), st, 1);
     // active lists (every level-start DOF active, local order) and the
     // per-DOF maps of this level (-1 for DOFs in no cell), built on the device
     int slot = have_prev ? 1 - prev_slot : 0;
     {
-      const size_t nd = std::max<size_t>(H.cell_dofs.size(), 1), nn = (size_t)std::max<int64_t>(n, 1);
+      const size_t nd = (size_t)std::max<int64_t>(H.ndof, 1), nn = (size_t)std::max<int64_t>(n, 1);
       D->act_cnt.alloc(sizeof(int) * std::max(H.ncell, 1), st);
       D->act_idx.alloc(sizeof(int) * nd, st);
       if (H.ncell > 0)
@@ -1521,30 +1693,42 @@ template <typename T> static void run_factor(Factor<T> &F) {
     const int base = (int)F.h_boxes.size();
     const int nb = (int)H.box_cell.size();
     int njmax_lvl = 0, ring_max = 0;
-    std::vector<int> njmaxv(nb), ringv(nb);
+    std::vector<int> njmaxv(nb), ringv(nb), bbox(nb);
     std::vector<float> fx((size_t)nb * MLP_NFEAT, 0.f);
     parallel_range(nb, 1024, [&](int64_t q0, int64_t q1) {
     for (int64_t q = q0; q < q1; q++) {
-      int c = H.box_cell[q], b = H.cell_b[c];
-      int nj = b, nnear_cells = 0;
-      int lim = dim == 3 ? 1 : 0;
-      for (int dz = -lim; dz <= lim; dz++)
-        for (int dy = -1; dy <= 1; dy++)
-          for (int dx = -1; dx <= 1; dx++) {
-            if (!dx && !dy && !dz) continue;
-            int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
-            if (nbc >= 0) nj += H.cell_b[nbc], nnear_cells++;
-          }
+      int b, nj, ring, nnear_cells, nring_cells;
+      if (H.on_device) {  // the device level build's per-box counts
+        b = H.box_b[q];
+        nj = H.box_nj[q];
+        ring = H.box_ring[q];
+        nnear_cells = H.box_nnc[q];
+        nring_cells = H.box_nrc[q];
+      } else {
+        const int c = H.box_cell[q];
+        b = H.cell_b[c];
+        nj = b, nnear_cells = 0;
+        int lim = dim == 3 ? 1 : 0;
+        for (int dz = -lim; dz <= lim; dz++)
+          for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+              if (!dx && !dy && !dz) continue;
+              int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
+              if (nbc >= 0) nj += H.cell_b[nbc], nnear_cells++;
+            }
+        // DOFs of the ring inside the proxy surface, bounded by level-start counts
+        ring = 0, nring_cells = 0;
+        int lim2 = dim == 3 ? 2 : 0;
+        for (int dz = -lim2; dz <= lim2; dz++)
+          for (int dy = -2; dy <= 2; dy++)
+            for (int dx = -2; dx <= 2; dx++) {
+              if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) != 2) continue;
+              int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
+              if (nbc >= 0) ring += H.cell_b[nbc], nring_cells++;
+            }
+      }
+      bbox[q] = b;
       njmaxv[q] = weak ? b : nj;  // a weak step eliminates against J = S
-      // DOFs of the ring inside the proxy surface, bounded by level-start counts
-      int ring = 0, nring_cells = 0, lim2 = dim == 3 ? 2 : 0;
-      for (int dz = -lim2; dz <= lim2; dz++)
-        for (int dy = -2; dy <= 2; dy++)
-          for (int dx = -2; dx <= 2; dx++) {
-            if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) != 2) continue;
-            int nbc = H.cell_nbr[(size_t)c * H.NB + code5(dx, dy, dz, dim)];
-            if (nbc >= 0) ring += H.cell_b[nbc], nring_cells++;
-          }
       // rows of the ID matrix from inside the proxy surface: the ring, and
       // for a weak step the near cells too
       ringv[q] = weak ? ring + (nj - b) : ring;
@@ -1564,7 +1748,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     // reservations: full size (r = b, |J| = level-start count), or from the
     // proposed ranks plus margins
     std::vector<int> rres(nb), njres(njmaxv);
-    for (int q = 0; q < nb; q++) rres[q] = H.cell_b[H.box_cell[q]];
+    for (int q = 0; q < nb; q++) rres[q] = bbox[q];
     if (F.mlp) {
       double tp0 = now_ms();
       DBuf d_fx, d_pr;
@@ -1604,7 +1788,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     }
     size_t sz_i64 = 0, sz_i32 = 0, sz_T = 0;
     for (int q = 0; q < nb; q++) {
-      const size_t b = H.cell_b[H.box_cell[q]], nj = njmaxv[q], rr = rres[q], njr = njres[q];
+      const size_t b = bbox[q], nj = njmaxv[q], rr = rres[q], njr = njres[q];
       sz_i64 += b + nj;
       sz_i32 += b + 2 * nj + b;
       sz_T += b * b / 4 + 1 + 2 * rr * rr + (symm ? 1 : 2) * njr * rr;
@@ -1614,7 +1798,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
     T *pT = (T *)F.alloc_store(sz_T * sizeof(T));
     F.reserved_T += (int64_t)sz_T;
     for (int q = 0; q < nb; q++) {
-      int c = H.box_cell[q], b = H.cell_b[c], nj = njmaxv[q], rr = rres[q], njr = njres[q];
+      int c = H.box_cell[q], b = bbox[q], nj = njmaxv[q], rr = rres[q], njr = njres[q];
       FBox<T> fb{};
       fb.cell = c;
       fb.depth = t;
@@ -1741,10 +1925,21 @@ template <typename T> static void run_factor(Factor<T> &F) {
     // ranks of this level -> active DOFs of the next
     CK(cudaMemcpyAsync(F.h_boxes.data() + base, ptr<FBox<T>>(F.d_boxes) + base, sizeof(FBox<T>) * nb,
                        cudaMemcpyDeviceToHost, st));
-    std::vector<int> ac(H.ncell), ai(H.cell_dofs.size());
-    CK(cudaMemcpyAsync(ac.data(), D->act_cnt.p, sizeof(int) * H.ncell, cudaMemcpyDeviceToHost, st));
-    if (!ai.empty())
-      CK(cudaMemcpyAsync(ai.data(), D->act_idx.p, sizeof(int) * ai.size(), cudaMemcpyDeviceToHost, st));
+    std::vector<int> ac(H.on_device ? 0 : H.ncell), ai(H.on_device ? 0 : H.cell_dofs.size());
+    uint32_t next_na = 0;
+    if (H.on_device) {  // the next level's active list, compacted on the device
+      d_act_next.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(dev_na, 1), st);
+      grow(lv_cpos, sizeof(uint32_t) * (size_t)std::max(H.ncell, 1), st, 1);
+      level_gpu_next_active(H.ncell, ptr<int64_t>(D->cell_dof_off), ptr<int64_t>(D->cell_dofs), ptr<int>(D->act_cnt),
+                            ptr<int>(D->act_idx), ptr<uint32_t>(lv_cpos), ptr<uint32_t>(lv_cnt),
+                            ptr<int64_t>(d_act_next), st);
+      check_launch("next active list");
+      CK(cudaMemcpyAsync(&next_na, lv_cnt.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    } else {
+      CK(cudaMemcpyAsync(ac.data(), D->act_cnt.p, sizeof(int) * H.ncell, cudaMemcpyDeviceToHost, st));
+      if (!ai.empty())
+        CK(cudaMemcpyAsync(ai.data(), D->act_idx.p, sizeof(int) * ai.size(), cudaMemcpyDeviceToHost, st));
+    }
     unsigned long long ovf_used = 0;
     if (F.mlp) CK(cudaMemcpyAsync(&ovf_used, F.d_ovf_used.p, sizeof(ovf_used), cudaMemcpyDeviceToHost, st));
     double tw0 = now_ms();
@@ -1765,6 +1960,12 @@ template <typename T> static void run_factor(Factor<T> &F) {
       if (par >= 0) child_b[((int64_t)box_prob[q] << 32) | (uint32_t)par] += fb.b;
     }
     double ta0 = now_ms();
+    if (H.on_device) {
+      dev_na = (int64_t)next_na;
+      std::swap(d_act.p, d_act_next.p);
+      std::swap(d_act.bytes, d_act_next.bytes);
+      std::swap(d_act.st, d_act_next.st);
+    } else {
     // each cell's active DOFs at its offset in the problem's list (an
     // exclusive scan of the counts), filled in parallel over cells
     std::vector<int64_t> aoff(H.ncell + 1, 0);
@@ -1786,6 +1987,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       std::vector<int64_t> &act = active[p];
       if (!std::is_sorted(act.begin(), act.end())) std::sort(act.begin(), act.end());
     });
+    }
     F.prof.host(KC_HOST_LEVEL, now_ms() - ta0);
     prevD = std::move(D);
     prevH = std::move(H);
@@ -1821,6 +2023,13 @@ template <typename T> static void run_factor(Factor<T> &F) {
   }
 
   // top blocks: every problem's DOFs still active (Sec. 3.3.3), dense LU
+  if (dev_lv) {  // the active list after the last level, for the top block
+    active[0].resize(dev_na);
+    if (dev_na > 0)
+      CK(cudaMemcpyAsync(active[0].data(), d_act.p, sizeof(int64_t) * dev_na, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (act_unsorted) std::sort(active[0].begin(), active[0].end());
+  }
   std::vector<int64_t> top;
   F.h_tn.assign(np, 0);
   F.h_toff.assign(np + 1, 0);

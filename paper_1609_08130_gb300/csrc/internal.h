@@ -235,6 +235,45 @@ void points_setup(const double *x, const int *c20, int64_t n, int dim, double D,
 void grid_detect(const double *x, const int64_t *perm, int64_t n, int dim, int64_t s, int64_t *gidx, unsigned *seen,
                  int *bad, cudaStream_t st);
 
+// A level's lists for one problem on the GPU (tree.cu).  level_gpu_keys:
+// the depth-t keys of the active DOFs (act, na of them, ascending tree
+// order; ksh = dim (20 - t)), *unsorted set when they are not in key order
+// (the caller then sorts keys and DOFs stably); level_gpu_runs: run starts
+// of the key-ordered list, their exclusive scan and the cell count at
+// *ncell.  level_gpu_tables (ncell known): the cells' DOF lists,
+// sizes, keys and coordinates, the neighbour table and pair-block offsets
+// (5^dim codes per cell; the pool size at *pool_total, the largest cell at
+// *bmax), and per tree node of depth t (node_coord, 3 ints each) six ints:
+// cell (-1: no active DOF), b, DOFs of the cell and its near cells, DOFs of
+// its ring cells, near and ring cells present.  level_gpu_next_active: the active DOFs after the
+// level's eliminations (act_cnt / act_idx per cell), their number at *total.
+struct LevelGpu {
+  const int64_t *act = nullptr;
+  int64_t na = 0;
+  int dim = 2, NB = 25, side = 1, ncell = 0, nbox = 0;
+  const uint64_t *dk = nullptr;
+  const uint32_t *flag = nullptr, *cpos = nullptr;
+  const int *node_coord = nullptr;
+  int *grid = nullptr;  // side^dim cells, or nullptr for binary search
+  int64_t *cell_dof_off = nullptr, *cell_dofs = nullptr, *pair_off = nullptr;
+  int *cell_b = nullptr, *cell_coord = nullptr, *cell_nbr = nullptr, *bmax = nullptr, *box_out = nullptr;
+  uint64_t *cell_key = nullptr;
+  unsigned long long *psz = nullptr, *pool_total = nullptr;
+};
+void level_gpu_keys(const uint64_t *key, const int64_t *act, int64_t na, int ksh, uint64_t *dk, uint32_t *unsorted,
+                    cudaStream_t st);
+void level_gpu_runs(const uint64_t *dk, int64_t na, uint32_t *flag, uint32_t *cpos, uint32_t *ncell, cudaStream_t st);
+// Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of
+// the keys, 8 bits a pass; the result is in (k0, v0); k1, v1 and hist
+// (sort_pairs_hist_bytes(n)) are scratch.
+int64_t sort_pairs_hist_bytes(int64_t n);
+void sort_pairs_u64(uint64_t *k0, int64_t *v0, uint64_t *k1, int64_t *v1, uint32_t *hist, int64_t n, int bits,
+                    cudaStream_t st);
+void level_gpu_tables(const LevelGpu &L, cudaStream_t st);
+void level_gpu_next_active(int ncell, const int64_t *cell_dof_off, const int64_t *cell_dofs, const int *act_cnt,
+                           const int *act_idx, uint32_t *aoff, uint32_t *total, int64_t *next, cudaStream_t st);
+void iota64(int64_t *p, int64_t n, cudaStream_t st);  // p[i] = i
+
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n = 1);
 long long launches_total();

@@ -107,42 +107,43 @@ __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *__restrict__ k
 // consecutive counts at a time (8 per thread, loaded together; warp scans
 // of the threads' sums, then the warps' totals), with a running carry.
 // total (may be NULL) receives the sum.
-__global__ void __launch_bounds__(1024) k_scan_excl(uint32_t *a, int64_t len, uint32_t *total) {
+template <typename U>
+__global__ void __launch_bounds__(1024) k_scan_excl(U *a, int64_t len, U *total) {
   constexpr int IT = 8;
-  __shared__ uint32_t wsum[32];
-  __shared__ uint32_t s_carry;
+  __shared__ U wsum[32];
+  __shared__ U s_carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (int64_t b0 = 0; b0 < len; b0 += 1024 * IT) {
     const int64_t i0 = b0 + (int64_t)tid * IT;
-    uint32_t v[IT], sum = 0;
+    U v[IT], sum = 0;
 #pragma unroll
     for (int u = 0; u < IT; u++) {
-      v[u] = i0 + u < len ? a[i0 + u] : 0u;
+      v[u] = i0 + u < len ? a[i0 + u] : (U)0;
       sum += v[u];
     }
-    uint32_t x = sum;
+    U x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const U y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
     if (warp == 0) {
-      uint32_t w = wsum[lane];
+      U w = wsum[lane];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        const U y = __shfl_up_sync(0xffffffffu, w, o);
         if (lane >= o) w += y;
       }
       wsum[lane] = w;  // inclusive over warps
     }
     __syncthreads();
-    const uint32_t carry = s_carry;
-    const uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u);
-    uint32_t run = carry + incl - sum;
+    const U carry = s_carry;
+    const U incl = x + (warp > 0 ? wsum[warp - 1] : (U)0);
+    U run = carry + incl - sum;
 #pragma unroll
     for (int u = 0; u < IT; u++) {
       if (i0 + u < len) a[i0 + u] = run;
@@ -316,6 +317,181 @@ __global__ void k_tree_sorted_cells(const int *__restrict__ c20, const int64_t *
 
 inline unsigned nb256(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+
+// ---------------------------------------------------------------------------
+// Level lists of one problem on the GPU.  The active DOFs of a level (tree
+// order, ascending) fall into the depth-t cells of their Morton keys (the
+// depth-20 key shifted right by dim (20 - t) bits); the list is sorted by
+// key, so a cell is a run of the list.  Its neighbours at Chebyshev
+// distance <= 2 (codes 0 .. 5^dim - 1) come from a dense lookup grid of the
+// level (side^dim cells), or by binary search in the sorted cell keys when
+// that grid would be too large; the pair blocks (cell, neighbour) are laid
+// out cell by cell in code order, each b_cell x b_neighbour.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t compact2(uint64_t x) {
+  x &= 0x5555555555555555ULL;
+  x = (x | (x >> 1)) & 0x3333333333333333ULL;
+  x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0fULL;
+  x = (x | (x >> 4)) & 0x00ff00ff00ff00ffULL;
+  x = (x | (x >> 8)) & 0x0000ffff0000ffffULL;
+  x = (x | (x >> 16)) & 0x00000000ffffffffULL;
+  return (uint32_t)x;
+}
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ULL;
+  x = (x | (x >> 2)) & 0x10c30c30c30c30c3ULL;
+  x = (x | (x >> 4)) & 0x100f00f00f00f00fULL;
+  x = (x | (x >> 8)) & 0x001f0000ff0000ffULL;
+  x = (x | (x >> 16)) & 0x001f00000000ffffULL;
+  x = (x | (x >> 32)) & 0x00000000001fffffULL;
+  return (uint32_t)x;
+}
+
+// depth-t keys of the active DOFs; *unsorted != 0 when the list is not in
+// key order (DOFs of a leaf shallower than t keep their original order)
+__global__ void k_lv_keys(const uint64_t *__restrict__ key, const int64_t *__restrict__ act, int64_t na, int ksh,
+                          uint64_t *__restrict__ dk, uint32_t *unsorted) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= na) return;
+  const uint64_t k = key[act[q]] >> ksh;
+  dk[q] = k;
+  if (q > 0 && (key[act[q - 1]] >> ksh) > k) atomicOr(unsorted, 1u);
+}
+
+// run starts of the key-ordered list
+__global__ void k_lv_runs(const uint64_t *__restrict__ dk, int64_t na, uint32_t *__restrict__ flag) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= na) return;
+  flag[q] = (q == 0 || dk[q - 1] != dk[q]) ? 1u : 0u;
+}
+
+// cpos: exclusive scan of the run starts (the cell of each DOF at a start)
+__global__ void k_lv_cells(const int64_t *__restrict__ act, int64_t na, int dim, const uint64_t *__restrict__ dk,
+                           const uint32_t *__restrict__ flag, const uint32_t *__restrict__ cpos,
+                           int64_t *__restrict__ cell_dof_off, int64_t *__restrict__ cell_dofs,
+                           uint64_t *__restrict__ cell_key, int *__restrict__ cell_coord) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= na) return;
+  cell_dofs[q] = act[q];
+  if (q == na - 1) cell_dof_off[cpos[q] + flag[q]] = na;
+  if (!flag[q]) return;
+  const uint32_t c = cpos[q];
+  const uint64_t k = dk[q];
+  cell_dof_off[c] = q;
+  cell_key[c] = k;
+  if (dim == 2) {
+    cell_coord[3 * c] = (int)compact2(k);
+    cell_coord[3 * c + 1] = (int)compact2(k >> 1);
+    cell_coord[3 * c + 2] = 0;
+  } else {
+    cell_coord[3 * c] = (int)compact3(k);
+    cell_coord[3 * c + 1] = (int)compact3(k >> 1);
+    cell_coord[3 * c + 2] = (int)compact3(k >> 2);
+  }
+}
+
+__global__ void k_lv_sizes(int ncell, const int64_t *__restrict__ cell_dof_off, int *__restrict__ cell_b, int *bmax,
+                           int *__restrict__ grid, int side, int dim, const int *__restrict__ cell_coord) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int b = (int)(cell_dof_off[c + 1] - cell_dof_off[c]);
+  cell_b[c] = b;
+  atomicMax(bmax, b);
+  if (grid) {
+    int64_t lin = 0, mul = 1;
+    for (int d = 0; d < dim; d++) lin += (int64_t)cell_coord[3 * c + d] * mul, mul *= side;
+    grid[lin] = c;
+  }
+}
+
+// cell of integer coordinates p at this level, or -1
+__device__ __forceinline__ int lv_lookup(const int64_t *p, int dim, int side, const int *grid,
+                                         const uint64_t *cell_key, int ncell) {
+  for (int d = 0; d < dim; d++)
+    if (p[d] < 0 || p[d] >= side) return -1;
+  if (grid) {
+    int64_t lin = 0, mul = 1;
+    for (int d = 0; d < dim; d++) lin += p[d] * mul, mul *= side;
+    return grid[lin];
+  }
+  const uint64_t k = dim == 2 ? (spread2((uint64_t)p[0]) | (spread2((uint64_t)p[1]) << 1))
+                              : (spread3((uint64_t)p[0]) | (spread3((uint64_t)p[1]) << 1) |
+                                 (spread3((uint64_t)p[2]) << 2));
+  int lo = 0, hi = ncell;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cell_key[mid] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < ncell && cell_key[lo] == k ? lo : -1;
+}
+
+// one thread per (cell, code): the neighbour and the size of the pair block
+__global__ void k_lv_nbrs(int ncell, int dim, int NB, int side, const int *__restrict__ grid,
+                          const uint64_t *__restrict__ cell_key, const int *__restrict__ cell_coord,
+                          const int *__restrict__ cell_b, int *__restrict__ cell_nbr,
+                          unsigned long long *__restrict__ psz) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ncell * NB) return;
+  const int c = (int)(e / NB), code = (int)(e % NB);
+  const int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+  const int64_t p[3] = {cell_coord[3 * c] + dx, cell_coord[3 * c + 1] + dy, cell_coord[3 * c + 2] + dz};
+  const int nb = lv_lookup(p, dim, side, grid, cell_key, ncell);
+  cell_nbr[e] = nb;
+  psz[e] = nb >= 0 ? (unsigned long long)cell_b[c] * (unsigned long long)cell_b[nb] : 0ull;
+}
+
+__global__ void k_lv_pairoff(int64_t len, const int *__restrict__ cell_nbr, const unsigned long long *__restrict__ excl,
+                             int64_t *__restrict__ pair_off) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  pair_off[e] = cell_nbr[e] >= 0 ? (int64_t)excl[e] : -1;
+}
+
+// one thread per tree node of depth t: its cell (-1 if none of its DOFs is
+// active) and the sizes the factor's records need: b, the DOFs of the cell
+// and its near cells, those of its ring cells (distance 2) and the numbers
+// of near and ring cells present
+__global__ void k_lv_boxes(int nbox, const int *__restrict__ node_coord, int dim, int side, int NB,
+                           const int *__restrict__ grid, const uint64_t *__restrict__ cell_key, int ncell,
+                           const int *__restrict__ cell_b, const int *__restrict__ cell_nbr,
+                           int *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbox) return;
+  const int64_t p[3] = {node_coord[3 * i], node_coord[3 * i + 1], node_coord[3 * i + 2]};
+  const int c = lv_lookup(p, dim, side, grid, cell_key, ncell);
+  int *o = out + 6 * (int64_t)i;
+  o[0] = c;
+  if (c < 0) return;
+  const int b = cell_b[c];
+  int nj = b, nnc = 0, ring = 0, nrc = 0;
+  for (int code = 0; code < NB; code++) {
+    const int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = dim == 3 ? code / 25 - 2 : 0;
+    const int dist = max(abs(dx), max(abs(dy), abs(dz)));
+    const int nb = cell_nbr[(int64_t)c * NB + code];
+    if (nb < 0 || dist == 0) continue;
+    if (dist == 1) nj += cell_b[nb], nnc++;
+    else ring += cell_b[nb], nrc++;
+  }
+  o[1] = b;
+  o[2] = nj;
+  o[3] = ring;
+  o[4] = nnc;
+  o[5] = nrc;
+}
+
+// the next level's active DOFs: each cell's survivors (local indices in
+// act_idx, ascending) at the exclusive scan of the counts
+__global__ void k_lv_compact(int ncell, const int64_t *__restrict__ cell_dof_off, const int64_t *__restrict__ cell_dofs,
+                             const int *__restrict__ act_cnt, const int *__restrict__ act_idx,
+                             const uint32_t *__restrict__ aoff, int64_t *__restrict__ next) {
+  const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const int64_t o = cell_dof_off[c];
+  for (int q = lane; q < act_cnt[c]; q += 32) next[aoff[c] + q] = cell_dofs[o + act_idx[o + q]];
+}
+
 }  // namespace
 
 int64_t tree_gpu_scratch_bytes(int64_t n, int dim) {
@@ -351,14 +527,14 @@ void tree_gpu_sort(TreeGpu &T, void *scratch, cudaStream_t st) {
   const int bits = dim * MAXD + T.prob_bits;
   for (int sh = 0; sh < bits; sh += 8) {
     k_rs_hist<<<(unsigned)T.nblk, RS_T, 0, st>>>(T.k0, n, sh, T.hist, (int)T.nblk); count_launch();
-    k_scan_excl<<<1, 1024, 0, st>>>(T.hist, 256 * T.nblk, nullptr); count_launch();
+    k_scan_excl<uint32_t><<<1, 1024, 0, st>>>(T.hist, 256 * T.nblk, nullptr); count_launch();
     k_rs_scatter<<<(unsigned)T.nblk, RS_T, 0, st>>>(T.k0, T.i0, T.k1, T.i1, n, sh, T.hist, (int)T.nblk);
     count_launch();
     std::swap(T.k0, T.k1);
     std::swap(T.i0, T.i1);
   }
   k_tree_depths<<<nb256(n), 256, 0, st>>>(T.k0, n, dim, T.leaf, T.Lp, T.nd); count_launch();
-  k_scan_excl<<<1, 1024, 0, st>>>(T.nd, n, T.total); count_launch();
+  k_scan_excl<uint32_t><<<1, 1024, 0, st>>>(T.nd, n, T.total); count_launch();
 }
 
 void tree_gpu_nodes(const TreeGpu &T, int *depth, int *parent, int *coord, int64_t *start, int64_t *count,
@@ -423,6 +599,81 @@ void grid_detect(const double *x, const int64_t *perm, int64_t n, int dim, int64
                  int *bad, cudaStream_t st) {
   if (n == 0) return;
   k_grid_detect<<<nb256(n), 256, 0, st>>>(x, perm, n, dim, s, gidx, seen, bad); count_launch();
+}
+
+
+void level_gpu_keys(const uint64_t *key, const int64_t *act, int64_t na, int ksh, uint64_t *dk, uint32_t *unsorted,
+                    cudaStream_t st) {
+  if (na == 0) return;
+  k_lv_keys<<<nb256(na), 256, 0, st>>>(key, act, na, ksh, dk, unsorted); count_launch();
+}
+
+void level_gpu_runs(const uint64_t *dk, int64_t na, uint32_t *flag, uint32_t *cpos, uint32_t *ncell, cudaStream_t st) {
+  if (na == 0) return;
+  k_lv_runs<<<nb256(na), 256, 0, st>>>(dk, na, flag); count_launch();
+  cudaMemcpyAsync(cpos, flag, sizeof(uint32_t) * (size_t)na, cudaMemcpyDeviceToDevice, st);
+  k_scan_excl<uint32_t><<<1, 1024, 0, st>>>(cpos, na, ncell); count_launch();
+}
+
+int64_t sort_pairs_hist_bytes(int64_t n) { return 4 * 256 * ((n + RS_TILE - 1) / RS_TILE) + 16; }
+
+void sort_pairs_u64(uint64_t *k0, int64_t *v0, uint64_t *k1, int64_t *v1, uint32_t *hist, int64_t n, int bits,
+                    cudaStream_t st) {
+  if (n <= 1) return;
+  const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+  uint64_t *ka = k0, *kb = k1;
+  int64_t *va = v0, *vb = v1;
+  for (int sh = 0; sh < bits; sh += 8) {
+    k_rs_hist<<<(unsigned)nblk, RS_T, 0, st>>>(ka, n, sh, hist, nblk); count_launch();
+    k_scan_excl<uint32_t><<<1, 1024, 0, st>>>(hist, 256 * (int64_t)nblk, nullptr); count_launch();
+    k_rs_scatter<<<(unsigned)nblk, RS_T, 0, st>>>(ka, va, kb, vb, n, sh, hist, nblk); count_launch();
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != k0) {
+    cudaMemcpyAsync(k0, ka, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(v0, va, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+  }
+}
+
+void level_gpu_tables(const LevelGpu &L, cudaStream_t st) {
+  if (L.na == 0 || L.ncell == 0) return;
+  k_lv_cells<<<nb256(L.na), 256, 0, st>>>(L.act, L.na, L.dim, L.dk, L.flag, L.cpos, L.cell_dof_off, L.cell_dofs,
+                                          L.cell_key, L.cell_coord);
+  count_launch();
+  k_lv_sizes<<<nb256(L.ncell), 256, 0, st>>>(L.ncell, L.cell_dof_off, L.cell_b, L.bmax, L.grid, L.side, L.dim,
+                                             L.cell_coord);
+  count_launch();
+  const int64_t len = (int64_t)L.ncell * L.NB;
+  k_lv_nbrs<<<nb256(len), 256, 0, st>>>(L.ncell, L.dim, L.NB, L.side, L.grid, L.cell_key, L.cell_coord, L.cell_b,
+                                        L.cell_nbr, L.psz);
+  count_launch();
+  k_scan_excl<unsigned long long><<<1, 1024, 0, st>>>(L.psz, len, L.pool_total); count_launch();
+  k_lv_pairoff<<<nb256(len), 256, 0, st>>>(len, L.cell_nbr, L.psz, L.pair_off); count_launch();
+  if (L.nbox > 0) {
+    k_lv_boxes<<<nb256(L.nbox), 256, 0, st>>>(L.nbox, L.node_coord, L.dim, L.side, L.NB, L.grid, L.cell_key, L.ncell,
+                                              L.cell_b, L.cell_nbr, L.box_out);
+    count_launch();
+  }
+}
+
+void level_gpu_next_active(int ncell, const int64_t *cell_dof_off, const int64_t *cell_dofs, const int *act_cnt,
+                           const int *act_idx, uint32_t *aoff, uint32_t *total, int64_t *next, cudaStream_t st) {
+  if (ncell == 0) return;
+  cudaMemcpyAsync(aoff, act_cnt, sizeof(uint32_t) * (size_t)ncell, cudaMemcpyDeviceToDevice, st);
+  k_scan_excl<uint32_t><<<1, 1024, 0, st>>>(aoff, ncell, total); count_launch();
+  k_lv_compact<<<(unsigned)(((int64_t)ncell * 32 + 255) / 256), 256, 0, st>>>(ncell, cell_dof_off, cell_dofs, act_cnt,
+                                                                            act_idx, aoff, next);
+  count_launch();
+}
+
+__global__ void k_iota64(int64_t *p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = i;
+}
+void iota64(int64_t *p, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  k_iota64<<<nb256(n), 256, 0, st>>>(p, n); count_launch();
 }
 
 }  // namespace rss
