@@ -1563,7 +1563,13 @@ __device__ __forceinline__ void warp_col_update(T (&p)[PR], const T (&v)[PR], T 
 // every lane applies it to its columns right of j and row j of R.
 template <typename T, int PR, int NS>
 __device__ __forceinline__ void warp_step(T (&p)[NS][PR], T *R, int ldr, int b, int lane, T *vb, int j) {
-  if (lane == (j & 31)) {
+  if constexpr (NS == 2) {  // the slot is uniform over the warp: no selects
+    if (j < 32) {
+      if (lane == j) publish_reflector<T, PR>(vb, p[0], R[j * ldr + j]);
+    } else if (lane == j - 32) {
+      publish_reflector<T, PR>(vb, p[1], R[j * ldr + j]);
+    }
+  } else if (lane == (j & 31)) {
     // the owner's column j, picked from its slots with static indices (so
     // that the panel stays in registers)
     const int js = j >> 5;
