@@ -305,8 +305,10 @@ def run_reference(args, rank, world):
 # DRAM bytes (read + write) per launch of a kernel class from an ncu capture,
 # valid only for the kernel source it was taken on (sha-256 of kernels.cu).
 NCU_TRAFFIC = {
-    "id": {"bytes_per_launch": 21.26e6,
-           "kernels_sha256": "c540d7ed44205238c4e7886ec0fb09e3be22abda77a08ae98692f96e39219395"},
+    # the ID's DRAM bytes per launch of the 512^2 step: an ncu capture of
+    # every ID launch of the 256^2 step, scaled by box count per depth
+    "id": {"bytes_per_launch": 56.3e6,
+           "kernels_sha256": "72221df3b13b6f3e6c03f4c0b1b0b5c05cd136a2e5c5e932f4c47ace8be9f097"},
 }
 
 
