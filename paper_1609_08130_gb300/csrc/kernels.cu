@@ -66,9 +66,20 @@ __global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__
     cid = L.col_ids + L.col_off[q];
     o = out + L.out_off[q];
   }
-  int64_t tot = (int64_t)nr * nc;
+  const int64_t tot = (int64_t)nr * nc;
+  // element e = (i, j) of the column-major block: e / nr by a multiply-high
+  // while the block has fewer than 2^31 entries (every pair block; the top
+  // block up to 46340 DOFs)
+  const bool small = tot < ((int64_t)1 << 31);
+  const FastDiv fnr(max(nr, 1));
   for (int64_t e = blockIdx.y * (int64_t)NT + threadIdx.x; e < tot; e += (int64_t)NT * gridDim.y) {
-    int i = (int)(e % nr), j = (int)(e / nr);
+    int i, j;
+    if (small) {
+      fnr.divmod((int)e, j, i);
+    } else {
+      i = (int)(e % nr);
+      j = (int)(e / nr);
+    }
     int64_t gi = rid[i], gj = cid[j];
     if (L.transpose) {
       int64_t tg = gi;
@@ -909,13 +920,15 @@ __device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShare
   if (own && part == 0) sh.lp[mylog] = col;
   group_bar(1, GT);
   // R12 := R11^{-1} R12 (columns of R12 are the logical positions k.. b-1)
+  const FastDiv fr(max(r, 1)), fk(max(k, 1));
   for (int i = k - 1; i >= 0; i--) {
     const int pi = sh.lp[i];
     const T inv = (T)1 / R[i * LDR + pi];
     for (int c = lt; c < r; c += GT) R[i * LDR + sh.lp[k + c]] *= inv;
     group_bar(1, GT);
     for (int e = lt; e < i * r; e += GT) {
-      const int l = e / r, c = e % r;
+      int l, c;
+      fr.divmod(e, l, c);
       const int pcol = sh.lp[k + c];
       R[l * LDR + pcol] -= R[l * LDR + pi] * R[i * LDR + pcol];
     }
@@ -923,7 +936,8 @@ __device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShare
   }
   // T (k x r, column-major, ld k)
   for (int e = lt; e < k * r; e += GT) {
-    const int i = e % k, c = e / k;
+    int i, c;
+    fk.divmod(e, c, i);
     fb.Tm[e] = R[i * LDR + sh.lp[k + c]];
   }
   if (lt < b) {
