@@ -860,7 +860,7 @@ template <typename T> struct Factor : FactorBase {
   cudaStream_t st = nullptr;
   int64_t n = 0;
   int dim = 2;
-  DBuf d_x, d_perm, d_cell, d_off, d_err, d_proxy, d_wdof;
+  DBuf d_x, d_perm, d_cell, d_off, d_err, d_proxy, d_wdof;  // d_proxy: unit proxy points in T
   DevTreePoints dev_pts;  // a single problem's tree-order points, kept on the device
   Points P{};
   std::vector<std::unique_ptr<DBuf>> store;  // factor storage chunks
@@ -1356,7 +1356,8 @@ template <typename T> static void run_factor(Factor<T> &F) {
         u[3 * m + 2] = z;
       }
     }
-    upload(F.d_proxy, u, st);
+    std::vector<T> uT(u.begin(), u.end());  // the ID kernels read them in the factor's precision
+    upload(F.d_proxy, uT, st);
   }
 
   F.maxdepth = 0;
@@ -1896,7 +1897,7 @@ template <typename T> static void run_factor(Factor<T> &F) {
       const int *bl = ptr<int>(d_list) + p.first;
       auto id_launch = [&] {
         launch_id<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ring_max, F.P, F.K, F.px,
-                     ptr<double>(F.d_proxy), F.eps, ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
+                     ptr<T>(F.d_proxy), F.eps, ptr<T>(gid), id_stride, id_smem, st, ptr<int>(F.d_err));
       };
       int pi = F.prof.begin(KC_ID, st, base + p.first, p.second);
       tuned_id_launch(F, large ? -H.bmax : H.bmax, p.second, id_launch);

@@ -115,6 +115,13 @@ __device__ __forceinline__ T entry(const Points &P, const KernelParams &K, int64
   const double w = P.wdof ? P.wdof[i] : K.w;
   return (T)w * kof(K.kind, Dist2<T>::eval(P, i, j));
 }
+// The same with the weight and the diagonal already in T (one problem, no
+// per-DOF weights): no FP64 conversion per entry.
+template <typename T>
+__device__ __forceinline__ T entry_t(const Points &P, int kind, T w, T diag, int64_t i, int64_t j) {
+  if (i == j) return diag;
+  return w * kof(kind, Dist2<T>::eval(P, i, j));
+}
 
 // Weight of the problem a DOF belongs to.
 __device__ __forceinline__ double weight_of(const Points &P, const KernelParams &K, int64_t i) {

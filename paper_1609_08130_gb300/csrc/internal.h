@@ -98,7 +98,7 @@ void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, con
 template <typename T>
 void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax,
                int mmax, const Points &P, const KernelParams &K, const ProxyParams &px,
-               const double *proxy_unit, double eps, T *gscratch, int64_t gscratch_stride, bool use_smem,
+               const T *proxy_unit, double eps, T *gscratch, int64_t gscratch_stride, bool use_smem,
                cudaStream_t st, int *err);
 // Launch shape of the next ID launch on this thread: CTAs per box << 8 |
 // threads per column << 4 | fold groups per box (0: default).

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__
   // block up to 46340 DOFs)
   const bool small = tot < ((int64_t)1 << 31);
   const FastDiv fnr(max(nr, 1));
+  const T wT = (T)K.w, dT = (T)K.diag;  // converted once per CTA, not once per entry
   for (int64_t e = blockIdx.y * (int64_t)NT + threadIdx.x; e < tot; e += (int64_t)NT * gridDim.y) {
     int i, j;
     if (small) {
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__
         done = true;
       }
     }
-    if (!done) v = entry<T>(P, K, gi, gj);
+    if (!done) v = P.wdof ? entry<T>(P, K, gi, gj) : entry_t<T>(P, K.kind, wT, dT, gi, gj);
     o[e] = v;
   }
 }
@@ -953,7 +954,7 @@ __device__ void idq_finish(T *R, int LDR, int b, double eps, int *perm, IdqShare
 
 template <typename T, int NC, int RPT = IdwRows<T>::PR>
 __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
-                                             Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
+                                             Points P, KernelParams K, ProxyParams px, const T *proxy_unit,
                                              double eps, int ring_max, int *err) {
   constexpr int PR = RPT;  // rows of a panel, all held by the column's thread
   constexpr int LDR = NC + 1;
@@ -1026,13 +1027,16 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
   const int64_t coff = lv.cell_dof_off[c];
   const double D = ldexp(1.0, -lv.t);
   const double rad = px.radius * D;
-  double xq[3];
+  // this column's point relative to the box centre, and the proxy radius, in
+  // T: the proxy rows' distances take no FP64 arithmetic in the FP32 factor
+  T xq[3];
+  const T radT = (T)rad;
   {
     const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
-      xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+      xq[d] = (col < b && d < dim) ? (T)(P.x[g * dim + d] - ctr) : (T)0;
     }
   }
   const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
@@ -1048,13 +1052,13 @@ __global__ void __launch_bounds__(256) k_idc(LevelDev<T> lv, FBox<T> *boxes, con
           v = lv.pool[s_rowsrc[row] + col];
         } else if (row < m) {
           const int pm = row - nO;
-          double r2 = 0.0;
+          T r2 = (T)0;
 #pragma unroll
           for (int d = 0; d < 3; d++) {
-            const double dd = rad * proxy_unit[3 * pm + d] - xq[d];
+            const T dd = radT * proxy_unit[3 * pm + d] - xq[d];
             r2 += dd * dd;
           }
-          v = w * kof(K.kind, (T)r2);
+          v = w * kof(K.kind, r2);
         }
       }
       pan[i] = v;
@@ -1145,7 +1149,7 @@ __device__ __forceinline__ void fold_group_q(T (&pan)[PR / TPC], T *R, int ldr, 
 
 template <typename T, int NC, int TPC>
 __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
-                                             Points P, KernelParams K, ProxyParams px, const double *proxy_unit,
+                                             Points P, KernelParams K, ProxyParams px, const T *proxy_unit,
                                              double eps, int ring_max, int *err) {
   constexpr int RPT = IdwRows<T>::PR;
   constexpr int PR = RPT * TPC;
@@ -1225,13 +1229,16 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
   const int64_t coff = lv.cell_dof_off[c];
   const double D = ldexp(1.0, -lv.t);
   const double rad = px.radius * D;
-  double xq[3];
+  // this column's point relative to the box centre, and the proxy radius, in
+  // T: the proxy rows' distances take no FP64 arithmetic in the FP32 factor
+  T xq[3];
+  const T radT = (T)rad;
   {
     const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
-      xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+      xq[d] = (col < b && d < dim) ? (T)(P.x[g * dim + d] - ctr) : (T)0;
     }
   }
   const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
@@ -1247,13 +1254,13 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
           v = lv.pool[s_rowsrc[row] + col];
         } else if (row < m) {
           const int pm = row - nO;
-          double r2 = 0.0;
+          T r2 = (T)0;
 #pragma unroll
           for (int d = 0; d < 3; d++) {
-            const double dd = rad * proxy_unit[3 * pm + d] - xq[d];
+            const T dd = radT * proxy_unit[3 * pm + d] - xq[d];
             r2 += dd * dd;
           }
-          v = w * kof(K.kind, (T)r2);
+          v = w * kof(K.kind, r2);
         }
       }
       pan[i] = v;
@@ -1293,7 +1300,7 @@ __global__ void __launch_bounds__(512) k_idq(LevelDev<T> lv, FBox<T> *boxes, con
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int TPC, bool GLOB>
 __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, int C, Points P,
-                                             KernelParams K, ProxyParams px, const double *proxy_unit, double eps,
+                                             KernelParams K, ProxyParams px, const T *proxy_unit, double eps,
                                              int ring_max, T *tri, int64_t tstride, int *cnt, int *err) {
   constexpr int RPT = IdwRows<T>::PR;
   constexpr int PR = RPT * TPC;
@@ -1393,13 +1400,16 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
   const int64_t coff = lv.cell_dof_off[c];
   const double D = ldexp(1.0, -lv.t);
   const double rad = px.radius * D;
-  double xq[3];
+  // this column's point relative to the box centre, and the proxy radius, in
+  // T: the proxy rows' distances take no FP64 arithmetic in the FP32 factor
+  T xq[3];
+  const T radT = (T)rad;
   {
     const int64_t g = col < b ? lv.cell_dofs[coff + col] : 0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
-      xq[d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+      xq[d] = (col < b && d < dim) ? (T)(P.x[g * dim + d] - ctr) : (T)0;
     }
   }
   const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
@@ -1415,13 +1425,13 @@ __global__ void __launch_bounds__(512) k_idm(LevelDev<T> lv, FBox<T> *boxes, con
           v = lv.pool[rowsrc(row) + col];
         } else if (row < m) {
           const int pm = row - nO;
-          double r2 = 0.0;
+          T r2 = (T)0;
 #pragma unroll
           for (int d = 0; d < 3; d++) {
-            const double dd = rad * proxy_unit[3 * pm + d] - xq[d];
+            const T dd = radT * proxy_unit[3 * pm + d] - xq[d];
             r2 += dd * dd;
           }
-          v = w * kof(K.kind, (T)r2);
+          v = w * kof(K.kind, r2);
         }
       }
       pan[i] = v;
@@ -1484,7 +1494,7 @@ static size_t idm_smem(int bmax, int ring_max) {
 
 template <typename T, int NC, int TPC, bool GLOB = false>
 static void launch_idm(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int C, int bmax,
-                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const T *proxy_unit,
                        double eps, int ring_max, T *tri, int64_t tstride, int *cnt, cudaStream_t st, int *err) {
   const size_t smem = idm_smem<T, NC, TPC, GLOB>(bmax, ring_max);
   cudaFuncSetAttribute(k_idm<T, NC, TPC, GLOB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1504,7 +1514,7 @@ template <typename T, int NC, int TPC> static size_t idq_smem(int bmax, int G, i
 
 template <typename T, int NC, int TPC>
 static void launch_idq(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G, int bmax,
-                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const T *proxy_unit,
                        double eps, int ring_max, cudaStream_t st, int *err) {
   constexpr int PR = IdwRows<T>::PR * TPC;
   const int TR = NC > 128 ? bmax : NC;
@@ -1524,7 +1534,7 @@ static void launch_idq(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_lis
 
 template <typename T, int NC, int RPT = IdwRows<T>::PR>
 static void launch_idc(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int G,
-                       const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit,
+                       const Points &P, const KernelParams &K, const ProxyParams &px, const T *proxy_unit,
                        double eps, int ring_max, cudaStream_t st, int *err) {
   constexpr int PR = RPT;
   const size_t tri = (size_t)NC * (NC + 1) * sizeof(T);
@@ -1620,7 +1630,7 @@ template <typename T, int NC> struct IdpRows {
 
 template <typename T, int W, int NC>
 __global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, const int *box_list, Points P,
-                                                KernelParams K, ProxyParams px, const double *proxy_unit, double eps,
+                                                KernelParams K, ProxyParams px, const T *proxy_unit, double eps,
                                                 int ring_max, int *err) {
   constexpr int PR = IdpRows<T, NC>::PR;
   constexpr int NS = NC / 32;  // columns per lane
@@ -1693,7 +1703,10 @@ __global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, 
   const int64_t coff = lv.cell_dof_off[c];
   const double D = ldexp(1.0, -lv.t);
   const double rad = px.radius * D;
-  double xq[NS][3];
+  // the lane's points relative to the box centre, and the proxy radius, in
+  // T: the proxy rows' distances take no FP64 arithmetic in the FP32 factor
+  T xq[NS][3];
+  const T radT = (T)rad;
 #pragma unroll
   for (int sl = 0; sl < NS; sl++) {
     const int col = lane + 32 * sl;
@@ -1701,7 +1714,7 @@ __global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, 
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double ctr = d < dim ? (lv.cell_coord[3 * c + d] + 0.5) * D : 0.0;
-      xq[sl][d] = (col < b && d < dim) ? P.x[g * dim + d] - ctr : 0.0;
+      xq[sl][d] = (col < b && d < dim) ? (T)(P.x[g * dim + d] - ctr) : (T)0;
     }
   }
   const T w = (T)weight_of(P, K, lv.cell_dofs[lv.cell_dof_off[c]]);
@@ -1728,15 +1741,15 @@ __global__ void __launch_bounds__(W * 32) k_idw(LevelDev<T> lv, FBox<T> *boxes, 
           }
         } else if (row < m) {
           const int pm = row - nO;
-          double u[3];
+          T u[3];
 #pragma unroll
-          for (int d = 0; d < 3; d++) u[d] = rad * proxy_unit[3 * pm + d];
+          for (int d = 0; d < 3; d++) u[d] = radT * proxy_unit[3 * pm + d];
 #pragma unroll
           for (int sl = 0; sl < NS; sl++) {
-            double r2 = 0.0;
+            T r2 = (T)0;
 #pragma unroll
             for (int d = 0; d < 3; d++) r2 += (u[d] - xq[sl][d]) * (u[d] - xq[sl][d]);
-            p[sl][i] = lane + 32 * sl < b ? w * kof(K.kind, (T)r2) : (T)0;
+            p[sl][i] = lane + 32 * sl < b ? w * kof(K.kind, r2) : (T)0;
           }
         } else {
 #pragma unroll
@@ -1759,7 +1772,7 @@ template <typename T, int W, int NC> static size_t idw_smem(int ring_max) {
 
 template <typename T, int W, int NC>
 static bool launch_idw(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, const Points &P,
-                       const KernelParams &K, const ProxyParams &px, const double *proxy_unit, double eps,
+                       const KernelParams &K, const ProxyParams &px, const T *proxy_unit, double eps,
                        int ring_max, cudaStream_t st, int *err) {
   const size_t smem = idw_smem<T, W, NC>(ring_max);
   if (smem > (size_t)(220u << 10)) return false;  // a ring too long for the row table
@@ -1782,7 +1795,7 @@ void set_id_multi(const IdMultiScratch &m) { id_multi = m; }
 
 template <typename T>
 void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, int mmax,
-               const Points &P, const KernelParams &K, const ProxyParams &px, const double *proxy_unit, double eps,
+               const Points &P, const KernelParams &K, const ProxyParams &px, const T *proxy_unit, double eps,
                T *gscratch, int64_t gscratch_stride, bool use_smem, cudaStream_t st, int *err) {
   (void)mmax;
   if (nbox == 0) return;
@@ -4198,7 +4211,7 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
   template void launch_assemble<T>(const AssembleList &, T *, const LevelDev<T> *, const Points &,             \
                                    const KernelParams &, int64_t, cudaStream_t);                              \
   template void launch_id<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, int, const Points &,       \
-                             const KernelParams &, const ProxyParams &, const double *, double, T *, int64_t, bool,  \
+                             const KernelParams &, const ProxyParams &, const T *, double, T *, int64_t, bool,       \
                              cudaStream_t,                                                                   \
                              int *);                                                                          \
   template void launch_elim<T>(const LevelDev<T> &, FBox<T> *, const int *, int, int, T *, int64_t,            \
