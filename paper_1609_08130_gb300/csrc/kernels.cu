@@ -108,12 +108,116 @@ __global__ void __launch_bounds__(NT) k_assemble(AssembleList L, T *__restrict__
   }
 }
 
+// The same for the pair blocks of a level whose cells hold at most AS_MAX
+// DOFs (level mode, no per-DOF weights): one CTA per block, the block's row
+// and column DOFs staged first -- their points, and their previous-level
+// cell, its coordinates and the DOF's place in it -- so that each entry is
+// a copy from the previous level's pool or a kernel evaluation from shared
+// memory.
+constexpr int AS_MAX = 128;
+template <typename T> struct AsPts;
+template <> struct AsPts<float> {
+  int c[3][AS_MAX];
+  float o[3][AS_MAX];
+};
+template <> struct AsPts<double> {
+  double x[3][AS_MAX];
+};
+struct AsPrev {
+  int cell[AS_MAX], loc[AS_MAX], cc[3][AS_MAX];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_assemble_staged(AssembleList L, T *__restrict__ out, LevelDev<T> prev,
+                                                        int has_prev, Points P, KernelParams K) {
+  __shared__ AsPts<T> sp[2];  // rows, columns
+  __shared__ AsPrev spv[2];
+  const int q = blockIdx.x;
+  const int nb = L.cell_nbr[q];
+  if (nb < 0) return;
+  const int c = q / L.NB;
+  const int nr = L.cell_b[c], nc = L.cell_b[nb];
+  const int64_t *ids[2] = {L.row_ids + L.cell_dof_off[c], L.col_ids + L.cell_dof_off[nb]};
+  const int cnt[2] = {nr, nc};
+  T *o = out + L.pair_off[q];
+  const int dim = P.dim;
+  for (int s = 0; s < 2; s++)
+    for (int i = threadIdx.x; i < cnt[s]; i += NT) {
+      const int64_t g = ids[s][i];
+      if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          sp[s].c[d][i] = P.cell[3 * g + d];
+          sp[s].o[d][i] = P.off[3 * g + d];
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; d++) sp[s].x[d][i] = d < dim ? P.x[g * dim + d] : 0.0;
+      }
+      const int pc = has_prev ? prev.dof_cell[g] : -1;
+      spv[s].cell[i] = pc;
+      spv[s].loc[i] = pc >= 0 ? prev.dof_loc[g] : 0;
+#pragma unroll
+      for (int d = 0; d < 3; d++) spv[s].cc[d][i] = pc >= 0 ? prev.cell_coord[3 * pc + d] : 0;
+    }
+  __syncthreads();
+  const T wT = (T)K.w, dT = (T)K.diag;
+  const FastDiv fnr(max(nr, 1));
+  for (int e = threadIdx.x; e < nr * nc; e += NT) {
+    int i, j;
+    fnr.divmod(e, j, i);
+    T v;
+    bool done = false;
+    const int ci = spv[0].cell[i], cj = spv[1].cell[j];
+    if (ci >= 0 && cj >= 0) {
+      const int dx = spv[1].cc[0][j] - spv[0].cc[0][i], dy = spv[1].cc[1][j] - spv[0].cc[1][i],
+                dz = spv[1].cc[2][j] - spv[0].cc[2][i];
+      if (dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2 && dz >= -2 && dz <= 2) {
+        const int64_t off = prev.pair_off[(int64_t)ci * prev.NB + code5(dx, dy, dz, prev.dim)];
+        v = prev.pool[off + spv[0].loc[i] + (int64_t)spv[1].loc[j] * prev.cell_b[ci]];
+        done = true;
+      }
+    }
+    if (!done) {
+      if (ids[0][i] == ids[1][j]) {
+        v = dT;
+      } else {
+        T r2;
+        if constexpr (sizeof(T) == 4) {
+          const float Dd = P.D;
+          const float ex = fmaf((float)(sp[0].c[0][i] - sp[1].c[0][j]), Dd, sp[0].o[0][i] - sp[1].o[0][j]);
+          const float ey = fmaf((float)(sp[0].c[1][i] - sp[1].c[1][j]), Dd, sp[0].o[1][i] - sp[1].o[1][j]);
+          r2 = ex * ex + ey * ey;
+          if (dim == 3) {
+            const float ez = fmaf((float)(sp[0].c[2][i] - sp[1].c[2][j]), Dd, sp[0].o[2][i] - sp[1].o[2][j]);
+            r2 = fmaf(ez, ez, r2);
+          }
+        } else {
+          const double ex = sp[0].x[0][i] - sp[1].x[0][j], ey = sp[0].x[1][i] - sp[1].x[1][j];
+          r2 = ex * ex + ey * ey;
+          if (dim == 3) {
+            const double ez = sp[0].x[2][i] - sp[1].x[2][j];
+            r2 += ez * ez;
+          }
+        }
+        v = wT * kof(K.kind, r2);
+      }
+    }
+    o[e] = v;
+  }
+}
+
 template <typename T>
 void launch_assemble(const AssembleList &L, T *out, const LevelDev<T> *prev, const Points &P,
                      const KernelParams &K, int64_t maxblk, cudaStream_t st) {
   if (L.nblock == 0) return;
   LevelDev<T> pv{};
   if (prev) pv = *prev;
+  if (L.cell_nbr && !P.wdof && maxblk <= (int64_t)AS_MAX * AS_MAX) {
+    k_assemble_staged<T><<<L.nblock, NT, 0, st>>>(L, out, pv, prev ? 1 : 0, P, K);
+    count_launch();
+    return;
+  }
   int gy = (int)((maxblk + NT * 8 - 1) / (NT * 8));
   if (gy < 1) gy = 1;
   if (gy > 1024) gy = 1024;
