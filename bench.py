@@ -73,7 +73,10 @@ def load_peaks():
 
 # kernel classes bound by moving bytes; the others (ID, elimination, top LU)
 # by FP32 / FP64 arithmetic latency and throughput
-HBM_CLASSES = {"schur", "sweep", "assemble", "permute", "top_solve", "refine_op"}
+HBM_CLASSES = {"schur", "sweep", "assemble", "permute", "top_solve"}
+# classes whose arithmetic is FP64 whatever the factor's precision: the
+# residual operator (FFT convolution or direct sum in FP64)
+FP64_CLASSES = {"refine_op"}
 
 
 def class_roofline(cls: str, d: dict, peaks: dict, prec: str):
@@ -86,7 +89,7 @@ def class_roofline(cls: str, d: dict, peaks: dict, prec: str):
     if cls in HBM_CLASSES:
         a = d["bytes"] / s / 1e9
         return {"bound": "hbm", "achieved": a, "peak": peaks["hbm"], "unit": "GB/s", "frac": a / peaks["hbm"]}
-    pk = alu_peak_tflops(prec, peaks["sm_mhz"], peaks.get("sms", 152))
+    pk = alu_peak_tflops("fp64" if cls in FP64_CLASSES else prec, peaks["sm_mhz"], peaks.get("sms", 152))
     a = d["flops"] / s / 1e12
     return {"bound": "alu", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk}
 

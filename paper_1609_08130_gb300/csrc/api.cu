@@ -873,6 +873,7 @@ template <typename T> struct Factor : FactorBase {
   std::vector<int> h_tn;
   std::vector<int64_t> h_toff, h_loff;
   DBuf d_top, d_topLU, d_toppiv, d_tn, d_toff, d_loff;
+  DBuf d_topinv;  // one problem's U^{-1} L^{-1} of the top block (ntop <= 1024), else empty
   mutable DBuf d_work, d_topwork;
   // Cholesky factors of the diagonal blocks for the generalized square root
   // (rss_sqrt_apply), built on its first use
@@ -2075,6 +2076,13 @@ template <typename T> static void run_factor(Factor<T> &F) {
       launch_lu_batched<T>(ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_toff),
                            ptr<int>(F.d_tn), np, st, ptr<int>(F.d_err));
     check_launch("top lu");
+    if (np == 1 && F.ntop <= 1024) {
+      // the solves multiply by U^{-1} L^{-1} instead of two triangular sweeps
+      F.d_topinv.alloc((size_t)F.ntop * F.ntop * sizeof(T), st);
+      F.factor_bytes += (int64_t)F.ntop * F.ntop * sizeof(T);
+      launch_top_inverse<T>(ptr<T>(F.d_topLU), F.ntop, ptr<T>(F.d_topinv), st);
+      check_launch("top inverse");
+    }
     F.prof.end(pi, st);
   }
   prevD.reset();
@@ -2159,7 +2167,8 @@ static void enqueue_sweeps(const Factor<T> &F, const double *in, double *out, T 
   double nt = F.ntop;
   pi = begin(KC_TOP, 0, 0, 0, nt * nt * sz + 2.0 * nt * nrhs * sz, 2.0 * nt * nt * nrhs);
   launch_top<T>(solve ? 0 : 1, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
-                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, ptr<T>(F.d_topwork), st);
+                ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nrhs, ptr<T>(F.d_topwork), st,
+                F.d_topinv.p ? ptr<T>(F.d_topinv) : nullptr);
   end(pi);
   for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) {
     pi = begin(KC_SWEEP, it->first, it->count, nrhs);
@@ -2239,7 +2248,25 @@ static void do_sweeps(const Factor<T> &F, const double *in, double *out, int nrh
 template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs);
 
 template <typename T> static void apply_A(const Factor<T> &F, const double *x, double *y, int nrhs) {
-  int pi = F.prof.begin(KC_REFINE_OP, F.st);
+  // FP64 flops of the FFT operator (the work of this class): per pair of
+  // right-hand sides a forward and an inverse transform over the lines the
+  // zero padding leaves (along axis a, the lines whose coordinates before a
+  // span L and after a span s), 5 L log2 L flops a line, and the pointwise
+  // product (6 flops per frequency)
+  double fl = 0.0;
+  if (F.grid_side > 0) {
+    const double s = F.grid_side, L = 2.0 * F.grid_side;
+    double lines = 0.0, vol = 1.0;
+    for (int a = 0; a < F.dim; a++) {
+      double l = 1.0;
+      for (int d = 0; d < F.dim; d++)
+        if (d != a) l *= d < a ? L : s;
+      lines += l;
+      vol *= L;
+    }
+    fl = (double)((nrhs + 1) / 2) * (2.0 * lines * 5.0 * L * std::log2(L) + 6.0 * vol);
+  }
+  int pi = F.prof.begin(KC_REFINE_OP, F.st, 0, 0, nrhs, 0.0, fl);
   apply_A_impl(F, x, y, nrhs);
   F.prof.end(pi, F.st);
 }
@@ -2654,7 +2681,8 @@ static void solve_noalloc(const Factor<T> &F, const double *b, double *x, int nr
     launch_permute<T>(0, ptr<int64_t>(F.d_perm), bc, v, nullptr, F.n, nc, st);
     for (const Phase &p : F.phases) sweep_phase<T>(F, SWEEP_SOLVE_FWD, p, v, nc, st);
     launch_top<T>(0, ptr<T>(F.d_topLU), ptr<int64_t>(F.d_loff), ptr<int>(F.d_toppiv), ptr<int64_t>(F.d_top),
-                  ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nc, topwork, st);
+                  ptr<int64_t>(F.d_toff), ptr<int>(F.d_tn), F.nprob, F.ntop, v, nc, topwork, st,
+                  F.d_topinv.p ? ptr<T>(F.d_topinv) : nullptr);
     for (auto it = F.phases.rbegin(); it != F.phases.rend(); ++it) sweep_phase<T>(F, SWEEP_SOLVE_BWD, *it, v, nc, st);
     launch_permute<T>(1, ptr<int64_t>(F.d_perm), nullptr, v, xc, F.n, nc, st);
     check_launch("rss_solve_noalloc");

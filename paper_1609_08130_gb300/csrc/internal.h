@@ -153,9 +153,14 @@ void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const 
 size_t sweep_chunk_smem(int bmax, int nrhs, int elem);
 // Set the shared-memory attributes of every sweep kernel on the current device.
 void sweep_kernel_attributes();
+// Top blocks: mode 0 solves with the LU factors (or, for one problem with
+// Winv = U^{-1} L^{-1} and at most 4 columns, multiplies by it), mode 1
+// multiplies by the block.  launch_top_inverse forms Winv (n <= 1024).
 template <typename T>
 void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, const int64_t *top, const int64_t *toff,
-                const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st);
+                const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st,
+                const T *Winv = nullptr);
+template <typename T> void launch_top_inverse(const T *LU, int n, T *W, cudaStream_t st);
 template <typename T>
 void launch_lu_batched(T *LU, const int64_t *loff, int *piv, const int64_t *toff, const int *tn, int nprob,
                        cudaStream_t st, int *err);

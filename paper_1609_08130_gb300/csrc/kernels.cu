@@ -4129,10 +4129,97 @@ __global__ void __launch_bounds__(1024) k_top(int mode, const T *LUall, const in
   }
 }
 
+// W = U^{-1} L^{-1} for one top block's LU (row-major; unit lower L below
+// the diagonal, U on and above), so that the solve's D^{-1} on the top
+// block is W (P v), a matrix-vector product, instead of two triangular
+// sweeps with a barrier per row.  One warp per column k of W: z = L^{-1}
+// e_k, then U^{-1} z, each row's dot product spread over the lanes; z in
+// shared memory.  Columns are independent, so the warps never wait on one
+// another.
+constexpr int TOPINV_WARPS = 4;
+template <typename T> __global__ void __launch_bounds__(32 * TOPINV_WARPS) k_top_inverse(const T *LU, int n, T *W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * TOPINV_WARPS + w;
+  if (k >= n) return;  // the whole warp: no barrier follows
+  T *z = reinterpret_cast<T *>(smem_raw) + (size_t)w * n;
+  for (int i = lane; i < n; i += 32) z[i] = i == k ? (T)1 : (T)0;
+  __syncwarp();
+  for (int i = k + 1; i < n; i++) {
+    const T *Li = LU + (int64_t)i * n;
+    T acc = (T)0;
+    for (int l = k + lane; l < i; l += 32) acc += Li[l] * z[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[i] = -acc;
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    const T *Ui = LU + (int64_t)i * n;
+    T acc = (T)0;
+    for (int l = i + 1 + lane; l < n; l += 32) acc += Ui[l] * z[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[i] = (z[i] - acc) / Ui[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) W[(int64_t)i * n + k] = z[i];
+}
+
+template <typename T> void launch_top_inverse(const T *LU, int n, T *W, cudaStream_t st) {
+  if (n == 0) return;
+  k_top_inverse<T><<<(n + TOPINV_WARPS - 1) / TOPINV_WARPS, 32 * TOPINV_WARPS,
+                     (size_t)TOPINV_WARPS * n * sizeof(T), st>>>(LU, n, W);
+  count_launch();
+}
+
+// y = P v_top (the pivoted gather), then v_top = W y with one warp per row.
+template <typename T>
+__global__ void k_top_gather(const int *piv, const int64_t *top, int n, const T *v, int nrhs, T *y) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * nrhs) return;
+  const int kk = e / nrhs, c = e - kk * nrhs;
+  y[e] = v[top[piv[kk]] * nrhs + c];
+}
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_top_gemv(const T *W, const int64_t *top, int n, const T *y, T *v) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const T *Wi = W + (int64_t)i * n;
+  T acc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; c++) acc[c] = (T)0;
+  for (int kk = lane; kk < n; kk += 32) {
+    const T w = Wi[kk];
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc[c] += w * y[kk * NR + c];
+  }
+#pragma unroll
+  for (int c = 0; c < NR; c++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NR; c++) v[top[i] * NR + c] = acc[c];
+}
+
 template <typename T>
 void launch_top(int mode, const T *LU, const int64_t *loff, const int *piv, const int64_t *top, const int64_t *toff,
-                const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st) {
+                const int *tn, int nprob, int ntop_total, T *v, int nrhs, T *work, cudaStream_t st, const T *Winv) {
   if (ntop_total == 0 || nprob == 0) return;
+  if (mode == 0 && Winv && nprob == 1 && nrhs >= 1 && nrhs <= 4) {
+    const int n = ntop_total;
+    k_top_gather<T><<<(n * nrhs + 255) / 256, 256, 0, st>>>(piv, top, n, v, nrhs, work);
+    count_launch();
+    const unsigned g = (unsigned)((n + 7) / 8);
+    if (nrhs == 1) k_top_gemv<T, 1><<<g, 256, 0, st>>>(Winv, top, n, work, v);
+    else if (nrhs == 2) k_top_gemv<T, 2><<<g, 256, 0, st>>>(Winv, top, n, work, v);
+    else if (nrhs == 3) k_top_gemv<T, 3><<<g, 256, 0, st>>>(Winv, top, n, work, v);
+    else k_top_gemv<T, 4><<<g, 256, 0, st>>>(Winv, top, n, work, v);
+    count_launch();
+    return;
+  }
   k_top<T><<<nprob * nrhs, 1024, 0, st>>>(mode, LU, loff, piv, top, toff, tn, v, nrhs, work);
   count_launch();
 }
@@ -4331,7 +4418,8 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
   template void launch_chol_apply<T>(const FBox<T> *, int, const int64_t *, const int64_t *, const int *, int,     \
                                      const T *, const int64_t *, T *, int, int, int, cudaStream_t);              \
   template void launch_top<T>(int, const T *, const int64_t *, const int *, const int64_t *, const int64_t *,     \
-                             const int *, int, int, T *, int, T *, cudaStream_t);                            \
+                             const int *, int, int, T *, int, T *, cudaStream_t, const T *);                 \
+  template void launch_top_inverse<T>(const T *, int, T *, cudaStream_t);                                     \
   template void launch_lu_batched<T>(T *, const int64_t *, int *, const int64_t *, const int *, int, cudaStream_t, \
                                      int *);                                                                  \
   template void launch_permute<T>(int, const int64_t *, const double *, T *, double *, int64_t, int,          \
