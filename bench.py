@@ -515,6 +515,8 @@ def main():
     peaks["sms"] = torch.cuda.get_device_properties(local).multi_processor_count
     tuned = [[e["elem_bytes"], e["width"], e["phase_class"], e["tpc"], e["groups"], e["ctas"], e["rows"]]
              for e in pkg.autotune_table()]
+    tuned_elim = [[e["elem_bytes"], e["width"], e["phase_class"], e["split"], e["ctas"]]
+                  for e in pkg.autotune_elim_table()]
     # dominant kernel class by time in the profiled pass
     gpu_classes = {k: v for k, v in prof_tot.items() if not k.startswith("host_")}
     dom = max(gpu_classes.items(), key=lambda kv: kv[1]["ms"])
@@ -559,7 +561,10 @@ def main():
             "gpu_launches": int(launches),
             "autotune": {"id_shapes": tuned, "fields": ["element bytes", "box width class", "phase-size class",
                                                         "threads per column", "fold groups", "CTAs per box",
-                                                        "panel rows per thread (units of 32 FP32 rows)"]},
+                                                        "panel rows per thread (units of 32 FP32 rows)"],
+                         "elim_shapes": tuned_elim,
+                         "elim_fields": ["element bytes", "box width class", "phase-size class",
+                                         "E and G in a separate product kernel", "CTAs per box"]},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -415,8 +415,21 @@ rss_status rss_autotune_table(int32_t *buf, size_t *nbytes);
  * width classes 64 and 128). */
 rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc, int groups, int ctas, int rows);
 
-/* rss_autotune_clear -- forget every choice; the next factorizations tune
- * again. */
+/* rss_autotune_elim_table -- the elimination's autotuned shapes so far in
+ * this process, as HOST int32 records of 10: {element bytes, box-width class
+ * (64 or 128), phase-size class, chosen split flag and CTAs per box, then the
+ * measured time in microseconds of the 5 candidates (split, CTAs per box) =
+ * (0,1) (1,1) (1,2) (1,4) (1,8)}.  Split 0 forms E and G in the same kernel
+ * as the LU of X_RR, one CTA per box; split 1 leaves X_JR and X_RJ in scratch
+ * for a phase-wide product kernel, the box's rows of J shared by that many
+ * CTAs.  The first phase of a key times every candidate (the elimination of
+ * a phase writes the same values however often it runs), keeps the fastest
+ * and re-runs it.  Not tuned with a rank proposal, on the large-box path, or
+ * with RSS_FLAG_NO_AUTOTUNE.  *nbytes in/out as in rss_tree_query. */
+rss_status rss_autotune_elim_table(int32_t *buf, size_t *nbytes);
+
+/* rss_autotune_clear -- forget every choice (ID and elimination); the next
+ * factorizations tune again. */
 void rss_autotune_clear(void);
 
 /* rss_free -- release a tree, factor or network handle (NULL-safe). */

@@ -7,4 +7,4 @@ The compute path is the CUDA library ``librss.so`` (C ABI in
 """
 from . import inputs  # noqa: F401
 from .rss import (FP64, MIXED, LAPLACE2D_LOG, LAPLACE3D_INV, Factorization, Mlp, RSSError, Tree,  # noqa: F401
-                  autotune_table, build, kernel_launches, lib)
+                  autotune_elim_table, autotune_table, build, kernel_launches, lib)

@@ -1211,6 +1211,74 @@ static void tuned_id_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
   set_id_groups(0);
 }
 
+// The elimination's launch shape (the k_elim2 path, boxes up to 128 wide):
+// E and G formed in the same kernel (one CTA per box), or X_JR and X_RJ
+// left in the scratch for the phase-wide k_elim_gemm with 1, 2, 4 or 8 CTAs
+// per box sharing a box's rows of J.  Tuned like the ID, per (precision,
+// width class, phase-size class): the elimination of a phase only writes
+// its boxes' records, its scratch and its cells' active lists, the same
+// values however often it runs, so re-running it on the first phase of a
+// key is safe.  Not tuned with a rank proposal (its storage claims are
+// counted) or on the forced large-box path.
+constexpr int kNElim = 5;
+static const int kElimShapes[kNElim][2] = {{0, 1}, {1, 1}, {1, 2}, {1, 4}, {1, 8}};  // (split, CTAs per box)
+struct ElimTuneEntry {
+  int shape;
+  float us[kNElim];
+};
+static std::map<std::tuple<int, int, int>, ElimTuneEntry> g_tune_elim;  // guarded by g_tune_m
+
+template <typename T, typename Launch>
+static void tuned_elim_launch(Factor<T> &F, int bmax, int nbox, Launch &&launch) {
+  const bool tunable = bmax > 0 && bmax <= 128 && !F.mlp && !(F.flags & RSS_FLAG_NO_AUTOTUNE);
+  if (!tunable) {
+    set_elim_shape(0);
+    launch();
+    return;
+  }
+  int bucket = 0;
+  while ((2 << bucket) <= nbox) bucket++;
+  const auto key = std::make_tuple((int)sizeof(T), bmax <= 64 ? 64 : 128, bucket);
+  int shape = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_m);
+    auto it = g_tune_elim.find(key);
+    if (it != g_tune_elim.end()) shape = it->second.shape;
+  }
+  auto hint = [](int c) { return (kElimShapes[c][0] << 4) | kElimShapes[c][1]; };
+  if (shape < 0) {
+    ElimTuneEntry te{-1, {}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    for (int ci = 0; ci < kNElim; ci++) {
+      set_elim_shape(hint(ci));
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; rep++) {  // the second launch is timed
+        CK(cudaEventRecord(e0, F.st));
+        launch();
+        CK(cudaEventRecord(e1, F.st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      te.us[ci] = std::max(1e3f * ms, 1e-3f);
+      if (te.shape < 0 || ms < best) {
+        best = ms;
+        te.shape = ci;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_m);
+    auto ins = g_tune_elim.insert({key, te});
+    shape = ins.first->second.shape;
+  }
+  set_elim_shape(hint(shape));
+  launch();
+  set_elim_shape(0);
+}
+
 // A level ran out of overflow space for boxes whose rank exceeded the
 // proposed reservation: the factorization is redone with full reservations.
 struct Retry {};
@@ -1905,8 +1973,11 @@ template <typename T> static void run_factor(Factor<T> &F) {
       check_launch("id");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_ELIM, st, base + p.first, p.second);
-      launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ptr<T>(gel), el_stride, ovf, st,
-                     ptr<int>(F.d_err), njmax_lvl);
+      auto elim_launch = [&] {
+        launch_elim<T>(view, ptr<FBox<T>>(F.d_boxes), bl, p.second, large ? -H.bmax : H.bmax, ptr<T>(gel), el_stride,
+                       ovf, st, ptr<int>(F.d_err), njmax_lvl);
+      };
+      tuned_elim_launch(F, large ? -H.bmax : H.bmax, p.second, elim_launch);
       check_launch("elim");
       F.prof.end(pi, st);
       pi = F.prof.begin(KC_SCHUR, st, base + p.first, p.second);
@@ -3383,9 +3454,33 @@ rss_status rss_autotune_set(int elem_bytes, int width, int phase_class, int tpc,
   });
 }
 
+rss_status rss_autotune_elim_table(int32_t *buf, size_t *nbytes) {
+  return guard([&] {
+    if (!nbytes) throw Fail{RSS_EINVAL, "rss_autotune_elim_table: bad arguments"};
+    std::vector<int32_t> v;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_m);
+      for (const auto &kv : g_tune_elim) {
+        v.push_back(std::get<0>(kv.first));
+        v.push_back(std::get<1>(kv.first));
+        v.push_back(std::get<2>(kv.first));
+        for (int f = 0; f < 2; f++) v.push_back(kElimShapes[kv.second.shape][f]);
+        for (int c = 0; c < kNElim; c++) v.push_back((int32_t)std::lround(kv.second.us[c]));
+      }
+    }
+    const size_t need = v.size() * sizeof(int32_t), cap = *nbytes;
+    *nbytes = need;
+    if (buf) {
+      if (cap < need) throw Fail{RSS_EINVAL, "rss_autotune_elim_table: buffer too small"};
+      if (need) memcpy(buf, v.data(), need);
+    }
+  });
+}
+
 void rss_autotune_clear(void) {
   std::lock_guard<std::mutex> lk(g_tune_m);
   g_tune.clear();
+  g_tune_elim.clear();
 }
 
 void rss_free(void *handle) {

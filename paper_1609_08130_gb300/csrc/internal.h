@@ -103,6 +103,9 @@ void launch_id(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int n
 // Launch shape of the next ID launch on this thread: CTAs per box << 8 |
 // threads per column << 4 | fold groups per box (0: default).
 void set_id_groups(int G);
+// Shape of the next elimination launch of this thread (k_elim2 path):
+// (split << 4) | CTAs per box, 0 for the built-in choice.
+void set_elim_shape(int h);
 // Scratch of the multi-CTA ID: triangle slots (slot_elems elements each,
 // max_slots of them; none for boxes wider than 512) and tree-node counters
 // (8 x max_slots ints, zero between launches).  kid_ctas: CTAs per box of

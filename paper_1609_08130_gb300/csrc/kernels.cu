@@ -3156,18 +3156,27 @@ __global__ void __launch_bounds__(NLU) k_elim_lu(LevelDev<T> lv, FBox<T> *boxes,
   if (tid == 0) lv.act_cnt[c] = k;
 }
 
+// Shape of the next k_elim2 launch on this thread: (split << 4) | CTAs per
+// box, or 0 for the built-in choice.  Set by the host's autotuner.
+static thread_local int elim_shape_hint = 0;
+void set_elim_shape(int h) { elim_shape_hint = h; }
+
 template <typename T>
 void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int nbox, int bmax, T *scratch,
                  int64_t scratch_stride, const Overflow<T> &ovf, cudaStream_t st, int *err, int njmax) {
   if (nbox == 0) return;
   const bool force_general = bmax < 0;  // large-box path requested
   if (force_general) bmax = -bmax;
-  // Phases of fewer than 300 boxes (upper levels) leave X_JR and X_RJ in the
-  // scratch and form E and G in k_elim_gemm, spread over the whole GPU;
-  // large phases form them in the one-CTA-per-box kernel (measured on the
-  // 512^2 grid).
-  const int split = nbox < 300 ? 1 : 0;
-  const int C = split ? std::min(8, std::max(1, (300 + nbox - 1) / nbox)) : 1;  // CTAs per box
+  // Built in: phases of fewer than 300 boxes (upper levels) leave X_JR and
+  // X_RJ in the scratch and form E and G in k_elim_gemm, spread over the
+  // whole GPU; large phases form them in the one-CTA-per-box kernel
+  // (measured on the 512^2 grid).  The autotuner may choose otherwise.
+  int split = nbox < 300 ? 1 : 0;
+  int C = split ? std::min(8, std::max(1, (300 + nbox - 1) / nbox)) : 1;  // CTAs per box
+  if (elim_shape_hint > 0) {
+    split = (elim_shape_hint >> 4) & 1;
+    C = split ? std::max(1, elim_shape_hint & 15) : 1;
+  }
   const int tr = (bmax + 63) / 64, tn = (std::max(njmax, 1) + 63) / 64;
   if (!force_general) {
     // worst case over k + r = b of the shared-memory form

@@ -109,6 +109,7 @@ _SIGS = {
     "rss_autotune_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_autotune_set": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "rss_autotune_clear": (None, []),
+    "rss_autotune_elim_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "rss_free": (None, [C.c_void_p]),
     "rss_last_error": (C.c_char_p, []),
     "rss_kernel_launches": (C.c_int64, []),
@@ -148,6 +149,21 @@ def autotune_table() -> list:
     recs = buf[:nb.value // 4].reshape(-1, rl)
     return [dict(elem_bytes=int(r[0]), width=int(r[1]), phase_class=int(r[2]), tpc=int(r[3]), groups=int(r[4]),
                  ctas=int(r[5]), rows=int(r[6]), us=[int(x) for x in r[7:rl]]) for r in recs]
+
+
+def autotune_elim_table() -> list:
+    """rss_autotune_elim_table: [{elem_bytes, width, phase_class, split, ctas, us: [5 candidates]}]."""
+    import numpy as np
+    nb = C.c_size_t(0)
+    _check(lib().rss_autotune_elim_table(None, C.byref(nb)))
+    buf = np.zeros(max(nb.value // 4, 1), dtype=np.int32)
+    _check(lib().rss_autotune_elim_table(C.c_void_p(buf.ctypes.data), C.byref(nb)))
+    recs = buf[:nb.value // 4].reshape(-1, 10)
+    return [dict(elem_bytes=int(r[0]), width=int(r[1]), phase_class=int(r[2]), split=int(r[3]), ctas=int(r[4]),
+                 us=[int(x) for x in r[5:10]]) for r in recs]
+
+
+ELIM_SHAPES = [(0, 1), (1, 1), (1, 2), (1, 4), (1, 8)]
 
 
 # (threads per column, fold groups, CTAs per box, panel rows per thread in

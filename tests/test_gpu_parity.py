@@ -406,6 +406,35 @@ def test_every_id_launch_shape_matches_oracle(pkg, prec):
     assert lib.rss_autotune_set(4, 64, 3, 2, 1, 1, 2) == pkg.rss.RSS_EINVAL  # two units of rows: one thread per column
 
 
+def test_elimination_shapes_match_oracle(pkg):
+    """The elimination autotuner's candidates (E and G in the LU's kernel, or
+    in a phase-wide product kernel with 1-8 CTAs per box): the first phase of
+    each key times them all, the factor is within 10 eps of the oracle, and a
+    second factorization with the choices recorded gives the same bits."""
+    pts = inputs.random_points(93, 3000, 2)  # boxes of width class 64 and 128
+    eps = 1e-6
+    of = oracle.Factor(oracle.Tree(pts, 64), 0, eps)
+    x = inputs.normal(96, len(pts))
+    yo = of.apply(x)
+    lib = pkg.lib()
+    lib.rss_autotune_clear()
+    try:
+        f1 = pkg.Factorization(_cuda(pts), 0, eps, leaf=64, prec=pkg.MIXED)
+        tab = pkg.autotune_elim_table()
+        assert tab, "no elimination entries after a factorization"
+        for e in tab:
+            assert (e["split"], e["ctas"]) in pkg.rss.ELIM_SHAPES
+            tried = [u for u in e["us"] if u > 0]
+            assert len(tried) == len(pkg.rss.ELIM_SHAPES)
+            assert e["us"][pkg.rss.ELIM_SHAPES.index((e["split"], e["ctas"]))] == min(tried)
+        y1 = f1.apply(_cuda(x))
+        assert np.linalg.norm(y1.cpu().numpy() - yo) / np.linalg.norm(yo) <= 10 * eps
+        f2 = pkg.Factorization(_cuda(pts), 0, eps, leaf=64, prec=pkg.MIXED)
+        assert torch.equal(f2.apply(_cuda(x)), y1)
+    finally:
+        lib.rss_autotune_clear()
+
+
 def test_wide_box_id_matches_oracle(pkg):
     """Boxes wider than 128 (an octree's upper level at eps 1e-3) take the ID
     kernel whose triangle is sized by the box; the factor matches the oracle
