@@ -3359,14 +3359,17 @@ constexpr int LB = 32;
 // updates them.  The row interchanges go to swp (local rows) and to the
 // permutation; k_lu_trsm applies them to the other columns.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, T *W, int *swp,
-                                                   int *err) {
+__global__ void __launch_bounds__(1024) k_lu_panel(T *A, int n, int kb, int nb, int *piv, T *Wg, int *swp,
+                                                   int *err, int in_smem) {
   constexpr int CH = sizeof(T) == 4 ? 16 : 8;  // panel entries a thread holds at once
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_val[32];
   __shared__ int s_idx[32];
   __shared__ T s_prow[LB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x / 32;
   const int h = n - kb;  // panel rows kb..n-1; W column-major, ld h
+  // the panel in shared memory when it fits, else in the global workspace
+  T *W = in_smem ? reinterpret_cast<T *>(smem_raw) : Wg;
   for (int e = tid; e < h * nb; e += blockDim.x) {
     const int i = e / nb, jj = e % nb;
     W[(int64_t)jj * h + i] = A[(int64_t)(kb + i) * n + kb + jj];
@@ -3505,7 +3508,18 @@ template <typename T> void launch_dense_lu(T *A, int n, int *piv, T *W, cudaStre
   for (int kb = 0; kb < n; kb += LB) {
     int nb = min(LB, n - kb);
     int *swp = reinterpret_cast<int *>(W + (int64_t)n * LB);
-    k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, W, swp, err); count_launch();
+    // the panel (n - kb rows x nb) in shared memory when it fits, and then
+    // a CTA of 256 threads (fewer warps at every barrier of the column steps)
+    const size_t psm = (size_t)(n - kb) * nb * sizeof(T);
+    const bool in_smem = psm <= (size_t)(160u << 10);
+    if (in_smem) {
+      if (!capturing(st))
+        cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
+      k_lu_panel<T><<<1, 256, psm, st>>>(A, n, kb, nb, piv, W, swp, err, 1);
+    } else {
+      k_lu_panel<T><<<1, 1024, 0, st>>>(A, n, kb, nb, piv, W, swp, err, 0);
+    }
+    count_launch();
     int rem = n - kb - nb;
     if (rem > 0 || kb > 0) {
       k_lu_trsm<T><<<(n + 127) / 128, 128, 0, st>>>(A, n, kb, nb, swp); count_launch();

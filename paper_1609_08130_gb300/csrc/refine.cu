@@ -37,12 +37,12 @@ __global__ void __launch_bounds__(256) k_fft_lines(double2 *data, int L, int log
   for (int p = 0; p < logL; p++) {
     const int half = L >> 1;
     for (int t = threadIdx.x; t < half; t += blockDim.x) {
-      int j = t % m;           // position inside the sub-transform
-      int k = t / m;           // which sub-transform pair
+      const int j = t & (m - 1);  // position inside the sub-transform (m = 2^p)
+      const int k = t >> p;       // which sub-transform pair
       double2 u = a[k * m + j];
       double2 v = a[k * m + j + half];
       // twiddle exp(sign * 2 pi i j / (2m)) = tw[j * (L / (2m))]^(sign)
-      double2 w = tw[j * (L / (2 * m))];
+      double2 w = tw[j << (logL - 1 - p)];  // j L / (2 m)
       if (sign > 0) w.y = -w.y;
       double2 vw = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
       b[2 * k * m + j] = make_double2(u.x + vw.x, u.y + vw.y);
