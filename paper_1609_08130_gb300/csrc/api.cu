@@ -2361,7 +2361,7 @@ template <typename T> static void apply_A_impl(const Factor<T> &F, const double 
       if (!F.grid_index.empty()) upload(F.g_gidx, F.grid_index, F.st);  // else detected on the device
       F.g_C.alloc(sizeof(double2) * tot, F.st);
       F.g_X.alloc(sizeof(double2) * tot, F.st);
-      F.g_tw.alloc(sizeof(double2) * (G.L / 2 + 1), F.st);
+      F.g_tw.alloc(sizeof(double2) * G.L, F.st);
       G.gidx = ptr<int64_t>(F.g_gidx);
       G.C = ptr<double2>(F.g_C);
       G.X = ptr<double2>(F.g_X);

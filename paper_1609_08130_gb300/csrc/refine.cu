@@ -18,7 +18,8 @@
 
 namespace rss {
 
-// One radix-2 Stockham FFT of length L (power of two, L <= 2048) per CTA
+// One Stockham FFT of length L (power of two, L <= 2048; radix 4, with one
+// radix-2 pass when log2 L is odd) per CTA
 // over lines of a complex array: line q starts at base(q) and has stride
 // `stride`; lines are enumerated as q = q0 + blockIdx.x.  sign = -1 forward,
 // +1 inverse (unscaled).
@@ -32,35 +33,62 @@ __global__ void __launch_bounds__(256) k_fft_lines(double2 *data, int L, int log
   const int64_t base = (q / line_div) * line_mul2 + (q % line_div) * line_mul;
   for (int i = threadIdx.x; i < L; i += blockDim.x) a[i] = data[base + (int64_t)i * stride];
   __syncthreads();
-  // Stockham autosort: pass p combines sub-transforms of length m = 2^p
-  int m = 1;
-  for (int p = 0; p < logL; p++) {
+  // Stockham autosort: a pass combines sub-transforms of length m = 2^lm
+  // into ones of length 2m (radix 2, once when log2 L is odd) or 4m (radix
+  // 4): output index (r k) m + j + q m from inputs k m + j + p L / r,
+  // twiddled by w_{r m}^{p j} (tw[x] = exp(-2 pi i x / L), conjugated for
+  // sign > 0) and combined by the r-point DFT
+  int lm = 0;
+  if (logL & 1) {
     const int half = L >> 1;
-    for (int t = threadIdx.x; t < half; t += blockDim.x) {
-      const int j = t & (m - 1);  // position inside the sub-transform (m = 2^p)
-      const int k = t >> p;       // which sub-transform pair
-      double2 u = a[k * m + j];
-      double2 v = a[k * m + j + half];
-      // twiddle exp(sign * 2 pi i j / (2m)) = tw[j * (L / (2m))]^(sign)
-      double2 w = tw[j << (logL - 1 - p)];  // j L / (2 m)
-      if (sign > 0) w.y = -w.y;
-      double2 vw = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
-      b[2 * k * m + j] = make_double2(u.x + vw.x, u.y + vw.y);
-      b[2 * k * m + j + m] = make_double2(u.x - vw.x, u.y - vw.y);
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {  // m = 1: no twiddle
+      const double2 u = a[t], v = a[t + half];
+      b[2 * t] = make_double2(u.x + v.x, u.y + v.y);
+      b[2 * t + 1] = make_double2(u.x - v.x, u.y - v.y);
     }
     __syncthreads();
     double2 *t0 = a;
     a = b;
     b = t0;
-    m <<= 1;
+    lm = 1;
+  }
+  const double sg = sign > 0 ? 1.0 : -1.0;
+  for (; lm < logL; lm += 2) {
+    const int m = 1 << lm, quarter = L >> 2, tsh = logL - lm - 2;
+    for (int t = threadIdx.x; t < quarter; t += blockDim.x) {
+      const int j = t & (m - 1), k = t >> lm;
+      const double2 a0 = a[t], a1 = a[t + quarter], a2 = a[t + 2 * quarter], a3 = a[t + 3 * quarter];
+      double2 w1 = tw[j << tsh], w2 = tw[(2 * j) << tsh], w3 = tw[(3 * j) << tsh];
+      if (sign > 0) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+        w3.y = -w3.y;
+      }
+      const double2 c1 = make_double2(fma(a1.x, w1.x, -a1.y * w1.y), fma(a1.x, w1.y, a1.y * w1.x));
+      const double2 c2 = make_double2(fma(a2.x, w2.x, -a2.y * w2.y), fma(a2.x, w2.y, a2.y * w2.x));
+      const double2 c3 = make_double2(fma(a3.x, w3.x, -a3.y * w3.y), fma(a3.x, w3.y, a3.y * w3.x));
+      const double2 t0 = make_double2(a0.x + c2.x, a0.y + c2.y), t1 = make_double2(a0.x - c2.x, a0.y - c2.y);
+      const double2 t2 = make_double2(c1.x + c3.x, c1.y + c3.y);
+      // (c1 - c3) times w_4 = sign i
+      const double2 t3 = make_double2(-sg * (c1.y - c3.y), sg * (c1.x - c3.x));
+      const int o = (k << (lm + 2)) + j;
+      b[o] = make_double2(t0.x + t2.x, t0.y + t2.y);
+      b[o + m] = make_double2(t1.x + t3.x, t1.y + t3.y);
+      b[o + 2 * m] = make_double2(t0.x - t2.x, t0.y - t2.y);
+      b[o + 3 * m] = make_double2(t1.x - t3.x, t1.y - t3.y);
+    }
+    __syncthreads();
+    double2 *t0 = a;
+    a = b;
+    b = t0;
   }
   for (int i = threadIdx.x; i < L; i += blockDim.x) data[base + (int64_t)i * stride] = a[i];
 }
 
-// tw[k] = exp(-2 pi i k / L), k < L/2
+// tw[k] = exp(-2 pi i k / L), k < L (a radix-4 pass reads up to 3L/4)
 __global__ void k_twiddle(double2 *tw, int L) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= L / 2) return;
+  if (k >= L) return;
   double s, c;
   sincospi(-2.0 * (double)k / (double)L, &s, &c);
   tw[k] = make_double2(c, s);
@@ -163,7 +191,7 @@ void grid_op_setup(GridOp &G, cudaStream_t st) {
   int64_t tot = 1;
   for (int d = 0; d < G.dim; d++) tot *= G.L;
   cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * G.L * (int)sizeof(double2));
-  k_twiddle<<<(G.L / 2 + 255) / 256, 256, 0, st>>>(G.tw, G.L); count_launch();
+  k_twiddle<<<(G.L + 255) / 256, 256, 0, st>>>(G.tw, G.L); count_launch();
   k_embed_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(G.C, G.dim, G.s, G.L, G.h, G.kind, G.w); count_launch();
   fft_nd(G.C, G.dim, G.L, G.logL, G.tw, -1, st);
 }
