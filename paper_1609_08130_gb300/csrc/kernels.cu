@@ -31,6 +31,7 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 constexpr int NT = 256;  // threads per CTA for the per-box kernels
+constexpr int SWEEP_TROWS = 4;  // rows of T^T v_S a warp of the forward sweep forms at once
 
 // Kernel attributes are set outside stream capture only (a captured launch
 // reuses the attribute set by an earlier uncaptured one).
@@ -3724,42 +3725,50 @@ __global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const in
   T *part = tmp + (size_t)r * NR;            // partial sums of X_RR^{-1} tmp
   sweep_gather<T, NR>(fb, v, vS, vR);
   __syncthreads();
-  for (int ri = warp; ri < r; ri += NT / 32) {
-    const T *tc = fb.Tm + (int64_t)ri * k;
-    T acc[NR];
+  // tmp = v_R - T^T v_S: a warp per SWEEP_TROWS rows at once, so that the
+  // loads of all of them are in flight together
+  for (int ri0 = warp * SWEEP_TROWS; ri0 < r; ri0 += (NT / 32) * SWEEP_TROWS) {
+    T acc[SWEEP_TROWS][NR];
 #pragma unroll
-    for (int c = 0; c < NR; c++) acc[c] = (T)0;
+    for (int u = 0; u < SWEEP_TROWS; u++)
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[u][c] = (T)0;
     for (int q = lane; q < k; q += 32) {
-      const T tq = tc[q];
+      T tq[SWEEP_TROWS];
 #pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] += tq * vS[q * NR + c];
+      for (int u = 0; u < SWEEP_TROWS; u++) tq[u] = ri0 + u < r ? __ldg(fb.Tm + q + (int64_t)(ri0 + u) * k) : (T)0;
+#pragma unroll
+      for (int u = 0; u < SWEEP_TROWS; u++)
+#pragma unroll
+        for (int c = 0; c < NR; c++) acc[u][c] += tq[u] * vS[q * NR + c];
     }
 #pragma unroll
-    for (int c = 0; c < NR; c++) acc[c] = warp_sum(acc[c]);
+    for (int u = 0; u < SWEEP_TROWS; u++)
+#pragma unroll
+      for (int c = 0; c < NR; c++) acc[u][c] = warp_sum(acc[u][c]);
     if (lane == 0)
 #pragma unroll
-      for (int c = 0; c < NR; c++) tmp[ri * NR + c] = vR[ri * NR + c] - acc[c];
+      for (int u = 0; u < SWEEP_TROWS; u++)
+        if (ri0 + u < r)
+#pragma unroll
+          for (int c = 0; c < NR; c++) tmp[(ri0 + u) * NR + c] = vR[(ri0 + u) * NR + c] - acc[u][c];
   }
   __syncthreads();
-  // rows of E: two threads per row, each over alternate columns; every lane
-  // of the warp calls this (valid or not) for the final shuffle
+  // rows of E: two threads per row, each over alternate columns, eight
+  // loads in flight (the last group predicated); every lane of the warp
+  // calls this (valid or not) for the final shuffle
   auto erow = [&](int a, bool valid, T *acc) {
     const T *ea = fb.E + a;
     const int h = tid & 1;
-    int ri = valid ? h : r;
-    for (; ri + 14 < r; ri += 16) {
+    for (int ri = valid ? h : r; ri < r; ri += 16) {
       T ev[8];
 #pragma unroll
-      for (int u = 0; u < 8; u++) ev[u] = __ldg(ea + (int64_t)(ri + 2 * u) * nj);
+      for (int u = 0; u < 8; u++) ev[u] = ri + 2 * u < r ? __ldg(ea + (int64_t)(ri + 2 * u) * nj) : (T)0;
 #pragma unroll
       for (int u = 0; u < 8; u++)
+        if (ri + 2 * u < r)
 #pragma unroll
-        for (int c = 0; c < NR; c++) acc[c] += ev[u] * tmp[(ri + 2 * u) * NR + c];
-    }
-    for (; ri < r; ri += 2) {
-      const T ev = __ldg(ea + (int64_t)ri * nj);
-#pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] += ev * tmp[ri * NR + c];
+          for (int c = 0; c < NR; c++) acc[c] += ev[u] * tmp[(ri + 2 * u) * NR + c];
     }
 #pragma unroll
     for (int c = 0; c < NR; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
@@ -3811,10 +3820,15 @@ __global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const in
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      for (int l = g; l < r; l += nch) {
-        const T xv = __ldg(fb.Xi + i + (int64_t)l * r);
+      for (int l = g; l < r; l += 8 * nch) {
+        T xv[8];
 #pragma unroll
-        for (int c = 0; c < NR; c++) acc[c] += xv * tmp[l * NR + c];
+        for (int u = 0; u < 8; u++) xv[u] = l + u * nch < r ? __ldg(fb.Xi + i + (int64_t)(l + u * nch) * r) : (T)0;
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          if (l + u * nch < r)
+#pragma unroll
+            for (int c = 0; c < NR; c++) acc[c] += xv[u] * tmp[(l + u * nch) * NR + c];
       }
 #pragma unroll
       for (int c = 0; c < NR; c++) part[((size_t)g * r + i) * NR + c] = acc[c];
@@ -3845,9 +3859,16 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
   const int k = fb.k, r = fb.r, nj = fb.nj;
   const int tid = threadIdx.x;
   T *part = reinterpret_cast<T *>(smem_raw);  // nch x r x NR, then vS, vR for the last CTA
-  const int a0 = ch * SWEEP_CHUNK, a1 = min(nj, a0 + SWEEP_CHUNK);
+  T *vJc = part + (size_t)NT * NR;             // this chunk's entries of v_J
+  const int a0 = ch * SWEEP_CHUNK, a1 = min(nj, a0 + SWEEP_CHUNK), na = a1 - a0;
   const int nch = r >= NT ? 1 : NT / r;
   T *pb = pbuf + poff[bi] + (int64_t)ch * r * NR;
+  // G(i, a) = gq[i * gsi + a * gsa]: the stored G, or E^T under symmetric storage
+  const T *gq = fb.G ? fb.G : fb.E;
+  const int64_t gsi = fb.G ? 1 : nj, gsa = fb.G ? r : 1;
+  // the chunk's v_J gathered once, all loads in flight together
+  for (int e = tid; e < na * NR; e += NT) vJc[e] = v[fb.J[a0 + e / NR] * NR + e % NR];
+  __syncthreads();
   for (int i0 = 0; i0 < r; i0 += NT) {
     const int rr = r >= NT ? NT : r;
     const int i = i0 + tid % rr, g = tid / rr;
@@ -3855,25 +3876,16 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      int a = a0 + g;
-      for (; a + 3 * nch < a1; a += 4 * nch) {
-        T gv[4];
-        int64_t ja[4];
+      const T *gi = gq + i * gsi + a0 * gsa;
+      for (int a = g; a < na; a += 8 * nch) {
+        T gv[8];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          gv[u] = gval(fb, i, a + u * nch);
-          ja[u] = fb.J[a + u * nch];
-        }
+        for (int u = 0; u < 8; u++) gv[u] = a + u * nch < na ? __ldg(gi + (a + u * nch) * gsa) : (T)0;
 #pragma unroll
-        for (int u = 0; u < 4; u++)
+        for (int u = 0; u < 8; u++)
+          if (a + u * nch < na)
 #pragma unroll
-          for (int c = 0; c < NR; c++) acc[c] += gv[u] * v[ja[u] * NR + c];
-      }
-      for (; a < a1; a += nch) {
-        const T gv = gval(fb, i, a);
-        const int64_t ja = fb.J[a];
-#pragma unroll
-        for (int c = 0; c < NR; c++) acc[c] += gv * v[ja * NR + c];
+            for (int c = 0; c < NR; c++) acc[c] += gv[u] * vJc[(a + u * nch) * NR + c];
       }
 #pragma unroll
       for (int c = 0; c < NR; c++) part[((size_t)g * rr + (i - i0)) * NR + c] = acc[c];
@@ -3907,18 +3919,39 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
     vR[e] -= sum;
   }
   __syncthreads();
-  for (int q = tid; q < k; q += NT) {
-    T acc[NR];
+  // v_S -= T v_R: the columns of T split over nq groups of threads (eight
+  // loads in flight each), the groups' partial sums added in group order
+  if (k > 0) {
+    const int kk = k >= NT ? NT : k, nq = k >= NT ? 1 : NT / k;
+    T *tp = part + (size_t)(k + r) * NR;  // nq x kk x NR partial sums
+    for (int q0 = 0; q0 < k; q0 += NT) {
+      const int q = q0 + tid % kk, g = tid / kk;
+      if (q < k && g < nq) {
+        T acc[NR];
 #pragma unroll
-    for (int c = 0; c < NR; c++) acc[c] = (T)0;
-    for (int ri = 0; ri < r; ri++) {
-      const T tv = __ldg(fb.Tm + q + (int64_t)ri * k);
+        for (int c = 0; c < NR; c++) acc[c] = (T)0;
+        for (int ri = g; ri < r; ri += 8 * nq) {
+          T tv[8];
 #pragma unroll
-      for (int c = 0; c < NR; c++) acc[c] += tv * vR[ri * NR + c];
+          for (int u = 0; u < 8; u++) tv[u] = ri + u * nq < r ? __ldg(fb.Tm + q + (int64_t)(ri + u * nq) * k) : (T)0;
+#pragma unroll
+          for (int u = 0; u < 8; u++)
+            if (ri + u * nq < r)
+#pragma unroll
+              for (int c = 0; c < NR; c++) acc[c] += tv[u] * vR[(ri + u * nq) * NR + c];
+        }
+#pragma unroll
+        for (int c = 0; c < NR; c++) tp[((size_t)g * kk + (q - q0)) * NR + c] = acc[c];
+      }
+      __syncthreads();
+      for (int e = tid; e < min(kk, k - q0) * NR; e += NT) {
+        const int ql = e / NR, c = e % NR;
+        T sum = (T)0;
+        for (int g2 = 0; g2 < nq; g2++) sum += tp[((size_t)g2 * kk + ql) * NR + c];
+        v[fb.ids[q0 + ql] * NR + c] = vS[(q0 + ql) * NR + c] - sum;
+      }
+      __syncthreads();
     }
-    T *vg = v + fb.ids[q] * NR;
-#pragma unroll
-    for (int c = 0; c < NR; c++) vg[c] = vS[q * NR + c] - acc[c];
   }
   for (int e = tid; e < r * NR; e += NT) v[fb.ids[k + e / NR] * NR + e % NR] = vR[e];
 }
@@ -3927,7 +3960,7 @@ template <typename T>
 void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const int *wchunk, int nwork, T *v,
                          int nrhs, int bmax, int *cnt, T *pbuf, const int64_t *poff, cudaStream_t st, int shared) {
   if (nwork == 0) return;
-  const size_t smem = ((size_t)4 * bmax + NT) * nrhs * sizeof(T) + 64;
+  const size_t smem = sweep_chunk_smem(bmax, nrhs, (int)sizeof(T));
   constexpr int SMAX = (200 << 10) + 64;  // callers keep smem within this
 #define RSS_SWEEP_NR(NRV)                                                                                   \
   case NRV:                                                                                                \
@@ -3949,7 +3982,9 @@ void launch_sweep_chunks(int mode, const FBox<T> *boxes, const int *wbox, const 
   count_launch();
 }
 
-size_t sweep_chunk_smem(int bmax, int nrhs, int elem) { return ((size_t)4 * bmax + NT) * nrhs * elem + 64; }
+size_t sweep_chunk_smem(int bmax, int nrhs, int elem) {
+  return ((size_t)4 * bmax + NT + SWEEP_CHUNK) * nrhs * elem + 64;
+}
 
 template <typename T>
 void launch_sweep(int mode, const FBox<T> *boxes, int first, int count, T *v, int nrhs, int bmax, int njmax,
