@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -32,6 +33,7 @@ long long launches_total() { return g_launches.load(std::memory_order_relaxed); 
 
 constexpr int NT = 256;  // threads per CTA for the per-box kernels
 constexpr int SWEEP_TROWS = 4;  // rows of T^T v_S a warp of the forward sweep forms at once
+constexpr int SWEEP_MLP = 8;    // independent loads a sweep thread keeps in flight
 
 // Kernel attributes are set outside stream capture only (a captured launch
 // reuses the attribute set by an earlier uncaptured one).
@@ -2298,49 +2300,91 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
 // for the Schur update.
 // ---------------------------------------------------------------------------
 
-// C (m x n) = A (m x K) B (K x n) from shared memory with a 2 x 4 register
-// tile per thread (256 threads as 16 x 16, a 32 x 64 block per pass);
+// C (m x n) = A (m x K) B (K x n) from shared memory, 256 threads as 16 x 16
+// with an MX x NY register tile each (a 16 MX x 16 NY block per pass);
 // A(i,l) = A[i*sai + l*sal], B(l,j) = B[l*sbl + j*sbj]; each result goes
-// to out(i, j, value).
+// to out(i, j, value).  In single precision pairs of columns share one
+// paired FMA (two correctly rounded FMAs, so the sums are those of the
+// scalar form: l ascending, one fused multiply-add per term).
+template <typename T, int MX, int NY, typename Out>
+__device__ __forceinline__ void smem_gemm_blk(int m, int n, int K, const T *A, int sai, int sal, const T *B, int sbl,
+                                              int sbj, Out out) {
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  for (int i0 = 0; i0 < m; i0 += 16 * MX)
+    for (int j0 = 0; j0 < n; j0 += 16 * NY) {
+      bool rv[MX], cv[NY];
+#pragma unroll
+      for (int x = 0; x < MX; x++) rv[x] = i0 + ti + 16 * x < m;
+#pragma unroll
+      for (int y = 0; y < NY; y++) cv[y] = j0 + tj + 16 * y < n;
+      // rows and columns past the matrix read row / column 0 (their
+      // products are never stored), so the loads need no predicate
+      const T *ap[MX], *bp[NY];
+#pragma unroll
+      for (int x = 0; x < MX; x++) ap[x] = A + (rv[x] ? (i0 + ti + 16 * x) * sai : 0);
+#pragma unroll
+      for (int y = 0; y < NY; y++) bp[y] = B + (cv[y] ? (j0 + tj + 16 * y) * sbj : 0);
+      T acc[MX][NY];
+      if constexpr (std::is_same<T, float>::value && NY % 2 == 0) {
+        float2 a2[MX][NY / 2];
+#pragma unroll
+        for (int x = 0; x < MX; x++)
+#pragma unroll
+          for (int y = 0; y < NY / 2; y++) a2[x][y] = make_float2(0.f, 0.f);
+        for (int l = 0; l < K; l++) {
+          float a[MX], bb[NY];
+#pragma unroll
+          for (int x = 0; x < MX; x++) a[x] = ap[x][l * sal];
+#pragma unroll
+          for (int y = 0; y < NY; y++) bb[y] = bp[y][l * sbl];
+#pragma unroll
+          for (int x = 0; x < MX; x++)
+#pragma unroll
+            for (int y = 0; y < NY / 2; y++)
+              a2[x][y] = __ffma2_rn(make_float2(a[x], a[x]), make_float2(bb[2 * y], bb[2 * y + 1]), a2[x][y]);
+        }
+#pragma unroll
+        for (int x = 0; x < MX; x++)
+#pragma unroll
+          for (int y = 0; y < NY / 2; y++) {
+            acc[x][2 * y] = a2[x][y].x;
+            acc[x][2 * y + 1] = a2[x][y].y;
+          }
+      } else {
+#pragma unroll
+        for (int x = 0; x < MX; x++)
+#pragma unroll
+          for (int y = 0; y < NY; y++) acc[x][y] = (T)0;
+        for (int l = 0; l < K; l++) {
+          T a[MX], bb[NY];
+#pragma unroll
+          for (int x = 0; x < MX; x++) a[x] = ap[x][l * sal];
+#pragma unroll
+          for (int y = 0; y < NY; y++) bb[y] = bp[y][l * sbl];
+#pragma unroll
+          for (int x = 0; x < MX; x++)
+#pragma unroll
+            for (int y = 0; y < NY; y++) acc[x][y] += a[x] * bb[y];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < MX; x++)
+#pragma unroll
+        for (int y = 0; y < NY; y++)
+          if (rv[x] && cv[y]) out(i0 + ti + 16 * x, j0 + tj + 16 * y, acc[x][y]);
+    }
+}
+
+// The block shape (32 x 64 or 64 x 32) that covers m x n in fewer passes;
+// every call of a CTA takes the same branch (m, n are uniform).
 template <typename T, typename Out>
 __device__ __forceinline__ void smem_gemm(int m, int n, int K, const T *A, int sai, int sal, const T *B, int sbl,
                                           int sbj, Out out) {
-  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-  for (int i0 = 0; i0 < m; i0 += 32)
-    for (int j0 = 0; j0 < n; j0 += 64) {
-      T acc[2][4];
-#pragma unroll
-      for (int x = 0; x < 2; x++)
-#pragma unroll
-        for (int y = 0; y < 4; y++) acc[x][y] = (T)0;
-      const bool rv[2] = {i0 + ti < m, i0 + ti + 16 < m};
-      bool cv[4];
-#pragma unroll
-      for (int y = 0; y < 4; y++) cv[y] = j0 + tj + 16 * y < n;
-      // rows and columns past the matrix read row / column 0 (their
-      // products are never stored), so the loads need no predicate
-      const T *ap[2], *bp[4];
-#pragma unroll
-      for (int x = 0; x < 2; x++) ap[x] = A + (rv[x] ? (i0 + ti + 16 * x) * sai : 0);
-#pragma unroll
-      for (int y = 0; y < 4; y++) bp[y] = B + (cv[y] ? (j0 + tj + 16 * y) * sbj : 0);
-      for (int l = 0; l < K; l++) {
-        T a[2], bb[4];
-#pragma unroll
-        for (int x = 0; x < 2; x++) a[x] = ap[x][l * sal];
-#pragma unroll
-        for (int y = 0; y < 4; y++) bb[y] = bp[y][l * sbl];
-#pragma unroll
-        for (int x = 0; x < 2; x++)
-#pragma unroll
-          for (int y = 0; y < 4; y++) acc[x][y] += a[x] * bb[y];
-      }
-#pragma unroll
-      for (int x = 0; x < 2; x++)
-#pragma unroll
-        for (int y = 0; y < 4; y++)
-          if (rv[x] && cv[y]) out(i0 + ti + 16 * x, j0 + tj + 16 * y, acc[x][y]);
-    }
+  const int p24 = ((m + 31) >> 5) * ((n + 63) >> 6), p42 = ((m + 63) >> 6) * ((n + 31) >> 5);
+  if (p42 < p24)
+    smem_gemm_blk<T, 4, 2>(m, n, K, A, sai, sal, B, sbl, sbj, out);
+  else
+    smem_gemm_blk<T, 2, 4>(m, n, K, A, sai, sal, B, sbl, sbj, out);
 }
 
 template <typename T> struct ElimChunk;
@@ -3754,18 +3798,18 @@ __global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const in
           for (int c = 0; c < NR; c++) tmp[(ri0 + u) * NR + c] = vR[(ri0 + u) * NR + c] - acc[u][c];
   }
   __syncthreads();
-  // rows of E: two threads per row, each over alternate columns, eight
+  // rows of E: two threads per row, each over alternate columns, SWEEP_MLP
   // loads in flight (the last group predicated); every lane of the warp
   // calls this (valid or not) for the final shuffle
   auto erow = [&](int a, bool valid, T *acc) {
     const T *ea = fb.E + a;
     const int h = tid & 1;
-    for (int ri = valid ? h : r; ri < r; ri += 16) {
-      T ev[8];
+    for (int ri = valid ? h : r; ri < r; ri += 2 * SWEEP_MLP) {
+      T ev[SWEEP_MLP];
 #pragma unroll
-      for (int u = 0; u < 8; u++) ev[u] = ri + 2 * u < r ? __ldg(ea + (int64_t)(ri + 2 * u) * nj) : (T)0;
+      for (int u = 0; u < SWEEP_MLP; u++) ev[u] = ri + 2 * u < r ? __ldg(ea + (int64_t)(ri + 2 * u) * nj) : (T)0;
 #pragma unroll
-      for (int u = 0; u < 8; u++)
+      for (int u = 0; u < SWEEP_MLP; u++)
         if (ri + 2 * u < r)
 #pragma unroll
           for (int c = 0; c < NR; c++) acc[c] += ev[u] * tmp[(ri + 2 * u) * NR + c];
@@ -3820,12 +3864,12 @@ __global__ void __launch_bounds__(NT) k_sweep_fwd(const FBox<T> *boxes, const in
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; c++) acc[c] = (T)0;
-      for (int l = g; l < r; l += 8 * nch) {
-        T xv[8];
+      for (int l = g; l < r; l += SWEEP_MLP * nch) {
+        T xv[SWEEP_MLP];
 #pragma unroll
-        for (int u = 0; u < 8; u++) xv[u] = l + u * nch < r ? __ldg(fb.Xi + i + (int64_t)(l + u * nch) * r) : (T)0;
+        for (int u = 0; u < SWEEP_MLP; u++) xv[u] = l + u * nch < r ? __ldg(fb.Xi + i + (int64_t)(l + u * nch) * r) : (T)0;
 #pragma unroll
-        for (int u = 0; u < 8; u++)
+        for (int u = 0; u < SWEEP_MLP; u++)
           if (l + u * nch < r)
 #pragma unroll
             for (int c = 0; c < NR; c++) acc[c] += xv[u] * tmp[(l + u * nch) * NR + c];
@@ -3877,12 +3921,12 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
 #pragma unroll
       for (int c = 0; c < NR; c++) acc[c] = (T)0;
       const T *gi = gq + i * gsi + a0 * gsa;
-      for (int a = g; a < na; a += 8 * nch) {
-        T gv[8];
+      for (int a = g; a < na; a += SWEEP_MLP * nch) {
+        T gv[SWEEP_MLP];
 #pragma unroll
-        for (int u = 0; u < 8; u++) gv[u] = a + u * nch < na ? __ldg(gi + (a + u * nch) * gsa) : (T)0;
+        for (int u = 0; u < SWEEP_MLP; u++) gv[u] = a + u * nch < na ? __ldg(gi + (a + u * nch) * gsa) : (T)0;
 #pragma unroll
-        for (int u = 0; u < 8; u++)
+        for (int u = 0; u < SWEEP_MLP; u++)
           if (a + u * nch < na)
 #pragma unroll
             for (int c = 0; c < NR; c++) acc[c] += gv[u] * vJc[(a + u * nch) * NR + c];
@@ -3919,8 +3963,8 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
     vR[e] -= sum;
   }
   __syncthreads();
-  // v_S -= T v_R: the columns of T split over nq groups of threads (eight
-  // loads in flight each), the groups' partial sums added in group order
+  // v_S -= T v_R: the columns of T split over nq groups of threads
+  // (SWEEP_MLP loads in flight each), the groups' partial sums added in group order
   if (k > 0) {
     const int kk = k >= NT ? NT : k, nq = k >= NT ? 1 : NT / k;
     T *tp = part + (size_t)(k + r) * NR;  // nq x kk x NR partial sums
@@ -3930,12 +3974,12 @@ __global__ void __launch_bounds__(NT) k_sweep_bwd(const FBox<T> *boxes, const in
         T acc[NR];
 #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] = (T)0;
-        for (int ri = g; ri < r; ri += 8 * nq) {
-          T tv[8];
+        for (int ri = g; ri < r; ri += SWEEP_MLP * nq) {
+          T tv[SWEEP_MLP];
 #pragma unroll
-          for (int u = 0; u < 8; u++) tv[u] = ri + u * nq < r ? __ldg(fb.Tm + q + (int64_t)(ri + u * nq) * k) : (T)0;
+          for (int u = 0; u < SWEEP_MLP; u++) tv[u] = ri + u * nq < r ? __ldg(fb.Tm + q + (int64_t)(ri + u * nq) * k) : (T)0;
 #pragma unroll
-          for (int u = 0; u < 8; u++)
+          for (int u = 0; u < SWEEP_MLP; u++)
             if (ri + u * nq < r)
 #pragma unroll
               for (int c = 0; c < NR; c++) acc[c] += tv[u] * vR[(ri + u * nq) * NR + c];
