@@ -2302,13 +2302,18 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
 
 // C (m x n) = A (m x K) B (K x n) from shared memory, 256 threads as 16 x 16
 // with an MX x NY register tile each (a 16 MX x 16 NY block per pass);
-// A(i,l) = A[i*sai + l*sal], B(l,j) = B[l*sbl + j*sbj]; each result goes
-// to out(i, j, value).  In single precision pairs of columns share one
-// paired FMA (two correctly rounded FMAs, so the sums are those of the
-// scalar form: l ascending, one fused multiply-add per term).
-template <typename T, int MX, int NY, typename Out>
-__device__ __forceinline__ void smem_gemm_blk(int m, int n, int K, const T *A, int sai, int sal, const T *B, int sbl,
+// A(i,l) = A[i*sai + l*sal], B(l,j) = B[l + j*sbj] (B is contiguous along
+// l); each result goes to out(i, j, value).  A's unit stride (AU = 1: sai
+// is 1, AU = 2: sal is 1) is a template argument so that the loads of a
+// thread address one register plus constant offsets.  In single precision
+// pairs of columns share one paired FMA (two correctly rounded FMAs, so the
+// sums are those of the scalar form: l ascending, one fused multiply-add
+// per term).
+template <typename T, int MX, int NY, int AU, typename Out>
+__device__ __forceinline__ void smem_gemm_blk(int m, int n, int K, const T *A, int sai_, int sal_, const T *B,
                                               int sbj, Out out) {
+  static_assert(AU == 1 || AU == 2, "A must be unit-stride along i or l");
+  const int sai = AU == 1 ? 1 : sai_, sal = AU == 2 ? 1 : sal_, sbl = 1;
   const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
   for (int i0 = 0; i0 < m; i0 += 16 * MX)
     for (int j0 = 0; j0 < n; j0 += 16 * NY) {
@@ -2331,6 +2336,7 @@ __device__ __forceinline__ void smem_gemm_blk(int m, int n, int K, const T *A, i
         for (int x = 0; x < MX; x++)
 #pragma unroll
           for (int y = 0; y < NY / 2; y++) a2[x][y] = make_float2(0.f, 0.f);
+#pragma unroll 4
         for (int l = 0; l < K; l++) {
           float a[MX], bb[NY];
 #pragma unroll
@@ -2355,6 +2361,7 @@ __device__ __forceinline__ void smem_gemm_blk(int m, int n, int K, const T *A, i
         for (int x = 0; x < MX; x++)
 #pragma unroll
           for (int y = 0; y < NY; y++) acc[x][y] = (T)0;
+#pragma unroll 4
         for (int l = 0; l < K; l++) {
           T a[MX], bb[NY];
 #pragma unroll
@@ -2377,14 +2384,14 @@ __device__ __forceinline__ void smem_gemm_blk(int m, int n, int K, const T *A, i
 
 // The block shape (32 x 64 or 64 x 32) that covers m x n in fewer passes;
 // every call of a CTA takes the same branch (m, n are uniform).
-template <typename T, typename Out>
-__device__ __forceinline__ void smem_gemm(int m, int n, int K, const T *A, int sai, int sal, const T *B, int sbl,
-                                          int sbj, Out out) {
+template <typename T, int AU, typename Out>
+__device__ __forceinline__ void smem_gemm(int m, int n, int K, const T *A, int sai, int sal, const T *B, int sbj,
+                                          Out out) {
   const int p24 = ((m + 31) >> 5) * ((n + 63) >> 6), p42 = ((m + 63) >> 6) * ((n + 31) >> 5);
   if (p42 < p24)
-    smem_gemm_blk<T, 4, 2>(m, n, K, A, sai, sal, B, sbl, sbj, out);
+    smem_gemm_blk<T, 4, 2, AU>(m, n, K, A, sai, sal, B, sbj, out);
   else
-    smem_gemm_blk<T, 2, 4>(m, n, K, A, sai, sal, B, sbl, sbj, out);
+    smem_gemm_blk<T, 2, 4, AU>(m, n, K, A, sai, sal, B, sbj, out);
 }
 
 template <typename T> struct ElimChunk;
@@ -2522,15 +2529,15 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   {
     T *xrs = XRS, *xsr = XSR, *lu = LU;
     const int rr = r, kk = k, ll = ldl;
-    smem_gemm<T>(r, k, k, Ts, k, 1, Ab, 1, ldb, [&](int ri, int s2, T v) { xrs[ri + s2 * rr] -= v; });
-    smem_gemm<T>(k, r, k, Ab, 1, ldb, Ts, 1, k, [&](int s2, int ri, T v) { xsr[s2 + ri * kk] -= v; });
-    smem_gemm<T>(r, r, k, Ts, k, 1, Ab + (size_t)k * ldb, 1, ldb, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
+    smem_gemm<T, 2>(r, k, k, Ts, k, 1, Ab, ldb, [&](int ri, int s2, T v) { xrs[ri + s2 * rr] -= v; });
+    smem_gemm<T, 1>(k, r, k, Ab, 1, ldb, Ts, k, [&](int s2, int ri, T v) { xsr[s2 + ri * kk] -= v; });
+    smem_gemm<T, 2>(r, r, k, Ts, k, 1, Ab + (size_t)k * ldb, ldb, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
   }
   __syncthreads();
   {
     T *lu = LU;
     const int ll = ldl;
-    smem_gemm<T>(r, r, k, XRS, 1, r, Ts, 1, k, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
+    smem_gemm<T, 1>(r, r, k, XRS, 1, r, Ts, k, [&](int ri, int rj, T v) { lu[ri * ll + rj] -= v; });
   }
   __syncthreads();
   if (cta == 0) {
@@ -2729,10 +2736,10 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       T *rJ = rawJ;
       T *rC = rawC;
       const int kk = k, aa0 = a0;
-      smem_gemm<T>(na, r, k, rawJ, 1, ldj, Ts, 1, k, [&](int al, int ri, T v) {
+      smem_gemm<T, 1>(na, r, k, rawJ, 1, ldj, Ts, k, [&](int al, int ri, T v) {
         if (aa0 + al >= kk) rJ[al + (kk + ri) * ldj] -= v;
       });
-      smem_gemm<T>(r, na, k, Ts, k, 1, rawC, 1, ldb, [&](int ri, int al, T v) {
+      smem_gemm<T, 2>(r, na, k, Ts, k, 1, rawC, ldb, [&](int ri, int al, T v) {
         if (aa0 + al >= kk) rC[(kk + ri) + al * ldb] -= v;
       });
     }
@@ -2757,11 +2764,11 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
     {
       T *Eo = fb.E, *Go = fb.G;
       const int njj = nj, rr = r, aa0 = a0;
-      smem_gemm<T>(na, r, r, rawJ + (size_t)k * (CH + 1), 1, CH + 1, Xi, 1, ldx, [&](int al, int ri, T v) {
+      smem_gemm<T, 1>(na, r, r, rawJ + (size_t)k * (CH + 1), 1, CH + 1, Xi, ldx, [&](int al, int ri, T v) {
         Eo[(aa0 + al) + (int64_t)ri * njj] = v;
       });
       if (Go)  // uniform over the CTA; symmetric storage keeps no G
-        smem_gemm<T>(r, na, r, Xi, 1, ldx, rawC + k, 1, ldb, [&](int ri, int al, T v) {
+        smem_gemm<T, 1>(r, na, r, Xi, 1, ldx, rawC + k, ldb, [&](int ri, int al, T v) {
           Go[ri + (int64_t)(aa0 + al) * rr] = v;
         });
     }
