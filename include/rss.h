@@ -223,7 +223,8 @@ rss_status rss_solve_noalloc(const rss_factorization *f, const double *b, double
  * (Carson & Higham): x0 = F^{-1} b, then FP64 residuals with the exact
  * operator (rss_matvec) and corrections from restarted FGMRES(10) in FP64,
  * right-preconditioned by the factor's solve (which runs in FP32 for a
- * RSS_MIXED factor).  The paper uses F as a CG preconditioner instead
+ * RSS_MIXED factor; for such a factor FGMRES's operator products are FP32
+ * too, on FP64 vectors, while the residuals and the update stay FP64).  The paper uses F as a CG preconditioner instead
  * (Sec. 4); GMRES is used here because a FP32 factor is not symmetric to
  * FP64 accuracy.
  *   b, x: device, n x nrhs column-major, may not alias.  maxit: outer
@@ -315,10 +316,11 @@ rss_status rss_stats_json(const rss_factorization *f, char *buf, size_t *nbytes)
 
 /* rss_profile -- per-kernel-class totals of a factor created with
  * options.profile = 1, accumulated over rss_factor and every later
- * rss_apply / rss_solve on it, into a HOST double array of 4 * 12 entries:
+ * rss_apply / rss_solve on it, into a HOST double array of 4 * 13 entries:
  * for class c in {0 assemble, 1 id, 2 elim, 3 schur, 4 top LU, 5 sweep,
  * 6 top solve/multiply, 7 permute, 8 host tree build, 9 host level build,
- * 10 host wait at level end, 11 FP64 residual operator}: {launches or calls,
+ * 10 host wait at level end, 11 FP64 residual operator, 12 FP32 operator
+ * products inside the refinement's GMRES}: {launches or calls,
  * milliseconds (CUDA events on the launching stream; host wall time for the
  * host classes), algorithmic bytes, algorithmic flops}.  The algorithmic
  * counts are the data the method must move or compute (stated per class in

@@ -787,7 +787,7 @@ struct Phase {
 // boxes it handled are known).
 enum KClass {
   KC_ASSEMBLE, KC_ID, KC_ELIM, KC_SCHUR, KC_TOPLU, KC_SWEEP, KC_TOP, KC_PERMUTE,
-  KC_HOST_TREE, KC_HOST_LEVEL, KC_HOST_WAIT, KC_REFINE_OP, KC_N
+  KC_HOST_TREE, KC_HOST_LEVEL, KC_HOST_WAIT, KC_REFINE_OP, KC_INNER_OP, KC_N
 };
 
 struct ProfRec {
@@ -908,7 +908,8 @@ template <typename T> struct Factor : FactorBase {
   std::vector<int64_t> grid_index;  // caller order
   mutable GridOp G;
   mutable DBuf g_gidx, g_C, g_X, g_tw;
-  mutable bool grid_ready = false;
+  mutable DBuf g_Cf, g_Xf, g_twf;  // FP32 copies for the inner GMRES products
+  mutable bool grid_ready = false, grid_f32_ready = false;
   int mv_ntile = 0;
   DBuf d_mv_ts, d_mv_te, d_mv_sb, d_mv_se;
   // rank proposal: the network (borrowed during rss_factor only), the
@@ -2316,9 +2317,11 @@ static void do_sweeps(const Factor<T> &F, const double *in, double *out, int nrh
   }
 }
 
-template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs);
+template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs, bool f32);
 
-template <typename T> static void apply_A(const Factor<T> &F, const double *x, double *y, int nrhs) {
+// y = A x in FP64 (f32: the kernel sums or the FFT convolution in FP32, for
+// the inner GMRES of the refinement; y is FP64 either way)
+template <typename T> static void apply_A(const Factor<T> &F, const double *x, double *y, int nrhs, bool f32 = false) {
   // FP64 flops of the FFT operator (the work of this class): per pair of
   // right-hand sides a forward and an inverse transform over the lines the
   // zero padding leaves (along axis a, the lines whose coordinates before a
@@ -2337,12 +2340,12 @@ template <typename T> static void apply_A(const Factor<T> &F, const double *x, d
     }
     fl = (double)((nrhs + 1) / 2) * (2.0 * lines * 5.0 * L * std::log2(L) + 6.0 * vol);
   }
-  int pi = F.prof.begin(KC_REFINE_OP, F.st, 0, 0, nrhs, 0.0, fl);
-  apply_A_impl(F, x, y, nrhs);
+  int pi = F.prof.begin(f32 ? KC_INNER_OP : KC_REFINE_OP, F.st, 0, 0, nrhs, 0.0, fl);
+  apply_A_impl(F, x, y, nrhs, f32);
   F.prof.end(pi, F.st);
 }
 
-template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs) {
+template <typename T> static void apply_A_impl(const Factor<T> &F, const double *x, double *y, int nrhs, bool f32) {
   if (F.grid_side > 0) {
     if (!F.grid_ready) {
       GridOp &G = F.G;
@@ -2370,7 +2373,24 @@ template <typename T> static void apply_A_impl(const Factor<T> &F, const double 
       check_launch("grid operator setup");
       F.grid_ready = true;
     }
-    grid_op_apply(F.G, x, y, nrhs, F.st);
+    if (f32 && !F.grid_f32_ready) {
+      GridOp &G = F.G;
+      int64_t tot = 1;
+      for (int d = 0; d < G.dim; d++) tot *= G.L;
+      F.g_Cf.alloc(sizeof(float2) * tot, F.st);
+      F.g_Xf.alloc(sizeof(float2) * tot, F.st);
+      F.g_twf.alloc(sizeof(float2) * G.L, F.st);
+      G.Cf = ptr<float2>(F.g_Cf);
+      G.Xf = ptr<float2>(F.g_Xf);
+      G.twf = ptr<float2>(F.g_twf);
+      grid_op_setup_f32(G, F.st);
+      check_launch("grid operator setup (FP32)");
+      F.grid_f32_ready = true;
+    }
+    grid_op_apply(F.G, x, y, nrhs, F.st, f32);
+  } else if (f32) {
+    launch_matvec_f32(F.P, F.K, ptr<int64_t>(F.d_perm), x, y, F.n, nrhs, F.mv_ntile, ptr<int64_t>(F.d_mv_ts),
+                      ptr<int64_t>(F.d_mv_te), ptr<int64_t>(F.d_mv_sb), ptr<int64_t>(F.d_mv_se), F.st);
   } else {
     launch_matvec(ptr<double>(F.d_x), F.dim, F.K, F.P.wdof, ptr<int64_t>(F.d_perm), x, y, F.n, nrhs, F.mv_ntile,
                   ptr<int64_t>(F.d_mv_ts), ptr<int64_t>(F.d_mv_te), ptr<int64_t>(F.d_mv_sb), ptr<int64_t>(F.d_mv_se),
@@ -2382,7 +2402,11 @@ template <typename T> static void apply_A_impl(const Factor<T> &F, const double 
 // GMRES-based iterative refinement (Carson & Higham): FP64 residuals with
 // the exact operator, each correction from restarted, right-preconditioned
 // FGMRES in FP64 whose preconditioner is the factor's solve (FP32 for the
-// mixed factor).  All right-hand sides advance in lock step.
+// mixed factor).  For the mixed factor the operator products inside FGMRES
+// are FP32 (kernel sums or FFT convolution accurate to FP32 rounding, FP64
+// vectors): the correction only needs relative accuracy well below 1, and
+// the next FP64 residual measures what it achieved.  All right-hand sides
+// advance in lock step.
 template <typename T>
 static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
                    double *relres) {
@@ -2446,7 +2470,7 @@ static bool refine(const Factor<T> &F, const double *b, double *x, int nrhs, dou
     int jdone = 0;
     for (int j = 0; j < m; j++) {
       do_sweeps(F, pV + j * nn, pZ + j * nn, nrhs, true, false);
-      apply_A(F, pZ + j * nn, pw, nrhs);
+      apply_A(F, pZ + j * nn, pw, nrhs, std::is_same<T, float>::value);
       std::vector<double> hh, hh2, hn;
       dots(pV, j + 1, pw, hh);  // hh[c * (j+1) + i]
       std::vector<double> neg(hh.size());
@@ -3217,7 +3241,8 @@ rss_status rss_stats_json(const rss_factorization *f, char *buf, size_t *nbytes)
       // kernel-class times when the factor was created with profiling
       const Prof &P = F.prof;
       static const char *cls[KC_N] = {"assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve",
-                                      "permute", "host_tree", "host_level", "host_wait", "residual_operator"};
+                                      "permute", "host_tree", "host_level", "host_wait", "residual_operator",
+                                      "inner_operator"};
       js += "\"profile_ms\": {";
       for (int c = 0; c < KC_N; c++) num(cls[c], P.ms[c], c + 1 < KC_N);
       js += "}}";

@@ -179,6 +179,13 @@ void launch_permute(int dir, const int64_t *perm, const double *in, T *out_or_in
 void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const double *wdof, const int64_t *perm,
                    const double *xin, double *yout, int64_t n, int nrhs, int ntile, const int64_t *tstart,
                    const int64_t *tend, const int64_t *sbeg, const int64_t *send, cudaStream_t st);
+// The same product with the kernel evaluated and summed in FP32 (the
+// points' distances from their depth-20 cells and offsets, as the FP32
+// factor's blocks; each tile of 256 sources summed in FP32, the tiles in
+// FP64): the operator of the inner GMRES of the refinement.
+void launch_matvec_f32(const Points &P, const KernelParams &K, const int64_t *perm, const double *xin,
+                       double *yout, int64_t n, int nrhs, int ntile, const int64_t *tstart, const int64_t *tend,
+                       const int64_t *sbeg, const int64_t *send, cudaStream_t st);
 
 // FP64 operator x -> A x for points on an s^d grid of cell centres, by FFT
 // convolution on the circulant of side L = 2s (refine.cu).
@@ -191,9 +198,13 @@ struct GridOp {
   double2 *C = nullptr;           // spectrum of the embedded kernel
   double2 *X = nullptr;           // work
   double2 *tw = nullptr;          // twiddles
+  float2 *Cf = nullptr, *Xf = nullptr, *twf = nullptr;  // the same in FP32 (inner products of GMRES-IR)
 };
 void grid_op_setup(GridOp &G, cudaStream_t st);
-void grid_op_apply(const GridOp &G, const double *x, double *y, int nrhs, cudaStream_t st);
+// Cf and twf rounded from C and tw (after grid_op_setup; Cf, Xf, twf allocated by the caller)
+void grid_op_setup_f32(GridOp &G, cudaStream_t st);
+// y = A x for nrhs columns; f32: the transforms in FP32 (y still FP64)
+void grid_op_apply(const GridOp &G, const double *x, double *y, int nrhs, cudaStream_t st, bool f32);
 void multidot(const double *V, int64_t vstride, int nv, const double *w, int64_t n, int nrhs, double *part,
               double *out, cudaStream_t st);
 void combine(double *y, double alpha, const double *V, int64_t vstride, int nv, const double *coef, int64_t n,

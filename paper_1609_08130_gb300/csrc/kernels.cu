@@ -4440,17 +4440,50 @@ void launch_permute(int dir, const int64_t *perm, const double *in, T *tv, doubl
   k_permute<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dir, perm, in, tv, out, n, nrhs); count_launch();
 }
 
+// Natural logarithm by Tang's table-driven method (P. T. P. Tang, ACM Trans.
+// Math. Softw. 16(4), 1990): x = 2^e m with m in [1, 2) read from the bits;
+// c = 1 + (2k + 1) / 256 is the centre of m's interval of width 1/128 (k
+// the top 7 bits of m's fraction), so log x = e ln 2 + log c + log(1 + t)
+// with t = (m - c) / c, |t| < 2^-8 (m - c is exact); log(1 + t) is its
+// Taylor series to t^6 (the first term left out is below 2^-58).
+// tab[k] = (1 / c, log c).  The absolute error is a few units of 2^-53
+// times max(1, |log x|).  Zero, negative, subnormal and non-finite x take
+// log() itself.
+__device__ __forceinline__ double log_tab(double x, const double2 *tab) {
+  const long long u = __double_as_longlong(x);
+  const int ef = (int)((u >> 52) & 0x7ff);
+  if (!(x > 0.0) || ef == 0 || ef == 0x7ff) return log(x);
+  const int k = (int)((u >> 45) & 127);
+  const double m = __longlong_as_double((u & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  const double c = 1.0 + (double)(2 * k + 1) * (1.0 / 256.0);
+  const double2 fl = tab[k];
+  const double t = (m - c) * fl.x;
+  // log(1 + t) = t + t^2 (-1/2 + t/3 - t^2/4 + t^3/5 - t^4/6)
+  double qv = fma(t, -1.0 / 6.0, 1.0 / 5.0);
+  qv = fma(t, qv, -0.25);
+  qv = fma(t, qv, 1.0 / 3.0);
+  qv = fma(t, qv, -0.5);
+  const double l1p = fma(t * t, qv, t);
+  return fma((double)(ef - 1023), 0.69314718055994530942, fl.y + l1p);
+}
+
 // Exact FP64 y = A x by direct summation (tree-ordered points, caller-order
 // vectors through perm), for one or several independent problems: tile q
 // covers targets [tstart[q], tend[q]) of a problem whose DOFs are
 // [sbeg[q], send[q]); sources are staged in shared memory.  Each point's
-// weight comes from wdof (or K.w).
+// weight comes from wdof (or K.w).  The 2D kernel's logarithm is log_tab's.
 __global__ void __launch_bounds__(256) k_matvec(const double *xt, int dim, KernelParams K, const double *wdof,
                                                 const int64_t *perm, const double *xin, double *yout, int64_t n,
                                                 int nrhs, const int64_t *tstart, const int64_t *tend,
                                                 const int64_t *sbeg, const int64_t *send) {
   __shared__ double sp[256 * 3];
   __shared__ double sx[256 * 4];
+  __shared__ double2 s_logtab[128];
+  if (threadIdx.x < 128) {
+    const double c = 1.0 + (double)(2 * threadIdx.x + 1) * (1.0 / 256.0);
+    s_logtab[threadIdx.x] = make_double2(1.0 / c, log(c));
+  }
+  __syncthreads();
   const int q = blockIdx.x;
   const int64_t i = tstart[q] + threadIdx.x;
   const bool live = i < tend[q];
@@ -4484,7 +4517,7 @@ __global__ void __launch_bounds__(256) k_matvec(const double *xt, int dim, Kerne
             double z = xi[d] - sp[qq * 3 + d];
             r2 += z * z;
           }
-          a = w * kof(K.kind, r2);
+          a = w * (K.kind == 0 ? -log_tab(r2, s_logtab) * (1.0 / (4.0 * kPi)) : (1.0 / (4.0 * kPi)) / sqrt(r2));
         }
         for (int c = 0; c < nc; c++) acc[c] += a * sx[qq * 4 + c];
       }
@@ -4501,6 +4534,68 @@ void launch_matvec(const double *x_tree, int dim, const KernelParams &K, const d
   if (n == 0 || ntile == 0) return;
   dim3 g((unsigned)ntile, (nrhs + 3) / 4);
   k_matvec<<<g, 256, 0, st>>>(x_tree, dim, K, wdof, perm, xin, yout, n, nrhs, tstart, tend, sbeg, send);
+  count_launch();
+}
+
+// y = A x with the kernel evaluated in FP32 (tiles as k_matvec; the
+// sources' depth-20 cells and offsets staged in shared memory; each tile's
+// 256 terms summed in FP32, the tiles' sums in FP64).
+__global__ void __launch_bounds__(256) k_matvec_f32(Points P, int kind, float wk, float diag, const int64_t *perm,
+                                                    const double *xin, double *yout, int64_t n, int nrhs,
+                                                    const int64_t *tstart, const int64_t *tend,
+                                                    const int64_t *sbeg, const int64_t *send) {
+  __shared__ int sc[256 * 3];
+  __shared__ float so[256 * 3];
+  __shared__ float sx[256 * 4];
+  const int q = blockIdx.x, dim = P.dim;
+  const int64_t i = tstart[q] + threadIdx.x;
+  const bool live = i < tend[q];
+  const int64_t j0b = sbeg[q], j1b = send[q];
+  const int cb = blockIdx.y * 4;
+  const int nc = min(4, nrhs - cb);
+  int ci[3] = {0, 0, 0};
+  float oi[3] = {0.f, 0.f, 0.f};
+  float w = wk;
+  if (live) {
+    for (int d = 0; d < dim; d++) ci[d] = P.cell[3 * i + d], oi[d] = P.off[3 * i + d];
+    if (P.wdof) w = (float)P.wdof[i];
+  }
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t j0 = j0b; j0 < j1b; j0 += 256) {
+    const int64_t j = j0 + threadIdx.x;
+    if (j < j1b) {
+      for (int d = 0; d < dim; d++) sc[threadIdx.x * 3 + d] = P.cell[3 * j + d], so[threadIdx.x * 3 + d] = P.off[3 * j + d];
+      for (int c = 0; c < nc; c++) sx[threadIdx.x * 4 + c] = (float)xin[perm[j] + (int64_t)(cb + c) * n];
+    }
+    __syncthreads();
+    const int lim = (int)min((int64_t)256, j1b - j0);
+    if (live) {
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+      const int self = (i >= j0 && i < j0 + lim) ? (int)(i - j0) : -1;
+      for (int qq = 0; qq < lim; qq++) {
+        float r2 = 0.f;
+        for (int d = 0; d < dim; d++) {
+          const float z = fmaf((float)(ci[d] - sc[qq * 3 + d]), P.D, oi[d] - so[qq * 3 + d]);
+          r2 = fmaf(z, z, r2);
+        }
+        const float a = qq == self ? diag : w * kof(kind, r2);
+        for (int c = 0; c < nc; c++) t[c] = fmaf(a, sx[qq * 4 + c], t[c]);
+      }
+      for (int c = 0; c < nc; c++) acc[c] += (double)t[c];
+    }
+    __syncthreads();
+  }
+  if (live)
+    for (int c = 0; c < nc; c++) yout[perm[i] + (int64_t)(cb + c) * n] = acc[c];
+}
+
+void launch_matvec_f32(const Points &P, const KernelParams &K, const int64_t *perm, const double *xin,
+                       double *yout, int64_t n, int nrhs, int ntile, const int64_t *tstart, const int64_t *tend,
+                       const int64_t *sbeg, const int64_t *send, cudaStream_t st) {
+  if (n == 0 || ntile == 0) return;
+  dim3 g((unsigned)ntile, (nrhs + 3) / 4);
+  k_matvec_f32<<<g, 256, 0, st>>>(P, K.kind, (float)K.w, (float)K.diag, perm, xin, yout, n, nrhs, tstart, tend,
+                                  sbeg, send);
   count_launch();
 }
 

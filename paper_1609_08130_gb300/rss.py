@@ -404,7 +404,7 @@ class Factorization:
         return feat, rank
 
     PROFILE_CLASSES = ["assemble", "id", "elim", "schur", "top_lu", "sweep", "top_solve", "permute",
-                       "host_tree", "host_level", "host_wait", "refine_op"]
+                       "host_tree", "host_level", "host_wait", "refine_op", "inner_op"]
 
     def profile(self, reset: bool = False) -> dict:
         """Per-kernel-class {launches, ms, bytes, flops} (needs profile=True)."""

@@ -133,6 +133,22 @@ def test_matvec_matches_oracle(pkg):
     assert np.allclose(y, oracle.matvec(pts, 1, x), rtol=1e-12, atol=1e-14)
 
 
+def test_matvec_log_kernel_matches_oracle(pkg):
+    """The FP64 direct sum of the 2D kernel (its logarithm table-driven)
+    against the oracle's numpy sum, on points whose squared distances span
+    about 1e-10 to 50: a tight cluster, the unit square and a few points out
+    to distance 7."""
+    pts = np.concatenate([inputs.random_points(9, 1500, 2),
+                          0.5 + 3e-4 * inputs.normal(41, 400).reshape(200, 2),
+                          5.0 * inputs.random_points(42, 100, 2)])
+    n = len(pts)
+    f = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64)
+    x = inputs.rhs(6, n, 3)
+    y = f.matvec(_cuda(x)).cpu().numpy()
+    ref = oracle.matvec(pts, 0, x)
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max(), np.abs(y - ref).max()
+
+
 def test_degenerate_sizes(pkg):
     # below one leaf: no skeletonization, F is the dense LU
     pts = inputs.random_points(2, 50, 2)
@@ -193,6 +209,25 @@ def test_refined_solve_reaches_tolerance(pkg, case, prec):
     true_rel = max(np.linalg.norm(r[c]) / np.linalg.norm(b[c]) for c in range(4))
     assert rel <= 1e-10 and true_rel <= 2e-10, (rel, true_rel, iters)
     assert iters <= 10
+
+
+@pytest.mark.parametrize("case", ["grid2d", "random2d"])
+def test_inner_operator_products_fp32_for_the_mixed_factor(pkg, case):
+    """GMRES-IR around a FP32 factor takes the operator products inside its
+    GMRES in FP32 (FFT convolution on a grid, direct sum otherwise) and its
+    residuals in FP64; around a FP64 factor both stay FP64.  Either way the
+    oracle's exact matvec confirms the 1e-10 residual."""
+    pts = inputs.grid_points(64, 2) if case == "grid2d" else inputs.random_points(13, 3000, 2)
+    b = inputs.rhs(5, len(pts), 2)
+    for prec in (pkg.MIXED, pkg.FP64):
+        f = pkg.Factorization(_cuda(pts), 0, 1e-6, leaf=64, prec=prec, profile=True)
+        x, iters, rel = f.solve_refined(_cuda(b), tol=1e-10, maxit=10)
+        p = f.profile()
+        assert rel <= 1e-10 and iters >= 1, (rel, iters)
+        assert p["refine_op"]["launches"] >= 2
+        assert p["inner_op"]["launches"] == (iters if prec == pkg.MIXED else 0), (p["inner_op"], iters)
+        r = b - oracle.matvec(pts, 0, x.cpu().numpy())
+        assert max(np.linalg.norm(r[c]) / np.linalg.norm(b[c]) for c in range(2)) <= 2e-10
 
 
 @pytest.mark.parametrize("case", ["grid2d_4096", "grid3d"])
