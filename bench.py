@@ -310,8 +310,8 @@ def run_reference(args, rank, world):
 NCU_TRAFFIC = {
     # the ID's DRAM bytes per launch of the 512^2 step: an ncu capture of
     # every ID launch of the 256^2 step, scaled by box count per depth
-    "id": {"bytes_per_launch": 56.3e6,
-           "kernels_sha256": "72221df3b13b6f3e6c03f4c0b1b0b5c05cd136a2e5c5e932f4c47ace8be9f097"},
+    "id": {"bytes_per_launch": 56.5e6,
+           "kernels_sha256": "3e66be0d3fe8772e68a90fd23c3b4946803be00fcfab3d15f4751be148abde01"},
 }
 
 
