@@ -2292,9 +2292,9 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
 }
 
 // ---------------------------------------------------------------------------
-// Elimination, shared-memory form for b small enough: the LU of X_RR is
-// computed by one warp (no block barriers), X_RR^{-1} = U^{-1} L^{-1} P is
-// formed column by column from the LU factors, and E = X_JR X_RR^{-1},
+// Elimination, shared-memory form for b small enough: the LU of X_RR and
+// X_RR^{-1} = U^{-1} L^{-1} P are formed by the whole CTA, one rank-1
+// update per step (warp 0 picks each pivot), and E = X_JR X_RR^{-1},
 // G = X_RR^{-1} X_RJ are produced in chunks of CH rows / columns of J as
 // shared-memory products, written coalesced.  X_RJ is kept in the scratch
 // for the Schur update.
@@ -2541,11 +2541,14 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   }
   __syncthreads();
   if (cta == 0) {
-  // LU with partial pivoting by warp 0 (largest |entry|, ties to the lowest row)
-  if (warp == 0) {
-    for (int i = lane; i < r; i += 32) spiv[i] = i;
-    __syncwarp();
-    for (int j = 0; j < r; j++) {
+  // LU with partial pivoting (largest |entry|, ties to the lowest row): per
+  // column, warp 0 picks the pivot, swaps the rows and scales the column;
+  // then every warp takes rows of the rank-1 update, its lanes 32
+  // consecutive columns
+  for (int i = tid; i < r; i += NT) spiv[i] = i;
+  __syncthreads();
+  for (int j = 0; j < r; j++) {
+    if (warp == 0) {
       T best = (T)-1;
       int bi = r;
       for (int i = j + lane; i < r; i += 32) {
@@ -2584,37 +2587,14 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
       __syncwarp();
       const T d = LU[j * ldl + j];
       for (int i = j + 1 + lane; i < r; i += 32) LU[i * ldl + j] /= d;
-      __syncwarp();
-      // rank-1 update: this lane's columns of the pivot row stay in registers,
-      // rows are taken four at a time (loads before stores)
-      const int c0 = j + 1 + lane, c1 = c0 + 32, c2 = c0 + 64, c3 = c0 + 96;
-      const T p0 = c0 < r ? LU[j * ldl + c0] : (T)0, p1 = c1 < r ? LU[j * ldl + c1] : (T)0;
-      const T p2 = c2 < r ? LU[j * ldl + c2] : (T)0, p3 = c3 < r ? LU[j * ldl + c3] : (T)0;
-      for (int i = j + 1; i < r; i += 4) {
-        T l[4], x[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int ii = i + u < r ? i + u : j;  // j: harmless dummy row (never stored)
-          l[u] = LU[ii * ldl + j];
-          x[u][0] = c0 < r ? LU[ii * ldl + c0] : (T)0;
-          x[u][1] = c1 < r ? LU[ii * ldl + c1] : (T)0;
-          x[u][2] = c2 < r ? LU[ii * ldl + c2] : (T)0;
-          x[u][3] = c3 < r ? LU[ii * ldl + c3] : (T)0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          if (i + u >= r) break;
-          const int ii = i + u;
-          if (c0 < r) LU[ii * ldl + c0] = x[u][0] - l[u] * p0;
-          if (c1 < r) LU[ii * ldl + c1] = x[u][1] - l[u] * p1;
-          if (c2 < r) LU[ii * ldl + c2] = x[u][2] - l[u] * p2;
-          if (c3 < r) LU[ii * ldl + c3] = x[u][3] - l[u] * p3;
-        }
-      }
-      __syncwarp();
     }
+    __syncthreads();
+    for (int i = j + 1 + warp; i < r; i += NT / 32) {
+      const T l = LU[i * ldl + j];
+      for (int cc = j + 1 + lane; cc < r; cc += 32) LU[i * ldl + cc] = LU[i * ldl + cc] - l * LU[j * ldl + cc];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = tid; i < r; i += NT) spinv[spiv[i]] = i;
   for (int e = tid; e < r * r; e += NT) {
     int qi, ri;
@@ -2623,37 +2603,38 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   }
   for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
   __syncthreads();
-  // X_RR^{-1} = U^{-1} L^{-1} P: column cc is U^{-1} L^{-1} e_{pinv[cc]}
-  // (four partial sums per dot product to shorten the dependence chains)
-  for (int cc = tid; cc < r; cc += NT) {
-    T *x = Xi + (size_t)cc * ldx;
-    const int i0 = spinv[cc];
-    for (int i = 0; i < r; i++) {
-      const T *Li = LU + i * ldl;
-      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
-      int l = i0;  // x[l] = 0 for l < i0
-      for (; l + 3 < i; l += 4) {
-        s0 += Li[l] * x[l];
-        s1 += Li[l + 1] * x[l + 1];
-        s2 += Li[l + 2] * x[l + 2];
-        s3 += Li[l + 3] * x[l + 3];
-      }
-      for (; l < i; l++) s0 += Li[l] * x[l];
-      x[i] = (i == i0 ? (T)1 : (T)0) - ((s0 + s1) + (s2 + s3));
+  // X_RR^{-1} = U^{-1} L^{-1} P for all columns at once: X = P (column cc
+  // is e_{pinv[cc]}); forward, step l subtracts L(i, l) times row l from
+  // every row i > l; backward, step l subtracts U(i, l) times row l from
+  // every row i < l, after which row l - 1 is complete and divided by its
+  // diagonal.  A step is a rank-1 update shared by the warps (rows) and
+  // their lanes (columns), one barrier apart.
+  for (int e = tid; e < r * r; e += NT) {
+    int cc, i;
+    fdr.divmod(e, cc, i);
+    Xi[i + (size_t)cc * ldx] = i == spinv[cc] ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  for (int l = 0; l + 1 < r; l++) {
+    for (int i = l + 1 + warp; i < r; i += NT / 32) {
+      const T li = LU[i * ldl + l];
+      for (int cc = lane; cc < r; cc += 32) Xi[i + (size_t)cc * ldx] -= li * Xi[l + (size_t)cc * ldx];
     }
-    for (int i = r - 1; i >= 0; i--) {
-      const T *Ui = LU + i * ldl;
-      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
-      int l = i + 1;
-      for (; l + 3 < r; l += 4) {
-        s0 += Ui[l] * x[l];
-        s1 += Ui[l + 1] * x[l + 1];
-        s2 += Ui[l + 2] * x[l + 2];
-        s3 += Ui[l + 3] * x[l + 3];
+    __syncthreads();
+  }
+  if (r > 0)
+    for (int cc = tid; cc < r; cc += NT) Xi[(r - 1) + (size_t)cc * ldx] /= LU[(r - 1) * ldl + (r - 1)];
+  __syncthreads();
+  for (int l = r - 1; l > 0; l--) {
+    for (int i = warp; i < l; i += NT / 32) {
+      const T ui = LU[i * ldl + l], di = LU[i * ldl + i];
+      for (int cc = lane; cc < r; cc += 32) {
+        T v = Xi[i + (size_t)cc * ldx] - ui * Xi[l + (size_t)cc * ldx];
+        if (i == l - 1) v = v / di;
+        Xi[i + (size_t)cc * ldx] = v;
       }
-      for (; l < r; l++) s0 += Ui[l] * x[l];
-      x[i] = (x[i] - ((s0 + s1) + (s2 + s3))) / Ui[i];
     }
+    __syncthreads();
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += NT) {
@@ -3234,7 +3215,7 @@ void launch_elim(const LevelDev<T> &lv, FBox<T> *boxes, const int *box_list, int
     // worst case over k + r = b of the shared-memory form
     size_t worst = 0;
     for (int r = 0; r <= bmax; r++) worst = std::max(worst, elim2_smem<T>(bmax, bmax - r, r));
-    // the warp LU keeps at most four pivot-row entries per lane: r <= 128
+    // boxes of up to 128 DOFs (wider ones take the blocked LU below)
     if (worst <= (size_t)(220 << 10) && bmax <= 128) {
       cudaFuncSetAttribute(k_elim2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)worst);
       k_elim2<T><<<nbox * C, NT, worst, st>>>(lv, boxes, box_list, scratch, scratch_stride, ovf, err, split, C);
