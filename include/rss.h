@@ -268,7 +268,8 @@ rss_status rss_sqrt_apply(const rss_factorization *f, const double *x, double *y
 /* rss_matvec -- y = A x in FP64 with the exact operator being factored:
  * an FFT convolution when the points are the cell centres of an s^dim grid
  * (s a power of two; exact up to FP64 rounding), direct summation over all
- * pairs otherwise.  Device buffers, n x nrhs column-major. */
+ * pairs otherwise (the 2D kernel's logarithm table-driven, to a few units
+ * of FP64 rounding).  Device buffers, n x nrhs column-major. */
 rss_status rss_matvec(const rss_factorization *f, const double *x, double *y, int nrhs);
 
 /* rss_sync -- wait for the factor's stream, then report an error the device

@@ -4,8 +4,8 @@
 // When the points are the cell centres of an s^d grid, K_ij = kappa(I_i - I_j)
 // depends only on the integer offset of the two cells, so K x is a discrete
 // convolution.  It is applied exactly (to FP64 rounding) by embedding the
-// kernel in a circulant of side L = 2s and using a radix-2 Stockham FFT
-// written here (one CTA per line, the line held in shared memory).  Two real
+// kernel in a circulant of side L = 2s and using a Stockham FFT written here
+// (radix-4 passes, one CTA per line, the line held in shared memory).  Two real
 // right-hand sides share one complex transform (x1 + i x2): the embedded
 // kernel is real and even, so its spectrum is real and the real and
 // imaginary parts of the product transform back to K x1 and K x2.
