@@ -311,7 +311,7 @@ NCU_TRAFFIC = {
     # the ID's DRAM bytes per launch of the 512^2 step: an ncu capture of
     # every ID launch of the 256^2 step, scaled by box count per depth
     "id": {"bytes_per_launch": 56.5e6,
-           "kernels_sha256": "b996f7ac7957ac1d0514aeea0841ba11f9053f8b0d4b15df93ea8587f45291c1"},
+           "kernels_sha256": "99f814ed756e6b283225728feb3d05a00f1215091221cac1355706e1481e9379"},
 }
 
 

@@ -2292,9 +2292,10 @@ __global__ void __launch_bounds__(NT) k_elim(LevelDev<T> lv, FBox<T> *boxes, con
 }
 
 // ---------------------------------------------------------------------------
-// Elimination, shared-memory form for b small enough: the LU of X_RR and
-// X_RR^{-1} = U^{-1} L^{-1} P are formed by the whole CTA, one rank-1
-// update per step (warp 0 picks each pivot), and E = X_JR X_RR^{-1},
+// Elimination, shared-memory form for b small enough: the LU of X_RR is
+// formed by the whole CTA, one rank-1 update per column (warp 0 picks each
+// pivot), X_RR^{-1} = U^{-1} L^{-1} P column by column from the LU factors
+// (a thread per column), and E = X_JR X_RR^{-1},
 // G = X_RR^{-1} X_RJ are produced in chunks of CH rows / columns of J as
 // shared-memory products, written coalesced.  X_RJ is kept in the scratch
 // for the Schur update.
@@ -2603,38 +2604,39 @@ __global__ void __launch_bounds__(NT) k_elim2(LevelDev<T> lv, FBox<T> *boxes, co
   }
   for (int i = tid; i < r; i += NT) fb.piv[i] = spiv[i];
   __syncthreads();
-  // X_RR^{-1} = U^{-1} L^{-1} P for all columns at once: X = P (column cc
-  // is e_{pinv[cc]}); forward, step l subtracts L(i, l) times row l from
-  // every row i > l; backward, step l subtracts U(i, l) times row l from
-  // every row i < l, after which row l - 1 is complete and divided by its
-  // diagonal.  A step is a rank-1 update shared by the warps (rows) and
-  // their lanes (columns), one barrier apart.
-  for (int e = tid; e < r * r; e += NT) {
-    int cc, i;
-    fdr.divmod(e, cc, i);
-    Xi[i + (size_t)cc * ldx] = i == spinv[cc] ? (T)1 : (T)0;
-  }
-  __syncthreads();
-  for (int l = 0; l + 1 < r; l++) {
-    for (int i = l + 1 + warp; i < r; i += NT / 32) {
-      const T li = LU[i * ldl + l];
-      for (int cc = lane; cc < r; cc += 32) Xi[i + (size_t)cc * ldx] -= li * Xi[l + (size_t)cc * ldx];
-    }
-    __syncthreads();
-  }
-  if (r > 0)
-    for (int cc = tid; cc < r; cc += NT) Xi[(r - 1) + (size_t)cc * ldx] /= LU[(r - 1) * ldl + (r - 1)];
-  __syncthreads();
-  for (int l = r - 1; l > 0; l--) {
-    for (int i = warp; i < l; i += NT / 32) {
-      const T ui = LU[i * ldl + l], di = LU[i * ldl + i];
-      for (int cc = lane; cc < r; cc += 32) {
-        T v = Xi[i + (size_t)cc * ldx] - ui * Xi[l + (size_t)cc * ldx];
-        if (i == l - 1) v = v / di;
-        Xi[i + (size_t)cc * ldx] = v;
+  // X_RR^{-1} = U^{-1} L^{-1} P: column cc is U^{-1} L^{-1} e_{pinv[cc]}
+  // (four partial sums per dot product to shorten the dependence chains;
+  // one thread per column measured faster than the whole CTA taking a
+  // rank-1 update per row step)
+  for (int cc = tid; cc < r; cc += NT) {
+    T *x = Xi + (size_t)cc * ldx;
+    const int i0 = spinv[cc];
+    for (int i = 0; i < r; i++) {
+      const T *Li = LU + i * ldl;
+      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+      int l = i0;  // x[l] = 0 for l < i0
+      for (; l + 3 < i; l += 4) {
+        s0 += Li[l] * x[l];
+        s1 += Li[l + 1] * x[l + 1];
+        s2 += Li[l + 2] * x[l + 2];
+        s3 += Li[l + 3] * x[l + 3];
       }
+      for (; l < i; l++) s0 += Li[l] * x[l];
+      x[i] = (i == i0 ? (T)1 : (T)0) - ((s0 + s1) + (s2 + s3));
     }
-    __syncthreads();
+    for (int i = r - 1; i >= 0; i--) {
+      const T *Ui = LU + i * ldl;
+      T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+      int l = i + 1;
+      for (; l + 3 < r; l += 4) {
+        s0 += Ui[l] * x[l];
+        s1 += Ui[l + 1] * x[l + 1];
+        s2 += Ui[l + 2] * x[l + 2];
+        s3 += Ui[l + 3] * x[l + 3];
+      }
+      for (; l < r; l++) s0 += Ui[l] * x[l];
+      x[i] = (x[i] - ((s0 + s1) + (s2 + s3))) / Ui[i];
+    }
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += NT) {
