@@ -41,3 +41,37 @@ def test_free_is_null_safe_and_errors_are_reported():
     assert b"bad arguments" in L.rss_last_error()
     st = L.rss_build_tree(None, 10, 4, 64, ctypes.byref(h))
     assert st == rss.RSS_EINVAL
+
+
+def test_autotune_table_host_api():
+    """The autotuner's table is host state: a shape is accepted for a key
+    exactly when it is a candidate for the key's box-width class (the rule
+    the binding's shape_fits states, plus several CTAs per box at width 256
+    only with two threads per column), the table returns what was set with
+    the candidate timings zero (nothing timed), and clearing empties it."""
+    from paper_1609_08130_gb300 import rss
+    L = rss.lib()
+    L.rss_autotune_clear()
+    try:
+        want = {}
+        for width in (64, 128, 256):
+            for cls, (tpc, g, ctas, rows) in enumerate(rss.AUTOTUNE_SHAPES):
+                ok = rss.shape_fits(width, tpc, g, rows) and not (width == 256 and ctas > 1 and tpc != 2)
+                st = L.rss_autotune_set(8, width, cls, tpc, g, ctas, rows)
+                assert st == (rss.RSS_OK if ok else rss.RSS_EINVAL), (width, tpc, g, ctas, rows, st)
+                if ok:
+                    want[(8, width, cls)] = (tpc, g, ctas, rows)
+        assert L.rss_autotune_set(3, 64, 0, 1, 1, 1, 1) == rss.RSS_EINVAL  # element size
+        assert L.rss_autotune_set(4, 96, 0, 1, 1, 1, 1) == rss.RSS_EINVAL  # width class
+        assert L.rss_autotune_set(4, 64, 41, 1, 1, 1, 1) == rss.RSS_EINVAL  # phase class
+        got = {(t["elem_bytes"], t["width"], t["phase_class"]): (t["tpc"], t["groups"], t["ctas"], t["rows"])
+               for t in rss.autotune_table()}
+        assert got == want
+        assert all(u == 0 for t in rss.autotune_table() for u in t["us"])
+        nb = ctypes.c_size_t(4)
+        buf = (ctypes.c_int32 * 1)()
+        assert L.rss_autotune_table(buf, ctypes.byref(nb)) == rss.RSS_EINVAL  # buffer too small
+        assert nb.value == 4 * len(want) * (7 + len(rss.AUTOTUNE_SHAPES))
+    finally:
+        L.rss_autotune_clear()
+    assert rss.autotune_table() == [] and rss.autotune_elim_table() == []
